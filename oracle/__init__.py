@@ -1,0 +1,27 @@
+"""CPU oracle for the element-based convex limited CG-WENO stage.
+
+TEST INFRASTRUCTURE ONLY: a plain, slow FP64 implementation written from
+the paper (Kuzmin, Hajduk, Vedral, arXiv 2509.04673).  Only tests/,
+__graft_entry__.smoke() and the cpu_baseline / reference legs of bench.py
+may import it.  It shares no code with the CUDA path: the library never
+imports, links or calls anything here.
+
+Parity status per function (what pins it, tests/test_oracle_*.py):
+  tables.tables          exact rationals; pinned by partition of unity,
+                         closed-form mass entries, derivative identities
+  scheme.cell_averages   pinned by conservation / LO finite-volume identity
+  scheme.low_order_facets, pseudo_time_steps
+                         pinned by the LO finite-volume identity and IDP
+  scheme.sensor          pinned by special cases (constant, linear and
+                         polynomial data give gamma = 1) and a brute-force
+                         semi-norm; the candidate construction is a reading
+  scheme.gradient_projection
+                         pinned against a dense consistent-mass solve
+  scheme.element_residual, fe_stage
+                         pinned by brute-force global assembly (Theorem of
+                         Sec. 4: MCL with alpha = beta = 1 equals CG-WENO),
+                         zero-sum, conservation, free stream, dt_e
+                         independence and the p+1 convergence rate
+  scheme.flux_limit, slope_limit, euler_alpha
+                         pinned by IDP invariants and closed-form cases
+"""
