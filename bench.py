@@ -1,0 +1,394 @@
+#!/usr/bin/env python3
+"""Benchmark of the explicit SSP-RK stage of the element-based convex-limited
+CG-WENO scheme on one GB300 (per rank), printing one JSON line.
+
+Workload: the KPP problem (f(u) = (sin u, cos u), Sec. 5.4.2 of the paper) on
+a 256 x 256 mesh of Bernstein Q2 elements, fixed boundary state pi/4,
+WENO-L with the flux limiter.  A step is one SSP-RK3 time step (three
+stages of the whole hot path plus the global time-step reduction); the
+metric counts DOF-stage updates: N_dof x 3 per step.
+
+  value    FP32-mixed form, inputs resident in HBM, CUDA events around each
+           timed step on the state's stream, L2 flushed between timed steps
+  fp64     the FP64 plain form, same protocol
+  e2e      the same metric through the C ABI with host buffers: set_state
+           (host -> device), one step, get_state (device -> host) per step
+  roofline dominant kernel of the mixed step: algorithmic bytes per launch
+           / its average event-timed duration, against the measured HBM peak
+  cpu_baseline  the FP64 oracle, single thread, on a bounded sample
+
+`--impl reference` times the oracle instead (host cores, bounded sample).
+Multi-GPU (torchrun): every rank runs an independent replica of the mesh
+(no data-path collective; the single-mesh path is replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "DOF-stage updates/s (FP32-mixed vs FP64 plain, same GB300); % of HBM roofline"
+UNIT = "DOF-stage/s"
+WORKLOAD = dict(name="kpp_256x256_q2", nx=256, ny=256, p=2)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cgl", choices=["cgl", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=6)
+    return ap.parse_args()
+
+
+def workload():
+    import inputs
+    return inputs.kpp_config(WORKLOAD["nx"], WORKLOAD["ny"], WORKLOAD["p"])
+
+
+def n_dof(mesh, nc=1):
+    return nc * mesh.nnx * mesh.nny
+
+
+# --------------------------------------------------------------------------
+# oracle timing (cpu_baseline leg and the reference arm)
+# --------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import sys, time, json
+sys.path.insert(0, {root!r})
+import inputs, oracle.scheme as S
+mesh, prob, u0 = inputs.kpp_config({nx}, {ny}, {p})
+om = S.OracleMesh(mesh)
+S.run(om, prob, u0, 1)                      # warm-up (tables, caches)
+t0 = time.perf_counter()
+u, t, st = S.run(om, prob, u0, {steps})
+dt = time.perf_counter() - t0
+print(json.dumps(dict(seconds=dt, steps={steps}, violations=st["violations"])))
+"""
+
+
+def time_oracle(steps):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET.format(root=ROOT, nx=WORKLOAD["nx"], ny=WORKLOAD["ny"], p=WORKLOAD["p"],
+                                 steps=steps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr)
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    mesh, _, _ = workload()
+    res["value"] = n_dof(mesh) * 3 * steps / res["seconds"]
+    res["cores"] = 1
+    res["sample"] = (f"{steps} SSP-RK3 steps of {WORKLOAD['name']} (FP64 oracle, numpy, "
+                     f"single thread), after one warm-up step")
+    return res
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes per launch of each kernel (minimum traffic of its inputs
+# and outputs; element vectors are (p+1)^2 values per element)
+# --------------------------------------------------------------------------
+def algorithmic_bytes(kernel, mesh, nc, rsz, k_g, k_u):
+    NN = mesh.nnx * mesh.nny
+    E = mesh.nx * mesh.ny
+    N2 = (mesh.p + 1) ** 2
+    d = 8
+    b = {
+        "k_avg": nc * NN * rsz + (3 * nc + 1) * E * d,
+        "k_pre": nc * NN * rsz + (3 * nc + 1) * E * d + (nc + 3) * E * d,
+        "k_grad_ev": nc * NN * rsz + E * N2 * 2 * nc * rsz,
+        "k_res_ev": 3 * nc * NN * rsz + 2 * E * d + E * N2 * nc * rsz,
+        "k_update_ev": 2 * nc * NN * rsz + (5 * nc + 1) * E * d + E * N2 * nc * rsz
+                       + E * N2 * nc * d + (nc + 1) * E * d,
+        "k_final": E * N2 * nc * d + 2 * nc * NN * rsz,
+    }
+    # gathers / sweeps / mass products average over their two field widths
+    nv_avg = (2 * nc * (1 + k_g) + nc * (1 + k_u)) / max(1, (1 + k_g) + (1 + k_u))
+    b["k_gather_init"] = E * N2 * nv_avg * rsz + 2 * nv_avg * NN * rsz
+    nvm = (2 * nc * k_g + nc * k_u) / max(1, k_g + k_u)
+    b["k_mass_ev"] = nvm * NN * rsz + E * N2 * nvm * rsz
+    b["k_gather_sweep"] = E * N2 * nvm * rsz + 3 * nvm * NN * rsz
+    return b.get(kernel)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+# ncu dram bytes per launch (read + write) of the dominant kernels, from the
+# captures summarised under profiles/ (None until captured for this kernel)
+NCU_TRAFFIC = {}
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    from paper_2509_04673_gb300 import build, cgl
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world > 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    mesh_d, prob, u0 = workload()
+    nd = n_dof(mesh_d)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def make(prec):
+        m = cgl.Mesh(mesh_d)
+        st = cgl.State(m, 1, prec, stream=stream.cuda_stream)
+        st.set_problem(prob)
+        st.set_state(u0)
+        st.set_time(0.0)
+        return m, st
+
+    def timed(st, K, W, sampler=None):
+        info = st.step(W)
+        assert info["violations"] == 0, info
+        c0 = st.counters()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = []
+        ctx = sampler if sampler is not None else _Null()
+        with ctx:
+            for _ in range(K):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                st.step_async(1)
+                b.record(stream)
+                evs.append((a, b))
+            torch.cuda.synchronize()
+        info = st.counters()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        if dist:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        info = {k: info[k] - c0[k] for k in info}
+        return ms, info
+
+    K, W = args.steps, args.warmup
+    # FP32-mixed (headline) -----------------------------------------------
+    m32, st32 = make(cgl.FP32_MIXED)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    smi_index = vis.split(",")[local] if vis else str(local)
+    sampler = ClockSampler(smi_index)
+    ms32, info32 = timed(st32, K, W, sampler)
+    launches = st32.launches_per_step()
+    prof = st32.profile(min(K, 20))
+    # FP64 plain -----------------------------------------------------------
+    m64, st64 = make(cgl.FP64)
+    ms64, info64 = timed(st64, K, W)
+    prof64 = st64.profile(min(K, 10))
+    # end-to-end through the C ABI with host buffers ------------------------
+    host_in = torch.empty(u0.size, dtype=torch.float64, pin_memory=True).numpy().reshape(u0.shape)
+    host_in[...] = u0
+    st32.set_time(0.0)
+    for _ in range(2):
+        st32.set_state(host_in)
+        st32.step(1)
+        out = st32.get_state()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        st32.set_state(host_in)
+        st32.step(1)
+        out = st32.get_state()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    # roofline of the dominant kernel of the mixed step ----------------------
+    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+    tot_ms, n_l = prof[dom]
+    avg_ms = tot_ms / n_l
+    pr = prob.as_dict()
+    alg = algorithmic_bytes(dom, mesh_d, 1, 4, pr["k_g"], pr["k_u"])
+    peak, peak_src = load_peaks()
+    roof = None
+    if alg is not None:
+        ach = alg / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 2), "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": round(ach / peak, 4),
+                "traffic": NCU_TRAFFIC.get((dom, WORKLOAD["name"])),
+                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": round(avg_ms, 5)}
+    share = {k: round(v[0] / sum(x[0] for x in prof.values()), 4) for k, v in prof.items() if v[1]}
+    share64 = {k: round(v[0] / sum(x[0] for x in prof64.values()), 4) for k, v in prof64.items() if v[1]}
+    value = world * nd * 3 * K / (ms32 * 1e-3)
+    value64 = world * nd * 3 * K / (ms64 * 1e-3)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = time_oracle(args.cpu_steps)
+            cpu = {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
+                   "sample": cpu["sample"]}
+        except Exception as ex:  # reported, never silently replaced
+            cpu = {"error": str(ex)[:200]}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms32 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 bulk + f64 averages/limiters", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "mesh": "256x256 quads", "degree": 2,
+                   "flux": "KPP", "bc": "fixed pi/4", "mode": "WENO-L + flux limiter",
+                   "n_dof": nd, "dof_stage_per_step": 3 * nd, "precision": "FP32-mixed",
+                   "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "fp64_plain": {"value": value64, "ms_per_step": ms64 / K, "kernel_share": share64},
+        "mixed_over_fp64": value / value64,
+        "kernel_share": share,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * nd * 3 * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nd * 4,
+                "d2h_bytes_per_step": nd * 4},
+        "gpu_launches": launches * K,
+        "clocks": sampler.summary(),
+        "violations": int(info32["violations"]) + int(info64["violations"]),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        pass
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    mesh, _, _ = workload()
+    steps = max(1, min(args.steps, 4))
+    for _ in range(max(1, args.warmup // 3)):
+        time_oracle(1)
+    res = time_oracle(steps)
+    value = res["value"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": res["seconds"] / steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "mesh": "256x256 quads", "degree": 2, "flux": "KPP",
+                   "bc": "fixed pi/4", "mode": "WENO-L + flux limiter", "n_dof": n_dof(mesh),
+                   "precision": "FP64 oracle (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                         "sample": res["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * cgl.h — C ABI of the GB300 (sm_103a) implementation of the explicit SSP-RK
+ * stage of the element-based convex-limited CG-WENO scheme of Kuzmin, Hajduk
+ * and Vedral (arXiv 2509.04673).
+ *
+ * Problem statement (Sec. 2 of the paper): a hyperbolic conservation law
+ * u_t + div f(u) = 0 on a rectangle, weakly imposed boundary data u_hat with
+ * boundary flux F(u, u_hat; n), discretised by continuous Bernstein Q_p
+ * finite elements on a uniform mesh of squares (Sec. 2.1), stabilised by
+ * the WENO dissipation of eq. (stab:WENO), written as the element-based
+ * monolithic convex limiting scheme of eq. (mcl) and advanced by SSP-RK3
+ * stages of the form eq. (eq:SSPupdate).
+ *
+ * Conventions for every entry point:
+ *   - return value: CGL_OK (0) or a negative error code; on error
+ *     cgl_last_error() returns a thread-local message;
+ *   - no C++ exception crosses this boundary;
+ *   - host arrays of nodal coefficients are float64, layout
+ *     [component][gy][gx] with gx fastest; a periodic direction of n
+ *     elements has n*p nodes (the duplicate at the far side is not stored),
+ *     a non-periodic one n*p + 1;
+ *   - per-element host arrays are float64, layout [component][ey][ex];
+ *   - the library owns every object it creates; destroy functions accept
+ *     NULL;
+ *   - a state is used from one host thread at a time; all its device work
+ *     runs on the stream given at creation, and every function that returns
+ *     host data synchronises that stream first.
+ */
+#ifndef CGL_H
+#define CGL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int cgl_status;
+
+#define CGL_OK 0
+#define CGL_EINVAL (-1)     /* invalid argument or unsupported combination */
+#define CGL_ECUDA (-2)      /* a CUDA call failed (no device, launch error) */
+#define CGL_EOOM (-3)       /* device or host allocation failed */
+#define CGL_EIDP (-4)       /* a node left the invariant domain beyond rounding */
+#define CGL_ENONFINITE (-5) /* a non-finite value was produced */
+#define CGL_EDT (-6)        /* the global time step collapsed */
+#define CGL_ETIMEOUT (-7)   /* a bounded device-side wait gave up */
+
+/* boundary conditions per direction (applied on both sides) */
+#define CGL_BC_PERIODIC 0
+#define CGL_BC_OUTFLOW 1    /* external state = internal state: F(u,u;n) = f(u).n */
+#define CGL_BC_FIXED 2      /* constant external state cgl_problem.ubc */
+
+/* flux functions */
+#define CGL_FLUX_ADVECTION 0 /* f(u) = (vx, vy) u */
+#define CGL_FLUX_BURGERS 1   /* f(u) = (u^2/2, u^2/2) */
+#define CGL_FLUX_KPP 2       /* f(u) = (sin u, cos u), Sec. 5.4.2 */
+#define CGL_FLUX_EULER 3     /* compressible Euler, ideal gas, Sec. 5.3 */
+
+/* method labels of Sec. 5.4: LO (gamma=beta=0), HO (gamma=beta=1),
+   WENO (sensor gamma, beta=1), WENO-L (sensor gamma, limited beta) */
+#define CGL_MODE_LO 0
+#define CGL_MODE_HO 1
+#define CGL_MODE_WENO 2
+#define CGL_MODE_WENO_L 3
+
+/* cell-average fluxes: 0 = high-order f^H (eq. (uebar)), 1 = flux-limited
+   (eqs. (uelim), (fAlim) / Appendix A), 2 = low-order LLF f^L (eq. (uebar2)) */
+#define CGL_FL_NONE 0
+#define CGL_FL_LIMITED 1
+#define CGL_FL_LOW 2
+
+/* storage / arithmetic precision */
+#define CGL_FP64 0        /* everything in float64 */
+#define CGL_FP32_MIXED 1  /* bulk (state, sensor, residual, g_h, udot, f_i^e)
+                             in float32; cell averages, pseudo time steps,
+                             facet fluxes and their limiter, limiter bound gaps,
+                             positivity tests, final nodal sums and
+                             conservation sums in float64 */
+
+typedef struct cgl_mesh cgl_mesh;
+typedef struct cgl_state cgl_state;
+
+/* Uniform mesh of nx x ny squares on [x0,x1] x [y0,y1] (Sec. 2.1, Table 1 of
+   the paper). Requires (x1-x0)/nx == (y1-y0)/ny, 1 <= p <= 4, nx, ny >= 1. */
+typedef struct cgl_mesh_desc {
+    int32_t nx, ny, p;
+    int32_t bc_x, bc_y;
+    int32_t reserved;
+    double x0, x1, y0, y1;
+} cgl_mesh_desc;
+
+/* Problem parameters. cgl_problem_defaults() fills the paper's defaults:
+   q = 1 (Sec. 5), r = 2 (Sec. 2.2), w_lin = 1e-3 (Sec. 5.5), gamma = 1.4
+   (Sec. 5.3), omega_CFL = 0.2, k_g = k_u = 1. */
+typedef struct cgl_problem {
+    int32_t flux;          /* CGL_FLUX_* */
+    int32_t mode;          /* CGL_MODE_* */
+    int32_t flux_limiter;  /* CGL_FL_* */
+    int32_t k_g;           /* Richardson sweeps of the g_h projection (>= 0) */
+    int32_t k_u;           /* Richardson sweeps of the udot solve (>= 0) */
+    int32_t reserved;
+    double vx, vy;         /* advection velocity */
+    double gamma_gas;      /* Euler adiabatic constant, 1 < gamma <= 5/3 */
+    double umin, umax;     /* scalar invariant domain G = [umin, umax] */
+    double pos_eps;        /* Euler positivity margin (rho*, p* >= eps-fraction) */
+    double q;              /* sensor steepening exponent, eq. (WENO:alpha) */
+    double r;              /* WENO weight exponent */
+    double weno_eps;       /* WENO weight epsilon */
+    double w_lin;          /* linear weight of each face-neighbour candidate */
+    double gamma_eps;      /* regulariser of the sensor ratio */
+    double cfl;            /* omega_CFL: dt = cfl * min_e dt_e */
+    double lambda_floor;   /* floor of the facet speed sum in eq. (dtmaxcell) */
+    double ubc[4];         /* FIXED boundary state (ncomp values) */
+} cgl_problem;
+
+typedef struct cgl_step_info {
+    double t;              /* time after the call */
+    double dt_last;        /* last global time step */
+    int64_t steps;         /* SSP-RK3 steps taken by the call */
+    int64_t violations;    /* nodes outside G beyond rounding, summed over stages */
+    int64_t clamps;        /* nodes clamped into G by rounding, summed over stages */
+    int64_t cfl_violations;/* elements with dt > dt_e at a later stage */
+    double mass[4];        /* sum_i m_i u_i per component after the call (float64) */
+    double umin[4];        /* range of the coefficients after the call */
+    double umax[4];
+} cgl_step_info;
+
+/* --- library ------------------------------------------------------------ */
+
+/* Thread-local message of the last failed call ("" if none). */
+const char *cgl_last_error(void);
+
+/* Library version string, e.g. "cgl 0.1 sm_103a". Never fails. */
+const char *cgl_version(void);
+
+/* Fill *p with the paper's defaults for the given flux kind (Sec. 5). */
+cgl_status cgl_problem_defaults(cgl_problem *p, int32_t flux);
+
+/* Export the library's own 1D Bernstein / Gauss tables of degree p (host
+   computation, no GPU needed). out receives, in order: M, C, D, Ep, Em
+   ((p+1)^2 each, row-major [a][b]), xq, wq (p+2 each), Bq, dBq
+   ((p+2)(p+1) each, [q][a]) and the semi-norm matrix A ((p+1)^4, [i][j]).
+   n must be at least the total count, returned in *needed. */
+cgl_status cgl_debug_tables(int32_t p, double *out, size_t n, size_t *needed);
+
+/* --- mesh ---------------------------------------------------------------- */
+
+/* Validate a mesh description and create a mesh object (host only). */
+cgl_status cgl_mesh_create(const cgl_mesh_desc *desc, cgl_mesh **out);
+void cgl_mesh_destroy(cgl_mesh *mesh);
+
+/* Node counts per direction and element count. */
+cgl_status cgl_mesh_sizes(const cgl_mesh *mesh, int64_t *nnx, int64_t *nny, int64_t *nelem);
+
+/* --- state ----------------------------------------------------------------- */
+
+/* Allocate device storage for ncomp components (1 scalar, 4 Euler) of the
+   given precision on the current CUDA device. stream is a cudaStream_t (or
+   NULL: the library creates its own non-blocking stream). The mesh must
+   outlive the state. Fails with CGL_ECUDA when no GPU is usable. */
+cgl_status cgl_state_create(const cgl_mesh *mesh, int32_t ncomp, int32_t precision,
+                            void *stream, cgl_state **out);
+void cgl_state_destroy(cgl_state *state);
+
+/* Set the problem (validated: flux/ncomp match, bounds, exponents, counts). */
+cgl_status cgl_set_problem(cgl_state *state, const cgl_problem *prob);
+
+/* Copy n = ncomp*nny*nnx float64 coefficients from the host into the state
+   (rounded to float32 in FP32_MIXED). Synchronous. */
+cgl_status cgl_set_state(cgl_state *state, const double *host, size_t n);
+
+/* Copy the state to the host as float64 (exact widening in FP32_MIXED). */
+cgl_status cgl_get_state(cgl_state *state, double *host, size_t n);
+
+/* Set the base state u^n used by cgl_stage (same layout as cgl_set_state). */
+cgl_status cgl_set_base_state(cgl_state *state, const double *host, size_t n);
+
+/* Simulation time. */
+cgl_status cgl_set_time(cgl_state *state, double t);
+cgl_status cgl_get_time(cgl_state *state, double *t);
+
+/* Advance min(nsteps, until t_end) SSP-RK3 steps with dt = cfl*min_e dt_e
+   taken from u^n each step (capped at t_end - t). Pass t_end = +inf for a
+   fixed step count. Returns CGL_EIDP if a node left G beyond rounding (the
+   state is still advanced), CGL_ENONFINITE on NaN/Inf. info may be NULL. */
+cgl_status cgl_step(cgl_state *state, int32_t nsteps, double t_end, cgl_step_info *info);
+
+/* Enqueue nsteps SSP-RK3 steps (as cgl_step with the t_end of the last
+   cgl_step call, +inf initially) on the state's stream and return without
+   waiting or reading diagnostics; a later cgl_step / cgl_get_state /
+   cgl_get_counters observes the result. */
+cgl_status cgl_step_async(cgl_state *state, int32_t nsteps);
+
+/* Cumulative counters since creation: out4 = {violations, clamps,
+   cfl_violations, non-finite values}. Synchronises the stream. */
+cgl_status cgl_get_counters(cgl_state *state, int64_t *out4);
+
+/* One SSP stage with a given dt: u <- a u^n + b FE(u), FE(u) the forward
+   Euler update eq. (eq:SSPupdate). Used by parity tests. */
+cgl_status cgl_stage(cgl_state *state, double dt, double a, double b, cgl_step_info *info);
+
+/* Global dt = cfl * min_e dt_e of the current state (eq. (dtmaxcell)). */
+cgl_status cgl_time_step(cgl_state *state, double *dt);
+
+/* Per-element intermediates of the last stage, float64 [comp][E] or [E]. */
+#define CGL_FIELD_UE 0      /* u^e        (ncomp x E) */
+#define CGL_FIELD_DTE 1     /* dt_e       (E)         */
+#define CGL_FIELD_UBL 2     /* ubar^{e,L} (ncomp x E) */
+#define CGL_FIELD_UBE 3     /* ubar^e     (ncomp x E) */
+#define CGL_FIELD_GAMMA 4   /* gamma_e    (E)         */
+#define CGL_FIELD_NU 5      /* nu_e       (E)         */
+#define CGL_FIELD_BETA 6    /* beta_e     (E)         */
+/* Nodal intermediates of the last stage, float64 [v][nny][nnx]. */
+#define CGL_FIELD_GX 16     /* g_h x-components (ncomp) */
+#define CGL_FIELD_GY 17     /* g_h y-components (ncomp) */
+#define CGL_FIELD_R 18      /* target residual r (ncomp) */
+#define CGL_FIELD_UDOT 19   /* udot (ncomp) */
+cgl_status cgl_get_field(cgl_state *state, int32_t field, double *host, size_t n);
+
+/* --- measurement ------------------------------------------------------------ */
+
+/* Name of kernel identifier id (0 <= id < 12), "" otherwise. */
+const char *cgl_kernel_name(int32_t id);
+
+/* Run nsteps (1..1000) SSP-RK3 steps launch by launch (no graph) with CUDA
+   events recorded around every kernel on the state's stream; ms[id] and
+   launches[id] receive the summed device time and the launch count per
+   kernel identifier (nk >= 12). The state is advanced like cgl_step. */
+cgl_status cgl_profile(cgl_state *state, int32_t nsteps, int32_t nk, double *ms, int64_t *launches);
+
+/* Number of kernels one cgl_step step launches with the current problem. */
+cgl_status cgl_launches_per_step(cgl_state *state, int64_t *kernels);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CGL_H */

@@ -299,6 +299,14 @@ def outward_sum(om: OracleMesh, Fx, Fy):
     return Fx[:, om.fE] - Fx[:, om.fW] + Fy[:, om.fN] - Fy[:, om.fS]
 
 
+def _seminorm2(V, A2):
+    """Squared semi-norm c^T A c of each row of V.  A annihilates constants
+    (the semi-norm has no k = 0 term), so the row mean is removed first; this
+    is exact algebra and avoids cancellation for nearly constant data."""
+    Vc = V - V.mean(axis=1, keepdims=True)
+    return np.einsum("ei,ij,ej->e", Vc, A2, Vc)
+
+
 def sensor(om: OracleMesh, U, prob):
     """WENO smoothness sensor gamma_e, eqs. (WENO:alpha), (WENO:norm).
 
@@ -326,14 +334,14 @@ def sensor(om: OracleMesh, U, prob):
         ne = sum(pr.astype(float) for pr in present[1:])
         wt = []
         for l, (Ul, pr) in enumerate(zip(cands, present)):
-            sig = np.maximum(np.einsum("ei,ij,ej->e", Ul, A2, Ul), 0.0)
+            sig = np.maximum(_seminorm2(Ul, A2), 0.0)
             wl = (1.0 - ne * w_lin) if l == 0 else w_lin * pr
             wt.append(wl / (sig ** (0.5 * r) + eps))
         tot = sum(wt)
         Us = sum((w / tot)[:, None] * Ul for w, Ul in zip(wt, cands))
         dlt = U0 - Us
-        num = np.sqrt(np.maximum(np.einsum("ei,ij,ej->e", dlt, A2, dlt), 0.0))
-        den = np.sqrt(np.maximum(np.einsum("ei,ij,ej->e", U0, A2, U0), 0.0))
+        num = np.sqrt(np.maximum(_seminorm2(dlt, A2), 0.0))
+        den = np.sqrt(np.maximum(_seminorm2(U0, A2), 0.0))
         ratio = num / (den + geps)
         gam = np.minimum(gam, 1.0 - np.minimum(1.0, ratio) ** q)
     return gam

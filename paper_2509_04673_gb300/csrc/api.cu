@@ -1,0 +1,886 @@
+// api.cu — C ABI (include/cgl.h) of the GB300 implementation of the explicit
+// SSP-RK stage of the element-based convex-limited CG-WENO scheme
+// (Kuzmin, Hajduk, Vedral, arXiv 2509.04673).
+//
+// Host responsibilities: argument validation, 1D Bernstein / Gauss tables
+// (closed forms, Newton iteration and de Casteljau continuation computed
+// here in float64), device allocation, the SSP-RK3 step loop captured as a
+// CUDA graph, and diagnostics read-back. Every step of the scheme runs in
+// the kernels of kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/cgl.h"
+#include "stage.cuh"
+
+using namespace cgl;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+static cgl_status fail(cgl_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define CUDA_TRY(x)                                                                  \
+    do {                                                                             \
+        cudaError_t e_ = (x);                                                        \
+        if (e_ != cudaSuccess)                                                       \
+            return fail(CGL_ECUDA, "%s failed: %s", #x, cudaGetErrorString(e_));    \
+    } while (0)
+
+extern "C" const char* cgl_last_error(void) { return g_err; }
+extern "C" const char* cgl_version(void) { return "cgl 0.1 sm_103a"; }
+
+// ---------------------------------------------------------------------------
+// host tables (independent closed forms)
+// ---------------------------------------------------------------------------
+static double binom(int n, int k) {
+    if (k < 0 || k > n) return 0.0;
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return std::round(r);
+}
+
+// int_0^1 B^m_i B^n_j = C(m,i) C(n,j) / ((m+n+1) C(m+n, i+j))
+static double bint(int m, int i, int n, int j) {
+    if (i < 0 || i > m || j < 0 || j > n) return 0.0;
+    return binom(m, i) * binom(n, j) / ((m + n + 1) * binom(m + n, i + j));
+}
+
+static double bern_val(int p, int a, double x) {
+    if (a < 0 || a > p) return 0.0;
+    double v = binom(p, a);
+    for (int k = 0; k < a; ++k) v *= x;
+    for (int k = 0; k < p - a; ++k) v *= (1.0 - x);
+    return v;
+}
+
+// Gauss-Legendre on [-1,1] by Newton iteration on P_n (three-term recurrence)
+static void gauss_legendre(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = pk;
+            }
+            double pn = (n == 1) ? z : p1, pm = (n == 1) ? 1.0 : p0;
+            double dp = n * (z * pn - pm) / (z * z - 1.0);
+            double dz = pn / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-17) {
+                // weight from the final iterate
+                p0 = 1.0;
+                p1 = z;
+                for (int k = 2; k <= n; ++k) {
+                    double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                    p0 = p1;
+                    p1 = pk;
+                }
+                pn = (n == 1) ? z : p1;
+                pm = (n == 1) ? 1.0 : p0;
+                dp = n * (z * pn - pm) / (z * z - 1.0);
+                w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+                x[i] = z;
+                break;
+            }
+            x[i] = z;
+            w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        }
+    }
+    // ascending order
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j)
+            if (x[j] < x[i]) {
+                std::swap(x[i], x[j]);
+                std::swap(w[i], w[j]);
+            }
+}
+
+// Bernstein coefficients, on [0,1], of the degree-p polynomial whose
+// coefficients on the neighbouring cell are the unit vector e_c:
+// side = +1 east neighbour ([1,2]), -1 west neighbour ([-1,0]); computed by
+// de Casteljau subdivision at t = -1 (left part) or t = 2 (right part).
+static void continuation(int p, int side, double out[N1MAX][N1MAX]) {
+    for (int c = 0; c <= p; ++c) {
+        double tri[N1MAX][N1MAX];
+        for (int j = 0; j <= p; ++j) tri[0][j] = (j == c) ? 1.0 : 0.0;
+        const double t = (side > 0) ? -1.0 : 2.0;
+        for (int k = 1; k <= p; ++k)
+            for (int j = 0; j + k <= p; ++j) tri[k][j] = (1.0 - t) * tri[k - 1][j] + t * tri[k - 1][j + 1];
+        for (int k = 0; k <= p; ++k) {
+            // east: q(x-1) on [0,1] = left subdivision at t=-1, reversed;
+            // west: q(x+1) on [0,1] = right subdivision at t=2, reversed
+            double v = (side > 0) ? tri[k][0] : tri[p - k][k];
+            out[p - k][c] = v;
+        }
+    }
+}
+
+struct HostTables {
+    Tab<double> td[PMAX + 1];
+    Tab<float> tf[PMAX + 1];
+    double a2d[A2_TOTAL];
+    float a2f[A2_TOTAL];
+};
+
+static void semi_norm_blocks(int p, std::vector<std::vector<double>>& S) {
+    // S[k][a*(p+1)+b] = int B_a^(k) B_b^(k), with
+    // B_a^(k) = p!/(p-k)! sum_j (-1)^(k-j) C(k,j) B^{p-k}_{a-j}
+    const int n = p + 1;
+    S.assign(p + 1, std::vector<double>(n * n, 0.0));
+    for (int k = 0; k <= p; ++k) {
+        double ff = 1.0;
+        for (int i = 0; i < k; ++i) ff *= (p - i);
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) {
+                double s = 0.0;
+                for (int j = 0; j <= k; ++j)
+                    for (int l = 0; l <= k; ++l) {
+                        double sg = ((2 * k - j - l) % 2) ? -1.0 : 1.0;
+                        s += sg * binom(k, j) * binom(k, l) * bint(p - k, a - j, p - k, b - l);
+                    }
+                S[k][a * n + b] = ff * ff * s;
+            }
+    }
+}
+
+static void build_tables(HostTables& H) {
+    std::memset(&H, 0, sizeof(H));
+    for (int p = 1; p <= PMAX; ++p) {
+        Tab<double>& T = H.td[p];
+        const int n = p + 1, nq = p + 2;
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) {
+                T.M[a][b] = bint(p, a, p, b);
+                T.C[a][b] = p * (bint(p - 1, a - 1, p, b) - bint(p - 1, a, p, b));
+                T.D[a][b] = (double)p * p *
+                            (bint(p - 1, a - 1, p - 1, b - 1) - bint(p - 1, a - 1, p - 1, b) -
+                             bint(p - 1, a, p - 1, b - 1) + bint(p - 1, a, p - 1, b));
+            }
+        continuation(p, +1, T.Ep);
+        continuation(p, -1, T.Em);
+        double xg[NQMAX], wg[NQMAX];
+        gauss_legendre(nq, xg, wg);
+        for (int q = 0; q < nq; ++q) {
+            double x = 0.5 * (xg[q] + 1.0);
+            T.wq[q] = 0.5 * wg[q];
+            for (int a = 0; a < n; ++a) {
+                T.Bq[q][a] = bern_val(p, a, x);
+                T.dBq[q][a] = p * (bern_val(p - 1, a - 1, x) - bern_val(p - 1, a, x));
+            }
+        }
+        // semi-norm matrix of eq. (WENO:norm): sum over 1 <= k1 + k2 <= p
+        std::vector<std::vector<double>> S;
+        semi_norm_blocks(p, S);
+        const int n2 = n * n, off = A2_OFF[p];
+        for (int i = 0; i < n2 * n2; ++i) H.a2d[off + i] = 0.0;
+        for (int k1 = 0; k1 <= p; ++k1)
+            for (int k2 = 0; k2 <= p; ++k2) {
+                if (k1 + k2 < 1 || k1 + k2 > p) continue;
+                for (int b = 0; b < n; ++b)
+                    for (int a = 0; a < n; ++a)
+                        for (int d = 0; d < n; ++d)
+                            for (int c = 0; c < n; ++c)
+                                H.a2d[off + (b * n + a) * n2 + d * n + c] +=
+                                    S[k1][a * n + c] * S[k2][b * n + d];
+            }
+        // float copies
+        Tab<float>& F = H.tf[p];
+        const double* src = (const double*)&T;
+        float* dst = (float*)&F;
+        for (size_t i = 0; i < sizeof(Tab<double>) / sizeof(double); ++i) dst[i] = (float)src[i];
+    }
+    for (int i = 0; i < A2_TOTAL; ++i) H.a2f[i] = (float)H.a2d[i];
+}
+
+static const HostTables& host_tables() {
+    static HostTables* H = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        H = new HostTables;
+        build_tables(*H);
+    });
+    return *H;
+}
+
+extern "C" cgl_status cgl_debug_tables(int32_t p, double* out, size_t n, size_t* needed) {
+    if (p < 1 || p > PMAX) return fail(CGL_EINVAL, "degree p=%d outside [1,%d]", p, PMAX);
+    const int n1 = p + 1, nq = p + 2, n2 = n1 * n1;
+    size_t need = 5 * n1 * n1 + 2 * nq + 2 * nq * n1 + n2 * n2;
+    if (needed) *needed = need;
+    if (!out) return CGL_OK;
+    if (n < need) return fail(CGL_EINVAL, "buffer too small: %zu < %zu", n, need);
+    const HostTables& H = host_tables();
+    const Tab<double>& T = H.td[p];
+    size_t k = 0;
+    for (int a = 0; a < n1; ++a) for (int b = 0; b < n1; ++b) out[k++] = T.M[a][b];
+    for (int a = 0; a < n1; ++a) for (int b = 0; b < n1; ++b) out[k++] = T.C[a][b];
+    for (int a = 0; a < n1; ++a) for (int b = 0; b < n1; ++b) out[k++] = T.D[a][b];
+    for (int a = 0; a < n1; ++a) for (int b = 0; b < n1; ++b) out[k++] = T.Ep[a][b];
+    for (int a = 0; a < n1; ++a) for (int b = 0; b < n1; ++b) out[k++] = T.Em[a][b];
+    double xg[NQMAX], wg[NQMAX];
+    gauss_legendre(nq, xg, wg);
+    for (int q = 0; q < nq; ++q) out[k++] = 0.5 * (xg[q] + 1.0);
+    for (int q = 0; q < nq; ++q) out[k++] = T.wq[q];
+    for (int q = 0; q < nq; ++q) for (int a = 0; a < n1; ++a) out[k++] = T.Bq[q][a];
+    for (int q = 0; q < nq; ++q) for (int a = 0; a < n1; ++a) out[k++] = T.dBq[q][a];
+    for (int i = 0; i < n2 * n2; ++i) out[k++] = H.a2d[A2_OFF[p] + i];
+    return CGL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// mesh
+// ---------------------------------------------------------------------------
+struct cgl_mesh {
+    cgl_mesh_desc d;
+    MeshDev m;
+};
+
+extern "C" cgl_status cgl_mesh_create(const cgl_mesh_desc* d, cgl_mesh** out) {
+    if (!d || !out) return fail(CGL_EINVAL, "null argument");
+    *out = nullptr;
+    if (d->nx < 1 || d->ny < 1) return fail(CGL_EINVAL, "nx, ny must be >= 1");
+    if (d->p < 1 || d->p > PMAX) return fail(CGL_EINVAL, "degree p=%d outside [1,%d]", d->p, PMAX);
+    for (int bc : {d->bc_x, d->bc_y})
+        if (bc != CGL_BC_PERIODIC && bc != CGL_BC_OUTFLOW && bc != CGL_BC_FIXED)
+            return fail(CGL_EINVAL, "unknown boundary condition %d", bc);
+    if (!(d->x1 > d->x0) || !(d->y1 > d->y0)) return fail(CGL_EINVAL, "empty domain");
+    double hx = (d->x1 - d->x0) / d->nx, hy = (d->y1 - d->y0) / d->ny;
+    if (std::fabs(hx - hy) > 1e-12 * std::fabs(hx))
+        return fail(CGL_EINVAL, "square elements required (hx=%g, hy=%g)", hx, hy);
+    long long nnx = (long long)d->nx * d->p + (d->bc_x == CGL_BC_PERIODIC ? 0 : 1);
+    long long nny = (long long)d->ny * d->p + (d->bc_y == CGL_BC_PERIODIC ? 0 : 1);
+    if ((long long)d->nx * d->ny > (1LL << 31) - 1 || nnx > (1LL << 30) || nny > (1LL << 30))
+        return fail(CGL_EINVAL, "mesh too large");
+    cgl_mesh* M = new (std::nothrow) cgl_mesh;
+    if (!M) return fail(CGL_EOOM, "host allocation failed");
+    M->d = *d;
+    MeshDev& m = M->m;
+    m.nx = d->nx;
+    m.ny = d->ny;
+    m.p = d->p;
+    m.nnx = (int)nnx;
+    m.nny = (int)nny;
+    m.px = d->bc_x == CGL_BC_PERIODIC;
+    m.py = d->bc_y == CGL_BC_PERIODIC;
+    m.bc_x = d->bc_x;
+    m.bc_y = d->bc_y;
+    m.E = d->nx * d->ny;
+    m.NN = nnx * nny;
+    m.h = hx;
+    *out = M;
+    return CGL_OK;
+}
+
+extern "C" void cgl_mesh_destroy(cgl_mesh* mesh) { delete mesh; }
+
+extern "C" cgl_status cgl_mesh_sizes(const cgl_mesh* mesh, int64_t* nnx, int64_t* nny, int64_t* nelem) {
+    if (!mesh) return fail(CGL_EINVAL, "null mesh");
+    if (nnx) *nnx = mesh->m.nnx;
+    if (nny) *nny = mesh->m.nny;
+    if (nelem) *nelem = mesh->m.E;
+    return CGL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// problem
+// ---------------------------------------------------------------------------
+extern "C" cgl_status cgl_problem_defaults(cgl_problem* p, int32_t flux) {
+    if (!p) return fail(CGL_EINVAL, "null problem");
+    if (flux < CGL_FLUX_ADVECTION || flux > CGL_FLUX_EULER) return fail(CGL_EINVAL, "unknown flux %d", flux);
+    std::memset(p, 0, sizeof(*p));
+    p->flux = flux;
+    p->mode = CGL_MODE_WENO_L;
+    p->flux_limiter = CGL_FL_LIMITED;
+    p->k_g = 1;
+    p->k_u = 1;
+    p->vx = 1.0;
+    p->vy = 0.5;
+    p->gamma_gas = 1.4;
+    p->umin = 0.0;
+    p->umax = 1.0;
+    p->pos_eps = 1e-10;
+    p->q = 1.0;
+    p->r = 2.0;
+    p->weno_eps = 1e-12;
+    p->w_lin = 1e-3;
+    p->gamma_eps = 1e-12;
+    p->cfl = 0.2;
+    p->lambda_floor = 1e-12;
+    return CGL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// state
+// ---------------------------------------------------------------------------
+struct cgl_state {
+    const cgl_mesh* mesh;
+    int nc, prec, device;
+    cudaStream_t st;
+    bool own_stream;
+    bool has_problem;
+    cgl_problem prob;
+    ProbDev pd;
+    StageFn stage;
+    Bufs B;
+    size_t rsz;  // bytes per bulk value
+    cudaGraphExec_t step_graph;
+    double* diag;       // device partials for diagnostics
+    std::vector<void*> allocs;
+};
+
+static std::mutex g_upload_mu;
+static std::vector<int> g_uploaded;  // devices whose constant memory holds the tables
+
+static cgl_status ensure_tables(int dev) {
+    std::lock_guard<std::mutex> lk(g_upload_mu);
+    for (int d : g_uploaded)
+        if (d == dev) return CGL_OK;
+    const HostTables& H = host_tables();
+    UploadFn fns[4] = {upload_adv, upload_burgers, upload_kpp, upload_euler};
+    for (UploadFn f : fns) CUDA_TRY(f(H.td, H.tf, H.a2d, H.a2f));
+    g_uploaded.push_back(dev);
+    return CGL_OK;
+}
+
+static cgl_status dalloc(cgl_state* S, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? CGL_EOOM : CGL_ECUDA, "cudaMalloc(%zu): %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    S->allocs.push_back(*p);
+    return CGL_OK;
+}
+
+extern "C" void cgl_state_destroy(cgl_state* S) {
+    if (!S) return;
+    if (S->step_graph) cudaGraphExecDestroy(S->step_graph);
+    for (void* p : S->allocs) cudaFree(p);
+    if (S->own_stream && S->st) cudaStreamDestroy(S->st);
+    delete S;
+}
+
+extern "C" cgl_status cgl_state_create(const cgl_mesh* mesh, int32_t ncomp, int32_t precision, void* stream,
+                                       cgl_state** out) {
+    if (!mesh || !out) return fail(CGL_EINVAL, "null argument");
+    *out = nullptr;
+    if (ncomp != 1 && ncomp != 4) return fail(CGL_EINVAL, "ncomp must be 1 or 4");
+    if (precision != CGL_FP64 && precision != CGL_FP32_MIXED) return fail(CGL_EINVAL, "unknown precision");
+    int ndev = 0;
+    cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce != cudaSuccess || ndev == 0)
+        return fail(CGL_ECUDA, "no usable CUDA device: %s", cudaGetErrorString(ce));
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    cgl_status rc = ensure_tables(dev);
+    if (rc) return rc;
+    cgl_state* S = new (std::nothrow) cgl_state();
+    if (!S) return fail(CGL_EOOM, "host allocation failed");
+    S->mesh = mesh;
+    S->nc = ncomp;
+    S->prec = precision;
+    S->device = dev;
+    S->rsz = precision == CGL_FP64 ? 8 : 4;
+    if (stream) {
+        S->st = (cudaStream_t)stream;
+        S->own_stream = false;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete S;
+            return fail(CGL_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        S->own_stream = true;
+    }
+    const MeshDev& m = mesh->m;
+    const size_t NN = (size_t)m.NN, E = (size_t)m.E, N2 = (size_t)(m.p + 1) * (m.p + 1), nc = ncomp;
+    const size_t r = S->rsz;
+    Bufs& B = S->B;
+    struct A { void** p; size_t b; } list[] = {
+        {&B.u, nc * NN * r},          {&B.un, nc * NN * r},        {&B.g, 2 * nc * NN * r},
+        {&B.bg, 2 * nc * NN * r},     {&B.r, nc * NN * r},         {&B.ud, nc * NN * r},
+        {&B.EV, E * N2 * 2 * nc * r}, {&B.ER, E * N2 * nc * r},    {(void**)&B.EW, E * N2 * nc * 8},
+        {(void**)&B.ue, nc * E * 8},  {(void**)&B.fue, 2 * nc * E * 8}, {(void**)&B.lame, E * 8},
+        {(void**)&B.dte, E * 8},      {(void**)&B.ubl, nc * E * 8}, {(void**)&B.gam, E * 8},
+        {(void**)&B.nu, E * 8},       {(void**)&B.ube, nc * E * 8}, {(void**)&B.beta, E * 8},
+        {(void**)&B.cnt, CNT_N * 8},  {(void**)&B.dtbits, 8},      {(void**)&B.dt, 8},
+        {(void**)&B.t, 8},            {(void**)&B.t_end, 8},       {(void**)&S->diag, 1024 * 12 * 8},
+    };
+    for (auto& a : list) {
+        rc = dalloc(S, a.p, a.b);
+        if (rc) {
+            cgl_state_destroy(S);
+            return rc;
+        }
+    }
+    // zero everything once so that fields read before the first stage are defined
+    for (auto& a : list) {
+        cudaError_t e = cudaMemsetAsync(*a.p, 0, a.b, S->st);
+        if (e != cudaSuccess) {
+            cgl_state_destroy(S);
+            return fail(CGL_ECUDA, "cudaMemset: %s", cudaGetErrorString(e));
+        }
+    }
+    double inf = std::numeric_limits<double>::infinity();
+    cudaMemcpyAsync(B.t_end, &inf, 8, cudaMemcpyHostToDevice, S->st);
+    cudaError_t e = cudaStreamSynchronize(S->st);
+    if (e != cudaSuccess) {
+        cgl_state_destroy(S);
+        return fail(CGL_ECUDA, "state init: %s", cudaGetErrorString(e));
+    }
+    *out = S;
+    return CGL_OK;
+}
+
+static double round_inward_f32(double v, bool up) {
+    float f = (float)v;
+    if (up) {
+        if ((double)f < v) f = std::nextafter(f, std::numeric_limits<float>::infinity());
+    } else {
+        if ((double)f > v) f = std::nextafter(f, -std::numeric_limits<float>::infinity());
+    }
+    return (double)f;
+}
+
+extern "C" cgl_status cgl_set_problem(cgl_state* S, const cgl_problem* p) {
+    if (!S || !p) return fail(CGL_EINVAL, "null argument");
+    if (p->flux < CGL_FLUX_ADVECTION || p->flux > CGL_FLUX_EULER) return fail(CGL_EINVAL, "unknown flux");
+    int need_nc = p->flux == CGL_FLUX_EULER ? 4 : 1;
+    if (need_nc != S->nc) return fail(CGL_EINVAL, "flux %d needs ncomp=%d, state has %d", p->flux, need_nc, S->nc);
+    if (p->mode < CGL_MODE_LO || p->mode > CGL_MODE_WENO_L) return fail(CGL_EINVAL, "unknown mode");
+    if (p->flux_limiter < CGL_FL_NONE || p->flux_limiter > CGL_FL_LOW) return fail(CGL_EINVAL, "unknown flux_limiter");
+    if (p->k_g < 0 || p->k_u < 0 || p->k_g > 64 || p->k_u > 64) return fail(CGL_EINVAL, "k_g, k_u in [0, 64]");
+    if (!(p->cfl > 0.0) || !(p->cfl <= 1.0)) return fail(CGL_EINVAL, "cfl must be in (0, 1]");
+    if (!(p->q >= 1.0) || !(p->r >= 1.0)) return fail(CGL_EINVAL, "q, r must be >= 1");
+    if (!(p->weno_eps > 0.0) || !(p->gamma_eps >= 0.0) || !(p->lambda_floor > 0.0))
+        return fail(CGL_EINVAL, "epsilons must be positive");
+    if (!(p->w_lin >= 0.0) || !(p->w_lin <= 0.25)) return fail(CGL_EINVAL, "w_lin in [0, 0.25]");
+    if (need_nc == 1 && !(p->umin < p->umax)) return fail(CGL_EINVAL, "umin < umax required");
+    if (p->flux == CGL_FLUX_EULER) {
+        if (!(p->gamma_gas > 1.0) || !(p->gamma_gas <= 5.0 / 3.0))
+            return fail(CGL_EINVAL, "gamma in (1, 5/3] required by the speed bound");
+        if (!(p->pos_eps >= 0.0) || !(p->pos_eps < 1.0)) return fail(CGL_EINVAL, "pos_eps in [0,1)");
+    }
+    const MeshDev& m = S->mesh->m;
+    if ((m.bc_x == CGL_BC_FIXED || m.bc_y == CGL_BC_FIXED) && need_nc == 1 &&
+        (p->ubc[0] < p->umin || p->ubc[0] > p->umax))
+        return fail(CGL_EINVAL, "fixed boundary state outside [umin, umax]");
+    StageFn fn = nullptr;
+    switch (p->flux) {
+        case CGL_FLUX_ADVECTION: fn = stage_fn_adv(S->prec, m.p); break;
+        case CGL_FLUX_BURGERS: fn = stage_fn_burgers(S->prec, m.p); break;
+        case CGL_FLUX_KPP: fn = stage_fn_kpp(S->prec, m.p); break;
+        default: fn = stage_fn_euler(S->prec, m.p); break;
+    }
+    if (!fn) return fail(CGL_EINVAL, "no kernel for this combination");
+    S->prob = *p;
+    ProbDev& d = S->pd;
+    d.flux = p->flux;
+    d.mode = p->mode;
+    d.fl = p->flux_limiter;
+    d.k_g = p->k_g;
+    d.k_u = p->k_u;
+    d.vx = p->vx;
+    d.vy = p->vy;
+    d.gam = p->gamma_gas;
+    d.umin = p->umin;
+    d.umax = p->umax;
+    d.umin32 = round_inward_f32(p->umin, true);
+    d.umax32 = round_inward_f32(p->umax, false);
+    d.pos_eps = p->pos_eps;
+    d.q = p->q;
+    d.r = p->r;
+    d.weno_eps = p->weno_eps;
+    d.w_lin = p->w_lin;
+    d.gamma_eps = p->gamma_eps;
+    d.cfl = p->cfl;
+    d.lambda_floor = p->lambda_floor;
+    for (int c = 0; c < 4; ++c) d.ubc[c] = p->ubc[c];
+    double sc = std::fmax(1.0, std::fmax(std::fabs(p->umin), std::fabs(p->umax)));
+    d.viol_tol = (S->prec == CGL_FP64 ? 1e-12 : 1e-6) * sc;
+    S->stage = fn;
+    S->has_problem = true;
+    if (S->step_graph) {
+        cudaGraphExecDestroy(S->step_graph);
+        S->step_graph = nullptr;
+    }
+    return CGL_OK;
+}
+
+static size_t state_count(const cgl_state* S) { return (size_t)S->nc * (size_t)S->mesh->m.NN; }
+
+static cgl_status upload_nodal(cgl_state* S, void* dst, const double* host, size_t n) {
+    if (!S || !host) return fail(CGL_EINVAL, "null argument");
+    if (n != state_count(S)) return fail(CGL_EINVAL, "expected %zu values, got %zu", state_count(S), n);
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(host[i])) return fail(CGL_ENONFINITE, "non-finite input at %zu", i);
+    if (S->prec == CGL_FP64) {
+        CUDA_TRY(cudaMemcpyAsync(dst, host, n * 8, cudaMemcpyHostToDevice, S->st));
+        CUDA_TRY(cudaStreamSynchronize(S->st));
+    } else {
+        std::vector<float> tmp(n);
+        for (size_t i = 0; i < n; ++i) tmp[i] = (float)host[i];
+        CUDA_TRY(cudaMemcpyAsync(dst, tmp.data(), n * 4, cudaMemcpyHostToDevice, S->st));
+        CUDA_TRY(cudaStreamSynchronize(S->st));
+    }
+    return CGL_OK;
+}
+
+static cgl_status download_any(cgl_state* S, const void* src, bool bulk, double* host, size_t n) {
+    if (bulk && S->prec != CGL_FP64) {
+        std::vector<float> tmp(n);
+        CUDA_TRY(cudaMemcpyAsync(tmp.data(), src, n * 4, cudaMemcpyDeviceToHost, S->st));
+        CUDA_TRY(cudaStreamSynchronize(S->st));
+        for (size_t i = 0; i < n; ++i) host[i] = (double)tmp[i];
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(host, src, n * 8, cudaMemcpyDeviceToHost, S->st));
+        CUDA_TRY(cudaStreamSynchronize(S->st));
+    }
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_set_state(cgl_state* S, const double* host, size_t n) {
+    if (!S) return fail(CGL_EINVAL, "null state");
+    return upload_nodal(S, S->B.u, host, n);
+}
+
+extern "C" cgl_status cgl_set_base_state(cgl_state* S, const double* host, size_t n) {
+    if (!S) return fail(CGL_EINVAL, "null state");
+    return upload_nodal(S, S->B.un, host, n);
+}
+
+extern "C" cgl_status cgl_get_state(cgl_state* S, double* host, size_t n) {
+    if (!S || !host) return fail(CGL_EINVAL, "null argument");
+    if (n != state_count(S)) return fail(CGL_EINVAL, "expected %zu values, got %zu", state_count(S), n);
+    return download_any(S, S->B.u, true, host, n);
+}
+
+extern "C" cgl_status cgl_set_time(cgl_state* S, double t) {
+    if (!S) return fail(CGL_EINVAL, "null state");
+    if (!std::isfinite(t)) return fail(CGL_EINVAL, "time must be finite");
+    CUDA_TRY(cudaMemcpyAsync(S->B.t, &t, 8, cudaMemcpyHostToDevice, S->st));
+    CUDA_TRY(cudaStreamSynchronize(S->st));
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_get_time(cgl_state* S, double* t) {
+    if (!S || !t) return fail(CGL_EINVAL, "null argument");
+    return download_any(S, S->B.t, false, t, 1);
+}
+
+extern "C" cgl_status cgl_get_field(cgl_state* S, int32_t field, double* host, size_t n) {
+    if (!S || !host) return fail(CGL_EINVAL, "null argument");
+    const MeshDev& m = S->mesh->m;
+    const size_t E = m.E, NN = m.NN, nc = S->nc;
+    const void* src = nullptr;
+    size_t cnt = 0;
+    bool bulk = false;
+    switch (field) {
+        case CGL_FIELD_UE: src = S->B.ue; cnt = nc * E; break;
+        case CGL_FIELD_DTE: src = S->B.dte; cnt = E; break;
+        case CGL_FIELD_UBL: src = S->B.ubl; cnt = nc * E; break;
+        case CGL_FIELD_UBE: src = S->B.ube; cnt = nc * E; break;
+        case CGL_FIELD_GAMMA: src = S->B.gam; cnt = E; break;
+        case CGL_FIELD_NU: src = S->B.nu; cnt = E; break;
+        case CGL_FIELD_BETA: src = S->B.beta; cnt = E; break;
+        case CGL_FIELD_GX: src = S->B.g; cnt = nc * NN; bulk = true; break;
+        case CGL_FIELD_GY: src = (const char*)S->B.g + nc * NN * S->rsz; cnt = nc * NN; bulk = true; break;
+        case CGL_FIELD_R: src = S->B.r; cnt = nc * NN; bulk = true; break;
+        case CGL_FIELD_UDOT: src = S->B.ud; cnt = nc * NN; bulk = true; break;
+        default: return fail(CGL_EINVAL, "unknown field %d", field);
+    }
+    if (n != cnt) return fail(CGL_EINVAL, "field %d has %zu values, got %zu", field, cnt, n);
+    return download_any(S, src, bulk, host, n);
+}
+
+// ---------------------------------------------------------------------------
+// stepping
+// ---------------------------------------------------------------------------
+template <class R, int NC>
+__global__ void k_diag(MeshDev m, const R* __restrict__ u, double* __restrict__ part) {
+    // per block: mass, min, max of each component (fixed-order grid-stride loop)
+    __shared__ double sm[3][NC][256];
+    double ms[NC], mn[NC], mx[NC];
+    for (int c = 0; c < NC; ++c) {
+        ms[c] = 0.0;
+        mn[c] = INFINITY;
+        mx[c] = -INFINITY;
+    }
+    const double me = m.h * m.h / ((m.p + 1) * (m.p + 1));
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < m.NN;
+         n += (long long)gridDim.x * blockDim.x) {
+        int gx = (int)(n % m.nnx), gy = (int)(n / m.nnx);
+        NodeCands nc = node_cands(m, gx, gy);
+        double mi = (double)(nc.nxc * nc.nyc) * me;
+        for (int c = 0; c < NC; ++c) {
+            double v = (double)u[c * m.NN + n];
+            ms[c] += mi * v;
+            mn[c] = fmin(mn[c], v);
+            mx[c] = fmax(mx[c], v);
+        }
+    }
+    for (int c = 0; c < NC; ++c) {
+        sm[0][c][threadIdx.x] = ms[c];
+        sm[1][c][threadIdx.x] = mn[c];
+        sm[2][c][threadIdx.x] = mx[c];
+    }
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int c = 0; c < NC; ++c) {
+                sm[0][c][threadIdx.x] += sm[0][c][threadIdx.x + s];
+                sm[1][c][threadIdx.x] = fmin(sm[1][c][threadIdx.x], sm[1][c][threadIdx.x + s]);
+                sm[2][c][threadIdx.x] = fmax(sm[2][c][threadIdx.x], sm[2][c][threadIdx.x + s]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < NC; ++c)
+            for (int k = 0; k < 3; ++k) part[(blockIdx.x * 3 + k) * 4 + c] = sm[k][c][0];
+}
+
+static cgl_status read_info(cgl_state* S, cgl_step_info* info, long long steps, unsigned long long* c0) {
+    unsigned long long cnt[CNT_N];
+    CUDA_TRY(cudaMemcpyAsync(cnt, S->B.cnt, sizeof(cnt), cudaMemcpyDeviceToHost, S->st));
+    const MeshDev& m = S->mesh->m;
+    const int NB = 1024;
+    if (S->prec == CGL_FP64) {
+        if (S->nc == 1) k_diag<double, 1><<<NB, 256, 0, S->st>>>(m, (const double*)S->B.u, S->diag);
+        else k_diag<double, 4><<<NB, 256, 0, S->st>>>(m, (const double*)S->B.u, S->diag);
+    } else {
+        if (S->nc == 1) k_diag<float, 1><<<NB, 256, 0, S->st>>>(m, (const float*)S->B.u, S->diag);
+        else k_diag<float, 4><<<NB, 256, 0, S->st>>>(m, (const float*)S->B.u, S->diag);
+    }
+    CUDA_TRY(cudaGetLastError());
+    std::vector<double> part((size_t)NB * 12);
+    CUDA_TRY(cudaMemcpyAsync(part.data(), S->diag, part.size() * 8, cudaMemcpyDeviceToHost, S->st));
+    double t = 0.0, dt = 0.0;
+    CUDA_TRY(cudaMemcpyAsync(&t, S->B.t, 8, cudaMemcpyDeviceToHost, S->st));
+    CUDA_TRY(cudaMemcpyAsync(&dt, S->B.dt, 8, cudaMemcpyDeviceToHost, S->st));
+    CUDA_TRY(cudaStreamSynchronize(S->st));
+    unsigned long long d[CNT_N];
+    for (int k = 0; k < CNT_N; ++k) d[k] = cnt[k] - (c0 ? c0[k] : 0ull);
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->t = t;
+        info->dt_last = dt;
+        info->steps = steps;
+        info->violations = (int64_t)d[CNT_VIOL];
+        info->clamps = (int64_t)d[CNT_CLAMP];
+        info->cfl_violations = (int64_t)d[CNT_CFL];
+        for (int c = 0; c < S->nc; ++c) {
+            double ms = 0.0, mn = INFINITY, mx = -INFINITY;
+            for (int b = 0; b < NB; ++b) {
+                ms += part[(b * 3 + 0) * 4 + c];
+                mn = std::fmin(mn, part[(b * 3 + 1) * 4 + c]);
+                mx = std::fmax(mx, part[(b * 3 + 2) * 4 + c]);
+            }
+            info->mass[c] = ms;
+            info->umin[c] = mn;
+            info->umax[c] = mx;
+        }
+    }
+    if (d[CNT_NONFINITE]) return fail(CGL_ENONFINITE, "%llu non-finite values", d[CNT_NONFINITE]);
+    if (d[CNT_VIOL]) return fail(CGL_EIDP, "%llu invariant-domain violations", d[CNT_VIOL]);
+    return CGL_OK;
+}
+
+static cudaError_t enqueue_step(cgl_state* S, Prof* prof = nullptr) {
+    const MeshDev& m = S->mesh->m;
+    const Bufs& B = S->B;
+    cudaError_t e = cudaSuccess;
+    CGL_LAUNCH(prof, KID_COPY, S->st,
+               (e = cudaMemcpyAsync(B.un, B.u, (size_t)S->nc * m.NN * S->rsz, cudaMemcpyDeviceToDevice, S->st)));
+    if (e != cudaSuccess) return e;
+    e = S->stage(B, m, S->pd, 0.0, 1.0, true, false, S->st, prof);
+    if (e != cudaSuccess) return e;
+    e = S->stage(B, m, S->pd, 0.75, 0.25, false, false, S->st, prof);
+    if (e != cudaSuccess) return e;
+    e = S->stage(B, m, S->pd, 1.0 / 3.0, 2.0 / 3.0, false, false, S->st, prof);
+    if (e != cudaSuccess) return e;
+    CGL_LAUNCH(prof, KID_TADV, S->st, (k_t_advance<<<1, 1, 0, S->st>>>(B.t, B.dt)));
+    return cudaGetLastError();
+}
+
+static cgl_status build_graph(cgl_state* S) {
+    if (S->step_graph) return CGL_OK;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(S->st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_step(S);
+    cudaError_t e2 = cudaStreamEndCapture(S->st, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(CGL_ECUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&S->step_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        S->step_graph = nullptr;
+        return fail(CGL_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    }
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_step(cgl_state* S, int32_t nsteps, double t_end, cgl_step_info* info) {
+    if (!S) return fail(CGL_EINVAL, "null state");
+    if (!S->has_problem) return fail(CGL_EINVAL, "cgl_set_problem first");
+    if (nsteps < 0) return fail(CGL_EINVAL, "nsteps < 0");
+    if (std::isnan(t_end)) return fail(CGL_EINVAL, "t_end is NaN");
+    unsigned long long c0[CNT_N];
+    CUDA_TRY(cudaMemcpyAsync(c0, S->B.cnt, sizeof(c0), cudaMemcpyDeviceToHost, S->st));
+    CUDA_TRY(cudaMemcpyAsync(S->B.t_end, &t_end, 8, cudaMemcpyHostToDevice, S->st));
+    CUDA_TRY(cudaStreamSynchronize(S->st));
+    cgl_status rc = build_graph(S);
+    if (rc) return rc;
+    long long taken = 0;
+    const bool finite_end = std::isfinite(t_end);
+    for (int s = 0; s < nsteps; ++s) {
+        if (finite_end) {
+            double t;
+            CUDA_TRY(cudaMemcpyAsync(&t, S->B.t, 8, cudaMemcpyDeviceToHost, S->st));
+            CUDA_TRY(cudaStreamSynchronize(S->st));
+            if (t >= t_end) break;
+        }
+        CUDA_TRY(cudaGraphLaunch(S->step_graph, S->st));
+        ++taken;
+    }
+    return read_info(S, info, taken, c0);
+}
+
+extern "C" cgl_status cgl_stage(cgl_state* S, double dt, double a, double b, cgl_step_info* info) {
+    if (!S) return fail(CGL_EINVAL, "null state");
+    if (!S->has_problem) return fail(CGL_EINVAL, "cgl_set_problem first");
+    if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(CGL_EINVAL, "dt must be finite and >= 0");
+    unsigned long long c0[CNT_N];
+    CUDA_TRY(cudaMemcpyAsync(c0, S->B.cnt, sizeof(c0), cudaMemcpyDeviceToHost, S->st));
+    CUDA_TRY(cudaMemcpyAsync(S->B.dt, &dt, 8, cudaMemcpyHostToDevice, S->st));
+    CUDA_TRY(cudaStreamSynchronize(S->st));
+    CUDA_TRY(S->stage(S->B, S->mesh->m, S->pd, a, b, false, false, S->st, nullptr));
+    return read_info(S, info, 0, c0);
+}
+
+extern "C" cgl_status cgl_time_step(cgl_state* S, double* dt) {
+    if (!S || !dt) return fail(CGL_EINVAL, "null argument");
+    if (!S->has_problem) return fail(CGL_EINVAL, "cgl_set_problem first");
+    // dt = cfl * min_e dt_e of the current state, without the t_end cap
+    double inf = std::numeric_limits<double>::infinity(), t_end = 0.0;
+    CUDA_TRY(cudaMemcpyAsync(&t_end, S->B.t_end, 8, cudaMemcpyDeviceToHost, S->st));
+    CUDA_TRY(cudaStreamSynchronize(S->st));
+    CUDA_TRY(cudaMemcpyAsync(S->B.t_end, &inf, 8, cudaMemcpyHostToDevice, S->st));
+    CUDA_TRY(S->stage(S->B, S->mesh->m, S->pd, 0.0, 1.0, true, true, S->st, nullptr));
+    CUDA_TRY(cudaMemcpyAsync(dt, S->B.dt, 8, cudaMemcpyDeviceToHost, S->st));
+    CUDA_TRY(cudaMemcpyAsync(S->B.t_end, &t_end, 8, cudaMemcpyHostToDevice, S->st));
+    CUDA_TRY(cudaStreamSynchronize(S->st));
+    return CGL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// per-kernel timing
+// ---------------------------------------------------------------------------
+static const char* const KNAMES[KID_COUNT] = {
+    "k_avg", "k_pre", "k_dt", "k_grad_ev", "k_gather_init", "k_mass_ev", "k_gather_sweep",
+    "k_res_ev", "k_update_ev", "k_final", "k_t_advance", "copy_u_un"};
+
+extern "C" const char* cgl_kernel_name(int32_t id) {
+    return (id >= 0 && id < KID_COUNT) ? KNAMES[id] : "";
+}
+
+extern "C" cgl_status cgl_profile(cgl_state* S, int32_t nsteps, int32_t nk, double* ms, int64_t* launches) {
+    if (!S || !ms || !launches) return fail(CGL_EINVAL, "null argument");
+    if (!S->has_problem) return fail(CGL_EINVAL, "cgl_set_problem first");
+    if (nk < KID_COUNT) return fail(CGL_EINVAL, "need room for %d kernels", (int)KID_COUNT);
+    if (nsteps < 1 || nsteps > 1000) return fail(CGL_EINVAL, "nsteps in [1, 1000]");
+    Prof P;
+    P.cap = nsteps * (40 + 6 * (S->prob.k_g + S->prob.k_u));
+    P.n = 0;
+    std::vector<Prof::Rec> recs(P.cap);
+    P.recs = recs.data();
+    for (auto& r : recs) {
+        r.a = r.b = nullptr;
+    }
+    cgl_status rc = CGL_OK;
+    for (auto& r : recs) {
+        if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+            rc = fail(CGL_ECUDA, "cudaEventCreate failed");
+            break;
+        }
+    }
+    if (rc == CGL_OK) {
+        for (int s = 0; s < nsteps && rc == CGL_OK; ++s) {
+            cudaError_t e = enqueue_step(S, &P);
+            if (e != cudaSuccess) rc = fail(CGL_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+        }
+        cudaError_t e = cudaStreamSynchronize(S->st);
+        if (rc == CGL_OK && e != cudaSuccess) rc = fail(CGL_ECUDA, "profile run: %s", cudaGetErrorString(e));
+    }
+    if (rc == CGL_OK) {
+        for (int k = 0; k < nk; ++k) {
+            ms[k] = 0.0;
+            launches[k] = 0;
+        }
+        for (int i = 0; i < P.n; ++i) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, recs[i].a, recs[i].b);
+            ms[recs[i].id] += t;
+            launches[recs[i].id] += 1;
+        }
+    }
+    for (auto& r : recs) {
+        if (r.a) cudaEventDestroy(r.a);
+        if (r.b) cudaEventDestroy(r.b);
+    }
+    return rc;
+}
+
+extern "C" cgl_status cgl_launches_per_step(cgl_state* S, int64_t* kernels) {
+    if (!S || !kernels) return fail(CGL_EINVAL, "null argument");
+    if (!S->has_problem) return fail(CGL_EINVAL, "cgl_set_problem first");
+    const int lo = S->prob.mode == CGL_MODE_LO;
+    int64_t per_stage = 2 + 2 + (lo ? 0 : 4 + 2 * (S->prob.k_g + S->prob.k_u));
+    *kernels = 3 * per_stage + 3 + 1;  // + dt reduction (3) + time advance (1)
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_step_async(cgl_state* S, int32_t nsteps) {
+    if (!S) return fail(CGL_EINVAL, "null state");
+    if (!S->has_problem) return fail(CGL_EINVAL, "cgl_set_problem first");
+    if (nsteps < 0) return fail(CGL_EINVAL, "nsteps < 0");
+    cgl_status rc = build_graph(S);
+    if (rc) return rc;
+    for (int s = 0; s < nsteps; ++s) CUDA_TRY(cudaGraphLaunch(S->step_graph, S->st));
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_get_counters(cgl_state* S, int64_t* out4) {
+    if (!S || !out4) return fail(CGL_EINVAL, "null argument");
+    unsigned long long cnt[CNT_N];
+    CUDA_TRY(cudaMemcpyAsync(cnt, S->B.cnt, sizeof(cnt), cudaMemcpyDeviceToHost, S->st));
+    CUDA_TRY(cudaStreamSynchronize(S->st));
+    out4[0] = (int64_t)cnt[CNT_VIOL];
+    out4[1] = (int64_t)cnt[CNT_CLAMP];
+    out4[2] = (int64_t)cnt[CNT_CFL];
+    out4[3] = (int64_t)cnt[CNT_NONFINITE];
+    return CGL_OK;
+}

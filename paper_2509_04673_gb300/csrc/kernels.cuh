@@ -1,0 +1,1045 @@
+// kernels.cuh — CUDA kernels of one SSP-RK stage of the element-based
+// convex-limited CG-WENO scheme (Kuzmin, Hajduk, Vedral, arXiv 2509.04673),
+// following the order of the algorithm summary in Sec. 4.3:
+//
+//   k_avg        cell averages u^e (eq. (ueold)), f(u^e), lambda_e
+//   k_pre        facet speeds, dt_e (eq. (dtmaxcell)), f^L, ubar^{e,L}
+//                (eq. (uelowFCT)), WENO sensor gamma_e (eqs. (WENO:alpha),
+//                (WENO:norm)), nu_e (eq. (stab:WENO))
+//   k_dt_*       global dt = omega_CFL min_e dt_e (eq. (cflglob), Sec. 5)
+//   k_grad_ev    element vectors int phi_i grad u_h for g_h
+//   k_res_ev     element residual: Galerkin part of eq. (weak:stab2) with
+//                boundary terms (eqs. (aec), (aecb)) and s_h (eq. (stab:WENO))
+//   k_mass_ev    consistent-mass products for the Richardson sweeps
+//   k_gather_*   node-centric sums over E_i in a fixed order (deterministic)
+//   k_update_ev  facet fluxes f^H (eq. (hoflux)), flux limiter (eq. (fAlim),
+//                Appendix A), ubar^e (eq. (uelim)), f_i^e (eq. (aec)),
+//                beta_e (eqs. (slimit1), (slimit2), Appendix A), element
+//                contributions of eq. (eq:SSPupdate)
+//   k_final      node gather, SSP-RK combination, invariant-domain check
+//
+// One thread per element (or node). Kernels are templated on the bulk
+// precision R (double, or float in the mixed form), the degree P and the
+// physics policy Ph. Cell averages, dt_e, facet fluxes, the flux limiter,
+// limiter bound gaps and final nodal sums are float64 in both forms.
+#pragma once
+
+#include "common.cuh"
+
+namespace cgl {
+
+template <int P>
+struct Dim {
+    static constexpr int N1 = P + 1, N2 = N1 * N1, NQ = P + 2;
+};
+
+enum { CNT_VIOL = 0, CNT_CLAMP = 1, CNT_CFL = 2, CNT_NONFINITE = 3, CNT_N = 8 };
+
+// global node of local (a, b) in element (ex, ey); periodic wrap at the far side
+DEV long long node_of(const MeshDev& m, int ex, int ey, int a, int b) {
+    int gx = ex * m.p + a, gy = ey * m.p + b;
+    if (m.px && gx == m.nnx) gx = 0;
+    if (m.py && gy == m.nny) gy = 0;
+    return (long long)gy * m.nnx + gx;
+}
+
+// face neighbour (0 W, 1 E, 2 S, 3 N) or -1 on a non-periodic boundary
+DEV int neighbour(const MeshDev& m, int ex, int ey, int dir) {
+    int jx = ex, jy = ey;
+    if (dir == 0) jx = ex - 1;
+    else if (dir == 1) jx = ex + 1;
+    else if (dir == 2) jy = ey - 1;
+    else jy = ey + 1;
+    if (jx < 0 || jx >= m.nx) {
+        if (!m.px) return -1;
+        jx = (jx + m.nx) % m.nx;
+    }
+    if (jy < 0 || jy >= m.ny) {
+        if (!m.py) return -1;
+        jy = (jy + m.ny) % m.ny;
+    }
+    return jy * m.nx + jx;
+}
+
+template <class R, int P, int NC>
+DEV void load_block(const R* __restrict__ u, const MeshDev& m, int ex, int ey,
+                    R (&U)[NC][Dim<P>::N2]) {
+    constexpr int N1 = P + 1;
+#pragma unroll
+    for (int b = 0; b < N1; ++b)
+#pragma unroll
+        for (int a = 0; a < N1; ++a) {
+            long long g = node_of(m, ex, ey, a, b);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) U[c][b * N1 + a] = u[c * m.NN + g];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// k_avg: u^e = mean of the coefficients (m_i^e = |K|/(p+1)^2), f(u^e), and
+// lambda_e = max over coefficients of the speed bound.
+// ---------------------------------------------------------------------------
+template <class R, int P, class Ph>
+__global__ void k_avg(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __restrict__ ue,
+                      double* __restrict__ fue, double* __restrict__ lame) {
+    constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.E) return;
+    int ex = e % m.nx, ey = e / m.nx;
+    R U[NC][N2];
+    load_block<R, P, NC>(u, m, ex, ey, U);
+    double avg[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < N2; ++i) s += (double)U[c][i];
+        avg[c] = s / N2;
+        ue[c * m.E + e] = avg[c];
+    }
+    double fx[NC], fy[NC];
+    Ph::template flux<double>(avg, fx, fy, pr);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        fue[(2 * c) * m.E + e] = fx[c];
+        fue[(2 * c + 1) * m.E + e] = fy[c];
+    }
+    R lm = R(0);
+#pragma unroll
+    for (int i = 0; i < N2; ++i) {
+        R ui[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ui[c] = U[c][i];
+        lm = fmax(lm, Ph::template node_speed<R>(ui, pr));
+    }
+    lame[e] = (double)lm;
+}
+
+// ---------------------------------------------------------------------------
+// low-order facet quantities of element e on its four faces in the canonical
+// orientation (normal +x for W/E, +y for S/N): lambda and F^L = F(u^L, u^R)
+// with f^L of Sec. 4; on a non-periodic boundary the external state is
+// u_hat (FIXED) or u^e itself (OUTFLOW) and the cell's outward normal is used.
+// ---------------------------------------------------------------------------
+template <class Ph>
+DEV void lo_facets(const MeshDev& m, const ProbDev& pr, const double* __restrict__ ue,
+                   const double* __restrict__ fue, int e, int ex, int ey, const int (&nb)[4],
+                   double (&lam)[4], double (&FL)[4][Ph::NC]) {
+    constexpr int NC = Ph::NC;
+    double us[NC], fxs[NC], fys[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        us[c] = ue[c * m.E + e];
+        fxs[c] = fue[(2 * c) * m.E + e];
+        fys[c] = fue[(2 * c + 1) * m.E + e];
+    }
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const double cnx = (d < 2) ? 1.0 : 0.0, cny = (d < 2) ? 0.0 : 1.0;
+        const bool self_is_L = (d == 1 || d == 3);
+        if (nb[d] >= 0) {
+            int o = nb[d];
+            double uo[NC], fxo[NC], fyo[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                uo[c] = ue[c * m.E + o];
+                fxo[c] = fue[(2 * c) * m.E + o];
+                fyo[c] = fue[(2 * c + 1) * m.E + o];
+            }
+            const double* uL = self_is_L ? us : uo;
+            const double* uR = self_is_L ? uo : us;
+            const double* fxL = self_is_L ? fxs : fxo;
+            const double* fyL = self_is_L ? fys : fyo;
+            const double* fxR = self_is_L ? fxo : fxs;
+            const double* fyR = self_is_L ? fyo : fys;
+            double l = Ph::template max_speed<double>(uL, uR, cnx, cny, pr);
+            lam[d] = l;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                double nL = fxL[c] * cnx + fyL[c] * cny;
+                double nR = fxR[c] * cnx + fyR[c] * cny;
+                FL[d][c] = 0.5 * (nL + nR) - 0.5 * l * (uR[c] - uL[c]);
+            }
+        } else {
+            const int bc = (d < 2) ? m.bc_x : m.bc_y;
+            double ux[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ux[c] = (bc == BC_FIXED) ? pr.ubc[c] : us[c];
+            const double sg = self_is_L ? 1.0 : -1.0;
+            double F[NC], l;
+            llf<Ph, double>(us, ux, sg * cnx, sg * cny, pr, F, &l);
+            lam[d] = l;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) FL[d][c] = sg * F[c];
+        }
+    }
+}
+
+// centred quadratic form of the semi-norm matrix A (A 1 = 0, so the
+// element mean is removed first to avoid cancellation)
+template <class R, int P>
+DEV R qform(const R (&v)[Dim<P>::N2]) {
+    constexpr int N2 = Dim<P>::N2;
+    constexpr int off = A2_OFF[P];
+    R mean = R(0);
+#pragma unroll
+    for (int i = 0; i < N2; ++i) mean += v[i];
+    mean = mean / R(N2);
+    R d[N2];
+#pragma unroll
+    for (int i = 0; i < N2; ++i) d[i] = v[i] - mean;
+    R s = R(0);
+#pragma unroll
+    for (int i = 0; i < N2; ++i) {
+        R t = R(0);
+#pragma unroll
+        for (int j = 0; j < N2; ++j) t += TabSel<R>::A2(off + i * N2 + j) * d[j];
+        s += d[i] * t;
+    }
+    return s;
+}
+
+// neighbour polynomial continued onto K_e: dir 0 W (Em in x), 1 E (Ep in x),
+// 2 S (Em in y), 3 N (Ep in y)
+template <class R, int P>
+DEV void continue_nb(int dir, const R (&src)[Dim<P>::N2], R (&dst)[Dim<P>::N2]) {
+    constexpr int N1 = P + 1;
+    const Tab<R>& T = TabSel<R>::t(P);
+#pragma unroll
+    for (int b = 0; b < N1; ++b)
+#pragma unroll
+        for (int a = 0; a < N1; ++a) {
+            R s = R(0);
+            if (dir < 2) {
+#pragma unroll
+                for (int c = 0; c < N1; ++c)
+                    s += (dir == 0 ? T.Em[a][c] : T.Ep[a][c]) * src[b * N1 + c];
+            } else {
+#pragma unroll
+                for (int d = 0; d < N1; ++d)
+                    s += (dir == 2 ? T.Em[b][d] : T.Ep[b][d]) * src[d * N1 + a];
+            }
+            dst[b * N1 + a] = s;
+        }
+}
+
+template <class R, int P, class Ph>
+DEV void load_comp(const R* __restrict__ u, const MeshDev& m, int e, int c, R (&V)[Dim<P>::N2]) {
+    constexpr int N1 = P + 1;
+    int ex = e % m.nx, ey = e / m.nx;
+#pragma unroll
+    for (int b = 0; b < N1; ++b)
+#pragma unroll
+        for (int a = 0; a < N1; ++a) V[b * N1 + a] = u[c * m.NN + node_of(m, ex, ey, a, b)];
+}
+
+// WENO smoothness sensor gamma_e, eq. (WENO:alpha), minimum over components.
+template <class R, int P, class Ph>
+DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
+             const R (&U)[Ph::NC][Dim<P>::N2], const int (&nb)[4]) {
+    constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
+    const R wl = R(pr.w_lin), eps = R(pr.weno_eps), geps = R(pr.gamma_eps);
+    const bool r2 = (pr.r == 2.0);
+    const R rh = R(0.5 * pr.r);
+    int ne = 0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) ne += (nb[d] >= 0);
+    R gam = R(1);
+#pragma unroll 1
+    for (int c = 0; c < NC; ++c) {
+        R U0[N2];
+#pragma unroll
+        for (int i = 0; i < N2; ++i) U0[i] = U[c][i];
+        R sig0 = fmax(qform<R, P>(U0), R(0));
+        R wt[5];
+        wt[0] = (R(1) - R(ne) * wl) / ((r2 ? sig0 : pow(sig0, rh)) + eps);
+#pragma unroll 1
+        for (int d = 0; d < 4; ++d) {
+            wt[d + 1] = R(0);
+            if (nb[d] >= 0) {
+                R V[N2], W[N2];
+                load_comp<R, P, Ph>(u, m, nb[d], c, V);
+                continue_nb<R, P>(d, V, W);
+                R sg = fmax(qform<R, P>(W), R(0));
+                wt[d + 1] = wl / ((r2 ? sg : pow(sg, rh)) + eps);
+            }
+        }
+        R tot = (((wt[0] + wt[1]) + wt[2]) + wt[3]) + wt[4];
+        R Us[N2];
+        R w0 = wt[0] / tot;
+#pragma unroll
+        for (int i = 0; i < N2; ++i) Us[i] = w0 * U0[i];
+#pragma unroll 1
+        for (int d = 0; d < 4; ++d) {
+            if (nb[d] >= 0) {
+                R V[N2], W[N2];
+                load_comp<R, P, Ph>(u, m, nb[d], c, V);
+                continue_nb<R, P>(d, V, W);
+                R wd = wt[d + 1] / tot;
+#pragma unroll
+                for (int i = 0; i < N2; ++i) Us[i] += wd * W[i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < N2; ++i) Us[i] = U0[i] - Us[i];
+        R num = sqrt(fmax(qform<R, P>(Us), R(0)));
+        R den = sqrt(sig0);
+        R ratio = num / (den + geps);
+        R gc = R(1) - pow(fmin(R(1), ratio), R(pr.q));
+        gam = fmin(gam, gc);
+    }
+    return gam;
+}
+
+// ---------------------------------------------------------------------------
+// k_pre: dt_e, ubar^{e,L}, gamma_e, nu_e
+// ---------------------------------------------------------------------------
+template <class R, int P, class Ph>
+__global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, const double* __restrict__ ue,
+                      const double* __restrict__ fue, const double* __restrict__ lame,
+                      double* __restrict__ dte_out, double* __restrict__ ubl_out,
+                      double* __restrict__ gam_out, double* __restrict__ nu_out) {
+    constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.E) return;
+    int ex = e % m.nx, ey = e / m.nx;
+    int nb[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
+    double lam[4], FL[4][NC];
+    lo_facets<Ph>(m, pr, ue, fue, e, ex, ey, nb, lam, FL);
+    double s = ((lam[0] + lam[1]) + lam[2]) + lam[3];
+    s = fmax(s, pr.lambda_floor);
+    const double h = m.h;
+    double dte = h * h / (h * s);
+    dte_out[e] = dte;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        double os = ((FL[1][c] - FL[0][c]) + FL[3][c]) - FL[2][c];
+        ubl_out[c * m.E + e] = ue[c * m.E + e] - (dte / h) * os;
+    }
+    double gam;
+    if (pr.mode == MODE_WENO || pr.mode == MODE_WENO_L) {
+        R U[NC][N2];
+        load_block<R, P, NC>(u, m, ex, ey, U);
+        gam = (double)sensor<R, P, Ph>(m, pr, u, U, nb);
+    } else {
+        gam = (pr.mode == MODE_HO) ? 1.0 : 0.0;
+    }
+    gam_out[e] = gam;
+    nu_out[e] = lame[e] * h / (2.0 * m.p);
+}
+
+// global dt: min over elements via an order-independent integer min on the
+// bit pattern of positive doubles (deterministic)
+static __global__ void k_dt_reset(unsigned long long* bits) { *bits = 0x7ff0000000000000ull; }
+
+static __global__ void k_dt_min(int E, const double* __restrict__ dte, unsigned long long* bits) {
+    __shared__ unsigned long long sm[32];
+    unsigned long long v = 0x7ff0000000000000ull;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+        unsigned long long b = (unsigned long long)__double_as_longlong(dte[e]);
+        v = b < v ? b : v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_down_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = (threadIdx.x < (blockDim.x >> 5)) ? sm[threadIdx.x] : 0x7ff0000000000000ull;
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long w = __shfl_down_sync(0xffffffffu, v, o);
+            v = w < v ? w : v;
+        }
+        if (threadIdx.x == 0) atomicMin(bits, v);
+    }
+}
+
+// dt = min(cfl * min_e dt_e, t_end - t), never negative
+static __global__ void k_dt_final(const unsigned long long* bits, double cfl, const double* t,
+                                  const double* t_end, double* dt) {
+    double d = cfl * __longlong_as_double((long long)*bits);
+    double rem = *t_end - *t;
+    if (rem < d) d = rem > 0.0 ? rem : 0.0;
+    *dt = d;
+}
+
+static __global__ void k_t_advance(double* t, const double* dt) { *t = *t + *dt; }
+
+// ---------------------------------------------------------------------------
+// k_grad_ev: b^e_i = (int phi_i d_x u_h, int phi_i d_y u_h), sum-factorised;
+// EV layout [(e*N2 + i)*NV + v], v = dim*NC + c, NV = 2 NC.
+// ---------------------------------------------------------------------------
+template <class R, int P, class Ph>
+__global__ void k_grad_ev(MeshDev m, const R* __restrict__ u, R* __restrict__ EV) {
+    constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2, NV = 2 * NC;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.E) return;
+    int ex = e % m.nx, ey = e / m.nx;
+    const Tab<R>& T = TabSel<R>::t(P);
+    const R h = R(m.h);
+    R U[NC][N2];
+    load_block<R, P, NC>(u, m, ex, ey, U);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        // x: bx[b][a] = h sum_d M[b][d] sum_c' C[c'][a] U[d][c']
+        R Y[N1][N1], Z[N1][N1];
+#pragma unroll
+        for (int d = 0; d < N1; ++d)
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                R sx = R(0), sy = R(0);
+#pragma unroll
+                for (int k = 0; k < N1; ++k) {
+                    sx += T.C[k][a] * U[c][d * N1 + k];
+                    sy += T.M[a][k] * U[c][d * N1 + k];
+                }
+                Y[d][a] = sx;
+                Z[d][a] = sy;
+            }
+#pragma unroll
+        for (int b = 0; b < N1; ++b)
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                R sx = R(0), sy = R(0);
+#pragma unroll
+                for (int d = 0; d < N1; ++d) {
+                    sx += T.M[b][d] * Y[d][a];
+                    sy += T.C[d][b] * Z[d][a];
+                }
+                long long base = ((long long)e * N2 + b * N1 + a) * NV;
+                EV[base + c] = h * sx;
+                EV[base + NC + c] = h * sy;
+            }
+    }
+}
+
+// k_mass_ev: (M_C x)^e_i = h^2 sum (M (x) M) x_e for NV nodal fields
+template <class R, int P, int NV>
+__global__ void k_mass_ev(MeshDev m, const R* __restrict__ x, R* __restrict__ EV) {
+    constexpr int N1 = P + 1, N2 = Dim<P>::N2;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.E) return;
+    int ex = e % m.nx, ey = e / m.nx;
+    const Tab<R>& T = TabSel<R>::t(P);
+    const R h2 = R(m.h * m.h);
+    R X[NV][N2];
+    load_block<R, P, NV>(x, m, ex, ey, X);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        R Y[N1][N1];
+#pragma unroll
+        for (int d = 0; d < N1; ++d)
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                R s = R(0);
+#pragma unroll
+                for (int k = 0; k < N1; ++k) s += T.M[a][k] * X[v][d * N1 + k];
+                Y[d][a] = s;
+            }
+#pragma unroll
+        for (int b = 0; b < N1; ++b)
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                R s = R(0);
+#pragma unroll
+                for (int d = 0; d < N1; ++d) s += T.M[b][d] * Y[d][a];
+                EV[((long long)e * N2 + b * N1 + a) * NV + v] = h2 * s;
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// node-centric gathers over E_i in a fixed order (lower neighbour first in
+// each direction): deterministic, no atomics.
+// ---------------------------------------------------------------------------
+struct NodeCands {
+    int nxc, nyc;
+    int ex[2], a[2], ey[2], b[2];
+};
+
+DEV NodeCands node_cands(const MeshDev& m, int gx, int gy) {
+    NodeCands nc;
+    const int p = m.p;
+    int ex = gx / p, a = gx - ex * p;
+    nc.nxc = 0;
+    if (a == 0) {
+        if (ex > 0 || m.px) {
+            nc.ex[nc.nxc] = (ex - 1 + m.nx) % m.nx;
+            nc.a[nc.nxc++] = p;
+        }
+        if (ex < m.nx) {
+            nc.ex[nc.nxc] = ex;
+            nc.a[nc.nxc++] = 0;
+        }
+    } else {
+        nc.ex[0] = ex;
+        nc.a[0] = a;
+        nc.nxc = 1;
+    }
+    int ey = gy / p, b = gy - ey * p;
+    nc.nyc = 0;
+    if (b == 0) {
+        if (ey > 0 || m.py) {
+            nc.ey[nc.nyc] = (ey - 1 + m.ny) % m.ny;
+            nc.b[nc.nyc++] = p;
+        }
+        if (ey < m.ny) {
+            nc.ey[nc.nyc] = ey;
+            nc.b[nc.nyc++] = 0;
+        }
+    } else {
+        nc.ey[0] = ey;
+        nc.b[0] = b;
+        nc.nyc = 1;
+    }
+    return nc;
+}
+
+// sum over E_i of element vectors; out[v*NN + node]; if xout, also x = sum / m_i
+template <class R, int NV>
+__global__ void k_gather_init(MeshDev m, const R* __restrict__ EV, R* __restrict__ bout,
+                              R* __restrict__ xout) {
+    long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= m.NN) return;
+    int gx = (int)(node % m.nnx), gy = (int)(node / m.nnx);
+    NodeCands nc = node_cands(m, gx, gy);
+    const int N1 = m.p + 1, N2 = N1 * N1;
+    R s[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s[v] = R(0);
+    for (int j = 0; j < nc.nyc; ++j)
+        for (int i = 0; i < nc.nxc; ++i) {
+            long long e = (long long)nc.ey[j] * m.nx + nc.ex[i];
+            long long base = (e * N2 + nc.b[j] * N1 + nc.a[i]) * NV;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) s[v] += EV[base + v];
+        }
+    const double mi = (double)(nc.nxc * nc.nyc) * (m.h * m.h / N2);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        if (bout) bout[v * m.NN + node] = s[v];
+        if (xout) xout[v * m.NN + node] = s[v] / R(mi);
+    }
+}
+
+// Richardson sweep x <- x + (b - sum EV) / m_i
+template <class R, int NV>
+__global__ void k_gather_sweep(MeshDev m, const R* __restrict__ EV, const R* __restrict__ b,
+                               R* __restrict__ x) {
+    long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= m.NN) return;
+    int gx = (int)(node % m.nnx), gy = (int)(node / m.nnx);
+    NodeCands nc = node_cands(m, gx, gy);
+    const int N1 = m.p + 1, N2 = N1 * N1;
+    R s[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s[v] = R(0);
+    for (int j = 0; j < nc.nyc; ++j)
+        for (int i = 0; i < nc.nxc; ++i) {
+            long long e = (long long)nc.ey[j] * m.nx + nc.ex[i];
+            long long base = (e * N2 + nc.b[j] * N1 + nc.a[i]) * NV;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) s[v] += EV[base + v];
+        }
+    const double mi = (double)(nc.nxc * nc.nyc) * (m.h * m.h / N2);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        long long k = v * m.NN + node;
+        x[k] = x[k] + (b[k] - s[v]) / R(mi);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_res_ev: R^e_i = W^e_i - s^e_i with
+//   W^e_i = int grad phi_i . f(u_h) - sum_{interior faces} int phi_i f_h.n
+//           - sum_{faces on dOmega} int phi_i F(u_h, u_hat; n)
+//   s^e_i = nu_e int grad phi_i . (grad u_h - gamma_e g_h)      eq. (stab:WENO)
+// (p+2)-point Gauss rule for nonlinear integrands; exact face mass for f_h.
+// ER layout [(e*N2 + i)*NC + c].
+// ---------------------------------------------------------------------------
+template <class R, int P, class Ph>
+__global__ void k_res_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ g,
+                         const double* __restrict__ gam, const double* __restrict__ nu,
+                         R* __restrict__ ER) {
+    constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2, NQ = Dim<P>::NQ;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.E) return;
+    int ex = e % m.nx, ey = e / m.nx;
+    const Tab<R>& T = TabSel<R>::t(P);
+    const R h = R(m.h);
+    R U[NC][N2];
+    load_block<R, P, NC>(u, m, ex, ey, U);
+    R W[NC][N2];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int i = 0; i < N2; ++i) W[c][i] = R(0);
+    // volume term: interpolate along x first
+    R X[NC][N1][NQ];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int d = 0; d < N1; ++d)
+#pragma unroll
+            for (int q1 = 0; q1 < NQ; ++q1) {
+                R s = R(0);
+#pragma unroll
+                for (int a = 0; a < N1; ++a) s += T.Bq[q1][a] * U[c][d * N1 + a];
+                X[c][d][q1] = s;
+            }
+#pragma unroll 1
+    for (int q2 = 0; q2 < NQ; ++q2) {
+        R Tx[NC][N1], Ty[NC][N1];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int a = 0; a < N1; ++a) Tx[c][a] = Ty[c][a] = R(0);
+#pragma unroll
+        for (int q1 = 0; q1 < NQ; ++q1) {
+            R uq[NC], fx[NC], fy[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                R s = R(0);
+#pragma unroll
+                for (int d = 0; d < N1; ++d) s += T.Bq[q2][d] * X[c][d][q1];
+                uq[c] = s;
+            }
+            Ph::template flux<R>(uq, fx, fy, pr);
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int a = 0; a < N1; ++a) {
+                    Tx[c][a] += T.wq[q1] * T.dBq[q1][a] * fx[c];
+                    Ty[c][a] += T.wq[q1] * T.Bq[q1][a] * fy[c];
+                }
+        }
+        const R hw = h * T.wq[q2];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int b = 0; b < N1; ++b)
+#pragma unroll
+                for (int a = 0; a < N1; ++a)
+                    W[c][b * N1 + a] += hw * (T.Bq[q2][b] * Tx[c][a] + T.dBq[q2][b] * Ty[c][a]);
+    }
+    // face terms
+    int nb[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const R nxo = (d == 0) ? R(-1) : (d == 1) ? R(1) : R(0);
+        const R nyo = (d == 2) ? R(-1) : (d == 3) ? R(1) : R(0);
+        R Uf[NC][N1];
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            int li = (d == 0) ? k * N1 : (d == 1) ? k * N1 + P : (d == 2) ? k : P * N1 + k;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) Uf[c][k] = U[c][li];
+        }
+        R term[NC][N1];
+        if (nb[d] >= 0) {
+            R fn[NC][N1];
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                R uk[NC], fx[NC], fy[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) uk[c] = Uf[c][k];
+                Ph::template flux<R>(uk, fx, fy, pr);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) fn[c][k] = fx[c] * nxo + fy[c] * nyo;
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int b = 0; b < N1; ++b) {
+                    R s = R(0);
+#pragma unroll
+                    for (int k = 0; k < N1; ++k) s += fn[c][k] * T.M[b][k];
+                    term[c][b] = h * s;
+                }
+        } else {
+            const int bc = (d < 2) ? m.bc_x : m.bc_y;
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int b = 0; b < N1; ++b) term[c][b] = R(0);
+#pragma unroll
+            for (int r = 0; r < NQ; ++r) {
+                R uq[NC], F[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    R s = R(0);
+#pragma unroll
+                    for (int k = 0; k < N1; ++k) s += Uf[c][k] * T.Bq[r][k];
+                    uq[c] = s;
+                }
+                if (bc == BC_FIXED) {
+                    R ub[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) ub[c] = R(pr.ubc[c]);
+                    llf<Ph, R>(uq, ub, nxo, nyo, pr, F, (R*)nullptr);
+                } else {
+                    R fx[NC], fy[NC];
+                    Ph::template flux<R>(uq, fx, fy, pr);
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) F[c] = fx[c] * nxo + fy[c] * nyo;
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int b = 0; b < N1; ++b) term[c][b] += (F[c] * T.wq[r]) * T.Bq[r][b];
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int b = 0; b < N1; ++b) term[c][b] *= h;
+        }
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            int li = (d == 0) ? k * N1 : (d == 1) ? k * N1 + P : (d == 2) ? k : P * N1 + k;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) W[c][li] -= term[c][k];
+        }
+    }
+    // stabilisation s = nu (K u - gamma (Gx gx + Gy gy))
+    const R nue = R(nu[e]), ge = R(gam[e]);
+#pragma unroll 1
+    for (int c = 0; c < NC; ++c) {
+        R GX[N2], GY[N2];
+#pragma unroll
+        for (int b = 0; b < N1; ++b)
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                long long n = node_of(m, ex, ey, a, b);
+                GX[b * N1 + a] = g[(long long)c * m.NN + n];
+                GY[b * N1 + a] = g[(long long)(NC + c) * m.NN + n];
+            }
+        // x-direction products: D u, M u, C gx, M gy
+        R Du[N1][N1], Mu[N1][N1], Cg[N1][N1], Mg[N1][N1];
+#pragma unroll
+        for (int d = 0; d < N1; ++d)
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                R s1 = R(0), s2 = R(0), s3 = R(0), s4 = R(0);
+#pragma unroll
+                for (int k = 0; k < N1; ++k) {
+                    s1 += T.D[a][k] * U[c][d * N1 + k];
+                    s2 += T.M[a][k] * U[c][d * N1 + k];
+                    s3 += T.C[a][k] * GX[d * N1 + k];
+                    s4 += T.M[a][k] * GY[d * N1 + k];
+                }
+                Du[d][a] = s1;
+                Mu[d][a] = s2;
+                Cg[d][a] = s3;
+                Mg[d][a] = s4;
+            }
+#pragma unroll
+        for (int b = 0; b < N1; ++b)
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                R ku = R(0), gg = R(0);
+#pragma unroll
+                for (int d = 0; d < N1; ++d) {
+                    ku += T.M[b][d] * Du[d][a] + T.D[b][d] * Mu[d][a];
+                    gg += T.M[b][d] * Cg[d][a] + T.C[b][d] * Mg[d][a];
+                }
+                R s = nue * (ku - ge * (h * gg));
+                ER[((long long)e * N2 + b * N1 + a) * NC + c] = W[c][b * N1 + a] - s;
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_update_ev: facet fluxes and flux limiter, ubar^e, f_i^e, beta_e and the
+// element contributions w_i^e = m_i^e [(1 - dt/dt_e) u_i + (dt/dt_e) ubar_i^e]
+// ---------------------------------------------------------------------------
+template <class R, int P, class Ph>
+__global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
+                            const double* __restrict__ ue, const double* __restrict__ fue,
+                            const double* __restrict__ dte_a, const double* __restrict__ ubl,
+                            const R* __restrict__ ER, const double* __restrict__ dtp,
+                            double* __restrict__ EW, double* __restrict__ ube_out,
+                            double* __restrict__ beta_out, unsigned long long* __restrict__ cnt) {
+    constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.E) return;
+    int ex = e % m.nx, ey = e / m.nx;
+    const Tab<R>& T = TabSel<R>::t(P);
+    const double h = m.h;
+    const double me = h * h / N2;
+    const double dt = *dtp;
+    const double dte = dte_a[e];
+    int nb[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
+    R U[NC][N2];
+    load_block<R, P, NC>(u, m, ex, ey, U);
+    double uec[NC], ublc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        uec[c] = ue[c * m.E + e];
+        ublc[c] = ubl[c * m.E + e];
+    }
+    // canonical high-order facet fluxes f^H (eq. (hoflux))
+    double FH[4][NC];
+    const bool need_fh = !(pr.mode == MODE_LO && pr.fl == FL_LOW);
+    if (need_fh) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            const R cnx = (d < 2) ? R(1) : R(0), cny = (d < 2) ? R(0) : R(1);
+            const int bc = (d < 2) ? m.bc_x : m.bc_y;
+            const bool fixed_b = (nb[d] < 0) && (bc == BC_FIXED);
+            const R sg = (d == 1 || d == 3) ? R(1) : R(-1);
+            double acc[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                int li = (d == 0) ? k * N1 : (d == 1) ? k * N1 + P : (d == 2) ? k : P * N1 + k;
+                R uk[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) uk[c] = U[c][li];
+                if (fixed_b) {
+                    R ub[NC], F[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) ub[c] = R(pr.ubc[c]);
+                    llf<Ph, R>(uk, ub, sg * cnx, sg * cny, pr, F, (R*)nullptr);
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) acc[c] += (double)F[c];
+                } else {
+                    R fx[NC], fy[NC];
+                    Ph::template flux<R>(uk, fx, fy, pr);
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) acc[c] += (double)(fx[c] * cnx + fy[c] * cny);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                FH[d][c] = fixed_b ? (double)sg * (acc[c] / N1) : acc[c] / N1;
+        }
+    }
+    // limited cell average ubar^e
+    double ubec[NC];
+    if (pr.fl == FL_LOW) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ubec[c] = ublc[c];
+    } else if (pr.fl == FL_NONE) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            double os = ((FH[1][c] - FH[0][c]) + FH[3][c]) - FH[2][c];
+            ubec[c] = uec[c] - (dte / h) * os;
+        }
+    } else {
+        double lam[4], FL[4][NC];
+        lo_facets<Ph>(m, pr, ue, fue, e, ex, ey, nb, lam, FL);
+        double FB[4][NC];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            const bool self_is_L = (d == 1 || d == 3);
+            double fA[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) fA[c] = FL[d][c] - FH[d][c];
+            // L and R cells of the canonical facet (-1: outside the domain)
+            const int Lc = self_is_L ? e : nb[d];
+            const int Rc = self_is_L ? nb[d] : e;
+            if (Ph::NC == 1) {
+                const double inf = __longlong_as_double(0x7ff0000000000000LL);
+                double fmaxv = inf, fminv = -inf;
+                if (Lc >= 0) {
+                    double dl = dte_a[Lc], bl = ubl[Lc];
+                    double Qp = fmax(0.0, (h / 4.0) * (pr.umax - bl) / dl);
+                    double Qm = fmin(0.0, (h / 4.0) * (pr.umin - bl) / dl);
+                    fmaxv = fmin(fmaxv, Qp);
+                    fminv = fmax(fminv, Qm);
+                }
+                if (Rc >= 0) {
+                    double dr = dte_a[Rc], br = ubl[Rc];
+                    double Qp = fmax(0.0, (h / 4.0) * (pr.umax - br) / dr);
+                    double Qm = fmin(0.0, (h / 4.0) * (pr.umin - br) / dr);
+                    fmaxv = fmin(fmaxv, -Qm);
+                    fminv = fmax(fminv, -Qp);
+                }
+                FB[d][0] = (fA[0] >= 0.0) ? fmin(fA[0], fmaxv) : fmax(fA[0], fminv);
+            } else {
+                double alpha = 1.0;
+                if (Lc >= 0) {
+                    double ub[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) ub[c] = ubl[c * m.E + Lc];
+                    double mL = (h / 4.0) / dte_a[Lc];
+                    alpha = fmin(alpha, euler_alpha<double>(ub, fA, mL, pr.pos_eps));
+                }
+                if (Rc >= 0) {
+                    double ub[NC], fm[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        ub[c] = ubl[c * m.E + Rc];
+                        fm[c] = -fA[c];
+                    }
+                    double mR = (h / 4.0) / dte_a[Rc];
+                    alpha = fmin(alpha, euler_alpha<double>(ub, fm, mR, pr.pos_eps));
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c) FB[d][c] = alpha * fA[c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            double os = ((FB[1][c] - FB[0][c]) + FB[3][c]) - FB[2][c];
+            ubec[c] = ublc[c] + (dte / h) * os;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ube_out[c * m.E + e] = ubec[c];
+    const double theta = dt / dte;
+    if (theta > 1.0) atomicAdd(&cnt[CNT_CFL], 1ull);
+    double beta = 0.0;
+    if (pr.mode == MODE_LO) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int i = 0; i < N2; ++i)
+                EW[((long long)e * N2 + i) * NC + c] =
+                    me * ((1.0 - theta) * (double)U[c][i] + theta * ubec[c]);
+        beta_out[e] = 0.0;
+        return;
+    }
+    // f_i^e, eq. (aec) with eq. (aecb) folded into the residual
+    R F[NC][N2];
+#pragma unroll 1
+    for (int c = 0; c < NC; ++c) {
+        R UD[N2];
+#pragma unroll
+        for (int b = 0; b < N1; ++b)
+#pragma unroll
+            for (int a = 0; a < N1; ++a)
+                UD[b * N1 + a] = ud[(long long)c * m.NN + node_of(m, ex, ey, a, b)];
+        R Y[N1][N1];
+#pragma unroll
+        for (int d = 0; d < N1; ++d)
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                R s = R(0);
+#pragma unroll
+                for (int k = 0; k < N1; ++k) s += T.M[a][k] * UD[d * N1 + k];
+                Y[d][a] = s;
+            }
+        const double fhs = ((FH[1][c] - FH[0][c]) + FH[3][c]) - FH[2][c];
+        const R fh_term = R((h / N2) * fhs);
+        const R h2 = R(h * h), meR = R(me), dteR = R(dte);
+#pragma unroll
+        for (int b = 0; b < N1; ++b)
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                R s = R(0);
+#pragma unroll
+                for (int d = 0; d < N1; ++d) s += T.M[b][d] * Y[d][a];
+                const int i = b * N1 + a;
+                R Ri = ER[((long long)e * N2 + i) * NC + c];
+                R dev = R((double)U[c][i] - uec[c]);
+                F[c][i] = meR * dev + dteR * (((Ri + fh_term) - h2 * s) + meR * UD[i]);
+            }
+    }
+    // slope limiter beta_e
+    if (pr.mode == MODE_WENO_L) {
+        if (Ph::NC == 1) {
+            double b = 1.0;
+            const double gp = me * (pr.umax - ubec[0]);
+            const double gm = me * (pr.umin - ubec[0]);
+#pragma unroll
+            for (int i = 0; i < N2; ++i) {
+                R f = F[0][i];
+                R bi = R(1);
+                if (f > R(0)) bi = fmin(R(1), R(gp) / f);
+                else if (f < R(0)) bi = fmin(R(1), R(gm) / f);
+                b = fmin(b, (double)bi);
+            }
+            beta = fmin(fmax(b, 0.0), 1.0);
+        } else {
+            double b = 1.0;
+#pragma unroll
+            for (int i = 0; i < N2; ++i) {
+                double f[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) f[c] = (double)F[c][i];
+                b = fmin(b, euler_alpha<double>(ubec, f, me, pr.pos_eps));
+            }
+            beta = b;
+        }
+    } else {
+        beta = 1.0;
+    }
+    beta_out[e] = beta;
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int i = 0; i < N2; ++i) {
+            double ubi = ubec[c] + (beta * (double)F[c][i]) / me;
+            EW[((long long)e * N2 + i) * NC + c] =
+                me * ((1.0 - theta) * (double)U[c][i] + theta * ubi);
+        }
+}
+
+// ---------------------------------------------------------------------------
+// k_final: u_i^SSP = sum_{e in E_i} w_i^e / m_i, RK combination a u^n + b u^SSP,
+// invariant-domain check and clamp (scalar IDP modes) / positivity count
+// (Euler), non-finite count; stores in the state precision.
+// ---------------------------------------------------------------------------
+template <class R, int NC>
+__global__ void k_final(MeshDev m, ProbDev pr, const double* __restrict__ EW,
+                        const R* __restrict__ un, R* __restrict__ u, double a, double b,
+                        unsigned long long* __restrict__ cnt) {
+    long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= m.NN) return;
+    int gx = (int)(node % m.nnx), gy = (int)(node / m.nnx);
+    NodeCands nc = node_cands(m, gx, gy);
+    const int N1 = m.p + 1, N2 = N1 * N1;
+    double s[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) s[c] = 0.0;
+    for (int j = 0; j < nc.nyc; ++j)
+        for (int i = 0; i < nc.nxc; ++i) {
+            long long e = (long long)nc.ey[j] * m.nx + nc.ex[i];
+            long long base = (e * N2 + nc.b[j] * N1 + nc.a[i]) * NC;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) s[c] += EW[base + c];
+        }
+    const double mi = (double)(nc.nxc * nc.nyc) * (m.h * m.h / N2);
+    double out[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        double ufe = s[c] / mi;
+        out[c] = (a != 0.0) ? a * (double)un[c * m.NN + node] + b * ufe : b * ufe;
+        if (!isfinite(out[c])) atomicAdd(&cnt[CNT_NONFINITE], 1ull);
+    }
+    if (NC == 1) {
+        if (pr.mode == MODE_LO || pr.mode == MODE_WENO_L) {
+            const double lo = (sizeof(R) == 4) ? pr.umin32 : pr.umin;
+            const double hi = (sizeof(R) == 4) ? pr.umax32 : pr.umax;
+            double v = out[0];
+            if (v < pr.umin - pr.viol_tol || v > pr.umax + pr.viol_tol)
+                atomicAdd(&cnt[CNT_VIOL], 1ull);
+            if (v < lo || v > hi) {
+                atomicAdd(&cnt[CNT_CLAMP], 1ull);
+                out[0] = fmin(fmax(v, lo), hi);
+            }
+        }
+    } else {
+        R uu[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) uu[c] = R(out[c]);
+        double dd[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) dd[c] = (double)uu[c];
+        double pres = PhysEuler::pressure<double>(dd, pr.gam);
+        if (!(dd[0] > 0.0) || !(pres > 0.0)) atomicAdd(&cnt[CNT_VIOL], 1ull);
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) u[c * m.NN + node] = R(out[c]);
+}
+
+}  // namespace cgl

@@ -1,0 +1,150 @@
+// stage.cuh — host-side launch sequence of one SSP-RK stage (Sec. 4.3 of
+// the paper: element loop, udot solve, facet loop, element loop, SSP update).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace cgl {
+
+// Device buffers of one state. R-typed arrays are void* here.
+struct Bufs {
+    void* u;      // state            [NC][NN]  (R)
+    void* un;     // RK base u^n      [NC][NN]  (R)
+    void* g;      // g_h              [2NC][NN] (R)
+    void* bg;     // rhs of g_h       [2NC][NN] (R)
+    void* r;      // target residual  [NC][NN]  (R)
+    void* ud;     // udot             [NC][NN]  (R)
+    void* EV;     // element vectors  [E][N2][2NC] (R)
+    void* ER;     // element residual [E][N2][NC]  (R)
+    double* EW;   // SSP contributions [E][N2][NC]
+    double *ue, *fue, *lame, *dte, *ubl, *gam, *nu, *ube, *beta;
+    unsigned long long* cnt;     // CNT_N counters
+    unsigned long long* dtbits;  // min dt_e as bits
+    double *dt, *t, *t_end;
+};
+
+// kernel identifiers for per-kernel timing
+enum KernelId {
+    KID_AVG = 0, KID_PRE, KID_DT, KID_GRAD, KID_GATHER, KID_MASS, KID_SWEEP, KID_RES,
+    KID_UPDATE, KID_FINAL, KID_TADV, KID_COPY, KID_COUNT
+};
+
+// optional per-launch timing: CUDA events recorded around every launch on
+// the launching stream (never used inside graph capture)
+struct Prof {
+    struct Rec { int id; cudaEvent_t a, b; };
+    Rec* recs;
+    int n, cap;
+    void begin(int id, cudaStream_t st) {
+        if (n < cap) {
+            recs[n].id = id;
+            cudaEventRecord(recs[n].a, st);
+        }
+    }
+    void end(cudaStream_t st) {
+        if (n < cap) cudaEventRecord(recs[n++].b, st);
+    }
+};
+
+#define CGL_LAUNCH(PROF, ID, ST, ...)             \
+    do {                                          \
+        if (PROF) (PROF)->begin((ID), (ST));      \
+        __VA_ARGS__;                              \
+        if (PROF) (PROF)->end((ST));              \
+    } while (0)
+
+// first: compute the global dt from this stage's dt_e (stage 1 of a step);
+// dt_only: stop after the dt reduction (time-step query)
+typedef cudaError_t (*StageFn)(const Bufs&, const MeshDev&, const ProbDev&, double a, double b,
+                               bool first, bool dt_only, cudaStream_t st, Prof* prof);
+
+inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+template <class R, int P, class Ph>
+cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, double a, double b,
+                      bool first, bool dt_only, cudaStream_t st, Prof* prof) {
+    ProbDev pr = pr_in;
+    if (dt_only) pr.mode = MODE_HO;  // no sensor needed for dt_e
+    constexpr int NC = Ph::NC;
+    const int BE = 128, BN = 256;
+    const unsigned ge = nblk(m.E, BE), gn = nblk(m.NN, BN);
+    R* u = (R*)B.u;
+    CGL_LAUNCH(prof, KID_AVG, st, (k_avg<R, P, Ph><<<ge, BE, 0, st>>>(m, pr, u, B.ue, B.fue, B.lame)));
+    CGL_LAUNCH(prof, KID_PRE, st,
+               (k_pre<R, P, Ph><<<ge, BE, 0, st>>>(m, pr, u, B.ue, B.fue, B.lame, B.dte, B.ubl, B.gam, B.nu)));
+    if (first) {
+        CGL_LAUNCH(prof, KID_DT, st, (k_dt_reset<<<1, 1, 0, st>>>(B.dtbits)));
+        CGL_LAUNCH(prof, KID_DT, st, (k_dt_min<<<nblk(m.E, 256), 256, 0, st>>>(m.E, B.dte, B.dtbits)));
+        CGL_LAUNCH(prof, KID_DT, st, (k_dt_final<<<1, 1, 0, st>>>(B.dtbits, pr.cfl, B.t, B.t_end, B.dt)));
+    }
+    if (dt_only) return cudaGetLastError();
+    if (pr.mode != MODE_LO) {
+        R* g = (R*)B.g;
+        R* bg = (R*)B.bg;
+        R* EV = (R*)B.EV;
+        CGL_LAUNCH(prof, KID_GRAD, st, (k_grad_ev<R, P, Ph><<<ge, BE, 0, st>>>(m, u, EV)));
+        CGL_LAUNCH(prof, KID_GATHER, st, (k_gather_init<R, 2 * NC><<<gn, BN, 0, st>>>(m, EV, bg, g)));
+        for (int k = 0; k < pr.k_g; ++k) {
+            CGL_LAUNCH(prof, KID_MASS, st, (k_mass_ev<R, P, 2 * NC><<<ge, BE, 0, st>>>(m, g, EV)));
+            CGL_LAUNCH(prof, KID_SWEEP, st, (k_gather_sweep<R, 2 * NC><<<gn, BN, 0, st>>>(m, EV, bg, g)));
+        }
+        R* ER = (R*)B.ER;
+        R* r = (R*)B.r;
+        R* ud = (R*)B.ud;
+        CGL_LAUNCH(prof, KID_RES, st, (k_res_ev<R, P, Ph><<<ge, BE, 0, st>>>(m, pr, u, g, B.gam, B.nu, ER)));
+        CGL_LAUNCH(prof, KID_GATHER, st, (k_gather_init<R, NC><<<gn, BN, 0, st>>>(m, ER, r, ud)));
+        for (int k = 0; k < pr.k_u; ++k) {
+            CGL_LAUNCH(prof, KID_MASS, st, (k_mass_ev<R, P, NC><<<ge, BE, 0, st>>>(m, ud, EV)));
+            CGL_LAUNCH(prof, KID_SWEEP, st, (k_gather_sweep<R, NC><<<gn, BN, 0, st>>>(m, EV, r, ud)));
+        }
+    }
+    CGL_LAUNCH(prof, KID_UPDATE, st,
+               (k_update_ev<R, P, Ph><<<ge, BE, 0, st>>>(m, pr, u, (const R*)B.ud, B.ue, B.fue, B.dte, B.ubl,
+                                                        (const R*)B.ER, B.dt, B.EW, B.ube, B.beta, B.cnt)));
+    CGL_LAUNCH(prof, KID_FINAL, st,
+               (k_final<R, NC><<<gn, BN, 0, st>>>(m, pr, B.EW, (const R*)B.un, u, a, b, B.cnt)));
+    return cudaGetLastError();
+}
+
+template <class Ph>
+StageFn select_stage(int prec, int p) {
+    if (prec == 0) {
+        switch (p) {
+            case 1: return run_stage<double, 1, Ph>;
+            case 2: return run_stage<double, 2, Ph>;
+            case 3: return run_stage<double, 3, Ph>;
+            case 4: return run_stage<double, 4, Ph>;
+        }
+    } else {
+        switch (p) {
+            case 1: return run_stage<float, 1, Ph>;
+            case 2: return run_stage<float, 2, Ph>;
+            case 3: return run_stage<float, 3, Ph>;
+            case 4: return run_stage<float, 4, Ph>;
+        }
+    }
+    return nullptr;
+}
+
+// copy the host tables into this translation unit's constant memory
+static inline cudaError_t upload_tables_here(const Tab<double>* td, const Tab<float>* tf,
+                                             const double* a2d, const float* a2f) {
+    cudaError_t e = cudaMemcpyToSymbol(c_tabd, td, sizeof(Tab<double>) * (PMAX + 1));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tabf, tf, sizeof(Tab<float>) * (PMAX + 1));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_A2d, a2d, sizeof(double) * A2_TOTAL);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_A2f, a2f, sizeof(float) * A2_TOTAL);
+    return e;
+}
+
+typedef cudaError_t (*UploadFn)(const Tab<double>*, const Tab<float>*, const double*, const float*);
+
+StageFn stage_fn_adv(int prec, int p);
+StageFn stage_fn_burgers(int prec, int p);
+StageFn stage_fn_kpp(int prec, int p);
+StageFn stage_fn_euler(int prec, int p);
+cudaError_t upload_adv(const Tab<double>*, const Tab<float>*, const double*, const float*);
+cudaError_t upload_burgers(const Tab<double>*, const Tab<float>*, const double*, const float*);
+cudaError_t upload_kpp(const Tab<double>*, const Tab<float>*, const double*, const float*);
+cudaError_t upload_euler(const Tab<double>*, const Tab<float>*, const double*, const float*);
+
+}  // namespace cgl
