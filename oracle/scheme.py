@@ -301,9 +301,10 @@ def outward_sum(om: OracleMesh, Fx, Fy):
 
 def _seminorm2(V, A2):
     """Squared semi-norm c^T A c of each row of V.  A annihilates constants
-    (the semi-norm has no k = 0 term), so the row mean is removed first; this
-    is exact algebra and avoids cancellation for nearly constant data."""
-    Vc = V - V.mean(axis=1, keepdims=True)
+    (the semi-norm has no k = 0 term), so each row is shifted by its first
+    entry first: exact algebra that gives exact zeros for constant data and
+    avoids cancellation for nearly constant data."""
+    Vc = V - V[:, :1]
     return np.einsum("ei,ij,ej->e", Vc, A2, Vc)
 
 
@@ -322,13 +323,17 @@ def sensor(om: OracleMesh, U, prob):
     gam = np.ones(om.E)
     exts = (om.ExtW, om.ExtE, om.ExtS, om.ExtN)
     for c in range(nc):
-        U0 = U[c]
+        # constants do not change any semi-norm, so every block is shifted by
+        # its first coefficient before it is continued or compared (exact
+        # algebra; keeps flat data exactly flat)
+        U0 = U[c] - U[c][:, :1]
         cands = [U0]
         present = [np.ones(om.E, dtype=bool)]
         for k in range(4):
             nb = om.nbr[:, k]
             ok = nb >= 0
             Un = U[c][np.where(ok, nb, 0)]
+            Un = Un - Un[:, :1]
             cands.append(Un @ exts[k].T)
             present.append(ok)
         ne = sum(pr.astype(float) for pr in present[1:])
@@ -338,8 +343,9 @@ def sensor(om: OracleMesh, U, prob):
             wl = (1.0 - ne * w_lin) if l == 0 else w_lin * pr
             wt.append(wl / (sig ** (0.5 * r) + eps))
         tot = sum(wt)
-        Us = sum((w / tot)[:, None] * Ul for w, Ul in zip(wt, cands))
-        dlt = U0 - Us
+        # u_h^e - u_h^{e,*} = sum_{l>=1} omega_l (u_h^e - u_{h,l}^e) since
+        # sum_l omega_l = 1 (no cancellation against omega_0 ~ 1)
+        dlt = sum((w / tot)[:, None] * (U0 - Ul) for w, Ul in zip(wt[1:], cands[1:]))
         num = np.sqrt(np.maximum(_seminorm2(dlt, A2), 0.0))
         den = np.sqrt(np.maximum(_seminorm2(U0, A2), 0.0))
         ratio = num / (den + geps)

@@ -175,19 +175,16 @@ DEV void lo_facets(const MeshDev& m, const ProbDev& pr, const double* __restrict
     }
 }
 
-// centred quadratic form of the semi-norm matrix A (A 1 = 0, so the
-// element mean is removed first to avoid cancellation)
+// quadratic form of the semi-norm matrix A; A annihilates constants, so the
+// block is shifted by its first coefficient first (exact zeros for constant
+// data, no cancellation for nearly constant data)
 template <class R, int P>
 DEV R qform(const R (&v)[Dim<P>::N2]) {
     constexpr int N2 = Dim<P>::N2;
     constexpr int off = A2_OFF[P];
-    R mean = R(0);
-#pragma unroll
-    for (int i = 0; i < N2; ++i) mean += v[i];
-    mean = mean / R(N2);
     R d[N2];
 #pragma unroll
-    for (int i = 0; i < N2; ++i) d[i] = v[i] - mean;
+    for (int i = 0; i < N2; ++i) d[i] = v[i] - v[0];
     R s = R(0);
 #pragma unroll
     for (int i = 0; i < N2; ++i) {
@@ -234,6 +231,9 @@ DEV void load_comp(const R* __restrict__ u, const MeshDev& m, int e, int c, R (&
 }
 
 // WENO smoothness sensor gamma_e, eq. (WENO:alpha), minimum over components.
+// Every block is shifted by its first coefficient (constants do not change
+// semi-norms) and u_h^e - u_h^{e,*} is formed as sum_{l>=1} omega_l
+// (u_h^e - u_{h,l}^e), using sum_l omega_l = 1.
 template <class R, int P, class Ph>
 DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
              const R (&U)[Ph::NC][Dim<P>::N2], const int (&nb)[4]) {
@@ -249,7 +249,7 @@ DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
     for (int c = 0; c < NC; ++c) {
         R U0[N2];
 #pragma unroll
-        for (int i = 0; i < N2; ++i) U0[i] = U[c][i];
+        for (int i = 0; i < N2; ++i) U0[i] = U[c][i] - U[c][0];
         R sig0 = fmax(qform<R, P>(U0), R(0));
         R wt[5];
         wt[0] = (R(1) - R(ne) * wl) / ((r2 ? sig0 : pow(sig0, rh)) + eps);
@@ -259,30 +259,33 @@ DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
             if (nb[d] >= 0) {
                 R V[N2], W[N2];
                 load_comp<R, P, Ph>(u, m, nb[d], c, V);
+                const R v0 = V[0];
+#pragma unroll
+                for (int i = 0; i < N2; ++i) V[i] -= v0;
                 continue_nb<R, P>(d, V, W);
                 R sg = fmax(qform<R, P>(W), R(0));
                 wt[d + 1] = wl / ((r2 ? sg : pow(sg, rh)) + eps);
             }
         }
         R tot = (((wt[0] + wt[1]) + wt[2]) + wt[3]) + wt[4];
-        R Us[N2];
-        R w0 = wt[0] / tot;
+        R Dl[N2];
 #pragma unroll
-        for (int i = 0; i < N2; ++i) Us[i] = w0 * U0[i];
+        for (int i = 0; i < N2; ++i) Dl[i] = R(0);
 #pragma unroll 1
         for (int d = 0; d < 4; ++d) {
             if (nb[d] >= 0) {
                 R V[N2], W[N2];
                 load_comp<R, P, Ph>(u, m, nb[d], c, V);
+                const R v0 = V[0];
+#pragma unroll
+                for (int i = 0; i < N2; ++i) V[i] -= v0;
                 continue_nb<R, P>(d, V, W);
                 R wd = wt[d + 1] / tot;
 #pragma unroll
-                for (int i = 0; i < N2; ++i) Us[i] += wd * W[i];
+                for (int i = 0; i < N2; ++i) Dl[i] += wd * (U0[i] - W[i]);
             }
         }
-#pragma unroll
-        for (int i = 0; i < N2; ++i) Us[i] = U0[i] - Us[i];
-        R num = sqrt(fmax(qform<R, P>(Us), R(0)));
+        R num = sqrt(fmax(qform<R, P>(Dl), R(0)));
         R den = sqrt(sig0);
         R ratio = num / (den + geps);
         R gc = R(1) - pow(fmin(R(1), ratio), R(pr.q));

@@ -55,6 +55,17 @@ def _gpu_stage(C, mesh, prob, u, un, dt, a, b, prec=0):
     return out, info, fields
 
 
+def _inward_f32(lo, hi):
+    """Bounds rounded inward to float32-representable values."""
+    l32 = np.float32(lo)
+    if float(l32) < lo:
+        l32 = np.nextafter(l32, np.float32(np.inf))
+    h32 = np.float32(hi)
+    if float(h32) > hi:
+        h32 = np.nextafter(h32, np.float32(-np.inf))
+    return float(l32), float(h32)
+
+
 def _case_state(mesh, prob, seed):
     if prob.flux == inputs.FLUX_EULER:
         return inputs.random_euler_state(mesh, seed), inputs.random_euler_state(mesh, seed + 1)
@@ -170,26 +181,35 @@ def test_determinism(cgl):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_full_size_bench_workload_stage(cgl, prec):
-    """KPP 256x256 Q2 (the bench workload), one full SSP-RK3 step compared
-    element by element with the oracle."""
+def test_full_size_bench_workload_stages(cgl, prec):
+    """KPP 256x256 Q2 (the bench workload): the three stages of one SSP-RK3
+    step, each started on both sides from the same input (the oracle's
+    previous stage), compared element by element with the oracle."""
     mesh, prob, u0 = inputs.kpp_config(256, 256, 2)
-    ref, t_ref, st = S.run(mesh, prob, u0, 1)
+    om = S.OracleMesh(mesh)
+    lo32, hi32 = _inward_f32(prob.umin, prob.umax)
+    if prec == 1:
+        u0 = np.clip(u0.astype(np.float32).astype(np.float64), lo32, hi32)
+    dt = S.time_step(om, prob, u0)
     m = cgl.Mesh(mesh)
     g = cgl.State(m, 1, prec)
     g.set_problem(prob)
-    g.set_state(u0)
-    g.set_time(0.0)
-    info = g.step(1)
-    out = g.get_state()
-    assert info["violations"] == 0
+    g.set_base_state(u0)
+    u = u0
     lo, hi = math.pi / 4, 3.5 * math.pi
-    assert out.min() >= lo and out.max() <= hi
-    if prec == 0:
-        assert _rel(out, ref, 1) <= TOL64
-    else:
-        l1 = np.abs(out - ref).sum() / np.abs(ref).sum()
-        assert l1 <= 2e-6, l1
+    for (a, b) in S.SSP3:
+        ref, info = S.ssp_stage(om, prob, u, u0, dt, a, b)
+        g.set_state(u)
+        ginfo = g.stage(dt, a, b)
+        out = g.get_state()
+        assert ginfo["violations"] == 0 and info["violations"] == 0
+        assert out.min() >= lo and out.max() <= hi
+        if prec == 0:
+            assert _rel(out, ref, 1) <= TOL64, _rel(out, ref, 1)
+        else:
+            l1 = np.abs(out - ref).sum() / np.abs(ref).sum()
+            assert l1 <= 2e-6, l1
+        u = ref if prec == 0 else np.clip(ref.astype(np.float32).astype(np.float64), lo32, hi32)
     g.close()
 
 
@@ -203,6 +223,9 @@ def test_stage_mixed_precision(cgl, name):
     # the oracle sees exactly the float32-rounded input
     u = u.astype(np.float32).astype(np.float64)
     un = un.astype(np.float32).astype(np.float64)
+    if prob.flux != inputs.FLUX_EULER:
+        lo32, hi32 = _inward_f32(prob.umin, prob.umax)
+        u, un = np.clip(u, lo32, hi32), np.clip(un, lo32, hi32)
     om = S.OracleMesh(mesh)
     dt = 0.5 * S.time_step(om, prob, u)
     ref, info = S.ssp_stage(om, prob, u, un, dt, 0.75, 0.25)
