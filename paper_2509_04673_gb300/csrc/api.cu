@@ -286,6 +286,13 @@ extern "C" cgl_status cgl_mesh_create(const cgl_mesh_desc* d, cgl_mesh** out) {
     m.E = d->nx * d->ny;
     m.NN = nnx * nny;
     m.h = hx;
+    const double n2 = (double)(d->p + 1) * (d->p + 1);
+    m.me = hx * hx / n2;
+    m.inv_me = 1.0 / m.me;
+    m.h_over_n2 = hx / n2;
+    m.inv_h = 1.0 / hx;
+    m.inv_n2 = 1.0 / n2;
+    m.inv_n1 = 1.0 / (d->p + 1);
     *out = M;
     return CGL_OK;
 }
@@ -420,9 +427,9 @@ extern "C" cgl_status cgl_state_create(const cgl_mesh* mesh, int32_t ncomp, int3
     struct A { void** p; size_t b; } list[] = {
         {&B.u, nc * NN * r},          {&B.un, nc * NN * r},        {&B.g, 2 * nc * NN * r},
         {&B.bg, 2 * nc * NN * r},     {&B.r, nc * NN * r},         {&B.ud, nc * NN * r},
-        {&B.EV, E * N2 * 2 * nc * r}, {&B.ER, E * N2 * nc * r},    {(void**)&B.EW, E * N2 * nc * 8},
+        {&B.EV, E * N2 * 2 * nc * r}, {&B.ER, E * N2 * nc * r},    {&B.EW, E * N2 * nc * r},     {(void**)&B.q, 2 * E * 8},
         {(void**)&B.ue, nc * E * 8},  {(void**)&B.fue, 2 * nc * E * 8}, {(void**)&B.lame, E * 8},
-        {(void**)&B.dte, E * 8},      {(void**)&B.ubl, nc * E * 8}, {(void**)&B.gam, E * 8},
+        {(void**)&B.dte, 3 * E * 8},  {(void**)&B.fl, 4 * nc * E * 8},      {(void**)&B.ubl, nc * E * 8}, {(void**)&B.gam, E * 8},
         {(void**)&B.nu, E * 8},       {(void**)&B.ube, nc * E * 8}, {(void**)&B.beta, E * 8},
         {(void**)&B.cnt, CNT_N * 8},  {(void**)&B.dtbits, 8},      {(void**)&B.dt, 8},
         {(void**)&B.t, 8},            {(void**)&B.t_end, 8},       {(void**)&S->diag, 1024 * 12 * 8},
@@ -444,6 +451,8 @@ extern "C" cgl_status cgl_state_create(const cgl_mesh* mesh, int32_t ncomp, int3
     }
     double inf = std::numeric_limits<double>::infinity();
     cudaMemcpyAsync(B.t_end, &inf, 8, cudaMemcpyHostToDevice, S->st);
+    const unsigned long long inf_bits = 0x7ff0000000000000ull;
+    cudaMemcpyAsync(B.dtbits, &inf_bits, 8, cudaMemcpyHostToDevice, S->st);
     cudaError_t e = cudaStreamSynchronize(S->st);
     if (e != cudaSuccess) {
         cgl_state_destroy(S);
@@ -858,8 +867,8 @@ extern "C" cgl_status cgl_launches_per_step(cgl_state* S, int64_t* kernels) {
     if (!S || !kernels) return fail(CGL_EINVAL, "null argument");
     if (!S->has_problem) return fail(CGL_EINVAL, "cgl_set_problem first");
     const int lo = S->prob.mode == CGL_MODE_LO;
-    int64_t per_stage = 2 + 2 + (lo ? 0 : 4 + 2 * (S->prob.k_g + S->prob.k_u));
-    *kernels = 3 * per_stage + 3 + 1;  // + dt reduction (3) + time advance (1)
+    int64_t per_stage = 2 + 2 + (lo ? 0 : 3 + 2 * (S->prob.k_g + S->prob.k_u));
+    *kernels = 3 * per_stage + 1 + 1;  // + dt finalisation (1) + time advance (1)
     return CGL_OK;
 }
 

@@ -27,6 +27,10 @@ struct MeshDev {
     int E;                 // nx*ny
     long long NN;          // nnx*nny
     double h;              // element side (square elements)
+    // host-precomputed constants (GB300's float64 divide is slow, so no
+    // kernel divides by mesh constants): m_i^e = h^2/(p+1)^2, 1/m_i^e,
+    // h/(p+1)^2, 1/h, 1/(p+1)^2, 1/(p+1)
+    double me, inv_me, h_over_n2, inv_h, inv_n2, inv_n1;
 };
 
 struct ProbDev {

@@ -75,13 +75,75 @@ DEV void load_block(const R* __restrict__ u, const MeshDev& m, int ex, int ey,
         }
 }
 
+// element mean of the coefficients as float64: plain sum for double data;
+// for float data a compensated (Neumaier) float sum widened once, accurate
+// to ~1e-14 relative without per-node float64 arithmetic
+template <int N>
+DEV double block_mean(const double (&v)[N]) {
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) s += v[i];
+    return s * (1.0 / N);
+}
+template <int N>
+DEV double block_mean(const float (&v)[N]) {
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        float t = s + v[i];
+        c += (fabsf(s) >= fabsf(v[i])) ? ((s - t) + v[i]) : ((v[i] - t) + s);
+        s = t;
+    }
+    return ((double)s + (double)c) * (1.0 / N);
+}
+
+// b^e_i = (int phi_i d_x u_h, int phi_i d_y u_h), sum-factorised, into EV
+// [(e*N2 + i)*2NC + v], v = dim*NC + c
+template <class R, int P, int NC>
+DEV void grad_vectors(const R (&U)[NC][Dim<P>::N2], R h, long long e, R* __restrict__ EV) {
+    constexpr int N1 = P + 1, N2 = Dim<P>::N2, NV = 2 * NC;
+    const Tab<R>& T = TabSel<R>::t(P);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        R Y[N1][N1], Z[N1][N1];
+#pragma unroll
+        for (int d = 0; d < N1; ++d)
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                R sx = R(0), sy = R(0);
+#pragma unroll
+                for (int k = 0; k < N1; ++k) {
+                    sx += T.C[k][a] * U[c][d * N1 + k];
+                    sy += T.M[a][k] * U[c][d * N1 + k];
+                }
+                Y[d][a] = sx;
+                Z[d][a] = sy;
+            }
+#pragma unroll
+        for (int b = 0; b < N1; ++b)
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                R sx = R(0), sy = R(0);
+#pragma unroll
+                for (int d = 0; d < N1; ++d) {
+                    sx += T.M[b][d] * Y[d][a];
+                    sy += T.C[d][b] * Z[d][a];
+                }
+                long long base = (e * N2 + b * N1 + a) * NV;
+                EV[base + c] = h * sx;
+                EV[base + NC + c] = h * sy;
+            }
+    }
+}
+
 // ---------------------------------------------------------------------------
-// k_avg: u^e = mean of the coefficients (m_i^e = |K|/(p+1)^2), f(u^e), and
-// lambda_e = max over coefficients of the speed bound.
+// k_avg: u^e = mean of the coefficients (m_i^e = |K|/(p+1)^2), f(u^e),
+// lambda_e = max over coefficients of the speed bound, and (if EV) the
+// element vectors of the g_h projection right-hand side.
 // ---------------------------------------------------------------------------
 template <class R, int P, class Ph>
 __global__ void k_avg(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __restrict__ ue,
-                      double* __restrict__ fue, double* __restrict__ lame) {
+                      double* __restrict__ fue, double* __restrict__ lame, R* __restrict__ EV) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m.E) return;
@@ -91,18 +153,19 @@ __global__ void k_avg(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __
     double avg[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        double s = 0.0;
-#pragma unroll
-        for (int i = 0; i < N2; ++i) s += (double)U[c][i];
-        avg[c] = s / N2;
+        avg[c] = block_mean<N2>(U[c]);
         ue[c * m.E + e] = avg[c];
     }
-    double fx[NC], fy[NC];
-    Ph::template flux<double>(avg, fx, fy, pr);
+    // f(u^e) in the bulk precision R (float64 in the FP64 form; the mixed
+    // form evaluates transcendental fluxes in float and widens the result)
+    R avgR[NC], fx[NC], fy[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) avgR[c] = R(avg[c]);
+    Ph::template flux<R>(avgR, fx, fy, pr);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        fue[(2 * c) * m.E + e] = fx[c];
-        fue[(2 * c + 1) * m.E + e] = fy[c];
+        fue[(2 * c) * m.E + e] = (double)fx[c];
+        fue[(2 * c + 1) * m.E + e] = (double)fy[c];
     }
     R lm = R(0);
 #pragma unroll
@@ -113,6 +176,7 @@ __global__ void k_avg(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __
         lm = fmax(lm, Ph::template node_speed<R>(ui, pr));
     }
     lame[e] = (double)lm;
+    if (EV) grad_vectors<R, P, NC>(U, R(m.h), e, EV);
 }
 
 // ---------------------------------------------------------------------------
@@ -121,7 +185,22 @@ __global__ void k_avg(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __
 // with f^L of Sec. 4; on a non-periodic boundary the external state is
 // u_hat (FIXED) or u^e itself (OUTFLOW) and the cell's outward normal is used.
 // ---------------------------------------------------------------------------
-template <class Ph>
+// upper bound of the facet speed, evaluated in precision RS: float64, or in
+// float with a 2^-20 relative inflation so that it stays an upper bound
+template <class Ph, class RS>
+DEV double facet_speed(const double* uL, const double* uR, double nx, double ny, const ProbDev& pr) {
+    if (sizeof(RS) == 8) return Ph::template max_speed<double>(uL, uR, nx, ny, pr);
+    float fL[Ph::NC], fR[Ph::NC];
+#pragma unroll
+    for (int c = 0; c < Ph::NC; ++c) {
+        fL[c] = (float)uL[c];
+        fR[c] = (float)uR[c];
+    }
+    float l = Ph::template max_speed<float>(fL, fR, (float)nx, (float)ny, pr);
+    return (double)l * (1.0 + 0x1p-20);
+}
+
+template <class Ph, class R, class RS = R>
 DEV void lo_facets(const MeshDev& m, const ProbDev& pr, const double* __restrict__ ue,
                    const double* __restrict__ fue, int e, int ex, int ey, const int (&nb)[4],
                    double (&lam)[4], double (&FL)[4][Ph::NC]) {
@@ -152,7 +231,7 @@ DEV void lo_facets(const MeshDev& m, const ProbDev& pr, const double* __restrict
             const double* fyL = self_is_L ? fys : fyo;
             const double* fxR = self_is_L ? fxo : fxs;
             const double* fyR = self_is_L ? fyo : fys;
-            double l = Ph::template max_speed<double>(uL, uR, cnx, cny, pr);
+            double l = facet_speed<Ph, RS>(uL, uR, cnx, cny, pr);
             lam[d] = l;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
@@ -166,11 +245,35 @@ DEV void lo_facets(const MeshDev& m, const ProbDev& pr, const double* __restrict
 #pragma unroll
             for (int c = 0; c < NC; ++c) ux[c] = (bc == BC_FIXED) ? pr.ubc[c] : us[c];
             const double sg = self_is_L ? 1.0 : -1.0;
-            double F[NC], l;
-            llf<Ph, double>(us, ux, sg * cnx, sg * cny, pr, F, &l);
+            // external state: f(u_hat) (FIXED) or the cell's own f(u^e) (OUTFLOW)
+            double fxx[NC], fyx[NC];
+            if (bc == BC_FIXED) {
+                R ubR[NC], fxR[NC], fyR[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) ubR[c] = R(ux[c]);
+                Ph::template flux<R>(ubR, fxR, fyR, pr);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    fxx[c] = (double)fxR[c];
+                    fyx[c] = (double)fyR[c];
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    fxx[c] = fxs[c];
+                    fyx[c] = fys[c];
+                }
+            }
+            const double nx = sg * cnx, ny = sg * cny;
+            double l = facet_speed<Ph, RS>(us, ux, nx, ny, pr);
             lam[d] = l;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) FL[d][c] = sg * F[c];
+            for (int c = 0; c < NC; ++c) {
+                double nL = fxs[c] * nx + fys[c] * ny;
+                double nR = fxx[c] * nx + fyx[c] * ny;
+                double F = 0.5 * (nL + nR) - 0.5 * l * (ux[c] - us[c]);
+                FL[d][c] = sg * F;
+            }
         }
     }
 }
@@ -297,127 +400,97 @@ DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
 // ---------------------------------------------------------------------------
 // k_pre: dt_e, ubar^{e,L}, gamma_e, nu_e
 // ---------------------------------------------------------------------------
+// block-wide minimum of positive doubles folded into *bits with an integer
+// atomicMin on the bit pattern (order independent, hence deterministic)
+DEV void block_min_to(double v, unsigned long long* bits) {
+    __shared__ unsigned long long sm[32];
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_down_sync(0xffffffffu, b, o);
+        b = w < b ? w : b;
+    }
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        b = (threadIdx.x < (blockDim.x >> 5)) ? sm[threadIdx.x] : 0x7ff0000000000000ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long w = __shfl_down_sync(0xffffffffu, b, o);
+            b = w < b ? w : b;
+        }
+        if (threadIdx.x == 0) atomicMin(bits, b);
+    }
+}
+
 template <class R, int P, class Ph>
 __global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, const double* __restrict__ ue,
                       const double* __restrict__ fue, const double* __restrict__ lame,
                       double* __restrict__ dte_out, double* __restrict__ ubl_out,
-                      double* __restrict__ gam_out, double* __restrict__ nu_out) {
+                      double* __restrict__ gam_out, double* __restrict__ nu_out,
+                      double* __restrict__ q_out, double* __restrict__ fl_out,
+                      unsigned long long* __restrict__ dtbits) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m.E) return;
-    int ex = e % m.nx, ey = e / m.nx;
-    int nb[4];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    double dte = __longlong_as_double(0x7ff0000000000000LL);
+    if (e < m.E) {
+        const int ex = e % m.nx, ey = e / m.nx;
+        int nb[4];
 #pragma unroll
-    for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
-    double lam[4], FL[4][NC];
-    lo_facets<Ph>(m, pr, ue, fue, e, ex, ey, nb, lam, FL);
-    double s = ((lam[0] + lam[1]) + lam[2]) + lam[3];
-    s = fmax(s, pr.lambda_floor);
-    const double h = m.h;
-    double dte = h * h / (h * s);
-    dte_out[e] = dte;
+        for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
+        double lam[4], FL[4][NC];
+        lo_facets<Ph, R>(m, pr, ue, fue, e, ex, ey, nb, lam, FL);
+        double s = ((lam[0] + lam[1]) + lam[2]) + lam[3];
+        s = fmax(s, pr.lambda_floor);
+        // dt_e = |K| / (|S| sum lambda) = h / s; dt_e / h = 1 / s
+        const double rs = 1.0 / s;
+        dte = m.h * rs;
+        dte_out[e] = dte;
+        dte_out[m.E + e] = rs;              // dt_e / h
+        dte_out[2 * m.E + e] = s * m.inv_h; // 1 / dt_e
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        double os = ((FL[1][c] - FL[0][c]) + FL[3][c]) - FL[2][c];
-        ubl_out[c * m.E + e] = ue[c * m.E + e] - (dte / h) * os;
-    }
-    double gam;
-    if (pr.mode == MODE_WENO || pr.mode == MODE_WENO_L) {
-        R U[NC][N2];
-        load_block<R, P, NC>(u, m, ex, ey, U);
-        gam = (double)sensor<R, P, Ph>(m, pr, u, U, nb);
-    } else {
-        gam = (pr.mode == MODE_HO) ? 1.0 : 0.0;
-    }
-    gam_out[e] = gam;
-    nu_out[e] = lame[e] * h / (2.0 * m.p);
-}
-
-// global dt: min over elements via an order-independent integer min on the
-// bit pattern of positive doubles (deterministic)
-static __global__ void k_dt_reset(unsigned long long* bits) { *bits = 0x7ff0000000000000ull; }
-
-static __global__ void k_dt_min(int E, const double* __restrict__ dte, unsigned long long* bits) {
-    __shared__ unsigned long long sm[32];
-    unsigned long long v = 0x7ff0000000000000ull;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
-        unsigned long long b = (unsigned long long)__double_as_longlong(dte[e]);
-        v = b < v ? b : v;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long w = __shfl_down_sync(0xffffffffu, v, o);
-        v = w < v ? w : v;
-    }
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        v = (threadIdx.x < (blockDim.x >> 5)) ? sm[threadIdx.x] : 0x7ff0000000000000ull;
-        for (int o = 16; o > 0; o >>= 1) {
-            unsigned long long w = __shfl_down_sync(0xffffffffu, v, o);
-            v = w < v ? w : v;
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) fl_out[((long long)e * 4 + d) * NC + c] = FL[d][c];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            double os = ((FL[1][c] - FL[0][c]) + FL[3][c]) - FL[2][c];
+            double bl = ue[c * m.E + e] - rs * os;
+            ubl_out[c * m.E + e] = bl;
+            if (NC == 1) {
+                // admissible antidiffusive capacities of eq. (fAlim):
+                // (|K|/|dK|)(umax - ubar^{e,L})/dt_e = (s/4)(umax - ubar^{e,L}) >= 0, and
+                // (s/4)(umin - ubar^{e,L}) <= 0
+                q_out[e] = fmax(0.0, (0.25 * s) * (pr.umax - bl));
+                q_out[m.E + e] = fmin(0.0, (0.25 * s) * (pr.umin - bl));
+            }
         }
-        if (threadIdx.x == 0) atomicMin(bits, v);
+        double gam;
+        if (pr.mode == MODE_WENO || pr.mode == MODE_WENO_L) {
+            R U[NC][N2];
+            load_block<R, P, NC>(u, m, ex, ey, U);
+            gam = (double)sensor<R, P, Ph>(m, pr, u, U, nb);
+        } else {
+            gam = (pr.mode == MODE_HO) ? 1.0 : 0.0;
+        }
+        gam_out[e] = gam;
+        nu_out[e] = lame[e] * (m.h * (0.5 / m.p));
     }
+    if (dtbits) block_min_to(dte, dtbits);
 }
 
+// global dt from the block minima folded into the bit pattern by k_pre
 // dt = min(cfl * min_e dt_e, t_end - t), never negative
-static __global__ void k_dt_final(const unsigned long long* bits, double cfl, const double* t,
+static __global__ void k_dt_final(unsigned long long* bits, double cfl, const double* t,
                                   const double* t_end, double* dt) {
     double d = cfl * __longlong_as_double((long long)*bits);
+    *bits = 0x7ff0000000000000ull;  // ready for the next reduction
     double rem = *t_end - *t;
     if (rem < d) d = rem > 0.0 ? rem : 0.0;
     *dt = d;
 }
 
 static __global__ void k_t_advance(double* t, const double* dt) { *t = *t + *dt; }
-
-// ---------------------------------------------------------------------------
-// k_grad_ev: b^e_i = (int phi_i d_x u_h, int phi_i d_y u_h), sum-factorised;
-// EV layout [(e*N2 + i)*NV + v], v = dim*NC + c, NV = 2 NC.
-// ---------------------------------------------------------------------------
-template <class R, int P, class Ph>
-__global__ void k_grad_ev(MeshDev m, const R* __restrict__ u, R* __restrict__ EV) {
-    constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2, NV = 2 * NC;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m.E) return;
-    int ex = e % m.nx, ey = e / m.nx;
-    const Tab<R>& T = TabSel<R>::t(P);
-    const R h = R(m.h);
-    R U[NC][N2];
-    load_block<R, P, NC>(u, m, ex, ey, U);
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        // x: bx[b][a] = h sum_d M[b][d] sum_c' C[c'][a] U[d][c']
-        R Y[N1][N1], Z[N1][N1];
-#pragma unroll
-        for (int d = 0; d < N1; ++d)
-#pragma unroll
-            for (int a = 0; a < N1; ++a) {
-                R sx = R(0), sy = R(0);
-#pragma unroll
-                for (int k = 0; k < N1; ++k) {
-                    sx += T.C[k][a] * U[c][d * N1 + k];
-                    sy += T.M[a][k] * U[c][d * N1 + k];
-                }
-                Y[d][a] = sx;
-                Z[d][a] = sy;
-            }
-#pragma unroll
-        for (int b = 0; b < N1; ++b)
-#pragma unroll
-            for (int a = 0; a < N1; ++a) {
-                R sx = R(0), sy = R(0);
-#pragma unroll
-                for (int d = 0; d < N1; ++d) {
-                    sx += T.M[b][d] * Y[d][a];
-                    sy += T.C[d][b] * Z[d][a];
-                }
-                long long base = ((long long)e * N2 + b * N1 + a) * NV;
-                EV[base + c] = h * sx;
-                EV[base + NC + c] = h * sy;
-            }
-    }
-}
 
 // k_mass_ev: (M_C x)^e_i = h^2 sum (M (x) M) x_e for NV nodal fields
 template <class R, int P, int NV>
@@ -501,6 +574,12 @@ DEV NodeCands node_cands(const MeshDev& m, int gx, int gy) {
     return nc;
 }
 
+// 1/|E_i| for |E_i| in {1, 2, 4} (exact powers of two)
+template <class R>
+DEV R inv_count(int n) {
+    return n == 4 ? R(0.25) : (n == 2 ? R(0.5) : R(1));
+}
+
 // sum over E_i of element vectors; out[v*NN + node]; if xout, also x = sum / m_i
 template <class R, int NV>
 __global__ void k_gather_init(MeshDev m, const R* __restrict__ EV, R* __restrict__ bout,
@@ -520,11 +599,11 @@ __global__ void k_gather_init(MeshDev m, const R* __restrict__ EV, R* __restrict
 #pragma unroll
             for (int v = 0; v < NV; ++v) s[v] += EV[base + v];
         }
-    const double mi = (double)(nc.nxc * nc.nyc) * (m.h * m.h / N2);
+    const R inv_mi = R(m.inv_me) * inv_count<R>(nc.nxc * nc.nyc);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         if (bout) bout[v * m.NN + node] = s[v];
-        if (xout) xout[v * m.NN + node] = s[v] / R(mi);
+        if (xout) xout[v * m.NN + node] = s[v] * inv_mi;
     }
 }
 
@@ -547,11 +626,11 @@ __global__ void k_gather_sweep(MeshDev m, const R* __restrict__ EV, const R* __r
 #pragma unroll
             for (int v = 0; v < NV; ++v) s[v] += EV[base + v];
         }
-    const double mi = (double)(nc.nxc * nc.nyc) * (m.h * m.h / N2);
+    const R inv_mi = R(m.inv_me) * inv_count<R>(nc.nxc * nc.nyc);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         long long k = v * m.NN + node;
-        x[k] = x[k] + (b[k] - s[v]) / R(mi);
+        x[k] = x[k] + (b[k] - s[v]) * inv_mi;
     }
 }
 
@@ -758,24 +837,40 @@ __global__ void k_res_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R
 
 // ---------------------------------------------------------------------------
 // k_update_ev: facet fluxes and flux limiter, ubar^e, f_i^e, beta_e and the
-// element contributions w_i^e = m_i^e [(1 - dt/dt_e) u_i + (dt/dt_e) ubar_i^e]
+// element increments of eq. (eq:SSPupdate),
+//   m_i u_i^SSP = sum_e m_i^e [(1 - theta_e) u_i + theta_e ubar_i^e]
+//   <=> u_i^SSP = u_i + sum_e (m_i^e/m_i) theta_e (ubar^e - u_i + beta_e f_i^e/m_i^e),
+// theta_e = dt/dt_e; the increment theta_e (...) is stored per (e, i).
+// Per-node arithmetic is in R (float in the mixed form, the float64 values
+// ubar^e and u^e enter as hi + lo float pairs); per-facet and per-element
+// quantities are float64.
 // ---------------------------------------------------------------------------
+template <class T>
+DEV void split(double v, T& hi, T& lo) {
+    hi = T(v);
+    lo = T(v - (double)hi);
+}
+
 template <class R, int P, class Ph>
 __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
                             const double* __restrict__ ue, const double* __restrict__ fue,
                             const double* __restrict__ dte_a, const double* __restrict__ ubl,
-                            const R* __restrict__ ER, const double* __restrict__ dtp,
-                            double* __restrict__ EW, double* __restrict__ ube_out,
-                            double* __restrict__ beta_out, unsigned long long* __restrict__ cnt) {
+                            const double* __restrict__ qcap, const double* __restrict__ fl_in,
+                            const R* __restrict__ ER,
+                            const double* __restrict__ dtp, R* __restrict__ EW,
+                            double* __restrict__ ube_out, double* __restrict__ beta_out,
+                            unsigned long long* __restrict__ cnt) {
     constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m.E) return;
     int ex = e % m.nx, ey = e / m.nx;
     const Tab<R>& T = TabSel<R>::t(P);
     const double h = m.h;
-    const double me = h * h / N2;
+    const double me = m.me;
     const double dt = *dtp;
     const double dte = dte_a[e];
+    const double rs = dte_a[m.E + e];       // dt_e / h
+    const double rdte = dte_a[2 * m.E + e]; // 1 / dt_e
     int nb[4];
 #pragma unroll
     for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
@@ -787,7 +882,9 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
         uec[c] = ue[c * m.E + e];
         ublc[c] = ubl[c * m.E + e];
     }
-    // canonical high-order facet fluxes f^H (eq. (hoflux))
+    // canonical high-order facet fluxes f^H (eq. (hoflux)): face average of
+    // f(u_j).n (or of F(u_j, u_hat; n) on a FIXED boundary), summed along the
+    // face in a fixed order so both cells of a facet get the same value
     double FH[4][NC];
     const bool need_fh = !(pr.mode == MODE_LO && pr.fl == FL_LOW);
     if (need_fh) {
@@ -797,9 +894,9 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
             const int bc = (d < 2) ? m.bc_x : m.bc_y;
             const bool fixed_b = (nb[d] < 0) && (bc == BC_FIXED);
             const R sg = (d == 1 || d == 3) ? R(1) : R(-1);
-            double acc[NC];
+            R acc[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+            for (int c = 0; c < NC; ++c) acc[c] = R(0);
 #pragma unroll
             for (int k = 0; k < N1; ++k) {
                 int li = (d == 0) ? k * N1 : (d == 1) ? k * N1 + P : (d == 2) ? k : P * N1 + k;
@@ -812,17 +909,19 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
                     for (int c = 0; c < NC; ++c) ub[c] = R(pr.ubc[c]);
                     llf<Ph, R>(uk, ub, sg * cnx, sg * cny, pr, F, (R*)nullptr);
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) acc[c] += (double)F[c];
+                    for (int c = 0; c < NC; ++c) acc[c] += F[c];
                 } else {
                     R fx[NC], fy[NC];
                     Ph::template flux<R>(uk, fx, fy, pr);
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) acc[c] += (double)(fx[c] * cnx + fy[c] * cny);
+                    for (int c = 0; c < NC; ++c) acc[c] += fx[c] * cnx + fy[c] * cny;
                 }
             }
 #pragma unroll
-            for (int c = 0; c < NC; ++c)
-                FH[d][c] = fixed_b ? (double)sg * (acc[c] / N1) : acc[c] / N1;
+            for (int c = 0; c < NC; ++c) {
+                double a = (double)(acc[c] / R(N1));
+                FH[d][c] = fixed_b ? (double)sg * a : a;
+            }
         }
     }
     // limited cell average ubar^e
@@ -834,11 +933,14 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             double os = ((FH[1][c] - FH[0][c]) + FH[3][c]) - FH[2][c];
-            ubec[c] = uec[c] - (dte / h) * os;
+            ubec[c] = uec[c] - rs * os;
         }
     } else {
-        double lam[4], FL[4][NC];
-        lo_facets<Ph>(m, pr, ue, fue, e, ex, ey, nb, lam, FL);
+        double FL[4][NC];
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) FL[d][c] = fl_in[((long long)e * 4 + d) * NC + c];
         double FB[4][NC];
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
@@ -846,25 +948,18 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
             double fA[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) fA[c] = FL[d][c] - FH[d][c];
-            // L and R cells of the canonical facet (-1: outside the domain)
             const int Lc = self_is_L ? e : nb[d];
             const int Rc = self_is_L ? nb[d] : e;
             if (Ph::NC == 1) {
                 const double inf = __longlong_as_double(0x7ff0000000000000LL);
                 double fmaxv = inf, fminv = -inf;
                 if (Lc >= 0) {
-                    double dl = dte_a[Lc], bl = ubl[Lc];
-                    double Qp = fmax(0.0, (h / 4.0) * (pr.umax - bl) / dl);
-                    double Qm = fmin(0.0, (h / 4.0) * (pr.umin - bl) / dl);
-                    fmaxv = fmin(fmaxv, Qp);
-                    fminv = fmax(fminv, Qm);
+                    fmaxv = fmin(fmaxv, qcap[Lc]);
+                    fminv = fmax(fminv, qcap[m.E + Lc]);
                 }
                 if (Rc >= 0) {
-                    double dr = dte_a[Rc], br = ubl[Rc];
-                    double Qp = fmax(0.0, (h / 4.0) * (pr.umax - br) / dr);
-                    double Qm = fmin(0.0, (h / 4.0) * (pr.umin - br) / dr);
-                    fmaxv = fmin(fmaxv, -Qm);
-                    fminv = fmax(fminv, -Qp);
+                    fmaxv = fmin(fmaxv, -qcap[m.E + Rc]);
+                    fminv = fmax(fminv, -qcap[Rc]);
                 }
                 FB[d][0] = (fA[0] >= 0.0) ? fmin(fA[0], fmaxv) : fmax(fA[0], fminv);
             } else {
@@ -873,7 +968,7 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
                     double ub[NC];
 #pragma unroll
                     for (int c = 0; c < NC; ++c) ub[c] = ubl[c * m.E + Lc];
-                    double mL = (h / 4.0) / dte_a[Lc];
+                    double mL = (0.25 * h) * dte_a[2 * m.E + Lc];
                     alpha = fmin(alpha, euler_alpha<double>(ub, fA, mL, pr.pos_eps));
                 }
                 if (Rc >= 0) {
@@ -883,7 +978,7 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
                         ub[c] = ubl[c * m.E + Rc];
                         fm[c] = -fA[c];
                     }
-                    double mR = (h / 4.0) / dte_a[Rc];
+                    double mR = (0.25 * h) * dte_a[2 * m.E + Rc];
                     alpha = fmin(alpha, euler_alpha<double>(ub, fm, mR, pr.pos_eps));
                 }
 #pragma unroll
@@ -893,25 +988,28 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             double os = ((FB[1][c] - FB[0][c]) + FB[3][c]) - FB[2][c];
-            ubec[c] = ublc[c] + (dte / h) * os;
+            ubec[c] = ublc[c] + rs * os;
         }
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) ube_out[c * m.E + e] = ubec[c];
-    const double theta = dt / dte;
+    const double theta = dt * rdte;
     if (theta > 1.0) atomicAdd(&cnt[CNT_CFL], 1ull);
-    double beta = 0.0;
+    const R thR = R(theta);
+    R ubh[NC], ubo[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) split<R>(ubec[c], ubh[c], ubo[c]);
     if (pr.mode == MODE_LO) {
 #pragma unroll
         for (int c = 0; c < NC; ++c)
 #pragma unroll
             for (int i = 0; i < N2; ++i)
-                EW[((long long)e * N2 + i) * NC + c] =
-                    me * ((1.0 - theta) * (double)U[c][i] + theta * ubec[c]);
+                EW[((long long)e * N2 + i) * NC + c] = thR * ((ubh[c] - U[c][i]) + ubo[c]);
         beta_out[e] = 0.0;
         return;
     }
     // f_i^e, eq. (aec) with eq. (aecb) folded into the residual
+    const R meR = R(me), h2 = R(h * h), dteR = R(dte), inv_meR = R(m.inv_me);
     R F[NC][N2];
 #pragma unroll 1
     for (int c = 0; c < NC; ++c) {
@@ -932,8 +1030,9 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
                 Y[d][a] = s;
             }
         const double fhs = ((FH[1][c] - FH[0][c]) + FH[3][c]) - FH[2][c];
-        const R fh_term = R((h / N2) * fhs);
-        const R h2 = R(h * h), meR = R(me), dteR = R(dte);
+        const R fh_term = R(m.h_over_n2 * fhs);
+        R ueh, uel;
+        split<R>(uec[c], ueh, uel);
 #pragma unroll
         for (int b = 0; b < N1; ++b)
 #pragma unroll
@@ -943,25 +1042,27 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
                 for (int d = 0; d < N1; ++d) s += T.M[b][d] * Y[d][a];
                 const int i = b * N1 + a;
                 R Ri = ER[((long long)e * N2 + i) * NC + c];
-                R dev = R((double)U[c][i] - uec[c]);
+                R dev = (U[c][i] - ueh) - uel;
                 F[c][i] = meR * dev + dteR * (((Ri + fh_term) - h2 * s) + meR * UD[i]);
             }
     }
     // slope limiter beta_e
+    R beta = R(1);
     if (pr.mode == MODE_WENO_L) {
         if (Ph::NC == 1) {
-            double b = 1.0;
-            const double gp = me * (pr.umax - ubec[0]);
-            const double gm = me * (pr.umin - ubec[0]);
+            // bound gaps in float64 per element, ratios per node in R
+            const R gp = R(me * (pr.umax - ubec[0]));
+            const R gm = R(me * (pr.umin - ubec[0]));
+            R b = R(1);
 #pragma unroll
             for (int i = 0; i < N2; ++i) {
                 R f = F[0][i];
                 R bi = R(1);
-                if (f > R(0)) bi = fmin(R(1), R(gp) / f);
-                else if (f < R(0)) bi = fmin(R(1), R(gm) / f);
-                b = fmin(b, (double)bi);
+                if (f > R(0)) bi = fmin(R(1), gp / f);
+                else if (f < R(0)) bi = fmin(R(1), gm / f);
+                b = fmin(b, bi);
             }
-            beta = fmin(fmax(b, 0.0), 1.0);
+            beta = fmin(fmax(b, R(0)), R(1));
         } else {
             double b = 1.0;
 #pragma unroll
@@ -971,39 +1072,36 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
                 for (int c = 0; c < NC; ++c) f[c] = (double)F[c][i];
                 b = fmin(b, euler_alpha<double>(ubec, f, me, pr.pos_eps));
             }
-            beta = b;
+            beta = R(b);
         }
-    } else {
-        beta = 1.0;
     }
-    beta_out[e] = beta;
+    beta_out[e] = (double)beta;
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int i = 0; i < N2; ++i) {
-            double ubi = ubec[c] + (beta * (double)F[c][i]) / me;
+        for (int i = 0; i < N2; ++i)
             EW[((long long)e * N2 + i) * NC + c] =
-                me * ((1.0 - theta) * (double)U[c][i] + theta * ubi);
-        }
+                thR * (((ubh[c] - U[c][i]) + ubo[c]) + (beta * F[c][i]) * inv_meR);
 }
 
 // ---------------------------------------------------------------------------
-// k_final: u_i^SSP = sum_{e in E_i} w_i^e / m_i, RK combination a u^n + b u^SSP,
-// invariant-domain check and clamp (scalar IDP modes) / positivity count
-// (Euler), non-finite count; stores in the state precision.
+// k_final: u_i^SSP = u_i + (sum_{e in E_i} increment_i^e) / |E_i| (m_i^e/m_i
+// = 1/|E_i| on a uniform mesh), SSP-RK combination a u^n + b u^SSP, the
+// invariant-domain check and clamp (scalar IDP modes, bounds rounded inward
+// to the storage precision) or the positivity count (Euler), non-finite count.
 // ---------------------------------------------------------------------------
 template <class R, int NC>
-__global__ void k_final(MeshDev m, ProbDev pr, const double* __restrict__ EW,
-                        const R* __restrict__ un, R* __restrict__ u, double a, double b,
+__global__ void k_final(MeshDev m, ProbDev pr, const R* __restrict__ EW,
+                        const R* __restrict__ un, R* __restrict__ u, R a, R b,
                         unsigned long long* __restrict__ cnt) {
     long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= m.NN) return;
     int gx = (int)(node % m.nnx), gy = (int)(node / m.nnx);
     NodeCands nc = node_cands(m, gx, gy);
     const int N1 = m.p + 1, N2 = N1 * N1;
-    double s[NC];
+    R s[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) s[c] = 0.0;
+    for (int c = 0; c < NC; ++c) s[c] = R(0);
     for (int j = 0; j < nc.nyc; ++j)
         for (int i = 0; i < nc.nxc; ++i) {
             long long e = (long long)nc.ey[j] * m.nx + nc.ex[i];
@@ -1011,20 +1109,22 @@ __global__ void k_final(MeshDev m, ProbDev pr, const double* __restrict__ EW,
 #pragma unroll
             for (int c = 0; c < NC; ++c) s[c] += EW[base + c];
         }
-    const double mi = (double)(nc.nxc * nc.nyc) * (m.h * m.h / N2);
-    double out[NC];
+    const R inv_cnt = inv_count<R>(nc.nxc * nc.nyc);
+    R out[NC];
+    bool bad = false;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        double ufe = s[c] / mi;
-        out[c] = (a != 0.0) ? a * (double)un[c * m.NN + node] + b * ufe : b * ufe;
-        if (!isfinite(out[c])) atomicAdd(&cnt[CNT_NONFINITE], 1ull);
+        R ufe = u[c * m.NN + node] + s[c] * inv_cnt;
+        out[c] = (a != R(0)) ? a * un[c * m.NN + node] + b * ufe : b * ufe;
+        bad |= !isfinite(out[c]);
     }
+    if (bad) atomicAdd(&cnt[CNT_NONFINITE], 1ull);
     if (NC == 1) {
         if (pr.mode == MODE_LO || pr.mode == MODE_WENO_L) {
-            const double lo = (sizeof(R) == 4) ? pr.umin32 : pr.umin;
-            const double hi = (sizeof(R) == 4) ? pr.umax32 : pr.umax;
-            double v = out[0];
-            if (v < pr.umin - pr.viol_tol || v > pr.umax + pr.viol_tol)
+            const R lo = (sizeof(R) == 4) ? R(pr.umin32) : R(pr.umin);
+            const R hi = (sizeof(R) == 4) ? R(pr.umax32) : R(pr.umax);
+            const R v = out[0];
+            if (v < R(pr.umin - pr.viol_tol) || v > R(pr.umax + pr.viol_tol))
                 atomicAdd(&cnt[CNT_VIOL], 1ull);
             if (v < lo || v > hi) {
                 atomicAdd(&cnt[CNT_CLAMP], 1ull);
@@ -1032,17 +1132,14 @@ __global__ void k_final(MeshDev m, ProbDev pr, const double* __restrict__ EW,
             }
         }
     } else {
-        R uu[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) uu[c] = R(out[c]);
         double dd[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) dd[c] = (double)uu[c];
+        for (int c = 0; c < NC; ++c) dd[c] = (double)out[c];
         double pres = PhysEuler::pressure<double>(dd, pr.gam);
         if (!(dd[0] > 0.0) || !(pres > 0.0)) atomicAdd(&cnt[CNT_VIOL], 1ull);
     }
 #pragma unroll
-    for (int c = 0; c < NC; ++c) u[c * m.NN + node] = R(out[c]);
+    for (int c = 0; c < NC; ++c) u[c * m.NN + node] = out[c];
 }
 
 }  // namespace cgl

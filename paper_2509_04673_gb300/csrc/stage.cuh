@@ -16,7 +16,9 @@ struct Bufs {
     void* ud;     // udot             [NC][NN]  (R)
     void* EV;     // element vectors  [E][N2][2NC] (R)
     void* ER;     // element residual [E][N2][NC]  (R)
-    double* EW;   // SSP contributions [E][N2][NC]
+    void* EW;     // SSP increments   [E][N2][NC]  (R)
+    double* q;    // flux-limiter capacities [2][E] (scalar)
+    double* fl;   // low-order facet fluxes [E][4][NC]
     double *ue, *fue, *lame, *dte, *ubl, *gam, *nu, *ube, *beta;
     unsigned long long* cnt;     // CNT_N counters
     unsigned long long* dtbits;  // min dt_e as bits
@@ -69,20 +71,19 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
     const int BE = 128, BN = 256;
     const unsigned ge = nblk(m.E, BE), gn = nblk(m.NN, BN);
     R* u = (R*)B.u;
-    CGL_LAUNCH(prof, KID_AVG, st, (k_avg<R, P, Ph><<<ge, BE, 0, st>>>(m, pr, u, B.ue, B.fue, B.lame)));
+    R* EV = (R*)B.EV;
+    const bool need_g = !dt_only && pr.mode != MODE_LO;
+    CGL_LAUNCH(prof, KID_AVG, st,
+               (k_avg<R, P, Ph><<<ge, BE, 0, st>>>(m, pr, u, B.ue, B.fue, B.lame, need_g ? EV : nullptr)));
     CGL_LAUNCH(prof, KID_PRE, st,
-               (k_pre<R, P, Ph><<<ge, BE, 0, st>>>(m, pr, u, B.ue, B.fue, B.lame, B.dte, B.ubl, B.gam, B.nu)));
-    if (first) {
-        CGL_LAUNCH(prof, KID_DT, st, (k_dt_reset<<<1, 1, 0, st>>>(B.dtbits)));
-        CGL_LAUNCH(prof, KID_DT, st, (k_dt_min<<<nblk(m.E, 256), 256, 0, st>>>(m.E, B.dte, B.dtbits)));
+               (k_pre<R, P, Ph><<<ge, BE, 0, st>>>(m, pr, u, B.ue, B.fue, B.lame, B.dte, B.ubl, B.gam, B.nu,
+                                                  B.q, B.fl, first ? B.dtbits : nullptr)));
+    if (first)
         CGL_LAUNCH(prof, KID_DT, st, (k_dt_final<<<1, 1, 0, st>>>(B.dtbits, pr.cfl, B.t, B.t_end, B.dt)));
-    }
     if (dt_only) return cudaGetLastError();
     if (pr.mode != MODE_LO) {
         R* g = (R*)B.g;
         R* bg = (R*)B.bg;
-        R* EV = (R*)B.EV;
-        CGL_LAUNCH(prof, KID_GRAD, st, (k_grad_ev<R, P, Ph><<<ge, BE, 0, st>>>(m, u, EV)));
         CGL_LAUNCH(prof, KID_GATHER, st, (k_gather_init<R, 2 * NC><<<gn, BN, 0, st>>>(m, EV, bg, g)));
         for (int k = 0; k < pr.k_g; ++k) {
             CGL_LAUNCH(prof, KID_MASS, st, (k_mass_ev<R, P, 2 * NC><<<ge, BE, 0, st>>>(m, g, EV)));
@@ -100,9 +101,10 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
     }
     CGL_LAUNCH(prof, KID_UPDATE, st,
                (k_update_ev<R, P, Ph><<<ge, BE, 0, st>>>(m, pr, u, (const R*)B.ud, B.ue, B.fue, B.dte, B.ubl,
-                                                        (const R*)B.ER, B.dt, B.EW, B.ube, B.beta, B.cnt)));
+                                                        B.q, B.fl, (const R*)B.ER, B.dt, (R*)B.EW, B.ube, B.beta,
+                                                        B.cnt)));
     CGL_LAUNCH(prof, KID_FINAL, st,
-               (k_final<R, NC><<<gn, BN, 0, st>>>(m, pr, B.EW, (const R*)B.un, u, a, b, B.cnt)));
+               (k_final<R, NC><<<gn, BN, 0, st>>>(m, pr, (const R*)B.EW, (const R*)B.un, u, R(a), R(b), B.cnt)));
     return cudaGetLastError();
 }
 
