@@ -160,21 +160,26 @@ class ClockSampler:
 # and outputs; element vectors are (p+1)^2 values per element)
 # --------------------------------------------------------------------------
 def algorithmic_bytes(kernel, mesh, nc, rsz, k_g, k_u):
+    """Minimum bytes one launch must move: its inputs read once and its
+    outputs written once (element vectors hold (p+1)^2 values per element)."""
     NN = mesh.nnx * mesh.nny
     E = mesh.nx * mesh.ny
     N2 = (mesh.p + 1) ** 2
     d = 8
     b = {
-        "k_avg": nc * NN * rsz + (3 * nc + 1) * E * d,
-        "k_pre": nc * NN * rsz + (3 * nc + 1) * E * d + (nc + 3) * E * d,
-        "k_grad_ev": nc * NN * rsz + E * N2 * 2 * nc * rsz,
+        # u (own and neighbour blocks read once) -> u^e, dt_e (3), ubar^{e,L},
+        # gamma, nu, Q (2), f^L (4 nc), gradient element vectors
+        "k_pre": nc * NN * rsz + (nc + 3 + nc + 2 + 2 + 4 * nc) * E * d + E * N2 * 2 * nc * rsz,
+        # u, g (2 nc), gamma, nu -> element residual
         "k_res_ev": 3 * nc * NN * rsz + 2 * E * d + E * N2 * nc * rsz,
-        "k_update_ev": 2 * nc * NN * rsz + (5 * nc + 1) * E * d + E * N2 * nc * rsz
-                       + E * N2 * nc * d + (nc + 1) * E * d,
-        "k_final": E * N2 * nc * d + 2 * nc * NN * rsz,
+        # u, udot, u^e, dt_e (3), ubar^{e,L}, Q (2), f^L (4 nc), element residual
+        # -> increments, ubar^e, beta
+        "k_update_ev": 2 * nc * NN * rsz + (nc + 3 + nc + 2 + 4 * nc) * E * d + E * N2 * nc * rsz
+                       + E * N2 * nc * rsz + (nc + 1) * E * d,
+        # increments, u^n, u -> u
+        "k_final": E * N2 * nc * rsz + 3 * nc * NN * rsz,
     }
-    # gathers / sweeps / mass products average over their two field widths
-    nv_avg = (2 * nc * (1 + k_g) + nc * (1 + k_u)) / max(1, (1 + k_g) + (1 + k_u))
+    nv_avg = (2 * nc + nc) / 2
     b["k_gather_init"] = E * N2 * nv_avg * rsz + 2 * nv_avg * NN * rsz
     nvm = (2 * nc * k_g + nc * k_u) / max(1, k_g + k_u)
     b["k_mass_ev"] = nvm * NN * rsz + E * N2 * nvm * rsz

@@ -2,12 +2,12 @@
 // convex-limited CG-WENO scheme (Kuzmin, Hajduk, Vedral, arXiv 2509.04673),
 // following the order of the algorithm summary in Sec. 4.3:
 //
-//   k_avg        cell averages u^e (eq. (ueold)), f(u^e), lambda_e
-//   k_pre        facet speeds, dt_e (eq. (dtmaxcell)), f^L, ubar^{e,L}
-//                (eq. (uelowFCT)), WENO sensor gamma_e (eqs. (WENO:alpha),
-//                (WENO:norm)), nu_e (eq. (stab:WENO))
-//   k_dt_*       global dt = omega_CFL min_e dt_e (eq. (cflglob), Sec. 5)
-//   k_grad_ev    element vectors int phi_i grad u_h for g_h
+//   k_pre        cell averages u^e of the element and its face neighbours
+//                (eq. (ueold)), facet speeds, dt_e (eq. (dtmaxcell)), f^L,
+//                ubar^{e,L} (eq. (uelowFCT)), WENO sensor gamma_e (eqs.
+//                (WENO:alpha), (WENO:norm)), nu_e (eq. (stab:WENO)), element
+//                vectors int phi_i grad u_h for g_h, block minimum of dt_e
+//   k_dt_final   global dt = omega_CFL min_e dt_e (eq. (cflglob), Sec. 5)
 //   k_res_ev     element residual: Galerkin part of eq. (weak:stab2) with
 //                boundary terms (eqs. (aec), (aecb)) and s_h (eq. (stab:WENO))
 //   k_mass_ev    consistent-mass products for the Richardson sweeps
@@ -59,6 +59,22 @@ DEV int neighbour(const MeshDev& m, int ex, int ey, int dir) {
         jy = (jy + m.ny) % m.ny;
     }
     return jy * m.nx + jx;
+}
+
+// 2D launches: elements as (x: ex, y: ey), nodes as (x: gx, y: gy); no
+// integer division by runtime sizes in the kernels
+DEV bool elem_of_thread(const MeshDev& m, int& ex, int& ey, int& e) {
+    ex = blockIdx.x * blockDim.x + threadIdx.x;
+    ey = blockIdx.y * blockDim.y + threadIdx.y;
+    e = ey * m.nx + ex;
+    return ex < m.nx && ey < m.ny;
+}
+
+DEV bool node_of_thread(const MeshDev& m, int& gx, int& gy, long long& node) {
+    gx = blockIdx.x * blockDim.x + threadIdx.x;
+    gy = blockIdx.y * blockDim.y + threadIdx.y;
+    node = (long long)gy * m.nnx + gx;
+    return gx < m.nnx && gy < m.nny;
 }
 
 template <class R, int P, int NC>
@@ -137,49 +153,6 @@ DEV void grad_vectors(const R (&U)[NC][Dim<P>::N2], R h, long long e, R* __restr
 }
 
 // ---------------------------------------------------------------------------
-// k_avg: u^e = mean of the coefficients (m_i^e = |K|/(p+1)^2), f(u^e),
-// lambda_e = max over coefficients of the speed bound, and (if EV) the
-// element vectors of the g_h projection right-hand side.
-// ---------------------------------------------------------------------------
-template <class R, int P, class Ph>
-__global__ void k_avg(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __restrict__ ue,
-                      double* __restrict__ fue, double* __restrict__ lame, R* __restrict__ EV) {
-    constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m.E) return;
-    int ex = e % m.nx, ey = e / m.nx;
-    R U[NC][N2];
-    load_block<R, P, NC>(u, m, ex, ey, U);
-    double avg[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        avg[c] = block_mean<N2>(U[c]);
-        ue[c * m.E + e] = avg[c];
-    }
-    // f(u^e) in the bulk precision R (float64 in the FP64 form; the mixed
-    // form evaluates transcendental fluxes in float and widens the result)
-    R avgR[NC], fx[NC], fy[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) avgR[c] = R(avg[c]);
-    Ph::template flux<R>(avgR, fx, fy, pr);
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        fue[(2 * c) * m.E + e] = (double)fx[c];
-        fue[(2 * c + 1) * m.E + e] = (double)fy[c];
-    }
-    R lm = R(0);
-#pragma unroll
-    for (int i = 0; i < N2; ++i) {
-        R ui[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) ui[c] = U[c][i];
-        lm = fmax(lm, Ph::template node_speed<R>(ui, pr));
-    }
-    lame[e] = (double)lm;
-    if (EV) grad_vectors<R, P, NC>(U, R(m.h), e, EV);
-}
-
-// ---------------------------------------------------------------------------
 // low-order facet quantities of element e on its four faces in the canonical
 // orientation (normal +x for W/E, +y for S/N): lambda and F^L = F(u^L, u^R)
 // with f^L of Sec. 4; on a non-periodic boundary the external state is
@@ -200,38 +173,24 @@ DEV double facet_speed(const double* uL, const double* uR, double nx, double ny,
     return (double)l * (1.0 + 0x1p-20);
 }
 
-template <class Ph, class R, class RS = R>
-DEV void lo_facets(const MeshDev& m, const ProbDev& pr, const double* __restrict__ ue,
-                   const double* __restrict__ fue, int e, int ex, int ey, const int (&nb)[4],
-                   double (&lam)[4], double (&FL)[4][Ph::NC]) {
+template <class Ph, class R>
+DEV void lo_facets(const MeshDev& m, const ProbDev& pr, const int (&nb)[4],
+                   const double (&us)[Ph::NC], const double (&fxs)[Ph::NC], const double (&fys)[Ph::NC],
+                   const double (&uo)[4][Ph::NC], const double (&fxo)[4][Ph::NC],
+                   const double (&fyo)[4][Ph::NC], double (&lam)[4], double (&FL)[4][Ph::NC]) {
     constexpr int NC = Ph::NC;
-    double us[NC], fxs[NC], fys[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        us[c] = ue[c * m.E + e];
-        fxs[c] = fue[(2 * c) * m.E + e];
-        fys[c] = fue[(2 * c + 1) * m.E + e];
-    }
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
         const double cnx = (d < 2) ? 1.0 : 0.0, cny = (d < 2) ? 0.0 : 1.0;
         const bool self_is_L = (d == 1 || d == 3);
         if (nb[d] >= 0) {
-            int o = nb[d];
-            double uo[NC], fxo[NC], fyo[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                uo[c] = ue[c * m.E + o];
-                fxo[c] = fue[(2 * c) * m.E + o];
-                fyo[c] = fue[(2 * c + 1) * m.E + o];
-            }
-            const double* uL = self_is_L ? us : uo;
-            const double* uR = self_is_L ? uo : us;
-            const double* fxL = self_is_L ? fxs : fxo;
-            const double* fyL = self_is_L ? fys : fyo;
-            const double* fxR = self_is_L ? fxo : fxs;
-            const double* fyR = self_is_L ? fyo : fys;
-            double l = facet_speed<Ph, RS>(uL, uR, cnx, cny, pr);
+            const double* uL = self_is_L ? us : uo[d];
+            const double* uR = self_is_L ? uo[d] : us;
+            const double* fxL = self_is_L ? fxs : fxo[d];
+            const double* fyL = self_is_L ? fys : fyo[d];
+            const double* fxR = self_is_L ? fxo[d] : fxs;
+            const double* fyR = self_is_L ? fyo[d] : fys;
+            double l = facet_speed<Ph, R>(uL, uR, cnx, cny, pr);
             lam[d] = l;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
@@ -265,7 +224,7 @@ DEV void lo_facets(const MeshDev& m, const ProbDev& pr, const double* __restrict
                 }
             }
             const double nx = sg * cnx, ny = sg * cny;
-            double l = facet_speed<Ph, RS>(us, ux, nx, ny, pr);
+            double l = facet_speed<Ph, R>(us, ux, nx, ny, pr);
             lam[d] = l;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
@@ -275,6 +234,28 @@ DEV void lo_facets(const MeshDev& m, const ProbDev& pr, const double* __restrict
                 FL[d][c] = sg * F;
             }
         }
+    }
+}
+
+// cell average u^e (float64) and f(u^e) (evaluated in the bulk precision R,
+// widened) of the block of element (jx, jy)
+template <class R, int P, class Ph>
+DEV void cell_state(const R* __restrict__ u, const MeshDev& m, const ProbDev& pr, int jx, int jy,
+                    double (&avg)[Ph::NC], double (&fx)[Ph::NC], double (&fy)[Ph::NC]) {
+    constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
+    R U[NC][N2];
+    load_block<R, P, NC>(u, m, jx, jy, U);
+    R aR[NC], fxR[NC], fyR[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        avg[c] = block_mean<N2>(U[c]);
+        aR[c] = R(avg[c]);
+    }
+    Ph::template flux<R>(aR, fxR, fyR, pr);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        fx[c] = (double)fxR[c];
+        fy[c] = (double)fyR[c];
     }
 }
 
@@ -404,42 +385,79 @@ DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
 // atomicMin on the bit pattern (order independent, hence deterministic)
 DEV void block_min_to(double v, unsigned long long* bits) {
     __shared__ unsigned long long sm[32];
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nt = blockDim.x * blockDim.y;
     unsigned long long b = (unsigned long long)__double_as_longlong(v);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         unsigned long long w = __shfl_down_sync(0xffffffffu, b, o);
         b = w < b ? w : b;
     }
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = b;
+    if ((t & 31) == 0) sm[t >> 5] = b;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        b = (threadIdx.x < (blockDim.x >> 5)) ? sm[threadIdx.x] : 0x7ff0000000000000ull;
+    if (t < 32) {
+        b = (t < (nt >> 5)) ? sm[t] : 0x7ff0000000000000ull;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             unsigned long long w = __shfl_down_sync(0xffffffffu, b, o);
             b = w < b ? w : b;
         }
-        if (threadIdx.x == 0) atomicMin(bits, b);
+        if (t == 0) atomicMin(bits, b);
     }
 }
 
+// ---------------------------------------------------------------------------
+// k_pre: per element u^e and the face neighbours' u^{e'} (from their blocks,
+// eq. (ueold)), f(u^e), lambda_e, the facet speeds and f^L, dt_e (eq.
+// (dtmaxcell)), ubar^{e,L} (eq. (uelowFCT)), the flux-limiter capacities,
+// gamma_e (eqs. (WENO:alpha), (WENO:norm)), nu_e, the element vectors of the
+// g_h right-hand side, and (stage 1) the block minimum of dt_e.
+// ---------------------------------------------------------------------------
 template <class R, int P, class Ph>
-__global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, const double* __restrict__ ue,
-                      const double* __restrict__ fue, const double* __restrict__ lame,
+__global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __restrict__ ue_out,
                       double* __restrict__ dte_out, double* __restrict__ ubl_out,
                       double* __restrict__ gam_out, double* __restrict__ nu_out,
-                      double* __restrict__ q_out, double* __restrict__ fl_out,
+                      double* __restrict__ q_out, double* __restrict__ fl_out, R* __restrict__ EV,
                       unsigned long long* __restrict__ dtbits) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int ex, ey, e;
+    const bool valid = elem_of_thread(m, ex, ey, e);
     double dte = __longlong_as_double(0x7ff0000000000000LL);
-    if (e < m.E) {
-        const int ex = e % m.nx, ey = e / m.nx;
+    if (valid) {
         int nb[4];
 #pragma unroll
         for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
+        R U[NC][N2];
+        load_block<R, P, NC>(u, m, ex, ey, U);
+        double us[NC], fxs[NC], fys[NC];
+        {
+            R aR[NC], fxR[NC], fyR[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                us[c] = block_mean<N2>(U[c]);
+                aR[c] = R(us[c]);
+                ue_out[c * m.E + e] = us[c];
+            }
+            Ph::template flux<R>(aR, fxR, fyR, pr);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                fxs[c] = (double)fxR[c];
+                fys[c] = (double)fyR[c];
+            }
+        }
+        double uo[4][NC], fxo[4][NC], fyo[4][NC];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            if (nb[d] >= 0) {
+                const int jx = nb[d] % m.nx, jy = nb[d] / m.nx;
+                cell_state<R, P, Ph>(u, m, pr, jx, jy, uo[d], fxo[d], fyo[d]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) uo[d][c] = fxo[d][c] = fyo[d][c] = 0.0;
+            }
+        }
         double lam[4], FL[4][NC];
-        lo_facets<Ph, R>(m, pr, ue, fue, e, ex, ey, nb, lam, FL);
+        lo_facets<Ph, R>(m, pr, nb, us, fxs, fys, uo, fxo, fyo, lam, FL);
         double s = ((lam[0] + lam[1]) + lam[2]) + lam[3];
         s = fmax(s, pr.lambda_floor);
         // dt_e = |K| / (|S| sum lambda) = h / s; dt_e / h = 1 / s
@@ -455,7 +473,7 @@ __global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, const doub
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             double os = ((FL[1][c] - FL[0][c]) + FL[3][c]) - FL[2][c];
-            double bl = ue[c * m.E + e] - rs * os;
+            double bl = us[c] - rs * os;
             ubl_out[c * m.E + e] = bl;
             if (NC == 1) {
                 // admissible antidiffusive capacities of eq. (fAlim):
@@ -467,14 +485,21 @@ __global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, const doub
         }
         double gam;
         if (pr.mode == MODE_WENO || pr.mode == MODE_WENO_L) {
-            R U[NC][N2];
-            load_block<R, P, NC>(u, m, ex, ey, U);
             gam = (double)sensor<R, P, Ph>(m, pr, u, U, nb);
         } else {
             gam = (pr.mode == MODE_HO) ? 1.0 : 0.0;
         }
         gam_out[e] = gam;
-        nu_out[e] = lame[e] * (m.h * (0.5 / m.p));
+        R lm = R(0);
+#pragma unroll
+        for (int i = 0; i < N2; ++i) {
+            R ui[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ui[c] = U[c][i];
+            lm = fmax(lm, Ph::template node_speed<R>(ui, pr));
+        }
+        nu_out[e] = (double)lm * (m.h * (0.5 / m.p));
+        if (EV) grad_vectors<R, P, NC>(U, R(m.h), e, EV);
     }
     if (dtbits) block_min_to(dte, dtbits);
 }
@@ -496,9 +521,8 @@ static __global__ void k_t_advance(double* t, const double* dt) { *t = *t + *dt;
 template <class R, int P, int NV>
 __global__ void k_mass_ev(MeshDev m, const R* __restrict__ x, R* __restrict__ EV) {
     constexpr int N1 = P + 1, N2 = Dim<P>::N2;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m.E) return;
-    int ex = e % m.nx, ey = e / m.nx;
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
     const Tab<R>& T = TabSel<R>::t(P);
     const R h2 = R(m.h * m.h);
     R X[NV][N2];
@@ -531,6 +555,112 @@ __global__ void k_mass_ev(MeshDev m, const R* __restrict__ x, R* __restrict__ EV
 // node-centric gathers over E_i in a fixed order (lower neighbour first in
 // each direction): deterministic, no atomics.
 // ---------------------------------------------------------------------------
+// elements containing node (gx, gy): at most two per direction (lower one
+// first), with the node's local index in each; compile-time P
+template <int P>
+struct NodeC {
+    int ex0, ex1, a0, a1, nxc;
+    int ey0, ey1, b0, b1, nyc;
+};
+
+template <int P>
+DEV NodeC<P> node_c(const MeshDev& m, int gx, int gy) {
+    NodeC<P> c;
+    int ex = gx / P, a = gx - ex * P;
+    if (a == 0) {
+        const bool lo = (ex > 0) || m.px, hi = ex < m.nx;
+        c.ex0 = lo ? (ex == 0 ? m.nx - 1 : ex - 1) : ex;
+        c.a0 = lo ? P : 0;
+        c.ex1 = ex;
+        c.a1 = 0;
+        c.nxc = (int)lo + (int)hi;
+    } else {
+        c.ex0 = c.ex1 = ex;
+        c.a0 = c.a1 = a;
+        c.nxc = 1;
+    }
+    int ey = gy / P, b = gy - ey * P;
+    if (b == 0) {
+        const bool lo = (ey > 0) || m.py, hi = ey < m.ny;
+        c.ey0 = lo ? (ey == 0 ? m.ny - 1 : ey - 1) : ey;
+        c.b0 = lo ? P : 0;
+        c.ey1 = ey;
+        c.b1 = 0;
+        c.nyc = (int)lo + (int)hi;
+    } else {
+        c.ey0 = c.ey1 = ey;
+        c.b0 = c.b1 = b;
+        c.nyc = 1;
+    }
+    return c;
+}
+
+// 1/|E_i| for |E_i| in {1, 2, 4} (exact powers of two)
+template <class R>
+DEV R inv_count(int n) {
+    return n == 4 ? R(0.25) : (n == 2 ? R(0.5) : R(1));
+}
+
+// s[v] = sum over E_i of the element vectors at node (gx, gy), fixed order
+template <class R, int P, int NV>
+DEV void gather_at(const MeshDev& m, const R* __restrict__ EV, const NodeC<P>& c, R (&s)[NV]) {
+    constexpr int N1 = P + 1, N2 = N1 * N1;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s[v] = R(0);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        if (j < c.nyc) {
+            const int ey = j ? c.ey1 : c.ey0, b = j ? c.b1 : c.b0;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                if (i < c.nxc) {
+                    const int ex = i ? c.ex1 : c.ex0, a = i ? c.a1 : c.a0;
+                    const long long base = (((long long)ey * m.nx + ex) * N2 + b * N1 + a) * NV;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) s[v] += EV[base + v];
+                }
+            }
+        }
+    }
+}
+
+// sum over E_i of element vectors; out[v*NN + node]; if xout, also x = sum / m_i
+template <class R, int P, int NV>
+__global__ void k_gather_init(MeshDev m, const R* __restrict__ EV, R* __restrict__ bout,
+                              R* __restrict__ xout) {
+    int gx, gy;
+    long long node;
+    if (!node_of_thread(m, gx, gy, node)) return;
+    const NodeC<P> c = node_c<P>(m, gx, gy);
+    R s[NV];
+    gather_at<R, P, NV>(m, EV, c, s);
+    const R inv_mi = R(m.inv_me) * inv_count<R>(c.nxc * c.nyc);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        if (bout) bout[v * m.NN + node] = s[v];
+        if (xout) xout[v * m.NN + node] = s[v] * inv_mi;
+    }
+}
+
+// Richardson sweep x <- x + (b - sum EV) / m_i
+template <class R, int P, int NV>
+__global__ void k_gather_sweep(MeshDev m, const R* __restrict__ EV, const R* __restrict__ b,
+                               R* __restrict__ x) {
+    int gx, gy;
+    long long node;
+    if (!node_of_thread(m, gx, gy, node)) return;
+    const NodeC<P> c = node_c<P>(m, gx, gy);
+    R s[NV];
+    gather_at<R, P, NV>(m, EV, c, s);
+    const R inv_mi = R(m.inv_me) * inv_count<R>(c.nxc * c.nyc);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        long long k = v * m.NN + node;
+        x[k] = x[k] + (b[k] - s[v]) * inv_mi;
+    }
+}
+
+// runtime-degree candidate list (diagnostics only)
 struct NodeCands {
     int nxc, nyc;
     int ex[2], a[2], ey[2], b[2];
@@ -574,66 +704,6 @@ DEV NodeCands node_cands(const MeshDev& m, int gx, int gy) {
     return nc;
 }
 
-// 1/|E_i| for |E_i| in {1, 2, 4} (exact powers of two)
-template <class R>
-DEV R inv_count(int n) {
-    return n == 4 ? R(0.25) : (n == 2 ? R(0.5) : R(1));
-}
-
-// sum over E_i of element vectors; out[v*NN + node]; if xout, also x = sum / m_i
-template <class R, int NV>
-__global__ void k_gather_init(MeshDev m, const R* __restrict__ EV, R* __restrict__ bout,
-                              R* __restrict__ xout) {
-    long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (node >= m.NN) return;
-    int gx = (int)(node % m.nnx), gy = (int)(node / m.nnx);
-    NodeCands nc = node_cands(m, gx, gy);
-    const int N1 = m.p + 1, N2 = N1 * N1;
-    R s[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) s[v] = R(0);
-    for (int j = 0; j < nc.nyc; ++j)
-        for (int i = 0; i < nc.nxc; ++i) {
-            long long e = (long long)nc.ey[j] * m.nx + nc.ex[i];
-            long long base = (e * N2 + nc.b[j] * N1 + nc.a[i]) * NV;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) s[v] += EV[base + v];
-        }
-    const R inv_mi = R(m.inv_me) * inv_count<R>(nc.nxc * nc.nyc);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        if (bout) bout[v * m.NN + node] = s[v];
-        if (xout) xout[v * m.NN + node] = s[v] * inv_mi;
-    }
-}
-
-// Richardson sweep x <- x + (b - sum EV) / m_i
-template <class R, int NV>
-__global__ void k_gather_sweep(MeshDev m, const R* __restrict__ EV, const R* __restrict__ b,
-                               R* __restrict__ x) {
-    long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (node >= m.NN) return;
-    int gx = (int)(node % m.nnx), gy = (int)(node / m.nnx);
-    NodeCands nc = node_cands(m, gx, gy);
-    const int N1 = m.p + 1, N2 = N1 * N1;
-    R s[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) s[v] = R(0);
-    for (int j = 0; j < nc.nyc; ++j)
-        for (int i = 0; i < nc.nxc; ++i) {
-            long long e = (long long)nc.ey[j] * m.nx + nc.ex[i];
-            long long base = (e * N2 + nc.b[j] * N1 + nc.a[i]) * NV;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) s[v] += EV[base + v];
-        }
-    const R inv_mi = R(m.inv_me) * inv_count<R>(nc.nxc * nc.nyc);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        long long k = v * m.NN + node;
-        x[k] = x[k] + (b[k] - s[v]) * inv_mi;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // k_res_ev: R^e_i = W^e_i - s^e_i with
 //   W^e_i = int grad phi_i . f(u_h) - sum_{interior faces} int phi_i f_h.n
@@ -647,9 +717,8 @@ __global__ void k_res_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R
                          const double* __restrict__ gam, const double* __restrict__ nu,
                          R* __restrict__ ER) {
     constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2, NQ = Dim<P>::NQ;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m.E) return;
-    int ex = e % m.nx, ey = e / m.nx;
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
     const Tab<R>& T = TabSel<R>::t(P);
     const R h = R(m.h);
     R U[NC][N2];
@@ -853,17 +922,15 @@ DEV void split(double v, T& hi, T& lo) {
 
 template <class R, int P, class Ph>
 __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
-                            const double* __restrict__ ue, const double* __restrict__ fue,
-                            const double* __restrict__ dte_a, const double* __restrict__ ubl,
+                            const double* __restrict__ ue, const double* __restrict__ dte_a, const double* __restrict__ ubl,
                             const double* __restrict__ qcap, const double* __restrict__ fl_in,
                             const R* __restrict__ ER,
                             const double* __restrict__ dtp, R* __restrict__ EW,
                             double* __restrict__ ube_out, double* __restrict__ beta_out,
                             unsigned long long* __restrict__ cnt) {
     constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m.E) return;
-    int ex = e % m.nx, ey = e / m.nx;
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
     const Tab<R>& T = TabSel<R>::t(P);
     const double h = m.h;
     const double me = m.me;
@@ -1090,25 +1157,16 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
 // invariant-domain check and clamp (scalar IDP modes, bounds rounded inward
 // to the storage precision) or the positivity count (Euler), non-finite count.
 // ---------------------------------------------------------------------------
-template <class R, int NC>
+template <class R, int P, int NC>
 __global__ void k_final(MeshDev m, ProbDev pr, const R* __restrict__ EW,
                         const R* __restrict__ un, R* __restrict__ u, R a, R b,
                         unsigned long long* __restrict__ cnt) {
-    long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (node >= m.NN) return;
-    int gx = (int)(node % m.nnx), gy = (int)(node / m.nnx);
-    NodeCands nc = node_cands(m, gx, gy);
-    const int N1 = m.p + 1, N2 = N1 * N1;
+    int gx, gy;
+    long long node;
+    if (!node_of_thread(m, gx, gy, node)) return;
+    const NodeC<P> nc = node_c<P>(m, gx, gy);
     R s[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) s[c] = R(0);
-    for (int j = 0; j < nc.nyc; ++j)
-        for (int i = 0; i < nc.nxc; ++i) {
-            long long e = (long long)nc.ey[j] * m.nx + nc.ex[i];
-            long long base = (e * N2 + nc.b[j] * N1 + nc.a[i]) * NC;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) s[c] += EW[base + c];
-        }
+    gather_at<R, P, NC>(m, EW, nc, s);
     const R inv_cnt = inv_count<R>(nc.nxc * nc.nyc);
     R out[NC];
     bool bad = false;

@@ -68,43 +68,42 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
     ProbDev pr = pr_in;
     if (dt_only) pr.mode = MODE_HO;  // no sensor needed for dt_e
     constexpr int NC = Ph::NC;
-    const int BE = 128, BN = 256;
-    const unsigned ge = nblk(m.E, BE), gn = nblk(m.NN, BN);
+    const dim3 be(64, 2), bn(128, 1);
+    const dim3 ge(nblk(m.nx, 64), nblk(m.ny, 2)), gn(nblk(m.nnx, 128), m.nny);
     R* u = (R*)B.u;
     R* EV = (R*)B.EV;
     const bool need_g = !dt_only && pr.mode != MODE_LO;
-    CGL_LAUNCH(prof, KID_AVG, st,
-               (k_avg<R, P, Ph><<<ge, BE, 0, st>>>(m, pr, u, B.ue, B.fue, B.lame, need_g ? EV : nullptr)));
     CGL_LAUNCH(prof, KID_PRE, st,
-               (k_pre<R, P, Ph><<<ge, BE, 0, st>>>(m, pr, u, B.ue, B.fue, B.lame, B.dte, B.ubl, B.gam, B.nu,
-                                                  B.q, B.fl, first ? B.dtbits : nullptr)));
+               (k_pre<R, P, Ph><<<ge, be, 0, st>>>(m, pr, u, B.ue, B.dte, B.ubl, B.gam, B.nu, B.q, B.fl,
+                                                  need_g ? EV : nullptr, first ? B.dtbits : nullptr)));
     if (first)
         CGL_LAUNCH(prof, KID_DT, st, (k_dt_final<<<1, 1, 0, st>>>(B.dtbits, pr.cfl, B.t, B.t_end, B.dt)));
     if (dt_only) return cudaGetLastError();
     if (pr.mode != MODE_LO) {
         R* g = (R*)B.g;
         R* bg = (R*)B.bg;
-        CGL_LAUNCH(prof, KID_GATHER, st, (k_gather_init<R, 2 * NC><<<gn, BN, 0, st>>>(m, EV, bg, g)));
+        CGL_LAUNCH(prof, KID_GATHER, st, (k_gather_init<R, P, 2 * NC><<<gn, bn, 0, st>>>(m, EV, bg, g)));
         for (int k = 0; k < pr.k_g; ++k) {
-            CGL_LAUNCH(prof, KID_MASS, st, (k_mass_ev<R, P, 2 * NC><<<ge, BE, 0, st>>>(m, g, EV)));
-            CGL_LAUNCH(prof, KID_SWEEP, st, (k_gather_sweep<R, 2 * NC><<<gn, BN, 0, st>>>(m, EV, bg, g)));
+            CGL_LAUNCH(prof, KID_MASS, st, (k_mass_ev<R, P, 2 * NC><<<ge, be, 0, st>>>(m, g, EV)));
+            CGL_LAUNCH(prof, KID_SWEEP, st, (k_gather_sweep<R, P, 2 * NC><<<gn, bn, 0, st>>>(m, EV, bg, g)));
         }
         R* ER = (R*)B.ER;
         R* r = (R*)B.r;
         R* ud = (R*)B.ud;
-        CGL_LAUNCH(prof, KID_RES, st, (k_res_ev<R, P, Ph><<<ge, BE, 0, st>>>(m, pr, u, g, B.gam, B.nu, ER)));
-        CGL_LAUNCH(prof, KID_GATHER, st, (k_gather_init<R, NC><<<gn, BN, 0, st>>>(m, ER, r, ud)));
+        CGL_LAUNCH(prof, KID_RES, st, (k_res_ev<R, P, Ph><<<ge, be, 0, st>>>(m, pr, u, g, B.gam, B.nu, ER)));
+        CGL_LAUNCH(prof, KID_GATHER, st, (k_gather_init<R, P, NC><<<gn, bn, 0, st>>>(m, ER, r, ud)));
         for (int k = 0; k < pr.k_u; ++k) {
-            CGL_LAUNCH(prof, KID_MASS, st, (k_mass_ev<R, P, NC><<<ge, BE, 0, st>>>(m, ud, EV)));
-            CGL_LAUNCH(prof, KID_SWEEP, st, (k_gather_sweep<R, NC><<<gn, BN, 0, st>>>(m, EV, r, ud)));
+            CGL_LAUNCH(prof, KID_MASS, st, (k_mass_ev<R, P, NC><<<ge, be, 0, st>>>(m, ud, EV)));
+            CGL_LAUNCH(prof, KID_SWEEP, st, (k_gather_sweep<R, P, NC><<<gn, bn, 0, st>>>(m, EV, r, ud)));
         }
     }
     CGL_LAUNCH(prof, KID_UPDATE, st,
-               (k_update_ev<R, P, Ph><<<ge, BE, 0, st>>>(m, pr, u, (const R*)B.ud, B.ue, B.fue, B.dte, B.ubl,
-                                                        B.q, B.fl, (const R*)B.ER, B.dt, (R*)B.EW, B.ube, B.beta,
+               (k_update_ev<R, P, Ph><<<ge, be, 0, st>>>(m, pr, u, (const R*)B.ud, B.ue, B.dte, B.ubl, B.q, B.fl,
+                                                        (const R*)B.ER, B.dt, (R*)B.EW, B.ube, B.beta,
                                                         B.cnt)));
     CGL_LAUNCH(prof, KID_FINAL, st,
-               (k_final<R, NC><<<gn, BN, 0, st>>>(m, pr, (const R*)B.EW, (const R*)B.un, u, R(a), R(b), B.cnt)));
+               (k_final<R, P, NC><<<gn, bn, 0, st>>>(m, pr, (const R*)B.EW, (const R*)B.un, u, R(a), R(b),
+                                                    B.cnt)));
     return cudaGetLastError();
 }
 
