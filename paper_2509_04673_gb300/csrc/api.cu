@@ -293,6 +293,10 @@ extern "C" cgl_status cgl_mesh_create(const cgl_mesh_desc* d, cgl_mesh** out) {
     m.inv_h = 1.0 / hx;
     m.inv_n2 = 1.0 / n2;
     m.inv_n1 = 1.0 / (d->p + 1);
+    m.h_f = (float)m.h;
+    m.me_f = (float)m.me;
+    m.inv_me_f = (float)m.inv_me;
+    m.h2_f = (float)(m.h * m.h);
     *out = M;
     return CGL_OK;
 }
@@ -528,6 +532,20 @@ extern "C" cgl_status cgl_set_problem(cgl_state* S, const cgl_problem* p) {
     for (int c = 0; c < 4; ++c) d.ubc[c] = p->ubc[c];
     double sc = std::fmax(1.0, std::fmax(std::fabs(p->umin), std::fabs(p->umax)));
     d.viol_tol = (S->prec == CGL_FP64 ? 1e-12 : 1e-6) * sc;
+    d.lo_tol = d.umin - d.viol_tol;
+    d.hi_tol = d.umax + d.viol_tol;
+    d.vx_f = (float)d.vx;
+    d.vy_f = (float)d.vy;
+    d.gam_f = (float)d.gam;
+    d.w_lin_f = (float)d.w_lin;
+    d.weno_eps_f = (float)d.weno_eps;
+    d.gamma_eps_f = (float)d.gamma_eps;
+    d.q_f = (float)d.q;
+    for (int c = 0; c < 4; ++c) d.ubc_f[c] = (float)d.ubc[c];
+    d.lo32_f = (float)d.umin32;
+    d.hi32_f = (float)d.umax32;
+    d.lo_tol_f = (float)d.lo_tol;
+    d.hi_tol_f = (float)d.hi_tol;
     S->stage = fn;
     S->has_problem = true;
     if (S->step_graph) {

@@ -31,6 +31,7 @@ struct MeshDev {
     // kernel divides by mesh constants): m_i^e = h^2/(p+1)^2, 1/m_i^e,
     // h/(p+1)^2, 1/h, 1/(p+1)^2, 1/(p+1)
     double me, inv_me, h_over_n2, inv_h, inv_n2, inv_n1;
+    float h_f, me_f, inv_me_f, h2_f;
 };
 
 struct ProbDev {
@@ -39,6 +40,52 @@ struct ProbDev {
     double q, r, weno_eps, w_lin, gamma_eps, cfl, lambda_floor;
     double ubc[4];
     double viol_tol;       // rounding tolerance of the bound check
+    double lo_tol, hi_tol; // umin - viol_tol, umax + viol_tol
+    // float copies for float kernels (a float64 -> float conversion runs on
+    // GB300's narrow float64 pipe, so per-thread code never converts)
+    float vx_f, vy_f, gam_f, w_lin_f, weno_eps_f, gamma_eps_f, q_f;
+    float ubc_f[4];
+    float lo32_f, hi32_f, lo_tol_f, hi_tol_f;
+};
+
+// typed views of the problem and mesh constants: float kernels read the
+// float copies, float64 kernels the originals
+template <class T> struct PV;
+template <> struct PV<double> {
+    static DEV double vx(const ProbDev& p) { return p.vx; }
+    static DEV double vy(const ProbDev& p) { return p.vy; }
+    static DEV double gam(const ProbDev& p) { return p.gam; }
+    static DEV double w_lin(const ProbDev& p) { return p.w_lin; }
+    static DEV double weno_eps(const ProbDev& p) { return p.weno_eps; }
+    static DEV double gamma_eps(const ProbDev& p) { return p.gamma_eps; }
+    static DEV double q(const ProbDev& p) { return p.q; }
+    static DEV double ubc(const ProbDev& p, int c) { return p.ubc[c]; }
+    static DEV double lo(const ProbDev& p) { return p.umin; }
+    static DEV double hi(const ProbDev& p) { return p.umax; }
+    static DEV double lo_tol(const ProbDev& p) { return p.lo_tol; }
+    static DEV double hi_tol(const ProbDev& p) { return p.hi_tol; }
+    static DEV double h(const MeshDev& m) { return m.h; }
+    static DEV double h2(const MeshDev& m) { return m.h * m.h; }
+    static DEV double me(const MeshDev& m) { return m.me; }
+    static DEV double inv_me(const MeshDev& m) { return m.inv_me; }
+};
+template <> struct PV<float> {
+    static DEV float vx(const ProbDev& p) { return p.vx_f; }
+    static DEV float vy(const ProbDev& p) { return p.vy_f; }
+    static DEV float gam(const ProbDev& p) { return p.gam_f; }
+    static DEV float w_lin(const ProbDev& p) { return p.w_lin_f; }
+    static DEV float weno_eps(const ProbDev& p) { return p.weno_eps_f; }
+    static DEV float gamma_eps(const ProbDev& p) { return p.gamma_eps_f; }
+    static DEV float q(const ProbDev& p) { return p.q_f; }
+    static DEV float ubc(const ProbDev& p, int c) { return p.ubc_f[c]; }
+    static DEV float lo(const ProbDev& p) { return p.lo32_f; }
+    static DEV float hi(const ProbDev& p) { return p.hi32_f; }
+    static DEV float lo_tol(const ProbDev& p) { return p.lo_tol_f; }
+    static DEV float hi_tol(const ProbDev& p) { return p.hi_tol_f; }
+    static DEV float h(const MeshDev& m) { return m.h_f; }
+    static DEV float h2(const MeshDev& m) { return m.h2_f; }
+    static DEV float me(const MeshDev& m) { return m.me_f; }
+    static DEV float inv_me(const MeshDev& m) { return m.inv_me_f; }
 };
 
 // 1D tables of degree p (index p), filled by the host from its own
@@ -87,14 +134,14 @@ template <> struct TabSel<float> {
 struct PhysAdv {
     static constexpr int NC = 1;
     template <class T> static DEV void flux(const T* u, T* fx, T* fy, const ProbDev& pr) {
-        fx[0] = T(pr.vx) * u[0];
-        fy[0] = T(pr.vy) * u[0];
+        fx[0] = PV<T>::vx(pr) * u[0];
+        fy[0] = PV<T>::vy(pr) * u[0];
     }
     template <class T> static DEV T max_speed(const T*, const T*, T nx, T ny, const ProbDev& pr) {
-        return fabs(T(pr.vx) * nx + T(pr.vy) * ny);
+        return fabs(PV<T>::vx(pr) * nx + PV<T>::vy(pr) * ny);
     }
     template <class T> static DEV T node_speed(const T*, const ProbDev& pr) {
-        return hypot(T(pr.vx), T(pr.vy));
+        return hypot(PV<T>::vx(pr), PV<T>::vy(pr));
     }
 };
 
@@ -129,7 +176,7 @@ struct PhysEuler {
         return (g - T(1)) * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) / u[0]);
     }
     template <class T> static DEV void flux(const T* u, T* fx, T* fy, const ProbDev& pr) {
-        const T g = T(pr.gam);
+        const T g = PV<T>::gam(pr);
         T rho = u[0], mx = u[1], my = u[2], E = u[3];
         T vx = mx / rho, vy = my / rho;
         T p = (g - T(1)) * (E - T(0.5) * (mx * mx + my * my) / rho);
@@ -143,7 +190,7 @@ struct PhysEuler {
         fy[3] = (E + p) * vy;
     }
     template <class T> static DEV T max_speed(const T* uL, const T* uR, T nx, T ny, const ProbDev& pr) {
-        const T g = T(pr.gam);
+        const T g = PV<T>::gam(pr);
         T rL = uL[0], rR = uR[0];
         T vL = (uL[1] * nx + uL[2] * ny) / rL;
         T vR = (uR[1] * nx + uR[2] * ny) / rR;
@@ -160,7 +207,7 @@ struct PhysEuler {
         return fmax(fabs(lam1), fabs(lam3));
     }
     template <class T> static DEV T node_speed(const T* u, const ProbDev& pr) {
-        const T g = T(pr.gam);
+        const T g = PV<T>::gam(pr);
         T c = sqrt(fmax(T(0), g * pressure(u, g) / u[0]));
         return hypot(u[1], u[2]) / u[0] + c;
     }

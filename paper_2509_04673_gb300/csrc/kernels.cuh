@@ -322,7 +322,7 @@ template <class R, int P, class Ph>
 DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
              const R (&U)[Ph::NC][Dim<P>::N2], const int (&nb)[4]) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
-    const R wl = R(pr.w_lin), eps = R(pr.weno_eps), geps = R(pr.gamma_eps);
+    const R wl = PV<R>::w_lin(pr), eps = PV<R>::weno_eps(pr), geps = PV<R>::gamma_eps(pr);
     const bool r2 = (pr.r == 2.0);
     const R rh = R(0.5 * pr.r);
     int ne = 0;
@@ -372,7 +372,7 @@ DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
         R num = sqrt(fmax(qform<R, P>(Dl), R(0)));
         R den = sqrt(sig0);
         R ratio = num / (den + geps);
-        R gc = R(1) - pow(fmin(R(1), ratio), R(pr.q));
+        R gc = R(1) - (pr.q == 1.0 ? fmin(R(1), ratio) : pow(fmin(R(1), ratio), PV<R>::q(pr)));
         gam = fmin(gam, gc);
     }
     return gam;
@@ -499,7 +499,7 @@ __global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __
             lm = fmax(lm, Ph::template node_speed<R>(ui, pr));
         }
         nu_out[e] = (double)lm * (m.h * (0.5 / m.p));
-        if (EV) grad_vectors<R, P, NC>(U, R(m.h), e, EV);
+        if (EV) grad_vectors<R, P, NC>(U, PV<R>::h(m), e, EV);
     }
     if (dtbits) block_min_to(dte, dtbits);
 }
@@ -524,7 +524,7 @@ __global__ void k_mass_ev(MeshDev m, const R* __restrict__ x, R* __restrict__ EV
     int ex, ey, e;
     if (!elem_of_thread(m, ex, ey, e)) return;
     const Tab<R>& T = TabSel<R>::t(P);
-    const R h2 = R(m.h * m.h);
+    const R h2 = PV<R>::h2(m);
     R X[NV][N2];
     load_block<R, P, NV>(x, m, ex, ey, X);
 #pragma unroll
@@ -634,7 +634,7 @@ __global__ void k_gather_init(MeshDev m, const R* __restrict__ EV, R* __restrict
     const NodeC<P> c = node_c<P>(m, gx, gy);
     R s[NV];
     gather_at<R, P, NV>(m, EV, c, s);
-    const R inv_mi = R(m.inv_me) * inv_count<R>(c.nxc * c.nyc);
+    const R inv_mi = PV<R>::inv_me(m) * inv_count<R>(c.nxc * c.nyc);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         if (bout) bout[v * m.NN + node] = s[v];
@@ -652,7 +652,7 @@ __global__ void k_gather_sweep(MeshDev m, const R* __restrict__ EV, const R* __r
     const NodeC<P> c = node_c<P>(m, gx, gy);
     R s[NV];
     gather_at<R, P, NV>(m, EV, c, s);
-    const R inv_mi = R(m.inv_me) * inv_count<R>(c.nxc * c.nyc);
+    const R inv_mi = PV<R>::inv_me(m) * inv_count<R>(c.nxc * c.nyc);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         long long k = v * m.NN + node;
@@ -720,7 +720,7 @@ __global__ void k_res_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R
     int ex, ey, e;
     if (!elem_of_thread(m, ex, ey, e)) return;
     const Tab<R>& T = TabSel<R>::t(P);
-    const R h = R(m.h);
+    const R h = PV<R>::h(m);
     R U[NC][N2];
     load_block<R, P, NC>(u, m, ex, ey, U);
     R W[NC][N2];
@@ -831,7 +831,7 @@ __global__ void k_res_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R
                 if (bc == BC_FIXED) {
                     R ub[NC];
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) ub[c] = R(pr.ubc[c]);
+                    for (int c = 0; c < NC; ++c) ub[c] = PV<R>::ubc(pr, c);
                     llf<Ph, R>(uq, ub, nxo, nyo, pr, F, (R*)nullptr);
                 } else {
                     R fx[NC], fy[NC];
@@ -973,7 +973,7 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
                 if (fixed_b) {
                     R ub[NC], F[NC];
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) ub[c] = R(pr.ubc[c]);
+                    for (int c = 0; c < NC; ++c) ub[c] = PV<R>::ubc(pr, c);
                     llf<Ph, R>(uk, ub, sg * cnx, sg * cny, pr, F, (R*)nullptr);
 #pragma unroll
                     for (int c = 0; c < NC; ++c) acc[c] += F[c];
@@ -1076,7 +1076,7 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
         return;
     }
     // f_i^e, eq. (aec) with eq. (aecb) folded into the residual
-    const R meR = R(me), h2 = R(h * h), dteR = R(dte), inv_meR = R(m.inv_me);
+    const R meR = PV<R>::me(m), h2 = PV<R>::h2(m), dteR = R(dte), inv_meR = PV<R>::inv_me(m);
     R F[NC][N2];
 #pragma unroll 1
     for (int c = 0; c < NC; ++c) {
@@ -1179,10 +1179,9 @@ __global__ void k_final(MeshDev m, ProbDev pr, const R* __restrict__ EW,
     if (bad) atomicAdd(&cnt[CNT_NONFINITE], 1ull);
     if (NC == 1) {
         if (pr.mode == MODE_LO || pr.mode == MODE_WENO_L) {
-            const R lo = (sizeof(R) == 4) ? R(pr.umin32) : R(pr.umin);
-            const R hi = (sizeof(R) == 4) ? R(pr.umax32) : R(pr.umax);
+            const R lo = PV<R>::lo(pr), hi = PV<R>::hi(pr);
             const R v = out[0];
-            if (v < R(pr.umin - pr.viol_tol) || v > R(pr.umax + pr.viol_tol))
+            if (v < PV<R>::lo_tol(pr) || v > PV<R>::hi_tol(pr))
                 atomicAdd(&cnt[CNT_VIOL], 1ull);
             if (v < lo || v > hi) {
                 atomicAdd(&cnt[CNT_CLAMP], 1ull);
