@@ -198,7 +198,9 @@ cgl_status cgl_step_async(cgl_state *state, int32_t nsteps);
 cgl_status cgl_get_counters(cgl_state *state, int64_t *out4);
 
 /* One SSP stage with a given dt: u <- a u^n + b FE(u), FE(u) the forward
-   Euler update eq. (eq:SSPupdate). Used by parity tests. */
+   Euler update eq. (eq:SSPupdate). With a = 0 the input state is also
+   stored as the base state u^n (as the first stage of a step does). Used by
+   parity tests. */
 cgl_status cgl_stage(cgl_state *state, double dt, double a, double b, cgl_step_info *info);
 
 /* Global dt = cfl * min_e dt_e of the current state (eq. (dtmaxcell)). */
@@ -218,6 +220,49 @@ cgl_status cgl_time_step(cgl_state *state, double *dt);
 #define CGL_FIELD_R 18      /* target residual r (ncomp) */
 #define CGL_FIELD_UDOT 19   /* udot (ncomp) */
 cgl_status cgl_get_field(cgl_state *state, int32_t field, double *host, size_t n);
+
+/* --- batches ------------------------------------------------------------------ */
+
+/* Many independent scalar instances (uneven sizes, degrees 1..4, own time
+   steps) advanced together: one persistent cooperative launch per SSP-RK
+   stage over all instances, the three launches of a step captured in a CUDA
+   graph. Every state must be FP32_MIXED, scalar (advection, Burgers, KPP),
+   on one device, with the same mode, k_g and k_u; the batch uses the first
+   state's stream and references (does not copy) the states, which must
+   outlive it. A batched instance evolves bitwise like the same state stepped
+   alone with cgl_step. */
+typedef struct cgl_batch cgl_batch;
+cgl_status cgl_batch_create(cgl_state *const *states, int32_t n, cgl_batch **out);
+void cgl_batch_destroy(cgl_batch *batch);
+
+/* nsteps SSP-RK3 steps of every instance; *violations receives the summed
+   invariant-domain violation counters of the instances (cumulative).
+   CGL_ETIMEOUT if a grid barrier gave up (the instances are then undefined). */
+cgl_status cgl_batch_step(cgl_batch *batch, int32_t nsteps, int64_t *violations);
+
+/* Enqueue nsteps steps without waiting. */
+cgl_status cgl_batch_step_async(cgl_batch *batch, int32_t nsteps);
+
+/* Launch geometry: persistent grid size, block size, tile counts, and
+   whether the step runs as a captured CUDA graph (1) or as direct launches. */
+cgl_status cgl_batch_info(cgl_batch *batch, int32_t *grid, int32_t *block, int32_t *elem_tiles,
+                          int32_t *node_tiles, int32_t *graph);
+
+/* Element-tile length per degree (tile_elems[p], p = 1..4, in [1, 128]). */
+cgl_status cgl_batch_set_tiles(cgl_batch *batch, const int32_t *tile_elems);
+cgl_status cgl_batch_get_tiles(cgl_batch *batch, int32_t *tile_elems);
+
+/* Autotuner: coordinate search of the tile length of every degree present
+   (32, 64, 96, 128), each trial timed over `steps` steps with CUDA events
+   (the states advance). Writes {"block", "tile_elems", "ms_per_step"} as
+   JSON to json_path unless it is NULL. */
+cgl_status cgl_batch_autotune(cgl_batch *batch, int32_t steps, const char *json_path);
+cgl_status cgl_batch_load_tuning(cgl_batch *batch, const char *json_path);
+
+/* Test hook: every grid barrier waits for phantom_blocks arrivals that never
+   come (0 = normal) and gives up after spin_limit polls, so the timeout path
+   (CGL_ETIMEOUT) can be exercised without any fault. */
+cgl_status cgl_batch_debug(cgl_batch *batch, int32_t phantom_blocks, int64_t spin_limit);
 
 /* --- measurement ------------------------------------------------------------ */
 

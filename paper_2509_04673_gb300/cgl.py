@@ -87,6 +87,16 @@ _PROTOS = [
     ("cgl_launches_per_step", C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     ("cgl_step_async", C.c_int, [C.c_void_p, C.c_int32]),
     ("cgl_get_counters", C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    ("cgl_batch_create", C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
+    ("cgl_batch_destroy", None, [C.c_void_p]),
+    ("cgl_batch_step", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
+    ("cgl_batch_step_async", C.c_int, [C.c_void_p, C.c_int32]),
+    ("cgl_batch_info", C.c_int, [C.c_void_p] + [C.POINTER(C.c_int32)] * 5),
+    ("cgl_batch_set_tiles", C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    ("cgl_batch_get_tiles", C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    ("cgl_batch_autotune", C.c_int, [C.c_void_p, C.c_int32, C.c_char_p]),
+    ("cgl_batch_load_tuning", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("cgl_batch_debug", C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
 ]
 
 
@@ -263,3 +273,55 @@ def debug_tables(p: int) -> dict:
         out[name] = buf[k:k + sz].reshape(shape)
         k += sz
     return out
+
+
+class Batch:
+    """Many independent FP32-mixed scalar states stepped together (one
+    persistent launch per SSP stage, CUDA graph per step)."""
+
+    def __init__(self, states):
+        self.states = list(states)
+        arr = (C.c_void_p * len(self.states))(*[s.h for s in self.states])
+        h = C.c_void_p()
+        check(lib().cgl_batch_create(arr, len(self.states), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.cgl_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def step(self, nsteps):
+        v = C.c_int64()
+        check(lib().cgl_batch_step(self.h, int(nsteps), C.byref(v)))
+        return v.value
+
+    def step_async(self, nsteps):
+        check(lib().cgl_batch_step_async(self.h, int(nsteps)))
+
+    def info(self):
+        vals = [C.c_int32() for _ in range(5)]
+        check(lib().cgl_batch_info(self.h, *[C.byref(v) for v in vals]))
+        return dict(zip(("grid", "block", "elem_tiles", "node_tiles", "graph"), [v.value for v in vals]))
+
+    def tiles(self):
+        t = (C.c_int32 * 5)()
+        check(lib().cgl_batch_get_tiles(self.h, t))
+        return list(t)
+
+    def set_tiles(self, tiles):
+        t = (C.c_int32 * 5)(*[int(x) for x in tiles])
+        check(lib().cgl_batch_set_tiles(self.h, t))
+
+    def autotune(self, steps=2, json_path=None):
+        check(lib().cgl_batch_autotune(self.h, int(steps), json_path.encode() if json_path else None))
+        return self.tiles()
+
+    def load_tuning(self, json_path):
+        check(lib().cgl_batch_load_tuning(self.h, json_path.encode()))
+
+    def debug(self, phantom_blocks, spin_limit):
+        check(lib().cgl_batch_debug(self.h, int(phantom_blocks), int(spin_limit)))

@@ -20,6 +20,7 @@
 
 #include "../../include/cgl.h"
 #include "stage.cuh"
+#include "state.h"
 
 using namespace cgl;
 
@@ -44,6 +45,16 @@ static cgl_status fail(cgl_status st, const char* fmt, ...) {
     } while (0)
 
 extern "C" const char* cgl_last_error(void) { return g_err; }
+
+namespace cgl {
+cgl_status set_error(cgl_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+}  // namespace cgl
 extern "C" const char* cgl_version(void) { return "cgl 0.1 sm_103a"; }
 
 // ---------------------------------------------------------------------------
@@ -249,10 +260,7 @@ extern "C" cgl_status cgl_debug_tables(int32_t p, double* out, size_t n, size_t*
 // ---------------------------------------------------------------------------
 // mesh
 // ---------------------------------------------------------------------------
-struct cgl_mesh {
-    cgl_mesh_desc d;
-    MeshDev m;
-};
+
 
 extern "C" cgl_status cgl_mesh_create(const cgl_mesh_desc* d, cgl_mesh** out) {
     if (!d || !out) return fail(CGL_EINVAL, "null argument");
@@ -342,21 +350,7 @@ extern "C" cgl_status cgl_problem_defaults(cgl_problem* p, int32_t flux) {
 // ---------------------------------------------------------------------------
 // state
 // ---------------------------------------------------------------------------
-struct cgl_state {
-    const cgl_mesh* mesh;
-    int nc, prec, device;
-    cudaStream_t st;
-    bool own_stream;
-    bool has_problem;
-    cgl_problem prob;
-    ProbDev pd;
-    StageFn stage;
-    Bufs B;
-    size_t rsz;  // bytes per bulk value
-    cudaGraphExec_t step_graph;
-    double* diag;       // device partials for diagnostics
-    std::vector<void*> allocs;
-};
+
 
 static std::mutex g_upload_mu;
 static std::vector<int> g_uploaded;  // devices whose constant memory holds the tables
@@ -366,7 +360,7 @@ static cgl_status ensure_tables(int dev) {
     for (int d : g_uploaded)
         if (d == dev) return CGL_OK;
     const HostTables& H = host_tables();
-    UploadFn fns[4] = {upload_adv, upload_burgers, upload_kpp, upload_euler};
+    UploadFn fns[5] = {upload_adv, upload_burgers, upload_kpp, upload_euler, upload_batch};
     for (UploadFn f : fns) CUDA_TRY(f(H.td, H.tf, H.a2d, H.a2f));
     g_uploaded.push_back(dev);
     return CGL_OK;
@@ -736,11 +730,8 @@ static cgl_status read_info(cgl_state* S, cgl_step_info* info, long long steps, 
 static cudaError_t enqueue_step(cgl_state* S, Prof* prof = nullptr) {
     const MeshDev& m = S->mesh->m;
     const Bufs& B = S->B;
-    cudaError_t e = cudaSuccess;
-    CGL_LAUNCH(prof, KID_COPY, S->st,
-               (e = cudaMemcpyAsync(B.un, B.u, (size_t)S->nc * m.NN * S->rsz, cudaMemcpyDeviceToDevice, S->st)));
-    if (e != cudaSuccess) return e;
-    e = S->stage(B, m, S->pd, 0.0, 1.0, true, false, S->st, prof);
+    // the first stage (a = 0) stores u^n into B.un as it overwrites u
+    cudaError_t e = S->stage(B, m, S->pd, 0.0, 1.0, true, false, S->st, prof);
     if (e != cudaSuccess) return e;
     e = S->stage(B, m, S->pd, 0.75, 0.25, false, false, S->st, prof);
     if (e != cudaSuccess) return e;

@@ -1,0 +1,584 @@
+// batch.cu — many independent scalar instances (uneven mesh sizes and
+// degrees, own time steps) advanced by one persistent cooperative launch per
+// SSP-RK stage, the three launches of a step captured in a CUDA graph.
+//
+// The work of every phase of the stage (the passes of Sec. 4.3 of the
+// paper, see kernels.cuh) is cut into tiles: (instance, run of elements) for
+// element phases, (instance, run of nodes) for node phases. The blocks of the
+// persistent grid walk the tiles of a phase, then meet at a grid barrier.
+// Each element / node is processed by exactly the device functions of the
+// single-instance kernels, so a batched instance is bitwise equal to the
+// same instance stepped alone. Element-tile lengths per degree are the tuning
+// knob (cgl_batch_autotune).
+//
+// Grid barriers spin with a bounded iteration count; a barrier that gives up
+// sets an error flag, every block returns at its next barrier, and the host
+// reports CGL_ETIMEOUT.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "state.h"
+
+namespace cgl {
+
+struct InstDev {
+    MeshDev m;
+    ProbDev pr;
+    float *u, *un, *g, *bg, *r, *ud, *EV, *ER, *EW;
+    double *ue, *dte, *ubl, *gam, *nu, *q, *fl, *ube, *beta;
+    unsigned long long *cnt, *dtbits;
+    double *dt, *t, *t_end;
+    int p, phys;
+};
+
+struct Tile {
+    int inst, begin, count, pad;
+};
+
+struct BatchSync {
+    unsigned int count;
+    unsigned int gen;
+    int err;
+    int phantom;  // extra arrivals a barrier waits for (0; > 0 only to test the timeout)
+};
+
+enum { PH_PRE = 0, PH_MASS_G, PH_RES, PH_MASS_U, PH_UPDATE };
+enum { PH_GATHER_G = 0, PH_SWEEP_G, PH_GATHER_R, PH_SWEEP_U, PH_FINAL };
+
+constexpr int BT = 128;  // threads per block of the persistent grid
+
+// bounded grid barrier: returns false if it gave up (or another block did)
+DEV bool grid_sync(BatchSync* s, long long limit) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned int* vgen = &s->gen;
+        volatile int* verr = &s->err;
+        const unsigned int g = *vgen;
+        __threadfence();
+        const unsigned int need = gridDim.x + (unsigned int)s->phantom;
+        const unsigned int arrived = atomicAdd(&s->count, 1u) + 1u;
+        if (arrived == need) {
+            atomicExch(&s->count, 0u);
+            __threadfence();
+            atomicAdd(&s->gen, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == g) {
+                if (*verr || ++it > limit) {
+                    atomicExch(&s->err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <int P, class Ph>
+DEV void elem_phase(int phase, const InstDev& D, int ex, int ey, int e, double& dte) {
+    switch (phase) {
+        case PH_PRE:
+            dte = pre_at<float, P, Ph>(D.m, D.pr, D.u, D.ue, D.dte, D.ubl, D.gam, D.nu, D.q, D.fl,
+                                       D.pr.mode != MODE_LO ? D.EV : nullptr, ex, ey, e);
+            break;
+        case PH_MASS_G: mass_at<float, P, 2>(D.m, D.g, D.EV, ex, ey, e); break;
+        case PH_RES: res_at<float, P, Ph>(D.m, D.pr, D.u, D.g, D.gam, D.nu, D.ER, ex, ey, e); break;
+        case PH_MASS_U: mass_at<float, P, 1>(D.m, D.ud, D.EV, ex, ey, e); break;
+        default:
+            update_at<float, P, Ph>(D.m, D.pr, D.u, D.ud, D.ue, D.dte, D.ubl, D.q, D.fl, D.ER, D.dt, D.EW,
+                                    D.ube, D.beta, D.cnt, ex, ey, e);
+    }
+}
+
+DEV void elem_dispatch(int phase, const InstDev& D, int ex, int ey, int e, double& dte) {
+    switch (D.p * 3 + D.phys) {
+        case 3: elem_phase<1, PhysAdv>(phase, D, ex, ey, e, dte); break;
+        case 4: elem_phase<1, PhysBurgers>(phase, D, ex, ey, e, dte); break;
+        case 5: elem_phase<1, PhysKPP>(phase, D, ex, ey, e, dte); break;
+        case 6: elem_phase<2, PhysAdv>(phase, D, ex, ey, e, dte); break;
+        case 7: elem_phase<2, PhysBurgers>(phase, D, ex, ey, e, dte); break;
+        case 8: elem_phase<2, PhysKPP>(phase, D, ex, ey, e, dte); break;
+        case 9: elem_phase<3, PhysAdv>(phase, D, ex, ey, e, dte); break;
+        case 10: elem_phase<3, PhysBurgers>(phase, D, ex, ey, e, dte); break;
+        case 11: elem_phase<3, PhysKPP>(phase, D, ex, ey, e, dte); break;
+        case 12: elem_phase<4, PhysAdv>(phase, D, ex, ey, e, dte); break;
+        case 13: elem_phase<4, PhysBurgers>(phase, D, ex, ey, e, dte); break;
+        default: elem_phase<4, PhysKPP>(phase, D, ex, ey, e, dte); break;
+    }
+}
+
+template <int P>
+DEV void node_phase(int phase, const InstDev& D, int gx, int gy, long long node, float a, float b) {
+    switch (phase) {
+        case PH_GATHER_G: gather_init_at<float, P, 2>(D.m, D.EV, D.bg, D.g, gx, gy, node); break;
+        case PH_SWEEP_G: gather_sweep_at<float, P, 2>(D.m, D.EV, D.bg, D.g, gx, gy, node); break;
+        case PH_GATHER_R: gather_init_at<float, P, 1>(D.m, D.ER, D.r, D.ud, gx, gy, node); break;
+        case PH_SWEEP_U: gather_sweep_at<float, P, 1>(D.m, D.EV, D.r, D.ud, gx, gy, node); break;
+        default: final_at<float, P, 1>(D.m, D.pr, D.EW, D.un, D.u, a, b, D.cnt, gx, gy, node);
+    }
+}
+
+DEV void node_dispatch(int phase, const InstDev& D, int gx, int gy, long long node, float a, float b) {
+    switch (D.p) {
+        case 1: node_phase<1>(phase, D, gx, gy, node, a, b); break;
+        case 2: node_phase<2>(phase, D, gx, gy, node, a, b); break;
+        case 3: node_phase<3>(phase, D, gx, gy, node, a, b); break;
+        default: node_phase<4>(phase, D, gx, gy, node, a, b); break;
+    }
+}
+
+DEV void elem_loop(int phase, const InstDev* __restrict__ I, const Tile* __restrict__ et, int net, bool first) {
+    for (int t = blockIdx.x; t < net; t += gridDim.x) {
+        const Tile T = et[t];
+        const InstDev& D = I[T.inst];
+        double dte = __longlong_as_double(0x7ff0000000000000LL);
+        if ((int)threadIdx.x < T.count) {
+            const int e = T.begin + threadIdx.x;
+            const int ey = e / D.m.nx, ex = e - ey * D.m.nx;
+            elem_dispatch(phase, D, ex, ey, e, dte);
+        }
+        if (phase == PH_PRE && first) block_min_to(dte, D.dtbits);
+    }
+}
+
+DEV void node_loop(int phase, const InstDev* __restrict__ I, const Tile* __restrict__ nt, int nnt, float a,
+                   float b) {
+    for (int t = blockIdx.x; t < nnt; t += gridDim.x) {
+        const Tile T = nt[t];
+        if ((int)threadIdx.x < T.count) {
+            const InstDev& D = I[T.inst];
+            const long long node = (long long)T.begin + threadIdx.x;
+            const int gy = (int)(node / D.m.nnx), gx = (int)(node - (long long)gy * D.m.nnx);
+            node_dispatch(phase, D, gx, gy, node, a, b);
+        }
+    }
+}
+
+// one SSP stage u <- a u^n + b FE(u) for every instance
+__global__ void __launch_bounds__(BT)
+    k_batch_stage(const InstDev* __restrict__ I, int ninst, const Tile* __restrict__ et, int net,
+                  const Tile* __restrict__ nt, int nnt, BatchSync* sync, float a, float b, int first,
+                  int last, int kg, int ku, int mode_lo, long long limit) {
+    elem_loop(PH_PRE, I, et, net, first != 0);
+    if (!grid_sync(sync, limit)) return;
+    if (first) {
+        // global dt of each instance from its block minima (eq. (cflglob),
+        // scaled by omega_CFL, capped at t_end - t)
+        for (int i = blockIdx.x * BT + threadIdx.x; i < ninst; i += gridDim.x * BT) {
+            const InstDev& D = I[i];
+            double d = D.pr.cfl * __longlong_as_double((long long)*D.dtbits);
+            *D.dtbits = 0x7ff0000000000000ull;
+            double rem = *D.t_end - *D.t;
+            if (rem < d) d = rem > 0.0 ? rem : 0.0;
+            *D.dt = d;
+        }
+        if (mode_lo && !grid_sync(sync, limit)) return;
+    }
+    if (!mode_lo) {
+        node_loop(PH_GATHER_G, I, nt, nnt, a, b);
+        if (!grid_sync(sync, limit)) return;
+        for (int k = 0; k < kg; ++k) {
+            elem_loop(PH_MASS_G, I, et, net, false);
+            if (!grid_sync(sync, limit)) return;
+            node_loop(PH_SWEEP_G, I, nt, nnt, a, b);
+            if (!grid_sync(sync, limit)) return;
+        }
+        elem_loop(PH_RES, I, et, net, false);
+        if (!grid_sync(sync, limit)) return;
+        node_loop(PH_GATHER_R, I, nt, nnt, a, b);
+        if (!grid_sync(sync, limit)) return;
+        for (int k = 0; k < ku; ++k) {
+            elem_loop(PH_MASS_U, I, et, net, false);
+            if (!grid_sync(sync, limit)) return;
+            node_loop(PH_SWEEP_U, I, nt, nnt, a, b);
+            if (!grid_sync(sync, limit)) return;
+        }
+    }
+    elem_loop(PH_UPDATE, I, et, net, false);
+    if (!grid_sync(sync, limit)) return;
+    node_loop(PH_FINAL, I, nt, nnt, a, b);
+    if (last) {
+        for (int i = blockIdx.x * BT + threadIdx.x; i < ninst; i += gridDim.x * BT) *I[i].t += *I[i].dt;
+    }
+}
+
+cudaError_t upload_batch(const Tab<double>* td, const Tab<float>* tf, const double* a2d, const float* a2f) {
+    return upload_tables_here(td, tf, a2d, a2f);
+}
+
+}  // namespace cgl
+
+using namespace cgl;
+
+struct cgl_batch {
+    std::vector<cgl_state*> states;
+    cudaStream_t st;
+    int ninst;
+    InstDev* d_inst;
+    Tile *d_et, *d_nt;
+    int net, nnt;
+    BatchSync* d_sync;
+    int grid;
+    int tile_elems[PMAX + 1];
+    int node_tile;
+    int mode_lo, kg, ku;
+    long long limit;
+    int phantom;
+    cudaGraphExec_t graph;
+    bool use_graph;
+};
+
+static cgl_status bfail(cgl_status st, const char* msg, cudaError_t e = cudaSuccess) {
+    if (e != cudaSuccess) return set_error(st, "%s: %s", msg, cudaGetErrorString(e));
+    return set_error(st, "%s", msg);
+}
+
+static cgl_status build_tiles(cgl_batch* B) {
+    std::vector<Tile> et, nt;
+    for (int i = 0; i < B->ninst; ++i) {
+        const MeshDev& m = B->states[i]->mesh->m;
+        const int T = std::max(1, std::min(BT, B->tile_elems[m.p]));
+        for (int b = 0; b < m.E; b += T) et.push_back(Tile{i, b, std::min(T, m.E - b), 0});
+        const int TN = BT;
+        for (long long b = 0; b < m.NN; b += TN)
+            nt.push_back(Tile{i, (int)b, (int)std::min<long long>(TN, m.NN - b), 0});
+    }
+    if (B->d_et) cudaFree(B->d_et);
+    if (B->d_nt) cudaFree(B->d_nt);
+    B->d_et = B->d_nt = nullptr;
+    cudaError_t e = cudaMalloc(&B->d_et, et.size() * sizeof(Tile));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_nt, nt.size() * sizeof(Tile));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B->d_et, et.data(), et.size() * sizeof(Tile), cudaMemcpyHostToDevice, B->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B->d_nt, nt.data(), nt.size() * sizeof(Tile), cudaMemcpyHostToDevice, B->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->st);
+    if (e != cudaSuccess) return bfail(CGL_ECUDA, "tile upload", e);
+    B->net = (int)et.size();
+    B->nnt = (int)nt.size();
+    if (B->graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
+    }
+    return CGL_OK;
+}
+
+static cudaError_t launch_stage(cgl_batch* B, float a, float b, int first, int last) {
+    void* args[] = {&B->d_inst, &B->ninst, &B->d_et, &B->net, &B->d_nt, &B->nnt, &B->d_sync, &a, &b,
+                    &first, &last, &B->kg, &B->ku, &B->mode_lo, &B->limit};
+    return cudaLaunchCooperativeKernel((const void*)k_batch_stage, dim3(B->grid), dim3(BT), args, 0, B->st);
+}
+
+static cudaError_t enqueue_batch_step(cgl_batch* B) {
+    cudaError_t e = launch_stage(B, 0.f, 1.f, 1, 0);
+    if (e == cudaSuccess) e = launch_stage(B, 0.75f, 0.25f, 0, 0);
+    if (e == cudaSuccess) e = launch_stage(B, 1.f / 3.f, 2.f / 3.f, 0, 1);
+    return e;
+}
+
+static cgl_status ensure_graph(cgl_batch* B) {
+    if (B->graph || !B->use_graph) return CGL_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(B->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        B->use_graph = false;
+        cudaGetLastError();
+        return CGL_OK;
+    }
+    cudaError_t e1 = enqueue_batch_step(B);
+    cudaError_t e2 = cudaStreamEndCapture(B->st, &g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        B->use_graph = false;  // cooperative launches not capturable here: launch directly
+        return CGL_OK;
+    }
+    e = cudaGraphInstantiate(&B->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        B->graph = nullptr;
+        B->use_graph = false;
+    }
+    return CGL_OK;
+}
+
+extern "C" void cgl_batch_destroy(cgl_batch* B) {
+    if (!B) return;
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    if (B->d_inst) cudaFree(B->d_inst);
+    if (B->d_et) cudaFree(B->d_et);
+    if (B->d_nt) cudaFree(B->d_nt);
+    if (B->d_sync) cudaFree(B->d_sync);
+    delete B;
+}
+
+extern "C" cgl_status cgl_batch_create(cgl_state* const* states, int32_t n, cgl_batch** out) {
+    if (!states || !out || n < 1) return bfail(CGL_EINVAL, "need at least one state");
+    *out = nullptr;
+    const cgl_state* s0 = states[0];
+    for (int i = 0; i < n; ++i) {
+        const cgl_state* s = states[i];
+        if (!s || !s->has_problem) return bfail(CGL_EINVAL, "every state needs a problem");
+        if (s->prec != CGL_FP32_MIXED) return bfail(CGL_EINVAL, "batched states must be FP32_MIXED");
+        if (s->nc != 1 || s->prob.flux == CGL_FLUX_EULER) return bfail(CGL_EINVAL, "batched states must be scalar");
+        if (s->device != s0->device) return bfail(CGL_EINVAL, "batched states must share a device");
+        if (s->prob.mode != s0->prob.mode || s->prob.k_g != s0->prob.k_g || s->prob.k_u != s0->prob.k_u)
+            return bfail(CGL_EINVAL, "batched states must share mode, k_g and k_u");
+        if ((long long)s->mesh->m.NN >= (1LL << 31)) return bfail(CGL_EINVAL, "instance too large for a batch");
+    }
+    cgl_batch* B = new (std::nothrow) cgl_batch();
+    if (!B) return bfail(CGL_EOOM, "host allocation failed");
+    B->states.assign(states, states + n);
+    B->st = s0->st;
+    B->ninst = n;
+    B->mode_lo = s0->prob.mode == CGL_MODE_LO;
+    B->kg = s0->prob.k_g;
+    B->ku = s0->prob.k_u;
+    B->limit = 1LL << 22;
+    B->phantom = 0;
+    B->node_tile = BT;
+    B->use_graph = true;
+    for (int p = 0; p <= PMAX; ++p) B->tile_elems[p] = BT;
+    std::vector<InstDev> h(n);
+    for (int i = 0; i < n; ++i) {
+        const cgl_state* s = states[i];
+        const Bufs& b = s->B;
+        InstDev& d = h[i];
+        d.m = s->mesh->m;
+        d.pr = s->pd;
+        d.u = (float*)b.u;
+        d.un = (float*)b.un;
+        d.g = (float*)b.g;
+        d.bg = (float*)b.bg;
+        d.r = (float*)b.r;
+        d.ud = (float*)b.ud;
+        d.EV = (float*)b.EV;
+        d.ER = (float*)b.ER;
+        d.EW = (float*)b.EW;
+        d.ue = b.ue;
+        d.dte = b.dte;
+        d.ubl = b.ubl;
+        d.gam = b.gam;
+        d.nu = b.nu;
+        d.q = b.q;
+        d.fl = b.fl;
+        d.ube = b.ube;
+        d.beta = b.beta;
+        d.cnt = b.cnt;
+        d.dtbits = b.dtbits;
+        d.dt = b.dt;
+        d.t = b.t;
+        d.t_end = b.t_end;
+        d.p = s->mesh->m.p;
+        d.phys = s->prob.flux;  // 0 advection, 1 Burgers, 2 KPP
+    }
+    cudaError_t e = cudaMalloc(&B->d_inst, n * sizeof(InstDev));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_sync, sizeof(BatchSync));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_inst, h.data(), n * sizeof(InstDev), cudaMemcpyHostToDevice, B->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_sync, 0, sizeof(BatchSync), B->st);
+    if (e != cudaSuccess) {
+        cgl_batch_destroy(B);
+        return bfail(CGL_ECUDA, "batch allocation", e);
+    }
+    int nsm = 0, per_sm = 0;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s0->device);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_stage, BT, 0);
+    if (e != cudaSuccess || per_sm < 1) {
+        cgl_batch_destroy(B);
+        return bfail(CGL_ECUDA, "occupancy query", e);
+    }
+    B->grid = nsm * per_sm;
+    cgl_status rc = build_tiles(B);
+    if (rc) {
+        cgl_batch_destroy(B);
+        return rc;
+    }
+    *out = B;
+    return CGL_OK;
+}
+
+static cgl_status check_sync(cgl_batch* B) {
+    BatchSync hs;
+    cudaError_t e = cudaMemcpyAsync(&hs, B->d_sync, sizeof(hs), cudaMemcpyDeviceToHost, B->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->st);
+    if (e != cudaSuccess) return bfail(CGL_ECUDA, "batch step", e);
+    if (hs.err) {
+        // reset the barrier for the next call
+        cudaMemsetAsync(B->d_sync, 0, sizeof(BatchSync), B->st);
+        int ph = B->phantom;
+        cudaMemcpyAsync(&B->d_sync->phantom, &ph, sizeof(int), cudaMemcpyHostToDevice, B->st);
+        cudaStreamSynchronize(B->st);
+        return set_error(CGL_ETIMEOUT, "a grid barrier of the batched stage gave up");
+    }
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_batch_step_async(cgl_batch* B, int32_t nsteps) {
+    if (!B || nsteps < 0) return bfail(CGL_EINVAL, "bad argument");
+    cgl_status rc = ensure_graph(B);
+    if (rc) return rc;
+    for (int s = 0; s < nsteps; ++s) {
+        cudaError_t e = B->graph ? cudaGraphLaunch(B->graph, B->st) : enqueue_batch_step(B);
+        if (e != cudaSuccess) return bfail(CGL_ECUDA, "batch launch", e);
+    }
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_batch_step(cgl_batch* B, int32_t nsteps, int64_t* violations) {
+    cgl_status rc = cgl_batch_step_async(B, nsteps);
+    if (rc) return rc;
+    rc = check_sync(B);
+    if (rc) return rc;
+    int64_t tot = 0;
+    for (cgl_state* s : B->states) {
+        unsigned long long c[CNT_N];
+        cudaError_t e = cudaMemcpyAsync(c, s->B.cnt, sizeof(c), cudaMemcpyDeviceToHost, B->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(B->st);
+        if (e != cudaSuccess) return bfail(CGL_ECUDA, "counter read", e);
+        tot += (int64_t)c[CNT_VIOL];
+    }
+    if (violations) *violations = tot;
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_batch_info(cgl_batch* B, int32_t* grid, int32_t* block, int32_t* elem_tiles,
+                                     int32_t* node_tiles, int32_t* graph) {
+    if (!B) return bfail(CGL_EINVAL, "null batch");
+    if (grid) *grid = B->grid;
+    if (block) *block = BT;
+    if (elem_tiles) *elem_tiles = B->net;
+    if (node_tiles) *node_tiles = B->nnt;
+    if (graph) *graph = B->graph ? 1 : 0;
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_batch_set_tiles(cgl_batch* B, const int32_t* tile_elems) {
+    if (!B || !tile_elems) return bfail(CGL_EINVAL, "null argument");
+    for (int p = 1; p <= PMAX; ++p)
+        if (tile_elems[p] < 1 || tile_elems[p] > BT) return bfail(CGL_EINVAL, "tile length must be in [1, 128]");
+    for (int p = 1; p <= PMAX; ++p) B->tile_elems[p] = tile_elems[p];
+    return build_tiles(B);
+}
+
+extern "C" cgl_status cgl_batch_get_tiles(cgl_batch* B, int32_t* tile_elems) {
+    if (!B || !tile_elems) return bfail(CGL_EINVAL, "null argument");
+    for (int p = 0; p <= PMAX; ++p) tile_elems[p] = B->tile_elems[p];
+    return CGL_OK;
+}
+
+static cgl_status time_steps(cgl_batch* B, int steps, float* ms) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cgl_status rc = cgl_batch_step_async(B, 1);  // warm-up (and graph build)
+    if (!rc) {
+        cudaEventRecord(a, B->st);
+        rc = cgl_batch_step_async(B, steps);
+        cudaEventRecord(b, B->st);
+    }
+    if (!rc) rc = check_sync(B);
+    if (!rc) cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return rc;
+}
+
+// Coordinate search over the element-tile length of each degree present in
+// the batch (candidates 32, 64, 96, 128), timing `steps` steps per trial.
+// The states are advanced by the trials. Writes the choice as JSON if path.
+extern "C" cgl_status cgl_batch_autotune(cgl_batch* B, int32_t steps, const char* json_path) {
+    if (!B || steps < 1) return bfail(CGL_EINVAL, "bad argument");
+    bool present[PMAX + 1] = {false};
+    for (cgl_state* s : B->states) present[s->mesh->m.p] = true;
+    const int cand[] = {32, 64, 96, 128};
+    float best_all = 0.f;
+    cgl_status rc = time_steps(B, steps, &best_all);
+    if (rc) return rc;
+    for (int p = 1; p <= PMAX; ++p) {
+        if (!present[p]) continue;
+        int best = B->tile_elems[p];
+        for (int c : cand) {
+            if (c == best) continue;
+            int keep = B->tile_elems[p];
+            B->tile_elems[p] = c;
+            rc = build_tiles(B);
+            float ms = 0.f;
+            if (!rc) rc = time_steps(B, steps, &ms);
+            if (rc) return rc;
+            if (ms < best_all) {
+                best_all = ms;
+                best = c;
+            } else {
+                B->tile_elems[p] = keep;
+            }
+        }
+        B->tile_elems[p] = best;
+        rc = build_tiles(B);
+        if (rc) return rc;
+    }
+    if (json_path && json_path[0]) {
+        FILE* f = std::fopen(json_path, "w");
+        if (!f) return bfail(CGL_EINVAL, "cannot write the tuning file");
+        std::fprintf(f, "{\"block\": %d, \"tile_elems\": {", BT);
+        bool firstk = true;
+        for (int p = 1; p <= PMAX; ++p) {
+            std::fprintf(f, "%s\"%d\": %d", firstk ? "" : ", ", p, B->tile_elems[p]);
+            firstk = false;
+        }
+        std::fprintf(f, "}, \"ms_per_step\": %.6f}\n", best_all / steps);
+        std::fclose(f);
+    }
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_batch_load_tuning(cgl_batch* B, const char* json_path) {
+    if (!B || !json_path) return bfail(CGL_EINVAL, "null argument");
+    FILE* f = std::fopen(json_path, "r");
+    if (!f) return bfail(CGL_EINVAL, "cannot read the tuning file");
+    char buf[4096];
+    size_t n = std::fread(buf, 1, sizeof(buf) - 1, f);
+    std::fclose(f);
+    buf[n] = 0;
+    int32_t t[PMAX + 1];
+    for (int p = 0; p <= PMAX; ++p) t[p] = B->tile_elems[p];
+    for (int p = 1; p <= PMAX; ++p) {
+        char key[16];
+        std::snprintf(key, sizeof(key), "\"%d\":", p);
+        const char* k = std::strstr(buf, key);
+        if (k) t[p] = std::atoi(k + std::strlen(key));
+    }
+    return cgl_batch_set_tiles(B, t);
+}
+
+// Test hook: make every grid barrier wait for `phantom_blocks` arrivals
+// that never come (0 = normal operation) and give up after `spin_limit`
+// polls. Used to exercise the timeout path without faulting anything.
+extern "C" cgl_status cgl_batch_debug(cgl_batch* B, int32_t phantom_blocks, int64_t spin_limit) {
+    if (!B || phantom_blocks < 0 || spin_limit < 1) return bfail(CGL_EINVAL, "bad argument");
+    B->phantom = phantom_blocks;
+    B->limit = spin_limit;
+    int ph = phantom_blocks;
+    cudaError_t e = cudaMemcpyAsync(&B->d_sync->phantom, &ph, sizeof(int), cudaMemcpyHostToDevice, B->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->st);
+    if (e != cudaSuccess) return bfail(CGL_ECUDA, "debug", e);
+    if (B->graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
+    }
+    return CGL_OK;
+}

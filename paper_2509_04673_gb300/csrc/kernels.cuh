@@ -414,16 +414,14 @@ DEV void block_min_to(double v, unsigned long long* bits) {
 // g_h right-hand side, and (stage 1) the block minimum of dt_e.
 // ---------------------------------------------------------------------------
 template <class R, int P, class Ph>
-__global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __restrict__ ue_out,
-                      double* __restrict__ dte_out, double* __restrict__ ubl_out,
-                      double* __restrict__ gam_out, double* __restrict__ nu_out,
-                      double* __restrict__ q_out, double* __restrict__ fl_out, R* __restrict__ EV,
-                      unsigned long long* __restrict__ dtbits) {
+DEV double pre_at(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __restrict__ ue_out,
+                  double* __restrict__ dte_out, double* __restrict__ ubl_out,
+                  double* __restrict__ gam_out, double* __restrict__ nu_out,
+                  double* __restrict__ q_out, double* __restrict__ fl_out, R* __restrict__ EV,
+                  int ex, int ey, int e) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
-    int ex, ey, e;
-    const bool valid = elem_of_thread(m, ex, ey, e);
-    double dte = __longlong_as_double(0x7ff0000000000000LL);
-    if (valid) {
+    double dte;
+    {
         int nb[4];
 #pragma unroll
         for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
@@ -501,6 +499,19 @@ __global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __
         nu_out[e] = (double)lm * (m.h * (0.5 / m.p));
         if (EV) grad_vectors<R, P, NC>(U, PV<R>::h(m), e, EV);
     }
+    return dte;
+}
+
+template <class R, int P, class Ph>
+__global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __restrict__ ue_out,
+                      double* __restrict__ dte_out, double* __restrict__ ubl_out,
+                      double* __restrict__ gam_out, double* __restrict__ nu_out,
+                      double* __restrict__ q_out, double* __restrict__ fl_out, R* __restrict__ EV,
+                      unsigned long long* __restrict__ dtbits) {
+    int ex, ey, e;
+    double dte = __longlong_as_double(0x7ff0000000000000LL);
+    if (elem_of_thread(m, ex, ey, e))
+        dte = pre_at<R, P, Ph>(m, pr, u, ue_out, dte_out, ubl_out, gam_out, nu_out, q_out, fl_out, EV, ex, ey, e);
     if (dtbits) block_min_to(dte, dtbits);
 }
 
@@ -519,10 +530,8 @@ static __global__ void k_t_advance(double* t, const double* dt) { *t = *t + *dt;
 
 // k_mass_ev: (M_C x)^e_i = h^2 sum (M (x) M) x_e for NV nodal fields
 template <class R, int P, int NV>
-__global__ void k_mass_ev(MeshDev m, const R* __restrict__ x, R* __restrict__ EV) {
+DEV void mass_at(MeshDev m, const R* __restrict__ x, R* __restrict__ EV, int ex, int ey, int e) {
     constexpr int N1 = P + 1, N2 = Dim<P>::N2;
-    int ex, ey, e;
-    if (!elem_of_thread(m, ex, ey, e)) return;
     const Tab<R>& T = TabSel<R>::t(P);
     const R h2 = PV<R>::h2(m);
     R X[NV][N2];
@@ -550,6 +559,14 @@ __global__ void k_mass_ev(MeshDev m, const R* __restrict__ x, R* __restrict__ EV
             }
     }
 }
+
+template <class R, int P, int NV>
+__global__ void k_mass_ev(MeshDev m, const R* __restrict__ x, R* __restrict__ EV) {
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
+    mass_at<R, P, NV>(m, x, EV, ex, ey, e);
+}
+
 
 // ---------------------------------------------------------------------------
 // node-centric gathers over E_i in a fixed order (lower neighbour first in
@@ -626,11 +643,8 @@ DEV void gather_at(const MeshDev& m, const R* __restrict__ EV, const NodeC<P>& c
 
 // sum over E_i of element vectors; out[v*NN + node]; if xout, also x = sum / m_i
 template <class R, int P, int NV>
-__global__ void k_gather_init(MeshDev m, const R* __restrict__ EV, R* __restrict__ bout,
-                              R* __restrict__ xout) {
-    int gx, gy;
-    long long node;
-    if (!node_of_thread(m, gx, gy, node)) return;
+DEV void gather_init_at(MeshDev m, const R* __restrict__ EV, R* __restrict__ bout,
+                              R* __restrict__ xout, int gx, int gy, long long node) {
     const NodeC<P> c = node_c<P>(m, gx, gy);
     R s[NV];
     gather_at<R, P, NV>(m, EV, c, s);
@@ -642,13 +656,20 @@ __global__ void k_gather_init(MeshDev m, const R* __restrict__ EV, R* __restrict
     }
 }
 
-// Richardson sweep x <- x + (b - sum EV) / m_i
 template <class R, int P, int NV>
-__global__ void k_gather_sweep(MeshDev m, const R* __restrict__ EV, const R* __restrict__ b,
-                               R* __restrict__ x) {
+__global__ void k_gather_init(MeshDev m, const R* __restrict__ EV, R* __restrict__ bout,
+                              R* __restrict__ xout) {
     int gx, gy;
     long long node;
     if (!node_of_thread(m, gx, gy, node)) return;
+    gather_init_at<R, P, NV>(m, EV, bout, xout, gx, gy, node);
+}
+
+
+// Richardson sweep x <- x + (b - sum EV) / m_i
+template <class R, int P, int NV>
+DEV void gather_sweep_at(MeshDev m, const R* __restrict__ EV, const R* __restrict__ b,
+                               R* __restrict__ x, int gx, int gy, long long node) {
     const NodeC<P> c = node_c<P>(m, gx, gy);
     R s[NV];
     gather_at<R, P, NV>(m, EV, c, s);
@@ -659,6 +680,16 @@ __global__ void k_gather_sweep(MeshDev m, const R* __restrict__ EV, const R* __r
         x[k] = x[k] + (b[k] - s[v]) * inv_mi;
     }
 }
+
+template <class R, int P, int NV>
+__global__ void k_gather_sweep(MeshDev m, const R* __restrict__ EV, const R* __restrict__ b,
+                               R* __restrict__ x) {
+    int gx, gy;
+    long long node;
+    if (!node_of_thread(m, gx, gy, node)) return;
+    gather_sweep_at<R, P, NV>(m, EV, b, x, gx, gy, node);
+}
+
 
 // runtime-degree candidate list (diagnostics only)
 struct NodeCands {
@@ -713,12 +744,10 @@ DEV NodeCands node_cands(const MeshDev& m, int gx, int gy) {
 // ER layout [(e*N2 + i)*NC + c].
 // ---------------------------------------------------------------------------
 template <class R, int P, class Ph>
-__global__ void k_res_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ g,
+DEV void res_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ g,
                          const double* __restrict__ gam, const double* __restrict__ nu,
-                         R* __restrict__ ER) {
+                         R* __restrict__ ER, int ex, int ey, int e) {
     constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2, NQ = Dim<P>::NQ;
-    int ex, ey, e;
-    if (!elem_of_thread(m, ex, ey, e)) return;
     const Tab<R>& T = TabSel<R>::t(P);
     const R h = PV<R>::h(m);
     R U[NC][N2];
@@ -904,6 +933,16 @@ __global__ void k_res_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R
     }
 }
 
+template <class R, int P, class Ph>
+__global__ void k_res_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ g,
+                         const double* __restrict__ gam, const double* __restrict__ nu,
+                         R* __restrict__ ER) {
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
+    res_at<R, P, Ph>(m, pr, u, g, gam, nu, ER, ex, ey, e);
+}
+
+
 // ---------------------------------------------------------------------------
 // k_update_ev: facet fluxes and flux limiter, ubar^e, f_i^e, beta_e and the
 // element increments of eq. (eq:SSPupdate),
@@ -921,16 +960,14 @@ DEV void split(double v, T& hi, T& lo) {
 }
 
 template <class R, int P, class Ph>
-__global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
+DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
                             const double* __restrict__ ue, const double* __restrict__ dte_a, const double* __restrict__ ubl,
                             const double* __restrict__ qcap, const double* __restrict__ fl_in,
                             const R* __restrict__ ER,
                             const double* __restrict__ dtp, R* __restrict__ EW,
                             double* __restrict__ ube_out, double* __restrict__ beta_out,
-                            unsigned long long* __restrict__ cnt) {
+                            unsigned long long* __restrict__ cnt, int ex, int ey, int e) {
     constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2;
-    int ex, ey, e;
-    if (!elem_of_thread(m, ex, ey, e)) return;
     const Tab<R>& T = TabSel<R>::t(P);
     const double h = m.h;
     const double me = m.me;
@@ -1151,6 +1188,20 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
                 thR * (((ubh[c] - U[c][i]) + ubo[c]) + (beta * F[c][i]) * inv_meR);
 }
 
+template <class R, int P, class Ph>
+__global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
+                            const double* __restrict__ ue, const double* __restrict__ dte_a, const double* __restrict__ ubl,
+                            const double* __restrict__ qcap, const double* __restrict__ fl_in,
+                            const R* __restrict__ ER,
+                            const double* __restrict__ dtp, R* __restrict__ EW,
+                            double* __restrict__ ube_out, double* __restrict__ beta_out,
+                            unsigned long long* __restrict__ cnt) {
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
+    update_at<R, P, Ph>(m, pr, u, ud, ue, dte_a, ubl, qcap, fl_in, ER, dtp, EW, ube_out, beta_out, cnt, ex, ey, e);
+}
+
+
 // ---------------------------------------------------------------------------
 // k_final: u_i^SSP = u_i + (sum_{e in E_i} increment_i^e) / |E_i| (m_i^e/m_i
 // = 1/|E_i| on a uniform mesh), SSP-RK combination a u^n + b u^SSP, the
@@ -1158,12 +1209,9 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
 // to the storage precision) or the positivity count (Euler), non-finite count.
 // ---------------------------------------------------------------------------
 template <class R, int P, int NC>
-__global__ void k_final(MeshDev m, ProbDev pr, const R* __restrict__ EW,
-                        const R* __restrict__ un, R* __restrict__ u, R a, R b,
-                        unsigned long long* __restrict__ cnt) {
-    int gx, gy;
-    long long node;
-    if (!node_of_thread(m, gx, gy, node)) return;
+DEV void final_at(MeshDev m, ProbDev pr, const R* __restrict__ EW,
+                        R* __restrict__ un, R* __restrict__ u, R a, R b,
+                        unsigned long long* __restrict__ cnt, int gx, int gy, long long node) {
     const NodeC<P> nc = node_c<P>(m, gx, gy);
     R s[NC];
     gather_at<R, P, NC>(m, EW, nc, s);
@@ -1172,8 +1220,14 @@ __global__ void k_final(MeshDev m, ProbDev pr, const R* __restrict__ EW,
     bool bad = false;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        R ufe = u[c * m.NN + node] + s[c] * inv_cnt;
-        out[c] = (a != R(0)) ? a * un[c * m.NN + node] + b * ufe : b * ufe;
+        const R uold = u[c * m.NN + node];
+        R ufe = uold + s[c] * inv_cnt;
+        if (a != R(0)) {
+            out[c] = a * un[c * m.NN + node] + b * ufe;
+        } else {
+            out[c] = b * ufe;
+            un[c * m.NN + node] = uold;  // first stage: keep u^n for the later stages
+        }
         bad |= !isfinite(out[c]);
     }
     if (bad) atomicAdd(&cnt[CNT_NONFINITE], 1ull);
@@ -1198,5 +1252,16 @@ __global__ void k_final(MeshDev m, ProbDev pr, const R* __restrict__ EW,
 #pragma unroll
     for (int c = 0; c < NC; ++c) u[c * m.NN + node] = out[c];
 }
+
+template <class R, int P, int NC>
+__global__ void k_final(MeshDev m, ProbDev pr, const R* __restrict__ EW,
+                        R* __restrict__ un, R* __restrict__ u, R a, R b,
+                        unsigned long long* __restrict__ cnt) {
+    int gx, gy;
+    long long node;
+    if (!node_of_thread(m, gx, gy, node)) return;
+    final_at<R, P, NC>(m, pr, EW, un, u, a, b, cnt, gx, gy, node);
+}
+
 
 }  // namespace cgl

@@ -102,7 +102,7 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
                                                         (const R*)B.ER, B.dt, (R*)B.EW, B.ube, B.beta,
                                                         B.cnt)));
     CGL_LAUNCH(prof, KID_FINAL, st,
-               (k_final<R, P, NC><<<gn, bn, 0, st>>>(m, pr, (const R*)B.EW, (const R*)B.un, u, R(a), R(b),
+               (k_final<R, P, NC><<<gn, bn, 0, st>>>(m, pr, (const R*)B.EW, (R*)B.un, u, R(a), R(b),
                                                     B.cnt)));
     return cudaGetLastError();
 }
@@ -147,5 +147,6 @@ cudaError_t upload_adv(const Tab<double>*, const Tab<float>*, const double*, con
 cudaError_t upload_burgers(const Tab<double>*, const Tab<float>*, const double*, const float*);
 cudaError_t upload_kpp(const Tab<double>*, const Tab<float>*, const double*, const float*);
 cudaError_t upload_euler(const Tab<double>*, const Tab<float>*, const double*, const float*);
+cudaError_t upload_batch(const Tab<double>*, const Tab<float>*, const double*, const float*);
 
 }  // namespace cgl

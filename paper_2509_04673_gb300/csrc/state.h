@@ -1,0 +1,36 @@
+// state.h — internal layout of the library's mesh and state objects
+// (shared by the C-ABI implementation and the batched launcher).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/cgl.h"
+#include "stage.cuh"
+
+struct cgl_mesh {
+    cgl_mesh_desc d;
+    cgl::MeshDev m;
+};
+
+struct cgl_state {
+    const cgl_mesh* mesh;
+    int nc, prec, device;
+    cudaStream_t st;
+    bool own_stream;
+    bool has_problem;
+    cgl_problem prob;
+    cgl::ProbDev pd;
+    cgl::StageFn stage;
+    cgl::Bufs B;
+    size_t rsz;  // bytes per bulk value
+    cudaGraphExec_t step_graph;
+    double* diag;       // device partials for diagnostics
+    std::vector<void*> allocs;
+};
+
+namespace cgl {
+// shared helpers of the C-ABI units
+cgl_status set_error(cgl_status st, const char* fmt, ...);
+}  // namespace cgl
