@@ -20,7 +20,8 @@ sys.path.insert(0, ROOT)
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="kpp",
-                    choices=["kpp", "advection", "euler_quadrants", "euler_blast"])
+                    choices=["kpp", "advection", "euler_quadrants", "euler_blast", "batched"])
+    ap.add_argument("--autotune", action="store_true", help="batched: tune tile lengths first")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--p", type=int, default=0, help="degree (0 = the workload's own)")
     ap.add_argument("--prec", type=int, default=1, help="0 FP64, 1 FP32-mixed")
@@ -30,6 +31,8 @@ def main():
     import inputs
     from paper_2509_04673_gb300 import build, cgl
     build.build()
+    if a.workload == "batched":
+        return run_batched(a)
     if a.workload == "kpp":
         mesh, prob, u0 = inputs.kpp_config(a.n, a.n, a.p or 2)
     elif a.workload == "advection":
@@ -56,6 +59,43 @@ def main():
     print(json.dumps(info))
     st.close()
     return 0 if info["violations"] == 0 else 1
+
+
+def run_batched(a):
+    """The 256-instance batch (uneven sizes 16..128, degrees 1..4, advection
+    or Burgers), FP32-mixed, one persistent launch per stage."""
+    import torch
+    import inputs
+    from paper_2509_04673_gb300 import build, cgl
+    build.build()
+    cases = inputs.batched_instances()
+    stream = torch.cuda.Stream()
+    states = []
+    for mesh, prob, u0 in cases:
+        st = cgl.State(cgl.Mesh(mesh), 1, cgl.FP32_MIXED, stream=stream.cuda_stream)
+        st.set_problem(prob)
+        st.set_state(u0)
+        st.set_time(0.0)
+        states.append(st)
+    b = cgl.Batch(states)
+    if a.autotune:
+        b.autotune(2)
+    b.step(1)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    b.step_async(a.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    viol = b.step(0)
+    ndof = sum(u0.size for _, _, u0 in cases)
+    ms = ev0.elapsed_time(ev1)
+    out = dict(workload="batched", instances=len(cases), n_dof=ndof, steps=a.steps, ms=ms,
+               dof_stage_per_s=ndof * 3 * a.steps / (ms * 1e-3), violations=viol, tiles=b.tiles(),
+               **b.info())
+    print(json.dumps(out))
+    return 0 if viol == 0 else 1
 
 
 if __name__ == "__main__":
