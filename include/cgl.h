@@ -264,6 +264,31 @@ cgl_status cgl_batch_load_tuning(cgl_batch *batch, const char *json_path);
    (CGL_ETIMEOUT) can be exercised without any fault. */
 cgl_status cgl_batch_debug(cgl_batch *batch, int32_t phantom_blocks, int64_t spin_limit);
 
+/* --- no-allocation entry point --------------------------------------------------- */
+
+/* Lumped gradient projection of a scalar FP64 field, g = M_L^-1 b with
+   b_i = sum_e int phi_i grad u_h (the first step of the g_h projection),
+   computed without allocating any memory. The paper has no counterpart:
+   this entry point exists for callers that cannot allocate device memory
+   while they run (host callbacks, allocator hooks, real-time loops,
+   embedders that only hand over fixed buffers).
+
+   u: device pointer, nny*nnx float64 coefficients ([gy][gx]) of the mesh.
+   g: device pointer, 2*nny*nnx float64 outputs, x-derivatives then
+      y-derivatives, same layout; owned and allocated by the caller.
+   stream: cudaStream_t or NULL; the call only enqueues work on it.
+
+   The element-vector scratch lives in a fixed device array of 2^21 float64
+   (16 MiB) that every GPU loading the library keeps until exit; meshes
+   with nx*ny*(p+1)^2 > 2^20 are rejected with CGL_EINVAL. The first call on
+   a device does a one-time set-up on that device (table upload, scratch
+   address lookup), so make it before any stream capture. All calls share
+   the scratch: calls that overlap on the GPU (on different streams, or from
+   different threads) race and must be serialised by the caller. No part of
+   the scratch needs to start at zero: every value read was written by the
+   same call. */
+cgl_status cgl_gradient_noalloc(const cgl_mesh *mesh, const double *u, double *g, void *stream);
+
 /* --- measurement ------------------------------------------------------------ */
 
 /* Name of kernel identifier id (0 <= id < 12), "" otherwise. */

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcgl.so")
-SOURCES = ["api.cu", "inst_adv.cu", "inst_burgers.cu", "inst_kpp.cu", "inst_euler.cu", "batch.cu"]
+SOURCES = ["api.cu", "inst_adv.cu", "inst_burgers.cu", "inst_kpp.cu", "inst_euler.cu", "batch.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

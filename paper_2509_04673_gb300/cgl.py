@@ -97,6 +97,7 @@ _PROTOS = [
     ("cgl_batch_autotune", C.c_int, [C.c_void_p, C.c_int32, C.c_char_p]),
     ("cgl_batch_load_tuning", C.c_int, [C.c_void_p, C.c_char_p]),
     ("cgl_batch_debug", C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    ("cgl_gradient_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 ]
 
 
@@ -325,3 +326,10 @@ class Batch:
 
     def debug(self, phantom_blocks, spin_limit):
         check(lib().cgl_batch_debug(self.h, int(phantom_blocks), int(spin_limit)))
+
+
+def gradient_noalloc(mesh: Mesh, u_dev_ptr: int, g_dev_ptr: int, stream=None):
+    """Lumped gradient projection into caller-owned device memory without any
+    allocation by the library (see cgl_gradient_noalloc in include/cgl.h)."""
+    check(lib().cgl_gradient_noalloc(mesh.h, C.c_void_p(u_dev_ptr), C.c_void_p(g_dev_ptr),
+                                     C.c_void_p(stream) if stream else None))

@@ -232,6 +232,14 @@ static const HostTables& host_tables() {
     return *H;
 }
 
+namespace cgl {
+// copy the host tables into the constant memory of the unit that owns `f`
+cudaError_t upload_host_tables(UploadFn f) {
+    const HostTables& H = host_tables();
+    return f(H.td, H.tf, H.a2d, H.a2f);
+}
+}  // namespace cgl
+
 extern "C" cgl_status cgl_debug_tables(int32_t p, double* out, size_t n, size_t* needed) {
     if (p < 1 || p > PMAX) return fail(CGL_EINVAL, "degree p=%d outside [1,%d]", p, PMAX);
     const int n1 = p + 1, nq = p + 2, n2 = n1 * n1;
