@@ -313,6 +313,7 @@ extern "C" cgl_status cgl_mesh_create(const cgl_mesh_desc* d, cgl_mesh** out) {
     m.me_f = (float)m.me;
     m.inv_me_f = (float)m.inv_me;
     m.h2_f = (float)(m.h * m.h);
+    m.h_over_n2_f = (float)m.h_over_n2;
     *out = M;
     return CGL_OK;
 }
@@ -433,9 +434,9 @@ extern "C" cgl_status cgl_state_create(const cgl_mesh* mesh, int32_t ncomp, int3
     struct A { void** p; size_t b; } list[] = {
         {&B.u, nc * NN * r},          {&B.un, nc * NN * r},        {&B.g, 2 * nc * NN * r},
         {&B.bg, 2 * nc * NN * r},     {&B.r, nc * NN * r},         {&B.ud, nc * NN * r},
-        {&B.EV, E * N2 * 2 * nc * r}, {&B.ER, E * N2 * nc * r},    {&B.EW, E * N2 * nc * r},     {(void**)&B.q, 2 * E * 8},
+        {&B.EV, E * N2 * 2 * nc * r}, {&B.ER, E * N2 * nc * r},    {&B.EW, E * N2 * nc * r},     {(void**)&B.q, 2 * E * r},
         {(void**)&B.ue, nc * E * 8},  {(void**)&B.fue, 2 * nc * E * 8}, {(void**)&B.lame, E * 8},
-        {(void**)&B.dte, 3 * E * 8},  {(void**)&B.fl, 4 * nc * E * 8},      {(void**)&B.ubl, nc * E * 8}, {(void**)&B.gam, E * 8},
+        {(void**)&B.dte, 3 * E * 8},  {(void**)&B.fl, 4 * nc * E * r},      {(void**)&B.ubl, nc * E * 8}, {(void**)&B.gam, E * 8},
         {(void**)&B.nu, E * 8},       {(void**)&B.ube, nc * E * 8}, {(void**)&B.beta, E * 8},
         {(void**)&B.cnt, CNT_N * 8},  {(void**)&B.dtbits, 8},      {(void**)&B.dt, 8},
         {(void**)&B.t, 8},            {(void**)&B.t_end, 8},       {(void**)&S->diag, 1024 * 12 * 8},
@@ -543,7 +544,10 @@ extern "C" cgl_status cgl_set_problem(cgl_state* S, const cgl_problem* p) {
     d.weno_eps_f = (float)d.weno_eps;
     d.gamma_eps_f = (float)d.gamma_eps;
     d.q_f = (float)d.q;
-    for (int c = 0; c < 4; ++c) d.ubc_f[c] = (float)d.ubc[c];
+    for (int c = 0; c < 4; ++c) {
+        d.ubc_f[c] = (float)d.ubc[c];
+        d.ubc_lo_f[c] = (float)(d.ubc[c] - (double)d.ubc_f[c]);
+    }
     d.lo32_f = (float)d.umin32;
     d.hi32_f = (float)d.umax32;
     d.lo_tol_f = (float)d.lo_tol;

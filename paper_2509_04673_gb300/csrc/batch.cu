@@ -33,7 +33,8 @@ struct InstDev {
     MeshDev m;
     ProbDev pr;
     float *u, *un, *g, *bg, *r, *ud, *EV, *ER, *EW;
-    double *ue, *dte, *ubl, *gam, *nu, *q, *fl, *ube, *beta;
+    double *ue, *dte, *ubl, *gam, *nu, *ube, *beta;
+    float *q, *fl;
     unsigned long long *cnt, *dtbits;
     double *dt, *t, *t_end;
     int p, phys;
@@ -375,8 +376,8 @@ extern "C" cgl_status cgl_batch_create(cgl_state* const* states, int32_t n, cgl_
         d.ubl = b.ubl;
         d.gam = b.gam;
         d.nu = b.nu;
-        d.q = b.q;
-        d.fl = b.fl;
+        d.q = (float*)b.q;
+        d.fl = (float*)b.fl;
         d.ube = b.ube;
         d.beta = b.beta;
         d.cnt = b.cnt;

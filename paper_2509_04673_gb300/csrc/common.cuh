@@ -31,7 +31,7 @@ struct MeshDev {
     // kernel divides by mesh constants): m_i^e = h^2/(p+1)^2, 1/m_i^e,
     // h/(p+1)^2, 1/h, 1/(p+1)^2, 1/(p+1)
     double me, inv_me, h_over_n2, inv_h, inv_n2, inv_n1;
-    float h_f, me_f, inv_me_f, h2_f;
+    float h_f, me_f, inv_me_f, h2_f, h_over_n2_f;
 };
 
 struct ProbDev {
@@ -44,7 +44,7 @@ struct ProbDev {
     // float copies for float kernels (a float64 -> float conversion runs on
     // GB300's narrow float64 pipe, so per-thread code never converts)
     float vx_f, vy_f, gam_f, w_lin_f, weno_eps_f, gamma_eps_f, q_f;
-    float ubc_f[4];
+    float ubc_f[4], ubc_lo_f[4];
     float lo32_f, hi32_f, lo_tol_f, hi_tol_f;
 };
 

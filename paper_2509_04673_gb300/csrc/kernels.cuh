@@ -266,16 +266,17 @@ template <class R, int P>
 DEV R qform(const R (&v)[Dim<P>::N2]) {
     constexpr int N2 = Dim<P>::N2;
     constexpr int off = A2_OFF[P];
+    // d = v - v_0 (d_0 = 0); A symmetric: s = sum_i d_i (A_ii d_i + 2 sum_{j>i} A_ij d_j)
     R d[N2];
 #pragma unroll
     for (int i = 0; i < N2; ++i) d[i] = v[i] - v[0];
     R s = R(0);
 #pragma unroll
-    for (int i = 0; i < N2; ++i) {
+    for (int i = 1; i < N2; ++i) {
         R t = R(0);
 #pragma unroll
-        for (int j = 0; j < N2; ++j) t += TabSel<R>::A2(off + i * N2 + j) * d[j];
-        s += d[i] * t;
+        for (int j = i + 1; j < N2; ++j) t += TabSel<R>::A2(off + i * N2 + j) * d[j];
+        s += d[i] * (TabSel<R>::A2(off + i * N2 + i) * d[i] + R(2) * t);
     }
     return s;
 }
@@ -378,6 +379,88 @@ DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
     return gam;
 }
 
+// scalar sensor with the four neighbour blocks already in registers (V[d]
+// holds the raw block of neighbour d when nb[d] >= 0); same arithmetic as
+// sensor() with NC = 1
+template <class R, int P>
+DEV R sensor_scalar(const ProbDev& pr, const R (&U)[Dim<P>::N2], const R (&V)[4][Dim<P>::N2],
+                    const int (&nb)[4]) {
+    constexpr int N2 = Dim<P>::N2;
+    const R wl = PV<R>::w_lin(pr), eps = PV<R>::weno_eps(pr), geps = PV<R>::gamma_eps(pr);
+    const bool r2 = (pr.r == 2.0);
+    const R rh = R(0.5 * pr.r);
+    int ne = 0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) ne += (nb[d] >= 0);
+    R U0[N2];
+#pragma unroll
+    for (int i = 0; i < N2; ++i) U0[i] = U[i] - U[0];
+    R sig0 = fmax(qform<R, P>(U0), R(0));
+    R wt[5];
+    wt[0] = (R(1) - R(ne) * wl) / ((r2 ? sig0 : pow(sig0, rh)) + eps);
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        wt[d + 1] = R(0);
+        if (nb[d] >= 0) {
+            R Vc[N2], W[N2];
+#pragma unroll
+            for (int i = 0; i < N2; ++i) Vc[i] = V[d][i] - V[d][0];
+            continue_nb<R, P>(d, Vc, W);
+            R sg = fmax(qform<R, P>(W), R(0));
+            wt[d + 1] = wl / ((r2 ? sg : pow(sg, rh)) + eps);
+        }
+    }
+    R tot = (((wt[0] + wt[1]) + wt[2]) + wt[3]) + wt[4];
+    R Dl[N2];
+#pragma unroll
+    for (int i = 0; i < N2; ++i) Dl[i] = R(0);
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        if (nb[d] >= 0) {
+            R Vc[N2], W[N2];
+#pragma unroll
+            for (int i = 0; i < N2; ++i) Vc[i] = V[d][i] - V[d][0];
+            continue_nb<R, P>(d, Vc, W);
+            R wd = wt[d + 1] / tot;
+#pragma unroll
+            for (int i = 0; i < N2; ++i) Dl[i] += wd * (U0[i] - W[i]);
+        }
+    }
+    R num = sqrt(fmax(qform<R, P>(Dl), R(0)));
+    R den = sqrt(sig0);
+    R ratio = num / (den + geps);
+    return R(1) - (pr.q == 1.0 ? fmin(R(1), ratio) : pow(fmin(R(1), ratio), PV<R>::q(pr)));
+}
+
+// float-float mean of N floats: compensated (Neumaier) sum, then a division
+// by N whose remainder is taken exactly with an FMA; hi + lo carries about
+// 1e-14 relative accuracy without float64 arithmetic
+template <int N>
+DEV void ff_mean(const float (&v)[N], float& hi, float& lo) {
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        float t = s + v[i];
+        c += (fabsf(s) >= fabsf(v[i])) ? ((s - t) + v[i]) : ((v[i] - t) + s);
+        s = t;
+    }
+    const float h = s + c;
+    const float l = c - (h - s);
+    const float k = 1.0f / N;
+    const float q = h * k;
+    const float r = fmaf(-q, (float)N, h);
+    hi = q;
+    lo = (r + l) * k;
+}
+
+// (ah + al) - (bh + bl) rounded to float (TwoSum on the high parts)
+DEV float ff_diff(float ah, float al, float bh, float bl) {
+    const float s = ah - bh;
+    const float bb = s - ah;
+    const float err = (ah - (s - bb)) + (-bh - bb);
+    return s + (err + (al - bl));
+}
+
 // ---------------------------------------------------------------------------
 // k_pre: dt_e, ubar^{e,L}, gamma_e, nu_e
 // ---------------------------------------------------------------------------
@@ -413,12 +496,159 @@ DEV void block_min_to(double v, unsigned long long* bits) {
 // gamma_e (eqs. (WENO:alpha), (WENO:norm)), nu_e, the element vectors of the
 // g_h right-hand side, and (stage 1) the block minimum of dt_e.
 // ---------------------------------------------------------------------------
+// FP32-mixed form of pre_at: cell means as float-float pairs, low-order
+// facet fluxes formed in float (their flux part is float-accurate anyway,
+// the jump term comes from float-float differences), float facet fluxes and
+// flux-limiter capacities (rounded toward zero, so they stay admissible)
+// stored for the update pass; float64 for u^e, the speed-sum reciprocal,
+// dt_e, ubar^{e,L} and the bound gaps.
+template <int P, class Ph>
+DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __restrict__ u,
+                        double* __restrict__ ue_out, double* __restrict__ dte_out,
+                        double* __restrict__ ubl_out, double* __restrict__ gam_out,
+                        double* __restrict__ nu_out, float* __restrict__ q_out,
+                        float* __restrict__ fl_out, float* __restrict__ EV, int ex, int ey, int e) {
+    constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
+    int nb[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
+    float U[NC][N2];
+    load_block<float, P, NC>(u, m, ex, ey, U);
+    float uh[NC], ul[NC], fxs[NC], fys[NC];
+    double ued[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        ff_mean<N2>(U[c], uh[c], ul[c]);
+        ued[c] = (double)uh[c] + (double)ul[c];
+        ue_out[c * m.E + e] = ued[c];
+    }
+    Ph::template flux<float>(uh, fxs, fys, pr);
+    // neighbours: means, fluxes (and, for scalars, the blocks for the sensor)
+    float oh[4][NC], ol[4][NC], ofx[4][NC], ofy[4][NC];
+    float V1[4][N2];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        if (nb[d] >= 0) {
+            const int jx = nb[d] % m.nx, jy = nb[d] / m.nx;
+            float B[NC][N2];
+            load_block<float, P, NC>(u, m, jx, jy, B);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ff_mean<N2>(B[c], oh[d][c], ol[d][c]);
+            Ph::template flux<float>(oh[d], ofx[d], ofy[d], pr);
+            if (NC == 1) {
+#pragma unroll
+                for (int i = 0; i < N2; ++i) V1[d][i] = B[0][i];
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) oh[d][c] = ol[d][c] = ofx[d][c] = ofy[d][c] = 0.f;
+            if (NC == 1) {
+#pragma unroll
+                for (int i = 0; i < N2; ++i) V1[d][i] = 0.f;
+            }
+        }
+    }
+    // canonical facet fluxes F(u^L, u^R; n), n = +x (W, E) or +y (S, N)
+    const float inflate = 1.0f + 0x1p-20f;
+    float lam[4], F[4][NC];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const bool xf = d < 2;
+        const float cnx = xf ? 1.f : 0.f, cny = xf ? 0.f : 1.f;
+        const bool self_is_L = (d == 1 || d == 3);
+        if (nb[d] >= 0) {
+            const float* Lh = self_is_L ? uh : oh[d];
+            const float* Ll = self_is_L ? ul : ol[d];
+            const float* Rh = self_is_L ? oh[d] : uh;
+            const float* Rl = self_is_L ? ol[d] : ul;
+            const float* fL = xf ? (self_is_L ? fxs : ofx[d]) : (self_is_L ? fys : ofy[d]);
+            const float* fR = xf ? (self_is_L ? ofx[d] : fxs) : (self_is_L ? ofy[d] : fys);
+            const float l = Ph::template max_speed<float>(Lh, Rh, cnx, cny, pr) * inflate;
+            lam[d] = l;
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                F[d][c] = 0.5f * (fL[c] + fR[c]) - 0.5f * l * ff_diff(Rh[c], Rl[c], Lh[c], Ll[c]);
+        } else {
+            const int bc = xf ? m.bc_x : m.bc_y;
+            const bool fixed = bc == BC_FIXED;
+            const float sg = self_is_L ? 1.f : -1.f;
+            float xh[NC], xl[NC], xfx[NC], xfy[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                xh[c] = fixed ? pr.ubc_f[c] : uh[c];
+                xl[c] = fixed ? pr.ubc_lo_f[c] : ul[c];
+            }
+            Ph::template flux<float>(xh, xfx, xfy, pr);
+            const float l = Ph::template max_speed<float>(uh, xh, sg * cnx, sg * cny, pr) * inflate;
+            lam[d] = l;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const float ns = sg * (xf ? fxs[c] : fys[c]);
+                const float nx = sg * (xf ? xfx[c] : xfy[c]);
+                const float Fo = 0.5f * (ns + nx) - 0.5f * l * ff_diff(xh[c], xl[c], uh[c], ul[c]);
+                F[d][c] = sg * Fo;
+            }
+        }
+    }
+    float sf = ((lam[0] + lam[1]) + lam[2]) + lam[3];
+    sf = fmaxf(sf, (float)pr.lambda_floor);
+    const double s = (double)sf;
+    const double rs = 1.0 / s;
+    const double dte = m.h * rs;
+    dte_out[e] = dte;
+    dte_out[m.E + e] = rs;
+    dte_out[2 * m.E + e] = s * m.inv_h;
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) fl_out[((long long)e * 4 + d) * NC + c] = F[d][c];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const double os = (((double)F[1][c] - (double)F[0][c]) + (double)F[3][c]) - (double)F[2][c];
+        const double bl = ued[c] - rs * os;
+        ubl_out[c * m.E + e] = bl;
+        if (NC == 1) {
+            q_out[e] = __double2float_rz(fmax(0.0, (0.25 * s) * (pr.umax - bl)));
+            q_out[m.E + e] = __double2float_rz(fmin(0.0, (0.25 * s) * (pr.umin - bl)));
+        }
+    }
+    float gam;
+    if (pr.mode == MODE_WENO || pr.mode == MODE_WENO_L) {
+        if (NC == 1) {
+            float U1[N2];
+#pragma unroll
+            for (int i = 0; i < N2; ++i) U1[i] = U[0][i];
+            gam = sensor_scalar<float, P>(pr, U1, V1, nb);
+        } else {
+            gam = sensor<float, P, Ph>(m, pr, u, U, nb);
+        }
+    } else {
+        gam = (pr.mode == MODE_HO) ? 1.f : 0.f;
+    }
+    gam_out[e] = (double)gam;
+    float lm = 0.f;
+#pragma unroll
+    for (int i = 0; i < N2; ++i) {
+        float ui[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ui[c] = U[c][i];
+        lm = fmaxf(lm, Ph::template node_speed<float>(ui, pr));
+    }
+    nu_out[e] = (double)(lm * (m.h_f * (0.5f / P)));
+    if (EV) grad_vectors<float, P, NC>(U, m.h_f, e, EV);
+    return dte;
+}
+
 template <class R, int P, class Ph>
 DEV double pre_at(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __restrict__ ue_out,
                   double* __restrict__ dte_out, double* __restrict__ ubl_out,
                   double* __restrict__ gam_out, double* __restrict__ nu_out,
-                  double* __restrict__ q_out, double* __restrict__ fl_out, R* __restrict__ EV,
+                  R* __restrict__ q_out, R* __restrict__ fl_out, R* __restrict__ EV,
                   int ex, int ey, int e) {
+    if constexpr (sizeof(R) == 4) {
+        return pre_at_mixed<P, Ph>(m, pr, u, ue_out, dte_out, ubl_out, gam_out, nu_out, q_out, fl_out, EV,
+                                   ex, ey, e);
+    } else {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
     double dte;
     {
@@ -500,13 +730,14 @@ DEV double pre_at(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __rest
         if (EV) grad_vectors<R, P, NC>(U, PV<R>::h(m), e, EV);
     }
     return dte;
+    }
 }
 
 template <class R, int P, class Ph>
 __global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __restrict__ ue_out,
                       double* __restrict__ dte_out, double* __restrict__ ubl_out,
                       double* __restrict__ gam_out, double* __restrict__ nu_out,
-                      double* __restrict__ q_out, double* __restrict__ fl_out, R* __restrict__ EV,
+                      R* __restrict__ q_out, R* __restrict__ fl_out, R* __restrict__ EV,
                       unsigned long long* __restrict__ dtbits) {
     int ex, ey, e;
     double dte = __longlong_as_double(0x7ff0000000000000LL);
@@ -962,7 +1193,7 @@ DEV void split(double v, T& hi, T& lo) {
 template <class R, int P, class Ph>
 DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
                             const double* __restrict__ ue, const double* __restrict__ dte_a, const double* __restrict__ ubl,
-                            const double* __restrict__ qcap, const double* __restrict__ fl_in,
+                            const R* __restrict__ qcap, const R* __restrict__ fl_in,
                             const R* __restrict__ ER,
                             const double* __restrict__ dtp, R* __restrict__ EW,
                             double* __restrict__ ube_out, double* __restrict__ beta_out,
@@ -990,6 +1221,7 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
     // f(u_j).n (or of F(u_j, u_hat; n) on a FIXED boundary), summed along the
     // face in a fixed order so both cells of a facet get the same value
     double FH[4][NC];
+    R FHr[4][NC];
     const bool need_fh = !(pr.mode == MODE_LO && pr.fl == FL_LOW);
     if (need_fh) {
 #pragma unroll
@@ -1023,8 +1255,9 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
             }
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                double a = (double)(acc[c] / R(N1));
-                FH[d][c] = fixed_b ? (double)sg * a : a;
+                const R a = acc[c] / R(N1);
+                FHr[d][c] = fixed_b ? sg * a : a;
+                FH[d][c] = (double)FHr[d][c];
             }
         }
     }
@@ -1040,23 +1273,23 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
             ubec[c] = uec[c] - rs * os;
         }
     } else {
-        double FL[4][NC];
+        R FLr[4][NC];
 #pragma unroll
         for (int d = 0; d < 4; ++d)
 #pragma unroll
-            for (int c = 0; c < NC; ++c) FL[d][c] = fl_in[((long long)e * 4 + d) * NC + c];
+            for (int c = 0; c < NC; ++c) FLr[d][c] = fl_in[((long long)e * 4 + d) * NC + c];
         double FB[4][NC];
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
             const bool self_is_L = (d == 1 || d == 3);
-            double fA[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) fA[c] = FL[d][c] - FH[d][c];
             const int Lc = self_is_L ? e : nb[d];
             const int Rc = self_is_L ? nb[d] : e;
             if (Ph::NC == 1) {
-                const double inf = __longlong_as_double(0x7ff0000000000000LL);
-                double fmaxv = inf, fminv = -inf;
+                // eq. (fAlim) with the capacities of both cells (R-typed; in the
+                // mixed form they were rounded toward zero, so still admissible)
+                const R fA = FLr[d][0] - FHr[d][0];
+                const R inf = R(__int_as_float(0x7f800000));
+                R fmaxv = inf, fminv = -inf;
                 if (Lc >= 0) {
                     fmaxv = fmin(fmaxv, qcap[Lc]);
                     fminv = fmax(fminv, qcap[m.E + Lc]);
@@ -1065,8 +1298,11 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
                     fmaxv = fmin(fmaxv, -qcap[m.E + Rc]);
                     fminv = fmax(fminv, -qcap[Rc]);
                 }
-                FB[d][0] = (fA[0] >= 0.0) ? fmin(fA[0], fmaxv) : fmax(fA[0], fminv);
+                FB[d][0] = (double)((fA >= R(0)) ? fmin(fA, fmaxv) : fmax(fA, fminv));
             } else {
+                double fA[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) fA[c] = (double)FLr[d][c] - FH[d][c];
                 double alpha = 1.0;
                 if (Lc >= 0) {
                     double ub[NC];
@@ -1114,6 +1350,7 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
     }
     // f_i^e, eq. (aec) with eq. (aecb) folded into the residual
     const R meR = PV<R>::me(m), h2 = PV<R>::h2(m), dteR = R(dte), inv_meR = PV<R>::inv_me(m);
+    const R h_over_n2R = (sizeof(R) == 4) ? R(m.h_over_n2_f) : R(m.h_over_n2);
     R F[NC][N2];
 #pragma unroll 1
     for (int c = 0; c < NC; ++c) {
@@ -1133,8 +1370,7 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
                 for (int k = 0; k < N1; ++k) s += T.M[a][k] * UD[d * N1 + k];
                 Y[d][a] = s;
             }
-        const double fhs = ((FH[1][c] - FH[0][c]) + FH[3][c]) - FH[2][c];
-        const R fh_term = R(m.h_over_n2 * fhs);
+        const R fh_term = h_over_n2R * (((FHr[1][c] - FHr[0][c]) + FHr[3][c]) - FHr[2][c]);
         R ueh, uel;
         split<R>(uec[c], ueh, uel);
 #pragma unroll
@@ -1191,7 +1427,7 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
 template <class R, int P, class Ph>
 __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
                             const double* __restrict__ ue, const double* __restrict__ dte_a, const double* __restrict__ ubl,
-                            const double* __restrict__ qcap, const double* __restrict__ fl_in,
+                            const R* __restrict__ qcap, const R* __restrict__ fl_in,
                             const R* __restrict__ ER,
                             const double* __restrict__ dtp, R* __restrict__ EW,
                             double* __restrict__ ube_out, double* __restrict__ beta_out,

@@ -17,8 +17,8 @@ struct Bufs {
     void* EV;     // element vectors  [E][N2][2NC] (R)
     void* ER;     // element residual [E][N2][NC]  (R)
     void* EW;     // SSP increments   [E][N2][NC]  (R)
-    double* q;    // flux-limiter capacities [2][E] (scalar)
-    double* fl;   // low-order facet fluxes [E][4][NC]
+    void* q;      // flux-limiter capacities [2][E] (scalar)  (R)
+    void* fl;     // low-order facet fluxes [E][4][NC]         (R)
     double *ue, *fue, *lame, *dte, *ubl, *gam, *nu, *ube, *beta;
     unsigned long long* cnt;     // CNT_N counters
     unsigned long long* dtbits;  // min dt_e as bits
@@ -74,7 +74,7 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
     R* EV = (R*)B.EV;
     const bool need_g = !dt_only && pr.mode != MODE_LO;
     CGL_LAUNCH(prof, KID_PRE, st,
-               (k_pre<R, P, Ph><<<ge, be, 0, st>>>(m, pr, u, B.ue, B.dte, B.ubl, B.gam, B.nu, B.q, B.fl,
+               (k_pre<R, P, Ph><<<ge, be, 0, st>>>(m, pr, u, B.ue, B.dte, B.ubl, B.gam, B.nu, (R*)B.q, (R*)B.fl,
                                                   need_g ? EV : nullptr, first ? B.dtbits : nullptr)));
     if (first)
         CGL_LAUNCH(prof, KID_DT, st, (k_dt_final<<<1, 1, 0, st>>>(B.dtbits, pr.cfl, B.t, B.t_end, B.dt)));
@@ -98,7 +98,7 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
         }
     }
     CGL_LAUNCH(prof, KID_UPDATE, st,
-               (k_update_ev<R, P, Ph><<<ge, be, 0, st>>>(m, pr, u, (const R*)B.ud, B.ue, B.dte, B.ubl, B.q, B.fl,
+               (k_update_ev<R, P, Ph><<<ge, be, 0, st>>>(m, pr, u, (const R*)B.ud, B.ue, B.dte, B.ubl, (const R*)B.q, (const R*)B.fl,
                                                         (const R*)B.ER, B.dt, (R*)B.EW, B.ube, B.beta,
                                                         B.cnt)));
     CGL_LAUNCH(prof, KID_FINAL, st,
