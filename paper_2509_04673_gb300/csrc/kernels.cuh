@@ -435,30 +435,40 @@ DEV R sensor_scalar(const ProbDev& pr, const R (&U)[Dim<P>::N2], const R (&V)[4]
 // float-float mean of N floats: compensated (Neumaier) sum, then a division
 // by N whose remainder is taken exactly with an FMA; hi + lo carries about
 // 1e-14 relative accuracy without float64 arithmetic
+// (explicit round-to-nearest intrinsics throughout: the compiler never
+// contracts or reorders them, so every kernel that inlines these helpers
+// computes the same bits)
 template <int N>
 DEV void ff_mean(const float (&v)[N], float& hi, float& lo) {
     float s = 0.f, c = 0.f;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        float t = s + v[i];
-        c += (fabsf(s) >= fabsf(v[i])) ? ((s - t) + v[i]) : ((v[i] - t) + s);
+        const float t = __fadd_rn(s, v[i]);
+        const float e = (fabsf(s) >= fabsf(v[i])) ? __fadd_rn(__fsub_rn(s, t), v[i])
+                                                   : __fadd_rn(__fsub_rn(v[i], t), s);
+        c = __fadd_rn(c, e);
         s = t;
     }
-    const float h = s + c;
-    const float l = c - (h - s);
+    const float h = __fadd_rn(s, c);
+    const float l = __fsub_rn(c, __fsub_rn(h, s));
     const float k = 1.0f / N;
-    const float q = h * k;
-    const float r = fmaf(-q, (float)N, h);
+    const float q = __fmul_rn(h, k);
+    const float r = __fmaf_rn(-q, (float)N, h);
     hi = q;
-    lo = (r + l) * k;
+    lo = __fmul_rn(__fadd_rn(r, l), k);
 }
 
 // (ah + al) - (bh + bl) rounded to float (TwoSum on the high parts)
 DEV float ff_diff(float ah, float al, float bh, float bl) {
-    const float s = ah - bh;
-    const float bb = s - ah;
-    const float err = (ah - (s - bb)) + (-bh - bb);
-    return s + (err + (al - bl));
+    const float s = __fsub_rn(ah, bh);
+    const float bb = __fsub_rn(s, ah);
+    const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(-bh, bb));
+    return __fadd_rn(s, __fadd_rn(err, __fsub_rn(al, bl)));
+}
+
+// LLF flux value 0.5 (nL + nR) - 0.5 lambda jump, with a fixed evaluation order
+DEV float llf_value(float nL, float nR, float lam, float jump) {
+    return __fmaf_rn(__fmul_rn(-0.5f, lam), jump, __fmul_rn(0.5f, __fadd_rn(nL, nR)));
 }
 
 // ---------------------------------------------------------------------------
@@ -563,11 +573,11 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
             const float* Rl = self_is_L ? ol[d] : ul;
             const float* fL = xf ? (self_is_L ? fxs : ofx[d]) : (self_is_L ? fys : ofy[d]);
             const float* fR = xf ? (self_is_L ? ofx[d] : fxs) : (self_is_L ? ofy[d] : fys);
-            const float l = Ph::template max_speed<float>(Lh, Rh, cnx, cny, pr) * inflate;
+            const float l = __fmul_rn(Ph::template max_speed<float>(Lh, Rh, cnx, cny, pr), inflate);
             lam[d] = l;
 #pragma unroll
             for (int c = 0; c < NC; ++c)
-                F[d][c] = 0.5f * (fL[c] + fR[c]) - 0.5f * l * ff_diff(Rh[c], Rl[c], Lh[c], Ll[c]);
+                F[d][c] = llf_value(fL[c], fR[c], l, ff_diff(Rh[c], Rl[c], Lh[c], Ll[c]));
         } else {
             const int bc = xf ? m.bc_x : m.bc_y;
             const bool fixed = bc == BC_FIXED;
@@ -579,18 +589,18 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
                 xl[c] = fixed ? pr.ubc_lo_f[c] : ul[c];
             }
             Ph::template flux<float>(xh, xfx, xfy, pr);
-            const float l = Ph::template max_speed<float>(uh, xh, sg * cnx, sg * cny, pr) * inflate;
+            const float l = __fmul_rn(Ph::template max_speed<float>(uh, xh, sg * cnx, sg * cny, pr), inflate);
             lam[d] = l;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const float ns = sg * (xf ? fxs[c] : fys[c]);
                 const float nx = sg * (xf ? xfx[c] : xfy[c]);
-                const float Fo = 0.5f * (ns + nx) - 0.5f * l * ff_diff(xh[c], xl[c], uh[c], ul[c]);
+                const float Fo = llf_value(ns, nx, l, ff_diff(xh[c], xl[c], uh[c], ul[c]));
                 F[d][c] = sg * Fo;
             }
         }
     }
-    float sf = ((lam[0] + lam[1]) + lam[2]) + lam[3];
+    float sf = __fadd_rn(__fadd_rn(__fadd_rn(lam[0], lam[1]), lam[2]), lam[3]);
     sf = fmaxf(sf, (float)pr.lambda_floor);
     const double s = (double)sf;
     const double rs = 1.0 / s;
