@@ -168,22 +168,24 @@ def algorithmic_bytes(kernel, mesh, nc, rsz, k_g, k_u):
     d = 8
     b = {
         # u (own and neighbour blocks read once) -> u^e, dt_e (3), ubar^{e,L},
-        # gamma, nu, Q (2), f^L (4 nc), gradient element vectors
-        "k_pre": nc * NN * rsz + (nc + 3 + nc + 2 + 2 + 4 * nc) * E * d + E * N2 * 2 * nc * rsz,
+        # gamma, nu (float64), Q (2), f^L (4 nc) (bulk precision)
+        "k_pre": nc * NN * rsz + (nc + 3 + nc + 2) * E * d + (2 + 4 * nc) * E * rsz,
         # u, g (2 nc), gamma, nu -> element residual
         "k_res_ev": 3 * nc * NN * rsz + 2 * E * d + E * N2 * nc * rsz,
-        # u, udot, u^e, dt_e (3), ubar^{e,L}, Q (2), f^L (4 nc), element residual
-        # -> increments, ubar^e, beta
-        "k_update_ev": 2 * nc * NN * rsz + (nc + 3 + nc + 2 + 4 * nc) * E * d + E * N2 * nc * rsz
-                       + E * N2 * nc * rsz + (nc + 1) * E * d,
+        # u, udot, u^e, dt_e (3), ubar^{e,L} (float64), Q (2), f^L (4 nc),
+        # element residual (bulk) -> increments (bulk), ubar^e, beta (float64)
+        "k_update_ev": 2 * nc * NN * rsz + (nc + 3 + nc) * E * d + (2 + 4 * nc) * E * rsz
+                       + E * N2 * nc * rsz + E * N2 * nc * rsz + (nc + 1) * E * d,
         # increments, u^n, u -> u
         "k_final": E * N2 * nc * rsz + 3 * nc * NN * rsz,
     }
-    nv_avg = (2 * nc + nc) / 2
-    b["k_gather_init"] = E * N2 * nv_avg * rsz + 2 * nv_avg * NN * rsz
+    # u -> b and the lumped g_h (2 nc fields each)
+    b["k_grad_rhs"] = nc * NN * rsz + 2 * 2 * nc * NN * rsz
+    # element residuals -> r and the lumped udot
+    b["k_gather_init"] = E * N2 * nc * rsz + 2 * nc * NN * rsz
+    # x_in, b -> x_out, averaged over the g_h (2 nc) and udot (nc) sweeps
     nvm = (2 * nc * k_g + nc * k_u) / max(1, k_g + k_u)
-    b["k_mass_ev"] = nvm * NN * rsz + E * N2 * nvm * rsz
-    b["k_gather_sweep"] = E * N2 * nvm * rsz + 3 * nvm * NN * rsz
+    b["k_mass_sweep"] = 3 * nvm * NN * rsz
     return b.get(kernel)
 
 

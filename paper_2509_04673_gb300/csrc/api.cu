@@ -433,8 +433,9 @@ extern "C" cgl_status cgl_state_create(const cgl_mesh* mesh, int32_t ncomp, int3
     Bufs& B = S->B;
     struct A { void** p; size_t b; } list[] = {
         {&B.u, nc * NN * r},          {&B.un, nc * NN * r},        {&B.g, 2 * nc * NN * r},
+        {&B.g2, 2 * nc * NN * r},     {&B.ud2, nc * NN * r},
         {&B.bg, 2 * nc * NN * r},     {&B.r, nc * NN * r},         {&B.ud, nc * NN * r},
-        {&B.EV, E * N2 * 2 * nc * r}, {&B.ER, E * N2 * nc * r},    {&B.EW, E * N2 * nc * r},     {(void**)&B.q, 2 * E * r},
+        {&B.EV, 16},                  {&B.ER, E * N2 * nc * r},    {&B.EW, E * N2 * nc * r},     {(void**)&B.q, 2 * E * r},
         {(void**)&B.ue, nc * E * 8},  {(void**)&B.fue, 2 * nc * E * 8}, {(void**)&B.lame, E * 8},
         {(void**)&B.dte, 3 * E * 8},  {(void**)&B.fl, 4 * nc * E * r},      {(void**)&B.ubl, nc * E * 8}, {(void**)&B.gam, E * 8},
         {(void**)&B.nu, E * 8},       {(void**)&B.ube, nc * E * 8}, {(void**)&B.beta, E * 8},
@@ -629,6 +630,8 @@ extern "C" cgl_status cgl_get_field(cgl_state* S, int32_t field, double* host, s
     const void* src = nullptr;
     size_t cnt = 0;
     bool bulk = false;
+    const void* gfin = (S->prob.k_g % 2 == 0) ? S->B.g : S->B.g2;
+    const void* udfin = (S->prob.k_u % 2 == 0) ? S->B.ud : S->B.ud2;
     switch (field) {
         case CGL_FIELD_UE: src = S->B.ue; cnt = nc * E; break;
         case CGL_FIELD_DTE: src = S->B.dte; cnt = E; break;
@@ -637,10 +640,11 @@ extern "C" cgl_status cgl_get_field(cgl_state* S, int32_t field, double* host, s
         case CGL_FIELD_GAMMA: src = S->B.gam; cnt = E; break;
         case CGL_FIELD_NU: src = S->B.nu; cnt = E; break;
         case CGL_FIELD_BETA: src = S->B.beta; cnt = E; break;
-        case CGL_FIELD_GX: src = S->B.g; cnt = nc * NN; bulk = true; break;
-        case CGL_FIELD_GY: src = (const char*)S->B.g + nc * NN * S->rsz; cnt = nc * NN; bulk = true; break;
+        // the Richardson sweeps ping-pong between two buffers
+        case CGL_FIELD_GX: src = gfin; cnt = nc * NN; bulk = true; break;
+        case CGL_FIELD_GY: src = (const char*)gfin + nc * NN * S->rsz; cnt = nc * NN; bulk = true; break;
         case CGL_FIELD_R: src = S->B.r; cnt = nc * NN; bulk = true; break;
-        case CGL_FIELD_UDOT: src = S->B.ud; cnt = nc * NN; bulk = true; break;
+        case CGL_FIELD_UDOT: src = udfin; cnt = nc * NN; bulk = true; break;
         default: return fail(CGL_EINVAL, "unknown field %d", field);
     }
     if (n != cnt) return fail(CGL_EINVAL, "field %d has %zu values, got %zu", field, cnt, n);
@@ -830,7 +834,7 @@ extern "C" cgl_status cgl_time_step(cgl_state* S, double* dt) {
 // per-kernel timing
 // ---------------------------------------------------------------------------
 static const char* const KNAMES[KID_COUNT] = {
-    "k_avg(merged)", "k_pre", "k_dt", "k_grad_ev(merged)", "k_gather_init", "k_mass_ev", "k_gather_sweep",
+    "k_avg(merged)", "k_pre", "k_dt", "k_grad_rhs", "k_gather_init", "k_mass_ev(unused)", "k_mass_sweep",
     "k_res_ev", "k_update_ev", "k_final", "k_t_advance", "copy_u_un"};
 
 // fixed-length delay (bounded both by a cycle count and by an iteration cap;
@@ -898,7 +902,7 @@ extern "C" cgl_status cgl_launches_per_step(cgl_state* S, int64_t* kernels) {
     if (!S || !kernels) return fail(CGL_EINVAL, "null argument");
     if (!S->has_problem) return fail(CGL_EINVAL, "cgl_set_problem first");
     const int lo = S->prob.mode == CGL_MODE_LO;
-    int64_t per_stage = 1 + 2 + (lo ? 0 : 3 + 2 * (S->prob.k_g + S->prob.k_u));
+    int64_t per_stage = 1 + 2 + (lo ? 0 : 3 + (S->prob.k_g + S->prob.k_u));
     *kernels = 3 * per_stage + 1 + 1;  // + dt finalisation (1) + time advance (1)
     return CGL_OK;
 }

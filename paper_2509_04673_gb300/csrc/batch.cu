@@ -32,7 +32,7 @@ namespace cgl {
 struct InstDev {
     MeshDev m;
     ProbDev pr;
-    float *u, *un, *g, *bg, *r, *ud, *EV, *ER, *EW;
+    float *u, *un, *g, *g2, *bg, *r, *ud, *ud2, *ER, *EW;
     double *ue, *dte, *ubl, *gam, *nu, *ube, *beta;
     float *q, *fl;
     unsigned long long *cnt, *dtbits;
@@ -51,8 +51,8 @@ struct BatchSync {
     int phantom;  // extra arrivals a barrier waits for (0; > 0 only to test the timeout)
 };
 
-enum { PH_PRE = 0, PH_MASS_G, PH_RES, PH_MASS_U, PH_UPDATE };
-enum { PH_GATHER_G = 0, PH_SWEEP_G, PH_GATHER_R, PH_SWEEP_U, PH_FINAL };
+enum { PH_PRE = 0, PH_RES, PH_UPDATE };
+enum { PH_GRAD = 0, PH_SWEEP_G, PH_GATHER_R, PH_SWEEP_U, PH_FINAL };
 
 constexpr int BT = 128;  // threads per block of the persistent grid
 
@@ -89,60 +89,71 @@ DEV bool grid_sync(BatchSync* s, long long limit) {
     return ok != 0;
 }
 
+// g_h and udot after k Richardson sweeps live in the first buffer for even k
+DEV const float* g_final(const InstDev& D, int kg) { return (kg & 1) ? D.g2 : D.g; }
+DEV const float* ud_final(const InstDev& D, int ku) { return (ku & 1) ? D.ud2 : D.ud; }
+
 template <int P, class Ph>
-DEV void elem_phase(int phase, const InstDev& D, int ex, int ey, int e, double& dte) {
+DEV void elem_phase(int phase, const InstDev& D, int ex, int ey, int e, double& dte, int kg, int ku) {
     switch (phase) {
         case PH_PRE:
-            dte = pre_at<float, P, Ph>(D.m, D.pr, D.u, D.ue, D.dte, D.ubl, D.gam, D.nu, D.q, D.fl,
-                                       D.pr.mode != MODE_LO ? D.EV : nullptr, ex, ey, e);
+            dte = pre_at<float, P, Ph>(D.m, D.pr, D.u, D.ue, D.dte, D.ubl, D.gam, D.nu, D.q, D.fl, nullptr, ex,
+                                       ey, e);
             break;
-        case PH_MASS_G: mass_at<float, P, 2>(D.m, D.g, D.EV, ex, ey, e); break;
-        case PH_RES: res_at<float, P, Ph>(D.m, D.pr, D.u, D.g, D.gam, D.nu, D.ER, ex, ey, e); break;
-        case PH_MASS_U: mass_at<float, P, 1>(D.m, D.ud, D.EV, ex, ey, e); break;
+        case PH_RES:
+            res_at<float, P, Ph>(D.m, D.pr, D.u, g_final(D, kg), D.gam, D.nu, D.ER, ex, ey, e);
+            break;
         default:
-            update_at<float, P, Ph>(D.m, D.pr, D.u, D.ud, D.ue, D.dte, D.ubl, D.q, D.fl, D.ER, D.dt, D.EW,
-                                    D.ube, D.beta, D.cnt, ex, ey, e);
+            update_at<float, P, Ph>(D.m, D.pr, D.u, ud_final(D, ku), D.ue, D.dte, D.ubl, D.q, D.fl, D.ER, D.dt,
+                                    D.EW, D.ube, D.beta, D.cnt, ex, ey, e);
     }
 }
 
-DEV void elem_dispatch(int phase, const InstDev& D, int ex, int ey, int e, double& dte) {
+DEV void elem_dispatch(int phase, const InstDev& D, int ex, int ey, int e, double& dte, int kg, int ku) {
     switch (D.p * 3 + D.phys) {
-        case 3: elem_phase<1, PhysAdv>(phase, D, ex, ey, e, dte); break;
-        case 4: elem_phase<1, PhysBurgers>(phase, D, ex, ey, e, dte); break;
-        case 5: elem_phase<1, PhysKPP>(phase, D, ex, ey, e, dte); break;
-        case 6: elem_phase<2, PhysAdv>(phase, D, ex, ey, e, dte); break;
-        case 7: elem_phase<2, PhysBurgers>(phase, D, ex, ey, e, dte); break;
-        case 8: elem_phase<2, PhysKPP>(phase, D, ex, ey, e, dte); break;
-        case 9: elem_phase<3, PhysAdv>(phase, D, ex, ey, e, dte); break;
-        case 10: elem_phase<3, PhysBurgers>(phase, D, ex, ey, e, dte); break;
-        case 11: elem_phase<3, PhysKPP>(phase, D, ex, ey, e, dte); break;
-        case 12: elem_phase<4, PhysAdv>(phase, D, ex, ey, e, dte); break;
-        case 13: elem_phase<4, PhysBurgers>(phase, D, ex, ey, e, dte); break;
-        default: elem_phase<4, PhysKPP>(phase, D, ex, ey, e, dte); break;
+        case 3: elem_phase<1, PhysAdv>(phase, D, ex, ey, e, dte, kg, ku); break;
+        case 4: elem_phase<1, PhysBurgers>(phase, D, ex, ey, e, dte, kg, ku); break;
+        case 5: elem_phase<1, PhysKPP>(phase, D, ex, ey, e, dte, kg, ku); break;
+        case 6: elem_phase<2, PhysAdv>(phase, D, ex, ey, e, dte, kg, ku); break;
+        case 7: elem_phase<2, PhysBurgers>(phase, D, ex, ey, e, dte, kg, ku); break;
+        case 8: elem_phase<2, PhysKPP>(phase, D, ex, ey, e, dte, kg, ku); break;
+        case 9: elem_phase<3, PhysAdv>(phase, D, ex, ey, e, dte, kg, ku); break;
+        case 10: elem_phase<3, PhysBurgers>(phase, D, ex, ey, e, dte, kg, ku); break;
+        case 11: elem_phase<3, PhysKPP>(phase, D, ex, ey, e, dte, kg, ku); break;
+        case 12: elem_phase<4, PhysAdv>(phase, D, ex, ey, e, dte, kg, ku); break;
+        case 13: elem_phase<4, PhysBurgers>(phase, D, ex, ey, e, dte, kg, ku); break;
+        default: elem_phase<4, PhysKPP>(phase, D, ex, ey, e, dte, kg, ku); break;
     }
 }
 
 template <int P>
-DEV void node_phase(int phase, const InstDev& D, int gx, int gy, long long node, float a, float b) {
+DEV void node_phase(int phase, const InstDev& D, int gx, int gy, long long node, float a, float b, int k) {
     switch (phase) {
-        case PH_GATHER_G: gather_init_at<float, P, 2>(D.m, D.EV, D.bg, D.g, gx, gy, node); break;
-        case PH_SWEEP_G: gather_sweep_at<float, P, 2>(D.m, D.EV, D.bg, D.g, gx, gy, node); break;
+        case PH_GRAD: grad_rhs_at<float, P, 1>(D.m, D.u, D.bg, D.g, gx, gy, node); break;
+        case PH_SWEEP_G:
+            if (k & 1) mass_sweep_at<float, P, 2>(D.m, D.g2, D.bg, D.g, gx, gy, node);
+            else mass_sweep_at<float, P, 2>(D.m, D.g, D.bg, D.g2, gx, gy, node);
+            break;
         case PH_GATHER_R: gather_init_at<float, P, 1>(D.m, D.ER, D.r, D.ud, gx, gy, node); break;
-        case PH_SWEEP_U: gather_sweep_at<float, P, 1>(D.m, D.EV, D.r, D.ud, gx, gy, node); break;
+        case PH_SWEEP_U:
+            if (k & 1) mass_sweep_at<float, P, 1>(D.m, D.ud2, D.r, D.ud, gx, gy, node);
+            else mass_sweep_at<float, P, 1>(D.m, D.ud, D.r, D.ud2, gx, gy, node);
+            break;
         default: final_at<float, P, 1>(D.m, D.pr, D.EW, D.un, D.u, a, b, D.cnt, gx, gy, node);
     }
 }
 
-DEV void node_dispatch(int phase, const InstDev& D, int gx, int gy, long long node, float a, float b) {
+DEV void node_dispatch(int phase, const InstDev& D, int gx, int gy, long long node, float a, float b, int k) {
     switch (D.p) {
-        case 1: node_phase<1>(phase, D, gx, gy, node, a, b); break;
-        case 2: node_phase<2>(phase, D, gx, gy, node, a, b); break;
-        case 3: node_phase<3>(phase, D, gx, gy, node, a, b); break;
-        default: node_phase<4>(phase, D, gx, gy, node, a, b); break;
+        case 1: node_phase<1>(phase, D, gx, gy, node, a, b, k); break;
+        case 2: node_phase<2>(phase, D, gx, gy, node, a, b, k); break;
+        case 3: node_phase<3>(phase, D, gx, gy, node, a, b, k); break;
+        default: node_phase<4>(phase, D, gx, gy, node, a, b, k); break;
     }
 }
 
-DEV void elem_loop(int phase, const InstDev* __restrict__ I, const Tile* __restrict__ et, int net, bool first) {
+DEV void elem_loop(int phase, const InstDev* __restrict__ I, const Tile* __restrict__ et, int net, bool first,
+                   int kg, int ku) {
     for (int t = blockIdx.x; t < net; t += gridDim.x) {
         const Tile T = et[t];
         const InstDev& D = I[T.inst];
@@ -150,21 +161,21 @@ DEV void elem_loop(int phase, const InstDev* __restrict__ I, const Tile* __restr
         if ((int)threadIdx.x < T.count) {
             const int e = T.begin + threadIdx.x;
             const int ey = e / D.m.nx, ex = e - ey * D.m.nx;
-            elem_dispatch(phase, D, ex, ey, e, dte);
+            elem_dispatch(phase, D, ex, ey, e, dte, kg, ku);
         }
         if (phase == PH_PRE && first) block_min_to(dte, D.dtbits);
     }
 }
 
 DEV void node_loop(int phase, const InstDev* __restrict__ I, const Tile* __restrict__ nt, int nnt, float a,
-                   float b) {
+                   float b, int k) {
     for (int t = blockIdx.x; t < nnt; t += gridDim.x) {
         const Tile T = nt[t];
         if ((int)threadIdx.x < T.count) {
             const InstDev& D = I[T.inst];
             const long long node = (long long)T.begin + threadIdx.x;
             const int gy = (int)(node / D.m.nnx), gx = (int)(node - (long long)gy * D.m.nnx);
-            node_dispatch(phase, D, gx, gy, node, a, b);
+            node_dispatch(phase, D, gx, gy, node, a, b, k);
         }
     }
 }
@@ -174,7 +185,7 @@ __global__ void __launch_bounds__(BT)
     k_batch_stage(const InstDev* __restrict__ I, int ninst, const Tile* __restrict__ et, int net,
                   const Tile* __restrict__ nt, int nnt, BatchSync* sync, float a, float b, int first,
                   int last, int kg, int ku, int mode_lo, long long limit) {
-    elem_loop(PH_PRE, I, et, net, first != 0);
+    elem_loop(PH_PRE, I, et, net, first != 0, kg, ku);
     if (!grid_sync(sync, limit)) return;
     if (first) {
         // global dt of each instance from its block minima (eq. (cflglob),
@@ -190,28 +201,24 @@ __global__ void __launch_bounds__(BT)
         if (mode_lo && !grid_sync(sync, limit)) return;
     }
     if (!mode_lo) {
-        node_loop(PH_GATHER_G, I, nt, nnt, a, b);
+        node_loop(PH_GRAD, I, nt, nnt, a, b, 0);
         if (!grid_sync(sync, limit)) return;
         for (int k = 0; k < kg; ++k) {
-            elem_loop(PH_MASS_G, I, et, net, false);
-            if (!grid_sync(sync, limit)) return;
-            node_loop(PH_SWEEP_G, I, nt, nnt, a, b);
+            node_loop(PH_SWEEP_G, I, nt, nnt, a, b, k);
             if (!grid_sync(sync, limit)) return;
         }
-        elem_loop(PH_RES, I, et, net, false);
+        elem_loop(PH_RES, I, et, net, false, kg, ku);
         if (!grid_sync(sync, limit)) return;
-        node_loop(PH_GATHER_R, I, nt, nnt, a, b);
+        node_loop(PH_GATHER_R, I, nt, nnt, a, b, 0);
         if (!grid_sync(sync, limit)) return;
         for (int k = 0; k < ku; ++k) {
-            elem_loop(PH_MASS_U, I, et, net, false);
-            if (!grid_sync(sync, limit)) return;
-            node_loop(PH_SWEEP_U, I, nt, nnt, a, b);
+            node_loop(PH_SWEEP_U, I, nt, nnt, a, b, k);
             if (!grid_sync(sync, limit)) return;
         }
     }
-    elem_loop(PH_UPDATE, I, et, net, false);
+    elem_loop(PH_UPDATE, I, et, net, false, kg, ku);
     if (!grid_sync(sync, limit)) return;
-    node_loop(PH_FINAL, I, nt, nnt, a, b);
+    node_loop(PH_FINAL, I, nt, nnt, a, b, 0);
     if (last) {
         for (int i = blockIdx.x * BT + threadIdx.x; i < ninst; i += gridDim.x * BT) *I[i].t += *I[i].dt;
     }
@@ -365,10 +372,11 @@ extern "C" cgl_status cgl_batch_create(cgl_state* const* states, int32_t n, cgl_
         d.u = (float*)b.u;
         d.un = (float*)b.un;
         d.g = (float*)b.g;
+        d.g2 = (float*)b.g2;
+        d.ud2 = (float*)b.ud2;
         d.bg = (float*)b.bg;
         d.r = (float*)b.r;
         d.ud = (float*)b.ud;
-        d.EV = (float*)b.EV;
         d.ER = (float*)b.ER;
         d.EW = (float*)b.EW;
         d.ue = b.ue;

@@ -932,6 +932,150 @@ __global__ void k_gather_sweep(MeshDev m, const R* __restrict__ EV, const R* __r
 }
 
 
+// ---------------------------------------------------------------------------
+// node-centric application of the assembled linear operators. On a uniform
+// mesh, sum_{e in E_i} of an element operator A^e = Ax (x) Ay is a separable
+// stencil over the (2p+1)^2 nodes around node i: along x the weight of offset
+// k is sum over the (at most two) elements containing i of Ax[a_e][k + a_e]
+// (a_e = local index of i in e); likewise along y.
+// ---------------------------------------------------------------------------
+// 1D weights of the assembled mass (WHICH 0: M[a][c]) or of the derivative on
+// the trial index (WHICH 1: C[c][a] = int B_c' B_a) for offsets -P..P
+template <class R, int P, int WHICH>
+DEV void weights_1d(const Tab<R>& T, int n, int a0, int a1, R (&w)[2 * P + 1]) {
+#pragma unroll
+    for (int k = 0; k < 2 * P + 1; ++k) w[k] = R(0);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        if (j < n) {
+            const int a = j ? a1 : a0;
+#pragma unroll
+            for (int c = 0; c <= P; ++c) {
+                const R v = (WHICH == 0) ? T.M[a][c] : T.C[c][a];
+                // offset c - a, stored at index c - a + P
+#pragma unroll
+                for (int k = 0; k < 2 * P + 1; ++k)
+                    if (k == c - a + P) w[k] += v;
+            }
+        }
+    }
+}
+
+// index of the node at offset k from g along a direction of n nodes
+DEV int offset_index(int g, int k, int n, int periodic) {
+    int x = g + k;
+    if (periodic) {
+        x = x < 0 ? x + n : (x >= n ? x - n : x);
+    } else {
+        x = x < 0 ? 0 : (x >= n ? n - 1 : x);  // only reached with a zero weight
+    }
+    return x;
+}
+
+// g_h right-hand side b_i = sum_e int phi_i grad u_h (x: derivative weights
+// along x, mass along y; y: the reverse) and the lumped first iterate b / m_i;
+// b and g hold [x components (NC)][y components (NC)]
+template <class R, int P, int NC>
+DEV void grad_rhs_at(MeshDev m, const R* __restrict__ u, R* __restrict__ bout, R* __restrict__ gout,
+                     int gx, int gy, long long node) {
+    const Tab<R>& T = TabSel<R>::t(P);
+    const NodeC<P> c = node_c<P>(m, gx, gy);
+    R wMx[2 * P + 1], wCx[2 * P + 1], wMy[2 * P + 1], wCy[2 * P + 1];
+    weights_1d<R, P, 0>(T, c.nxc, c.a0, c.a1, wMx);
+    weights_1d<R, P, 1>(T, c.nxc, c.a0, c.a1, wCx);
+    weights_1d<R, P, 0>(T, c.nyc, c.b0, c.b1, wMy);
+    weights_1d<R, P, 1>(T, c.nyc, c.b0, c.b1, wCy);
+    R sx[NC], sy[NC];
+#pragma unroll
+    for (int v = 0; v < NC; ++v) sx[v] = sy[v] = R(0);
+#pragma unroll
+    for (int ky = 0; ky < 2 * P + 1; ++ky) {
+        const long long row = (long long)offset_index(gy, ky - P, m.nny, m.py) * m.nnx;
+        R tx[NC], ty[NC];
+#pragma unroll
+        for (int v = 0; v < NC; ++v) tx[v] = ty[v] = R(0);
+#pragma unroll
+        for (int kx = 0; kx < 2 * P + 1; ++kx) {
+            const long long idx = row + offset_index(gx, kx - P, m.nnx, m.px);
+#pragma unroll
+            for (int v = 0; v < NC; ++v) {
+                const R x = u[v * m.NN + idx];
+                tx[v] += wCx[kx] * x;
+                ty[v] += wMx[kx] * x;
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NC; ++v) {
+            sx[v] += wMy[ky] * tx[v];
+            sy[v] += wCy[ky] * ty[v];
+        }
+    }
+    const R h = PV<R>::h(m);
+    const R inv_mi = PV<R>::inv_me(m) * inv_count<R>(c.nxc * c.nyc);
+#pragma unroll
+    for (int v = 0; v < NC; ++v) {
+        const R bx = h * sx[v], by = h * sy[v];
+        bout[v * m.NN + node] = bx;
+        bout[(NC + v) * m.NN + node] = by;
+        gout[v * m.NN + node] = bx * inv_mi;
+        gout[(NC + v) * m.NN + node] = by * inv_mi;
+    }
+}
+
+// one lumped-preconditioned Richardson sweep for NV fields,
+// x_out = x_in + (b - M_C x_in) / m_i, with M_C applied as a stencil
+template <class R, int P, int NV>
+DEV void mass_sweep_at(MeshDev m, const R* __restrict__ xin, const R* __restrict__ b, R* __restrict__ xout,
+                       int gx, int gy, long long node) {
+    const Tab<R>& T = TabSel<R>::t(P);
+    const NodeC<P> c = node_c<P>(m, gx, gy);
+    R wx[2 * P + 1], wy[2 * P + 1];
+    weights_1d<R, P, 0>(T, c.nxc, c.a0, c.a1, wx);
+    weights_1d<R, P, 0>(T, c.nyc, c.b0, c.b1, wy);
+    R s[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s[v] = R(0);
+#pragma unroll
+    for (int ky = 0; ky < 2 * P + 1; ++ky) {
+        const long long row = (long long)offset_index(gy, ky - P, m.nny, m.py) * m.nnx;
+        R t[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) t[v] = R(0);
+#pragma unroll
+        for (int kx = 0; kx < 2 * P + 1; ++kx) {
+            const long long idx = row + offset_index(gx, kx - P, m.nnx, m.px);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) t[v] += wx[kx] * xin[v * m.NN + idx];
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) s[v] += wy[ky] * t[v];
+    }
+    const R h2 = PV<R>::h2(m);
+    const R inv_mi = PV<R>::inv_me(m) * inv_count<R>(c.nxc * c.nyc);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const long long k = v * m.NN + node;
+        xout[k] = xin[k] + (b[k] - h2 * s[v]) * inv_mi;
+    }
+}
+
+template <class R, int P, int NC>
+__global__ void k_grad_rhs(MeshDev m, const R* __restrict__ u, R* __restrict__ bout, R* __restrict__ gout) {
+    int gx, gy;
+    long long node;
+    if (!node_of_thread(m, gx, gy, node)) return;
+    grad_rhs_at<R, P, NC>(m, u, bout, gout, gx, gy, node);
+}
+
+template <class R, int P, int NV>
+__global__ void k_mass_sweep(MeshDev m, const R* __restrict__ xin, const R* __restrict__ b,
+                             R* __restrict__ xout) {
+    int gx, gy;
+    long long node;
+    if (!node_of_thread(m, gx, gy, node)) return;
+    mass_sweep_at<R, P, NV>(m, xin, b, xout, gx, gy, node);
+}
+
 // runtime-degree candidate list (diagnostics only)
 struct NodeCands {
     int nxc, nyc;

@@ -11,6 +11,8 @@ struct Bufs {
     void* u;      // state            [NC][NN]  (R)
     void* un;     // RK base u^n      [NC][NN]  (R)
     void* g;      // g_h              [2NC][NN] (R)
+    void* g2;     // g_h ping-pong    [2NC][NN] (R)
+    void* ud2;    // udot ping-pong   [NC][NN]  (R)
     void* bg;     // rhs of g_h       [2NC][NN] (R)
     void* r;      // target residual  [NC][NN]  (R)
     void* ud;     // udot             [NC][NN]  (R)
@@ -71,34 +73,39 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
     const dim3 be(64, 2), bn(128, 1);
     const dim3 ge(nblk(m.nx, 64), nblk(m.ny, 2)), gn(nblk(m.nnx, 128), m.nny);
     R* u = (R*)B.u;
-    R* EV = (R*)B.EV;
-    const bool need_g = !dt_only && pr.mode != MODE_LO;
     CGL_LAUNCH(prof, KID_PRE, st,
                (k_pre<R, P, Ph><<<ge, be, 0, st>>>(m, pr, u, B.ue, B.dte, B.ubl, B.gam, B.nu, (R*)B.q, (R*)B.fl,
-                                                  need_g ? EV : nullptr, first ? B.dtbits : nullptr)));
+                                                  nullptr, first ? B.dtbits : nullptr)));
     if (first)
         CGL_LAUNCH(prof, KID_DT, st, (k_dt_final<<<1, 1, 0, st>>>(B.dtbits, pr.cfl, B.t, B.t_end, B.dt)));
     if (dt_only) return cudaGetLastError();
+    R* ud = (R*)B.ud;
     if (pr.mode != MODE_LO) {
+        // g_h: stencil right-hand side and lumped iterate, then k_g sweeps (ping-pong)
         R* g = (R*)B.g;
+        R* g2 = (R*)B.g2;
         R* bg = (R*)B.bg;
-        CGL_LAUNCH(prof, KID_GATHER, st, (k_gather_init<R, P, 2 * NC><<<gn, bn, 0, st>>>(m, EV, bg, g)));
+        CGL_LAUNCH(prof, KID_GRAD, st, (k_grad_rhs<R, P, NC><<<gn, bn, 0, st>>>(m, u, bg, g)));
         for (int k = 0; k < pr.k_g; ++k) {
-            CGL_LAUNCH(prof, KID_MASS, st, (k_mass_ev<R, P, 2 * NC><<<ge, be, 0, st>>>(m, g, EV)));
-            CGL_LAUNCH(prof, KID_SWEEP, st, (k_gather_sweep<R, P, 2 * NC><<<gn, bn, 0, st>>>(m, EV, bg, g)));
+            CGL_LAUNCH(prof, KID_SWEEP, st, (k_mass_sweep<R, P, 2 * NC><<<gn, bn, 0, st>>>(m, g, bg, g2)));
+            R* t = g;
+            g = g2;
+            g2 = t;
         }
         R* ER = (R*)B.ER;
         R* r = (R*)B.r;
-        R* ud = (R*)B.ud;
+        R* ud2 = (R*)B.ud2;
         CGL_LAUNCH(prof, KID_RES, st, (k_res_ev<R, P, Ph><<<ge, be, 0, st>>>(m, pr, u, g, B.gam, B.nu, ER)));
         CGL_LAUNCH(prof, KID_GATHER, st, (k_gather_init<R, P, NC><<<gn, bn, 0, st>>>(m, ER, r, ud)));
         for (int k = 0; k < pr.k_u; ++k) {
-            CGL_LAUNCH(prof, KID_MASS, st, (k_mass_ev<R, P, NC><<<ge, be, 0, st>>>(m, ud, EV)));
-            CGL_LAUNCH(prof, KID_SWEEP, st, (k_gather_sweep<R, P, NC><<<gn, bn, 0, st>>>(m, EV, r, ud)));
+            CGL_LAUNCH(prof, KID_SWEEP, st, (k_mass_sweep<R, P, NC><<<gn, bn, 0, st>>>(m, ud, r, ud2)));
+            R* t = ud;
+            ud = ud2;
+            ud2 = t;
         }
     }
     CGL_LAUNCH(prof, KID_UPDATE, st,
-               (k_update_ev<R, P, Ph><<<ge, be, 0, st>>>(m, pr, u, (const R*)B.ud, B.ue, B.dte, B.ubl, (const R*)B.q, (const R*)B.fl,
+               (k_update_ev<R, P, Ph><<<ge, be, 0, st>>>(m, pr, u, (const R*)ud, B.ue, B.dte, B.ubl, (const R*)B.q, (const R*)B.fl,
                                                         (const R*)B.ER, B.dt, (R*)B.EW, B.ube, B.beta,
                                                         B.cnt)));
     CGL_LAUNCH(prof, KID_FINAL, st,
