@@ -93,8 +93,11 @@ DEV bool grid_sync(BatchSync* s, long long limit) {
 DEV const float* g_final(const InstDev& D, int kg) { return (kg & 1) ? D.g2 : D.g; }
 DEV const float* ud_final(const InstDev& D, int ku) { return (ku & 1) ? D.ud2 : D.ud; }
 
+// per-degree phase bodies are separate functions (not inlined into the
+// persistent kernel) so that each gets its own register allocation
 template <int P, class Ph>
-DEV void elem_phase(int phase, const InstDev& D, int ex, int ey, int e, double& dte, int kg, int ku) {
+__device__ __noinline__ void elem_phase(int phase, const InstDev& D, int ex, int ey, int e, double& dte, int kg,
+                                        int ku) {
     switch (phase) {
         case PH_PRE:
             dte = pre_at<float, P, Ph>(D.m, D.pr, D.u, D.ue, D.dte, D.ubl, D.gam, D.nu, D.q, D.fl, nullptr, ex,
@@ -127,7 +130,8 @@ DEV void elem_dispatch(int phase, const InstDev& D, int ex, int ey, int e, doubl
 }
 
 template <int P>
-DEV void node_phase(int phase, const InstDev& D, int gx, int gy, long long node, float a, float b, int k) {
+__device__ __noinline__ void node_phase(int phase, const InstDev& D, int gx, int gy, long long node, float a,
+                                        float b, int k) {
     switch (phase) {
         case PH_GRAD: grad_rhs_at<float, P, 1>(D.m, D.u, D.bg, D.g, gx, gy, node); break;
         case PH_SWEEP_G:

@@ -940,36 +940,42 @@ __global__ void k_gather_sweep(MeshDev m, const R* __restrict__ EV, const R* __r
 // (a_e = local index of i in e); likewise along y.
 // ---------------------------------------------------------------------------
 // 1D weights of the assembled mass (WHICH 0: M[a][c]) or of the derivative on
-// the trial index (WHICH 1: C[c][a] = int B_c' B_a) for offsets -P..P
+// the trial index (WHICH 1: C[c][a] = int B_c' B_a) for offsets -P..P. The
+// node's first containing element has local index a0 (0..P); a second one
+// (n == 2, a shared vertex) has local index 0. Built from compile-time table
+// entries by selects (no runtime-indexed arrays).
 template <class R, int P, int WHICH>
-DEV void weights_1d(const Tab<R>& T, int n, int a0, int a1, R (&w)[2 * P + 1]) {
+DEV R wtab(const Tab<R>& T, int a, int c) {
+    return (WHICH == 0) ? T.M[a][c] : T.C[c][a];
+}
+
+template <class R, int P, int WHICH>
+DEV void weights_1d(const Tab<R>& T, int n, int a0, int /*a1*/, R (&w)[2 * P + 1]) {
 #pragma unroll
-    for (int k = 0; k < 2 * P + 1; ++k) w[k] = R(0);
+    for (int k = 0; k < 2 * P + 1; ++k) {
+        const int off = k - P;
+        R s = R(0);
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        if (j < n) {
-            const int a = j ? a1 : a0;
-#pragma unroll
-            for (int c = 0; c <= P; ++c) {
-                const R v = (WHICH == 0) ? T.M[a][c] : T.C[c][a];
-                // offset c - a, stored at index c - a + P
-#pragma unroll
-                for (int k = 0; k < 2 * P + 1; ++k)
-                    if (k == c - a + P) w[k] += v;
-            }
+        for (int aa = 0; aa <= P; ++aa) {
+            const int cc = off + aa;
+            if (cc >= 0 && cc <= P) s = (a0 == aa) ? wtab<R, P, WHICH>(T, aa, cc) : s;
         }
+        if (off >= 0 && off <= P) s += (n == 2) ? wtab<R, P, WHICH>(T, 0, off) : R(0);
+        w[k] = s;
     }
 }
 
-// index of the node at offset k from g along a direction of n nodes
-DEV int offset_index(int g, int k, int n, int periodic) {
-    int x = g + k;
-    if (periodic) {
-        x = x < 0 ? x + n : (x >= n ? x - n : x);
-    } else {
-        x = x < 0 ? 0 : (x >= n ? n - 1 : x);  // only reached with a zero weight
+// indices of the 2P+1 nodes at offsets -P..P around g along a direction of
+// n nodes (periodic wrap; clamped where only zero weights reach)
+template <int P>
+DEV void offsets_1d(int g, int n, int periodic, int (&idx)[2 * P + 1]) {
+#pragma unroll
+    for (int k = 0; k < 2 * P + 1; ++k) {
+        int x = g + k - P;
+        if (periodic) x = x < 0 ? x + n : (x >= n ? x - n : x);
+        else x = x < 0 ? 0 : (x >= n ? n - 1 : x);
+        idx[k] = x;
     }
-    return x;
 }
 
 // g_h right-hand side b_i = sum_e int phi_i grad u_h (x: derivative weights
@@ -985,18 +991,21 @@ DEV void grad_rhs_at(MeshDev m, const R* __restrict__ u, R* __restrict__ bout, R
     weights_1d<R, P, 1>(T, c.nxc, c.a0, c.a1, wCx);
     weights_1d<R, P, 0>(T, c.nyc, c.b0, c.b1, wMy);
     weights_1d<R, P, 1>(T, c.nyc, c.b0, c.b1, wCy);
+    int cols[2 * P + 1], rows[2 * P + 1];
+    offsets_1d<P>(gx, m.nnx, m.px, cols);
+    offsets_1d<P>(gy, m.nny, m.py, rows);
     R sx[NC], sy[NC];
 #pragma unroll
     for (int v = 0; v < NC; ++v) sx[v] = sy[v] = R(0);
 #pragma unroll
     for (int ky = 0; ky < 2 * P + 1; ++ky) {
-        const long long row = (long long)offset_index(gy, ky - P, m.nny, m.py) * m.nnx;
+        const long long row = (long long)rows[ky] * m.nnx;
         R tx[NC], ty[NC];
 #pragma unroll
         for (int v = 0; v < NC; ++v) tx[v] = ty[v] = R(0);
 #pragma unroll
         for (int kx = 0; kx < 2 * P + 1; ++kx) {
-            const long long idx = row + offset_index(gx, kx - P, m.nnx, m.px);
+            const long long idx = row + cols[kx];
 #pragma unroll
             for (int v = 0; v < NC; ++v) {
                 const R x = u[v * m.NN + idx];
@@ -1032,18 +1041,21 @@ DEV void mass_sweep_at(MeshDev m, const R* __restrict__ xin, const R* __restrict
     R wx[2 * P + 1], wy[2 * P + 1];
     weights_1d<R, P, 0>(T, c.nxc, c.a0, c.a1, wx);
     weights_1d<R, P, 0>(T, c.nyc, c.b0, c.b1, wy);
+    int cols[2 * P + 1], rows[2 * P + 1];
+    offsets_1d<P>(gx, m.nnx, m.px, cols);
+    offsets_1d<P>(gy, m.nny, m.py, rows);
     R s[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) s[v] = R(0);
 #pragma unroll
     for (int ky = 0; ky < 2 * P + 1; ++ky) {
-        const long long row = (long long)offset_index(gy, ky - P, m.nny, m.py) * m.nnx;
+        const long long row = (long long)rows[ky] * m.nnx;
         R t[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) t[v] = R(0);
 #pragma unroll
         for (int kx = 0; kx < 2 * P + 1; ++kx) {
-            const long long idx = row + offset_index(gx, kx - P, m.nnx, m.px);
+            const long long idx = row + cols[kx];
 #pragma unroll
             for (int v = 0; v < NV; ++v) t[v] += wx[kx] * xin[v * m.NN + idx];
         }
