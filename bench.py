@@ -258,9 +258,7 @@ def run_gpu(args):
         info = st.counters()
         ms = sum(a.elapsed_time(b) for a, b in evs)
         if dist:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = reduce_over_ranks(ms, dist, "cuda")
             dist.barrier()
         info = {k: info[k] - c0[k] for k in info}
         return ms, info
@@ -297,9 +295,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = reduce_over_ranks(e2e_s, dist, "cuda")
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -320,8 +316,8 @@ def run_gpu(args):
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": round(avg_ms, 5)}
     share = {k: round(v[0] / sum(x[0] for x in prof.values()), 4) for k, v in prof.items() if v[1]}
     share64 = {k: round(v[0] / sum(x[0] for x in prof64.values()), 4) for k, v in prof64.items() if v[1]}
-    value = world * nd * 3 * K / (ms32 * 1e-3)
-    value64 = world * nd * 3 * K / (ms64 * 1e-3)
+    value = aggregate_rate(nd * 3 * K, ms32, world)
+    value64 = aggregate_rate(nd * 3 * K, ms64, world)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         try:
@@ -344,7 +340,7 @@ def run_gpu(args):
         "kernel_share": share,
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * nd * 3 * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nd * 4,
+        "e2e": {"value": aggregate_rate(nd * 3 * K, e2e_s * 1e3, world), "unit": UNIT, "h2d_bytes_per_step": nd * 4,
                 "d2h_bytes_per_step": nd * 4},
         "gpu_launches": launches * K,
         "clocks": sampler.summary(),
@@ -353,6 +349,23 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def reduce_over_ranks(ms: float, dist=None, device="cpu") -> float:
+    """Max of a per-rank time over all ranks (the job ends with the slowest
+    rank); the identity without torch.distributed."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: float, ms_max: float, world: int) -> float:
+    """Whole-job rate: the units all ranks processed over the slowest rank's
+    time (replicas of the same workload, weak scaling)."""
+    return world * units_per_rank / (ms_max * 1e-3)
 
 
 class _Null:
