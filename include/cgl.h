@@ -94,13 +94,21 @@ typedef struct cgl_mesh_desc {
 /* Problem parameters. cgl_problem_defaults() fills the paper's defaults:
    q = 1 (Sec. 5), r = 2 (Sec. 2.2), w_lin = 1e-3 (Sec. 5.5), gamma = 1.4
    (Sec. 5.3), omega_CFL = 0.2, k_g = k_u = 1. */
+/* cgl_problem.options.  CGL_OPT_FP64_LIMITER: in the FP32-mixed form, evaluate
+ * every Appendix-A positivity factor (facet and nodal limiter) with the float64
+ * formula.  By default a float32 evaluation with a rigorous error bound first
+ * certifies the factors that equal 1 and only the others are evaluated in
+ * float64; the results are identical, the option exists to check that.
+ * No effect in the FP64 form or for scalar fluxes. */
+#define CGL_OPT_FP64_LIMITER 1
+
 typedef struct cgl_problem {
     int32_t flux;          /* CGL_FLUX_* */
     int32_t mode;          /* CGL_MODE_* */
     int32_t flux_limiter;  /* CGL_FL_* */
     int32_t k_g;           /* Richardson sweeps of the g_h projection (>= 0) */
     int32_t k_u;           /* Richardson sweeps of the udot solve (>= 0) */
-    int32_t reserved;
+    int32_t options;       /* CGL_OPT_* bits, 0 by default */
     double vx, vy;         /* advection velocity */
     double gamma_gas;      /* Euler adiabatic constant, 1 < gamma <= 5/3 */
     double umin, umax;     /* scalar invariant domain G = [umin, umax] */

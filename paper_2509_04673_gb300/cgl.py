@@ -22,6 +22,7 @@ FLUX_ADVECTION, FLUX_BURGERS, FLUX_KPP, FLUX_EULER = 0, 1, 2, 3
 MODE_LO, MODE_HO, MODE_WENO, MODE_WENO_L = 0, 1, 2, 3
 FL_NONE, FL_LIMITED, FL_LOW = 0, 1, 2
 FP64, FP32_MIXED = 0, 1
+OPT_FP64_LIMITER = 1
 FIELD_UE, FIELD_DTE, FIELD_UBL, FIELD_UBE, FIELD_GAMMA, FIELD_NU, FIELD_BETA = 0, 1, 2, 3, 4, 5, 6
 FIELD_GX, FIELD_GY, FIELD_R, FIELD_UDOT = 16, 17, 18, 19
 
@@ -34,7 +35,7 @@ class cgl_mesh_desc(C.Structure):
 
 class cgl_problem(C.Structure):
     _fields_ = [("flux", C.c_int32), ("mode", C.c_int32), ("flux_limiter", C.c_int32),
-                ("k_g", C.c_int32), ("k_u", C.c_int32), ("reserved", C.c_int32),
+                ("k_g", C.c_int32), ("k_u", C.c_int32), ("options", C.c_int32),
                 ("vx", C.c_double), ("vy", C.c_double), ("gamma_gas", C.c_double),
                 ("umin", C.c_double), ("umax", C.c_double), ("pos_eps", C.c_double),
                 ("q", C.c_double), ("r", C.c_double), ("weno_eps", C.c_double),

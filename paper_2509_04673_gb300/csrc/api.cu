@@ -436,7 +436,7 @@ extern "C" cgl_status cgl_state_create(const cgl_mesh* mesh, int32_t ncomp, int3
         {&B.g2, 2 * nc * NN * r},     {&B.ud2, nc * NN * r},
         {&B.bg, 2 * nc * NN * r},     {&B.r, nc * NN * r},         {&B.ud, nc * NN * r},
         {&B.EV, 16},                  {&B.ER, E * N2 * nc * r},    {&B.EW, E * N2 * nc * r},     {(void**)&B.q, 2 * E * r},
-        {(void**)&B.ue, nc * E * 8},  {(void**)&B.fue, 2 * nc * E * 8}, {(void**)&B.lame, E * 8},
+        {(void**)&B.ue, nc * E * 8},  {(void**)&B.cf, (1 + nc) * E * 4},
         {(void**)&B.dte, 3 * E * 8},  {(void**)&B.fl, 4 * nc * E * r},      {(void**)&B.ubl, nc * E * 8}, {(void**)&B.gam, E * 8},
         {(void**)&B.nu, E * 8},       {(void**)&B.ube, nc * E * 8}, {(void**)&B.beta, E * 8},
         {(void**)&B.cnt, CNT_N * 8},  {(void**)&B.dtbits, 8},      {(void**)&B.dt, 8},
@@ -488,6 +488,7 @@ extern "C" cgl_status cgl_set_problem(cgl_state* S, const cgl_problem* p) {
     if (p->mode < CGL_MODE_LO || p->mode > CGL_MODE_WENO_L) return fail(CGL_EINVAL, "unknown mode");
     if (p->flux_limiter < CGL_FL_NONE || p->flux_limiter > CGL_FL_LOW) return fail(CGL_EINVAL, "unknown flux_limiter");
     if (p->k_g < 0 || p->k_u < 0 || p->k_g > 64 || p->k_u > 64) return fail(CGL_EINVAL, "k_g, k_u in [0, 64]");
+    if (p->options & ~CGL_OPT_FP64_LIMITER) return fail(CGL_EINVAL, "unknown option bits");
     if (!(p->cfl > 0.0) || !(p->cfl <= 1.0)) return fail(CGL_EINVAL, "cfl must be in (0, 1]");
     if (!(p->q >= 1.0) || !(p->r >= 1.0)) return fail(CGL_EINVAL, "q, r must be >= 1");
     if (!(p->weno_eps > 0.0) || !(p->gamma_eps >= 0.0) || !(p->lambda_floor > 0.0))
@@ -553,6 +554,8 @@ extern "C" cgl_status cgl_set_problem(cgl_state* S, const cgl_problem* p) {
     d.hi32_f = (float)d.umax32;
     d.lo_tol_f = (float)d.lo_tol;
     d.hi_tol_f = (float)d.hi_tol;
+    d.opts = p->options;
+    d.ome_f = (float)(1.0 - d.pos_eps);
     S->stage = fn;
     S->has_problem = true;
     if (S->step_graph) {
@@ -753,7 +756,9 @@ static cudaError_t enqueue_step(cgl_state* S, Prof* prof = nullptr) {
     if (e != cudaSuccess) return e;
     e = S->stage(B, m, S->pd, 1.0 / 3.0, 2.0 / 3.0, false, false, S->st, prof);
     if (e != cudaSuccess) return e;
-    CGL_LAUNCH(prof, KID_TADV, S->st, (k_t_advance<<<1, 1, 0, S->st>>>(B.t, B.dt)));
+    CGL_LAUNCH(prof, KID_TADV, S->st, (e = launch(prof == nullptr, k_t_advance, dim3(1), dim3(1), S->st, B.t,
+                                                   (const double*)B.dt)));
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

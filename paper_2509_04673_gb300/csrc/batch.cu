@@ -100,15 +100,15 @@ __device__ __noinline__ void elem_phase(int phase, const InstDev& D, int ex, int
                                         int ku) {
     switch (phase) {
         case PH_PRE:
-            dte = pre_at<float, P, Ph>(D.m, D.pr, D.u, D.ue, D.dte, D.ubl, D.gam, D.nu, D.q, D.fl, nullptr, ex,
-                                       ey, e);
+            dte = pre_at<float, P, Ph>(D.m, D.pr, D.u, D.ue, D.dte, D.ubl, D.gam, D.nu, D.q, D.fl, nullptr, nullptr,
+                                       ex, ey, e);
             break;
         case PH_RES:
             res_at<float, P, Ph>(D.m, D.pr, D.u, g_final(D, kg), D.gam, D.nu, D.ER, ex, ey, e);
             break;
         default:
-            update_at<float, P, Ph>(D.m, D.pr, D.u, ud_final(D, ku), D.ue, D.dte, D.ubl, D.q, D.fl, D.ER, D.dt,
-                                    D.EW, D.ube, D.beta, D.cnt, ex, ey, e);
+            update_at<float, P, Ph>(D.m, D.pr, D.u, ud_final(D, ku), D.ue, D.dte, D.ubl, D.q, D.fl, D.ER, nullptr,
+                                    D.dt, D.EW, D.ube, D.beta, D.cnt, ex, ey, e);
     }
 }
 

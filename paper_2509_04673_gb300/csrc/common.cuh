@@ -5,8 +5,10 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <cstring>
 
 #define DEV __device__ __forceinline__
+#define HDEV __host__ __device__ __forceinline__
 
 namespace cgl {
 
@@ -46,7 +48,11 @@ struct ProbDev {
     float vx_f, vy_f, gam_f, w_lin_f, weno_eps_f, gamma_eps_f, q_f;
     float ubc_f[4], ubc_lo_f[4];
     float lo32_f, hi32_f, lo_tol_f, hi_tol_f;
+    int opts;              // CGL_OPT_* bits
+    float ome_f;           // 1 - pos_eps rounded to float
 };
+
+enum { OPT_FP64_LIMITER = 1 };
 
 // typed views of the problem and mesh constants: float kernels read the
 // float copies, float64 kernels the originals
@@ -233,7 +239,7 @@ DEV void llf(const T* uL, const T* uR, T nx, T ny, const ProbDev& pr, T* F, T* l
 // alpha f / m, with the positivity margin eps (rho* >= eps rho_bar and the
 // pressure constraint scaled by (1 - eps)).
 template <class T>
-DEV T euler_alpha(const T* ub, const T* f, T m, T eps) {
+HDEV T euler_alpha(const T* ub, const T* f, T m, T eps) {
     T rho = ub[0], mx = ub[1], my = ub[2], E = ub[3];
     T fr = f[0], fmx = f[1], fmy = f[2], fE = f[3];
     T thr = m * rho * (T(1) - eps);
@@ -244,6 +250,77 @@ DEV T euler_alpha(const T* ub, const T* f, T m, T eps) {
     T a_p = (R < Q) ? Q / R : T(1);
     T a = fmin(a_rho, a_p);
     return fmin(fmax(a, T(0)), T(1));
+}
+
+// Float32 certificate for euler_alpha: true only when the float64 evaluation
+// of euler_alpha<double> on inputs that these floats round (relative error
+// <= 2^-24 each: ub, f, m, 1 - eps) certainly returns exactly 1, i.e. both
+// constraints of Appendix A hold with alpha = 1:
+//   T1 = m rho (1 - eps) + f_rho  >= 0,
+//   T2 = R - Q                    >= 0.
+// T1 is homogeneous of degree 1 in (ub, f) and in (f, m), T2 of degree 2 in
+// (ub, f) and 1 in (f, m), so the inputs are first scaled by exact powers of
+// two to rho, m in [1, 2); this changes neither sign.  Each T is then
+// evaluated in float together with A, the same expression with every
+// monomial in absolute value.  With n operations and k rounded inputs
+// (n + k < 40) the float error is below (n + k) 2^-24 A and the float64 one
+// below (n + k) 2^-53 A.  Scaled values are required to be at most 2^40, so
+// an underflowed input or product (error <= 2^-150) is amplified to at most
+// 2^-109 and all of them together stay below 2^-100.  So T > 2^-16 A +
+// 2^-100 certifies T > 0 for both evaluations.  NaN, infinite, zero or
+// subnormal rho or m fail and are left to the float64 formula.
+HDEV int bits_of(float x) {
+#ifdef __CUDA_ARCH__
+    return __float_as_int(x);
+#else
+    int i;
+    std::memcpy(&i, &x, 4);
+    return i;
+#endif
+}
+HDEV float float_of(int i) {
+#ifdef __CUDA_ARCH__
+    return __int_as_float(i);
+#else
+    float x;
+    std::memcpy(&x, &i, 4);
+    return x;
+#endif
+}
+HDEV float pow2f(int k) { return float_of((127 + k) << 23); }  // 2^k, -126 <= k <= 127
+
+HDEV bool euler_alpha_is_one(const float* ub, const float* f, float m, float ome) {
+    const int brho = bits_of(ub[0]), bm = bits_of(m);
+    const int erho = (brho >> 23) & 0xff, em = (bm >> 23) & 0xff;
+    // rho and m positive, normal and finite
+    if (brho <= 0 || bm <= 0 || erho == 0 || em == 0 || erho == 0xff || em == 0xff) return false;
+    const float sj = pow2f(127 - erho), sk = pow2f(127 - em);  // rho sj, m sk in [1, 2)
+    const float rho = ub[0] * sj, mx = ub[1] * sj, my = ub[2] * sj, E = ub[3] * sj;
+    const float fr = (f[0] * sj) * sk, fmx = (f[1] * sj) * sk, fmy = (f[2] * sj) * sk, fE = (f[3] * sj) * sk;
+    const float ms = m * sk;
+    const float big = 0x1p40f;
+    if (!(fabsf(mx) <= big && fabsf(my) <= big && fabsf(E) <= big && fabsf(fr) <= big && fabsf(fmx) <= big &&
+          fabsf(fmy) <= big && fabsf(fE) <= big))
+        return false;
+    const float K = 0x1p-16f, A0 = 0x1p-100f;
+    // density constraint
+    const float thr = ms * rho * ome;
+    const float t1 = thr + fr;
+    const float a1 = fabsf(thr) + fabsf(fr);
+    // pressure constraint: Q = (1 - eps) m (|m|^2/2 - rho E),
+    // R = rho fE + E fr - m.fm + min(0, fE fr - |fm|^2/2) / m
+    const float kin = 0.5f * (mx * mx + my * my);
+    const float rE = rho * E;
+    const float Q = ome * ms * (kin - rE);
+    const float aQ = ms * (kin + fabsf(rE));
+    const float frE = fE * fr, fkin = 0.5f * (fmx * fmx + fmy * fmy);
+    const float c = frE - fkin;
+    const float p1 = rho * fE, p2 = E * fr, p3 = mx * fmx, p4 = my * fmy;
+    const float Rv = ((p1 + p2) - (p3 + p4)) + fminf(0.f, c) / ms;
+    const float aR = ((fabsf(p1) + fabsf(p2)) + (fabsf(p3) + fabsf(p4))) + (fabsf(frE) + fkin) / ms;
+    const float t2 = Rv - Q;
+    const float a2 = aR + aQ;
+    return (t1 > K * a1 + A0) && (t2 > K * a2 + A0);
 }
 
 }  // namespace cgl

@@ -2,31 +2,56 @@
 // convex-limited CG-WENO scheme (Kuzmin, Hajduk, Vedral, arXiv 2509.04673),
 // following the order of the algorithm summary in Sec. 4.3:
 //
-//   k_pre        cell averages u^e of the element and its face neighbours
-//                (eq. (ueold)), facet speeds, dt_e (eq. (dtmaxcell)), f^L,
-//                ubar^{e,L} (eq. (uelowFCT)), WENO sensor gamma_e (eqs.
-//                (WENO:alpha), (WENO:norm)), nu_e (eq. (stab:WENO)), element
-//                vectors int phi_i grad u_h for g_h, block minimum of dt_e
-//   k_dt_final   global dt = omega_CFL min_e dt_e (eq. (cflglob), Sec. 5)
-//   k_res_ev     element residual: Galerkin part of eq. (weak:stab2) with
-//                boundary terms (eqs. (aec), (aecb)) and s_h (eq. (stab:WENO))
-//   k_mass_ev    consistent-mass products for the Richardson sweeps
-//   k_gather_*   node-centric sums over E_i in a fixed order (deterministic)
-//   k_update_ev  facet fluxes f^H (eq. (hoflux)), flux limiter (eq. (fAlim),
-//                Appendix A), ubar^e (eq. (uelim)), f_i^e (eq. (aec)),
-//                beta_e (eqs. (slimit1), (slimit2), Appendix A), element
-//                contributions of eq. (eq:SSPupdate)
-//   k_final      node gather, SSP-RK combination, invariant-domain check
+//   k_pre          cell averages u^e of the element and its face neighbours
+//                  (eq. (ueold)), facet speeds, dt_e (eq. (dtmaxcell)), f^L,
+//                  ubar^{e,L} (eq. (uelowFCT)), WENO sensor gamma_e (eqs.
+//                  (WENO:alpha), (WENO:norm)), nu_e (eq. (stab:WENO)), block
+//                  minimum of dt_e
+//   k_dt_final     global dt = omega_CFL min_e dt_e (eq. (cflglob), Sec. 5)
+//   k_grad_rhs     right-hand side of the g_h projection, int phi_i grad u_h,
+//                  as a tiled separable stencil, and its lumped iterate
+//   k_mass_sweep   lumped-preconditioned Richardson sweep with M_C applied
+//                  as a tiled separable stencil
+//   k_res_ev       element residual: Galerkin part of eq. (weak:stab2) with
+//                  boundary terms (eqs. (aec), (aecb)) and s_h (eq. (stab:WENO))
+//   k_gather_init  node-centric sum over E_i of the element residuals in a
+//                  fixed order (deterministic), and its lumped iterate
+//   k_update_ev    facet fluxes f^H (eq. (hoflux)), flux limiter (eq. (fAlim),
+//                  Appendix A), ubar^e (eq. (uelim)), f_i^e (eq. (aec)),
+//                  beta_e (eqs. (slimit1), (slimit2), Appendix A), element
+//                  contributions of eq. (eq:SSPupdate)
+//   k_final        node gather, SSP-RK combination, invariant-domain check
 //
-// One thread per element (or node). Kernels are templated on the bulk
-// precision R (double, or float in the mixed form), the degree P and the
-// physics policy Ph. Cell averages, dt_e, facet fluxes, the flux limiter,
-// limiter bound gaps and final nodal sums are float64 in both forms.
+// One thread per element (or node; the stencils use 32 x 16 node tiles).
+// Kernels are templated on the bulk precision R (double, or float in the
+// mixed form), the degree P and the physics policy Ph. Cell averages, dt_e,
+// the facet flux limiter, limiter bound gaps and positivity factors are
+// float64 in both forms.
+//
+// Element vectors (ER, EW and the no-allocation scratch) are stored
+// component-major, [local node i][field v][element e]: a warp of consecutive
+// elements writes, and a warp of consecutive nodes reads, contiguous runs.
 #pragma once
 
 #include "common.cuh"
 
 namespace cgl {
+
+// element-vector layout: value v of local node i of element e, NV values
+DEV long long ev_at(long long E, int e, int i, int v, int NV) { return (long long)(i * NV + v) * E + e; }
+
+
+// Programmatic dependent launch: every kernel of a stage first lets the next
+// kernel of the stream be scheduled (it launches once all blocks of this one
+// are resident) and then waits until the previous kernel has completed and
+// its writes are visible.  Each kernel calls this first, in every thread,
+// before any global memory access; for a kernel launched without the
+// programmatic-serialisation attribute both instructions do nothing.
+DEV void pdl_begin() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 
 template <int P>
 struct Dim {
@@ -114,9 +139,9 @@ DEV double block_mean(const float (&v)[N]) {
 }
 
 // b^e_i = (int phi_i d_x u_h, int phi_i d_y u_h), sum-factorised, into EV
-// [(e*N2 + i)*2NC + v], v = dim*NC + c
+// at ev_at(E, e, i, v, 2NC), v = dim*NC + c
 template <class R, int P, int NC>
-DEV void grad_vectors(const R (&U)[NC][Dim<P>::N2], R h, long long e, R* __restrict__ EV) {
+DEV void grad_vectors(const R (&U)[NC][Dim<P>::N2], R h, long long E, int e, R* __restrict__ EV) {
     constexpr int N1 = P + 1, N2 = Dim<P>::N2, NV = 2 * NC;
     const Tab<R>& T = TabSel<R>::t(P);
 #pragma unroll
@@ -145,9 +170,8 @@ DEV void grad_vectors(const R (&U)[NC][Dim<P>::N2], R h, long long e, R* __restr
                     sx += T.M[b][d] * Y[d][a];
                     sy += T.C[d][b] * Z[d][a];
                 }
-                long long base = (e * N2 + b * N1 + a) * NV;
-                EV[base + c] = h * sx;
-                EV[base + NC + c] = h * sy;
+                EV[ev_at(E, e, b * N1 + a, c, NV)] = h * sx;
+                EV[ev_at(E, e, b * N1 + a, NC + c, NV)] = h * sy;
             }
     }
 }
@@ -517,7 +541,8 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
                         double* __restrict__ ue_out, double* __restrict__ dte_out,
                         double* __restrict__ ubl_out, double* __restrict__ gam_out,
                         double* __restrict__ nu_out, float* __restrict__ q_out,
-                        float* __restrict__ fl_out, float* __restrict__ EV, int ex, int ey, int e) {
+                        float* __restrict__ fl_out, float* __restrict__ EV, float* __restrict__ cf_out,
+                        int ex, int ey, int e) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
     int nb[4];
 #pragma unroll
@@ -620,8 +645,12 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
         if (NC == 1) {
             q_out[e] = __double2float_rz(fmax(0.0, (0.25 * s) * (pr.umax - bl)));
             q_out[m.E + e] = __double2float_rz(fmin(0.0, (0.25 * s) * (pr.umin - bl)));
+        } else {
+            // float copies for the certificate of the facet limiter (euler_alpha_is_one)
+            cf_out[(1 + c) * m.E + e] = (float)bl;
         }
     }
+    if (NC > 1) cf_out[e] = sf;
     float gam;
     if (pr.mode == MODE_WENO || pr.mode == MODE_WENO_L) {
         if (NC == 1) {
@@ -645,7 +674,7 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
         lm = fmaxf(lm, Ph::template node_speed<float>(ui, pr));
     }
     nu_out[e] = (double)(lm * (m.h_f * (0.5f / P)));
-    if (EV) grad_vectors<float, P, NC>(U, m.h_f, e, EV);
+    if (EV) grad_vectors<float, P, NC>(U, m.h_f, m.E, e, EV);
     return dte;
 }
 
@@ -654,10 +683,10 @@ DEV double pre_at(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __rest
                   double* __restrict__ dte_out, double* __restrict__ ubl_out,
                   double* __restrict__ gam_out, double* __restrict__ nu_out,
                   R* __restrict__ q_out, R* __restrict__ fl_out, R* __restrict__ EV,
-                  int ex, int ey, int e) {
+                  float* __restrict__ cf_out, int ex, int ey, int e) {
     if constexpr (sizeof(R) == 4) {
         return pre_at_mixed<P, Ph>(m, pr, u, ue_out, dte_out, ubl_out, gam_out, nu_out, q_out, fl_out, EV,
-                                   ex, ey, e);
+                                   cf_out, ex, ey, e);
     } else {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
     double dte;
@@ -737,7 +766,7 @@ DEV double pre_at(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __rest
             lm = fmax(lm, Ph::template node_speed<R>(ui, pr));
         }
         nu_out[e] = (double)lm * (m.h * (0.5 / m.p));
-        if (EV) grad_vectors<R, P, NC>(U, PV<R>::h(m), e, EV);
+        if (EV) grad_vectors<R, P, NC>(U, PV<R>::h(m), m.E, e, EV);
     }
     return dte;
     }
@@ -748,11 +777,13 @@ __global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __
                       double* __restrict__ dte_out, double* __restrict__ ubl_out,
                       double* __restrict__ gam_out, double* __restrict__ nu_out,
                       R* __restrict__ q_out, R* __restrict__ fl_out, R* __restrict__ EV,
-                      unsigned long long* __restrict__ dtbits) {
+                      float* __restrict__ cf_out, unsigned long long* __restrict__ dtbits) {
+    pdl_begin();
     int ex, ey, e;
     double dte = __longlong_as_double(0x7ff0000000000000LL);
     if (elem_of_thread(m, ex, ey, e))
-        dte = pre_at<R, P, Ph>(m, pr, u, ue_out, dte_out, ubl_out, gam_out, nu_out, q_out, fl_out, EV, ex, ey, e);
+        dte = pre_at<R, P, Ph>(m, pr, u, ue_out, dte_out, ubl_out, gam_out, nu_out, q_out, fl_out, EV, cf_out,
+                               ex, ey, e);
     if (dtbits) block_min_to(dte, dtbits);
 }
 
@@ -760,6 +791,7 @@ __global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __
 // dt = min(cfl * min_e dt_e, t_end - t), never negative
 static __global__ void k_dt_final(unsigned long long* bits, double cfl, const double* t,
                                   const double* t_end, double* dt) {
+    pdl_begin();
     double d = cfl * __longlong_as_double((long long)*bits);
     *bits = 0x7ff0000000000000ull;  // ready for the next reduction
     double rem = *t_end - *t;
@@ -767,46 +799,8 @@ static __global__ void k_dt_final(unsigned long long* bits, double cfl, const do
     *dt = d;
 }
 
-static __global__ void k_t_advance(double* t, const double* dt) { *t = *t + *dt; }
+static __global__ void k_t_advance(double* t, const double* dt) { pdl_begin(); *t = *t + *dt; }
 
-// k_mass_ev: (M_C x)^e_i = h^2 sum (M (x) M) x_e for NV nodal fields
-template <class R, int P, int NV>
-DEV void mass_at(MeshDev m, const R* __restrict__ x, R* __restrict__ EV, int ex, int ey, int e) {
-    constexpr int N1 = P + 1, N2 = Dim<P>::N2;
-    const Tab<R>& T = TabSel<R>::t(P);
-    const R h2 = PV<R>::h2(m);
-    R X[NV][N2];
-    load_block<R, P, NV>(x, m, ex, ey, X);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        R Y[N1][N1];
-#pragma unroll
-        for (int d = 0; d < N1; ++d)
-#pragma unroll
-            for (int a = 0; a < N1; ++a) {
-                R s = R(0);
-#pragma unroll
-                for (int k = 0; k < N1; ++k) s += T.M[a][k] * X[v][d * N1 + k];
-                Y[d][a] = s;
-            }
-#pragma unroll
-        for (int b = 0; b < N1; ++b)
-#pragma unroll
-            for (int a = 0; a < N1; ++a) {
-                R s = R(0);
-#pragma unroll
-                for (int d = 0; d < N1; ++d) s += T.M[b][d] * Y[d][a];
-                EV[((long long)e * N2 + b * N1 + a) * NV + v] = h2 * s;
-            }
-    }
-}
-
-template <class R, int P, int NV>
-__global__ void k_mass_ev(MeshDev m, const R* __restrict__ x, R* __restrict__ EV) {
-    int ex, ey, e;
-    if (!elem_of_thread(m, ex, ey, e)) return;
-    mass_at<R, P, NV>(m, x, EV, ex, ey, e);
-}
 
 
 // ---------------------------------------------------------------------------
@@ -873,9 +867,9 @@ DEV void gather_at(const MeshDev& m, const R* __restrict__ EV, const NodeC<P>& c
             for (int i = 0; i < 2; ++i) {
                 if (i < c.nxc) {
                     const int ex = i ? c.ex1 : c.ex0, a = i ? c.a1 : c.a0;
-                    const long long base = (((long long)ey * m.nx + ex) * N2 + b * N1 + a) * NV;
+                    const int e = ey * m.nx + ex;
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) s[v] += EV[base + v];
+                    for (int v = 0; v < NV; ++v) s[v] += EV[ev_at(m.E, e, b * N1 + a, v, NV)];
                 }
             }
         }
@@ -900,6 +894,7 @@ DEV void gather_init_at(MeshDev m, const R* __restrict__ EV, R* __restrict__ bou
 template <class R, int P, int NV>
 __global__ void k_gather_init(MeshDev m, const R* __restrict__ EV, R* __restrict__ bout,
                               R* __restrict__ xout) {
+    pdl_begin();
     int gx, gy;
     long long node;
     if (!node_of_thread(m, gx, gy, node)) return;
@@ -907,30 +902,20 @@ __global__ void k_gather_init(MeshDev m, const R* __restrict__ EV, R* __restrict
 }
 
 
-// Richardson sweep x <- x + (b - sum EV) / m_i
-template <class R, int P, int NV>
-DEV void gather_sweep_at(MeshDev m, const R* __restrict__ EV, const R* __restrict__ b,
-                               R* __restrict__ x, int gx, int gy, long long node) {
-    const NodeC<P> c = node_c<P>(m, gx, gy);
-    R s[NV];
-    gather_at<R, P, NV>(m, EV, c, s);
-    const R inv_mi = PV<R>::inv_me(m) * inv_count<R>(c.nxc * c.nyc);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        long long k = v * m.NN + node;
-        x[k] = x[k] + (b[k] - s[v]) * inv_mi;
-    }
-}
 
-template <class R, int P, int NV>
-__global__ void k_gather_sweep(MeshDev m, const R* __restrict__ EV, const R* __restrict__ b,
-                               R* __restrict__ x) {
-    int gx, gy;
-    long long node;
-    if (!node_of_thread(m, gx, gy, node)) return;
-    gather_sweep_at<R, P, NV>(m, EV, b, x, gx, gy, node);
-}
 
+// explicitly rounded multiply-add and multiply (no contraction choices left
+// to the compiler, so the per-node and the tiled stencils give equal bits)
+DEV float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+DEV double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
+DEV float mul_r(float a, float b) { return __fmul_rn(a, b); }
+DEV double mul_r(double a, double b) { return __dmul_rn(a, b); }
+
+// Richardson update x + (b - h^2 s) / m_i with s = (M (x) M) x at the node
+template <class R>
+DEV R sweep_value(R x, R b, R s, R h2, R inv_mi) {
+    return fma_r(fma_r(-h2, s, b), inv_mi, x);
+}
 
 // ---------------------------------------------------------------------------
 // node-centric application of the assembled linear operators. On a uniform
@@ -1009,25 +994,25 @@ DEV void grad_rhs_at(MeshDev m, const R* __restrict__ u, R* __restrict__ bout, R
 #pragma unroll
             for (int v = 0; v < NC; ++v) {
                 const R x = u[v * m.NN + idx];
-                tx[v] += wCx[kx] * x;
-                ty[v] += wMx[kx] * x;
+                tx[v] = fma_r(wCx[kx], x, tx[v]);
+                ty[v] = fma_r(wMx[kx], x, ty[v]);
             }
         }
 #pragma unroll
         for (int v = 0; v < NC; ++v) {
-            sx[v] += wMy[ky] * tx[v];
-            sy[v] += wCy[ky] * ty[v];
+            sx[v] = fma_r(wMy[ky], tx[v], sx[v]);
+            sy[v] = fma_r(wCy[ky], ty[v], sy[v]);
         }
     }
     const R h = PV<R>::h(m);
-    const R inv_mi = PV<R>::inv_me(m) * inv_count<R>(c.nxc * c.nyc);
+    const R inv_mi = mul_r(PV<R>::inv_me(m), inv_count<R>(c.nxc * c.nyc));
 #pragma unroll
     for (int v = 0; v < NC; ++v) {
-        const R bx = h * sx[v], by = h * sy[v];
+        const R bx = mul_r(h, sx[v]), by = mul_r(h, sy[v]);
         bout[v * m.NN + node] = bx;
         bout[(NC + v) * m.NN + node] = by;
-        gout[v * m.NN + node] = bx * inv_mi;
-        gout[(NC + v) * m.NN + node] = by * inv_mi;
+        gout[v * m.NN + node] = mul_r(bx, inv_mi);
+        gout[(NC + v) * m.NN + node] = mul_r(by, inv_mi);
     }
 }
 
@@ -1057,35 +1042,218 @@ DEV void mass_sweep_at(MeshDev m, const R* __restrict__ xin, const R* __restrict
         for (int kx = 0; kx < 2 * P + 1; ++kx) {
             const long long idx = row + cols[kx];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) t[v] += wx[kx] * xin[v * m.NN + idx];
+            for (int v = 0; v < NV; ++v) t[v] = fma_r(wx[kx], xin[v * m.NN + idx], t[v]);
         }
 #pragma unroll
-        for (int v = 0; v < NV; ++v) s[v] += wy[ky] * t[v];
+        for (int v = 0; v < NV; ++v) s[v] = fma_r(wy[ky], t[v], s[v]);
     }
     const R h2 = PV<R>::h2(m);
-    const R inv_mi = PV<R>::inv_me(m) * inv_count<R>(c.nxc * c.nyc);
+    const R inv_mi = mul_r(PV<R>::inv_me(m), inv_count<R>(c.nxc * c.nyc));
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         const long long k = v * m.NN + node;
-        xout[k] = xin[k] + (b[k] - h2 * s[v]) * inv_mi;
+        xout[k] = sweep_value(xin[k], b[k], s[v], h2, inv_mi);
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tiled forms of the two stencils: a block of 32 x 8 threads owns a tile of
+// 32 x 16 nodes, stages one field of the tile plus a halo of p nodes in
+// shared memory (coalesced rows, periodic wrap, zeros outside a
+// non-periodic mesh, where every weight that reaches them is 0), applies
+// the 1D operator along x for all halo rows, then along y.  The weights of
+// a node depend only on its class along each direction (local index 1..p-1
+// inside an element, an interior vertex shared by two elements, or a
+// boundary vertex); the class tables are built per block from the element
+// tables with the same additions as weights_1d.  Same arithmetic, in the
+// same order with the same roundings, as grad_rhs_at / mass_sweep_at.
+// ---------------------------------------------------------------------------
+constexpr int ST_TX = 32, ST_TY = 16, ST_BY = 8;
+
+// class of node g along a direction of n nodes: 1..P-1 inside an element,
+// 0 vertex shared by two elements, P lower boundary vertex, P+1 upper one
+template <int P>
+DEV int node_class(int g, int n, int periodic) {
+    const int a = g % P;
+    if (a != 0) return a;
+    if (!periodic) {
+        if (g == 0) return P;
+        if (g == n - 1) return P + 1;
+    }
+    return 0;
+}
+
+// weight of offset off (-P..P) for a node of class cls (WHICH 0: mass,
+// 1: derivative on the trial index), as weights_1d computes it
+template <class R, int P, int WHICH>
+DEV R class_weight(const Tab<R>& T, int cls, int off) {
+    // first containing element and the node's local index in it
+    const int a0 = (cls == 0 || cls == P + 1) ? P : (cls == P ? 0 : cls);
+    const bool two = cls == 0;
+    R s = R(0);
+    const int cc = off + a0;
+    if (cc >= 0 && cc <= P) s = wtab<R, P, WHICH>(T, a0, cc);
+    if (two && off >= 0 && off <= P) s += wtab<R, P, WHICH>(T, 0, off);
+    return s;
+}
+
+// stage one field (rows gy0-P.., columns gx0-P..) of the tile in shared memory
+template <class R, int P>
+DEV void stage_tile(const MeshDev& m, const R* __restrict__ x, R (*xs)[ST_TX + 2 * P], int gx0, int gy0, int tid) {
+    constexpr int HX = ST_TX + 2 * P, HY = ST_TY + 2 * P;
+    for (int i = tid; i < HX * HY; i += ST_TX * ST_BY) {
+        const int r = i / HX, c = i - r * HX;
+        int gy = gy0 - P + r, gx = gx0 - P + c;
+        bool in = true;
+        if (m.py) gy = gy < 0 ? gy + m.nny : (gy >= m.nny ? gy - m.nny : gy);
+        else in = gy >= 0 && gy < m.nny;
+        if (m.px) gx = gx < 0 ? gx + m.nnx : (gx >= m.nnx ? gx - m.nnx : gx);
+        else in = in && gx >= 0 && gx < m.nnx;
+        xs[r][c] = in ? x[(long long)gy * m.nnx + gx] : R(0);
+    }
+}
+
+// fields staged together: as many as fit in 32 KB of shared memory (a
+// divisor of NV), so one round of loads and barriers serves all of them
+template <class R, int P, int NV, int NT>
+struct StFields {
+    static constexpr int HX = ST_TX + 2 * P, HY = ST_TY + 2 * P;
+    static constexpr int bytes(int f) { return f * (HY * HX + NT * HY * ST_TX) * (int)sizeof(R); }
+    static constexpr int value = (bytes(NV) <= 32768) ? NV
+                                 : (NV % 4 == 0 && bytes(4) <= 32768) ? 4
+                                 : (NV % 2 == 0 && bytes(2) <= 32768) ? 2 : 1;
+};
+
 template <class R, int P, int NC>
-__global__ void k_grad_rhs(MeshDev m, const R* __restrict__ u, R* __restrict__ bout, R* __restrict__ gout) {
-    int gx, gy;
-    long long node;
-    if (!node_of_thread(m, gx, gy, node)) return;
-    grad_rhs_at<R, P, NC>(m, u, bout, gout, gx, gy, node);
+__global__ void __launch_bounds__(ST_TX * ST_BY) k_grad_rhs(MeshDev m, const R* __restrict__ u,
+                                                            R* __restrict__ bout, R* __restrict__ gout) {
+    pdl_begin();
+    constexpr int HX = ST_TX + 2 * P, HY = ST_TY + 2 * P, NW = 2 * P + 1, NCL = P + 2, NJ = ST_TY / ST_BY;
+    constexpr int FB = StFields<R, P, NC, 2>::value;
+    __shared__ R xs[FB][HY][HX];
+    __shared__ R tC[FB][HY][ST_TX], tM[FB][HY][ST_TX];
+    __shared__ R WM[NCL][NW], WC[NCL][NW];
+    const Tab<R>& T = TabSel<R>::t(P);
+    const int tid = threadIdx.y * ST_TX + threadIdx.x;
+    if (tid < NCL * NW) {
+        const int cls = tid / NW, k = tid - cls * NW;
+        WM[cls][k] = class_weight<R, P, 0>(T, cls, k - P);
+        WC[cls][k] = class_weight<R, P, 1>(T, cls, k - P);
+    }
+    const int gx0 = blockIdx.x * ST_TX, gy0 = blockIdx.y * ST_TY;
+    const int gx = gx0 + threadIdx.x;
+    const int clx = node_class<P>(gx, m.nnx, m.px);
+    const R h = PV<R>::h(m);
+    for (int v0 = 0; v0 < NC; v0 += FB) {
+        __syncthreads();  // weights ready; previous fields consumed
+#pragma unroll
+        for (int f = 0; f < FB; ++f) stage_tile<R, P>(m, u + (long long)(v0 + f) * m.NN, xs[f], gx0, gy0, tid);
+        __syncthreads();
+        // along x, every halo row: derivative (for b_x) and mass (for b_y)
+        for (int r = threadIdx.y; r < HY; r += ST_BY) {
+#pragma unroll
+            for (int f = 0; f < FB; ++f) {
+                R sc = R(0), sm = R(0);
+#pragma unroll
+                for (int k = 0; k < NW; ++k) {
+                    const R x = xs[f][r][threadIdx.x + k];
+                    sc = fma_r(WC[clx][k], x, sc);
+                    sm = fma_r(WM[clx][k], x, sm);
+                }
+                tC[f][r][threadIdx.x] = sc;
+                tM[f][r][threadIdx.x] = sm;
+            }
+        }
+        __syncthreads();
+        // along y and the outputs
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int r = threadIdx.y + j * ST_BY, gy = gy0 + r;
+            if (gx >= m.nnx || gy >= m.nny) continue;
+            const int cly = node_class<P>(gy, m.nny, m.py);
+            const int cnt = (clx == 0 ? 2 : 1) * (cly == 0 ? 2 : 1);
+            const R inv_mi = mul_r(PV<R>::inv_me(m), inv_count<R>(cnt));
+            const long long node = (long long)gy * m.nnx + gx;
+#pragma unroll
+            for (int f = 0; f < FB; ++f) {
+                const int v = v0 + f;
+                R sx = R(0), sy = R(0);
+#pragma unroll
+                for (int k = 0; k < NW; ++k) {
+                    sx = fma_r(WM[cly][k], tC[f][r + k][threadIdx.x], sx);
+                    sy = fma_r(WC[cly][k], tM[f][r + k][threadIdx.x], sy);
+                }
+                const R bx = mul_r(h, sx), by = mul_r(h, sy);
+                bout[v * m.NN + node] = bx;
+                bout[(NC + v) * m.NN + node] = by;
+                gout[v * m.NN + node] = mul_r(bx, inv_mi);
+                gout[(NC + v) * m.NN + node] = mul_r(by, inv_mi);
+            }
+        }
+    }
 }
 
 template <class R, int P, int NV>
-__global__ void k_mass_sweep(MeshDev m, const R* __restrict__ xin, const R* __restrict__ b,
-                             R* __restrict__ xout) {
-    int gx, gy;
-    long long node;
-    if (!node_of_thread(m, gx, gy, node)) return;
-    mass_sweep_at<R, P, NV>(m, xin, b, xout, gx, gy, node);
+__global__ void __launch_bounds__(ST_TX * ST_BY) k_mass_sweep(MeshDev m, const R* __restrict__ xin,
+                                                              const R* __restrict__ b, R* __restrict__ xout) {
+    pdl_begin();
+    constexpr int HX = ST_TX + 2 * P, HY = ST_TY + 2 * P, NW = 2 * P + 1, NCL = P + 2, NJ = ST_TY / ST_BY;
+    constexpr int FB = StFields<R, P, NV, 1>::value;
+    __shared__ R xs[FB][HY][HX];
+    __shared__ R t[FB][HY][ST_TX];
+    __shared__ R W[NCL][NW];
+    const Tab<R>& T = TabSel<R>::t(P);
+    const int tid = threadIdx.y * ST_TX + threadIdx.x;
+    if (tid < NCL * NW) {
+        const int cls = tid / NW, k = tid - cls * NW;
+        W[cls][k] = class_weight<R, P, 0>(T, cls, k - P);
+    }
+    const int gx0 = blockIdx.x * ST_TX, gy0 = blockIdx.y * ST_TY;
+    const int gx = gx0 + threadIdx.x;
+    const int clx = node_class<P>(gx, m.nnx, m.px);
+    const R h2 = PV<R>::h2(m);
+    for (int v0 = 0; v0 < NV; v0 += FB) {
+        // right-hand sides of this thread's nodes, loaded ahead of the barriers
+        R bv[FB][NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int gy = gy0 + threadIdx.y + j * ST_BY;
+            const bool in = gx < m.nnx && gy < m.nny;
+#pragma unroll
+            for (int f = 0; f < FB; ++f)
+                bv[f][j] = in ? b[(long long)(v0 + f) * m.NN + (long long)gy * m.nnx + gx] : R(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int f = 0; f < FB; ++f) stage_tile<R, P>(m, xin + (long long)(v0 + f) * m.NN, xs[f], gx0, gy0, tid);
+        __syncthreads();
+        for (int r = threadIdx.y; r < HY; r += ST_BY) {
+#pragma unroll
+            for (int f = 0; f < FB; ++f) {
+                R sx = R(0);
+#pragma unroll
+                for (int k = 0; k < NW; ++k) sx = fma_r(W[clx][k], xs[f][r][threadIdx.x + k], sx);
+                t[f][r][threadIdx.x] = sx;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int r = threadIdx.y + j * ST_BY, gy = gy0 + r;
+            if (gx >= m.nnx || gy >= m.nny) continue;
+            const int cly = node_class<P>(gy, m.nny, m.py);
+            const int cnt = (clx == 0 ? 2 : 1) * (cly == 0 ? 2 : 1);
+            const R inv_mi = mul_r(PV<R>::inv_me(m), inv_count<R>(cnt));
+#pragma unroll
+            for (int f = 0; f < FB; ++f) {
+                R sy = R(0);
+#pragma unroll
+                for (int k = 0; k < NW; ++k) sy = fma_r(W[cly][k], t[f][r + k][threadIdx.x], sy);
+                const long long k = (long long)(v0 + f) * m.NN + (long long)gy * m.nnx + gx;
+                xout[k] = sweep_value(xs[f][r + P][threadIdx.x + P], bv[f][j], sy, h2, inv_mi);
+            }
+        }
+    }
 }
 
 // runtime-degree candidate list (diagnostics only)
@@ -1138,7 +1306,7 @@ DEV NodeCands node_cands(const MeshDev& m, int gx, int gy) {
 //           - sum_{faces on dOmega} int phi_i F(u_h, u_hat; n)
 //   s^e_i = nu_e int grad phi_i . (grad u_h - gamma_e g_h)      eq. (stab:WENO)
 // (p+2)-point Gauss rule for nonlinear integrands; exact face mass for f_h.
-// ER layout [(e*N2 + i)*NC + c].
+// ER layout ev_at(E, e, i, c, NC).
 // ---------------------------------------------------------------------------
 template <class R, int P, class Ph>
 DEV void res_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ g,
@@ -1325,7 +1493,7 @@ DEV void res_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restr
                     gg += T.M[b][d] * Cg[d][a] + T.C[b][d] * Mg[d][a];
                 }
                 R s = nue * (ku - ge * (h * gg));
-                ER[((long long)e * N2 + b * N1 + a) * NC + c] = W[c][b * N1 + a] - s;
+                ER[ev_at(m.E, e, b * N1 + a, c, NC)] = W[c][b * N1 + a] - s;
             }
     }
 }
@@ -1334,6 +1502,7 @@ template <class R, int P, class Ph>
 __global__ void k_res_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ g,
                          const double* __restrict__ gam, const double* __restrict__ nu,
                          R* __restrict__ ER) {
+    pdl_begin();
     int ex, ey, e;
     if (!elem_of_thread(m, ex, ey, e)) return;
     res_at<R, P, Ph>(m, pr, u, g, gam, nu, ER, ex, ey, e);
@@ -1360,7 +1529,7 @@ template <class R, int P, class Ph>
 DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
                             const double* __restrict__ ue, const double* __restrict__ dte_a, const double* __restrict__ ubl,
                             const R* __restrict__ qcap, const R* __restrict__ fl_in,
-                            const R* __restrict__ ER,
+                            const R* __restrict__ ER, const float* __restrict__ cf,
                             const double* __restrict__ dtp, R* __restrict__ EW,
                             double* __restrict__ ube_out, double* __restrict__ beta_out,
                             unsigned long long* __restrict__ cnt, int ex, int ey, int e) {
@@ -1469,6 +1638,34 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
                 double fA[NC];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) fA[c] = (double)FLr[d][c] - FH[d][c];
+                if constexpr (sizeof(R) == 4) {
+                    // float32 certificate first: where both cells certainly
+                    // give alpha = 1 the float64 formula is skipped (same result)
+                    if (!(pr.opts & OPT_FP64_LIMITER)) {
+                        float fAf[NC], fAm[NC], ub[NC];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) {
+                            fAf[c] = __fsub_rn(FLr[d][c], FHr[d][c]);
+                            fAm[c] = -fAf[c];
+                        }
+                        bool one = true;
+                        if (Lc >= 0) {
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) ub[c] = cf[(1 + c) * m.E + Lc];
+                            one = euler_alpha_is_one(ub, fAf, 0.25f * cf[Lc], pr.ome_f);
+                        }
+                        if (one && Rc >= 0) {
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) ub[c] = cf[(1 + c) * m.E + Rc];
+                            one = euler_alpha_is_one(ub, fAm, 0.25f * cf[Rc], pr.ome_f);
+                        }
+                        if (one) {
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) FB[d][c] = fA[c];
+                            continue;
+                        }
+                    }
+                }
                 double alpha = 1.0;
                 if (Lc >= 0) {
                     double ub[NC];
@@ -1510,7 +1707,7 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
         for (int c = 0; c < NC; ++c)
 #pragma unroll
             for (int i = 0; i < N2; ++i)
-                EW[((long long)e * N2 + i) * NC + c] = thR * ((ubh[c] - U[c][i]) + ubo[c]);
+                EW[ev_at(m.E, e, i, c, NC)] = thR * ((ubh[c] - U[c][i]) + ubo[c]);
         beta_out[e] = 0.0;
         return;
     }
@@ -1518,7 +1715,9 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
     const R meR = PV<R>::me(m), h2 = PV<R>::h2(m), dteR = R(dte), inv_meR = PV<R>::inv_me(m);
     const R h_over_n2R = (sizeof(R) == 4) ? R(m.h_over_n2_f) : R(m.h_over_n2);
     R F[NC][N2];
-#pragma unroll 1
+    // components unrolled for p >= 3 (registers); at p <= 2 the rolled loop
+    // keeps occupancy higher (measured on the Euler workloads)
+#pragma unroll (P >= 3 ? Ph::NC : 1)
     for (int c = 0; c < NC; ++c) {
         R UD[N2];
 #pragma unroll
@@ -1547,7 +1746,7 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
 #pragma unroll
                 for (int d = 0; d < N1; ++d) s += T.M[b][d] * Y[d][a];
                 const int i = b * N1 + a;
-                R Ri = ER[((long long)e * N2 + i) * NC + c];
+                R Ri = ER[ev_at(m.E, e, i, c, NC)];
                 R dev = (U[c][i] - ueh) - uel;
                 F[c][i] = meR * dev + dteR * (((Ri + fh_term) - h2 * s) + meR * UD[i]);
             }
@@ -1571,8 +1770,20 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
             beta = fmin(fmax(b, R(0)), R(1));
         } else {
             double b = 1.0;
+            float ubf[NC];
+            const bool cert = (sizeof(R) == 4) && !(pr.opts & OPT_FP64_LIMITER);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ubf[c] = cert ? (float)ubec[c] : 0.f;
 #pragma unroll
             for (int i = 0; i < N2; ++i) {
+                // float32 certificate first; the float64 formula only where
+                // it cannot show alpha_i = 1 (min(b, 1) = b: same result)
+                if (cert) {
+                    float ff[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) ff[c] = (float)F[c][i];
+                    if (euler_alpha_is_one(ubf, ff, m.me_f, pr.ome_f)) continue;
+                }
                 double f[NC];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) f[c] = (double)F[c][i];
@@ -1586,7 +1797,7 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
     for (int c = 0; c < NC; ++c)
 #pragma unroll
         for (int i = 0; i < N2; ++i)
-            EW[((long long)e * N2 + i) * NC + c] =
+            EW[ev_at(m.E, e, i, c, NC)] =
                 thR * (((ubh[c] - U[c][i]) + ubo[c]) + (beta * F[c][i]) * inv_meR);
 }
 
@@ -1594,13 +1805,15 @@ template <class R, int P, class Ph>
 __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
                             const double* __restrict__ ue, const double* __restrict__ dte_a, const double* __restrict__ ubl,
                             const R* __restrict__ qcap, const R* __restrict__ fl_in,
-                            const R* __restrict__ ER,
+                            const R* __restrict__ ER, const float* __restrict__ cf,
                             const double* __restrict__ dtp, R* __restrict__ EW,
                             double* __restrict__ ube_out, double* __restrict__ beta_out,
                             unsigned long long* __restrict__ cnt) {
+    pdl_begin();
     int ex, ey, e;
     if (!elem_of_thread(m, ex, ey, e)) return;
-    update_at<R, P, Ph>(m, pr, u, ud, ue, dte_a, ubl, qcap, fl_in, ER, dtp, EW, ube_out, beta_out, cnt, ex, ey, e);
+    update_at<R, P, Ph>(m, pr, u, ud, ue, dte_a, ubl, qcap, fl_in, ER, cf, dtp, EW, ube_out, beta_out, cnt, ex, ey,
+                        e);
 }
 
 
@@ -1659,6 +1872,7 @@ template <class R, int P, int NC>
 __global__ void k_final(MeshDev m, ProbDev pr, const R* __restrict__ EW,
                         R* __restrict__ un, R* __restrict__ u, R a, R b,
                         unsigned long long* __restrict__ cnt) {
+    pdl_begin();
     int gx, gy;
     long long node;
     if (!node_of_thread(m, gx, gy, node)) return;

@@ -16,12 +16,13 @@ struct Bufs {
     void* bg;     // rhs of g_h       [2NC][NN] (R)
     void* r;      // target residual  [NC][NN]  (R)
     void* ud;     // udot             [NC][NN]  (R)
-    void* EV;     // element vectors  [E][N2][2NC] (R)
-    void* ER;     // element residual [E][N2][NC]  (R)
-    void* EW;     // SSP increments   [E][N2][NC]  (R)
+    void* EV;     // unused (16 bytes)
+    void* ER;     // element residual [N2][NC][E]  (R)
+    void* EW;     // SSP increments   [N2][NC][E]  (R)
     void* q;      // flux-limiter capacities [2][E] (scalar)  (R)
     void* fl;     // low-order facet fluxes [E][4][NC]         (R)
-    double *ue, *fue, *lame, *dte, *ubl, *gam, *nu, *ube, *beta;
+    float* cf;    // float copies for the Euler limiter certificate [1+NC][E]: s, ubar^{e,L}
+    double *ue, *dte, *ubl, *gam, *nu, *ube, *beta;
     unsigned long long* cnt;     // CNT_N counters
     unsigned long long* dtbits;  // min dt_e as bits
     double *dt, *t, *t_end;
@@ -64,6 +65,24 @@ typedef cudaError_t (*StageFn)(const Bufs&, const MeshDev&, const ProbDev&, doub
 
 inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// Launch with programmatic stream serialisation (pdl): the kernel may be
+// scheduled while the previous kernel of the stream drains and waits for it
+// in pdl_begin(); inside a captured graph this becomes a programmatic edge.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 template <class R, int P, class Ph>
 cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, double a, double b,
                       bool first, bool dt_only, cudaStream_t st, Prof* prof) {
@@ -72,22 +91,32 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
     constexpr int NC = Ph::NC;
     const dim3 be(64, 2), bn(128, 1);
     const dim3 ge(nblk(m.nx, 64), nblk(m.ny, 2)), gn(nblk(m.nnx, 128), m.nny);
+    const dim3 bt(ST_TX, ST_BY), gt(nblk(m.nnx, ST_TX), nblk(m.nny, ST_TY));  // tiled stencils
+    // per-launch timing records events between kernels: plain launches then
+    const bool pdl = prof == nullptr;
+    cudaError_t err = cudaSuccess;
+    auto chk = [&](cudaError_t e) {
+        if (e != cudaSuccess && err == cudaSuccess) err = e;
+    };
     R* u = (R*)B.u;
     CGL_LAUNCH(prof, KID_PRE, st,
-               (k_pre<R, P, Ph><<<ge, be, 0, st>>>(m, pr, u, B.ue, B.dte, B.ubl, B.gam, B.nu, (R*)B.q, (R*)B.fl,
-                                                  nullptr, first ? B.dtbits : nullptr)));
+               chk(launch(pdl, k_pre<R, P, Ph>, ge, be, st, m, pr, (const R*)u, B.ue, B.dte, B.ubl, B.gam, B.nu,
+                          (R*)B.q, (R*)B.fl, (R*)nullptr, B.cf, first ? B.dtbits : nullptr)));
     if (first)
-        CGL_LAUNCH(prof, KID_DT, st, (k_dt_final<<<1, 1, 0, st>>>(B.dtbits, pr.cfl, B.t, B.t_end, B.dt)));
-    if (dt_only) return cudaGetLastError();
+        CGL_LAUNCH(prof, KID_DT, st,
+                   chk(launch(pdl, k_dt_final, dim3(1), dim3(1), st, B.dtbits, pr.cfl, (const double*)B.t,
+                              (const double*)B.t_end, B.dt)));
+    if (dt_only) return err != cudaSuccess ? err : cudaGetLastError();
     R* ud = (R*)B.ud;
     if (pr.mode != MODE_LO) {
         // g_h: stencil right-hand side and lumped iterate, then k_g sweeps (ping-pong)
         R* g = (R*)B.g;
         R* g2 = (R*)B.g2;
         R* bg = (R*)B.bg;
-        CGL_LAUNCH(prof, KID_GRAD, st, (k_grad_rhs<R, P, NC><<<gn, bn, 0, st>>>(m, u, bg, g)));
+        CGL_LAUNCH(prof, KID_GRAD, st, chk(launch(pdl, k_grad_rhs<R, P, NC>, gt, bt, st, m, (const R*)u, bg, g)));
         for (int k = 0; k < pr.k_g; ++k) {
-            CGL_LAUNCH(prof, KID_SWEEP, st, (k_mass_sweep<R, P, 2 * NC><<<gn, bn, 0, st>>>(m, g, bg, g2)));
+            CGL_LAUNCH(prof, KID_SWEEP, st,
+                       chk(launch(pdl, k_mass_sweep<R, P, 2 * NC>, gt, bt, st, m, (const R*)g, (const R*)bg, g2)));
             R* t = g;
             g = g2;
             g2 = t;
@@ -95,23 +124,28 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
         R* ER = (R*)B.ER;
         R* r = (R*)B.r;
         R* ud2 = (R*)B.ud2;
-        CGL_LAUNCH(prof, KID_RES, st, (k_res_ev<R, P, Ph><<<ge, be, 0, st>>>(m, pr, u, g, B.gam, B.nu, ER)));
-        CGL_LAUNCH(prof, KID_GATHER, st, (k_gather_init<R, P, NC><<<gn, bn, 0, st>>>(m, ER, r, ud)));
+        CGL_LAUNCH(prof, KID_RES, st,
+                   chk(launch(pdl, k_res_ev<R, P, Ph>, ge, be, st, m, pr, (const R*)u, (const R*)g,
+                              (const double*)B.gam, (const double*)B.nu, ER)));
+        CGL_LAUNCH(prof, KID_GATHER, st,
+                   chk(launch(pdl, k_gather_init<R, P, NC>, gn, bn, st, m, (const R*)ER, r, ud)));
         for (int k = 0; k < pr.k_u; ++k) {
-            CGL_LAUNCH(prof, KID_SWEEP, st, (k_mass_sweep<R, P, NC><<<gn, bn, 0, st>>>(m, ud, r, ud2)));
+            CGL_LAUNCH(prof, KID_SWEEP, st,
+                       chk(launch(pdl, k_mass_sweep<R, P, NC>, gt, bt, st, m, (const R*)ud, (const R*)r, ud2)));
             R* t = ud;
             ud = ud2;
             ud2 = t;
         }
     }
     CGL_LAUNCH(prof, KID_UPDATE, st,
-               (k_update_ev<R, P, Ph><<<ge, be, 0, st>>>(m, pr, u, (const R*)ud, B.ue, B.dte, B.ubl, (const R*)B.q, (const R*)B.fl,
-                                                        (const R*)B.ER, B.dt, (R*)B.EW, B.ube, B.beta,
-                                                        B.cnt)));
+               chk(launch(pdl, k_update_ev<R, P, Ph>, ge, be, st, m, pr, (const R*)u, (const R*)ud,
+                          (const double*)B.ue, (const double*)B.dte, (const double*)B.ubl, (const R*)B.q,
+                          (const R*)B.fl, (const R*)B.ER, (const float*)B.cf, (const double*)B.dt, (R*)B.EW,
+                          B.ube, B.beta, B.cnt)));
     CGL_LAUNCH(prof, KID_FINAL, st,
-               (k_final<R, P, NC><<<gn, bn, 0, st>>>(m, pr, (const R*)B.EW, (R*)B.un, u, R(a), R(b),
-                                                    B.cnt)));
-    return cudaGetLastError();
+               chk(launch(pdl, k_final<R, P, NC>, gn, bn, st, m, pr, (const R*)B.EW, (R*)B.un, u, R(a), R(b),
+                          B.cnt)));
+    return err != cudaSuccess ? err : cudaGetLastError();
 }
 
 template <class Ph>

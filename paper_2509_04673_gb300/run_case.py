@@ -26,6 +26,8 @@ def main():
     ap.add_argument("--p", type=int, default=0, help="degree (0 = the workload's own)")
     ap.add_argument("--prec", type=int, default=1, help="0 FP64, 1 FP32-mixed")
     ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--profile", type=int, default=0,
+                    help="also time every kernel over this many steps (CUDA events per launch)")
     a = ap.parse_args()
     import torch
     import inputs
@@ -55,7 +57,13 @@ def main():
     torch.cuda.synchronize()
     ndof = u0.size
     info.update(workload=a.workload, n=a.n, p=mesh.p, prec=a.prec, n_dof=ndof,
-                ms=ev0.elapsed_time(ev1))
+                ms=ev0.elapsed_time(ev1),
+                dof_stage_per_s=ndof * 3 * info["steps"] / (ev0.elapsed_time(ev1) * 1e-3))
+    if a.profile:
+        prof = st.profile(a.profile)
+        tot = sum(ms for ms, n in prof.values() if n)
+        info["kernels"] = {k: {"ms": round(ms, 4), "launches": n, "share": round(ms / tot, 4)}
+                           for k, (ms, n) in prof.items() if n}
     print(json.dumps(info))
     st.close()
     return 0 if info["violations"] == 0 else 1
