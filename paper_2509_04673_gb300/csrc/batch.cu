@@ -164,7 +164,8 @@ DEV void elem_loop(int phase, const InstDev* __restrict__ I, const Tile* __restr
         double dte = __longlong_as_double(0x7ff0000000000000LL);
         if ((int)threadIdx.x < T.count) {
             const int e = T.begin + threadIdx.x;
-            const int ey = e / D.m.nx, ex = e - ey * D.m.nx;
+            const int nx = D.m.nx;
+            const int ey = e / nx, ex = e - ey * nx;
             elem_dispatch(phase, D, ex, ey, e, dte, kg, ku);
         }
         if (phase == PH_PRE && first) block_min_to(dte, D.dtbits);
@@ -177,15 +178,19 @@ DEV void node_loop(int phase, const InstDev* __restrict__ I, const Tile* __restr
         const Tile T = nt[t];
         if ((int)threadIdx.x < T.count) {
             const InstDev& D = I[T.inst];
-            const long long node = (long long)T.begin + threadIdx.x;
-            const int gy = (int)(node / D.m.nnx), gx = (int)(node - (long long)gy * D.m.nnx);
-            node_dispatch(phase, D, gx, gy, node, a, b, k);
+            // an instance has fewer than 2^31 nodes: 32-bit index arithmetic
+            const int node = T.begin + (int)threadIdx.x;
+            const int nnx = D.m.nnx;
+            const int gy = node / nnx, gx = node - gy * nnx;
+            node_dispatch(phase, D, gx, gy, (long long)node, a, b, k);
         }
     }
 }
 
 // one SSP stage u <- a u^n + b FE(u) for every instance
-__global__ void __launch_bounds__(BT)
+// 4 blocks per SM: the register cap (128) costs a few spills in the p = 4
+// element phases but doubles the warps that hide the latency of the tile loops
+__global__ void __launch_bounds__(BT, 4)
     k_batch_stage(const InstDev* __restrict__ I, int ninst, const Tile* __restrict__ et, int net,
                   const Tile* __restrict__ nt, int nnt, BatchSync* sync, float a, float b, int first,
                   int last, int kg, int ku, int mode_lo, long long limit) {
