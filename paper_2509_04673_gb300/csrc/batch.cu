@@ -41,7 +41,7 @@ struct InstDev {
 };
 
 struct Tile {
-    int inst, begin, count, pad;
+    int inst, begin, count, pad;  // element tiles: a run of elements; node tiles: begin = gx0, count = gy0
 };
 
 struct BatchSync {
@@ -55,6 +55,15 @@ enum { PH_PRE = 0, PH_RES, PH_UPDATE };
 enum { PH_GRAD = 0, PH_SWEEP_G, PH_GATHER_R, PH_SWEEP_U, PH_FINAL };
 
 constexpr int BT = 128;  // threads per block of the persistent grid
+constexpr int BY = BT / ST_TX;  // node tiles of ST_TX x ST_TY nodes: the block as 32 x BY threads
+
+// shared workspace of the tiled stencils, the largest over the degrees
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+template <int P>
+constexpr int ws_deg() {
+    return cmax(StFields<float, P, 1, 2>::ws, cmax(StFields<float, P, 2, 1>::ws, StFields<float, P, 1, 1>::ws));
+}
+constexpr int WS_MAX = cmax(cmax(ws_deg<1>(), ws_deg<2>()), cmax(ws_deg<3>(), ws_deg<4>()));
 
 // bounded grid barrier: returns false if it gave up (or another block did)
 DEV bool grid_sync(BatchSync* s, long long limit) {
@@ -129,30 +138,44 @@ DEV void elem_dispatch(int phase, const InstDev& D, int ex, int ey, int e, doubl
     }
 }
 
+// node phases on one ST_TX x ST_TY node tile of an instance: the stencils
+// (g_h right-hand side, Richardson sweeps) with the tiled shared-memory
+// functions of the single-state kernels, the gathers node by node
+// (ST_TY / BY nodes per thread)
 template <int P>
-__device__ __noinline__ void node_phase(int phase, const InstDev& D, int gx, int gy, long long node, float a,
-                                        float b, int k) {
+__device__ __noinline__ void node_phase(int phase, const InstDev& D, int gx0, int gy0, float a, float b, int k,
+                                        float* ws) {
+    const int tx = threadIdx.x % ST_TX, ty = threadIdx.x / ST_TX;
     switch (phase) {
-        case PH_GRAD: grad_rhs_at<float, P, 1>(D.m, D.u, D.bg, D.g, gx, gy, node); break;
+        case PH_GRAD: grad_tile<float, P, 1, BY>(D.m, D.u, D.bg, D.g, gx0, gy0, tx, ty, ws); break;
         case PH_SWEEP_G:
-            if (k & 1) mass_sweep_at<float, P, 2>(D.m, D.g2, D.bg, D.g, gx, gy, node);
-            else mass_sweep_at<float, P, 2>(D.m, D.g, D.bg, D.g2, gx, gy, node);
+            if (k & 1) sweep_tile<float, P, 2, BY>(D.m, D.g2, D.bg, D.g, gx0, gy0, tx, ty, ws);
+            else sweep_tile<float, P, 2, BY>(D.m, D.g, D.bg, D.g2, gx0, gy0, tx, ty, ws);
             break;
-        case PH_GATHER_R: gather_init_at<float, P, 1>(D.m, D.ER, D.r, D.ud, gx, gy, node); break;
         case PH_SWEEP_U:
-            if (k & 1) mass_sweep_at<float, P, 1>(D.m, D.ud2, D.r, D.ud, gx, gy, node);
-            else mass_sweep_at<float, P, 1>(D.m, D.ud, D.r, D.ud2, gx, gy, node);
+            if (k & 1) sweep_tile<float, P, 1, BY>(D.m, D.ud2, D.r, D.ud, gx0, gy0, tx, ty, ws);
+            else sweep_tile<float, P, 1, BY>(D.m, D.ud, D.r, D.ud2, gx0, gy0, tx, ty, ws);
             break;
-        default: final_at<float, P, 1>(D.m, D.pr, D.EW, D.un, D.u, a, b, D.cnt, gx, gy, node);
+        default: {
+            const int gx = gx0 + tx, nnx = D.m.nnx, nny = D.m.nny;
+#pragma unroll
+            for (int j = 0; j < ST_TY / BY; ++j) {
+                const int gy = gy0 + ty + j * BY;
+                if (gx >= nnx || gy >= nny) continue;
+                const long long node = (long long)gy * nnx + gx;
+                if (phase == PH_GATHER_R) gather_init_at<float, P, 1>(D.m, D.ER, D.r, D.ud, gx, gy, node);
+                else final_at<float, P, 1>(D.m, D.pr, D.EW, D.un, D.u, a, b, D.cnt, gx, gy, node);
+            }
+        }
     }
 }
 
-DEV void node_dispatch(int phase, const InstDev& D, int gx, int gy, long long node, float a, float b, int k) {
+DEV void node_dispatch(int phase, const InstDev& D, int gx0, int gy0, float a, float b, int k, float* ws) {
     switch (D.p) {
-        case 1: node_phase<1>(phase, D, gx, gy, node, a, b, k); break;
-        case 2: node_phase<2>(phase, D, gx, gy, node, a, b, k); break;
-        case 3: node_phase<3>(phase, D, gx, gy, node, a, b, k); break;
-        default: node_phase<4>(phase, D, gx, gy, node, a, b, k); break;
+        case 1: node_phase<1>(phase, D, gx0, gy0, a, b, k, ws); break;
+        case 2: node_phase<2>(phase, D, gx0, gy0, a, b, k, ws); break;
+        case 3: node_phase<3>(phase, D, gx0, gy0, a, b, k, ws); break;
+        default: node_phase<4>(phase, D, gx0, gy0, a, b, k, ws); break;
     }
 }
 
@@ -172,18 +195,12 @@ DEV void elem_loop(int phase, const InstDev* __restrict__ I, const Tile* __restr
     }
 }
 
+// every block takes whole node tiles (the tiled stencils synchronise the block)
 DEV void node_loop(int phase, const InstDev* __restrict__ I, const Tile* __restrict__ nt, int nnt, float a,
-                   float b, int k) {
+                   float b, int k, float* ws) {
     for (int t = blockIdx.x; t < nnt; t += gridDim.x) {
         const Tile T = nt[t];
-        if ((int)threadIdx.x < T.count) {
-            const InstDev& D = I[T.inst];
-            // an instance has fewer than 2^31 nodes: 32-bit index arithmetic
-            const int node = T.begin + (int)threadIdx.x;
-            const int nnx = D.m.nnx;
-            const int gy = node / nnx, gx = node - gy * nnx;
-            node_dispatch(phase, D, gx, gy, (long long)node, a, b, k);
-        }
+        node_dispatch(phase, I[T.inst], T.begin, T.count, a, b, k, ws);
     }
 }
 
@@ -194,6 +211,7 @@ __global__ void __launch_bounds__(BT, 4)
     k_batch_stage(const InstDev* __restrict__ I, int ninst, const Tile* __restrict__ et, int net,
                   const Tile* __restrict__ nt, int nnt, BatchSync* sync, float a, float b, int first,
                   int last, int kg, int ku, int mode_lo, long long limit) {
+    __shared__ float ws[WS_MAX];
     elem_loop(PH_PRE, I, et, net, first != 0, kg, ku);
     if (!grid_sync(sync, limit)) return;
     if (first) {
@@ -210,24 +228,24 @@ __global__ void __launch_bounds__(BT, 4)
         if (mode_lo && !grid_sync(sync, limit)) return;
     }
     if (!mode_lo) {
-        node_loop(PH_GRAD, I, nt, nnt, a, b, 0);
+        node_loop(PH_GRAD, I, nt, nnt, a, b, 0, ws);
         if (!grid_sync(sync, limit)) return;
         for (int k = 0; k < kg; ++k) {
-            node_loop(PH_SWEEP_G, I, nt, nnt, a, b, k);
+            node_loop(PH_SWEEP_G, I, nt, nnt, a, b, k, ws);
             if (!grid_sync(sync, limit)) return;
         }
         elem_loop(PH_RES, I, et, net, false, kg, ku);
         if (!grid_sync(sync, limit)) return;
-        node_loop(PH_GATHER_R, I, nt, nnt, a, b, 0);
+        node_loop(PH_GATHER_R, I, nt, nnt, a, b, 0, ws);
         if (!grid_sync(sync, limit)) return;
         for (int k = 0; k < ku; ++k) {
-            node_loop(PH_SWEEP_U, I, nt, nnt, a, b, k);
+            node_loop(PH_SWEEP_U, I, nt, nnt, a, b, k, ws);
             if (!grid_sync(sync, limit)) return;
         }
     }
     elem_loop(PH_UPDATE, I, et, net, false, kg, ku);
     if (!grid_sync(sync, limit)) return;
-    node_loop(PH_FINAL, I, nt, nnt, a, b, 0);
+    node_loop(PH_FINAL, I, nt, nnt, a, b, 0, ws);
     if (last) {
         for (int i = blockIdx.x * BT + threadIdx.x; i < ninst; i += gridDim.x * BT) *I[i].t += *I[i].dt;
     }
@@ -270,9 +288,8 @@ static cgl_status build_tiles(cgl_batch* B) {
         const MeshDev& m = B->states[i]->mesh->m;
         const int T = std::max(1, std::min(BT, B->tile_elems[m.p]));
         for (int b = 0; b < m.E; b += T) et.push_back(Tile{i, b, std::min(T, m.E - b), 0});
-        const int TN = BT;
-        for (long long b = 0; b < m.NN; b += TN)
-            nt.push_back(Tile{i, (int)b, (int)std::min<long long>(TN, m.NN - b), 0});
+        for (int gy0 = 0; gy0 < m.nny; gy0 += ST_TY)
+            for (int gx0 = 0; gx0 < m.nnx; gx0 += ST_TX) nt.push_back(Tile{i, gx0, gy0, 0});
     }
     if (B->d_et) cudaFree(B->d_et);
     if (B->d_nt) cudaFree(B->d_nt);
@@ -368,7 +385,7 @@ extern "C" cgl_status cgl_batch_create(cgl_state* const* states, int32_t n, cgl_
     B->ku = s0->prob.k_u;
     B->limit = 1LL << 22;
     B->phantom = 0;
-    B->node_tile = BT;
+    B->node_tile = ST_TX * ST_TY;
     B->use_graph = true;
     for (int p = 0; p <= PMAX; ++p) B->tile_elems[p] = BT;
     std::vector<InstDev> h(n);

@@ -1098,10 +1098,10 @@ DEV R class_weight(const Tab<R>& T, int cls, int off) {
 }
 
 // stage one field (rows gy0-P.., columns gx0-P..) of the tile in shared memory
-template <class R, int P>
+template <class R, int P, int BY>
 DEV void stage_tile(const MeshDev& m, const R* __restrict__ x, R (*xs)[ST_TX + 2 * P], int gx0, int gy0, int tid) {
     constexpr int HX = ST_TX + 2 * P, HY = ST_TY + 2 * P;
-    for (int i = tid; i < HX * HY; i += ST_TX * ST_BY) {
+    for (int i = tid; i < HX * HY; i += ST_TX * BY) {
         const int r = i / HX, c = i - r * HX;
         int gy = gy0 - P + r, gx = gx0 - P + c;
         bool in = true;
@@ -1122,53 +1122,61 @@ struct StFields {
     static constexpr int value = (bytes(NV) <= 32768) ? NV
                                  : (NV % 4 == 0 && bytes(4) <= 32768) ? 4
                                  : (NV % 2 == 0 && bytes(2) <= 32768) ? 2 : 1;
+    // shared workspace in elements of R: staged fields, NT pass-1 arrays
+    // per field, NT class-weight tables
+    static constexpr int ws = value * (HY * HX + NT * HY * ST_TX) + NT * (P + 2) * (2 * P + 1);
 };
 
-template <class R, int P, int NC>
-__global__ void __launch_bounds__(ST_TX * ST_BY) k_grad_rhs(MeshDev m, const R* __restrict__ u,
-                                                            R* __restrict__ bout, R* __restrict__ gout) {
-    pdl_begin();
-    constexpr int HX = ST_TX + 2 * P, HY = ST_TY + 2 * P, NW = 2 * P + 1, NCL = P + 2, NJ = ST_TY / ST_BY;
+// g_h right-hand side and lumped iterate on the 32 x 16 node tile at
+// (gx0, gy0) by a block of 32 x BY threads (thread (tx, ty)); ws: shared
+// workspace of StFields<R, P, NC, 2>::ws elements.  All threads of the block
+// call it together.
+template <class R, int P, int NC, int BY>
+DEV void grad_tile(const MeshDev& m, const R* __restrict__ u, R* __restrict__ bout, R* __restrict__ gout,
+                   int gx0, int gy0, int tx, int ty, R* ws) {
+    constexpr int HX = ST_TX + 2 * P, HY = ST_TY + 2 * P, NW = 2 * P + 1, NCL = P + 2, NJ = ST_TY / BY;
     constexpr int FB = StFields<R, P, NC, 2>::value;
-    __shared__ R xs[FB][HY][HX];
-    __shared__ R tC[FB][HY][ST_TX], tM[FB][HY][ST_TX];
-    __shared__ R WM[NCL][NW], WC[NCL][NW];
+    R(*xs)[HY][HX] = reinterpret_cast<R(*)[HY][HX]>(ws);
+    R(*tC)[HY][ST_TX] = reinterpret_cast<R(*)[HY][ST_TX]>(ws + FB * HY * HX);
+    R(*tM)[HY][ST_TX] = reinterpret_cast<R(*)[HY][ST_TX]>(ws + FB * HY * HX + FB * HY * ST_TX);
+    R(*WM)[NW] = reinterpret_cast<R(*)[NW]>(ws + FB * (HY * HX + 2 * HY * ST_TX));
+    R(*WC)[NW] = reinterpret_cast<R(*)[NW]>(ws + FB * (HY * HX + 2 * HY * ST_TX) + NCL * NW);
     const Tab<R>& T = TabSel<R>::t(P);
-    const int tid = threadIdx.y * ST_TX + threadIdx.x;
+    const int tid = ty * ST_TX + tx;
+    __syncthreads();  // the workspace is free
     if (tid < NCL * NW) {
         const int cls = tid / NW, k = tid - cls * NW;
         WM[cls][k] = class_weight<R, P, 0>(T, cls, k - P);
         WC[cls][k] = class_weight<R, P, 1>(T, cls, k - P);
     }
-    const int gx0 = blockIdx.x * ST_TX, gy0 = blockIdx.y * ST_TY;
-    const int gx = gx0 + threadIdx.x;
+    const int gx = gx0 + tx;
     const int clx = node_class<P>(gx, m.nnx, m.px);
     const R h = PV<R>::h(m);
     for (int v0 = 0; v0 < NC; v0 += FB) {
-        __syncthreads();  // weights ready; previous fields consumed
+        if (v0 > 0) __syncthreads();  // previous fields consumed
 #pragma unroll
-        for (int f = 0; f < FB; ++f) stage_tile<R, P>(m, u + (long long)(v0 + f) * m.NN, xs[f], gx0, gy0, tid);
+        for (int f = 0; f < FB; ++f) stage_tile<R, P, BY>(m, u + (long long)(v0 + f) * m.NN, xs[f], gx0, gy0, tid);
         __syncthreads();
         // along x, every halo row: derivative (for b_x) and mass (for b_y)
-        for (int r = threadIdx.y; r < HY; r += ST_BY) {
+        for (int r = ty; r < HY; r += BY) {
 #pragma unroll
             for (int f = 0; f < FB; ++f) {
                 R sc = R(0), sm = R(0);
 #pragma unroll
                 for (int k = 0; k < NW; ++k) {
-                    const R x = xs[f][r][threadIdx.x + k];
+                    const R x = xs[f][r][tx + k];
                     sc = fma_r(WC[clx][k], x, sc);
                     sm = fma_r(WM[clx][k], x, sm);
                 }
-                tC[f][r][threadIdx.x] = sc;
-                tM[f][r][threadIdx.x] = sm;
+                tC[f][r][tx] = sc;
+                tM[f][r][tx] = sm;
             }
         }
         __syncthreads();
         // along y and the outputs
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
-            const int r = threadIdx.y + j * ST_BY, gy = gy0 + r;
+            const int r = ty + j * BY, gy = gy0 + r;
             if (gx >= m.nnx || gy >= m.nny) continue;
             const int cly = node_class<P>(gy, m.nny, m.py);
             const int cnt = (clx == 0 ? 2 : 1) * (cly == 0 ? 2 : 1);
@@ -1180,8 +1188,8 @@ __global__ void __launch_bounds__(ST_TX * ST_BY) k_grad_rhs(MeshDev m, const R* 
                 R sx = R(0), sy = R(0);
 #pragma unroll
                 for (int k = 0; k < NW; ++k) {
-                    sx = fma_r(WM[cly][k], tC[f][r + k][threadIdx.x], sx);
-                    sy = fma_r(WC[cly][k], tM[f][r + k][threadIdx.x], sy);
+                    sx = fma_r(WM[cly][k], tC[f][r + k][tx], sx);
+                    sy = fma_r(WC[cly][k], tM[f][r + k][tx], sy);
                 }
                 const R bx = mul_r(h, sx), by = mul_r(h, sy);
                 bout[v * m.NN + node] = bx;
@@ -1193,23 +1201,24 @@ __global__ void __launch_bounds__(ST_TX * ST_BY) k_grad_rhs(MeshDev m, const R* 
     }
 }
 
-template <class R, int P, int NV>
-__global__ void __launch_bounds__(ST_TX * ST_BY) k_mass_sweep(MeshDev m, const R* __restrict__ xin,
-                                                              const R* __restrict__ b, R* __restrict__ xout) {
-    pdl_begin();
-    constexpr int HX = ST_TX + 2 * P, HY = ST_TY + 2 * P, NW = 2 * P + 1, NCL = P + 2, NJ = ST_TY / ST_BY;
+// one Richardson sweep for NV fields on the 32 x 16 node tile at (gx0, gy0);
+// ws: StFields<R, P, NV, 1>::ws elements of shared memory
+template <class R, int P, int NV, int BY>
+DEV void sweep_tile(const MeshDev& m, const R* __restrict__ xin, const R* __restrict__ b, R* __restrict__ xout,
+                    int gx0, int gy0, int tx, int ty, R* ws) {
+    constexpr int HX = ST_TX + 2 * P, HY = ST_TY + 2 * P, NW = 2 * P + 1, NCL = P + 2, NJ = ST_TY / BY;
     constexpr int FB = StFields<R, P, NV, 1>::value;
-    __shared__ R xs[FB][HY][HX];
-    __shared__ R t[FB][HY][ST_TX];
-    __shared__ R W[NCL][NW];
+    R(*xs)[HY][HX] = reinterpret_cast<R(*)[HY][HX]>(ws);
+    R(*t)[HY][ST_TX] = reinterpret_cast<R(*)[HY][ST_TX]>(ws + FB * HY * HX);
+    R(*W)[NW] = reinterpret_cast<R(*)[NW]>(ws + FB * (HY * HX + HY * ST_TX));
     const Tab<R>& T = TabSel<R>::t(P);
-    const int tid = threadIdx.y * ST_TX + threadIdx.x;
+    const int tid = ty * ST_TX + tx;
+    __syncthreads();  // the workspace is free
     if (tid < NCL * NW) {
         const int cls = tid / NW, k = tid - cls * NW;
         W[cls][k] = class_weight<R, P, 0>(T, cls, k - P);
     }
-    const int gx0 = blockIdx.x * ST_TX, gy0 = blockIdx.y * ST_TY;
-    const int gx = gx0 + threadIdx.x;
+    const int gx = gx0 + tx;
     const int clx = node_class<P>(gx, m.nnx, m.px);
     const R h2 = PV<R>::h2(m);
     for (int v0 = 0; v0 < NV; v0 += FB) {
@@ -1217,29 +1226,29 @@ __global__ void __launch_bounds__(ST_TX * ST_BY) k_mass_sweep(MeshDev m, const R
         R bv[FB][NJ];
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
-            const int gy = gy0 + threadIdx.y + j * ST_BY;
+            const int gy = gy0 + ty + j * BY;
             const bool in = gx < m.nnx && gy < m.nny;
 #pragma unroll
             for (int f = 0; f < FB; ++f)
                 bv[f][j] = in ? b[(long long)(v0 + f) * m.NN + (long long)gy * m.nnx + gx] : R(0);
         }
-        __syncthreads();
+        if (v0 > 0) __syncthreads();
 #pragma unroll
-        for (int f = 0; f < FB; ++f) stage_tile<R, P>(m, xin + (long long)(v0 + f) * m.NN, xs[f], gx0, gy0, tid);
+        for (int f = 0; f < FB; ++f) stage_tile<R, P, BY>(m, xin + (long long)(v0 + f) * m.NN, xs[f], gx0, gy0, tid);
         __syncthreads();
-        for (int r = threadIdx.y; r < HY; r += ST_BY) {
+        for (int r = ty; r < HY; r += BY) {
 #pragma unroll
             for (int f = 0; f < FB; ++f) {
                 R sx = R(0);
 #pragma unroll
-                for (int k = 0; k < NW; ++k) sx = fma_r(W[clx][k], xs[f][r][threadIdx.x + k], sx);
-                t[f][r][threadIdx.x] = sx;
+                for (int k = 0; k < NW; ++k) sx = fma_r(W[clx][k], xs[f][r][tx + k], sx);
+                t[f][r][tx] = sx;
             }
         }
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
-            const int r = threadIdx.y + j * ST_BY, gy = gy0 + r;
+            const int r = ty + j * BY, gy = gy0 + r;
             if (gx >= m.nnx || gy >= m.nny) continue;
             const int cly = node_class<P>(gy, m.nny, m.py);
             const int cnt = (clx == 0 ? 2 : 1) * (cly == 0 ? 2 : 1);
@@ -1248,12 +1257,30 @@ __global__ void __launch_bounds__(ST_TX * ST_BY) k_mass_sweep(MeshDev m, const R
             for (int f = 0; f < FB; ++f) {
                 R sy = R(0);
 #pragma unroll
-                for (int k = 0; k < NW; ++k) sy = fma_r(W[cly][k], t[f][r + k][threadIdx.x], sy);
+                for (int k = 0; k < NW; ++k) sy = fma_r(W[cly][k], t[f][r + k][tx], sy);
                 const long long k = (long long)(v0 + f) * m.NN + (long long)gy * m.nnx + gx;
-                xout[k] = sweep_value(xs[f][r + P][threadIdx.x + P], bv[f][j], sy, h2, inv_mi);
+                xout[k] = sweep_value(xs[f][r + P][tx + P], bv[f][j], sy, h2, inv_mi);
             }
         }
     }
+}
+
+template <class R, int P, int NC>
+__global__ void __launch_bounds__(ST_TX * ST_BY) k_grad_rhs(MeshDev m, const R* __restrict__ u,
+                                                            R* __restrict__ bout, R* __restrict__ gout) {
+    pdl_begin();
+    __shared__ R ws[StFields<R, P, NC, 2>::ws];
+    grad_tile<R, P, NC, ST_BY>(m, u, bout, gout, blockIdx.x * ST_TX, blockIdx.y * ST_TY, threadIdx.x, threadIdx.y,
+                               ws);
+}
+
+template <class R, int P, int NV>
+__global__ void __launch_bounds__(ST_TX * ST_BY) k_mass_sweep(MeshDev m, const R* __restrict__ xin,
+                                                              const R* __restrict__ b, R* __restrict__ xout) {
+    pdl_begin();
+    __shared__ R ws[StFields<R, P, NV, 1>::ws];
+    sweep_tile<R, P, NV, ST_BY>(m, xin, b, xout, blockIdx.x * ST_TX, blockIdx.y * ST_TY, threadIdx.x, threadIdx.y,
+                                ws);
 }
 
 // runtime-degree candidate list (diagnostics only)
