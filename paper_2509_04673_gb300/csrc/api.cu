@@ -436,7 +436,7 @@ extern "C" cgl_status cgl_state_create(const cgl_mesh* mesh, int32_t ncomp, int3
         {&B.g2, 2 * nc * NN * r},     {&B.ud2, nc * NN * r},
         {&B.bg, 2 * nc * NN * r},     {&B.r, nc * NN * r},         {&B.ud, nc * NN * r},
         {&B.EV, 16},                  {&B.ER, E * N2 * nc * r},    {&B.EW, E * N2 * nc * r},     {(void**)&B.q, 2 * E * r},
-        {(void**)&B.ue, nc * E * 8},  {(void**)&B.cf, (1 + nc) * E * 4},
+        {(void**)&B.ue, nc * E * 8},  {(void**)&B.cf, (1 + nc) * E * 4},  {(void**)&B.avg, 2 * nc * E * 4},
         {(void**)&B.dte, 3 * E * 8},  {(void**)&B.fl, 4 * nc * E * r},      {(void**)&B.ubl, nc * E * 8}, {(void**)&B.gam, E * 8},
         {(void**)&B.nu, E * 8},       {(void**)&B.ube, nc * E * 8}, {(void**)&B.beta, E * 8},
         {(void**)&B.cnt, CNT_N * 8},  {(void**)&B.dtbits, 8},      {(void**)&B.dt, 8},
@@ -839,7 +839,7 @@ extern "C" cgl_status cgl_time_step(cgl_state* S, double* dt) {
 // per-kernel timing
 // ---------------------------------------------------------------------------
 static const char* const KNAMES[KID_COUNT] = {
-    "k_avg(merged)", "k_pre", "k_dt", "k_grad_rhs", "k_gather_init", "k_mass_ev(unused)", "k_mass_sweep",
+    "k_avg", "k_pre", "k_dt", "k_grad_rhs", "k_gather_init", "k_mass_ev(unused)", "k_mass_sweep",
     "k_res_ev", "k_update_ev", "k_final", "k_t_advance", "copy_u_un"};
 
 // fixed-length delay (bounded both by a cycle count and by an iteration cap;
@@ -908,6 +908,7 @@ extern "C" cgl_status cgl_launches_per_step(cgl_state* S, int64_t* kernels) {
     if (!S->has_problem) return fail(CGL_EINVAL, "cgl_set_problem first");
     const int lo = S->prob.mode == CGL_MODE_LO;
     int64_t per_stage = 1 + 2 + (lo ? 0 : 3 + (S->prob.k_g + S->prob.k_u));
+    if (S->prec == CGL_FP32_MIXED && S->nc > 1) per_stage += 1;  // k_avg
     *kernels = 3 * per_stage + 1 + 1;  // + dt finalisation (1) + time advance (1)
     return CGL_OK;
 }

@@ -110,7 +110,7 @@ __device__ __noinline__ void elem_phase(int phase, const InstDev& D, int ex, int
     switch (phase) {
         case PH_PRE:
             dte = pre_at<float, P, Ph>(D.m, D.pr, D.u, D.ue, D.dte, D.ubl, D.gam, D.nu, D.q, D.fl, nullptr, nullptr,
-                                       ex, ey, e);
+                                       nullptr, ex, ey, e);
             break;
         case PH_RES:
             res_at<float, P, Ph>(D.m, D.pr, D.u, g_final(D, kg), D.gam, D.nu, D.ER, ex, ey, e);

@@ -542,7 +542,7 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
                         double* __restrict__ ubl_out, double* __restrict__ gam_out,
                         double* __restrict__ nu_out, float* __restrict__ q_out,
                         float* __restrict__ fl_out, float* __restrict__ EV, float* __restrict__ cf_out,
-                        int ex, int ey, int e) {
+                        const float* __restrict__ avg, int ex, int ey, int e) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
     int nb[4];
 #pragma unroll
@@ -560,24 +560,36 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
     Ph::template flux<float>(uh, fxs, fys, pr);
     // neighbours: means, fluxes (and, for scalars, the blocks for the sensor)
     float oh[4][NC], ol[4][NC], ofx[4][NC], ofy[4][NC];
-    float V1[4][N2];
+    // scalars at p <= 2 keep the neighbour blocks for the sensor; at p >= 3
+    // the sensor reloads them (registers, hence occupancy, matter more)
+    constexpr bool keepV = (NC == 1) && (P <= 2);
+    float V1[keepV ? 4 : 1][keepV ? N2 : 1];
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
         if (nb[d] >= 0) {
-            const int jx = nb[d] % m.nx, jy = nb[d] / m.nx;
-            float B[NC][N2];
-            load_block<float, P, NC>(u, m, jx, jy, B);
+            if constexpr (NC > 1) {
+                // systems: the neighbours' float-float means from k_avg
 #pragma unroll
-            for (int c = 0; c < NC; ++c) ff_mean<N2>(B[c], oh[d][c], ol[d][c]);
-            Ph::template flux<float>(oh[d], ofx[d], ofy[d], pr);
-            if (NC == 1) {
+                for (int c = 0; c < NC; ++c) {
+                    oh[d][c] = avg[(2 * c) * m.E + nb[d]];
+                    ol[d][c] = avg[(2 * c + 1) * m.E + nb[d]];
+                }
+            } else {
+                const int jx = nb[d] % m.nx, jy = nb[d] / m.nx;
+                float B[NC][N2];
+                load_block<float, P, NC>(u, m, jx, jy, B);
 #pragma unroll
-                for (int i = 0; i < N2; ++i) V1[d][i] = B[0][i];
+                for (int c = 0; c < NC; ++c) ff_mean<N2>(B[c], oh[d][c], ol[d][c]);
+                if constexpr (keepV) {
+#pragma unroll
+                    for (int i = 0; i < N2; ++i) V1[d][i] = B[0][i];
+                }
             }
+            Ph::template flux<float>(oh[d], ofx[d], ofy[d], pr);
         } else {
 #pragma unroll
             for (int c = 0; c < NC; ++c) oh[d][c] = ol[d][c] = ofx[d][c] = ofy[d][c] = 0.f;
-            if (NC == 1) {
+            if constexpr (keepV) {
 #pragma unroll
                 for (int i = 0; i < N2; ++i) V1[d][i] = 0.f;
             }
@@ -653,7 +665,7 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
     if (NC > 1) cf_out[e] = sf;
     float gam;
     if (pr.mode == MODE_WENO || pr.mode == MODE_WENO_L) {
-        if (NC == 1) {
+        if constexpr (keepV) {
             float U1[N2];
 #pragma unroll
             for (int i = 0; i < N2; ++i) U1[i] = U[0][i];
@@ -683,10 +695,10 @@ DEV double pre_at(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __rest
                   double* __restrict__ dte_out, double* __restrict__ ubl_out,
                   double* __restrict__ gam_out, double* __restrict__ nu_out,
                   R* __restrict__ q_out, R* __restrict__ fl_out, R* __restrict__ EV,
-                  float* __restrict__ cf_out, int ex, int ey, int e) {
+                  float* __restrict__ cf_out, const float* __restrict__ avg, int ex, int ey, int e) {
     if constexpr (sizeof(R) == 4) {
         return pre_at_mixed<P, Ph>(m, pr, u, ue_out, dte_out, ubl_out, gam_out, nu_out, q_out, fl_out, EV,
-                                   cf_out, ex, ey, e);
+                                   cf_out, avg, ex, ey, e);
     } else {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
     double dte;
@@ -772,18 +784,39 @@ DEV double pre_at(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __rest
     }
 }
 
+// k_avg (FP32-mixed systems): float-float cell means of every element, read
+// by k_pre for the four face neighbours instead of their coefficient blocks;
+// avg[(2c) E + e] = high part, avg[(2c+1) E + e] = low part of component c
+template <int P, int NC>
+__global__ void k_avg(MeshDev m, const float* __restrict__ u, float* __restrict__ avg) {
+    pdl_begin();
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
+    constexpr int N2 = Dim<P>::N2;
+    float U[NC][N2];
+    load_block<float, P, NC>(u, m, ex, ey, U);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        float hi, lo;
+        ff_mean<N2>(U[c], hi, lo);
+        avg[(2 * c) * m.E + e] = hi;
+        avg[(2 * c + 1) * m.E + e] = lo;
+    }
+}
+
 template <class R, int P, class Ph>
 __global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __restrict__ ue_out,
                       double* __restrict__ dte_out, double* __restrict__ ubl_out,
                       double* __restrict__ gam_out, double* __restrict__ nu_out,
                       R* __restrict__ q_out, R* __restrict__ fl_out, R* __restrict__ EV,
-                      float* __restrict__ cf_out, unsigned long long* __restrict__ dtbits) {
+                      float* __restrict__ cf_out, const float* __restrict__ avg,
+                      unsigned long long* __restrict__ dtbits) {
     pdl_begin();
     int ex, ey, e;
     double dte = __longlong_as_double(0x7ff0000000000000LL);
     if (elem_of_thread(m, ex, ey, e))
         dte = pre_at<R, P, Ph>(m, pr, u, ue_out, dte_out, ubl_out, gam_out, nu_out, q_out, fl_out, EV, cf_out,
-                               ex, ey, e);
+                               avg, ex, ey, e);
     if (dtbits) block_min_to(dte, dtbits);
 }
 

@@ -22,6 +22,7 @@ struct Bufs {
     void* q;      // flux-limiter capacities [2][E] (scalar)  (R)
     void* fl;     // low-order facet fluxes [E][4][NC]         (R)
     float* cf;    // float copies for the Euler limiter certificate [1+NC][E]: s, ubar^{e,L}
+    float* avg;   // float-float cell means [2NC][E] (FP32-mixed systems)
     double *ue, *dte, *ubl, *gam, *nu, *ube, *beta;
     unsigned long long* cnt;     // CNT_N counters
     unsigned long long* dtbits;  // min dt_e as bits
@@ -99,9 +100,13 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
         if (e != cudaSuccess && err == cudaSuccess) err = e;
     };
     R* u = (R*)B.u;
+    constexpr bool use_avg = sizeof(R) == 4 && NC > 1;
+    if constexpr (use_avg)
+        CGL_LAUNCH(prof, KID_AVG, st, chk(launch(pdl, k_avg<P, NC>, ge, be, st, m, (const float*)u, B.avg)));
     CGL_LAUNCH(prof, KID_PRE, st,
                chk(launch(pdl, k_pre<R, P, Ph>, ge, be, st, m, pr, (const R*)u, B.ue, B.dte, B.ubl, B.gam, B.nu,
-                          (R*)B.q, (R*)B.fl, (R*)nullptr, B.cf, first ? B.dtbits : nullptr)));
+                          (R*)B.q, (R*)B.fl, (R*)nullptr, B.cf, (const float*)B.avg,
+                          first ? B.dtbits : nullptr)));
     if (first)
         CGL_LAUNCH(prof, KID_DT, st,
                    chk(launch(pdl, k_dt_final, dim3(1), dim3(1), st, B.dtbits, pr.cfl, (const double*)B.t,
