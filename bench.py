@@ -197,9 +197,19 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-# ncu dram bytes per launch (read + write) of the dominant kernels, from the
-# captures summarised under profiles/ (None until captured for this kernel)
-NCU_TRAFFIC = {}
+# ncu dram bytes per launch (read + write) of the kernels of one stage of the
+# bench workload, from the capture summarised in
+# profiles/kpp256_q2_dram_per_launch.md (kernels unchanged since; the two
+# Richardson sweeps averaged like their algorithmic bytes)
+NCU_TRAFFIC = {
+    ("k_pre", "kpp_256x256_q2"): 1136384,
+    ("k_grad_rhs", "kpp_256x256_q2"): 1065984,
+    ("k_mass_sweep", "kpp_256x256_q2"): (4226816 + 2117376) // 2,
+    ("k_res_ev", "kpp_256x256_q2"): 4409344,
+    ("k_gather_init", "kpp_256x256_q2"): 2364416,
+    ("k_update_ev", "kpp_256x256_q2"): 8809984,
+    ("k_final", "kpp_256x256_q2"): 4471040,
+}
 
 
 # --------------------------------------------------------------------------
