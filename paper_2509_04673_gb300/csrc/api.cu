@@ -311,6 +311,8 @@ extern "C" cgl_status cgl_mesh_create(const cgl_mesh_desc* d, cgl_mesh** out) {
     m.inv_n1 = 1.0 / (d->p + 1);
     m.h_f = (float)m.h;
     m.me_f = (float)m.me;
+    m.me_rz_f = m.me_f;
+    if ((double)m.me_rz_f > m.me) m.me_rz_f = std::nextafter(m.me_rz_f, 0.0f);
     m.inv_me_f = (float)m.inv_me;
     m.h2_f = (float)(m.h * m.h);
     m.h_over_n2_f = (float)m.h_over_n2;
@@ -556,6 +558,7 @@ extern "C" cgl_status cgl_set_problem(cgl_state* S, const cgl_problem* p) {
     d.hi_tol_f = (float)d.hi_tol;
     d.opts = p->options;
     d.ome_f = (float)(1.0 - d.pos_eps);
+    d.lambda_floor_f = (float)d.lambda_floor;
     S->stage = fn;
     S->has_problem = true;
     if (S->step_graph) {

@@ -34,6 +34,7 @@ struct MeshDev {
     // h/(p+1)^2, 1/h, 1/(p+1)^2, 1/(p+1)
     double me, inv_me, h_over_n2, inv_h, inv_n2, inv_n1;
     float h_f, me_f, inv_me_f, h2_f, h_over_n2_f;
+    float me_rz_f;         // m_i^e rounded toward zero (admissible bound gaps)
 };
 
 struct ProbDev {
@@ -50,6 +51,7 @@ struct ProbDev {
     float lo32_f, hi32_f, lo_tol_f, hi_tol_f;
     int opts;              // CGL_OPT_* bits
     float ome_f;           // 1 - pos_eps rounded to float
+    float lambda_floor_f;
 };
 
 enum { OPT_FP64_LIMITER = 1 };

@@ -490,6 +490,23 @@ DEV float ff_diff(float ah, float al, float bh, float bl) {
     return __fadd_rn(s, __fadd_rn(err, __fsub_rn(al, bl)));
 }
 
+// error-free sum a + b = s + t (Knuth's TwoSum)
+DEV void two_sum(float a, float b, float& s, float& t) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// ((a - b) + c) - d as a float-float pair hi + lo (relative error ~2^-44)
+DEV void ff_sum4(float a, float b, float c, float d, float& hi, float& lo) {
+    float s1, t1, s2, t2, s3, t3;
+    two_sum(a, -b, s1, t1);
+    two_sum(s1, c, s2, t2);
+    two_sum(s2, -d, s3, t3);
+    hi = s3;
+    lo = __fadd_rn(__fadd_rn(t1, t2), t3);
+}
+
 // LLF flux value 0.5 (nL + nR) - 0.5 lambda jump, with a fixed evaluation order
 DEV float llf_value(float nL, float nR, float lam, float jump) {
     return __fmaf_rn(__fmul_rn(-0.5f, lam), jump, __fmul_rn(0.5f, __fadd_rn(nL, nR)));
@@ -542,7 +559,7 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
                         double* __restrict__ ubl_out, double* __restrict__ gam_out,
                         double* __restrict__ nu_out, float* __restrict__ q_out,
                         float* __restrict__ fl_out, float* __restrict__ EV, float* __restrict__ cf_out,
-                        const float* __restrict__ avg, int ex, int ey, int e) {
+                        float* __restrict__ avg, int ex, int ey, int e) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
     int nb[4];
 #pragma unroll
@@ -638,9 +655,13 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
         }
     }
     float sf = __fadd_rn(__fadd_rn(__fadd_rn(lam[0], lam[1]), lam[2]), lam[3]);
-    sf = fmaxf(sf, (float)pr.lambda_floor);
+    sf = fmaxf(sf, pr.lambda_floor_f);
+    // dt_e / h = 1 / s: float reciprocal refined by one float64 Newton step
+    // (relative error ~2^-46, far inside the 2^-20 inflation of the speeds;
+    // GB300's float64 divide is a long sequence on its narrow float64 pipe)
     const double s = (double)sf;
-    const double rs = 1.0 / s;
+    const double r0 = (double)__frcp_rn(sf);
+    const double rs = fma(r0, fma(-s, r0, 1.0), r0);
     const double dte = m.h * rs;
     dte_out[e] = dte;
     dte_out[m.E + e] = rs;
@@ -649,14 +670,24 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
     for (int d = 0; d < 4; ++d)
 #pragma unroll
         for (int c = 0; c < NC; ++c) fl_out[((long long)e * 4 + d) * NC + c] = F[d][c];
+    const float s4 = 0.25f * sf;  // |K| / (|dK| dt_e), exact
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        const double os = (((double)F[1][c] - (double)F[0][c]) + (double)F[3][c]) - (double)F[2][c];
+        // facet flux sum (F_E - F_W) + F_N - F_S as a float-float pair, widened once
+        float osh, osl;
+        ff_sum4(F[1][c], F[0][c], F[3][c], F[2][c], osh, osl);
+        const double os = (double)osh + (double)osl;
         const double bl = ued[c] - rs * os;
         ubl_out[c * m.E + e] = bl;
         if (NC == 1) {
-            q_out[e] = __double2float_rz(fmax(0.0, (0.25 * s) * (pr.umax - bl)));
-            q_out[m.E + e] = __double2float_rz(fmin(0.0, (0.25 * s) * (pr.umin - bl)));
+            // capacities (s/4)(umax - bl) >= 0 and (s/4)(umin - bl) <= 0: bound
+            // gaps in float64, both factors and the product rounded toward zero
+            // (smaller magnitudes stay admissible)
+            q_out[e] = __fmul_rz(s4, fmaxf(0.f, __double2float_rz(pr.umax - bl)));
+            q_out[m.E + e] = __fmul_rz(s4, fminf(0.f, __double2float_rz(pr.umin - bl)));
+            // the float-float mean, for the element contributions of k_update_ev
+            avg[e] = uh[0];
+            avg[m.E + e] = ul[0];
         } else {
             // float copies for the certificate of the facet limiter (euler_alpha_is_one)
             cf_out[(1 + c) * m.E + e] = (float)bl;
@@ -695,7 +726,7 @@ DEV double pre_at(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __rest
                   double* __restrict__ dte_out, double* __restrict__ ubl_out,
                   double* __restrict__ gam_out, double* __restrict__ nu_out,
                   R* __restrict__ q_out, R* __restrict__ fl_out, R* __restrict__ EV,
-                  float* __restrict__ cf_out, const float* __restrict__ avg, int ex, int ey, int e) {
+                  float* __restrict__ cf_out, float* __restrict__ avg, int ex, int ey, int e) {
     if constexpr (sizeof(R) == 4) {
         return pre_at_mixed<P, Ph>(m, pr, u, ue_out, dte_out, ubl_out, gam_out, nu_out, q_out, fl_out, EV,
                                    cf_out, avg, ex, ey, e);
@@ -809,7 +840,7 @@ __global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __
                       double* __restrict__ dte_out, double* __restrict__ ubl_out,
                       double* __restrict__ gam_out, double* __restrict__ nu_out,
                       R* __restrict__ q_out, R* __restrict__ fl_out, R* __restrict__ EV,
-                      float* __restrict__ cf_out, const float* __restrict__ avg,
+                      float* __restrict__ cf_out, float* __restrict__ avg,
                       unsigned long long* __restrict__ dtbits) {
     pdl_begin();
     int ex, ey, e;
@@ -1590,6 +1621,7 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
                             const double* __restrict__ ue, const double* __restrict__ dte_a, const double* __restrict__ ubl,
                             const R* __restrict__ qcap, const R* __restrict__ fl_in,
                             const R* __restrict__ ER, const float* __restrict__ cf,
+                            const float* __restrict__ avg,
                             const double* __restrict__ dtp, R* __restrict__ EW,
                             double* __restrict__ ube_out, double* __restrict__ beta_out,
                             unsigned long long* __restrict__ cnt, int ex, int ey, int e) {
@@ -1674,6 +1706,7 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
 #pragma unroll
             for (int c = 0; c < NC; ++c) FLr[d][c] = fl_in[((long long)e * 4 + d) * NC + c];
         double FB[4][NC];
+        R FBr[4];  // scalar limited fluxes in the bulk precision
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
             const bool self_is_L = (d == 1 || d == 3);
@@ -1693,7 +1726,8 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
                     fmaxv = fmin(fmaxv, -qcap[m.E + Rc]);
                     fminv = fmax(fminv, -qcap[Rc]);
                 }
-                FB[d][0] = (double)((fA >= R(0)) ? fmin(fA, fmaxv) : fmax(fA, fminv));
+                FBr[d] = (fA >= R(0)) ? fmin(fA, fmaxv) : fmax(fA, fminv);
+                FB[d][0] = (double)FBr[d];
             } else {
                 double fA[NC];
 #pragma unroll
@@ -1750,7 +1784,15 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
         }
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            double os = ((FB[1][c] - FB[0][c]) + FB[3][c]) - FB[2][c];
+            double os;
+            if constexpr (sizeof(R) == 4 && Ph::NC == 1) {
+                // float limited fluxes summed as a float-float pair, widened once
+                float osh, osl;
+                ff_sum4(FBr[1], FBr[0], FBr[3], FBr[2], osh, osl);
+                os = (double)osh + (double)osl;
+            } else {
+                os = ((FB[1][c] - FB[0][c]) + FB[3][c]) - FB[2][c];
+            }
             ubec[c] = ublc[c] + rs * os;
         }
     }
@@ -1797,7 +1839,13 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
             }
         const R fh_term = h_over_n2R * (((FHr[1][c] - FHr[0][c]) + FHr[3][c]) - FHr[2][c]);
         R ueh, uel;
-        split<R>(uec[c], ueh, uel);
+        if constexpr (sizeof(R) == 4) {
+            // the float-float mean itself (k_pre for scalars, k_avg for systems)
+            ueh = avg[(2 * c) * m.E + e];
+            uel = avg[(2 * c + 1) * m.E + e];
+        } else {
+            split<R>(uec[c], ueh, uel);
+        }
 #pragma unroll
         for (int b = 0; b < N1; ++b)
 #pragma unroll
@@ -1816,8 +1864,16 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
     if (pr.mode == MODE_WENO_L) {
         if (Ph::NC == 1) {
             // bound gaps in float64 per element, ratios per node in R
-            const R gp = R(me * (pr.umax - ubec[0]));
-            const R gm = R(me * (pr.umin - ubec[0]));
+            R gp, gm;
+            if constexpr (sizeof(R) == 4) {
+                // gaps in float64; m_i^e, the gaps and the products rounded
+                // toward zero (smaller magnitudes stay admissible)
+                gp = __fmul_rz(m.me_rz_f, __double2float_rz(pr.umax - ubec[0]));
+                gm = __fmul_rz(m.me_rz_f, __double2float_rz(pr.umin - ubec[0]));
+            } else {
+                gp = R(me * (pr.umax - ubec[0]));
+                gm = R(me * (pr.umin - ubec[0]));
+            }
             R b = R(1);
 #pragma unroll
             for (int i = 0; i < N2; ++i) {
@@ -1866,14 +1922,15 @@ __global__ void k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, cons
                             const double* __restrict__ ue, const double* __restrict__ dte_a, const double* __restrict__ ubl,
                             const R* __restrict__ qcap, const R* __restrict__ fl_in,
                             const R* __restrict__ ER, const float* __restrict__ cf,
+                            const float* __restrict__ avg,
                             const double* __restrict__ dtp, R* __restrict__ EW,
                             double* __restrict__ ube_out, double* __restrict__ beta_out,
                             unsigned long long* __restrict__ cnt) {
     pdl_begin();
     int ex, ey, e;
     if (!elem_of_thread(m, ex, ey, e)) return;
-    update_at<R, P, Ph>(m, pr, u, ud, ue, dte_a, ubl, qcap, fl_in, ER, cf, dtp, EW, ube_out, beta_out, cnt, ex, ey,
-                        e);
+    update_at<R, P, Ph>(m, pr, u, ud, ue, dte_a, ubl, qcap, fl_in, ER, cf, avg, dtp, EW, ube_out, beta_out, cnt, ex,
+                        ey, e);
 }
 
 

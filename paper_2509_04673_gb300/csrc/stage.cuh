@@ -22,7 +22,7 @@ struct Bufs {
     void* q;      // flux-limiter capacities [2][E] (scalar)  (R)
     void* fl;     // low-order facet fluxes [E][4][NC]         (R)
     float* cf;    // float copies for the Euler limiter certificate [1+NC][E]: s, ubar^{e,L}
-    float* avg;   // float-float cell means [2NC][E] (FP32-mixed systems)
+    float* avg;   // float-float cell means [2NC][E] (FP32-mixed: k_avg for systems, k_pre for scalars)
     double *ue, *dte, *ubl, *gam, *nu, *ube, *beta;
     unsigned long long* cnt;     // CNT_N counters
     unsigned long long* dtbits;  // min dt_e as bits
@@ -105,7 +105,7 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
         CGL_LAUNCH(prof, KID_AVG, st, chk(launch(pdl, k_avg<P, NC>, ge, be, st, m, (const float*)u, B.avg)));
     CGL_LAUNCH(prof, KID_PRE, st,
                chk(launch(pdl, k_pre<R, P, Ph>, ge, be, st, m, pr, (const R*)u, B.ue, B.dte, B.ubl, B.gam, B.nu,
-                          (R*)B.q, (R*)B.fl, (R*)nullptr, B.cf, (const float*)B.avg,
+                          (R*)B.q, (R*)B.fl, (R*)nullptr, B.cf, B.avg,
                           first ? B.dtbits : nullptr)));
     if (first)
         CGL_LAUNCH(prof, KID_DT, st,
@@ -145,7 +145,8 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
     CGL_LAUNCH(prof, KID_UPDATE, st,
                chk(launch(pdl, k_update_ev<R, P, Ph>, ge, be, st, m, pr, (const R*)u, (const R*)ud,
                           (const double*)B.ue, (const double*)B.dte, (const double*)B.ubl, (const R*)B.q,
-                          (const R*)B.fl, (const R*)B.ER, (const float*)B.cf, (const double*)B.dt, (R*)B.EW,
+                          (const R*)B.fl, (const R*)B.ER, (const float*)B.cf, (const float*)B.avg,
+                          (const double*)B.dt, (R*)B.EW,
                           B.ube, B.beta, B.cnt)));
     CGL_LAUNCH(prof, KID_FINAL, st,
                chk(launch(pdl, k_final<R, P, NC>, gn, bn, st, m, pr, (const R*)B.EW, (R*)B.un, u, R(a), R(b),
