@@ -168,14 +168,18 @@ def algorithmic_bytes(kernel, mesh, nc, rsz, k_g, k_u):
     d = 8
     b = {
         # u (own and neighbour blocks read once) -> u^e, dt_e (3), ubar^{e,L},
-        # gamma, nu (float64), Q (2), f^L (4 nc) (bulk precision)
-        "k_pre": nc * NN * rsz + (nc + 3 + nc + 2) * E * d + (2 + 4 * nc) * E * rsz,
+        # gamma, nu (float64), Q (2), f^L (4 nc) (bulk precision), and in the
+        # mixed form the float-float means (2 nc floats)
+        "k_pre": nc * NN * rsz + (nc + 3 + nc + 2) * E * d + (2 + 4 * nc) * E * rsz
+                 + (2 * nc * E * 4 if rsz == 4 else 0),
         # u, g (2 nc), gamma, nu -> element residual
         "k_res_ev": 3 * nc * NN * rsz + 2 * E * d + E * N2 * nc * rsz,
         # u, udot, u^e, dt_e (3), ubar^{e,L} (float64), Q (2), f^L (4 nc),
-        # element residual (bulk) -> increments (bulk), ubar^e, beta (float64)
+        # element residual (bulk), float-float means (mixed) -> increments
+        # (bulk), ubar^e, beta (float64)
         "k_update_ev": 2 * nc * NN * rsz + (nc + 3 + nc) * E * d + (2 + 4 * nc) * E * rsz
-                       + E * N2 * nc * rsz + E * N2 * nc * rsz + (nc + 1) * E * d,
+                       + E * N2 * nc * rsz + E * N2 * nc * rsz + (nc + 1) * E * d
+                       + (2 * nc * E * 4 if rsz == 4 else 0),
         # increments, u^n, u -> u
         "k_final": E * N2 * nc * rsz + 3 * nc * NN * rsz,
     }
@@ -202,13 +206,13 @@ def load_peaks():
 # profiles/kpp256_q2_dram_per_launch.md (kernels unchanged since; the two
 # Richardson sweeps averaged like their algorithmic bytes)
 NCU_TRAFFIC = {
-    ("k_pre", "kpp_256x256_q2"): 1136384,
+    ("k_pre", "kpp_256x256_q2"): 1135104,
     ("k_grad_rhs", "kpp_256x256_q2"): 1065984,
-    ("k_mass_sweep", "kpp_256x256_q2"): (4226816 + 2117376) // 2,
-    ("k_res_ev", "kpp_256x256_q2"): 4409344,
+    ("k_mass_sweep", "kpp_256x256_q2"): (4226560 + 2117376) // 2,
+    ("k_res_ev", "kpp_256x256_q2"): 4409856,
     ("k_gather_init", "kpp_256x256_q2"): 2364416,
-    ("k_update_ev", "kpp_256x256_q2"): 8809984,
-    ("k_final", "kpp_256x256_q2"): 4471040,
+    ("k_update_ev", "kpp_256x256_q2"): 9334272,
+    ("k_final", "kpp_256x256_q2"): 4471296,
 }
 
 
