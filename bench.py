@@ -187,6 +187,10 @@ def algorithmic_bytes(kernel, mesh, nc, rsz, k_g, k_u):
     b["k_grad_rhs"] = nc * NN * rsz + 2 * 2 * nc * NN * rsz
     # element residuals -> r and the lumped udot
     b["k_gather_init"] = E * N2 * nc * rsz + 2 * nc * NN * rsz
+    # fused forms (FP32-mixed): u -> g after the first sweep (and b_g when more
+    # sweeps follow); element residuals -> r and udot after the first sweep
+    b["k_grad_sweep"] = nc * NN * rsz + 2 * nc * NN * rsz * (2 if k_g > 1 else 1)
+    b["k_udot_sweep"] = E * N2 * nc * rsz + 2 * nc * NN * rsz
     # x_in, b -> x_out, averaged over the g_h (2 nc) and udot (nc) sweeps
     nvm = (2 * nc * k_g + nc * k_u) / max(1, k_g + k_u)
     b["k_mass_sweep"] = 3 * nvm * NN * rsz

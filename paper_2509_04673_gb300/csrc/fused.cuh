@@ -1,0 +1,240 @@
+// fused.cuh — the first Richardson sweep fused into the kernel that builds
+// its right-hand side (FP32-mixed form).
+//
+// k_grad_sweep: g_h right-hand side b = int phi_i grad u_h, lumped iterate
+//   g0 = b / m_i and the first sweep g1 = g0 + (b - M_C g0) / m_i (Sec. 2.2,
+//   Richardson reading of the consistent L2 projection) in one pass over a
+//   32 x 16 node tile.
+// k_udot_sweep: node gather r_i = sum_e R^e_i, lumped iterate udot0 = r / m_i
+//   and the first sweep (Sec. 4.3, step 2) in one pass over a tile.
+//
+// A sweep needs its lumped iterate on the tile plus a halo of p nodes, so
+// each block recomputes the right-hand side there (the grad stencil reads u
+// on a halo of 2p nodes).  The arithmetic is that of grad_tile,
+// gather_init_at and sweep_tile, in the same order with the same explicit
+// roundings, so the fused kernels give the same bits as the separate ones
+// (the batched stage, which keeps them separate, is compared bitwise).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace cgl {
+
+// wrap (gx, gy) on periodic directions; false outside a non-periodic mesh
+DEV bool wrap_node(const MeshDev& m, int& gx, int& gy) {
+    bool in = true;
+    if (m.py) gy = gy < 0 ? gy + m.nny : (gy >= m.nny ? gy - m.nny : gy);
+    else in = gy >= 0 && gy < m.nny;
+    if (m.px) gx = gx < 0 ? gx + m.nnx : (gx >= m.nnx ? gx - m.nnx : gx);
+    else in = in && gx >= 0 && gx < m.nnx;
+    return in;
+}
+
+template <int P, int NC>
+struct GradSweepWs {
+    static constexpr int HX1 = ST_TX + 2 * P, HY1 = ST_TY + 2 * P;  // tile + p halo
+    static constexpr int HX2 = ST_TX + 4 * P, HY2 = ST_TY + 4 * P;  // tile + 2p halo
+    static constexpr int NW = 2 * P + 1, NCL = P + 2;
+    static constexpr int A = HY2 * HX2;                // u on the 2p halo
+    static constexpr int B = 2 * HY2 * HX1;            // x-pass of the grad stencil; later the sweep's x-pass
+    static constexpr int C = 2 * HY1 * HX1;            // g0 (x and y parts) on the p halo
+    static constexpr int D = 2 * ST_TY * ST_TX;        // b on the tile
+    static constexpr int size = A + B + C + D + 2 * NCL * NW;
+};
+
+template <int P, int NC>
+__global__ void __launch_bounds__(ST_TX * ST_BY)
+    k_grad_sweep(MeshDev m, const float* __restrict__ u, float* __restrict__ bout, float* __restrict__ gout) {
+    pdl_begin();
+    using WS = GradSweepWs<P, NC>;
+    constexpr int HX1 = WS::HX1, HY1 = WS::HY1, HX2 = WS::HX2, HY2 = WS::HY2, NW = WS::NW, NCL = WS::NCL;
+    constexpr int NT = ST_TX * ST_BY, NJ = ST_TY / ST_BY;
+    __shared__ float ws[WS::size];
+    float(*A)[HX2] = reinterpret_cast<float(*)[HX2]>(ws);
+    float(*tC)[HX1] = reinterpret_cast<float(*)[HX1]>(ws + WS::A);
+    float(*tM)[HX1] = reinterpret_cast<float(*)[HX1]>(ws + WS::A + HY2 * HX1);
+    float(*t)[HY1][ST_TX] = reinterpret_cast<float(*)[HY1][ST_TX]>(ws + WS::A);  // after tC, tM are consumed
+    float(*G)[HY1][HX1] = reinterpret_cast<float(*)[HY1][HX1]>(ws + WS::A + WS::B);
+    float(*Bt)[ST_TY][ST_TX] = reinterpret_cast<float(*)[ST_TY][ST_TX]>(ws + WS::A + WS::B + WS::C);
+    float(*WM)[NW] = reinterpret_cast<float(*)[NW]>(ws + WS::A + WS::B + WS::C + WS::D);
+    float(*WC)[NW] = reinterpret_cast<float(*)[NW]>(ws + WS::A + WS::B + WS::C + WS::D + NCL * NW);
+    const Tab<float>& T = TabSel<float>::t(P);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ST_TX + tx;
+    if (tid < NCL * NW) {
+        const int cls = tid / NW, k = tid - cls * NW;
+        WM[cls][k] = class_weight<float, P, 0>(T, cls, k - P);
+        WC[cls][k] = class_weight<float, P, 1>(T, cls, k - P);
+    }
+    const int gx0 = blockIdx.x * ST_TX, gy0 = blockIdx.y * ST_TY;
+    const float h = m.h_f, h2 = m.h2_f;
+    for (int c = 0; c < NC; ++c) {
+        __syncthreads();  // weights ready; previous component consumed
+        // u of component c on the tile plus a halo of 2p nodes
+        for (int i = tid; i < HY2 * HX2; i += NT) {
+            const int r = i / HX2, cc = i - r * HX2;
+            int gx = gx0 - 2 * P + cc, gy = gy0 - 2 * P + r;
+            const bool in = wrap_node(m, gx, gy);
+            A[r][cc] = in ? u[(long long)c * m.NN + (long long)gy * m.nnx + gx] : 0.f;
+        }
+        __syncthreads();
+        // grad stencil along x for the columns of the p halo, all 2p-halo rows
+        for (int i = tid; i < HY2 * HX1; i += NT) {
+            const int r = i / HX1, cc = i - r * HX1;
+            int gx = gx0 - P + cc, gy = 0;
+            wrap_node(m, gx, gy);
+            const int clx = node_class<P>(gx, m.nnx, m.px);
+            float sc = 0.f, sm = 0.f;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const float x = A[r][cc + k];
+                sc = fma_r(WC[clx][k], x, sc);
+                sm = fma_r(WM[clx][k], x, sm);
+            }
+            tC[r][cc] = sc;
+            tM[r][cc] = sm;
+        }
+        __syncthreads();
+        // along y: b and g0 = b / m_i on the p halo (zero outside the mesh)
+        for (int i = tid; i < HY1 * HX1; i += NT) {
+            const int r = i / HX1, cc = i - r * HX1;
+            int gx = gx0 - P + cc, gy = gy0 - P + r;
+            const bool in = wrap_node(m, gx, gy);
+            const int clx = node_class<P>(gx, m.nnx, m.px), cly = node_class<P>(gy, m.nny, m.py);
+            float sx = 0.f, sy = 0.f;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                sx = fma_r(WM[cly][k], tC[r + k][cc], sx);
+                sy = fma_r(WC[cly][k], tM[r + k][cc], sy);
+            }
+            const int cnt = (clx == 0 ? 2 : 1) * (cly == 0 ? 2 : 1);
+            const float inv_mi = mul_r(m.inv_me_f, inv_count<float>(cnt));
+            const float bx = mul_r(h, sx), by = mul_r(h, sy);
+            G[0][r][cc] = in ? mul_r(bx, inv_mi) : 0.f;
+            G[1][r][cc] = in ? mul_r(by, inv_mi) : 0.f;
+            const int rt = r - P, ct = cc - P;
+            if (rt >= 0 && rt < ST_TY && ct >= 0 && ct < ST_TX) {
+                Bt[0][rt][ct] = bx;
+                Bt[1][rt][ct] = by;
+            }
+        }
+        __syncthreads();
+        // first sweep, along x for every p-halo row (the mass weights)
+        const int gxt = gx0 + tx;
+        const int clxt = node_class<P>(gxt, m.nnx, m.px);
+        for (int r = ty; r < HY1; r += ST_BY) {
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                float sx = 0.f;
+#pragma unroll
+                for (int k = 0; k < NW; ++k) sx = fma_r(WM[clxt][k], G[f][r][tx + k], sx);
+                t[f][r][tx] = sx;
+            }
+        }
+        __syncthreads();
+        // along y and the outputs: g1 (and b where more sweeps follow)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int r = ty + j * ST_BY, gy = gy0 + r;
+            if (gxt >= m.nnx || gy >= m.nny) continue;
+            const int cly = node_class<P>(gy, m.nny, m.py);
+            const int cnt = (clxt == 0 ? 2 : 1) * (cly == 0 ? 2 : 1);
+            const float inv_mi = mul_r(m.inv_me_f, inv_count<float>(cnt));
+            const long long node = (long long)gy * m.nnx + gxt;
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                float sy = 0.f;
+#pragma unroll
+                for (int k = 0; k < NW; ++k) sy = fma_r(WM[cly][k], t[f][r + k][tx], sy);
+                const long long k = (long long)(f * NC + c) * m.NN + node;
+                gout[k] = sweep_value(G[f][r + P][tx + P], Bt[f][r][tx], sy, h2, inv_mi);
+                if (bout) bout[k] = Bt[f][r][tx];
+            }
+        }
+    }
+}
+
+template <int P, int NC>
+struct UdotSweepWs {
+    static constexpr int HX = ST_TX + 2 * P, HY = ST_TY + 2 * P, NW = 2 * P + 1, NCL = P + 2;
+    static constexpr int size = NC * (HY * HX + HY * ST_TX + ST_TY * ST_TX) + NCL * NW;
+};
+
+// r = sum over E_i of the element residuals (stored for further sweeps and
+// diagnostics), udot0 = r / m_i on the tile plus a p halo, and the first
+// sweep udot1 = udot0 + (r - M_C udot0) / m_i on the tile
+template <int P, int NC>
+__global__ void __launch_bounds__(ST_TX * ST_BY)
+    k_udot_sweep(MeshDev m, const float* __restrict__ ER, float* __restrict__ rout, float* __restrict__ xout) {
+    pdl_begin();
+    using WS = UdotSweepWs<P, NC>;
+    constexpr int HX = WS::HX, HY = WS::HY, NW = WS::NW, NCL = WS::NCL;
+    constexpr int NT = ST_TX * ST_BY, NJ = ST_TY / ST_BY;
+    __shared__ float ws[WS::size];
+    float(*xs)[HY][HX] = reinterpret_cast<float(*)[HY][HX]>(ws);
+    float(*t)[HY][ST_TX] = reinterpret_cast<float(*)[HY][ST_TX]>(ws + NC * HY * HX);
+    float(*rt)[ST_TY][ST_TX] = reinterpret_cast<float(*)[ST_TY][ST_TX]>(ws + NC * (HY * HX + HY * ST_TX));
+    float(*W)[NW] = reinterpret_cast<float(*)[NW]>(ws + NC * (HY * HX + HY * ST_TX + ST_TY * ST_TX));
+    const Tab<float>& T = TabSel<float>::t(P);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ST_TX + tx;
+    if (tid < NCL * NW) {
+        const int cls = tid / NW, k = tid - cls * NW;
+        W[cls][k] = class_weight<float, P, 0>(T, cls, k - P);
+    }
+    const int gx0 = blockIdx.x * ST_TX, gy0 = blockIdx.y * ST_TY;
+    // gathers on the tile plus a p halo (gather_init_at's arithmetic)
+    for (int i = tid; i < HY * HX; i += NT) {
+        const int r = i / HX, cc = i - r * HX;
+        int gx = gx0 - P + cc, gy = gy0 - P + r;
+        const bool in = wrap_node(m, gx, gy);
+        float s[NC];
+        float inv_mi = 0.f;
+        if (in) {
+            const NodeC<P> nc = node_c<P>(m, gx, gy);
+            gather_at<float, P, NC>(m, ER, nc, s);
+            inv_mi = PV<float>::inv_me(m) * inv_count<float>(nc.nxc * nc.nyc);
+        }
+        const int rr = r - P, ct = cc - P;
+        const bool tile = rr >= 0 && rr < ST_TY && ct >= 0 && ct < ST_TX;
+        const long long node = (long long)gy * m.nnx + gx;
+#pragma unroll
+        for (int v = 0; v < NC; ++v) {
+            xs[v][r][cc] = in ? s[v] * inv_mi : 0.f;
+            if (tile) {
+                rt[v][rr][ct] = in ? s[v] : 0.f;
+                if (in) rout[v * m.NN + node] = s[v];
+            }
+        }
+    }
+    __syncthreads();
+    const int gx = gx0 + tx;
+    const int clx = node_class<P>(gx, m.nnx, m.px);
+    for (int r = ty; r < HY; r += ST_BY) {
+#pragma unroll
+        for (int v = 0; v < NC; ++v) {
+            float sx = 0.f;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) sx = fma_r(W[clx][k], xs[v][r][tx + k], sx);
+            t[v][r][tx] = sx;
+        }
+    }
+    __syncthreads();
+    const float h2 = PV<float>::h2(m);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int r = ty + j * ST_BY, gy = gy0 + r;
+        if (gx >= m.nnx || gy >= m.nny) continue;
+        const int cly = node_class<P>(gy, m.nny, m.py);
+        const int cnt = (clx == 0 ? 2 : 1) * (cly == 0 ? 2 : 1);
+        const float inv_mi = mul_r(PV<float>::inv_me(m), inv_count<float>(cnt));
+        const long long node = (long long)gy * m.nnx + gx;
+#pragma unroll
+        for (int v = 0; v < NC; ++v) {
+            float sy = 0.f;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) sy = fma_r(W[cly][k], t[v][r + k][tx], sy);
+            xout[v * m.NN + node] = sweep_value(xs[v][r + P][tx + P], rt[v][r][tx], sy, h2, inv_mi);
+        }
+    }
+}
+
+}  // namespace cgl

@@ -2,7 +2,7 @@
 // the paper: element loop, udot solve, facet loop, element loop, SSP update).
 #pragma once
 
-#include "kernels.cuh"
+#include "fused.cuh"
 
 namespace cgl {
 
@@ -31,8 +31,8 @@ struct Bufs {
 
 // kernel identifiers for per-kernel timing
 enum KernelId {
-    KID_AVG = 0, KID_PRE, KID_DT, KID_GRAD, KID_GATHER, KID_MASS, KID_SWEEP, KID_RES,
-    KID_UPDATE, KID_FINAL, KID_TADV, KID_COPY, KID_COUNT
+    KID_AVG = 0, KID_PRE, KID_DT, KID_GRAD, KID_GATHER, KID_GRADF, KID_SWEEP, KID_RES,
+    KID_UPDATE, KID_FINAL, KID_TADV, KID_UDOTF, KID_COUNT
 };
 
 // optional per-launch timing: CUDA events recorded around every launch on
@@ -118,8 +118,23 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
         R* g = (R*)B.g;
         R* g2 = (R*)B.g2;
         R* bg = (R*)B.bg;
-        CGL_LAUNCH(prof, KID_GRAD, st, chk(launch(pdl, k_grad_rhs<R, P, NC>, gt, bt, st, m, (const R*)u, bg, g)));
-        for (int k = 0; k < pr.k_g; ++k) {
+        // FP32-mixed: the right-hand side and the first sweep in one kernel
+        constexpr bool fuse = sizeof(R) == 4;
+        int k0 = 0;
+        if (fuse && pr.k_g >= 1) {
+            if constexpr (fuse)
+                CGL_LAUNCH(prof, KID_GRADF, st,
+                           chk(launch(pdl, k_grad_sweep<P, NC>, gt, bt, st, m, (const float*)u,
+                                      pr.k_g > 1 ? (float*)bg : (float*)nullptr, (float*)g2)));
+            R* t = g;
+            g = g2;
+            g2 = t;
+            k0 = 1;
+        } else {
+            CGL_LAUNCH(prof, KID_GRAD, st,
+                       chk(launch(pdl, k_grad_rhs<R, P, NC>, gt, bt, st, m, (const R*)u, bg, g)));
+        }
+        for (int k = k0; k < pr.k_g; ++k) {
             CGL_LAUNCH(prof, KID_SWEEP, st,
                        chk(launch(pdl, k_mass_sweep<R, P, 2 * NC>, gt, bt, st, m, (const R*)g, (const R*)bg, g2)));
             R* t = g;
@@ -132,9 +147,21 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
         CGL_LAUNCH(prof, KID_RES, st,
                    chk(launch(pdl, k_res_ev<R, P, Ph>, ge, be, st, m, pr, (const R*)u, (const R*)g,
                               (const double*)B.gam, (const double*)B.nu, ER)));
-        CGL_LAUNCH(prof, KID_GATHER, st,
-                   chk(launch(pdl, k_gather_init<R, P, NC>, gn, bn, st, m, (const R*)ER, r, ud)));
-        for (int k = 0; k < pr.k_u; ++k) {
+        int k1 = 0;
+        if (fuse && pr.k_u >= 1) {
+            if constexpr (fuse)
+                CGL_LAUNCH(prof, KID_UDOTF, st,
+                           chk(launch(pdl, k_udot_sweep<P, NC>, gt, bt, st, m, (const float*)ER, (float*)r,
+                                      (float*)ud2)));
+            R* t = ud;
+            ud = ud2;
+            ud2 = t;
+            k1 = 1;
+        } else {
+            CGL_LAUNCH(prof, KID_GATHER, st,
+                       chk(launch(pdl, k_gather_init<R, P, NC>, gn, bn, st, m, (const R*)ER, r, ud)));
+        }
+        for (int k = k1; k < pr.k_u; ++k) {
             CGL_LAUNCH(prof, KID_SWEEP, st,
                        chk(launch(pdl, k_mass_sweep<R, P, NC>, gt, bt, st, m, (const R*)ud, (const R*)r, ud2)));
             R* t = ud;
