@@ -101,6 +101,12 @@ typedef struct cgl_mesh_desc {
  * float64; the results are identical, the option exists to check that.
  * No effect in the FP64 form or for scalar fluxes. */
 #define CGL_OPT_FP64_LIMITER 1
+/* cgl_problem.options.  CGL_OPT_UNFUSED_SWEEPS: in the FP32-mixed form on meshes
+ * of 2^22 nodes or more, run the right-hand sides of the g_h and udot solves and
+ * their first Richardson sweeps as separate kernels.  By default they are
+ * fused there (one kernel each); the results are identical, the option exists
+ * to check that. */
+#define CGL_OPT_UNFUSED_SWEEPS 2
 
 typedef struct cgl_problem {
     int32_t flux;          /* CGL_FLUX_* */

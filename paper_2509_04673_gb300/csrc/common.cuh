@@ -54,7 +54,7 @@ struct ProbDev {
     float lambda_floor_f;
 };
 
-enum { OPT_FP64_LIMITER = 1 };
+enum { OPT_FP64_LIMITER = 1, OPT_UNFUSED_SWEEPS = 2 };
 
 // typed views of the problem and mesh constants: float kernels read the
 // float copies, float64 kernels the originals

@@ -66,6 +66,12 @@ typedef cudaError_t (*StageFn)(const Bufs&, const MeshDev&, const ProbDev&, doub
 
 inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// The fused first sweeps (fused.cuh) save the traffic of the lumped iterates
+// but lengthen each block's chain of dependent phases.  Measured on GB300,
+// they win from about 4M nodes (KPP 1024^2 Q2: -4 % per step, Euler blast
+// 2048^2) and lose below (KPP 256^2: +4 %; Euler 512^2 Q3: +1.5 %).
+inline bool fuse_sweeps(const MeshDev& m) { return m.NN >= (1LL << 22); }
+
 // Launch with programmatic stream serialisation (pdl): the kernel may be
 // scheduled while the previous kernel of the stream drains and waits for it
 // in pdl_begin(); inside a captured graph this becomes a programmatic edge.
@@ -118,10 +124,12 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
         R* g = (R*)B.g;
         R* g2 = (R*)B.g2;
         R* bg = (R*)B.bg;
-        // FP32-mixed: the right-hand side and the first sweep in one kernel
+        // FP32-mixed on large meshes: the right-hand side and the first sweep
+        // in one kernel
         constexpr bool fuse = sizeof(R) == 4;
+        const bool fuse_here = fuse && fuse_sweeps(m) && !(pr.opts & OPT_UNFUSED_SWEEPS);
         int k0 = 0;
-        if (fuse && pr.k_g >= 1) {
+        if (fuse_here && pr.k_g >= 1) {
             if constexpr (fuse)
                 CGL_LAUNCH(prof, KID_GRADF, st,
                            chk(launch(pdl, k_grad_sweep<P, NC>, gt, bt, st, m, (const float*)u,
@@ -148,7 +156,7 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
                    chk(launch(pdl, k_res_ev<R, P, Ph>, ge, be, st, m, pr, (const R*)u, (const R*)g,
                               (const double*)B.gam, (const double*)B.nu, ER)));
         int k1 = 0;
-        if (fuse && pr.k_u >= 1) {
+        if (fuse_here && pr.k_u >= 1) {
             if constexpr (fuse)
                 CGL_LAUNCH(prof, KID_UDOTF, st,
                            chk(launch(pdl, k_udot_sweep<P, NC>, gt, bt, st, m, (const float*)ER, (float*)r,

@@ -78,14 +78,17 @@ def _origins(mesh):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("which", ["euler_quadrants_512_q3", "euler_blast_2048_q2", "kpp_256_q2"])
+@pytest.mark.parametrize("which", ["euler_quadrants_512_q3", "euler_blast_2048_q2", "kpp_256_q2", "kpp_2048_q2"])
 def test_full_size_windows(cgl, which, prec):
     if which == "euler_quadrants_512_q3":
         mesh, prob, u0 = inputs.euler_quadrant_config(512, 512, 3)
     elif which == "euler_blast_2048_q2":
         mesh, prob, u0 = inputs.euler_blast_config(2048, 2048, 2)
-    else:
+    elif which == "kpp_256_q2":
         mesh, prob, u0 = inputs.kpp_config(256, 256, 2)
+    else:
+        # large enough for the fused first sweeps of the FP32-mixed form
+        mesh, prob, u0 = inputs.kpp_config(2048, 2048, 2)
     nc = u0.shape[0]
     if prec == 1:
         u0 = u0.astype(np.float32).astype(np.float64)
