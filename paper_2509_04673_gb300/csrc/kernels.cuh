@@ -1399,6 +1399,54 @@ DEV NodeCands node_cands(const MeshDev& m, int gx, int gy) {
 // (p+2)-point Gauss rule for nonlinear integrands; exact face mass for f_h.
 // ER layout ev_at(E, e, i, c, NC).
 // ---------------------------------------------------------------------------
+// boundary-face part of the weak form of element e on face d: the
+// (p+2)-point quadrature of phi_i F(u_h, u_hat; n) (FIXED) or phi_i f(u_h).n
+// (OUTFLOW), scaled by h; Uf and term are [NC][p+1]
+template <class R, int P, class Ph>
+__device__ __noinline__ void boundary_face_term(const MeshDev& m, const ProbDev& pr, int d, const R* Uf, R* term) {
+    constexpr int NC = Ph::NC, N1 = P + 1, NQ = Dim<P>::NQ;
+    const Tab<R>& T = TabSel<R>::t(P);
+    const R h = PV<R>::h(m);
+    const R nxo = (d == 0) ? R(-1) : (d == 1) ? R(1) : R(0);
+    const R nyo = (d == 2) ? R(-1) : (d == 3) ? R(1) : R(0);
+    const int bc = (d < 2) ? m.bc_x : m.bc_y;
+    R acc[NC][N1];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int b = 0; b < N1; ++b) acc[c][b] = R(0);
+#pragma unroll
+    for (int r = 0; r < NQ; ++r) {
+        R uq[NC], F[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            R s = R(0);
+#pragma unroll
+            for (int k = 0; k < N1; ++k) s += Uf[c * N1 + k] * T.Bq[r][k];
+            uq[c] = s;
+        }
+        if (bc == BC_FIXED) {
+            R ub[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ub[c] = PV<R>::ubc(pr, c);
+            llf<Ph, R>(uq, ub, nxo, nyo, pr, F, (R*)nullptr);
+        } else {
+            R fx[NC], fy[NC];
+            Ph::template flux<R>(uq, fx, fy, pr);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) F[c] = fx[c] * nxo + fy[c] * nyo;
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int b = 0; b < N1; ++b) acc[c][b] += (F[c] * T.wq[r]) * T.Bq[r][b];
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int b = 0; b < N1; ++b) term[c * N1 + b] = acc[c][b] * h;
+}
+
 template <class R, int P, class Ph>
 DEV void res_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ g,
                          const double* __restrict__ gam, const double* __restrict__ nu,
@@ -1498,41 +1546,9 @@ DEV void res_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restr
                     term[c][b] = h * s;
                 }
         } else {
-            const int bc = (d < 2) ? m.bc_x : m.bc_y;
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-#pragma unroll
-                for (int b = 0; b < N1; ++b) term[c][b] = R(0);
-#pragma unroll
-            for (int r = 0; r < NQ; ++r) {
-                R uq[NC], F[NC];
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    R s = R(0);
-#pragma unroll
-                    for (int k = 0; k < N1; ++k) s += Uf[c][k] * T.Bq[r][k];
-                    uq[c] = s;
-                }
-                if (bc == BC_FIXED) {
-                    R ub[NC];
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) ub[c] = PV<R>::ubc(pr, c);
-                    llf<Ph, R>(uq, ub, nxo, nyo, pr, F, (R*)nullptr);
-                } else {
-                    R fx[NC], fy[NC];
-                    Ph::template flux<R>(uq, fx, fy, pr);
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) F[c] = fx[c] * nxo + fy[c] * nyo;
-                }
-#pragma unroll
-                for (int c = 0; c < NC; ++c)
-#pragma unroll
-                    for (int b = 0; b < N1; ++b) term[c][b] += (F[c] * T.wq[r]) * T.Bq[r][b];
-            }
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-#pragma unroll
-                for (int b = 0; b < N1; ++b) term[c][b] *= h;
+            // a face on the domain boundary: out of line, so the common
+            // interior path stays compact in the instruction cache
+            boundary_face_term<R, P, Ph>(m, pr, d, &Uf[0][0], &term[0][0]);
         }
 #pragma unroll
         for (int k = 0; k < N1; ++k) {
