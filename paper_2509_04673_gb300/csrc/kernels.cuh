@@ -553,6 +553,44 @@ DEV void block_min_to(double v, unsigned long long* bits) {
 // flux-limiter capacities (rounded toward zero, so they stay admissible)
 // stored for the update pass; float64 for u^e, the speed-sum reciprocal,
 // dt_e, ubar^{e,L} and the bound gaps.
+template <class R, int NC>
+struct CompVec {
+    R v[NC];
+};
+
+// low-order quantities of a boundary facet of the FP32-mixed k_pre: the
+// speed bound (inflated like the interior ones) and F(u^e, u_hat; n) in the
+// canonical orientation for FIXED (u_hat = u_bc) or OUTFLOW (u_hat = u^e);
+// uh, ul: the element's float-float mean, fn: its flux along the facet axis;
+// returns [F_0 .. F_{NC-1}, lambda]
+template <class Ph>
+__device__ __noinline__ CompVec<float, Ph::NC + 1> boundary_facet_lo(const ProbDev& pr, bool fixed, bool xf,
+                                                                    float sg, CompVec<float, Ph::NC> uh,
+                                                                    CompVec<float, Ph::NC> ul,
+                                                                    CompVec<float, Ph::NC> fn) {
+    constexpr int NC = Ph::NC;
+    const float inflate = 1.0f + 0x1p-20f;
+    const float cnx = xf ? 1.f : 0.f, cny = xf ? 0.f : 1.f;
+    float xh[NC], xl[NC], xfx[NC], xfy[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        xh[c] = fixed ? pr.ubc_f[c] : uh.v[c];
+        xl[c] = fixed ? pr.ubc_lo_f[c] : ul.v[c];
+    }
+    Ph::template flux<float>(xh, xfx, xfy, pr);
+    const float l = __fmul_rn(Ph::template max_speed<float>(uh.v, xh, sg * cnx, sg * cny, pr), inflate);
+    CompVec<float, NC + 1> out;
+    out.v[NC] = l;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const float ns = sg * fn.v[c];
+        const float nx = sg * (xf ? xfx[c] : xfy[c]);
+        const float Fo = llf_value(ns, nx, l, ff_diff(xh[c], xl[c], uh.v[c], ul.v[c]));
+        out.v[c] = sg * Fo;
+    }
+    return out;
+}
+
 template <int P, class Ph>
 DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __restrict__ u,
                         double* __restrict__ ue_out, double* __restrict__ dte_out,
@@ -633,25 +671,20 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
             for (int c = 0; c < NC; ++c)
                 F[d][c] = llf_value(fL[c], fR[c], l, ff_diff(Rh[c], Rl[c], Lh[c], Ll[c]));
         } else {
+            // boundary facet: out of line (rare; keeps the hot code small)
             const int bc = xf ? m.bc_x : m.bc_y;
-            const bool fixed = bc == BC_FIXED;
-            const float sg = self_is_L ? 1.f : -1.f;
-            float xh[NC], xl[NC], xfx[NC], xfy[NC];
+            CompVec<float, NC> vh, vl, vf;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                xh[c] = fixed ? pr.ubc_f[c] : uh[c];
-                xl[c] = fixed ? pr.ubc_lo_f[c] : ul[c];
+                vh.v[c] = uh[c];
+                vl.v[c] = ul[c];
+                vf.v[c] = xf ? fxs[c] : fys[c];
             }
-            Ph::template flux<float>(xh, xfx, xfy, pr);
-            const float l = __fmul_rn(Ph::template max_speed<float>(uh, xh, sg * cnx, sg * cny, pr), inflate);
-            lam[d] = l;
+            const CompVec<float, NC + 1> o =
+                boundary_facet_lo<Ph>(pr, bc == BC_FIXED, xf, self_is_L ? 1.f : -1.f, vh, vl, vf);
+            lam[d] = o.v[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const float ns = sg * (xf ? fxs[c] : fys[c]);
-                const float nx = sg * (xf ? xfx[c] : xfy[c]);
-                const float Fo = llf_value(ns, nx, l, ff_diff(xh[c], xl[c], uh[c], ul[c]));
-                F[d][c] = sg * Fo;
-            }
+            for (int c = 0; c < NC; ++c) F[d][c] = o.v[c];
         }
     }
     float sf = __fadd_rn(__fadd_rn(__fadd_rn(lam[0], lam[1]), lam[2]), lam[3]);
@@ -1632,6 +1665,30 @@ DEV void split(double v, T& hi, T& lo) {
     lo = T(v - (double)hi);
 }
 
+// sum over the face nodes of F(u_j, u_hat; n) on a FIXED boundary face
+// (f^H of eq. (hoflux) before the division by p+1); Uf is [NC][p+1]
+template <class R, int P, class Ph>
+__device__ __noinline__ CompVec<R, Ph::NC> fixed_face_llf_sum(const ProbDev& pr, R nx, R ny, const R* Uf) {
+    constexpr int NC = Ph::NC, N1 = P + 1;
+    CompVec<R, NC> out;
+    R* acc = out.v;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = R(0);
+    R ub[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ub[c] = PV<R>::ubc(pr, c);
+#pragma unroll
+    for (int k = 0; k < N1; ++k) {
+        R uk[NC], F[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) uk[c] = Uf[c * N1 + k];
+        llf<Ph, R>(uk, ub, nx, ny, pr, F, (R*)nullptr);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] += F[c];
+    }
+    return out;
+}
+
 template <class R, int P, class Ph>
 DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
                             const double* __restrict__ ue, const double* __restrict__ dte_a, const double* __restrict__ ubl,
@@ -1676,21 +1733,25 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
             R acc[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] = R(0);
+            if (fixed_b) {
+                // FIXED boundary face: out of line (rare; keeps the hot code small)
+                R Uf[NC * N1];
 #pragma unroll
-            for (int k = 0; k < N1; ++k) {
-                int li = (d == 0) ? k * N1 : (d == 1) ? k * N1 + P : (d == 2) ? k : P * N1 + k;
-                R uk[NC];
+                for (int k = 0; k < N1; ++k) {
+                    const int li = (d == 0) ? k * N1 : (d == 1) ? k * N1 + P : (d == 2) ? k : P * N1 + k;
 #pragma unroll
-                for (int c = 0; c < NC; ++c) uk[c] = U[c][li];
-                if (fixed_b) {
-                    R ub[NC], F[NC];
+                    for (int c = 0; c < NC; ++c) Uf[c * N1 + k] = U[c][li];
+                }
+                const CompVec<R, NC> fs = fixed_face_llf_sum<R, P, Ph>(pr, sg * cnx, sg * cny, Uf);
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) ub[c] = PV<R>::ubc(pr, c);
-                    llf<Ph, R>(uk, ub, sg * cnx, sg * cny, pr, F, (R*)nullptr);
+                for (int c = 0; c < NC; ++c) acc[c] = fs.v[c];  // acc was 0: same sums
+            } else {
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) acc[c] += F[c];
-                } else {
-                    R fx[NC], fy[NC];
+                for (int k = 0; k < N1; ++k) {
+                    const int li = (d == 0) ? k * N1 : (d == 1) ? k * N1 + P : (d == 2) ? k : P * N1 + k;
+                    R uk[NC], fx[NC], fy[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) uk[c] = U[c][li];
                     Ph::template flux<R>(uk, fx, fy, pr);
 #pragma unroll
                     for (int c = 0; c < NC; ++c) acc[c] += fx[c] * cnx + fy[c] * cny;
