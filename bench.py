@@ -210,12 +210,12 @@ def load_peaks():
 # profiles/kpp256_q2_dram_per_launch.md (kernels unchanged since; the two
 # Richardson sweeps averaged like their algorithmic bytes)
 NCU_TRAFFIC = {
-    ("k_pre", "kpp_256x256_q2"): 1135104,
-    ("k_grad_rhs", "kpp_256x256_q2"): 1065984,
-    ("k_mass_sweep", "kpp_256x256_q2"): (4226560 + 2117376) // 2,
-    ("k_res_ev", "kpp_256x256_q2"): 4409856,
-    ("k_gather_init", "kpp_256x256_q2"): 2364416,
-    ("k_update_ev", "kpp_256x256_q2"): 9334272,
+    ("k_pre", "kpp_256x256_q2"): 1124864,
+    ("k_grad_rhs", "kpp_256x256_q2"): 1066240,
+    ("k_mass_sweep", "kpp_256x256_q2"): (4227328 + 2116864) // 2,
+    ("k_res_ev", "kpp_256x256_q2"): 4303360,
+    ("k_gather_init", "kpp_256x256_q2"): 2364672,
+    ("k_update_ev", "kpp_256x256_q2"): 9260032,
     ("k_final", "kpp_256x256_q2"): 4471296,
 }
 
