@@ -205,9 +205,11 @@ DEV void node_loop(int phase, const InstDev* __restrict__ I, const Tile* __restr
 }
 
 // one SSP stage u <- a u^n + b FE(u) for every instance
-// 4 blocks per SM: the register cap (128) costs a few spills in the p = 4
-// element phases but doubles the warps that hide the latency of the tile loops
-__global__ void __launch_bounds__(BT, 4)
+// 7 blocks per SM (a 72-register cap): the spills it costs in the element
+// phases are cheaper than the latency that fewer resident warps leave
+// unhidden in the tile loops (measured: 4 blocks 11.6 ms, 6: 10.4, 7: 10.2,
+// 8: 10.3 per step of the 256-instance batch)
+__global__ void __launch_bounds__(BT, 7)
     k_batch_stage(const InstDev* __restrict__ I, int ninst, const Tile* __restrict__ et, int net,
                   const Tile* __restrict__ nt, int nnt, BatchSync* sync, float a, float b, int first,
                   int last, int kg, int ku, int mode_lo, long long limit) {
