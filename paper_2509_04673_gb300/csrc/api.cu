@@ -310,6 +310,7 @@ extern "C" cgl_status cgl_mesh_create(const cgl_mesh_desc* d, cgl_mesh** out) {
     m.inv_n2 = 1.0 / n2;
     m.inv_n1 = 1.0 / (d->p + 1);
     m.h_f = (float)m.h;
+    m.inv_h_f = (float)(1.0 / m.h);
     m.me_f = (float)m.me;
     m.me_rz_f = m.me_f;
     if ((double)m.me_rz_f > m.me) m.me_rz_f = std::nextafter(m.me_rz_f, 0.0f);

@@ -34,7 +34,7 @@ struct InstDev {
     ProbDev pr;
     float *u, *un, *g, *g2, *bg, *r, *ud, *ud2, *ER, *EW;
     double *ue, *dte, *ubl, *gam, *nu, *ube, *beta;
-    float *q, *fl, *avg;
+    float *q, *fl, *avg, *cf;
     unsigned long long *cnt, *dtbits;
     double *dt, *t, *t_end;
     int p, phys;
@@ -109,14 +109,14 @@ __device__ __noinline__ void elem_phase(int phase, const InstDev& D, int ex, int
                                         int ku) {
     switch (phase) {
         case PH_PRE:
-            dte = pre_at<float, P, Ph>(D.m, D.pr, D.u, D.ue, D.dte, D.ubl, D.gam, D.nu, D.q, D.fl, nullptr, nullptr,
+            dte = pre_at<float, P, Ph>(D.m, D.pr, D.u, D.ue, D.dte, D.ubl, D.gam, D.nu, D.q, D.fl, nullptr, D.cf,
                                        D.avg, ex, ey, e);
             break;
         case PH_RES:
             res_at<float, P, Ph>(D.m, D.pr, D.u, g_final(D, kg), D.gam, D.nu, D.ER, ex, ey, e);
             break;
         default:
-            update_at<float, P, Ph>(D.m, D.pr, D.u, ud_final(D, ku), D.ue, D.dte, D.ubl, D.q, D.fl, D.ER, nullptr,
+            update_at<float, P, Ph>(D.m, D.pr, D.u, ud_final(D, ku), D.ue, D.dte, D.ubl, D.q, D.fl, D.ER, D.cf,
                                     D.avg, D.dt, D.EW, D.ube, D.beta, D.cnt, ex, ey, e);
     }
 }
@@ -408,6 +408,7 @@ extern "C" cgl_status cgl_batch_create(cgl_state* const* states, int32_t n, cgl_
         d.ER = (float*)b.ER;
         d.EW = (float*)b.EW;
         d.avg = b.avg;
+        d.cf = b.cf;
         d.ue = b.ue;
         d.dte = b.dte;
         d.ubl = b.ubl;

@@ -35,6 +35,7 @@ struct MeshDev {
     double me, inv_me, h_over_n2, inv_h, inv_n2, inv_n1;
     float h_f, me_f, inv_me_f, h2_f, h_over_n2_f;
     float me_rz_f;         // m_i^e rounded toward zero (admissible bound gaps)
+    float inv_h_f;
 };
 
 struct ProbDev {

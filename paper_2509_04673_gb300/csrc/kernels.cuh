@@ -86,6 +86,16 @@ DEV int neighbour(const MeshDev& m, int ex, int ey, int dir) {
     return jy * m.nx + jx;
 }
 
+// coordinates (jx, jy) of the face neighbour of element (ex, ey) in
+// direction dir (0 W, 1 E, 2 S, 3 N), wrapped on periodic directions; only
+// meaningful where neighbour() is >= 0 (no integer division)
+DEV void neighbour_xy(const MeshDev& m, int ex, int ey, int dir, int& jx, int& jy) {
+    jx = ex + (dir == 0 ? -1 : dir == 1 ? 1 : 0);
+    jy = ey + (dir == 2 ? -1 : dir == 3 ? 1 : 0);
+    jx = jx < 0 ? jx + m.nx : (jx >= m.nx ? jx - m.nx : jx);
+    jy = jy < 0 ? jy + m.ny : (jy >= m.ny ? jy - m.ny : jy);
+}
+
 // 2D launches: elements as (x: ex, y: ey), nodes as (x: gx, y: gy); no
 // integer division by runtime sizes in the kernels
 DEV bool elem_of_thread(const MeshDev& m, int& ex, int& ey, int& e) {
@@ -330,9 +340,8 @@ DEV void continue_nb(int dir, const R (&src)[Dim<P>::N2], R (&dst)[Dim<P>::N2]) 
 }
 
 template <class R, int P, class Ph>
-DEV void load_comp(const R* __restrict__ u, const MeshDev& m, int e, int c, R (&V)[Dim<P>::N2]) {
+DEV void load_comp(const R* __restrict__ u, const MeshDev& m, int ex, int ey, int c, R (&V)[Dim<P>::N2]) {
     constexpr int N1 = P + 1;
-    int ex = e % m.nx, ey = e / m.nx;
 #pragma unroll
     for (int b = 0; b < N1; ++b)
 #pragma unroll
@@ -345,7 +354,7 @@ DEV void load_comp(const R* __restrict__ u, const MeshDev& m, int e, int c, R (&
 // (u_h^e - u_{h,l}^e), using sum_l omega_l = 1.
 template <class R, int P, class Ph>
 DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
-             const R (&U)[Ph::NC][Dim<P>::N2], const int (&nb)[4]) {
+             const R (&U)[Ph::NC][Dim<P>::N2], const int (&nb)[4], int ex, int ey) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
     const R wl = PV<R>::w_lin(pr), eps = PV<R>::weno_eps(pr), geps = PV<R>::gamma_eps(pr);
     const bool r2 = (pr.r == 2.0);
@@ -367,7 +376,9 @@ DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
             wt[d + 1] = R(0);
             if (nb[d] >= 0) {
                 R V[N2], W[N2];
-                load_comp<R, P, Ph>(u, m, nb[d], c, V);
+                int jx, jy;
+                neighbour_xy(m, ex, ey, d, jx, jy);
+                load_comp<R, P, Ph>(u, m, jx, jy, c, V);
                 const R v0 = V[0];
 #pragma unroll
                 for (int i = 0; i < N2; ++i) V[i] -= v0;
@@ -384,7 +395,9 @@ DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
         for (int d = 0; d < 4; ++d) {
             if (nb[d] >= 0) {
                 R V[N2], W[N2];
-                load_comp<R, P, Ph>(u, m, nb[d], c, V);
+                int jx, jy;
+                neighbour_xy(m, ex, ey, d, jx, jy);
+                load_comp<R, P, Ph>(u, m, jx, jy, c, V);
                 const R v0 = V[0];
 #pragma unroll
                 for (int i = 0; i < N2; ++i) V[i] -= v0;
@@ -630,7 +643,8 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
                     ol[d][c] = avg[(2 * c + 1) * m.E + nb[d]];
                 }
             } else {
-                const int jx = nb[d] % m.nx, jy = nb[d] / m.nx;
+                int jx, jy;
+                neighbour_xy(m, ex, ey, d, jx, jy);
                 float B[NC][N2];
                 load_block<float, P, NC>(u, m, jx, jy, B);
 #pragma unroll
@@ -726,7 +740,7 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
             cf_out[(1 + c) * m.E + e] = (float)bl;
         }
     }
-    if (NC > 1) cf_out[e] = sf;
+    cf_out[e] = sf;  // the float speed sum (dt_e in float for k_update_ev)
     float gam;
     if (pr.mode == MODE_WENO || pr.mode == MODE_WENO_L) {
         if constexpr (keepV) {
@@ -735,7 +749,7 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
             for (int i = 0; i < N2; ++i) U1[i] = U[0][i];
             gam = sensor_scalar<float, P>(pr, U1, V1, nb);
         } else {
-            gam = sensor<float, P, Ph>(m, pr, u, U, nb);
+            gam = sensor<float, P, Ph>(m, pr, u, U, nb, ex, ey);
         }
     } else {
         gam = (pr.mode == MODE_HO) ? 1.f : 0.f;
@@ -792,7 +806,8 @@ DEV double pre_at(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __rest
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
             if (nb[d] >= 0) {
-                const int jx = nb[d] % m.nx, jy = nb[d] / m.nx;
+                int jx, jy;
+                neighbour_xy(m, ex, ey, d, jx, jy);
                 cell_state<R, P, Ph>(u, m, pr, jx, jy, uo[d], fxo[d], fyo[d]);
             } else {
 #pragma unroll
@@ -828,7 +843,7 @@ DEV double pre_at(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __rest
         }
         double gam;
         if (pr.mode == MODE_WENO || pr.mode == MODE_WENO_L) {
-            gam = (double)sensor<R, P, Ph>(m, pr, u, U, nb);
+            gam = (double)sensor<R, P, Ph>(m, pr, u, U, nb, ex, ey);
         } else {
             gam = (pr.mode == MODE_HO) ? 1.0 : 0.0;
         }
@@ -1876,9 +1891,17 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) ube_out[c * m.E + e] = ubec[c];
-    const double theta = dt * rdte;
-    if (theta > 1.0) atomicAdd(&cnt[CNT_CFL], 1ull);
-    const R thR = R(theta);
+    // theta = dt / dt_e = dt s / h; FP32-mixed: in float from the float
+    // speed sum of k_pre (it weights float increments; the check counts only)
+    R thR;
+    if constexpr (sizeof(R) == 4) {
+        thR = __fmul_rn((float)dt, __fmul_rn(cf[e], m.inv_h_f));
+        if (thR > 1.f) atomicAdd(&cnt[CNT_CFL], 1ull);
+    } else {
+        const double theta = dt * rdte;
+        if (theta > 1.0) atomicAdd(&cnt[CNT_CFL], 1ull);
+        thR = R(theta);
+    }
     R ubh[NC], ubo[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) split<R>(ubec[c], ubh[c], ubo[c]);
@@ -1892,7 +1915,10 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
         return;
     }
     // f_i^e, eq. (aec) with eq. (aecb) folded into the residual
-    const R meR = PV<R>::me(m), h2 = PV<R>::h2(m), dteR = R(dte), inv_meR = PV<R>::inv_me(m);
+    const R meR = PV<R>::me(m), h2 = PV<R>::h2(m), inv_meR = PV<R>::inv_me(m);
+    R dteR;
+    if constexpr (sizeof(R) == 4) dteR = __fmul_rn(m.h_f, __frcp_rn(cf[e]));  // h / s in float
+    else dteR = R(dte);
     const R h_over_n2R = (sizeof(R) == 4) ? R(m.h_over_n2_f) : R(m.h_over_n2);
     R F[NC][N2];
     // components unrolled for p >= 3 (registers); at p <= 2 the rolled loop
