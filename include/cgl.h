@@ -178,12 +178,32 @@ cgl_status cgl_state_create(const cgl_mesh *mesh, int32_t ncomp, int32_t precisi
                             void *stream, cgl_state **out);
 void cgl_state_destroy(cgl_state *state);
 
+/* As cgl_state_create, but the nodal state itself lives in caller-owned device
+   memory: u_device holds ncomp*nny*nnx values of the state's precision
+   (float64 for CGL_FP64, float32 for CGL_FP32_MIXED), layout [comp][gy][gx]
+   as in cgl_set_state, on the current device, 16-byte aligned, u_bytes at
+   least that size.  Every stage reads and writes it in place, so a caller
+   (for instance a framework tensor) sees the state without copies.  The
+   caller keeps ownership; the memory must outlive the state, and nothing else
+   may write it while a step is in flight on the state's stream.  All scratch
+   is still allocated by the library.  CGL_EINVAL for a null, misaligned,
+   too small or non-device pointer. */
+cgl_status cgl_state_create_external(const cgl_mesh *mesh, int32_t ncomp, int32_t precision, void *u_device,
+                                     size_t u_bytes, void *stream, cgl_state **out);
+
 /* Set the problem (validated: flux/ncomp match, bounds, exponents, counts). */
 cgl_status cgl_set_problem(cgl_state *state, const cgl_problem *prob);
 
 /* Copy n = ncomp*nny*nnx float64 coefficients from the host into the state
    (rounded to float32 in FP32_MIXED). Synchronous. */
 cgl_status cgl_set_state(cgl_state *state, const double *host, size_t n);
+
+/* Nodal initialisation u_j(0) = u0(x_j) at the Bernstein nodal points x_j
+   of the uniform sub-grid (spacing h/p; Sec. 5 sets the initial coefficients
+   this way): u0(x, y, comp, ctx) is called on the host for every component
+   and node, then the values are copied as by cgl_set_state.  Synchronous. */
+cgl_status cgl_set_state_nodal(cgl_state *state, double (*u0)(double x, double y, int32_t comp, void *ctx),
+                               void *ctx);
 
 /* Copy the state to the host as float64 (exact widening in FP32_MIXED). */
 cgl_status cgl_get_state(cgl_state *state, double *host, size_t n);

@@ -73,6 +73,9 @@ _PROTOS = [
     ("cgl_mesh_destroy", None, [C.c_void_p]),
     ("cgl_mesh_sizes", C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     ("cgl_state_create", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("cgl_state_create_external", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t,
+                                            C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("cgl_set_state_nodal", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("cgl_state_destroy", None, [C.c_void_p]),
     ("cgl_set_problem", C.c_int, [C.c_void_p, C.POINTER(cgl_problem)]),
     ("cgl_set_state", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_size_t]),
@@ -165,14 +168,30 @@ class Mesh:
             self.h = None
 
 
+# u0(x, y, comp, ctx) for cgl_set_state_nodal
+NODAL_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_double, C.c_int32, C.c_void_p)
+
+
 class State:
-    def __init__(self, mesh: Mesh, ncomp: int, precision: int = FP64, stream=None):
+    """u_device / u_bytes: optional caller-owned device buffer that holds the
+    nodal state in place (cgl_state_create_external)."""
+
+    def __init__(self, mesh: Mesh, ncomp: int, precision: int = FP64, stream=None, u_device=None, u_bytes=0):
         self.mesh = mesh
         self.nc = ncomp
         h = C.c_void_p()
         s = C.c_void_p(stream) if stream else None
-        check(lib().cgl_state_create(mesh.h, ncomp, precision, s, C.byref(h)))
+        if u_device:
+            check(lib().cgl_state_create_external(mesh.h, ncomp, precision, C.c_void_p(u_device), int(u_bytes), s,
+                                                  C.byref(h)))
+        else:
+            check(lib().cgl_state_create(mesh.h, ncomp, precision, s, C.byref(h)))
         self.h = h
+
+    def set_state_nodal(self, u0):
+        """u_j(0) = u0(x_j, y_j, comp) at the nodal points (host callback)."""
+        cb = NODAL_FN(lambda x, y, c, ctx: float(u0(x, y, c)))
+        check(lib().cgl_set_state_nodal(self.h, C.cast(cb, C.c_void_p), None))
 
     def close(self):
         if getattr(self, "h", None) and _lib is not None:

@@ -398,6 +398,38 @@ extern "C" void cgl_state_destroy(cgl_state* S) {
     delete S;
 }
 
+extern "C" cgl_status cgl_state_create_external(const cgl_mesh* mesh, int32_t ncomp, int32_t precision,
+                                                void* u_device, size_t u_bytes, void* stream, cgl_state** out) {
+    if (!mesh || !out || !u_device) return fail(CGL_EINVAL, "null argument");
+    *out = nullptr;
+    if (((uintptr_t)u_device & 15) != 0) return fail(CGL_EINVAL, "u_device must be 16-byte aligned");
+    const size_t need = (size_t)(ncomp > 0 ? ncomp : 0) * (size_t)mesh->m.NN * (precision == CGL_FP64 ? 8 : 4);
+    if (u_bytes < need) return fail(CGL_EINVAL, "u_device holds %zu bytes, the state needs %zu", u_bytes, need);
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, u_device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CGL_EINVAL, "u_device is not a CUDA pointer");
+    }
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+        return fail(CGL_EINVAL, "u_device is not device memory of the current device");
+    cgl_state* S = nullptr;
+    cgl_status rc = cgl_state_create(mesh, ncomp, precision, stream, &S);
+    if (rc) return rc;
+    // hand the state's own u buffer back and adopt the caller's
+    for (size_t i = 0; i < S->allocs.size(); ++i) {
+        if (S->allocs[i] == S->B.u) {
+            cudaFree(S->allocs[i]);
+            S->allocs.erase(S->allocs.begin() + i);
+            break;
+        }
+    }
+    S->B.u = u_device;
+    *out = S;
+    return CGL_OK;
+}
+
 extern "C" cgl_status cgl_state_create(const cgl_mesh* mesh, int32_t ncomp, int32_t precision, void* stream,
                                        cgl_state** out) {
     if (!mesh || !out) return fail(CGL_EINVAL, "null argument");
@@ -604,6 +636,25 @@ static cgl_status download_any(cgl_state* S, const void* src, bool bulk, double*
 extern "C" cgl_status cgl_set_state(cgl_state* S, const double* host, size_t n) {
     if (!S) return fail(CGL_EINVAL, "null state");
     return upload_nodal(S, S->B.u, host, n);
+}
+
+extern "C" cgl_status cgl_set_state_nodal(cgl_state* S, double (*u0)(double, double, int32_t, void*), void* ctx) {
+    if (!S || !u0) return fail(CGL_EINVAL, "null argument");
+    const cgl_mesh_desc& d = S->mesh->d;
+    const MeshDev& m = S->mesh->m;
+    // nodal points of the uniform sub-grid: spacing h/p in each direction
+    const double hx = (d.x1 - d.x0) / d.nx / d.p, hy = (d.y1 - d.y0) / d.ny / d.p;
+    std::vector<double> host;
+    try {
+        host.resize(state_count(S));
+    } catch (...) {
+        return fail(CGL_EOOM, "host allocation failed");
+    }
+    size_t k = 0;
+    for (int c = 0; c < S->nc; ++c)
+        for (int gy = 0; gy < m.nny; ++gy)
+            for (int gx = 0; gx < m.nnx; ++gx) host[k++] = u0(d.x0 + gx * hx, d.y0 + gy * hy, c, ctx);
+    return upload_nodal(S, S->B.u, host.data(), host.size());
 }
 
 extern "C" cgl_status cgl_set_base_state(cgl_state* S, const double* host, size_t n) {
