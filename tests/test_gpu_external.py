@@ -28,7 +28,7 @@ def cgl():
 @pytest.mark.parametrize("prec", [0, 1])
 def test_external_buffer_steps_in_place(cgl, prec):
     import torch
-    mesh, prob, u0 = inputs.kpp_config(48, 40, 2)
+    mesh, prob, u0 = inputs.kpp_config(40, 40, 2)
     m = cgl.Mesh(mesh)
     ref = cgl.State(m, 1, prec)
     ref.set_problem(prob)
