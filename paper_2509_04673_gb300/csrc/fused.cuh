@@ -45,7 +45,8 @@ struct GradSweepWs {
 template <int P, int NC>
 __global__ void __launch_bounds__(ST_TX * ST_BY)
     k_grad_sweep(MeshDev m, const float* __restrict__ u, float* __restrict__ bout, float* __restrict__ gout) {
-    pdl_begin();
+    // like k_grad_rhs: runs beside k_pre, waits for it before exiting
+    pdl_trigger();
     using WS = GradSweepWs<P, NC>;
     constexpr int HX1 = WS::HX1, HY1 = WS::HY1, HX2 = WS::HX2, HY2 = WS::HY2, NW = WS::NW, NCL = WS::NCL;
     constexpr int NT = ST_TX * ST_BY, NJ = ST_TY / ST_BY;
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(ST_TX * ST_BY)
             const int r = i / HX2, cc = i - r * HX2;
             int gx = gx0 - 2 * P + cc, gy = gy0 - 2 * P + r;
             const bool in = wrap_node(m, gx, gy);
-            A[r][cc] = in ? u[(long long)c * m.NN + (long long)gy * m.nnx + gx] : 0.f;
+            A[r][cc] = in ? __ldcg(&u[(long long)c * m.NN + (long long)gy * m.nnx + gx]) : 0.f;
         }
         __syncthreads();
         // grad stencil along x for the columns of the p halo, all 2p-halo rows
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(ST_TX * ST_BY)
             }
         }
     }
+    pdl_wait();
 }
 
 template <int P, int NC>

@@ -52,6 +52,18 @@ DEV void pdl_begin() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// k_pre waits first and lets the next kernel be scheduled only then: when
+// k_grad_rhs / k_grad_sweep (which need only u) start, the kernel that last
+// wrote u has completed, so they can run beside k_pre.
+DEV void pdl_wait_then_trigger() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+DEV void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// the gradient kernels wait for k_pre only before they exit, so that they
+// complete after it and later kernels may rely on both
+DEV void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 
 template <int P>
 struct Dim {
@@ -890,7 +902,7 @@ __global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __
                       R* __restrict__ q_out, R* __restrict__ fl_out, R* __restrict__ EV,
                       float* __restrict__ cf_out, float* __restrict__ avg,
                       unsigned long long* __restrict__ dtbits) {
-    pdl_begin();
+    pdl_wait_then_trigger();
     int ex, ey, e;
     double dte = __longlong_as_double(0x7ff0000000000000LL);
     if (elem_of_thread(m, ex, ey, e))
@@ -1221,7 +1233,9 @@ DEV void stage_tile(const MeshDev& m, const R* __restrict__ x, R (*xs)[ST_TX + 2
         else in = gy >= 0 && gy < m.nny;
         if (m.px) gx = gx < 0 ? gx + m.nnx : (gx >= m.nnx ? gx - m.nnx : gx);
         else in = in && gx >= 0 && gx < m.nnx;
-        xs[r][c] = in ? x[(long long)gy * m.nnx + gx] : R(0);
+        // through L2 (ld.global.cg): k_grad_rhs reads u without waiting for
+        // the kernel launched just before it
+        xs[r][c] = in ? __ldcg(&x[(long long)gy * m.nnx + gx]) : R(0);
     }
 }
 
@@ -1377,13 +1391,17 @@ DEV void sweep_tile(const MeshDev& m, const R* __restrict__ xin, const R* __rest
     }
 }
 
+// needs only u, whose last writer completed before k_pre let this kernel
+// start (pdl_wait_then_trigger), so it runs beside k_pre and waits for it
+// only before exiting
 template <class R, int P, int NC>
 __global__ void __launch_bounds__(ST_TX * ST_BY) k_grad_rhs(MeshDev m, const R* __restrict__ u,
                                                             R* __restrict__ bout, R* __restrict__ gout) {
-    pdl_begin();
+    pdl_trigger();
     __shared__ R ws[StFields<R, P, NC, 2>::ws];
     grad_tile<R, P, NC, ST_BY>(m, u, bout, gout, blockIdx.x * ST_TX, blockIdx.y * ST_TY, threadIdx.x, threadIdx.y,
                                ws);
+    pdl_wait();
 }
 
 template <class R, int P, int NV>
