@@ -191,6 +191,14 @@ def algorithmic_bytes(kernel, mesh, nc, rsz, k_g, k_u):
     # sweeps follow); element residuals -> r and udot after the first sweep
     b["k_grad_sweep"] = nc * NN * rsz + 2 * nc * NN * rsz * (2 if k_g > 1 else 1)
     b["k_udot_sweep"] = E * N2 * nc * rsz + 2 * nc * NN * rsz
+    # FP32-mixed split update: k_facet reads u, ubar^{e,L}, dt_e/h (float64),
+    # Q (2), f^L (4 nc) and writes ubar^e (float64) and the facet terms;
+    # k_update_ev (k_update_el) reads u, udot, the residuals, ubar^e, the facet
+    # terms, the speed sum and the means and writes the increments and beta
+    if rsz == 4:
+        b["k_facet"] = nc * NN * 4 + (nc + 1) * E * d + (2 + 4 * nc) * E * 4 + nc * E * d + nc * E * 4
+        b["k_update_ev"] = (2 * nc * NN * 4 + E * N2 * nc * 4 + nc * E * d + nc * E * 4 + E * 4
+                            + 2 * nc * E * 4 + E * N2 * nc * 4 + E * d)
     # x_in, b -> x_out, averaged over the g_h (2 nc) and udot (nc) sweeps
     nvm = (2 * nc * k_g + nc * k_u) / max(1, k_g + k_u)
     b["k_mass_sweep"] = 3 * nvm * NN * rsz
@@ -205,7 +213,7 @@ def stage_algorithmic_bytes(mesh, nc, rsz, k_g, k_u):
     NN = mesh.nnx * mesh.nny
     E = mesh.nx * mesh.ny
     ab = lambda k: algorithmic_bytes(k, mesh, nc, rsz, k_g, k_u)
-    b = ab("k_pre") + ab("k_res_ev") + ab("k_update_ev") + ab("k_final")
+    b = ab("k_pre") + ab("k_res_ev") + ab("k_update_ev") + ab("k_final") + (ab("k_facet") if rsz == 4 else 0)
     if rsz == 4 and nc > 1:
         b += nc * NN * 4 + 2 * nc * E * 4
     if rsz == 4 and NN >= (1 << 22):
@@ -235,7 +243,6 @@ NCU_TRAFFIC = {
     ("k_mass_sweep", "kpp_256x256_q2"): (4227328 + 2116864) // 2,
     ("k_res_ev", "kpp_256x256_q2"): 4303360,
     ("k_gather_init", "kpp_256x256_q2"): 2364672,
-    ("k_update_ev", "kpp_256x256_q2"): 9260032,
     ("k_final", "kpp_256x256_q2"): 4471296,
 }
 

@@ -259,12 +259,13 @@ class State:
 
     def profile(self, nsteps):
         """Per-kernel device time (ms) and launch counts over nsteps steps."""
-        nk = 12
+        nk = 16
         ms = np.zeros(nk)
         ln = np.zeros(nk, dtype=np.int64)
         check(lib().cgl_profile(self.h, int(nsteps), nk, _dptr(ms),
                                 ln.ctypes.data_as(C.POINTER(C.c_int64))))
-        return {lib().cgl_kernel_name(i).decode(): (float(ms[i]), int(ln[i])) for i in range(nk)}
+        names = [lib().cgl_kernel_name(i).decode() for i in range(nk)]
+        return {names[i]: (float(ms[i]), int(ln[i])) for i in range(nk) if names[i]}
 
     def launches_per_step(self):
         k = C.c_int64()

@@ -394,6 +394,9 @@ extern "C" void cgl_state_destroy(cgl_state* S) {
     if (!S) return;
     if (S->step_graph) cudaGraphExecDestroy(S->step_graph);
     for (void* p : S->allocs) cudaFree(p);
+    if (S->B.ev_fork) cudaEventDestroy(S->B.ev_fork);
+    if (S->B.ev_join) cudaEventDestroy(S->B.ev_join);
+    if (S->B.st2) cudaStreamDestroy(S->B.st2);
     if (S->own_stream && S->st) cudaStreamDestroy(S->st);
     delete S;
 }
@@ -472,6 +475,7 @@ extern "C" cgl_status cgl_state_create(const cgl_mesh* mesh, int32_t ncomp, int3
         {&B.bg, 2 * nc * NN * r},     {&B.r, nc * NN * r},         {&B.ud, nc * NN * r},
         {&B.EV, 16},                  {&B.ER, E * N2 * nc * r},    {&B.EW, E * N2 * nc * r},     {(void**)&B.q, 2 * E * r},
         {(void**)&B.ue, nc * E * 8},  {(void**)&B.cf, (1 + nc) * E * 4},  {(void**)&B.avg, 2 * nc * E * 4},
+        {(void**)&B.fht, nc * E * 4},
         {(void**)&B.dte, 3 * E * 8},  {(void**)&B.fl, 4 * nc * E * r},      {(void**)&B.ubl, nc * E * 8}, {(void**)&B.gam, E * 8},
         {(void**)&B.nu, E * 8},       {(void**)&B.ube, nc * E * 8}, {(void**)&B.beta, E * 8},
         {(void**)&B.cnt, CNT_N * 8},  {(void**)&B.dtbits, 8},      {(void**)&B.dt, 8},
@@ -482,6 +486,16 @@ extern "C" cgl_status cgl_state_create(const cgl_mesh* mesh, int32_t ncomp, int3
         if (rc) {
             cgl_state_destroy(S);
             return rc;
+        }
+    }
+    // second stream and fork/join events of a stage (k_facet beside the g_h and udot kernels)
+    {
+        cudaError_t e1 = cudaStreamCreateWithFlags(&B.st2, cudaStreamNonBlocking);
+        cudaError_t e2 = e1 == cudaSuccess ? cudaEventCreateWithFlags(&B.ev_fork, cudaEventDisableTiming) : e1;
+        cudaError_t e3 = e2 == cudaSuccess ? cudaEventCreateWithFlags(&B.ev_join, cudaEventDisableTiming) : e2;
+        if (e3 != cudaSuccess) {
+            cgl_state_destroy(S);
+            return fail(CGL_ECUDA, "stream/event creation: %s", cudaGetErrorString(e3));
         }
     }
     // zero everything once so that fields read before the first stage are defined
@@ -895,7 +909,7 @@ extern "C" cgl_status cgl_time_step(cgl_state* S, double* dt) {
 // ---------------------------------------------------------------------------
 static const char* const KNAMES[KID_COUNT] = {
     "k_avg", "k_pre", "k_dt", "k_grad_rhs", "k_gather_init", "k_grad_sweep", "k_mass_sweep",
-    "k_res_ev", "k_update_ev", "k_final", "k_t_advance", "k_udot_sweep"};
+    "k_res_ev", "k_update_ev", "k_final", "k_t_advance", "k_udot_sweep", "k_facet"};
 
 // fixed-length delay (bounded both by a cycle count and by an iteration cap;
 // it waits on nothing) that keeps the stream busy while the host enqueues the
@@ -964,6 +978,7 @@ extern "C" cgl_status cgl_launches_per_step(cgl_state* S, int64_t* kernels) {
     const int lo = S->prob.mode == CGL_MODE_LO;
     int64_t per_stage = 1 + 2 + (lo ? 0 : 3 + (S->prob.k_g + S->prob.k_u));
     if (S->prec == CGL_FP32_MIXED && S->nc > 1) per_stage += 1;  // k_avg
+    if (S->prec == CGL_FP32_MIXED) per_stage += 1;                // k_facet
     if (S->prec == CGL_FP32_MIXED && !lo && fuse_sweeps(S->mesh->m) && !(S->prob.options & CGL_OPT_UNFUSED_SWEEPS)) {
         // the first sweep of each solve runs inside k_grad_sweep / k_udot_sweep
         per_stage -= (S->prob.k_g >= 1) + (S->prob.k_u >= 1);

@@ -1723,34 +1723,17 @@ __device__ __noinline__ CompVec<R, Ph::NC> fixed_face_llf_sum(const ProbDev& pr,
     return out;
 }
 
+// facet part of the element update: canonical f^H, the flux limiter and
+// ubar^e (eqs. (hoflux), (fAlim)/(uelim), Appendix A), and the facet term
+// (h/(p+1)^2) sum_d +-f^H_d of the element contributions f_i^e (eq. (aec))
 template <class R, int P, class Ph>
-DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
-                            const double* __restrict__ ue, const double* __restrict__ dte_a, const double* __restrict__ ubl,
-                            const R* __restrict__ qcap, const R* __restrict__ fl_in,
-                            const R* __restrict__ ER, const float* __restrict__ cf,
-                            const float* __restrict__ avg,
-                            const double* __restrict__ dtp, R* __restrict__ EW,
-                            double* __restrict__ ube_out, double* __restrict__ beta_out,
-                            unsigned long long* __restrict__ cnt, int ex, int ey, int e) {
-    constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2;
-    const Tab<R>& T = TabSel<R>::t(P);
+DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Dim<P>::N2], const int (&nb)[4],
+                    const double (&uec)[Ph::NC], const double (&ublc)[Ph::NC], double rs,
+                    const double* __restrict__ dte_a, const double* __restrict__ ubl,
+                    const R* __restrict__ qcap, const R* __restrict__ fl_in, const float* __restrict__ cf, int e,
+                    double (&ubec)[Ph::NC], R (&fh)[Ph::NC]) {
+    constexpr int NC = Ph::NC, N1 = P + 1;
     const double h = m.h;
-    const double me = m.me;
-    const double dt = *dtp;
-    const double dte = dte_a[e];
-    const double rs = dte_a[m.E + e];       // dt_e / h
-    const double rdte = dte_a[2 * m.E + e]; // 1 / dt_e
-    int nb[4];
-#pragma unroll
-    for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
-    R U[NC][N2];
-    load_block<R, P, NC>(u, m, ex, ey, U);
-    double uec[NC], ublc[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        uec[c] = ue[c * m.E + e];
-        ublc[c] = ubl[c * m.E + e];
-    }
     // canonical high-order facet fluxes f^H (eq. (hoflux)): face average of
     // f(u_j).n (or of F(u_j, u_hat; n) on a FIXED boundary), summed along the
     // face in a fixed order so both cells of a facet get the same value
@@ -1800,7 +1783,6 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
         }
     }
     // limited cell average ubar^e
-    double ubec[NC];
     if (pr.fl == FL_LOW) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) ubec[c] = ublc[c];
@@ -1907,8 +1889,23 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
             ubec[c] = ublc[c] + rs * os;
         }
     }
+    const R h_over_n2R = (sizeof(R) == 4) ? R(m.h_over_n2_f) : R(m.h_over_n2);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) ube_out[c * m.E + e] = ubec[c];
+    for (int c = 0; c < NC; ++c)
+        fh[c] = need_fh ? h_over_n2R * (((FHr[1][c] - FHr[0][c]) + FHr[3][c]) - FHr[2][c]) : R(0);
+}
+
+// element part of the update: theta, f_i^e (eq. (aec)), the slope limiter
+// beta_e (eqs. (slimit1), (slimit2), Appendix A) and the SSP increments
+template <class R, int P, class Ph>
+DEV void element_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Dim<P>::N2],
+                      const R* __restrict__ ud, const R* __restrict__ ER, const float* __restrict__ cf,
+                      const float* __restrict__ avg, const double (&uec)[Ph::NC], double dt, double dte, double rdte,
+                      const double (&ubec)[Ph::NC], const R (&fh)[Ph::NC], R* __restrict__ EW,
+                      double* __restrict__ beta_out, unsigned long long* __restrict__ cnt, int ex, int ey, int e) {
+    constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2;
+    const Tab<R>& T = TabSel<R>::t(P);
+    const double me = m.me;
     // theta = dt / dt_e = dt s / h; FP32-mixed: in float from the float
     // speed sum of k_pre (it weights float increments; the check counts only)
     R thR;
@@ -1937,7 +1934,6 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
     R dteR;
     if constexpr (sizeof(R) == 4) dteR = __fmul_rn(m.h_f, __frcp_rn(cf[e]));  // h / s in float
     else dteR = R(dte);
-    const R h_over_n2R = (sizeof(R) == 4) ? R(m.h_over_n2_f) : R(m.h_over_n2);
     R F[NC][N2];
     // components unrolled for p >= 3 (registers); at p <= 2 the rolled loop
     // keeps occupancy higher (measured on the Euler workloads)
@@ -1959,7 +1955,7 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
                 for (int k = 0; k < N1; ++k) s += T.M[a][k] * UD[d * N1 + k];
                 Y[d][a] = s;
             }
-        const R fh_term = h_over_n2R * (((FHr[1][c] - FHr[0][c]) + FHr[3][c]) - FHr[2][c]);
+        const R fh_term = fh[c];
         R ueh, uel;
         if constexpr (sizeof(R) == 4) {
             // the float-float mean itself (k_pre for scalars, k_avg for systems)
@@ -2039,6 +2035,42 @@ DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __re
                 thR * (((ubh[c] - U[c][i]) + ubo[c]) + (beta * F[c][i]) * inv_meR);
 }
 
+template <class R, int P, class Ph>
+DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
+                            const double* __restrict__ ue, const double* __restrict__ dte_a, const double* __restrict__ ubl,
+                            const R* __restrict__ qcap, const R* __restrict__ fl_in,
+                            const R* __restrict__ ER, const float* __restrict__ cf,
+                            const float* __restrict__ avg,
+                            const double* __restrict__ dtp, R* __restrict__ EW,
+                            double* __restrict__ ube_out, double* __restrict__ beta_out,
+                            unsigned long long* __restrict__ cnt, int ex, int ey, int e) {
+    constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2;
+    const Tab<R>& T = TabSel<R>::t(P);
+    const double h = m.h;
+    const double me = m.me;
+    const double dt = *dtp;
+    const double dte = dte_a[e];
+    const double rs = dte_a[m.E + e];       // dt_e / h
+    const double rdte = dte_a[2 * m.E + e]; // 1 / dt_e
+    int nb[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
+    R U[NC][N2];
+    load_block<R, P, NC>(u, m, ex, ey, U);
+    double uec[NC], ublc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        uec[c] = ue[c * m.E + e];
+        ublc[c] = ubl[c * m.E + e];
+    }
+    double ubec[NC];
+    R fh[NC];
+    facet_part<R, P, Ph>(m, pr, U, nb, uec, ublc, rs, dte_a, ubl, qcap, fl_in, cf, e, ubec, fh);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ube_out[c * m.E + e] = ubec[c];
+    element_part<R, P, Ph>(m, pr, U, ud, ER, cf, avg, uec, dt, dte, rdte, ubec, fh, EW, beta_out, cnt, ex, ey, e);
+}
+
 // Euler at p = 2: 3 blocks of 128 per SM (a 170-register cap, no spills)
 // instead of the 2 that the uncapped allocation leaves (measured faster)
 template <class R, int P, class Ph>
@@ -2057,6 +2089,65 @@ __global__ void __launch_bounds__(128, (Ph::NC > 1 && P == 2) ? 3 : 1) k_update_
                         ey, e);
 }
 
+
+// FP32-mixed: the update in two kernels.  k_facet needs only u and the
+// outputs of k_pre, so it runs on a second stream beside the g_h and udot
+// kernels; k_update_el then reads its ubar^e and facet terms.  Together they
+// compute what k_update_ev computes, in the same arithmetic.
+template <int P, class Ph>
+__global__ void __launch_bounds__(128) k_facet(MeshDev m, ProbDev pr, const float* __restrict__ u,
+                                               const double* __restrict__ ue, const double* __restrict__ dte_a,
+                                               const double* __restrict__ ubl, const float* __restrict__ qcap,
+                                               const float* __restrict__ fl_in, const float* __restrict__ cf,
+                                               double* __restrict__ ube_out, float* __restrict__ fht) {
+    pdl_begin();
+    constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
+    int nb[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
+    float U[NC][N2];
+    load_block<float, P, NC>(u, m, ex, ey, U);
+    double uec[NC], ublc[NC], ubec[NC];
+    float fh[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        uec[c] = ue[c * m.E + e];
+        ublc[c] = ubl[c * m.E + e];
+    }
+    facet_part<float, P, Ph>(m, pr, U, nb, uec, ublc, dte_a[m.E + e], dte_a, ubl, qcap, fl_in, cf, e, ubec, fh);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        ube_out[c * m.E + e] = ubec[c];
+        fht[c * m.E + e] = fh[c];
+    }
+}
+
+template <int P, class Ph>
+__global__ void __launch_bounds__(128, (Ph::NC > 1 && P == 2) ? 3 : 1)
+    k_update_el(MeshDev m, ProbDev pr, const float* __restrict__ u, const float* __restrict__ ud,
+                const double* __restrict__ ue, const double* __restrict__ dte_a, const float* __restrict__ ER,
+                const float* __restrict__ cf, const float* __restrict__ avg, const double* __restrict__ ube,
+                const float* __restrict__ fht, const double* __restrict__ dtp, float* __restrict__ EW,
+                double* __restrict__ beta_out, unsigned long long* __restrict__ cnt) {
+    pdl_begin();
+    constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
+    float U[NC][N2];
+    load_block<float, P, NC>(u, m, ex, ey, U);
+    double uec[NC], ubec[NC];
+    float fh[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        uec[c] = ue[c * m.E + e];
+        ubec[c] = ube[c * m.E + e];
+        fh[c] = fht[c * m.E + e];
+    }
+    element_part<float, P, Ph>(m, pr, U, ud, ER, cf, avg, uec, *dtp, dte_a[e], dte_a[2 * m.E + e], ubec, fh, EW,
+                               beta_out, cnt, ex, ey, e);
+}
 
 // ---------------------------------------------------------------------------
 // k_final: u_i^SSP = u_i + (sum_{e in E_i} increment_i^e) / |E_i| (m_i^e/m_i

@@ -23,6 +23,9 @@ struct Bufs {
     void* fl;     // low-order facet fluxes [E][4][NC]         (R)
     float* cf;    // float copies for the Euler limiter certificate [1+NC][E]: s, ubar^{e,L}
     float* avg;   // float-float cell means [2NC][E] (FP32-mixed: k_avg for systems, k_pre for scalars)
+    float* fht;   // facet terms of f_i^e [NC][E] (FP32-mixed, k_facet -> k_update_el)
+    cudaStream_t st2;            // second stream of a stage (k_facet)
+    cudaEvent_t ev_fork, ev_join;
     double *ue, *dte, *ubl, *gam, *nu, *ube, *beta;
     unsigned long long* cnt;     // CNT_N counters
     unsigned long long* dtbits;  // min dt_e as bits
@@ -32,7 +35,7 @@ struct Bufs {
 // kernel identifiers for per-kernel timing
 enum KernelId {
     KID_AVG = 0, KID_PRE, KID_DT, KID_GRAD, KID_GATHER, KID_GRADF, KID_SWEEP, KID_RES,
-    KID_UPDATE, KID_FINAL, KID_TADV, KID_UDOTF, KID_COUNT
+    KID_UPDATE, KID_FINAL, KID_TADV, KID_UDOTF, KID_FACET, KID_COUNT
 };
 
 // optional per-launch timing: CUDA events recorded around every launch on
@@ -118,6 +121,18 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
                    chk(launch(pdl, k_dt_final, dim3(1), dim3(1), st, B.dtbits, pr.cfl, (const double*)B.t,
                               (const double*)B.t_end, B.dt)));
     if (dt_only) return err != cudaSuccess ? err : cudaGetLastError();
+    // FP32-mixed: the facet part of the update on the second stream, beside
+    // the g_h and udot kernels
+    constexpr bool split_update = sizeof(R) == 4;
+    if constexpr (split_update) {
+        chk(cudaEventRecord(B.ev_fork, st));
+        chk(cudaStreamWaitEvent(B.st2, B.ev_fork, 0));
+        CGL_LAUNCH(prof, KID_FACET, B.st2,
+                   chk(launch(false, k_facet<P, Ph>, ge, be, B.st2, m, pr, (const float*)u, (const double*)B.ue,
+                              (const double*)B.dte, (const double*)B.ubl, (const float*)B.q, (const float*)B.fl,
+                              (const float*)B.cf, B.ube, B.fht)));
+        chk(cudaEventRecord(B.ev_join, B.st2));
+    }
     R* ud = (R*)B.ud;
     if (pr.mode != MODE_LO) {
         // g_h: stencil right-hand side and lumped iterate, then k_g sweeps (ping-pong)
@@ -177,6 +192,14 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
             ud2 = t;
         }
     }
+    if constexpr (split_update) {
+        chk(cudaStreamWaitEvent(st, B.ev_join, 0));
+        CGL_LAUNCH(prof, KID_UPDATE, st,
+                   chk(launch(pdl, k_update_el<P, Ph>, ge, be, st, m, pr, (const float*)u, (const float*)ud,
+                              (const double*)B.ue, (const double*)B.dte, (const float*)B.ER, (const float*)B.cf,
+                              (const float*)B.avg, (const double*)B.ube, (const float*)B.fht,
+                              (const double*)B.dt, (float*)B.EW, B.beta, B.cnt)));
+    } else
     CGL_LAUNCH(prof, KID_UPDATE, st,
                chk(launch(pdl, k_update_ev<R, P, Ph>, ge, be, st, m, pr, (const R*)u, (const R*)ud,
                           (const double*)B.ue, (const double*)B.dte, (const double*)B.ubl, (const R*)B.q,
