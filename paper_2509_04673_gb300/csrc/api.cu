@@ -396,6 +396,8 @@ extern "C" void cgl_state_destroy(cgl_state* S) {
     for (void* p : S->allocs) cudaFree(p);
     if (S->B.ev_fork) cudaEventDestroy(S->B.ev_fork);
     if (S->B.ev_join) cudaEventDestroy(S->B.ev_join);
+    if (S->B.ev_fork0) cudaEventDestroy(S->B.ev_fork0);
+    if (S->B.ev_w) cudaEventDestroy(S->B.ev_w);
     if (S->B.st2) cudaStreamDestroy(S->B.st2);
     if (S->own_stream && S->st) cudaStreamDestroy(S->st);
     delete S;
@@ -492,6 +494,8 @@ extern "C" cgl_status cgl_state_create(const cgl_mesh* mesh, int32_t ncomp, int3
     {
         cudaError_t e1 = cudaStreamCreateWithFlags(&B.st2, cudaStreamNonBlocking);
         cudaError_t e2 = e1 == cudaSuccess ? cudaEventCreateWithFlags(&B.ev_fork, cudaEventDisableTiming) : e1;
+        if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&B.ev_fork0, cudaEventDisableTiming);
+        if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&B.ev_w, cudaEventDisableTiming);
         cudaError_t e3 = e2 == cudaSuccess ? cudaEventCreateWithFlags(&B.ev_join, cudaEventDisableTiming) : e2;
         if (e3 != cudaSuccess) {
             cgl_state_destroy(S);
@@ -909,7 +913,7 @@ extern "C" cgl_status cgl_time_step(cgl_state* S, double* dt) {
 // ---------------------------------------------------------------------------
 static const char* const KNAMES[KID_COUNT] = {
     "k_avg", "k_pre", "k_dt", "k_grad_rhs", "k_gather_init", "k_grad_sweep", "k_mass_sweep",
-    "k_res_ev", "k_update_ev", "k_final", "k_t_advance", "k_udot_sweep", "k_facet"};
+    "k_res_ev", "k_update_ev", "k_final", "k_t_advance", "k_udot_sweep", "k_facet", "k_res_w"};
 
 // fixed-length delay (bounded both by a cycle count and by an iteration cap;
 // it waits on nothing) that keeps the stream busy while the host enqueues the
@@ -979,6 +983,7 @@ extern "C" cgl_status cgl_launches_per_step(cgl_state* S, int64_t* kernels) {
     int64_t per_stage = 1 + 2 + (lo ? 0 : 3 + (S->prob.k_g + S->prob.k_u));
     if (S->prec == CGL_FP32_MIXED && S->nc > 1) per_stage += 1;  // k_avg
     if (S->prec == CGL_FP32_MIXED) per_stage += 1;                // k_facet
+    if (S->prec == CGL_FP32_MIXED && !lo && split_residual(S->mesh->m)) per_stage += 1;  // k_res_w beside k_res_s
     if (S->prec == CGL_FP32_MIXED && !lo && fuse_sweeps(S->mesh->m) && !(S->prob.options & CGL_OPT_UNFUSED_SWEEPS)) {
         // the first sweep of each solve runs inside k_grad_sweep / k_udot_sweep
         per_stage -= (S->prob.k_g >= 1) + (S->prob.k_u >= 1);

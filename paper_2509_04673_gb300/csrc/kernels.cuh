@@ -1513,16 +1513,14 @@ __device__ __noinline__ void boundary_face_term(const MeshDev& m, const ProbDev&
         for (int b = 0; b < N1; ++b) term[c * N1 + b] = acc[c][b] * h;
 }
 
+// Galerkin part W^e of the element residual: volume and face terms of the
+// weak form (needs only u)
 template <class R, int P, class Ph>
-DEV void res_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ g,
-                         const double* __restrict__ gam, const double* __restrict__ nu,
-                         R* __restrict__ ER, int ex, int ey, int e) {
+DEV void w_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Dim<P>::N2], int ex, int ey,
+                R (&W)[Ph::NC][Dim<P>::N2]) {
     constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2, NQ = Dim<P>::NQ;
     const Tab<R>& T = TabSel<R>::t(P);
     const R h = PV<R>::h(m);
-    R U[NC][N2];
-    load_block<R, P, NC>(u, m, ex, ey, U);
-    R W[NC][N2];
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -1623,6 +1621,17 @@ DEV void res_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restr
             for (int c = 0; c < NC; ++c) W[c][li] -= term[c][k];
         }
     }
+}
+
+// stabilisation s^e = nu_e (K u - gamma_e G g_h) and the residual
+// R^e = W^e - s^e into ER
+template <class R, int P, class Ph>
+DEV void stab_part(const MeshDev& m, const R (&U)[Ph::NC][Dim<P>::N2], const R* __restrict__ g,
+                   const double* __restrict__ gam, const double* __restrict__ nu, const R (&W)[Ph::NC][Dim<P>::N2],
+                   R* __restrict__ ER, int ex, int ey, int e) {
+    constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2;
+    const Tab<R>& T = TabSel<R>::t(P);
+    const R h = PV<R>::h(m);
     // stabilisation s = nu (K u - gamma (Gx gx + Gy gy))
     const R nue = R(nu[e]), ge = R(gam[e]);
 #pragma unroll 1
@@ -1672,6 +1681,19 @@ DEV void res_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restr
 }
 
 // Euler at p = 2: 3 blocks of 128 per SM (170-register cap; measured faster)
+
+template <class R, int P, class Ph>
+DEV void res_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ g,
+                         const double* __restrict__ gam, const double* __restrict__ nu,
+                         R* __restrict__ ER, int ex, int ey, int e) {
+    constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
+    R U[NC][N2];
+    load_block<R, P, NC>(u, m, ex, ey, U);
+    R W[NC][N2];
+    w_part<R, P, Ph>(m, pr, U, ex, ey, W);
+    stab_part<R, P, Ph>(m, U, g, gam, nu, W, ER, ex, ey, e);
+}
+
 template <class R, int P, class Ph>
 __global__ void __launch_bounds__(128, (Ph::NC > 1 && P == 2) ? 3 : 1) k_res_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ g,
                          const double* __restrict__ gam, const double* __restrict__ nu,
@@ -2147,6 +2169,44 @@ __global__ void __launch_bounds__(128, (Ph::NC > 1 && P == 2) ? 3 : 1)
     }
     element_part<float, P, Ph>(m, pr, U, ud, ER, cf, avg, uec, *dtp, dte_a[e], dte_a[2 * m.E + e], ubec, fh, EW,
                                beta_out, cnt, ex, ey, e);
+}
+
+// FP32-mixed: the residual in two kernels.  k_res_w (the Galerkin part W^e,
+// needs only u) runs on the second stream from the start of the stage,
+// beside k_pre and the g_h kernels; k_res_s adds the stabilisation, which
+// needs g_h, gamma_e and nu_e.  W^e passes through the increment buffer,
+// which is free until k_update_el.  Same device functions as k_res_ev.
+template <int P, class Ph>
+__global__ void __launch_bounds__(128) k_res_w(MeshDev m, ProbDev pr, const float* __restrict__ u,
+                                               float* __restrict__ WV) {
+    pdl_begin();
+    constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
+    float U[NC][N2], W[NC][N2];
+    load_block<float, P, NC>(u, m, ex, ey, U);
+    w_part<float, P, Ph>(m, pr, U, ex, ey, W);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int i = 0; i < N2; ++i) WV[ev_at(m.E, e, i, c, NC)] = W[c][i];
+}
+
+template <int P, class Ph>
+__global__ void __launch_bounds__(128) k_res_s(MeshDev m, const float* __restrict__ u, const float* __restrict__ g,
+                                               const double* __restrict__ gam, const double* __restrict__ nu,
+                                               const float* __restrict__ WV, float* __restrict__ ER) {
+    pdl_begin();
+    constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
+    float U[NC][N2], W[NC][N2];
+    load_block<float, P, NC>(u, m, ex, ey, U);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int i = 0; i < N2; ++i) W[c][i] = WV[ev_at(m.E, e, i, c, NC)];
+    stab_part<float, P, Ph>(m, U, g, gam, nu, W, ER, ex, ey, e);
 }
 
 // ---------------------------------------------------------------------------

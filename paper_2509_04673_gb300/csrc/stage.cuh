@@ -25,7 +25,7 @@ struct Bufs {
     float* avg;   // float-float cell means [2NC][E] (FP32-mixed: k_avg for systems, k_pre for scalars)
     float* fht;   // facet terms of f_i^e [NC][E] (FP32-mixed, k_facet -> k_update_el)
     cudaStream_t st2;            // second stream of a stage (k_facet)
-    cudaEvent_t ev_fork, ev_join;
+    cudaEvent_t ev_fork0, ev_fork, ev_w, ev_join;
     double *ue, *dte, *ubl, *gam, *nu, *ube, *beta;
     unsigned long long* cnt;     // CNT_N counters
     unsigned long long* dtbits;  // min dt_e as bits
@@ -35,7 +35,7 @@ struct Bufs {
 // kernel identifiers for per-kernel timing
 enum KernelId {
     KID_AVG = 0, KID_PRE, KID_DT, KID_GRAD, KID_GATHER, KID_GRADF, KID_SWEEP, KID_RES,
-    KID_UPDATE, KID_FINAL, KID_TADV, KID_UDOTF, KID_FACET, KID_COUNT
+    KID_UPDATE, KID_FINAL, KID_TADV, KID_UDOTF, KID_FACET, KID_RESW, KID_COUNT
 };
 
 // optional per-launch timing: CUDA events recorded around every launch on
@@ -75,6 +75,12 @@ inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs)
 // 2048^2) and lose below (KPP 256^2: +4 %; Euler 512^2 Q3: +1.5 %).
 inline bool fuse_sweeps(const MeshDev& m) { return m.NN >= (1LL << 22); }
 
+// The split residual (k_res_w on the second stream, k_res_s) overlaps the
+// quadrature with k_pre and the g_h kernels but adds a kernel and the W^e
+// traffic: measured, it wins on KPP 1024^2 (-4 % per step) and Euler 512^2
+// Q3 (-1 %) and loses slightly at 256^2 (+0.7 %).
+inline bool split_residual(const MeshDev& m) { return m.NN >= (1LL << 20); }
+
 // Launch with programmatic stream serialisation (pdl): the kernel may be
 // scheduled while the previous kernel of the stream drains and waits for it
 // in pdl_begin(); inside a captured graph this becomes a programmatic edge.
@@ -109,6 +115,18 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
         if (e != cudaSuccess && err == cudaSuccess) err = e;
     };
     R* u = (R*)B.u;
+    // FP32-mixed: the second stream starts with the Galerkin part of the
+    // residual, which needs only u
+    constexpr bool split = sizeof(R) == 4;
+    const bool split_res = split && split_residual(m);
+    if (split_res && !dt_only && pr.mode != MODE_LO) {
+        chk(cudaEventRecord(B.ev_fork0, st));
+        chk(cudaStreamWaitEvent(B.st2, B.ev_fork0, 0));
+        if constexpr (split)
+            CGL_LAUNCH(prof, KID_RESW, B.st2,
+                       chk(launch(false, k_res_w<P, Ph>, ge, be, B.st2, m, pr, (const float*)u, (float*)B.EW)));
+        chk(cudaEventRecord(B.ev_w, B.st2));
+    }
     constexpr bool use_avg = sizeof(R) == 4 && NC > 1;
     if constexpr (use_avg)
         CGL_LAUNCH(prof, KID_AVG, st, chk(launch(pdl, k_avg<P, NC>, ge, be, st, m, (const float*)u, B.avg)));
@@ -167,9 +185,16 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
         R* ER = (R*)B.ER;
         R* r = (R*)B.r;
         R* ud2 = (R*)B.ud2;
-        CGL_LAUNCH(prof, KID_RES, st,
-                   chk(launch(pdl, k_res_ev<R, P, Ph>, ge, be, st, m, pr, (const R*)u, (const R*)g,
-                              (const double*)B.gam, (const double*)B.nu, ER)));
+        if (split_res) {
+            chk(cudaStreamWaitEvent(st, B.ev_w, 0));
+            CGL_LAUNCH(prof, KID_RES, st,
+                       chk(launch(pdl, k_res_s<P, Ph>, ge, be, st, m, (const float*)u, (const float*)g,
+                                  (const double*)B.gam, (const double*)B.nu, (const float*)B.EW, (float*)ER)));
+        } else {
+            CGL_LAUNCH(prof, KID_RES, st,
+                       chk(launch(pdl, k_res_ev<R, P, Ph>, ge, be, st, m, pr, (const R*)u, (const R*)g,
+                                  (const double*)B.gam, (const double*)B.nu, ER)));
+        }
         int k1 = 0;
         if (fuse_here && pr.k_u >= 1) {
             if constexpr (fuse)
