@@ -2133,9 +2133,10 @@ __global__ void __launch_bounds__(128) k_facet(MeshDev m, ProbDev pr, const floa
     load_block<float, P, NC>(u, m, ex, ey, U);
     double uec[NC], ublc[NC], ubec[NC];
     float fh[NC];
+    const bool need_ue = pr.fl == FL_NONE;  // u^e enters ubar^e only without the flux limiter
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        uec[c] = ue[c * m.E + e];
+        uec[c] = need_ue ? ue[c * m.E + e] : 0.0;
         ublc[c] = ubl[c * m.E + e];
     }
     facet_part<float, P, Ph>(m, pr, U, nb, uec, ublc, dte_a[m.E + e], dte_a, ubl, qcap, fl_in, cf, e, ubec, fh);
@@ -2159,16 +2160,19 @@ __global__ void __launch_bounds__(128, (Ph::NC > 1 && P == 2) ? 3 : 1)
     if (!elem_of_thread(m, ex, ey, e)) return;
     float U[NC][N2];
     load_block<float, P, NC>(u, m, ex, ey, U);
+    // the float path of element_part takes dt_e and theta from the float
+    // speed sum and the mean from the float-float pair: u^e, dt_e and 1/dt_e
+    // in float64 are not read
     double uec[NC], ubec[NC];
     float fh[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        uec[c] = ue[c * m.E + e];
+        uec[c] = 0.0;
         ubec[c] = ube[c * m.E + e];
         fh[c] = fht[c * m.E + e];
     }
-    element_part<float, P, Ph>(m, pr, U, ud, ER, cf, avg, uec, *dtp, dte_a[e], dte_a[2 * m.E + e], ubec, fh, EW,
-                               beta_out, cnt, ex, ey, e);
+    element_part<float, P, Ph>(m, pr, U, ud, ER, cf, avg, uec, *dtp, 0.0, 0.0, ubec, fh, EW, beta_out, cnt, ex, ey,
+                               e);
 }
 
 // FP32-mixed: the residual in two kernels.  k_res_w (the Galerkin part W^e,
