@@ -212,10 +212,14 @@ def stage_algorithmic_bytes(mesh, nc, rsz, k_g, k_u):
     form)."""
     NN = mesh.nnx * mesh.nny
     E = mesh.nx * mesh.ny
+    N2 = (mesh.p + 1) ** 2
     ab = lambda k: algorithmic_bytes(k, mesh, nc, rsz, k_g, k_u)
     b = ab("k_pre") + ab("k_res_ev") + ab("k_update_ev") + ab("k_final") + (ab("k_facet") if rsz == 4 else 0)
     if rsz == 4 and nc > 1:
         b += nc * NN * 4 + 2 * nc * E * 4
+    if rsz == 4 and NN >= (1 << 20):
+        # split residual: k_res_w reads u and writes W^e, k_res_s reads W^e
+        b += nc * NN * 4 + 2 * E * N2 * nc * 4
     if rsz == 4 and NN >= (1 << 22):
         b += ab("k_grad_sweep") + (k_g - 1) * 3 * 2 * nc * NN * rsz
         b += ab("k_udot_sweep") + (k_u - 1) * 3 * nc * NN * rsz
