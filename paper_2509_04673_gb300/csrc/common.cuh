@@ -186,7 +186,7 @@ HDEV float fma_hd(float a, float b, float c) {
 }
 
 #ifdef __CUDA_ARCH__
-__device__ __noinline__ void sincos_wide(float x, float* s, float* c) { sincosf(x, s, c); }
+static __device__ __noinline__ void sincos_wide(float x, float* s, float* c) { sincosf(x, s, c); }
 #else
 inline void sincos_wide(float x, float* s, float* c) {
     *s = (float)std::sin((double)x);
