@@ -2,7 +2,7 @@
 """Benchmark of the explicit SSP-RK stage of the element-based convex-limited
 CG-WENO scheme on one GB300 (per rank), printing one JSON line.
 
-Workload: the KPP problem (f(u) = (sin u, cos u), Sec. 5.4.2 of the paper) on
+Workload: the KPP problem (f(u) = (sin u, cos u), Sec. 5.3.2 of the paper) on
 a 256 x 256 mesh of Bernstein Q2 elements, fixed boundary state pi/4,
 WENO-L with the flux limiter.  A step is one SSP-RK3 time step (three
 stages of the whole hot path plus the global time-step reduction); the

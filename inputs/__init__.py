@@ -29,6 +29,7 @@ MASK64 = (1 << 64) - 1
 BC_PERIODIC = 0
 BC_OUTFLOW = 1
 BC_FIXED = 2
+BC_WALL = 3
 
 FLUX_ADVECTION = 0
 FLUX_BURGERS = 1
@@ -104,7 +105,7 @@ class Problem:
     flux: int = FLUX_ADVECTION
     vx: float = 1.0
     vy: float = 0.5
-    gamma_gas: float = 1.4            # Sec. 5.3: gamma = 1.4
+    gamma_gas: float = 1.4            # Sec. 5.2: gamma = 1.4
     mode: int = MODE_WENO_L
     flux_limiter: int = 1
     umin: float = 0.0
@@ -113,13 +114,16 @@ class Problem:
     q: float = 1.0                    # Sec. 5: q = 1 unless stated
     r: float = 2.0                    # Sec. 2.2: r = 2 (Jiang-Shu default)
     weno_eps: float = 1e-12
-    w_lin: float = 1e-3               # Sec. 5.5: default 1e-3; Sec. 5.4 uses 0.2 (2D scalar)
+    w_lin: float = 1e-3               # Sec. 5.4: default 1e-3; Sec. 5.3 uses 0.2 (2D scalar)
     gamma_eps: float = 1e-12
     cfl: float = 0.2
     k_g: int = 1
     k_u: int = 1
     lambda_floor: float = 1e-12
     ubc: tuple = (0.0, 0.0, 0.0, 0.0)
+    # optional per-side boundary table {side: boundary_side(...)} for the
+    # sides W, E, S, N; None: the mesh's bc_x / bc_y with the state ubc
+    boundary: dict | None = None
 
     @property
     def ncomp(self) -> int:
@@ -178,7 +182,7 @@ def advection_config(nx=32, ny=32, p=2, seed_index=1, **prob):
 
 def kpp_config(nx=256, ny=256, p=2, **prob):
     """KPP problem: f(u) = (sin u, cos u) on (-2,2)x(-2.5,1.5), u0 = 7pi/2 in r<=1
-    else pi/4 (Sec. 5.4.2), fixed boundary state pi/4."""
+    else pi/4 (Sec. 5.3.2), fixed boundary state pi/4."""
     mesh = Mesh(nx, ny, p, -2.0, 2.0, -2.5, 1.5, BC_FIXED, BC_FIXED)
     lo, hi = math.pi / 4, 3.5 * math.pi
     problem = Problem(flux=FLUX_KPP, umin=lo, umax=hi, cfl=0.2, w_lin=0.2,
@@ -244,6 +248,55 @@ def euler_blast_config(nx=2048, ny=2048, p=2, energy=0.25, **prob):
     block[gy0:gy1 + 1, gx0:gx1 + 1] = True
     total_w = w[block].sum()
     u0[3][block] += energy / total_w
+    return mesh, problem, u0
+
+
+def boundary_side(kind, state=(0.0, 0.0, 0.0, 0.0), kind_hi=None, state_hi=None, s0=math.inf, s1=0.0):
+    """Boundary data of one side: points whose coordinate along the side lies
+    below s0 + s1 t take (kind, state), the others (kind_hi, state_hi)
+    (default: the same)."""
+    kh = kind if kind_hi is None else kind_hi
+    sh = state if state_hi is None else state_hi
+    return {"kind": (int(kind), int(kh)),
+            "state": (tuple(float(v) for v in state), tuple(float(v) for v in sh)),
+            "s0": float(s0), "s1": float(s1)}
+
+
+def dmr_states(gamma=1.4):
+    """Post-shock and pre-shock states of the double Mach reflection (Sec. 5.4
+    of the paper): (rho, vx, vy, p) = (8, 8.25 cos 30deg, -8.25 sin 30deg,
+    116.5) and (1.4, 0, 0, 1), as conserved variables."""
+    a = math.radians(30.0)
+    post = euler_primitive_to_conserved(np.array(8.0), np.array(8.25 * math.cos(a)),
+                                        np.array(-8.25 * math.sin(a)), np.array(116.5), gamma)
+    pre = euler_primitive_to_conserved(np.array(1.4), np.array(0.0), np.array(0.0), np.array(1.0), gamma)
+    return tuple(float(v) for v in post), tuple(float(v) for v in pre)
+
+
+def dmr_config(ny=192, p=2, **prob):
+    """Double Mach reflection on (0,4) x (0,1) with 4 ny x ny elements (Sec.
+    5.4): post-shock state for x < 1/6 + y/sqrt(3), pre-shock state elsewhere
+    (nodal values); boundary: W inflow (post-shock), E outflow, S post-shock
+    inflow for x < 1/6 and reflecting wall for x >= 1/6, N post-shock inflow
+    for x < 1/6 + (1 + 20 t)/sqrt(3) and pre-shock inflow beyond.  The
+    paper's meshes: Q1 with ny = 384 and Q2 with ny = 192 (591,745 nodes)."""
+    mesh = Mesh(4 * ny, ny, p, 0.0, 4.0, 0.0, 1.0, BC_OUTFLOW, BC_OUTFLOW)
+    problem = Problem(flux=FLUX_EULER, w_lin=1e-3, q=1.0, cfl=0.2, umin=0.0, umax=0.0)
+    for k, v in prob.items():
+        setattr(problem, k, v)
+    post, pre = dmr_states(problem.gamma_gas)
+    r3 = math.sqrt(3.0)
+    problem.boundary = {
+        "W": boundary_side(BC_FIXED, post),
+        "E": boundary_side(BC_OUTFLOW),
+        "S": boundary_side(BC_FIXED, post, BC_WALL, post, s0=1.0 / 6.0),
+        "N": boundary_side(BC_FIXED, post, BC_FIXED, pre, s0=1.0 / 6.0 + 1.0 / r3, s1=20.0 / r3),
+    }
+    X, Y = node_coords(mesh)
+    left = X < 1.0 / 6.0 + Y / r3
+    u0 = np.zeros((4,) + X.shape)
+    for c in range(4):
+        u0[c] = np.where(left, post[c], pre[c])
     return mesh, problem, u0
 
 

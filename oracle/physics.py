@@ -6,9 +6,9 @@ Arrays carry the component axis first: u has shape (ncomp, ...).
 Sources:
   * LLF flux F(uL, uR; n) = (f(uL) + f(uR))/2 . n - lambda/2 (uR - uL),
     Sec. 3, eq. (fluxLLF).
-  * KPP flux f(u) = (sin u, cos u), Sec. 5.4.2.
-  * Euler: p = (gamma - 1)(rho E - |rho v|^2 / (2 rho)), Sec. 5.3; sound
-    speed c = sqrt(max(0, gamma p / rho)), Sec. 5.3.3.
+  * KPP flux f(u) = (sin u, cos u), Sec. 5.3.2.
+  * Euler: p = (gamma - 1)(rho E - |rho v|^2 / (2 rho)), Sec. 5.2; sound
+    speed c = sqrt(max(0, gamma p / rho)), Sec. 5.2.2.
   * Max speeds are deferred by the paper to its references (Sec. 2.2).
     Readings used here: advection |v.n|; Burgers max(|uL|,|uR|) |nx + ny|;
     KPP 1 (|f'(u).n| <= 1); Euler the two-rarefaction upper bound of

@@ -40,7 +40,10 @@ import numpy as np
 from . import physics as ph
 from .tables import tables
 
-BC_PERIODIC, BC_OUTFLOW, BC_FIXED = 0, 1, 2
+BC_PERIODIC, BC_OUTFLOW, BC_FIXED, BC_WALL = 0, 1, 2, 3
+SIDES = ("W", "E", "S", "N")
+# SSP-RK3 stage times t + c dt of the Shu-Osher stages
+SSP3_C = (0.0, 1.0, 0.5)
 MODE_LO, MODE_HO, MODE_WENO, MODE_WENO_L = 0, 1, 2, 3
 FL_NONE, FL_LIMITED, FL_LOW = 0, 1, 2
 
@@ -199,18 +202,75 @@ def _prob(prob):
     return prob if isinstance(prob, dict) else prob.as_dict()
 
 
+def boundary_table(om: OracleMesh, prob, nc):
+    """Boundary data of the four sides W, E, S, N as
+    {side: (kinds, states, s0, s1)}.  The part of a side whose coordinate
+    (y on W and E, x on S and N) lies below s(t) = s0 + s1 t takes
+    (kinds[0], states[0]), the rest (kinds[1], states[1]).  Without a
+    "boundary" entry each non-periodic side takes its axis's bc and the
+    state ubc everywhere (Sec. 2: weakly imposed data u_hat)."""
+    b = prob.get("boundary")
+    tab = {}
+    for side in SIDES:
+        if b is None:
+            bc = om.bc_x if side in ("W", "E") else om.bc_y
+            st = np.asarray(prob["ubc"][:nc], dtype=np.float64)
+            tab[side] = ((bc, bc), (st, st), math.inf, 0.0)
+        else:
+            sd = b[side]
+            kinds = tuple(int(k) for k in sd["kind"])
+            states = tuple(np.asarray(list(x)[:nc], dtype=np.float64) for x in sd["state"])
+            tab[side] = (kinds, states, float(sd["s0"]), float(sd["s1"]))
+    return tab
+
+
+def side_hi(spec, pos, ts):
+    """True where a boundary point at coordinate pos lies at or above the
+    split s0 + s1 ts of its side (stage time ts)."""
+    _, _, s0, s1 = spec
+    sp = s0 if s1 == 0.0 else s0 + s1 * ts
+    return np.asarray(pos) >= sp
+
+
+def side_is_plain(spec):
+    """A side that is OUTFLOW everywhere: F(u, u; n) = f(u).n."""
+    return spec[0][0] == BC_OUTFLOW and spec[0][1] == BC_OUTFLOW
+
+
+def external_state(side, spec, hi, Uin):
+    """u_hat at boundary points of one side from the interior states Uin
+    (nc, ...): FIXED gives the side's state, OUTFLOW the interior state and
+    WALL the interior state with the normal momentum reversed,
+    m - 2 (m.n) n (a reflecting wall; the sides' normals are +-x, +-y)."""
+    Uin = np.asarray(Uin, dtype=np.float64)
+    out = Uin.copy()
+    hi = np.broadcast_to(hi, Uin.shape[1:])
+    for slot, sel in ((0, ~hi), (1, hi)):
+        if not sel.any():
+            continue
+        kind, state = spec[0][slot], spec[1][slot]
+        if kind == BC_FIXED:
+            out[:, sel] = state[:, None]
+        elif kind == BC_WALL:
+            comp = 1 if side in ("W", "E") else 2
+            out[comp, sel] = -Uin[comp, sel]
+    return out
+
+
 def cell_averages(om: OracleMesh, U):
     """u^e = (1/|K_e|) sum_i m_i^e u_i = mean of the (p+1)^2 coefficients, eq. (ueold)."""
     return U.mean(axis=2)
 
 
-def facet_states(om: OracleMesh, ue, prob):
+def facet_states(om: OracleMesh, ue, prob, t=0.0):
     """Left/right cell states of the canonical x- and y-facets; on a
-    non-periodic boundary the external state is the fixed state (FIXED) or
-    the cell's own average (OUTFLOW, the reading F(u, u; n) = f(u).n)."""
+    non-periodic boundary the external state is u_hat of the side at the
+    facet midpoint and time t, taken from the cell's own average (FIXED: the
+    side's state; OUTFLOW: the average itself, the reading F(u, u; n) =
+    f(u).n; WALL: the average with reversed normal momentum)."""
     nc = ue.shape[0]
-    ub = np.asarray(prob["ubc"][:nc], dtype=np.float64)
-    nx, ny = om.nx, om.ny
+    tab = boundary_table(om, prob, nc)
+    nx, ny, h = om.nx, om.ny, om.h
     ue3 = ue.reshape(nc, ny, nx)
     out = {}
     # x-facets [ey, i]
@@ -222,12 +282,11 @@ def facet_states(om: OracleMesh, ue, prob):
     else:
         R[:, :, :nx] = ue3
         L[:, :, 1:] = ue3
-        if om.bc_x == BC_FIXED:
-            L[:, :, 0] = ub[:, None]
-            R[:, :, nx] = ub[:, None]
-        else:
-            L[:, :, 0] = ue3[:, :, 0]
-            R[:, :, nx] = ue3[:, :, nx - 1]
+        ymid = om.y0 + (np.arange(ny) + 0.5) * h
+        for side, col, dst in (("W", 0, (L, 0)), ("E", nx - 1, (R, nx))):
+            spec = tab[side]
+            own = ue3[:, :, col]
+            dst[0][:, :, dst[1]] = external_state(side, spec, side_hi(spec, ymid, t), own)
     out["x"] = (L.reshape(nc, -1), R.reshape(nc, -1))
     # y-facets stored [ex, j]
     ueT = ue3.transpose(0, 2, 1)   # [c, ex, ey]
@@ -239,12 +298,11 @@ def facet_states(om: OracleMesh, ue, prob):
     else:
         R[:, :, :ny] = ueT
         L[:, :, 1:] = ueT
-        if om.bc_y == BC_FIXED:
-            L[:, :, 0] = ub[:, None]
-            R[:, :, ny] = ub[:, None]
-        else:
-            L[:, :, 0] = ueT[:, :, 0]
-            R[:, :, ny] = ueT[:, :, ny - 1]
+        xmid = om.x0 + (np.arange(nx) + 0.5) * h
+        for side, row, dst in (("S", 0, (L, 0)), ("N", ny - 1, (R, ny))):
+            spec = tab[side]
+            own = ueT[:, :, row]
+            dst[0][:, :, dst[1]] = external_state(side, spec, side_hi(spec, xmid, t), own)
     out["y"] = (L.reshape(nc, -1), R.reshape(nc, -1))
     return out
 
@@ -264,12 +322,12 @@ def _facet_kind(om, axis):
     return k.ravel()
 
 
-def low_order_facets(om: OracleMesh, ue, prob):
+def low_order_facets(om: OracleMesh, ue, prob, t=0.0):
     """lambda_ee' and f^L_ee' = F(u^e, u^e'; n_ee') on canonical facets
     (normal +x or +y), Sec. 3 eq. (uebar2) and Sec. 4 (f^L).  Boundary facets
     use the cell's outward normal and are stored with the canonical sign."""
     kind = prob["flux"]
-    st = facet_states(om, ue, prob)
+    st = facet_states(om, ue, prob, t)
     res = {}
     for axis, (nx_, ny_) in (("x", (1.0, 0.0)), ("y", (0.0, 1.0))):
         L, R = st[axis]
@@ -387,7 +445,7 @@ def boundary_face_mask(om: OracleMesh, name):
     return (om.EY == om.ny - 1) & (not om.py)
 
 
-def element_residual(om: OracleMesh, U, prob):
+def element_residual(om: OracleMesh, U, prob, t=0.0):
     """W_i^e = int grad phi_i . f(u_h) - sum_{interior faces} int phi_i f_h.n
               - sum_{faces on dOmega} int phi_i F(u_h, u_hat; n).
 
@@ -405,7 +463,7 @@ def element_residual(om: OracleMesh, U, prob):
     fx, fy = ph.flux(kind, Uq, prob)
     W = h * ((fx * om.Wq) @ om.dPx + (fy * om.Wq) @ om.dPy)
     M = T["M"]
-    ub = np.asarray(prob["ubc"][:nc], dtype=np.float64)
+    tab = boundary_table(om, prob, nc)
     for name, (nxo, nyo) in _face_geometry(om):
         fn = om.face_nodes[name]
         Uf = U[:, :, fn]                                 # (nc, E, n) face coefficients
@@ -415,29 +473,36 @@ def element_residual(om: OracleMesh, U, prob):
         fnrm = ph.normal_flux(kind, Uf, nxo, nyo, prob)
         term = h * fnrm @ M.T
         if bmask.any():
-            bc = om.bc_x if name in ("W", "E") else om.bc_y
-            # boundary: int_S phi_i F(u_h, u_hat; n) ds by Gauss quadrature
+            spec = tab[name]
+            # boundary: int_S phi_i F(u_h, u_hat; n) ds by Gauss quadrature,
+            # u_hat taken at each Gauss point of the face at time t
             Ufq = Uf[:, bmask] @ T["Bq"].T               # (nc, nb, nq)
-            if bc == BC_FIXED:
-                ext = np.broadcast_to(ub[:, None, None], Ufq.shape)
-                Fq, _ = ph.llf(kind, Ufq, ext, nxo, nyo, prob)
-            else:
+            if side_is_plain(spec):
                 Fq = ph.normal_flux(kind, Ufq, nxo, nyo, prob)
+            else:
+                # coordinate along the side of the Gauss points
+                cell = (om.EY if name in ("W", "E") else om.EX)[bmask]
+                o0 = om.y0 if name in ("W", "E") else om.x0
+                pos = (o0 + cell * h)[:, None] + T["xq"][None, :] * h
+                ext = external_state(name, spec, side_hi(spec, pos, t), Ufq)
+                Fq, _ = ph.llf(kind, Ufq, ext, nxo, nyo, prob)
             term_b = h * (Fq * T["wq"]) @ T["Bq"]        # (nc, nb, n)
             term[:, bmask] = term_b
         W[:, :, fn] -= term
     return W
 
 
-def high_order_facets(om: OracleMesh, u, prob):
+def high_order_facets(om: OracleMesh, u, prob, t=0.0):
     """f^H_ee' on canonical facets, eq. (hoflux): the face average of f_h.n,
     (1/(p+1)) sum_{j on S} f(u_j).n (Bernstein face integrals equal
-    |S|/(p+1)); on a FIXED boundary the average LLF flux f^d_ee' with the
-    nodal Riemann data (u_j, u_hat)."""
+    |S|/(p+1)); on a boundary side that is not OUTFLOW everywhere the
+    average LLF flux f^d_ee' with the nodal Riemann data (u_j, u_hat_j),
+    u_hat_j taken at the node's position x_j and time t."""
     kind = prob["flux"]
     nc = u.shape[0]
     p, nx, ny = om.p, om.nx, om.ny
-    ub = np.asarray(prob["ubc"][:nc], dtype=np.float64)
+    tab = boundary_table(om, prob, nc)
+    hn = om.h / p
     uu = u.reshape(nc, om.nny, om.nnx)
     b = np.arange(p + 1)
     # x-facets [ey, i]: face nodes gx = i p, gy = ey p + b
@@ -447,10 +512,13 @@ def high_order_facets(om: OracleMesh, u, prob):
         GY = GY % om.nny
     Uf = uu[:, GY[:, None, :], GX[None, :, None]]            # (nc, ny, nfx, p+1)
     Fx = ph.normal_flux(kind, Uf, 1.0, 0.0, prob).mean(axis=-1)
-    if not om.px and om.bc_x == BC_FIXED:
-        for i, sgn in ((0, -1.0), (nx, 1.0)):
+    if not om.px:
+        for side, i, sgn in (("W", 0, -1.0), ("E", nx, 1.0)):
+            spec = tab[side]
+            if side_is_plain(spec):
+                continue
             Ub = Uf[:, :, i, :]
-            ext = np.broadcast_to(ub[:, None, None], Ub.shape)
+            ext = external_state(side, spec, side_hi(spec, om.y0 + GY * hn, t), Ub)
             Fj, _ = ph.llf(kind, Ub, ext, sgn, 0.0, prob)
             Fx[:, :, i] = sgn * Fj.mean(axis=-1)
     # y-facets [ex, j]: face nodes gy = j p, gx = ex p + b
@@ -460,10 +528,13 @@ def high_order_facets(om: OracleMesh, u, prob):
         GX = GX % om.nnx
     Uf = uu[:, GY[None, :, None], GX[:, None, :]]            # (nc, nx, nfy, p+1)
     Fy = ph.normal_flux(kind, Uf, 0.0, 1.0, prob).mean(axis=-1)
-    if not om.py and om.bc_y == BC_FIXED:
-        for j, sgn in ((0, -1.0), (ny, 1.0)):
+    if not om.py:
+        for side, j, sgn in (("S", 0, -1.0), ("N", ny, 1.0)):
+            spec = tab[side]
+            if side_is_plain(spec):
+                continue
             Ub = Uf[:, :, j, :]
-            ext = np.broadcast_to(ub[:, None, None], Ub.shape)
+            ext = external_state(side, spec, side_hi(spec, om.x0 + GX * hn, t), Ub)
             Fj, _ = ph.llf(kind, Ub, ext, 0.0, sgn, prob)
             Fy[:, :, j] = sgn * Fj.mean(axis=-1)
     return Fx.reshape(nc, -1), Fy.reshape(nc, -1)
@@ -560,9 +631,10 @@ def slope_limit(om: OracleMesh, fie, ube, prob):
     return euler_alpha(ub, fie, m, prob).min(axis=1)
 
 
-def fe_stage(mesh, prob, u, dt):
+def fe_stage(mesh, prob, u, dt, t=0.0):
     """One forward-Euler stage u -> u^SSP, eq. (eq:SSPupdate), with all
-    intermediates.  u has shape (nc, nny, nnx)."""
+    intermediates.  u has shape (nc, nny, nnx); t is the stage time, which
+    only time-dependent boundary data use."""
     prob = _prob(prob)
     om = mesh if isinstance(mesh, OracleMesh) else OracleMesh(mesh)
     kind, mode, fl = prob["flux"], int(prob["mode"]), int(prob["flux_limiter"])
@@ -570,14 +642,14 @@ def fe_stage(mesh, prob, u, dt):
     uf = u.reshape(nc, -1)
     U = om.blocks(u)
     ue = cell_averages(om, U)
-    lo = low_order_facets(om, ue, prob)
+    lo = low_order_facets(om, ue, prob, t)
     dte = pseudo_time_steps(om, lo, prob)
     FLx, FLy = lo["x"][0], lo["y"][0]
     ubL = ue - (dte / om.h) * outward_sum(om, FLx, FLy)          # eq. (uelowFCT)
     info = dict(ue=ue, dte=dte, ubL=ubL)
     need_ho = mode != MODE_LO or fl != FL_LOW
     if need_ho:
-        FHx, FHy = high_order_facets(om, u, prob)
+        FHx, FHy = high_order_facets(om, u, prob, t)
     # limited cell averages, eq. (uelim)
     if fl == FL_LOW:
         ube = ubL.copy()
@@ -602,7 +674,7 @@ def fe_stage(mesh, prob, u, dt):
         nu = lam_e * om.h / (2.0 * om.p)
         gx, gy = gradient_projection(om, U, prob)
         Gx, Gy = om.blocks(gx.reshape(u.shape)), om.blocks(gy.reshape(u.shape))
-        W = element_residual(om, U, prob)
+        W = element_residual(om, U, prob, t)
         s = nu[None, :, None] * (U @ om.Stiff2.T
                                  - gamma[None, :, None] * (Gx @ om.Gx2.T + Gy @ om.Gy2.T))
         Rl = W - s
@@ -653,9 +725,10 @@ def bound_check(prob, u, clamp=True):
 SSP3 = ((0.0, 1.0), (0.75, 0.25), (1.0 / 3.0, 2.0 / 3.0))
 
 
-def ssp_stage(mesh, prob, u, un, dt, a, b):
-    """u_out = a u^n + b FE(u), then the invariant-domain check (clamp)."""
-    ufe, info = fe_stage(mesh, prob, u, dt)
+def ssp_stage(mesh, prob, u, un, dt, a, b, t=0.0):
+    """u_out = a u^n + b FE(u) with FE taken at stage time t, then the
+    invariant-domain check (clamp)."""
+    ufe, info = fe_stage(mesh, prob, u, dt, t)
     out = a * un + b * ufe if a != 0.0 else b * ufe
     out, viol, ncl = bound_check(prob, out)
     info["violations"] = viol
@@ -663,14 +736,14 @@ def ssp_stage(mesh, prob, u, un, dt, a, b):
     return out, info
 
 
-def time_step(mesh, prob, u):
+def time_step(mesh, prob, u, t=0.0):
     """Global dt = cfl * min_e dt_e from the state u, eq. (cflglob) scaled by
     omega_CFL (Sec. 5)."""
     prob = _prob(prob)
     om = mesh if isinstance(mesh, OracleMesh) else OracleMesh(mesh)
     U = om.blocks(u)
     ue = cell_averages(om, U)
-    lo = low_order_facets(om, ue, prob)
+    lo = low_order_facets(om, ue, prob, t)
     return prob["cfl"] * pseudo_time_steps(om, lo, prob).min()
 
 
@@ -682,10 +755,10 @@ def run(mesh, prob, u, nsteps, t_end=math.inf, t=0.0, collect=False):
     for _ in range(nsteps):
         if t >= t_end:
             break
-        dt = min(time_step(om, prob, u), t_end - t)
+        dt = min(time_step(om, prob, u, t), t_end - t)
         un = u
-        for (a, b) in SSP3:
-            u, info = ssp_stage(om, prob, u, un, dt, a, b)
+        for (a, b), c in zip(SSP3, SSP3_C):
+            u, info = ssp_stage(om, prob, u, un, dt, a, b, t if c == 0.0 else t + c * dt)
             stats["violations"] += info["violations"]
             stats["clamps"] += info["clamps"]
         t += dt

@@ -1,0 +1,184 @@
+"""Pins of the oracle's per-side boundary data (reflecting wall, FIXED and
+OUTFLOW parts, a split that moves with time), checked against what the
+mathematics fixes rather than against the oracle itself:
+
+  * a reflecting wall carries no mass and no energy: in a closed box of
+    walls the sums of m_i rho_i and m_i E_i stay constant to rounding over
+    several SSP-RK3 steps (a mirrored tangential instead of normal
+    momentum, or a wrong sign, puts a mass flux through the wall);
+  * with walls only on S and N and periodic x, the total x-momentum is
+    conserved too (the wall flux has no tangential component);
+  * a gas at rest in a closed box stays at rest (the boundary pressure term
+    balances the volume term exactly; a dropped or sign-flipped boundary
+    term moves the wall nodes);
+  * a uniform flow parallel to the walls of a channel with the same state
+    imposed at the inlet and an outlet is preserved (free-stream
+    preservation: u_hat = u on every boundary point);
+  * a table with one FIXED kind per side reproduces the per-axis FIXED
+    condition bit for bit, and a split s0 + s1 t at stage time t gives the
+    same stage as the static split at s0 + s1 t;
+  * the double Mach reflection data of Sec. 5.4: at the start the
+    post-shock region and the boundary data agree, so the boundary facets
+    next to x = 0 carry the post-shock flux exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+from inputs import BC_FIXED, BC_OUTFLOW, BC_PERIODIC, BC_WALL, Mesh, Problem, boundary_side
+import oracle.scheme as S
+from oracle import physics as ph
+
+
+def _walls(sides="WESN", periodic_x=False):
+    b = {}
+    for s in "WESN":
+        if periodic_x and s in "WE":
+            b[s] = boundary_side(BC_PERIODIC)
+        elif s in sides:
+            b[s] = boundary_side(BC_WALL)
+        else:
+            b[s] = boundary_side(BC_OUTFLOW)
+    return b
+
+
+def _euler_problem(**kw):
+    p = Problem(flux=inputs.FLUX_EULER, w_lin=1e-3, cfl=0.2, umin=0.0, umax=0.0)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _smooth_euler_state(mesh, seed):
+    """Positive density and pressure with smooth variation (random phases)."""
+    rng = inputs.SplitMix64(inputs.BASE_SEED + seed)
+    X, Y = inputs.node_coords(mesh)
+    ph_ = [rng.uniform(0.0, 2 * math.pi) for _ in range(4)]
+    rho = 1.0 + 0.3 * np.sin(2 * math.pi * X + ph_[0]) * np.cos(2 * math.pi * Y + ph_[1])
+    vx = 0.4 * np.sin(2 * math.pi * Y + ph_[2])
+    vy = 0.3 * np.cos(2 * math.pi * X + ph_[3])
+    p = 1.0 + 0.2 * np.cos(2 * math.pi * (X + Y))
+    return inputs.euler_primitive_to_conserved(rho, vx, vy, p)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_closed_box_conserves_mass_and_energy(p):
+    mesh = Mesh(6, 5, p, 0.0, 1.2, 0.0, 1.0, BC_OUTFLOW, BC_OUTFLOW)
+    prob = _euler_problem(boundary=_walls())
+    u0 = _smooth_euler_state(mesh, 11)
+    m0 = S.mass(mesh, u0)
+    u, t, st = S.run(mesh, prob.as_dict(), u0, 4)
+    m1 = S.mass(mesh, u)
+    assert st["violations"] == 0
+    for c in (0, 3):
+        assert abs(m1[c] - m0[c]) <= 1e-13 * abs(m0[c]), c
+    # momentum is not conserved: the walls push back
+    assert abs(m1[1] - m0[1]) > 1e-9
+
+
+def test_channel_conserves_tangential_momentum():
+    mesh = Mesh(6, 5, 2, 0.0, 1.2, 0.0, 1.0, BC_PERIODIC, BC_OUTFLOW)
+    prob = _euler_problem(boundary=_walls("SN", periodic_x=True))
+    u0 = _smooth_euler_state(mesh, 12)
+    m0 = S.mass(mesh, u0)
+    u, _, _ = S.run(mesh, prob.as_dict(), u0, 4)
+    m1 = S.mass(mesh, u)
+    for c in (0, 1, 3):
+        assert abs(m1[c] - m0[c]) <= 1e-13 * max(abs(m0[c]), 1.0), c
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_rest_state_in_closed_box(p):
+    mesh = Mesh(4, 3, p, 0.0, 4 / 3, 0.0, 1.0, BC_OUTFLOW, BC_OUTFLOW)
+    prob = _euler_problem(boundary=_walls())
+    shape = (mesh.nny, mesh.nnx)
+    u0 = inputs.euler_primitive_to_conserved(np.full(shape, 1.3), np.zeros(shape), np.zeros(shape),
+                                             np.full(shape, 2.0))
+    u, _, _ = S.run(mesh, prob.as_dict(), u0, 3)
+    for c in range(4):
+        assert np.abs(u[c] - u0[c]).max() <= 1e-13 * max(np.abs(u0[c]).max(), 1.0), c
+
+
+def test_free_stream_in_walled_channel():
+    mesh = Mesh(6, 3, 2, 0.0, 2.0, 0.0, 1.0, BC_OUTFLOW, BC_OUTFLOW)
+    shape = (mesh.nny, mesh.nnx)
+    u0 = inputs.euler_primitive_to_conserved(np.full(shape, 1.1), np.full(shape, 0.7), np.zeros(shape),
+                                             np.full(shape, 0.9))
+    state = tuple(float(u0[c, 0, 0]) for c in range(4))
+    b = {"W": boundary_side(BC_FIXED, state), "E": boundary_side(BC_OUTFLOW),
+         "S": boundary_side(BC_WALL), "N": boundary_side(BC_WALL)}
+    u, _, _ = S.run(mesh, _euler_problem(boundary=b).as_dict(), u0, 3)
+    for c in range(4):
+        assert np.abs(u[c] - u0[c]).max() <= 1e-13 * max(np.abs(u0[c]).max(), 1.0), c
+    # the same flow with the walls mirroring the tangential component instead
+    # would not be preserved: check that the wall state differs from that
+    ext = S.external_state("S", ((BC_WALL, BC_WALL), (None, None), math.inf, 0.0), np.array(False),
+                           u0[:, 0, 0])
+    assert ext[1] == u0[1, 0, 0] and ext[2] == -u0[2, 0, 0]
+
+
+def test_table_reproduces_axis_fixed_condition():
+    mesh, prob, u0 = inputs.kpp_config(8, 8, 2)
+    assert mesh.bc_x == BC_FIXED and mesh.bc_y == BC_FIXED
+    ub = prob.ubc
+    b = {s: boundary_side(BC_FIXED, ub) for s in "WESN"}
+    dt = S.time_step(mesh, prob.as_dict(), u0)
+    a, _ = S.fe_stage(mesh, prob.as_dict(), u0, dt)
+    prob.boundary = b
+    c, _ = S.fe_stage(mesh, prob.as_dict(), u0, dt)
+    assert np.array_equal(a, c)
+
+
+def test_moving_split_equals_static_split_at_stage_time():
+    mesh = Mesh(8, 4, 2, 0.0, 2.0, 0.0, 1.0, BC_OUTFLOW, BC_OUTFLOW)
+    post, pre = inputs.dmr_states()
+    u0 = _smooth_euler_state(mesh, 13)
+    s0, s1, t = 0.3, 2.0, 0.37
+
+    def prob_with(s0_, s1_):
+        b = {"W": boundary_side(BC_OUTFLOW), "E": boundary_side(BC_OUTFLOW),
+             "S": boundary_side(BC_WALL),
+             "N": boundary_side(BC_FIXED, post, BC_FIXED, pre, s0=s0_, s1=s1_)}
+        return _euler_problem(boundary=b).as_dict()
+
+    dt = 1e-4
+    a, _ = S.fe_stage(mesh, prob_with(s0, s1), u0, dt, t)
+    c, _ = S.fe_stage(mesh, prob_with(s0 + s1 * t, 0.0), u0, dt, 0.0)
+    assert np.array_equal(a, c)
+    # and the split matters: at t = 0 the post-shock part is shorter
+    d, _ = S.fe_stage(mesh, prob_with(s0, s1), u0, dt, 0.0)
+    assert not np.array_equal(a, d)
+
+
+def test_external_state_kinds():
+    spec = ((BC_FIXED, BC_WALL), (np.array([1.0, 2.0, 3.0, 9.0]), np.zeros(4)), 0.5, 0.0)
+    U = np.array([[1.5, 1.5], [0.2, 0.2], [0.3, 0.3], [4.0, 4.0]])
+    hi = S.side_hi(spec, np.array([0.25, 0.75]), 0.0)
+    ext = S.external_state("N", spec, hi, U)
+    assert np.array_equal(ext[:, 0], [1.0, 2.0, 3.0, 9.0])          # FIXED below the split
+    assert np.array_equal(ext[:, 1], [1.5, 0.2, -0.3, 4.0])         # WALL: m_y reversed on N
+    ext_w = S.external_state("W", ((BC_WALL, BC_WALL), (None, None), math.inf, 0.0), np.array([False, False]), U)
+    assert np.array_equal(ext_w[1], -U[1]) and np.array_equal(ext_w[2], U[2])
+    # a point exactly on the split belongs to the upper part (the paper's wall
+    # starts at x = 1/6 inclusive); the node at x = 64 (1/384) is exactly 1/6
+    assert S.side_hi(((0, 0), (None, None), 1.0 / 6.0, 0.0), 0.0 + 64 * (1.0 / 384.0), 0.0)
+
+
+def test_dmr_inflow_facets_carry_post_shock_flux():
+    mesh, prob, u0 = inputs.dmr_config(6, 2)
+    om = S.OracleMesh(mesh)
+    post, _ = inputs.dmr_states()
+    U = om.blocks(u0)
+    ue = S.cell_averages(om, U)
+    lo = S.low_order_facets(om, ue, prob.as_dict(), 0.0)
+    Fx = lo["x"][0].reshape(4, mesh.ny, om.nfx)
+    # W side: elements of column 0 whose cells lie entirely in the post-shock
+    # region (x < 1/6 + y/sqrt 3 at every node) see u_hat = u^e = post
+    fpost = ph.normal_flux(ph.EULER, np.array(post)[:, None], 1.0, 0.0, prob.as_dict())[:, 0]
+    X, Y = inputs.node_coords(mesh)
+    for ey in range(mesh.ny):
+        cell = (slice(ey * 2, ey * 2 + 3), slice(0, 3))
+        if np.all(X[cell] < 1.0 / 6.0 + Y[cell] / math.sqrt(3.0)):
+            assert np.allclose(Fx[:, ey, 0], fpost, rtol=1e-14, atol=1e-12)

@@ -6,7 +6,7 @@
   * identical states give lambda = |v.n| + c;
   * Appendix A limiter: ubar + alpha f / m keeps rho > 0 and p > 0 for
     random admissible ubar and arbitrary f;
-  * conservation on a periodic mesh and positivity (Sec. 5.3: rho > 0,
+  * conservation on a periodic mesh and positivity (Sec. 5.2: rho > 0,
     p > 0) of every Bernstein coefficient after WENO-L steps;
   * the blast wave stays positive (zero violations)."""
 import math
