@@ -497,7 +497,9 @@ def high_order_facets(om: OracleMesh, u, prob, t=0.0):
     (1/(p+1)) sum_{j on S} f(u_j).n (Bernstein face integrals equal
     |S|/(p+1)); on a boundary side that is not OUTFLOW everywhere the
     average LLF flux f^d_ee' with the nodal Riemann data (u_j, u_hat_j),
-    u_hat_j taken at the node's position x_j and time t."""
+    u_hat_j taken at time t and at the node's position on the element's face,
+    x_e + k h/p (unwrapped: on a periodic direction the last node of the last
+    element lies at x1, not at its periodic image x0)."""
     kind = prob["flux"]
     nc = u.shape[0]
     p, nx, ny = om.p, om.nx, om.ny
@@ -508,6 +510,8 @@ def high_order_facets(om: OracleMesh, u, prob, t=0.0):
     # x-facets [ey, i]: face nodes gx = i p, gy = ey p + b
     GX = (np.arange(om.nfx) * p) % om.nnx
     GY = np.arange(ny)[:, None] * p + b[None, :]
+    # positions along a side: the unwrapped node index of the face (x_e + k h/p)
+    posy = om.y0 + GY * hn
     if om.py:
         GY = GY % om.nny
     Uf = uu[:, GY[:, None, :], GX[None, :, None]]            # (nc, ny, nfx, p+1)
@@ -518,12 +522,13 @@ def high_order_facets(om: OracleMesh, u, prob, t=0.0):
             if side_is_plain(spec):
                 continue
             Ub = Uf[:, :, i, :]
-            ext = external_state(side, spec, side_hi(spec, om.y0 + GY * hn, t), Ub)
+            ext = external_state(side, spec, side_hi(spec, posy, t), Ub)
             Fj, _ = ph.llf(kind, Ub, ext, sgn, 0.0, prob)
             Fx[:, :, i] = sgn * Fj.mean(axis=-1)
     # y-facets [ex, j]: face nodes gy = j p, gx = ex p + b
     GY = (np.arange(om.nfy) * p) % om.nny
     GX = np.arange(nx)[:, None] * p + b[None, :]
+    posx = om.x0 + GX * hn
     if om.px:
         GX = GX % om.nnx
     Uf = uu[:, GY[None, :, None], GX[:, None, :]]            # (nc, nx, nfy, p+1)
@@ -534,7 +539,7 @@ def high_order_facets(om: OracleMesh, u, prob, t=0.0):
             if side_is_plain(spec):
                 continue
             Ub = Uf[:, :, j, :]
-            ext = external_state(side, spec, side_hi(spec, om.x0 + GX * hn, t), Ub)
+            ext = external_state(side, spec, side_hi(spec, posx, t), Ub)
             Fj, _ = ph.llf(kind, Ub, ext, 0.0, sgn, prob)
             Fy[:, :, j] = sgn * Fj.mean(axis=-1)
     return Fx.reshape(nc, -1), Fy.reshape(nc, -1)

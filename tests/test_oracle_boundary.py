@@ -182,3 +182,23 @@ def test_dmr_inflow_facets_carry_post_shock_flux():
         cell = (slice(ey * 2, ey * 2 + 3), slice(0, 3))
         if np.all(X[cell] < 1.0 / 6.0 + Y[cell] / math.sqrt(3.0)):
             assert np.allclose(Fx[:, ey, 0], fpost, rtol=1e-14, atol=1e-12)
+
+
+def test_periodic_seam_node_takes_its_face_position():
+    """Boundary data along a periodic direction are taken at the position on
+    the element's own face, x_e + k h/p: the last node of the last element
+    lies at x1 (not at its periodic image x0), so a side that is OUTFLOW below
+    s0 = 0.7 and WALL above gives that element's face a pure wall flux (no
+    mass or energy through it)."""
+    mesh = Mesh(9, 4, 2, 0.0, 2.25, 0.0, 1.0, BC_PERIODIC, BC_OUTFLOW)
+    b = {"W": boundary_side(BC_PERIODIC), "E": boundary_side(BC_PERIODIC), "S": boundary_side(BC_WALL),
+         "N": boundary_side(BC_OUTFLOW, kind_hi=BC_WALL, s0=0.7)}
+    u0 = _smooth_euler_state(mesh, 14)
+    om = S.OracleMesh(mesh)
+    _, FHy = S.high_order_facets(om, u0, _euler_problem(boundary=b).as_dict(), 0.0)
+    FHy = FHy.reshape(4, mesh.nx, om.nfy)
+    last = FHy[:, mesh.nx - 1, mesh.ny]
+    assert last[0] == 0.0 and last[3] == 0.0
+    # the first element's face lies below the split: an outflow flux
+    first = FHy[:, 0, mesh.ny]
+    assert abs(first[0]) > 1e-3
