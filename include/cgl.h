@@ -51,14 +51,16 @@ typedef int cgl_status;
 #define CGL_BC_PERIODIC 0
 #define CGL_BC_OUTFLOW 1    /* external state = internal state: F(u,u;n) = f(u).n */
 #define CGL_BC_FIXED 2      /* constant external state cgl_problem.ubc */
+#define CGL_BC_WALL 3       /* reflecting wall (Euler, cgl_set_boundary only):
+                               u_hat = (rho, m - 2 (m.n) n, E) */
 
 /* flux functions */
 #define CGL_FLUX_ADVECTION 0 /* f(u) = (vx, vy) u */
 #define CGL_FLUX_BURGERS 1   /* f(u) = (u^2/2, u^2/2) */
-#define CGL_FLUX_KPP 2       /* f(u) = (sin u, cos u), Sec. 5.4.2 */
-#define CGL_FLUX_EULER 3     /* compressible Euler, ideal gas, Sec. 5.3 */
+#define CGL_FLUX_KPP 2       /* f(u) = (sin u, cos u), Sec. 5.3.2 */
+#define CGL_FLUX_EULER 3     /* compressible Euler, ideal gas, Sec. 5.2 */
 
-/* method labels of Sec. 5.4: LO (gamma=beta=0), HO (gamma=beta=1),
+/* method labels of Sec. 5.3: LO (gamma=beta=0), HO (gamma=beta=1),
    WENO (sensor gamma, beta=1), WENO-L (sensor gamma, limited beta) */
 #define CGL_MODE_LO 0
 #define CGL_MODE_HO 1
@@ -92,8 +94,8 @@ typedef struct cgl_mesh_desc {
 } cgl_mesh_desc;
 
 /* Problem parameters. cgl_problem_defaults() fills the paper's defaults:
-   q = 1 (Sec. 5), r = 2 (Sec. 2.2), w_lin = 1e-3 (Sec. 5.5), gamma = 1.4
-   (Sec. 5.3), omega_CFL = 0.2, k_g = k_u = 1. */
+   q = 1 (Sec. 5), r = 2 (Sec. 2.2), w_lin = 1e-3 (Sec. 5.4), gamma = 1.4
+   (Sec. 5.2), omega_CFL = 0.2, k_g = k_u = 1. */
 /* cgl_problem.options.  CGL_OPT_FP64_LIMITER: in the FP32-mixed form, evaluate
  * every Appendix-A positivity factor (facet and nodal limiter) with the float64
  * formula.  By default a float32 evaluation with a rigorous error bound first
@@ -193,6 +195,35 @@ cgl_status cgl_state_create_external(const cgl_mesh *mesh, int32_t ncomp, int32_
 
 /* Set the problem (validated: flux/ncomp match, bounds, exponents, counts). */
 cgl_status cgl_set_problem(cgl_state *state, const cgl_problem *prob);
+
+/* Boundary data per side for cgl_set_boundary (Sec. 2 of the paper: the
+   boundary flux F(u_h, u_hat; n) with weakly imposed data u_hat; the
+   double Mach reflection of Sec. 5.4 combines a reflecting wall, a supersonic
+   outlet and time-dependent inflow).  Side k: 0 = W (x = x0), 1 = E (x = x1),
+   2 = S (y = y0), 3 = N (y = y1).  A boundary point whose coordinate along
+   its side (y on W and E, x on S and N) lies below s_k(t) = s0[k] + s1[k] t
+   takes kind_lo[k] / state_lo[k], every other point kind_hi[k] /
+   state_hi[k]; t is the time of the SSP-RK stage (t, t + dt, t + dt/2 in
+   cgl_step; the state's time in cgl_stage).  s0 = +inf gives one kind on the
+   whole side.  Kinds: CGL_BC_OUTFLOW (u_hat = u), CGL_BC_FIXED (u_hat =
+   state, ncomp values used), CGL_BC_WALL (u_hat = u with the normal momentum
+   reversed; Euler only).  The data are taken at the Gauss points of a face
+   in the residual, at the face nodes in the high-order facet fluxes and at
+   the face midpoint in the low-order facet fluxes.  Sides on a periodic
+   direction must carry CGL_BC_PERIODIC in both kinds. */
+typedef struct cgl_boundary {
+    int32_t kind_lo[4], kind_hi[4];
+    double s0[4], s1[4];
+    double state_lo[4][4], state_hi[4][4];
+} cgl_boundary;
+
+/* Replace the mesh's per-axis boundary conditions of the state with the
+   per-side table b (copied), or restore them with b = NULL.  A table needs
+   the problem set first.  CGL_EINVAL for an unknown kind, WALL with a scalar
+   flux, a FIXED state outside G (scalar) or with rho <= 0 or p <= 0 (Euler),
+   a NaN split or a non-finite s1.  A later cgl_set_problem checks the
+   table against the new problem.  States with a table cannot be batched. */
+cgl_status cgl_set_boundary(cgl_state *state, const cgl_boundary *b);
 
 /* Copy n = ncomp*nny*nnx float64 coefficients from the host into the state
    (rounded to float32 in FP32_MIXED). Synchronous. */

@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(HERE, "libcgl.so")
 
 OK = 0
 EINVAL, ECUDA, EOOM, EIDP, ENONFINITE, EDT, ETIMEOUT = -1, -2, -3, -4, -5, -6, -7
-BC_PERIODIC, BC_OUTFLOW, BC_FIXED = 0, 1, 2
+BC_PERIODIC, BC_OUTFLOW, BC_FIXED, BC_WALL = 0, 1, 2, 3
+SIDES = ("W", "E", "S", "N")
 FLUX_ADVECTION, FLUX_BURGERS, FLUX_KPP, FLUX_EULER = 0, 1, 2, 3
 MODE_LO, MODE_HO, MODE_WENO, MODE_WENO_L = 0, 1, 2, 3
 FL_NONE, FL_LIMITED, FL_LOW = 0, 1, 2
@@ -42,6 +43,11 @@ class cgl_problem(C.Structure):
                 ("q", C.c_double), ("r", C.c_double), ("weno_eps", C.c_double),
                 ("w_lin", C.c_double), ("gamma_eps", C.c_double), ("cfl", C.c_double),
                 ("lambda_floor", C.c_double), ("ubc", C.c_double * 4)]
+
+
+class cgl_boundary(C.Structure):
+    _fields_ = [("kind_lo", C.c_int32 * 4), ("kind_hi", C.c_int32 * 4), ("s0", C.c_double * 4),
+                ("s1", C.c_double * 4), ("state_lo", (C.c_double * 4) * 4), ("state_hi", (C.c_double * 4) * 4)]
 
 
 class cgl_step_info(C.Structure):
@@ -78,6 +84,7 @@ _PROTOS = [
     ("cgl_set_state_nodal", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("cgl_state_destroy", None, [C.c_void_p]),
     ("cgl_set_problem", C.c_int, [C.c_void_p, C.POINTER(cgl_problem)]),
+    ("cgl_set_boundary", C.c_int, [C.c_void_p, C.c_void_p]),
     ("cgl_set_state", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_size_t]),
     ("cgl_get_state", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_size_t]),
     ("cgl_set_base_state", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_size_t]),
@@ -149,6 +156,21 @@ def problem_struct(prob) -> cgl_problem:
     return p
 
 
+def boundary_struct(bnd) -> cgl_boundary:
+    """Fill a cgl_boundary from {side: {"kind": (lo, hi), "state": (lo, hi),
+    "s0": s0, "s1": s1}} for the sides W, E, S, N."""
+    b = cgl_boundary()
+    for k, side in enumerate(SIDES):
+        sd = bnd[side]
+        b.kind_lo[k], b.kind_hi[k] = int(sd["kind"][0]), int(sd["kind"][1])
+        b.s0[k], b.s1[k] = float(sd["s0"]), float(sd["s1"])
+        for slot, arr in ((0, b.state_lo), (1, b.state_hi)):
+            vals = [float(v) for v in list(sd["state"][slot])] + [0.0] * 4
+            for c in range(4):
+                arr[k][c] = vals[c]
+    return b
+
+
 class Mesh:
     def __init__(self, mesh):
         d = mesh if isinstance(mesh, dict) else mesh.as_dict()
@@ -206,8 +228,20 @@ class State:
         return (self.nc, self.mesh.nny, self.mesh.nnx)
 
     def set_problem(self, prob):
+        """Set the problem; a "boundary" entry (per-side table) is passed on
+        to cgl_set_boundary, its absence restores the mesh's conditions."""
         p = problem_struct(prob)
+        d = prob if isinstance(prob, dict) else prob.as_dict()
+        check(lib().cgl_set_boundary(self.h, None))
         check(lib().cgl_set_problem(self.h, C.byref(p)))
+        self.set_boundary(d.get("boundary"))
+
+    def set_boundary(self, bnd):
+        if bnd is None:
+            check(lib().cgl_set_boundary(self.h, None))
+        else:
+            b = boundary_struct(bnd)
+            check(lib().cgl_set_boundary(self.h, C.byref(b)))
 
     def set_state(self, u):
         a = np.ascontiguousarray(u, dtype=np.float64).reshape(self.shape)

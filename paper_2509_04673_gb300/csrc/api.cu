@@ -193,6 +193,7 @@ static void build_tables(HostTables& H) {
         for (int q = 0; q < nq; ++q) {
             double x = 0.5 * (xg[q] + 1.0);
             T.wq[q] = 0.5 * wg[q];
+            T.xq[q] = x;
             for (int a = 0; a < n; ++a) {
                 T.Bq[q][a] = bern_val(p, a, x);
                 T.dBq[q][a] = p * (bern_val(p - 1, a - 1, x) - bern_val(p - 1, a, x));
@@ -317,6 +318,9 @@ extern "C" cgl_status cgl_mesh_create(const cgl_mesh_desc* d, cgl_mesh** out) {
     m.inv_me_f = (float)m.inv_me;
     m.h2_f = (float)(m.h * m.h);
     m.h_over_n2_f = (float)m.h_over_n2;
+    m.x0 = d->x0;
+    m.y0 = d->y0;
+    m.hn = m.h / d->p;
     *out = M;
     return CGL_OK;
 }
@@ -533,6 +537,91 @@ static double round_inward_f32(double v, bool up) {
     return (double)f;
 }
 
+// boundary data of the four sides (Sec. 2: weakly imposed u_hat) ---------
+static void side_state_copy(SideDev& sd, int slot, const double* st) {
+    for (int c = 0; c < 4; ++c) {
+        sd.st[slot][c] = st[c];
+        sd.st_f[slot][c] = (float)st[c];
+        sd.st_lo_f[slot][c] = (float)(st[c] - (double)sd.st_f[slot][c]);
+    }
+}
+
+// the side table of the kernels: the custom boundary, or on every side the
+// bc of its axis with the state ubc
+static void fill_sides(cgl_state* S) {
+    ProbDev& d = S->pd;
+    const MeshDev& m = S->mesh->m;
+    for (int k = 0; k < 4; ++k) {
+        SideDev& sd = d.side[k];
+        if (S->has_bnd) {
+            sd.kind[0] = S->bnd.kind_lo[k];
+            sd.kind[1] = S->bnd.kind_hi[k];
+            sd.s0 = S->bnd.s0[k];
+            sd.s1 = S->bnd.s1[k];
+            side_state_copy(sd, 0, S->bnd.state_lo[k]);
+            side_state_copy(sd, 1, S->bnd.state_hi[k]);
+        } else {
+            const int bc = (k < 2) ? m.bc_x : m.bc_y;
+            sd.kind[0] = sd.kind[1] = bc;
+            sd.s0 = std::numeric_limits<double>::infinity();
+            sd.s1 = 0.0;
+            side_state_copy(sd, 0, S->prob.ubc);
+            side_state_copy(sd, 1, S->prob.ubc);
+        }
+    }
+    d.t_dev = S->B.t;
+    d.dt_dev = S->B.dt;
+    d.tc = 0.0;
+}
+
+static cgl_status check_boundary(const cgl_state* S, const cgl_problem* p, const cgl_boundary* b) {
+    const MeshDev& m = S->mesh->m;
+    const bool euler = p->flux == CGL_FLUX_EULER;
+    for (int k = 0; k < 4; ++k) {
+        if ((k < 2 && m.px) || (k >= 2 && m.py)) {
+            if (b->kind_lo[k] != CGL_BC_PERIODIC || b->kind_hi[k] != CGL_BC_PERIODIC)
+                return fail(CGL_EINVAL, "side %d lies on a periodic direction: kinds must be CGL_BC_PERIODIC", k);
+            continue;
+        }
+        if (!std::isfinite(b->s1[k]) || std::isnan(b->s0[k]))
+            return fail(CGL_EINVAL, "side %d: split s0 must not be NaN and s1 must be finite", k);
+        for (int slot = 0; slot < 2; ++slot) {
+            const int kind = slot ? b->kind_hi[k] : b->kind_lo[k];
+            const double* st = slot ? b->state_hi[k] : b->state_lo[k];
+            if (kind != CGL_BC_OUTFLOW && kind != CGL_BC_FIXED && kind != CGL_BC_WALL)
+                return fail(CGL_EINVAL, "side %d: kind %d is not OUTFLOW, FIXED or WALL", k, kind);
+            if (kind == CGL_BC_WALL && !euler) return fail(CGL_EINVAL, "side %d: WALL needs the Euler flux", k);
+            if (kind != CGL_BC_FIXED) continue;
+            if (euler) {
+                const double g = p->gamma_gas;
+                const double pr = (g - 1.0) * (st[3] - 0.5 * (st[1] * st[1] + st[2] * st[2]) / st[0]);
+                if (!(st[0] > 0.0) || !(pr > 0.0) || !std::isfinite(pr))
+                    return fail(CGL_EINVAL, "side %d: FIXED state needs rho > 0 and p > 0", k);
+            } else if (!(st[0] >= p->umin && st[0] <= p->umax)) {
+                return fail(CGL_EINVAL, "side %d: FIXED state outside [umin, umax]", k);
+            }
+        }
+    }
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_set_boundary(cgl_state* S, const cgl_boundary* b) {
+    if (!S) return fail(CGL_EINVAL, "null state");
+    if (b && !S->has_problem) return fail(CGL_EINVAL, "cgl_set_problem first");
+    if (b) {
+        cgl_status bs = check_boundary(S, &S->prob, b);
+        if (bs) return bs;
+        S->bnd = *b;
+    }
+    S->has_bnd = b != nullptr;
+    if (S->has_problem) fill_sides(S);
+    if (S->step_graph) {
+        cudaGraphExecDestroy(S->step_graph);
+        S->step_graph = nullptr;
+    }
+    return CGL_OK;
+}
+
 extern "C" cgl_status cgl_set_problem(cgl_state* S, const cgl_problem* p) {
     if (!S || !p) return fail(CGL_EINVAL, "null argument");
     if (p->flux < CGL_FLUX_ADVECTION || p->flux > CGL_FLUX_EULER) return fail(CGL_EINVAL, "unknown flux");
@@ -557,6 +646,10 @@ extern "C" cgl_status cgl_set_problem(cgl_state* S, const cgl_problem* p) {
     if ((m.bc_x == CGL_BC_FIXED || m.bc_y == CGL_BC_FIXED) && need_nc == 1 &&
         (p->ubc[0] < p->umin || p->ubc[0] > p->umax))
         return fail(CGL_EINVAL, "fixed boundary state outside [umin, umax]");
+    if (S->has_bnd) {
+        cgl_status bs = check_boundary(S, p, &S->bnd);
+        if (bs) return bs;
+    }
     StageFn fn = nullptr;
     switch (p->flux) {
         case CGL_FLUX_ADVECTION: fn = stage_fn_adv(S->prec, m.p); break;
@@ -612,6 +705,7 @@ extern "C" cgl_status cgl_set_problem(cgl_state* S, const cgl_problem* p) {
     d.lambda_floor_f = (float)d.lambda_floor;
     S->stage = fn;
     S->has_problem = true;
+    fill_sides(S);
     if (S->step_graph) {
         cudaGraphExecDestroy(S->step_graph);
         S->step_graph = nullptr;
@@ -823,11 +917,15 @@ static cudaError_t enqueue_step(cgl_state* S, Prof* prof = nullptr) {
     const MeshDev& m = S->mesh->m;
     const Bufs& B = S->B;
     // the first stage (a = 0) stores u^n into B.un as it overwrites u
+    // stage times t, t + dt, t + dt/2 (read only by moving boundary splits)
+    ProbDev p2 = S->pd, p3 = S->pd;
+    p2.tc = 1.0;
+    p3.tc = 0.5;
     cudaError_t e = S->stage(B, m, S->pd, 0.0, 1.0, true, false, S->st, prof);
     if (e != cudaSuccess) return e;
-    e = S->stage(B, m, S->pd, 0.75, 0.25, false, false, S->st, prof);
+    e = S->stage(B, m, p2, 0.75, 0.25, false, false, S->st, prof);
     if (e != cudaSuccess) return e;
-    e = S->stage(B, m, S->pd, 1.0 / 3.0, 2.0 / 3.0, false, false, S->st, prof);
+    e = S->stage(B, m, p3, 1.0 / 3.0, 2.0 / 3.0, false, false, S->st, prof);
     if (e != cudaSuccess) return e;
     CGL_LAUNCH(prof, KID_TADV, S->st, (e = launch(prof == nullptr, k_t_advance, dim3(1), dim3(1), S->st, B.t,
                                                    (const double*)B.dt)));

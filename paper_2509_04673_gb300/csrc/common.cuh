@@ -17,7 +17,7 @@ constexpr int PMAX = 4;        // highest supported degree
 constexpr int N1MAX = PMAX + 1;
 constexpr int NQMAX = PMAX + 2;
 
-enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_FIXED = 2 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_FIXED = 2, BC_WALL = 3 };
 enum { MODE_LO = 0, MODE_HO = 1, MODE_WENO = 2, MODE_WENO_L = 3 };
 enum { FL_NONE = 0, FL_LIMITED = 1, FL_LOW = 2 };
 
@@ -37,6 +37,20 @@ struct MeshDev {
     float h_f, me_f, inv_me_f, h2_f, h_over_n2_f;
     float me_rz_f;         // m_i^e rounded toward zero (admissible bound gaps)
     float inv_h_f;
+    double x0, y0, hn;     // domain corner; node spacing h/p (node gx sits at x0 + gx*hn)
+};
+
+// Boundary data of one side of the domain (W, E, S, N), Sec. 2: weakly
+// imposed data u_hat in F(u_h, u_hat; n).  A boundary point whose coordinate
+// along the side (y on W and E, x on S and N) lies below s0 + s1 t at the
+// stage time t takes slot 0, any other point slot 1.  Kinds: OUTFLOW
+// (u_hat = u), FIXED (u_hat = st), WALL (u_hat = u with the normal momentum
+// reversed).
+struct SideDev {
+    int kind[2];
+    double s0, s1;
+    double st[2][4];
+    float st_f[2][4], st_lo_f[2][4];  // float-float copies of st
 };
 
 struct ProbDev {
@@ -54,6 +68,10 @@ struct ProbDev {
     int opts;              // CGL_OPT_* bits
     float ome_f;           // 1 - pos_eps rounded to float
     float lambda_floor_f;
+    SideDev side[4];       // W, E, S, N
+    const double* t_dev;   // device time t of the step and its dt: the stage
+    const double* dt_dev;  // time is t + tc dt (read only by moving splits)
+    double tc;
 };
 
 enum { OPT_FP64_LIMITER = 1, OPT_UNFUSED_SWEEPS = 2 };
@@ -70,6 +88,7 @@ template <> struct PV<double> {
     static DEV double gamma_eps(const ProbDev& p) { return p.gamma_eps; }
     static DEV double q(const ProbDev& p) { return p.q; }
     static DEV double ubc(const ProbDev& p, int c) { return p.ubc[c]; }
+    static DEV double side_state(const SideDev& s, int slot, int c) { return s.st[slot][c]; }
     static DEV double lo(const ProbDev& p) { return p.umin; }
     static DEV double hi(const ProbDev& p) { return p.umax; }
     static DEV double lo_tol(const ProbDev& p) { return p.lo_tol; }
@@ -88,6 +107,7 @@ template <> struct PV<float> {
     static DEV float gamma_eps(const ProbDev& p) { return p.gamma_eps_f; }
     static DEV float q(const ProbDev& p) { return p.q_f; }
     static DEV float ubc(const ProbDev& p, int c) { return p.ubc_f[c]; }
+    static DEV float side_state(const SideDev& s, int slot, int c) { return s.st_f[slot][c]; }
     static DEV float lo(const ProbDev& p) { return p.lo32_f; }
     static DEV float hi(const ProbDev& p) { return p.hi32_f; }
     static DEV float lo_tol(const ProbDev& p) { return p.lo_tol_f; }
@@ -110,6 +130,7 @@ struct Tab {
     T Bq[NQMAX][N1MAX];    // B_a(x_q)
     T dBq[NQMAX][N1MAX];   // B_a'(x_q)
     T wq[NQMAX];           // Gauss weights on [0,1]
+    T xq[NQMAX];           // Gauss points on [0,1]
 };
 
 // semi-norm matrices (n2 x n2 for p = 1..4) packed at offsets

@@ -108,6 +108,63 @@ DEV void neighbour_xy(const MeshDev& m, int ex, int ey, int dir, int& jx, int& j
     jy = jy < 0 ? jy + m.ny : (jy >= m.ny ? jy - m.ny : jy);
 }
 
+// ---------------------------------------------------------------------------
+// boundary data u_hat on the sides d = 0..3 (W, E, S, N), Sec. 2.  The
+// positions and the split are evaluated in float64 with explicit rounding
+// (no contraction), so that a point that lies exactly on a split (a node at
+// x = 1/6 on a mesh of width 1/192) takes the same side as the plain
+// evaluation s0 + s1 (t + c dt) and x0 + k hn.
+// ---------------------------------------------------------------------------
+DEV bool side_plain(const ProbDev& pr, int d) {
+    return pr.side[d].kind[0] == BC_OUTFLOW && pr.side[d].kind[1] == BC_OUTFLOW;
+}
+
+// slot (0 below the split, 1 at or above it) of a point at coordinate pos
+DEV int side_slot(const ProbDev& pr, int d, double pos) {
+    const SideDev& sd = pr.side[d];
+    double sp = sd.s0;
+    if (sd.s1 != 0.0) {
+        double ts = *pr.t_dev;
+        if (pr.tc != 0.0) ts = __dadd_rn(ts, __dmul_rn(pr.tc, *pr.dt_dev));
+        sp = __dadd_rn(sd.s0, __dmul_rn(sd.s1, ts));
+    }
+    return pos < sp ? 0 : 1;
+}
+
+// coordinate along side d of node k (0..p) of the face of element (ex, ey)
+DEV double side_node_pos(const MeshDev& m, int d, int ex, int ey, int k) {
+    const int g = ((d < 2) ? ey : ex) * m.p + k;
+    return __dadd_rn((d < 2) ? m.y0 : m.x0, __dmul_rn((double)g, m.hn));
+}
+
+// coordinate along side d of the midpoint of the face of element (ex, ey)
+DEV double side_mid_pos(const MeshDev& m, int d, int ex, int ey) {
+    const int c = (d < 2) ? ey : ex;
+    return __dadd_rn((d < 2) ? m.y0 : m.x0, __dmul_rn((double)c + 0.5, m.h));
+}
+
+// coordinate along side d of the Gauss point x_q (on [0,1]) of that face
+DEV double side_quad_pos(const MeshDev& m, int d, int ex, int ey, double xq) {
+    const int c = (d < 2) ? ey : ex;
+    return __dadd_rn(__dadd_rn((d < 2) ? m.y0 : m.x0, __dmul_rn((double)c, m.h)), __dmul_rn(xq, m.h));
+}
+
+// u_hat from the interior state u: FIXED -> the side's state, OUTFLOW -> u,
+// WALL -> u with the normal momentum reversed, m - 2 (m.n) n (Euler; the
+// normals of the sides are +-x and +-y)
+template <class T, int NC>
+DEV void ext_state(const ProbDev& pr, int d, int slot, const T* u, T* uh) {
+    const int kind = pr.side[d].kind[slot];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) uh[c] = (kind == BC_FIXED) ? PV<T>::side_state(pr.side[d], slot, c) : u[c];
+    if constexpr (NC == 4) {
+        if (kind == BC_WALL) {
+            if (d < 2) uh[1] = -u[1];
+            else uh[2] = -u[2];
+        }
+    }
+}
+
 // 2D launches: elements as (x: ex, y: ey), nodes as (x: gx, y: gy); no
 // integer division by runtime sizes in the kernels
 DEV bool elem_of_thread(const MeshDev& m, int& ex, int& ey, int& e) {
@@ -220,7 +277,7 @@ DEV double facet_speed(const double* uL, const double* uR, double nx, double ny,
 }
 
 template <class Ph, class R>
-DEV void lo_facets(const MeshDev& m, const ProbDev& pr, const int (&nb)[4],
+DEV void lo_facets(const MeshDev& m, const ProbDev& pr, const int (&nb)[4], int ex, int ey,
                    const double (&us)[Ph::NC], const double (&fxs)[Ph::NC], const double (&fys)[Ph::NC],
                    const double (&uo)[4][Ph::NC], const double (&fxo)[4][Ph::NC],
                    const double (&fyo)[4][Ph::NC], double (&lam)[4], double (&FL)[4][Ph::NC]) {
@@ -245,14 +302,15 @@ DEV void lo_facets(const MeshDev& m, const ProbDev& pr, const int (&nb)[4],
                 FL[d][c] = 0.5 * (nL + nR) - 0.5 * l * (uR[c] - uL[c]);
             }
         } else {
-            const int bc = (d < 2) ? m.bc_x : m.bc_y;
+            // external state u_hat at the facet midpoint from the cell average
+            const int slot = side_slot(pr, d, side_mid_pos(m, d, ex, ey));
+            const int kind = pr.side[d].kind[slot];
             double ux[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) ux[c] = (bc == BC_FIXED) ? pr.ubc[c] : us[c];
+            ext_state<double, NC>(pr, d, slot, us, ux);
             const double sg = self_is_L ? 1.0 : -1.0;
-            // external state: f(u_hat) (FIXED) or the cell's own f(u^e) (OUTFLOW)
+            // f(u_hat) (FIXED, WALL) or the cell's own f(u^e) (OUTFLOW)
             double fxx[NC], fyx[NC];
-            if (bc == BC_FIXED) {
+            if (kind != BC_OUTFLOW) {
                 R ubR[NC], fxR[NC], fyR[NC];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) ubR[c] = R(ux[c]);
@@ -585,22 +643,34 @@ struct CompVec {
 
 // low-order quantities of a boundary facet of the FP32-mixed k_pre: the
 // speed bound (inflated like the interior ones) and F(u^e, u_hat; n) in the
-// canonical orientation for FIXED (u_hat = u_bc) or OUTFLOW (u_hat = u^e);
-// uh, ul: the element's float-float mean, fn: its flux along the facet axis;
-// returns [F_0 .. F_{NC-1}, lambda]
+// canonical orientation, u_hat of side d at the facet midpoint in float-float
+// (FIXED: the side's state; OUTFLOW: u^e; WALL: u^e with reversed normal
+// momentum); uh, ul: the element's float-float mean, fn: its flux along the
+// facet axis; returns [F_0 .. F_{NC-1}, lambda]
 template <class Ph>
-__device__ __noinline__ CompVec<float, Ph::NC + 1> boundary_facet_lo(const ProbDev& pr, bool fixed, bool xf,
-                                                                    float sg, CompVec<float, Ph::NC> uh,
+__device__ __noinline__ CompVec<float, Ph::NC + 1> boundary_facet_lo(const MeshDev& m, const ProbDev& pr, int d,
+                                                                    int ex, int ey, float sg,
+                                                                    CompVec<float, Ph::NC> uh,
                                                                     CompVec<float, Ph::NC> ul,
                                                                     CompVec<float, Ph::NC> fn) {
     constexpr int NC = Ph::NC;
+    const bool xf = d < 2;
     const float inflate = 1.0f + 0x1p-20f;
     const float cnx = xf ? 1.f : 0.f, cny = xf ? 0.f : 1.f;
+    const int slot = side_slot(pr, d, side_mid_pos(m, d, ex, ey));
+    const int kind = pr.side[d].kind[slot];
     float xh[NC], xl[NC], xfx[NC], xfy[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        xh[c] = fixed ? pr.ubc_f[c] : uh.v[c];
-        xl[c] = fixed ? pr.ubc_lo_f[c] : ul.v[c];
+        xh[c] = (kind == BC_FIXED) ? pr.side[d].st_f[slot][c] : uh.v[c];
+        xl[c] = (kind == BC_FIXED) ? pr.side[d].st_lo_f[slot][c] : ul.v[c];
+    }
+    if constexpr (NC == 4) {
+        if (kind == BC_WALL) {
+            const int cn = xf ? 1 : 2;
+            xh[cn] = -xh[cn];
+            xl[cn] = -xl[cn];
+        }
     }
     Ph::template flux<float>(xh, xfx, xfy, pr);
     const float l = __fmul_rn(Ph::template max_speed<float>(uh.v, xh, sg * cnx, sg * cny, pr), inflate);
@@ -698,7 +768,6 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
                 F[d][c] = llf_value(fL[c], fR[c], l, ff_diff(Rh[c], Rl[c], Lh[c], Ll[c]));
         } else {
             // boundary facet: out of line (rare; keeps the hot code small)
-            const int bc = xf ? m.bc_x : m.bc_y;
             CompVec<float, NC> vh, vl, vf;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
@@ -707,7 +776,7 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
                 vf.v[c] = xf ? fxs[c] : fys[c];
             }
             const CompVec<float, NC + 1> o =
-                boundary_facet_lo<Ph>(pr, bc == BC_FIXED, xf, self_is_L ? 1.f : -1.f, vh, vl, vf);
+                boundary_facet_lo<Ph>(m, pr, d, ex, ey, self_is_L ? 1.f : -1.f, vh, vl, vf);
             lam[d] = o.v[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) F[d][c] = o.v[c];
@@ -827,7 +896,7 @@ DEV double pre_at(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __rest
             }
         }
         double lam[4], FL[4][NC];
-        lo_facets<Ph, R>(m, pr, nb, us, fxs, fys, uo, fxo, fyo, lam, FL);
+        lo_facets<Ph, R>(m, pr, nb, ex, ey, us, fxs, fys, uo, fxo, fyo, lam, FL);
         double s = ((lam[0] + lam[1]) + lam[2]) + lam[3];
         s = fmax(s, pr.lambda_floor);
         // dt_e = |K| / (|S| sum lambda) = h / s; dt_e / h = 1 / s
@@ -1465,17 +1534,20 @@ DEV NodeCands node_cands(const MeshDev& m, int gx, int gy) {
 // (p+2)-point Gauss rule for nonlinear integrands; exact face mass for f_h.
 // ER layout ev_at(E, e, i, c, NC).
 // ---------------------------------------------------------------------------
-// boundary-face part of the weak form of element e on face d: the
-// (p+2)-point quadrature of phi_i F(u_h, u_hat; n) (FIXED) or phi_i f(u_h).n
-// (OUTFLOW), scaled by h; Uf and term are [NC][p+1]
+// boundary-face part of the weak form of element (ex, ey) on face d: the
+// (p+2)-point quadrature of phi_i F(u_h, u_hat; n), u_hat of the side at
+// each Gauss point, or of phi_i f(u_h).n on a side that is OUTFLOW
+// everywhere; scaled by h; Uf and term are [NC][p+1]
 template <class R, int P, class Ph>
-__device__ __noinline__ void boundary_face_term(const MeshDev& m, const ProbDev& pr, int d, const R* Uf, R* term) {
+__device__ __noinline__ void boundary_face_term(const MeshDev& m, const ProbDev& pr, int d, int ex, int ey,
+                                                const R* Uf, R* term) {
     constexpr int NC = Ph::NC, N1 = P + 1, NQ = Dim<P>::NQ;
     const Tab<R>& T = TabSel<R>::t(P);
+    const Tab<double>& Td = TabSel<double>::t(P);
     const R h = PV<R>::h(m);
     const R nxo = (d == 0) ? R(-1) : (d == 1) ? R(1) : R(0);
     const R nyo = (d == 2) ? R(-1) : (d == 3) ? R(1) : R(0);
-    const int bc = (d < 2) ? m.bc_x : m.bc_y;
+    const bool plain = side_plain(pr, d);
     R acc[NC][N1];
 #pragma unroll
     for (int c = 0; c < NC; ++c)
@@ -1491,10 +1563,10 @@ __device__ __noinline__ void boundary_face_term(const MeshDev& m, const ProbDev&
             for (int k = 0; k < N1; ++k) s += Uf[c * N1 + k] * T.Bq[r][k];
             uq[c] = s;
         }
-        if (bc == BC_FIXED) {
+        if (!plain) {
+            const int slot = side_slot(pr, d, side_quad_pos(m, d, ex, ey, Td.xq[r]));
             R ub[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) ub[c] = PV<R>::ubc(pr, c);
+            ext_state<R, NC>(pr, d, slot, uq, ub);
             llf<Ph, R>(uq, ub, nxo, nyo, pr, F, (R*)nullptr);
         } else {
             R fx[NC], fy[NC];
@@ -1612,7 +1684,7 @@ DEV void w_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Dim<P>
         } else {
             // a face on the domain boundary: out of line, so the common
             // interior path stays compact in the instruction cache
-            boundary_face_term<R, P, Ph>(m, pr, d, &Uf[0][0], &term[0][0]);
+            boundary_face_term<R, P, Ph>(m, pr, d, ex, ey, &Uf[0][0], &term[0][0]);
         }
 #pragma unroll
         for (int k = 0; k < N1; ++k) {
@@ -1721,23 +1793,25 @@ DEV void split(double v, T& hi, T& lo) {
     lo = T(v - (double)hi);
 }
 
-// sum over the face nodes of F(u_j, u_hat; n) on a FIXED boundary face
-// (f^H of eq. (hoflux) before the division by p+1); Uf is [NC][p+1]
+// sum over the face nodes of F(u_j, u_hat_j; n) on a boundary face of side
+// d that is not OUTFLOW everywhere (f^H of eq. (hoflux) before the division
+// by p+1), u_hat_j of the side at node j; Uf is [NC][p+1]
 template <class R, int P, class Ph>
-__device__ __noinline__ CompVec<R, Ph::NC> fixed_face_llf_sum(const ProbDev& pr, R nx, R ny, const R* Uf) {
+__device__ __noinline__ CompVec<R, Ph::NC> bnd_face_llf_sum(const MeshDev& m, const ProbDev& pr, int d, int e,
+                                                           R nx, R ny, const R* Uf) {
     constexpr int NC = Ph::NC, N1 = P + 1;
+    const int ey = e / m.nx, ex = e - ey * m.nx;
     CompVec<R, NC> out;
     R* acc = out.v;
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = R(0);
-    R ub[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) ub[c] = PV<R>::ubc(pr, c);
 #pragma unroll
     for (int k = 0; k < N1; ++k) {
-        R uk[NC], F[NC];
+        R uk[NC], ub[NC], F[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) uk[c] = Uf[c * N1 + k];
+        const int slot = side_slot(pr, d, side_node_pos(m, d, ex, ey, k));
+        ext_state<R, NC>(pr, d, slot, uk, ub);
         llf<Ph, R>(uk, ub, nx, ny, pr, F, (R*)nullptr);
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] += F[c];
@@ -1766,14 +1840,13 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
             const R cnx = (d < 2) ? R(1) : R(0), cny = (d < 2) ? R(0) : R(1);
-            const int bc = (d < 2) ? m.bc_x : m.bc_y;
-            const bool fixed_b = (nb[d] < 0) && (bc == BC_FIXED);
+            const bool fixed_b = (nb[d] < 0) && !side_plain(pr, d);
             const R sg = (d == 1 || d == 3) ? R(1) : R(-1);
             R acc[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] = R(0);
             if (fixed_b) {
-                // FIXED boundary face: out of line (rare; keeps the hot code small)
+                // boundary face with u_hat data: out of line (rare; keeps the hot code small)
                 R Uf[NC * N1];
 #pragma unroll
                 for (int k = 0; k < N1; ++k) {
@@ -1781,7 +1854,7 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
 #pragma unroll
                     for (int c = 0; c < NC; ++c) Uf[c * N1 + k] = U[c][li];
                 }
-                const CompVec<R, NC> fs = fixed_face_llf_sum<R, P, Ph>(pr, sg * cnx, sg * cny, Uf);
+                const CompVec<R, NC> fs = bnd_face_llf_sum<R, P, Ph>(m, pr, d, e, sg * cnx, sg * cny, Uf);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) acc[c] = fs.v[c];  // acc was 0: same sums
             } else {

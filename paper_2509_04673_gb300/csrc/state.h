@@ -21,6 +21,8 @@ struct cgl_state {
     bool own_stream;
     bool has_problem;
     cgl_problem prob;
+    bool has_bnd;          // a cgl_set_boundary table is in force
+    cgl_boundary bnd;
     cgl::ProbDev pd;
     cgl::StageFn stage;
     cgl::Bufs B;

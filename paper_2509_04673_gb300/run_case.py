@@ -21,7 +21,9 @@ sys.path.insert(0, ROOT)
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="kpp",
-                    choices=["kpp", "advection", "euler_quadrants", "euler_blast", "batched"])
+                    choices=["kpp", "advection", "euler_quadrants", "euler_blast", "dmr", "batched"])
+    ap.add_argument("--t-end", type=float, default=0.0,
+                    help="run to this time instead of a step count (reports the steps taken)")
     ap.add_argument("--autotune", action="store_true", help="batched: tune tile lengths first")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--p", type=int, default=0, help="degree (0 = the workload's own)")
@@ -43,6 +45,9 @@ def main():
         mesh, prob, u0 = inputs.advection_config(a.n, a.n, a.p or 2)
     elif a.workload == "euler_quadrants":
         mesh, prob, u0 = inputs.euler_quadrant_config(a.n, a.n, a.p or 3)
+    elif a.workload == "dmr":
+        # --n is the number of elements across the height (4n x n elements)
+        mesh, prob, u0 = inputs.dmr_config(a.n, a.p or 2)
     else:
         mesh, prob, u0 = inputs.euler_blast_config(a.n, a.n, a.p or 2)
     stream = torch.cuda.Stream()
@@ -55,11 +60,15 @@ def main():
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    st.step_async(a.steps)
+    if a.t_end > 0:
+        taken = st.step(1 << 30, t_end=a.t_end, raise_on_idp=False)["steps"]
+    else:
+        st.step_async(a.steps)
+        taken = a.steps
     ev1.record(stream)
     torch.cuda.synchronize()
     info = st.step(0, raise_on_idp=False)
-    info["steps"] = a.steps
+    info["steps"] = taken
     info["violations"] = st.counters()["violations"]
     ndof = u0.size
     info.update(workload=a.workload, n=a.n, p=mesh.p, prec=a.prec, n_dof=ndof,
