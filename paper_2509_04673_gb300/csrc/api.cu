@@ -547,10 +547,12 @@ static void side_state_copy(SideDev& sd, int slot, const double* st) {
 }
 
 // the side table of the kernels: the custom boundary, or on every side the
-// bc of its axis with the state ubc
-static void fill_sides(cgl_state* S) {
+// bc of its axis with the state ubc; the masks mark the sides that are
+// OUTFLOW everywhere and those with two parts
+static cgl_status fill_sides(cgl_state* S) {
     ProbDev& d = S->pd;
     const MeshDev& m = S->mesh->m;
+    d.plain_mask = d.split_mask = 0;
     for (int k = 0; k < 4; ++k) {
         SideDev& sd = d.side[k];
         if (S->has_bnd) {
@@ -569,9 +571,16 @@ static void fill_sides(cgl_state* S) {
             side_state_copy(sd, 1, S->prob.ubc);
         }
     }
+    for (int k = 0; k < 4; ++k) {
+        const SideDev& sd = d.side[k];
+        if (sd.kind[0] == CGL_BC_OUTFLOW && sd.kind[1] == CGL_BC_OUTFLOW) d.plain_mask |= 1 << k;
+        // one part (slot 0) only if the split never moves and lies at +inf
+        if (sd.s1 != 0.0 || !(sd.s0 == std::numeric_limits<double>::infinity())) d.split_mask |= 1 << k;
+    }
     d.t_dev = S->B.t;
     d.dt_dev = S->B.dt;
     d.tc = 0.0;
+    return CGL_OK;
 }
 
 static cgl_status check_boundary(const cgl_state* S, const cgl_problem* p, const cgl_boundary* b) {
@@ -614,7 +623,10 @@ extern "C" cgl_status cgl_set_boundary(cgl_state* S, const cgl_boundary* b) {
         S->bnd = *b;
     }
     S->has_bnd = b != nullptr;
-    if (S->has_problem) fill_sides(S);
+    if (S->has_problem) {
+        cgl_status fs = fill_sides(S);
+        if (fs) return fs;
+    }
     if (S->step_graph) {
         cudaGraphExecDestroy(S->step_graph);
         S->step_graph = nullptr;
@@ -705,7 +717,8 @@ extern "C" cgl_status cgl_set_problem(cgl_state* S, const cgl_problem* p) {
     d.lambda_floor_f = (float)d.lambda_floor;
     S->stage = fn;
     S->has_problem = true;
-    fill_sides(S);
+    cgl_status fs = fill_sides(S);
+    if (fs) return fs;
     if (S->step_graph) {
         cudaGraphExecDestroy(S->step_graph);
         S->step_graph = nullptr;

@@ -69,6 +69,8 @@ struct ProbDev {
     float ome_f;           // 1 - pos_eps rounded to float
     float lambda_floor_f;
     SideDev side[4];       // W, E, S, N
+    int plain_mask;        // bit d: side d is OUTFLOW everywhere
+    int split_mask;        // bit d: side d has two parts (its split lies inside or moves)
     const double* t_dev;   // device time t of the step and its dt: the stage
     const double* dt_dev;  // time is t + tc dt (read only by moving splits)
     double tc;
@@ -314,6 +316,22 @@ DEV void llf(const T* uL, const T* uR, T nx, T ny, const ProbDev& pr, T* F, T* l
         F[c] = T(0.5) * (nL + nR) - T(0.5) * lam * (uR[c] - uL[c]);
     }
     if (lam_out) *lam_out = lam;
+}
+
+// the same LLF flux with f(uR) given (a constant external state: its flux is
+// evaluated once per face; the result is identical to llf)
+template <class Ph, class T>
+DEV void llf_given_fR(const T* uL, const T* uR, const T* fxR, const T* fyR, T nx, T ny, const ProbDev& pr,
+                      T* F) {
+    T fxL[Ph::NC], fyL[Ph::NC];
+    Ph::flux(uL, fxL, fyL, pr);
+    T lam = Ph::max_speed(uL, uR, nx, ny, pr);
+#pragma unroll
+    for (int c = 0; c < Ph::NC; ++c) {
+        T nL = fxL[c] * nx + fyL[c] * ny;
+        T nR = fxR[c] * nx + fyR[c] * ny;
+        F[c] = T(0.5) * (nL + nR) - T(0.5) * lam * (uR[c] - uL[c]);
+    }
 }
 
 // Appendix A bound for the correction factor of one state ubar modified by

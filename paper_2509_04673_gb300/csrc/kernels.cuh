@@ -115,11 +115,11 @@ DEV void neighbour_xy(const MeshDev& m, int ex, int ey, int dir, int& jx, int& j
 // x = 1/6 on a mesh of width 1/192) takes the same side as the plain
 // evaluation s0 + s1 (t + c dt) and x0 + k hn.
 // ---------------------------------------------------------------------------
-DEV bool side_plain(const ProbDev& pr, int d) {
-    return pr.side[d].kind[0] == BC_OUTFLOW && pr.side[d].kind[1] == BC_OUTFLOW;
-}
+DEV bool side_plain(const ProbDev& pr, int d) { return (pr.plain_mask >> d) & 1; }
+DEV bool side_split(const ProbDev& pr, int d) { return (pr.split_mask >> d) & 1; }
 
 // slot (0 below the split, 1 at or above it) of a point at coordinate pos
+// of a side with two parts
 DEV int side_slot(const ProbDev& pr, int d, double pos) {
     const SideDev& sd = pr.side[d];
     double sp = sd.s0;
@@ -154,9 +154,10 @@ DEV double side_quad_pos(const MeshDev& m, int d, int ex, int ey, double xq) {
 // normals of the sides are +-x and +-y)
 template <class T, int NC>
 DEV void ext_state(const ProbDev& pr, int d, int slot, const T* u, T* uh) {
-    const int kind = pr.side[d].kind[slot];
+    const SideDev& sd = pr.side[d];
+    const int kind = sd.kind[slot];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) uh[c] = (kind == BC_FIXED) ? PV<T>::side_state(pr.side[d], slot, c) : u[c];
+    for (int c = 0; c < NC; ++c) uh[c] = (kind == BC_FIXED) ? PV<T>::side_state(sd, slot, c) : u[c];
     if constexpr (NC == 4) {
         if (kind == BC_WALL) {
             if (d < 2) uh[1] = -u[1];
@@ -303,7 +304,7 @@ DEV void lo_facets(const MeshDev& m, const ProbDev& pr, const int (&nb)[4], int 
             }
         } else {
             // external state u_hat at the facet midpoint from the cell average
-            const int slot = side_slot(pr, d, side_mid_pos(m, d, ex, ey));
+            const int slot = side_split(pr, d) ? side_slot(pr, d, side_mid_pos(m, d, ex, ey)) : 0;
             const int kind = pr.side[d].kind[slot];
             double ux[NC];
             ext_state<double, NC>(pr, d, slot, us, ux);
@@ -657,13 +658,14 @@ __device__ __noinline__ CompVec<float, Ph::NC + 1> boundary_facet_lo(const MeshD
     const bool xf = d < 2;
     const float inflate = 1.0f + 0x1p-20f;
     const float cnx = xf ? 1.f : 0.f, cny = xf ? 0.f : 1.f;
-    const int slot = side_slot(pr, d, side_mid_pos(m, d, ex, ey));
-    const int kind = pr.side[d].kind[slot];
+    const int slot = side_split(pr, d) ? side_slot(pr, d, side_mid_pos(m, d, ex, ey)) : 0;
+    const SideDev& sd = pr.side[d];
+    const int kind = sd.kind[slot];
     float xh[NC], xl[NC], xfx[NC], xfy[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        xh[c] = (kind == BC_FIXED) ? pr.side[d].st_f[slot][c] : uh.v[c];
-        xl[c] = (kind == BC_FIXED) ? pr.side[d].st_lo_f[slot][c] : ul.v[c];
+        xh[c] = (kind == BC_FIXED) ? sd.st_f[slot][c] : uh.v[c];
+        xl[c] = (kind == BC_FIXED) ? sd.st_lo_f[slot][c] : ul.v[c];
     }
     if constexpr (NC == 4) {
         if (kind == BC_WALL) {
@@ -850,7 +852,7 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
 }
 
 template <class R, int P, class Ph>
-DEV double pre_at(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __restrict__ ue_out,
+DEV double pre_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u, double* __restrict__ ue_out,
                   double* __restrict__ dte_out, double* __restrict__ ubl_out,
                   double* __restrict__ gam_out, double* __restrict__ nu_out,
                   R* __restrict__ q_out, R* __restrict__ fl_out, R* __restrict__ EV,
@@ -1548,6 +1550,14 @@ __device__ __noinline__ void boundary_face_term(const MeshDev& m, const ProbDev&
     const R nxo = (d == 0) ? R(-1) : (d == 1) ? R(1) : R(0);
     const R nyo = (d == 2) ? R(-1) : (d == 3) ? R(1) : R(0);
     const bool plain = side_plain(pr, d);
+    // a FIXED side with one part: one external state, its flux evaluated once
+    const bool fixed1 = !plain && !side_split(pr, d) && pr.side[d].kind[0] == BC_FIXED;
+    R ub1[NC], fxb[NC], fyb[NC];
+    if (fixed1) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ub1[c] = PV<R>::side_state(pr.side[d], 0, c);
+        Ph::template flux<R>(ub1, fxb, fyb, pr);
+    }
     R acc[NC][N1];
 #pragma unroll
     for (int c = 0; c < NC; ++c)
@@ -1563,8 +1573,10 @@ __device__ __noinline__ void boundary_face_term(const MeshDev& m, const ProbDev&
             for (int k = 0; k < N1; ++k) s += Uf[c * N1 + k] * T.Bq[r][k];
             uq[c] = s;
         }
-        if (!plain) {
-            const int slot = side_slot(pr, d, side_quad_pos(m, d, ex, ey, Td.xq[r]));
+        if (fixed1) {
+            llf_given_fR<Ph, R>(uq, ub1, fxb, fyb, nxo, nyo, pr, F);
+        } else if (!plain) {
+            const int slot = side_split(pr, d) ? side_slot(pr, d, side_quad_pos(m, d, ex, ey, Td.xq[r])) : 0;
             R ub[NC];
             ext_state<R, NC>(pr, d, slot, uq, ub);
             llf<Ph, R>(uq, ub, nxo, nyo, pr, F, (R*)nullptr);
@@ -1755,7 +1767,7 @@ DEV void stab_part(const MeshDev& m, const R (&U)[Ph::NC][Dim<P>::N2], const R* 
 // Euler at p = 2: 3 blocks of 128 per SM (170-register cap; measured faster)
 
 template <class R, int P, class Ph>
-DEV void res_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ g,
+DEV void res_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u, const R* __restrict__ g,
                          const double* __restrict__ gam, const double* __restrict__ nu,
                          R* __restrict__ ER, int ex, int ey, int e) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
@@ -1800,17 +1812,36 @@ template <class R, int P, class Ph>
 __device__ __noinline__ CompVec<R, Ph::NC> bnd_face_llf_sum(const MeshDev& m, const ProbDev& pr, int d, int e,
                                                            R nx, R ny, const R* Uf) {
     constexpr int NC = Ph::NC, N1 = P + 1;
-    const int ey = e / m.nx, ex = e - ey * m.nx;
+    const bool split = side_split(pr, d);
+    int ex = 0, ey = 0;
+    if (split) {
+        ey = e / m.nx;
+        ex = e - ey * m.nx;
+    }
     CompVec<R, NC> out;
     R* acc = out.v;
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = R(0);
+    // a FIXED side with one part: one external state, its flux evaluated once
+    const bool fixed1 = !split && pr.side[d].kind[0] == BC_FIXED;
+    R ub1[NC], fxb[NC], fyb[NC];
+    if (fixed1) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ub1[c] = PV<R>::side_state(pr.side[d], 0, c);
+        Ph::template flux<R>(ub1, fxb, fyb, pr);
+    }
 #pragma unroll
     for (int k = 0; k < N1; ++k) {
         R uk[NC], ub[NC], F[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) uk[c] = Uf[c * N1 + k];
-        const int slot = side_slot(pr, d, side_node_pos(m, d, ex, ey, k));
+        if (fixed1) {
+            llf_given_fR<Ph, R>(uk, ub1, fxb, fyb, nx, ny, pr, F);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c] += F[c];
+            continue;
+        }
+        const int slot = split ? side_slot(pr, d, side_node_pos(m, d, ex, ey, k)) : 0;
         ext_state<R, NC>(pr, d, slot, uk, ub);
         llf<Ph, R>(uk, ub, nx, ny, pr, F, (R*)nullptr);
 #pragma unroll
@@ -2131,7 +2162,7 @@ DEV void element_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][
 }
 
 template <class R, int P, class Ph>
-DEV void update_at(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
+DEV void update_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u, const R* __restrict__ ud,
                             const double* __restrict__ ue, const double* __restrict__ dte_a, const double* __restrict__ ubl,
                             const R* __restrict__ qcap, const R* __restrict__ fl_in,
                             const R* __restrict__ ER, const float* __restrict__ cf,
@@ -2293,7 +2324,7 @@ __global__ void __launch_bounds__(128) k_res_s(MeshDev m, const float* __restric
 // to the storage precision) or the positivity count (Euler), non-finite count.
 // ---------------------------------------------------------------------------
 template <class R, int P, int NC>
-DEV void final_at(MeshDev m, ProbDev pr, const R* __restrict__ EW,
+DEV void final_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ EW,
                         R* __restrict__ un, R* __restrict__ u, R a, R b,
                         unsigned long long* __restrict__ cnt, int gx, int gy, long long node) {
     const NodeC<P> nc = node_c<P>(m, gx, gy);
