@@ -242,14 +242,14 @@ def load_peaks():
 # profiles/kpp256_q2_dram_per_launch.md (kernels unchanged since; the two
 # Richardson sweeps averaged like their algorithmic bytes)
 NCU_TRAFFIC = {
-    ("k_pre", "kpp_256x256_q2"): 1122816,
-    ("k_facet", "kpp_256x256_q2"): 3746304,
+    ("k_pre", "kpp_256x256_q2"): 1123840,
+    ("k_facet", "kpp_256x256_q2"): 3719680,
     ("k_grad_rhs", "kpp_256x256_q2"): 1064704,
-    ("k_mass_sweep", "kpp_256x256_q2"): (4223744 + 2115328) // 2,
-    ("k_res_ev", "kpp_256x256_q2"): 4304896,
-    ("k_gather_init", "kpp_256x256_q2"): 2364160,
+    ("k_mass_sweep", "kpp_256x256_q2"): (4223488 + 2115328) // 2,
+    ("k_res_ev", "kpp_256x256_q2"): 4270080,
+    ("k_gather_init", "kpp_256x256_q2"): 2364928,
     ("k_update_ev", "kpp_256x256_q2"): 6056960,
-    ("k_final", "kpp_256x256_q2"): 4471808,
+    ("k_final", "kpp_256x256_q2"): 3418624,
 }
 
 
