@@ -120,6 +120,7 @@ class Problem:
     k_g: int = 1
     k_u: int = 1
     lambda_floor: float = 1e-12
+    options: int = 0                  # bits as in cgl_problem.options
     ubc: tuple = (0.0, 0.0, 0.0, 0.0)
     # optional per-side boundary table {side: boundary_side(...)} for the
     # sides W, E, S, N; None: the mesh's bc_x / bc_y with the state ubc

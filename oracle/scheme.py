@@ -41,6 +41,7 @@ from . import physics as ph
 from .tables import tables
 
 BC_PERIODIC, BC_OUTFLOW, BC_FIXED, BC_WALL = 0, 1, 2, 3
+OPT_SUBCELL_DT = 4
 SIDES = ("W", "E", "S", "N")
 # SSP-RK3 stage times t + c dt of the Shu-Osher stages
 SSP3_C = (0.0, 1.0, 0.5)
@@ -352,6 +353,54 @@ def pseudo_time_steps(om: OracleMesh, lo, prob):
     return om.h * om.h / (om.h * s)
 
 
+def subcell_time_steps(om: OracleMesh, U, prob):
+    """dt_e^max of Lemma 1, eq. (dtmaxsubcell), the pseudo time step of the
+    unlimited-flux variant (Sec. 4.3, step 4: flux limiter deactivated):
+
+      dt_e = (1/s) min{ min_{i in N_e^b} m_i^e / (|c_ie| lambda_0i),
+                        m_0^e / sum_{i in N_e^b} |c_ie| lambda_0i }
+
+    N_e^b: the nodes on the element boundary; u_0^e: the mass-weighted mean
+    of the interior nodes, m_0^e their mass; c_ie = int_{dK_e} phi_i n ds
+    (|S|/(p+1) times the outward normal of each face through node i, so a
+    corner node gets the diagonal); lambda_0i: the speed bound of the
+    Riemann problem (u_0^e, u_i) along c_ie/|c_ie|; s = 1.  Without interior
+    nodes (Q1): u_0^e = u^e, m_0^e = |K_e| and s = 2 (the lemma's second
+    case).  Readings: a node term with zero speed is dropped, and the sum is
+    floored at lambda_floor |S| (as eq. (dtmaxcell) floors its speed sum)."""
+    kind = prob["flux"]
+    p, n, h = om.p, om.n1, om.h
+    nc = U.shape[0]
+    me = om.me
+    a_idx = np.arange(n * n) % n
+    b_idx = np.arange(n * n) // n
+    cx = np.where(a_idx == 0, -1.0, np.where(a_idx == p, 1.0, 0.0))
+    cy = np.where(b_idx == 0, -1.0, np.where(b_idx == p, 1.0, 0.0))
+    bnd = (cx != 0.0) | (cy != 0.0)
+    if p >= 2:
+        inner = ~bnd
+        u0 = U[:, :, inner].mean(axis=2)                  # equal masses m_i^e
+        m0 = inner.sum() * me
+        s_fac = 1.0
+    else:
+        u0 = U.mean(axis=2)
+        m0 = h * h
+        s_fac = 2.0
+    norm = np.sqrt(cx * cx + cy * cy)
+    best = np.full(om.E, np.inf)
+    total = np.zeros(om.E)
+    for i in np.nonzero(bnd)[0]:
+        c_abs = (h / (p + 1)) * norm[i]
+        nx_, ny_ = cx[i] / norm[i], cy[i] / norm[i]
+        lam = ph.max_speed(kind, u0, U[:, :, i], nx_, ny_, prob)
+        w = c_abs * lam
+        total = total + w
+        with np.errstate(divide="ignore"):
+            best = np.minimum(best, np.where(w > 0.0, me / np.where(w > 0.0, w, 1.0), np.inf))
+    total = np.maximum(total, prob["lambda_floor"] * h)
+    return np.minimum(best, m0 / total) / s_fac
+
+
 def outward_sum(om: OracleMesh, Fx, Fy):
     """sum_{e'} of the outward canonical facet values of each element."""
     return Fx[:, om.fE] - Fx[:, om.fW] + Fy[:, om.fN] - Fy[:, om.fS]
@@ -649,6 +698,8 @@ def fe_stage(mesh, prob, u, dt, t=0.0):
     ue = cell_averages(om, U)
     lo = low_order_facets(om, ue, prob, t)
     dte = pseudo_time_steps(om, lo, prob)
+    if int(prob.get("options", 0)) & OPT_SUBCELL_DT:
+        dte = subcell_time_steps(om, U, prob)
     FLx, FLy = lo["x"][0], lo["y"][0]
     ubL = ue - (dte / om.h) * outward_sum(om, FLx, FLy)          # eq. (uelowFCT)
     info = dict(ue=ue, dte=dte, ubL=ubL)
@@ -748,6 +799,8 @@ def time_step(mesh, prob, u, t=0.0):
     om = mesh if isinstance(mesh, OracleMesh) else OracleMesh(mesh)
     U = om.blocks(u)
     ue = cell_averages(om, U)
+    if int(prob.get("options", 0)) & OPT_SUBCELL_DT:
+        return prob["cfl"] * subcell_time_steps(om, U, prob).min()
     lo = low_order_facets(om, ue, prob, t)
     return prob["cfl"] * pseudo_time_steps(om, lo, prob).min()
 
