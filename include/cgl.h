@@ -109,6 +109,16 @@ typedef struct cgl_mesh_desc {
  * fused there (one kernel each); the results are identical, the option exists
  * to check that. */
 #define CGL_OPT_UNFUSED_SWEEPS 2
+/* cgl_problem.options.  CGL_OPT_SUBCELL_DT: the unlimited-flux variant of the
+ * paper's Sec. 4.3 (step 4 with the flux limiter deactivated): the pseudo time
+ * steps dt_e are the subcell bound dt_e^max of Lemma 1, eq. (dtmaxsubcell),
+ * instead of the macrocell bound of eq. (dtmaxcell); the global dt is
+ * omega_CFL min_e dt_e as before.  Requires flux_limiter = CGL_FL_NONE
+ * (CGL_EINVAL otherwise).  u_0^e is the mean of the interior coefficients
+ * (Q1: the cell average, with s = 2), c_ie = |S|/(p+1) times the summed
+ * outward normals of the faces through boundary node i, a zero-speed node
+ * term is dropped and the speed sum is floored at lambda_floor |S|. */
+#define CGL_OPT_SUBCELL_DT 4
 
 typedef struct cgl_problem {
     int32_t flux;          /* CGL_FLUX_* */

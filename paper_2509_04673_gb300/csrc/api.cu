@@ -642,7 +642,10 @@ extern "C" cgl_status cgl_set_problem(cgl_state* S, const cgl_problem* p) {
     if (p->mode < CGL_MODE_LO || p->mode > CGL_MODE_WENO_L) return fail(CGL_EINVAL, "unknown mode");
     if (p->flux_limiter < CGL_FL_NONE || p->flux_limiter > CGL_FL_LOW) return fail(CGL_EINVAL, "unknown flux_limiter");
     if (p->k_g < 0 || p->k_u < 0 || p->k_g > 64 || p->k_u > 64) return fail(CGL_EINVAL, "k_g, k_u in [0, 64]");
-    if (p->options & ~(CGL_OPT_FP64_LIMITER | CGL_OPT_UNFUSED_SWEEPS)) return fail(CGL_EINVAL, "unknown option bits");
+    if (p->options & ~(CGL_OPT_FP64_LIMITER | CGL_OPT_UNFUSED_SWEEPS | CGL_OPT_SUBCELL_DT))
+        return fail(CGL_EINVAL, "unknown option bits");
+    if ((p->options & CGL_OPT_SUBCELL_DT) && p->flux_limiter != CGL_FL_NONE)
+        return fail(CGL_EINVAL, "CGL_OPT_SUBCELL_DT needs flux_limiter = CGL_FL_NONE");
     if (!(p->cfl > 0.0) || !(p->cfl <= 1.0)) return fail(CGL_EINVAL, "cfl must be in (0, 1]");
     if (!(p->q >= 1.0) || !(p->r >= 1.0)) return fail(CGL_EINVAL, "q, r must be >= 1");
     if (!(p->weno_eps > 0.0) || !(p->gamma_eps >= 0.0) || !(p->lambda_floor > 0.0))

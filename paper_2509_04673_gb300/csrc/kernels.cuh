@@ -642,6 +642,65 @@ struct CompVec {
     R v[NC];
 };
 
+// pseudo time step dt_e^max of Lemma 1, eq. (dtmaxsubcell), for the
+// unlimited-flux variant (option OPT_SUBCELL_DT with the flux limiter off):
+//   dt_e = (1/s) min{ min_{i on dK_e} m_i^e / (|c_ie| lambda_0i),
+//                     m_0^e / sum_{i on dK_e} |c_ie| lambda_0i }
+// with u_0^e the mean of the interior coefficients (m_0^e their mass),
+// c_ie = int_{dK_e} phi_i n ds = |S|/(p+1) times the sum of the outward
+// normals of the faces through node i, lambda_0i the speed bound of
+// (u_0^e, u_i) along c_ie/|c_ie|, s = 1; for Q1 (no interior node) u_0^e =
+// u^e, m_0^e = |K_e| and s = 2.  A node term with zero speed is dropped and
+// the sum is floored at lambda_floor |S|.  Float64 from the element's
+// coefficients; out of line (not on the default path).
+template <class R, int P, class Ph>
+__device__ __noinline__ double subcell_dt(const R* __restrict__ u, const MeshDev& m, const ProbDev& pr, int ex,
+                                          int ey) {
+    constexpr int NC = Ph::NC, N1 = P + 1, N2 = N1 * N1;
+    R Ub[NC][N2];
+    load_block<R, P, NC>(u, m, ex, ey, Ub);
+    double u0[NC];
+    double m0, sfac;
+    if constexpr (P >= 2) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            double acc = 0.0;
+            for (int b = 1; b < P; ++b)
+                for (int a = 1; a < P; ++a) acc += (double)Ub[c][b * N1 + a];
+            u0[c] = acc / (double)((P - 1) * (P - 1));
+        }
+        m0 = (double)((P - 1) * (P - 1)) * m.me;
+        sfac = 1.0;
+    } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            double acc = 0.0;
+            for (int i = 0; i < N2; ++i) acc += (double)Ub[c][i];
+            u0[c] = acc / (double)N2;
+        }
+        m0 = m.h * m.h;
+        sfac = 2.0;
+    }
+    const double cface = m.h / (double)N1;
+    double best = __longlong_as_double(0x7ff0000000000000LL), total = 0.0;
+    for (int b = 0; b < N1; ++b)
+        for (int a = 0; a < N1; ++a) {
+            const double cx = (a == 0) ? -1.0 : (a == P) ? 1.0 : 0.0;
+            const double cy = (b == 0) ? -1.0 : (b == P) ? 1.0 : 0.0;
+            if (cx == 0.0 && cy == 0.0) continue;
+            const double nrm = sqrt(cx * cx + cy * cy);
+            double ui[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ui[c] = (double)Ub[c][b * N1 + a];
+            const double lam = Ph::template max_speed<double>(u0, ui, cx / nrm, cy / nrm, pr);
+            const double w = (cface * nrm) * lam;
+            total += w;
+            if (w > 0.0) best = fmin(best, m.me / w);
+        }
+    total = fmax(total, pr.lambda_floor * m.h);
+    return fmin(best, m0 / total) / sfac;
+}
+
 // low-order quantities of a boundary facet of the FP32-mixed k_pre: the
 // speed bound (inflated like the interior ones) and F(u^e, u_hat; n) in the
 // canonical orientation, u_hat of side d at the facet midpoint in float-float
@@ -688,7 +747,9 @@ __device__ __noinline__ CompVec<float, Ph::NC + 1> boundary_facet_lo(const MeshD
     return out;
 }
 
-template <int P, class Ph>
+// SUB: pseudo time steps from the subcell bound of Lemma 1 (a separate
+// instantiation, so that the default kernels carry none of its code)
+template <int P, class Ph, bool SUB = false>
 DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __restrict__ u,
                         double* __restrict__ ue_out, double* __restrict__ dte_out,
                         double* __restrict__ ubl_out, double* __restrict__ gam_out,
@@ -789,9 +850,18 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
     // dt_e / h = 1 / s: float reciprocal refined by one float64 Newton step
     // (relative error ~2^-46, far inside the 2^-20 inflation of the speeds;
     // GB300's float64 divide is a long sequence on its narrow float64 pipe)
-    const double s = (double)sf;
-    const double r0 = (double)__frcp_rn(sf);
-    const double rs = fma(r0, fma(-s, r0, 1.0), r0);
+    double s, rs;
+    if constexpr (SUB) {
+        // Lemma 1 bound; the float speed sum is rounded up (a float dt_e no
+        // larger than the bound)
+        rs = subcell_dt<float, P, Ph>(u, m, pr, ex, ey) * m.inv_h;
+        s = 1.0 / rs;
+        sf = __double2float_ru(s);
+    } else {
+        s = (double)sf;
+        const double r0 = (double)__frcp_rn(sf);
+        rs = fma(r0, fma(-s, r0, 1.0), r0);
+    }
     const double dte = m.h * rs;
     dte_out[e] = dte;
     dte_out[m.E + e] = rs;
@@ -851,15 +921,15 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
     return dte;
 }
 
-template <class R, int P, class Ph>
+template <class R, int P, class Ph, bool SUB = false>
 DEV double pre_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u, double* __restrict__ ue_out,
                   double* __restrict__ dte_out, double* __restrict__ ubl_out,
                   double* __restrict__ gam_out, double* __restrict__ nu_out,
                   R* __restrict__ q_out, R* __restrict__ fl_out, R* __restrict__ EV,
                   float* __restrict__ cf_out, float* __restrict__ avg, int ex, int ey, int e) {
     if constexpr (sizeof(R) == 4) {
-        return pre_at_mixed<P, Ph>(m, pr, u, ue_out, dte_out, ubl_out, gam_out, nu_out, q_out, fl_out, EV,
-                                   cf_out, avg, ex, ey, e);
+        return pre_at_mixed<P, Ph, SUB>(m, pr, u, ue_out, dte_out, ubl_out, gam_out, nu_out, q_out, fl_out, EV,
+                                        cf_out, avg, ex, ey, e);
     } else {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
     double dte;
@@ -902,7 +972,12 @@ DEV double pre_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u, 
         double s = ((lam[0] + lam[1]) + lam[2]) + lam[3];
         s = fmax(s, pr.lambda_floor);
         // dt_e = |K| / (|S| sum lambda) = h / s; dt_e / h = 1 / s
-        const double rs = 1.0 / s;
+        double rs = 1.0 / s;
+        if constexpr (SUB) {
+            // Lemma 1 bound instead (the unlimited-flux variant)
+            rs = subcell_dt<R, P, Ph>(u, m, pr, ex, ey) * m.inv_h;
+            s = 1.0 / rs;
+        }
         dte = m.h * rs;
         dte_out[e] = dte;
         dte_out[m.E + e] = rs;              // dt_e / h
@@ -966,7 +1041,7 @@ __global__ void k_avg(MeshDev m, const float* __restrict__ u, float* __restrict_
     }
 }
 
-template <class R, int P, class Ph>
+template <class R, int P, class Ph, bool SUB = false>
 __global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __restrict__ ue_out,
                       double* __restrict__ dte_out, double* __restrict__ ubl_out,
                       double* __restrict__ gam_out, double* __restrict__ nu_out,
@@ -977,8 +1052,8 @@ __global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __
     int ex, ey, e;
     double dte = __longlong_as_double(0x7ff0000000000000LL);
     if (elem_of_thread(m, ex, ey, e))
-        dte = pre_at<R, P, Ph>(m, pr, u, ue_out, dte_out, ubl_out, gam_out, nu_out, q_out, fl_out, EV, cf_out,
-                               avg, ex, ey, e);
+        dte = pre_at<R, P, Ph, SUB>(m, pr, u, ue_out, dte_out, ubl_out, gam_out, nu_out, q_out, fl_out, EV, cf_out,
+                                    avg, ex, ey, e);
     if (dtbits) block_min_to(dte, dtbits);
 }
 

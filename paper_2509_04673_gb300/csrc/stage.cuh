@@ -130,8 +130,9 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
     constexpr bool use_avg = sizeof(R) == 4 && NC > 1;
     if constexpr (use_avg)
         CGL_LAUNCH(prof, KID_AVG, st, chk(launch(pdl, k_avg<P, NC>, ge, be, st, m, (const float*)u, B.avg)));
+    auto* kpre = (pr.opts & OPT_SUBCELL_DT) ? k_pre<R, P, Ph, true> : k_pre<R, P, Ph, false>;
     CGL_LAUNCH(prof, KID_PRE, st,
-               chk(launch(pdl, k_pre<R, P, Ph>, ge, be, st, m, pr, (const R*)u, B.ue, B.dte, B.ubl, B.gam, B.nu,
+               chk(launch(pdl, kpre, ge, be, st, m, pr, (const R*)u, B.ue, B.dte, B.ubl, B.gam, B.nu,
                           (R*)B.q, (R*)B.fl, (R*)nullptr, B.cf, B.avg,
                           first ? B.dtbits : nullptr)));
     if (first)
