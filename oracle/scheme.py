@@ -42,6 +42,7 @@ from .tables import tables
 
 BC_PERIODIC, BC_OUTFLOW, BC_FIXED, BC_WALL = 0, 1, 2, 3
 OPT_SUBCELL_DT = 4
+OPT_AEC_Q1 = 8
 SIDES = ("W", "E", "S", "N")
 # SSP-RK3 stage times t + c dt of the Shu-Osher stages
 SSP3_C = (0.0, 1.0, 0.5)
@@ -724,6 +725,11 @@ def fe_stage(mesh, prob, u, dt, t=0.0):
         beta = np.zeros(om.E)
         fie = np.zeros_like(U)
         gamma = np.zeros(om.E)
+    elif int(prob.get("options", 0)) & OPT_AEC_Q1:
+        gamma = sensor(om, U, prob) if mode in (MODE_WENO, MODE_WENO_L) else np.ones(om.E)
+        fie, udl = aec_q1(om, U, ue, ube, dte, gamma, prob)
+        beta = slope_limit(om, fie, ube, prob) if mode == MODE_WENO_L else np.ones(om.E)
+        info.update(gamma=gamma, udot_l=udl, fie=fie)
     else:
         gamma = sensor(om, U, prob) if mode in (MODE_WENO, MODE_WENO_L) else np.ones(om.E)
         lam_e = element_speed(om, U, prob)
@@ -755,6 +761,41 @@ def fe_stage(mesh, prob, u, dt, t=0.0):
     w = me * ((1.0 - theta)[None, :, None] * U + theta[None, :, None] * ubi)
     unew = om.gather(w) / om.mi
     return unew.reshape(u.shape), info
+
+
+def low_order_time_derivative(om: OracleMesh, U, ube, dte):
+    """udot^L_i of the low-order scheme, eq. (weak:low2):
+    m_i udot^L_i = sum_{e in E_i} m_i^e (ubar^e - u_i) / dt_e, with the
+    stage's intermediate averages ubar^e (reading for the 'low-order
+    approximation to the time derivative' of eq. (aecQ1))."""
+    w = om.me * (ube[:, :, None] - U) / dte[None, :, None]
+    return om.gather(w) / om.mi
+
+
+def flux_divergence_term(om: OracleMesh, U, prob):
+    """D_i = int_{K_e} (phi_i - m_i^e/|K_e|) div f_h dx of eq. (aecQ1), with
+    f_h = sum_j f(u_j) phi_j (eq. (gfe)): sum_j (B_ij - (m_i^e/|K_e|) c_j) . f(u_j),
+    B_ij = int phi_i grad phi_j, c_j = int grad phi_j = sum_i B_ij."""
+    fx, fy = ph.flux(prob["flux"], U, prob)             # (nc, E, n2) nodal fluxes
+    cx = om.Bx2.sum(axis=0)
+    cy = om.By2.sum(axis=0)
+    return fx @ om.Bx2.T + fy @ om.By2.T - (om.me / (om.h * om.h)) * (fx @ cx + fy @ cy)[:, :, None]
+
+
+def aec_q1(om: OracleMesh, U, ue, ube, dte, gamma, prob):
+    """Element contributions of eq. (aecQ1), the Q1 variant of Sec. 5.3:
+      f_i^e = gamma_e ( m_i^e (u_i - u^e) - dt_e [ int (phi_i - m_i^e/|K_e|) div f_h
+                                                  + int phi_i (udot^L_h - udot^L_i) ] )
+    with f_h = sum_j f(u_j) phi_j (eq. (gfe)), so that
+    int phi_i div f_h = sum_j int phi_i grad phi_j . f(u_j) and
+    int div f_h = sum_j c_j . f(u_j), c_j = int grad phi_j; the last term is
+    (M udot^L)_i - m_i^e udot^L_i with the consistent element mass matrix M.
+    Written for any p; the paper applies it to Q1."""
+    D = flux_divergence_term(om, U, prob)
+    udl = low_order_time_derivative(om, U, ube, dte)
+    UDL = om.blocks(udl.reshape((U.shape[0], om.nny, om.nnx)))
+    inner = D + UDL @ om.Mass2.T - om.me * UDL
+    return gamma[None, :, None] * (om.me * (U - ue[:, :, None]) - dte[None, :, None] * inner), udl
 
 
 def bound_check(prob, u, clamp=True):
