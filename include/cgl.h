@@ -119,6 +119,16 @@ typedef struct cgl_mesh_desc {
  * outward normals of the faces through boundary node i, a zero-speed node
  * term is dropped and the speed sum is floored at lambda_floor |S|. */
 #define CGL_OPT_SUBCELL_DT 4
+/* cgl_problem.options.  CGL_OPT_AEC_Q1: the element contributions of eq. (aecQ1)
+ * (the paper's Sec. 5.3 variant, stated there for Q1, computed here for every p):
+ *   f_i^e = gamma_e ( m_i^e (u_i - u^e) - dt_e [ int (phi_i - m_i^e/|K_e|) div f_h
+ *                                                + int phi_i (udot^L_h - udot^L_i) ] )
+ * with f_h = sum_j f(u_j) phi_j and the low-order time derivative
+ * m_i udot^L_i = sum_e m_i^e (ubar^e - u_i)/dt_e of eq. (weak:low2) taken from
+ * the stage's intermediate averages ubar^e.  The g_h projection, the target
+ * residual and the udot solve are skipped.  The KPP entropy correction of that
+ * section is not included. */
+#define CGL_OPT_AEC_Q1 8
 
 typedef struct cgl_problem {
     int32_t flux;          /* CGL_FLUX_* */
@@ -293,7 +303,7 @@ cgl_status cgl_time_step(cgl_state *state, double *dt);
 #define CGL_FIELD_GX 16     /* g_h x-components (ncomp) */
 #define CGL_FIELD_GY 17     /* g_h y-components (ncomp) */
 #define CGL_FIELD_R 18      /* target residual r (ncomp) */
-#define CGL_FIELD_UDOT 19   /* udot (ncomp) */
+#define CGL_FIELD_UDOT 19   /* udot (ncomp); udot^L of eq. (weak:low2) with CGL_OPT_AEC_Q1 */
 cgl_status cgl_get_field(cgl_state *state, int32_t field, double *host, size_t n);
 
 /* --- batches ------------------------------------------------------------------ */

@@ -26,6 +26,7 @@ FP64, FP32_MIXED = 0, 1
 OPT_FP64_LIMITER = 1
 OPT_UNFUSED_SWEEPS = 2
 OPT_SUBCELL_DT = 4
+OPT_AEC_Q1 = 8
 FIELD_UE, FIELD_DTE, FIELD_UBL, FIELD_UBE, FIELD_GAMMA, FIELD_NU, FIELD_BETA = 0, 1, 2, 3, 4, 5, 6
 FIELD_GX, FIELD_GY, FIELD_R, FIELD_UDOT = 16, 17, 18, 19
 

@@ -642,7 +642,7 @@ extern "C" cgl_status cgl_set_problem(cgl_state* S, const cgl_problem* p) {
     if (p->mode < CGL_MODE_LO || p->mode > CGL_MODE_WENO_L) return fail(CGL_EINVAL, "unknown mode");
     if (p->flux_limiter < CGL_FL_NONE || p->flux_limiter > CGL_FL_LOW) return fail(CGL_EINVAL, "unknown flux_limiter");
     if (p->k_g < 0 || p->k_u < 0 || p->k_g > 64 || p->k_u > 64) return fail(CGL_EINVAL, "k_g, k_u in [0, 64]");
-    if (p->options & ~(CGL_OPT_FP64_LIMITER | CGL_OPT_UNFUSED_SWEEPS | CGL_OPT_SUBCELL_DT))
+    if (p->options & ~(CGL_OPT_FP64_LIMITER | CGL_OPT_UNFUSED_SWEEPS | CGL_OPT_SUBCELL_DT | CGL_OPT_AEC_Q1))
         return fail(CGL_EINVAL, "unknown option bits");
     if ((p->options & CGL_OPT_SUBCELL_DT) && p->flux_limiter != CGL_FL_NONE)
         return fail(CGL_EINVAL, "CGL_OPT_SUBCELL_DT needs flux_limiter = CGL_FL_NONE");
@@ -817,7 +817,10 @@ extern "C" cgl_status cgl_get_field(cgl_state* S, int32_t field, double* host, s
     size_t cnt = 0;
     bool bulk = false;
     const void* gfin = (S->prob.k_g % 2 == 0) ? S->B.g : S->B.g2;
-    const void* udfin = (S->prob.k_u % 2 == 0) ? S->B.ud : S->B.ud2;
+    // the udot solve ends in ud or ud2 by the parity of k_u; the Q1 variant
+    // stores udot^L in ud
+    const bool q1 = (S->prob.options & CGL_OPT_AEC_Q1) && S->prob.mode != CGL_MODE_LO;
+    const void* udfin = (q1 || S->prob.k_u % 2 == 0) ? S->B.ud : S->B.ud2;
     switch (field) {
         case CGL_FIELD_UE: src = S->B.ue; cnt = nc * E; break;
         case CGL_FIELD_DTE: src = S->B.dte; cnt = E; break;
@@ -1027,7 +1030,7 @@ extern "C" cgl_status cgl_time_step(cgl_state* S, double* dt) {
 // ---------------------------------------------------------------------------
 static const char* const KNAMES[KID_COUNT] = {
     "k_avg", "k_pre", "k_dt", "k_grad_rhs", "k_gather_init", "k_grad_sweep", "k_mass_sweep",
-    "k_res_ev", "k_update_ev", "k_final", "k_t_advance", "k_udot_sweep", "k_facet", "k_res_w"};
+    "k_res_ev", "k_update_ev", "k_final", "k_t_advance", "k_udot_sweep", "k_facet", "k_res_w", "k_q1_facet", "k_udl"};
 
 // fixed-length delay (bounded both by a cycle count and by an iteration cap;
 // it waits on nothing) that keeps the stream busy while the host enqueues the
@@ -1101,6 +1104,10 @@ extern "C" cgl_status cgl_launches_per_step(cgl_state* S, int64_t* kernels) {
     if (S->prec == CGL_FP32_MIXED && !lo && fuse_sweeps(S->mesh->m) && !(S->prob.options & CGL_OPT_UNFUSED_SWEEPS)) {
         // the first sweep of each solve runs inside k_grad_sweep / k_udot_sweep
         per_stage -= (S->prob.k_g >= 1) + (S->prob.k_u >= 1);
+    }
+    if ((S->prob.options & CGL_OPT_AEC_Q1) && !lo) {
+        // k_pre, k_q1_facet, k_udl, k_q1_update, k_final (+ k_avg for mixed systems)
+        per_stage = 5 + ((S->prec == CGL_FP32_MIXED && S->nc > 1) ? 1 : 0);
     }
     *kernels = 3 * per_stage + 1 + 1;  // + dt finalisation (1) + time advance (1)
     return CGL_OK;

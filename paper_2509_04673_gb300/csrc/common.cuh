@@ -76,7 +76,7 @@ struct ProbDev {
     double tc;
 };
 
-enum { OPT_FP64_LIMITER = 1, OPT_UNFUSED_SWEEPS = 2, OPT_SUBCELL_DT = 4 };
+enum { OPT_FP64_LIMITER = 1, OPT_UNFUSED_SWEEPS = 2, OPT_SUBCELL_DT = 4, OPT_AEC_Q1 = 8 };
 
 // typed views of the problem and mesh constants: float kernels read the
 // float copies, float64 kernels the originals

@@ -2098,12 +2098,16 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
 
 // element part of the update: theta, f_i^e (eq. (aec)), the slope limiter
 // beta_e (eqs. (slimit1), (slimit2), Appendix A) and the SSP increments
-template <class R, int P, class Ph>
+// Q1: the variant of eq. (aecQ1); the caller passes ER = -D_i (the
+// divergence term), ud = udot^L and fh = 0, and the contributions are scaled
+// by gamma_e (gq)
+template <class R, int P, class Ph, bool Q1 = false>
 DEV void element_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Dim<P>::N2],
                       const R* __restrict__ ud, const R* __restrict__ ER, const float* __restrict__ cf,
                       const float* __restrict__ avg, const double (&uec)[Ph::NC], double dt, double dte, double rdte,
                       const double (&ubec)[Ph::NC], const R (&fh)[Ph::NC], R* __restrict__ EW,
-                      double* __restrict__ beta_out, unsigned long long* __restrict__ cnt, int ex, int ey, int e) {
+                      double* __restrict__ beta_out, unsigned long long* __restrict__ cnt, int ex, int ey, int e,
+                      double gq = 1.0) {
     constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2;
     const Tab<R>& T = TabSel<R>::t(P);
     const double me = m.me;
@@ -2176,6 +2180,7 @@ DEV void element_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][
                 R Ri = ER[ev_at(m.E, e, i, c, NC)];
                 R dev = (U[c][i] - ueh) - uel;
                 F[c][i] = meR * dev + dteR * (((Ri + fh_term) - h2 * s) + meR * UD[i]);
+                if constexpr (Q1) F[c][i] = R(gq) * F[c][i];
             }
     }
     // slope limiter beta_e
@@ -2270,6 +2275,155 @@ DEV void update_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
 #pragma unroll
     for (int c = 0; c < NC; ++c) ube_out[c * m.E + e] = ubec[c];
     element_part<R, P, Ph>(m, pr, U, ud, ER, cf, avg, uec, dt, dte, rdte, ubec, fh, EW, beta_out, cnt, ex, ey, e);
+}
+
+// ---------------------------------------------------------------------------
+// The Q1 variant, eq. (aecQ1) (option OPT_AEC_Q1):
+//   f_i^e = gamma_e ( m_i^e (u_i - u^e) - dt_e [ D_i + (M udot^L)_i - m_i^e udot^L_i ] ),
+//   D_i = int (phi_i - m_i^e/|K_e|) div f_h,  f_h = sum_j f(u_j) phi_j,
+// udot^L from the low-order scheme, eq. (weak:low2).  Three kernels replace
+// the g_h, residual and udot kernels: k_q1_facet (ubar^e and -D_i),
+// k_udl (udot^L at the nodes) and k_q1_update (the element part of the
+// update with ER = -D_i, udot := udot^L, no facet term, scaled by gamma_e).
+// ---------------------------------------------------------------------------
+template <class R, int P, class Ph>
+__global__ void __launch_bounds__(128) k_q1_facet(MeshDev m, ProbDev pr, const R* __restrict__ u,
+                                                  const double* __restrict__ ue, const double* __restrict__ dte_a,
+                                                  const double* __restrict__ ubl, const R* __restrict__ qcap,
+                                                  const R* __restrict__ fl_in, const float* __restrict__ cf,
+                                                  R* __restrict__ ER, double* __restrict__ ube_out) {
+    pdl_begin();
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
+    constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2;
+    const Tab<R>& T = TabSel<R>::t(P);
+    int nb[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
+    R U[NC][N2];
+    load_block<R, P, NC>(u, m, ex, ey, U);
+    double uec[NC], ublc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        uec[c] = ue[c * m.E + e];
+        ublc[c] = ubl[c * m.E + e];
+    }
+    double ubec[NC];
+    R fh[NC];
+    facet_part<R, P, Ph>(m, pr, U, nb, uec, ublc, dte_a[m.E + e], dte_a, ubl, qcap, fl_in, cf, e, ubec, fh);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ube_out[c * m.E + e] = ubec[c];
+    // nodal fluxes f(u_j)
+    R FX[NC][N2], FY[NC][N2];
+#pragma unroll
+    for (int j = 0; j < N2; ++j) {
+        R uj[NC], fx[NC], fy[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) uj[c] = U[c][j];
+        Ph::template flux<R>(uj, fx, fy, pr);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            FX[c][j] = fx[c];
+            FY[c][j] = fy[c];
+        }
+    }
+    // int phi_i d_x phi_j = h int B_a B_c' int B_b B_d (C[c][a] = int B_c' B_a),
+    // int d_x phi_j = sum_i of it; the same with x and y exchanged
+    const R h = PV<R>::h(m);
+    R csum[N1], msum[N1];
+#pragma unroll
+    for (int c = 0; c < N1; ++c) {
+        R s1 = R(0), s2 = R(0);
+#pragma unroll
+        for (int a = 0; a < N1; ++a) {
+            s1 += T.C[c][a];
+            s2 += T.M[a][c];
+        }
+        csum[c] = s1;
+        msum[c] = s2;
+    }
+    const R inv_n2 = R(1) / R(N2);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        // mean term (m_i^e/|K_e|) sum_j c_j . f(u_j), the same for every i
+        R mean = R(0);
+#pragma unroll
+        for (int d = 0; d < N1; ++d)
+#pragma unroll
+            for (int cc = 0; cc < N1; ++cc)
+                mean += (csum[cc] * msum[d]) * FX[c][d * N1 + cc] + (msum[cc] * csum[d]) * FY[c][d * N1 + cc];
+        mean = h * mean * inv_n2;
+#pragma unroll
+        for (int b = 0; b < N1; ++b)
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                R s = R(0);
+#pragma unroll
+                for (int d = 0; d < N1; ++d)
+#pragma unroll
+                    for (int cc = 0; cc < N1; ++cc)
+                        s += (T.C[cc][a] * T.M[b][d]) * FX[c][d * N1 + cc] + (T.M[a][cc] * T.C[d][b]) * FY[c][d * N1 + cc];
+                ER[ev_at(m.E, e, b * N1 + a, c, NC)] = -(h * s - mean);
+            }
+    }
+}
+
+// udot^L_i = (1/|E_i|) sum_{e in E_i} (ubar^e - u_i) / dt_e, eq. (weak:low2)
+// with m_i = |E_i| m_i^e (float64 sums, fixed order)
+template <class R, int P, int NC>
+__global__ void k_udl(MeshDev m, const R* __restrict__ u, const double* __restrict__ ube,
+                      const double* __restrict__ dte_a, R* __restrict__ ud) {
+    pdl_begin();
+    int gx, gy;
+    long long node;
+    if (!node_of_thread(m, gx, gy, node)) return;
+    const NodeC<P> c = node_c<P>(m, gx, gy);
+    const double w = inv_count<double>(c.nxc * c.nyc);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const double ui = (double)u[(long long)k * m.NN + node];
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (j < c.nyc) {
+                const int ey = j ? c.ey1 : c.ey0;
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    if (i < c.nxc) {
+                        const int e = ey * m.nx + (i ? c.ex1 : c.ex0);
+                        s += (ube[k * m.E + e] - ui) * dte_a[2 * m.E + e];
+                    }
+                }
+            }
+        }
+        ud[(long long)k * m.NN + node] = R(s * w);
+    }
+}
+
+template <class R, int P, class Ph>
+__global__ void __launch_bounds__(128) k_q1_update(MeshDev m, ProbDev pr, const R* __restrict__ u,
+                                                   const R* __restrict__ udl, const double* __restrict__ ue,
+                                                   const double* __restrict__ dte_a, const R* __restrict__ ER,
+                                                   const float* __restrict__ cf, const float* __restrict__ avg,
+                                                   const double* __restrict__ ube, const double* __restrict__ gam,
+                                                   const double* __restrict__ dtp, R* __restrict__ EW,
+                                                   double* __restrict__ beta_out, unsigned long long* __restrict__ cnt) {
+    pdl_begin();
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
+    constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
+    R U[NC][N2];
+    load_block<R, P, NC>(u, m, ex, ey, U);
+    double uec[NC], ubec[NC];
+    R fh[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        uec[c] = ue[c * m.E + e];
+        ubec[c] = ube[c * m.E + e];
+        fh[c] = R(0);
+    }
+    element_part<R, P, Ph, true>(m, pr, U, udl, ER, cf, avg, uec, *dtp, dte_a[e], dte_a[2 * m.E + e], ubec, fh, EW,
+                                 beta_out, cnt, ex, ey, e, gam[e]);
 }
 
 // Euler at p = 2: 3 blocks of 128 per SM (a 170-register cap, no spills)

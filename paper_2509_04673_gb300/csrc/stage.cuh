@@ -35,7 +35,7 @@ struct Bufs {
 // kernel identifiers for per-kernel timing
 enum KernelId {
     KID_AVG = 0, KID_PRE, KID_DT, KID_GRAD, KID_GATHER, KID_GRADF, KID_SWEEP, KID_RES,
-    KID_UPDATE, KID_FINAL, KID_TADV, KID_UDOTF, KID_FACET, KID_RESW, KID_COUNT
+    KID_UPDATE, KID_FINAL, KID_TADV, KID_UDOTF, KID_FACET, KID_RESW, KID_Q1F, KID_UDL, KID_COUNT
 };
 
 // optional per-launch timing: CUDA events recorded around every launch on
@@ -118,7 +118,9 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
     // FP32-mixed: the second stream starts with the Galerkin part of the
     // residual, which needs only u
     constexpr bool split = sizeof(R) == 4;
-    const bool split_res = split && split_residual(m);
+    // the Q1 variant of eq. (aecQ1) needs neither g_h, nor the residual, nor udot
+    const bool q1 = (pr.opts & OPT_AEC_Q1) != 0 && pr.mode != MODE_LO;
+    const bool split_res = split && split_residual(m) && !q1;
     if (split_res && !dt_only && pr.mode != MODE_LO) {
         chk(cudaEventRecord(B.ev_fork0, st));
         chk(cudaStreamWaitEvent(B.st2, B.ev_fork0, 0));
@@ -140,6 +142,24 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
                    chk(launch(pdl, k_dt_final, dim3(1), dim3(1), st, B.dtbits, pr.cfl, (const double*)B.t,
                               (const double*)B.t_end, B.dt)));
     if (dt_only) return err != cudaSuccess ? err : cudaGetLastError();
+    if (q1) {
+        CGL_LAUNCH(prof, KID_Q1F, st,
+                   chk(launch(pdl, k_q1_facet<R, P, Ph>, ge, be, st, m, pr, (const R*)u, (const double*)B.ue,
+                              (const double*)B.dte, (const double*)B.ubl, (const R*)B.q, (const R*)B.fl,
+                              (const float*)B.cf, (R*)B.ER, B.ube)));
+        CGL_LAUNCH(prof, KID_UDL, st,
+                   chk(launch(pdl, k_udl<R, P, NC>, gn, bn, st, m, (const R*)u, (const double*)B.ube,
+                              (const double*)B.dte, (R*)B.ud)));
+        CGL_LAUNCH(prof, KID_UPDATE, st,
+                   chk(launch(pdl, k_q1_update<R, P, Ph>, ge, be, st, m, pr, (const R*)u, (const R*)B.ud,
+                              (const double*)B.ue, (const double*)B.dte, (const R*)B.ER, (const float*)B.cf,
+                              (const float*)B.avg, (const double*)B.ube, (const double*)B.gam,
+                              (const double*)B.dt, (R*)B.EW, B.beta, B.cnt)));
+        CGL_LAUNCH(prof, KID_FINAL, st,
+                   chk(launch(pdl, k_final<R, P, NC>, gn, bn, st, m, pr, (const R*)B.EW, (R*)B.un, u, R(a), R(b),
+                              B.cnt)));
+        return err != cudaSuccess ? err : cudaGetLastError();
+    }
     // FP32-mixed: the facet part of the update on the second stream, beside
     // the g_h and udot kernels
     constexpr bool split_update = sizeof(R) == 4;

@@ -22,6 +22,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="kpp",
                     choices=["kpp", "advection", "euler_quadrants", "euler_blast", "dmr", "batched"])
+    ap.add_argument("--options", type=int, default=0, help="cgl_problem.options bits to add (e.g. 8: eq. (aecQ1))")
+    ap.add_argument("--fl", type=int, default=-1, help="flux limiter setting (default: the workload's own)")
     ap.add_argument("--t-end", type=float, default=0.0,
                     help="run to this time instead of a step count (reports the steps taken)")
     ap.add_argument("--autotune", action="store_true", help="batched: tune tile lengths first")
@@ -50,6 +52,9 @@ def main():
         mesh, prob, u0 = inputs.dmr_config(a.n, a.p or 2)
     else:
         mesh, prob, u0 = inputs.euler_blast_config(a.n, a.n, a.p or 2)
+    prob.options |= a.options
+    if a.fl >= 0:
+        prob.flux_limiter = a.fl
     stream = torch.cuda.Stream()
     m = cgl.Mesh(mesh)
     st = cgl.State(m, u0.shape[0], a.prec, stream=stream.cuda_stream)
@@ -92,6 +97,9 @@ def run_batched(a):
     from paper_2509_04673_gb300 import build, cgl
     build.build()
     cases = inputs.batched_instances()
+    prob.options |= a.options
+    if a.fl >= 0:
+        prob.flux_limiter = a.fl
     stream = torch.cuda.Stream()
     states = []
     for mesh, prob, u0 in cases:

@@ -1,0 +1,118 @@
+"""GPU parity of the Q1-variant element contributions of eq. (aecQ1) (option
+CGL_OPT_AEC_Q1): udot^L, ubar^e, beta_e and the nodal values after one
+stage within 1e-12 of the oracle in FP64 (Q1 and Q2, every flux, modes HO
+and WENO-L, flux limiter off and on), several steps with device dt, and the
+FP32-mixed form with zero invariant-domain violations.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+from inputs import Mesh, Problem
+import oracle.scheme as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cgl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2509_04673_gb300 import build, cgl as C
+    build.build()
+    return C
+
+
+def _rel(a, b, nc):
+    a = a.reshape(nc, -1)
+    b = b.reshape(nc, -1)
+    sc = np.maximum(np.abs(b).max(axis=1), 1e-300)
+    return float((np.abs(a - b).max(axis=1) / sc).max())
+
+
+def _case(flux, p, mode=inputs.MODE_WENO_L, fl=0):
+    if flux == inputs.FLUX_EULER:
+        mesh = Mesh(11, 7, p, 0.0, 11 / 7, 0.0, 1.0, inputs.BC_OUTFLOW, inputs.BC_OUTFLOW)
+        prob = Problem(flux=flux, mode=mode, flux_limiter=fl, options=8, umin=0.0, umax=0.0)
+        return mesh, prob, inputs.random_euler_state(mesh, 80 + p)
+    mesh = Mesh(11, 7, p, 0.0, 11 / 7, 0.0, 1.0)
+    lo, hi = (0.0, 1.0) if flux != inputs.FLUX_KPP else (math.pi / 4, 3.5 * math.pi)
+    prob = Problem(flux=flux, vx=0.8, vy=-0.6, umin=lo, umax=hi, mode=mode, flux_limiter=fl, options=8,
+                   w_lin=0.2)
+    return mesh, prob, inputs.random_scalar_state(mesh, 90 + p + 10 * flux, lo, hi, 0.4)
+
+
+FLUXES = [inputs.FLUX_ADVECTION, inputs.FLUX_BURGERS, inputs.FLUX_KPP, inputs.FLUX_EULER]
+
+
+@pytest.mark.parametrize("flux", FLUXES)
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("mode, fl", [(inputs.MODE_WENO_L, 0), (inputs.MODE_HO, 0), (inputs.MODE_WENO_L, 1)])
+def test_stage_parity_fp64(cgl, flux, p, mode, fl):
+    mesh, prob, u = _case(flux, p, mode, fl)
+    om = S.OracleMesh(mesh)
+    dt = 0.5 * S.time_step(om, prob.as_dict(), u)
+    ref, info = S.ssp_stage(om, prob.as_dict(), u, u, dt, 0.0, 1.0)
+    _, fo = S.fe_stage(om, prob.as_dict(), u, dt)
+    st = cgl.State(cgl.Mesh(mesh), u.shape[0], cgl.FP64)
+    st.set_problem(prob)
+    st.set_state(u)
+    st.set_base_state(u)
+    st.set_time(0.0)
+    ginfo = st.stage(dt, 0.0, 1.0, raise_on_idp=False)
+    out = st.get_state()
+    udl = st.get_field(cgl.FIELD_UDOT).reshape(fo["udot_l"].shape)
+    ube = st.get_field(cgl.FIELD_UBE).reshape(fo["ube"].shape)
+    beta = st.get_field(cgl.FIELD_BETA).reshape(-1)[:om.E]
+    st.close()
+    nc = u.shape[0]
+    assert ginfo["violations"] == info["violations"] == 0
+    assert np.abs(ube - fo["ube"]).max() <= 1e-12 * max(np.abs(fo["ube"]).max(), 1.0)
+    assert np.abs(udl - fo["udot_l"]).max() <= 1e-12 * max(np.abs(fo["udot_l"]).max(), 1.0)
+    assert np.abs(beta - fo["beta"]).max() <= 1e-10
+    assert _rel(out, ref, nc) <= 1e-12, _rel(out, ref, nc)
+
+
+@pytest.mark.parametrize("flux", [inputs.FLUX_KPP, inputs.FLUX_EULER])
+def test_multi_step_fp64(cgl, flux):
+    mesh, prob, u0 = _case(flux, 1)
+    ref, t_ref, st_ = S.run(mesh, prob.as_dict(), u0, 5)
+    g = cgl.State(cgl.Mesh(mesh), u0.shape[0], cgl.FP64)
+    g.set_problem(prob)
+    g.set_state(u0)
+    g.set_time(0.0)
+    info = g.step(5, raise_on_idp=False)
+    out = g.get_state()
+    g.close()
+    assert abs(info["t"] - t_ref) <= 1e-13 * t_ref
+    assert info["violations"] == 0 and st_["violations"] == 0
+    assert _rel(out, ref, u0.shape[0]) <= 1e-11
+
+
+@pytest.mark.parametrize("flux", FLUXES)
+def test_mixed_precision_idp(cgl, flux):
+    mesh, prob, u = _case(flux, 1)
+    u = u.astype(np.float32).astype(np.float64)
+    if flux != inputs.FLUX_EULER:
+        lo32 = np.float32(prob.umin)
+        if float(lo32) < prob.umin:
+            lo32 = np.nextafter(lo32, np.float32(np.inf))
+        hi32 = np.float32(prob.umax)
+        if float(hi32) > prob.umax:
+            hi32 = np.nextafter(hi32, np.float32(-np.inf))
+        u = np.clip(u, float(lo32), float(hi32))
+    ref, _, _ = S.run(mesh, prob.as_dict(), u, 3)
+    g = cgl.State(cgl.Mesh(mesh), u.shape[0], cgl.FP32_MIXED)
+    g.set_problem(prob)
+    g.set_state(u)
+    g.set_time(0.0)
+    info = g.step(3, raise_on_idp=False)
+    out = g.get_state()
+    g.close()
+    nc = u.shape[0]
+    assert info["violations"] == 0
+    l1 = np.abs(out - ref).reshape(nc, -1).sum(axis=1) / np.abs(ref).reshape(nc, -1).sum(axis=1)
+    assert l1.max() <= 2e-5, l1
