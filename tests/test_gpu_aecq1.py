@@ -116,3 +116,37 @@ def test_mixed_precision_idp(cgl, flux):
     assert info["violations"] == 0
     l1 = np.abs(out - ref).reshape(nc, -1).sum(axis=1) / np.abs(ref).reshape(nc, -1).sum(axis=1)
     assert l1.max() <= 2e-5, l1
+
+
+@pytest.mark.parametrize("mode, paper", [(inputs.MODE_LO, (0.785, 10.885)), (inputs.MODE_HO, (-2.054, 14.547))])
+def test_kpp_paper_setting(cgl, mode, paper):
+    """The 2D KPP test of Sec. 5.3.2 as the paper runs it: Q1, h = 1/128 on
+    (-2,2) x (-2.5,1.5), eq. (aecQ1), flux limiter off, dt_e from eq.
+    (dtmaxcell), fixed dt = 1e-3 to t = 1 (SSP-RK3 through cgl_stage), FP64.
+    LO must stay in [pi/4, 7pi/2] with its maximum near the paper's 10.885;
+    HO overshoots and undershoots as in the paper (range printed for the
+    record)."""
+    mesh, prob, u0 = inputs.kpp_config(512, 512, 1)
+    prob.mode = mode
+    prob.flux_limiter = 0
+    prob.options = 8
+    st = cgl.State(cgl.Mesh(mesh), 1, cgl.FP64)
+    st.set_problem(prob)
+    st.set_state(u0)
+    st.set_base_state(u0)
+    dt = 1e-3
+    for k in range(1000):
+        st.set_time(k * dt)
+        for a, b in S.SSP3:
+            st.stage(dt, a, b, raise_on_idp=False)
+    u = st.get_state()
+    st.close()
+    lo, hi = float(u.min()), float(u.max())
+    print(f"KPP Q1 h=1/128 mode {mode}: [{lo:.3f}, {hi:.3f}], paper {paper}")
+    assert np.isfinite(u).all()
+    if mode == inputs.MODE_LO:
+        assert lo >= math.pi / 4 - 1e-12 and hi <= 3.5 * math.pi + 1e-12
+        assert abs(hi - paper[1]) <= 0.05 * paper[1]
+    else:
+        # the HO solution leaves [pi/4, 7pi/2] on both sides, as in the paper
+        assert lo < math.pi / 4 - 0.1 and hi > 3.5 * math.pi + 0.1
