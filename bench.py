@@ -249,7 +249,6 @@ NCU_TRAFFIC = {
     ("k_res_ev", "kpp_256x256_q2"): 4270080,
     ("k_gather_init", "kpp_256x256_q2"): 2364928,
     ("k_update_ev", "kpp_256x256_q2"): 6056960,
-    ("k_final", "kpp_256x256_q2"): 3418624,
 }
 
 

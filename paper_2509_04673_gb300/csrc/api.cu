@@ -940,14 +940,12 @@ static cudaError_t enqueue_step(cgl_state* S, Prof* prof = nullptr) {
     ProbDev p2 = S->pd, p3 = S->pd;
     p2.tc = 1.0;
     p3.tc = 0.5;
+    p3.last_stage = 1;  // its k_final advances t by dt
     cudaError_t e = S->stage(B, m, S->pd, 0.0, 1.0, true, false, S->st, prof);
     if (e != cudaSuccess) return e;
     e = S->stage(B, m, p2, 0.75, 0.25, false, false, S->st, prof);
     if (e != cudaSuccess) return e;
     e = S->stage(B, m, p3, 1.0 / 3.0, 2.0 / 3.0, false, false, S->st, prof);
-    if (e != cudaSuccess) return e;
-    CGL_LAUNCH(prof, KID_TADV, S->st, (e = launch(prof == nullptr, k_t_advance, dim3(1), dim3(1), S->st, B.t,
-                                                   (const double*)B.dt)));
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -1109,7 +1107,7 @@ extern "C" cgl_status cgl_launches_per_step(cgl_state* S, int64_t* kernels) {
         // k_pre, k_q1_facet, k_udl, k_q1_update, k_final (+ k_avg for mixed systems)
         per_stage = 5 + ((S->prec == CGL_FP32_MIXED && S->nc > 1) ? 1 : 0);
     }
-    *kernels = 3 * per_stage + 1 + 1;  // + dt finalisation (1) + time advance (1)
+    *kernels = 3 * per_stage + 1;  // + dt finalisation; the time advance rides in the last k_final
     return CGL_OK;
 }
 

@@ -74,6 +74,7 @@ struct ProbDev {
     const double* t_dev;   // device time t of the step and its dt: the stage
     const double* dt_dev;  // time is t + tc dt (read only by moving splits)
     double tc;
+    int last_stage;        // the stage ends a step: its k_final advances t
 };
 
 enum { OPT_FP64_LIMITER = 1, OPT_UNFUSED_SWEEPS = 2, OPT_SUBCELL_DT = 4, OPT_AEC_Q1 = 8 };

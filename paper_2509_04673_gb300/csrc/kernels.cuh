@@ -20,7 +20,8 @@
 //                  Appendix A), ubar^e (eq. (uelim)), f_i^e (eq. (aec)),
 //                  beta_e (eqs. (slimit1), (slimit2), Appendix A), element
 //                  contributions of eq. (eq:SSPupdate)
-//   k_final        node gather, SSP-RK combination, invariant-domain check
+//   k_final        node gather, SSP-RK combination, invariant-domain check;
+//                  on the last stage of a step also t += dt
 //
 // One thread per element (or node; the stencils use 32 x 16 node tiles).
 // Kernels are templated on the bulk precision R (double, or float in the
@@ -1068,10 +1069,6 @@ static __global__ void k_dt_final(unsigned long long* bits, double cfl, const do
     if (rem < d) d = rem > 0.0 ? rem : 0.0;
     *dt = d;
 }
-
-static __global__ void k_t_advance(double* t, const double* dt) { pdl_begin(); *t = *t + *dt; }
-
-
 
 // ---------------------------------------------------------------------------
 // node-centric gathers over E_i in a fixed order (lower neighbour first in
@@ -2600,8 +2597,12 @@ DEV void final_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ EW,
 template <class R, int P, int NC>
 __global__ void k_final(MeshDev m, ProbDev pr, const R* __restrict__ EW,
                         R* __restrict__ un, R* __restrict__ u, R a, R b,
-                        unsigned long long* __restrict__ cnt) {
+                        unsigned long long* __restrict__ cnt, double* __restrict__ t_adv,
+                        const double* __restrict__ dtp) {
     pdl_begin();
+    // last stage of a step: one thread advances the time (nothing in this
+    // kernel reads it)
+    if (t_adv && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) *t_adv += *dtp;
     int gx, gy;
     long long node;
     if (!node_of_thread(m, gx, gy, node)) return;

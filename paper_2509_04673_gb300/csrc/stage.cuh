@@ -157,7 +157,7 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
                               (const double*)B.dt, (R*)B.EW, B.beta, B.cnt)));
         CGL_LAUNCH(prof, KID_FINAL, st,
                    chk(launch(pdl, k_final<R, P, NC>, gn, bn, st, m, pr, (const R*)B.EW, (R*)B.un, u, R(a), R(b),
-                              B.cnt)));
+                              B.cnt, pr.last_stage ? B.t : (double*)nullptr, (const double*)B.dt)));
         return err != cudaSuccess ? err : cudaGetLastError();
     }
     // FP32-mixed: the facet part of the update on the second stream, beside
@@ -254,7 +254,7 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
                           B.ube, B.beta, B.cnt)));
     CGL_LAUNCH(prof, KID_FINAL, st,
                chk(launch(pdl, k_final<R, P, NC>, gn, bn, st, m, pr, (const R*)B.EW, (R*)B.un, u, R(a), R(b),
-                          B.cnt)));
+                          B.cnt, pr.last_stage ? B.t : (double*)nullptr, (const double*)B.dt)));
     return err != cudaSuccess ? err : cudaGetLastError();
 }
 
