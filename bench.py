@@ -242,13 +242,14 @@ def load_peaks():
 # profiles/kpp256_q2_dram_per_launch.md (kernels unchanged since; the two
 # Richardson sweeps averaged like their algorithmic bytes)
 NCU_TRAFFIC = {
-    ("k_pre", "kpp_256x256_q2"): 1123840,
-    ("k_facet", "kpp_256x256_q2"): 3719680,
-    ("k_grad_rhs", "kpp_256x256_q2"): 1064704,
-    ("k_mass_sweep", "kpp_256x256_q2"): (4223488 + 2115328) // 2,
+    ("k_pre", "kpp_256x256_q2"): 1124608,
+    ("k_facet", "kpp_256x256_q2"): 3719168,
+    ("k_grad_rhs", "kpp_256x256_q2"): 1064448,
+    ("k_mass_sweep", "kpp_256x256_q2"): (4223744 + 2115584) // 2,
     ("k_res_ev", "kpp_256x256_q2"): 4270080,
-    ("k_gather_init", "kpp_256x256_q2"): 2364928,
-    ("k_update_ev", "kpp_256x256_q2"): 6056960,
+    ("k_gather_init", "kpp_256x256_q2"): 2364416,
+    ("k_update_ev", "kpp_256x256_q2"): 6058496,
+    ("k_final", "kpp_256x256_q2"): 3418112,
 }
 
 
