@@ -1365,9 +1365,9 @@ DEV R class_weight(const Tab<R>& T, int cls, int off) {
 }
 
 // stage one field (rows gy0-P.., columns gx0-P..) of the tile in shared memory
-template <class R, int P, int BY>
+template <class R, int P, int BY, int TY = ST_TY>
 DEV void stage_tile(const MeshDev& m, const R* __restrict__ x, R (*xs)[ST_TX + 2 * P], int gx0, int gy0, int tid) {
-    constexpr int HX = ST_TX + 2 * P, HY = ST_TY + 2 * P;
+    constexpr int HX = ST_TX + 2 * P, HY = TY + 2 * P;
     for (int i = tid; i < HX * HY; i += ST_TX * BY) {
         const int r = i / HX, c = i - r * HX;
         int gy = gy0 - P + r, gx = gx0 - P + c;
@@ -1384,9 +1384,9 @@ DEV void stage_tile(const MeshDev& m, const R* __restrict__ x, R (*xs)[ST_TX + 2
 
 // fields staged together: as many as fit in 32 KB of shared memory (a
 // divisor of NV), so one round of loads and barriers serves all of them
-template <class R, int P, int NV, int NT>
+template <class R, int P, int NV, int NT, int TY = ST_TY>
 struct StFields {
-    static constexpr int HX = ST_TX + 2 * P, HY = ST_TY + 2 * P;
+    static constexpr int HX = ST_TX + 2 * P, HY = TY + 2 * P;
     static constexpr int bytes(int f) { return f * (HY * HX + NT * HY * ST_TX) * (int)sizeof(R); }
     static constexpr int value = (bytes(NV) <= 32768) ? NV
                                  : (NV % 4 == 0 && bytes(4) <= 32768) ? 4
@@ -1400,11 +1400,11 @@ struct StFields {
 // (gx0, gy0) by a block of 32 x BY threads (thread (tx, ty)); ws: shared
 // workspace of StFields<R, P, NC, 2>::ws elements.  All threads of the block
 // call it together.
-template <class R, int P, int NC, int BY>
+template <class R, int P, int NC, int BY, int TY = ST_TY>
 DEV void grad_tile(const MeshDev& m, const R* __restrict__ u, R* __restrict__ bout, R* __restrict__ gout,
                    int gx0, int gy0, int tx, int ty, R* ws) {
-    constexpr int HX = ST_TX + 2 * P, HY = ST_TY + 2 * P, NW = 2 * P + 1, NCL = P + 2, NJ = ST_TY / BY;
-    constexpr int FB = StFields<R, P, NC, 2>::value;
+    constexpr int HX = ST_TX + 2 * P, HY = TY + 2 * P, NW = 2 * P + 1, NCL = P + 2, NJ = TY / BY;
+    constexpr int FB = StFields<R, P, NC, 2, TY>::value;
     R(*xs)[HY][HX] = reinterpret_cast<R(*)[HY][HX]>(ws);
     R(*tC)[HY][ST_TX] = reinterpret_cast<R(*)[HY][ST_TX]>(ws + FB * HY * HX);
     R(*tM)[HY][ST_TX] = reinterpret_cast<R(*)[HY][ST_TX]>(ws + FB * HY * HX + FB * HY * ST_TX);
@@ -1424,7 +1424,7 @@ DEV void grad_tile(const MeshDev& m, const R* __restrict__ u, R* __restrict__ bo
     for (int v0 = 0; v0 < NC; v0 += FB) {
         if (v0 > 0) __syncthreads();  // previous fields consumed
 #pragma unroll
-        for (int f = 0; f < FB; ++f) stage_tile<R, P, BY>(m, u + (long long)(v0 + f) * m.NN, xs[f], gx0, gy0, tid);
+        for (int f = 0; f < FB; ++f) stage_tile<R, P, BY, TY>(m, u + (long long)(v0 + f) * m.NN, xs[f], gx0, gy0, tid);
         __syncthreads();
         // along x, every halo row: derivative (for b_x) and mass (for b_y)
         for (int r = ty; r < HY; r += BY) {
@@ -1472,11 +1472,11 @@ DEV void grad_tile(const MeshDev& m, const R* __restrict__ u, R* __restrict__ bo
 
 // one Richardson sweep for NV fields on the 32 x 16 node tile at (gx0, gy0);
 // ws: StFields<R, P, NV, 1>::ws elements of shared memory
-template <class R, int P, int NV, int BY>
+template <class R, int P, int NV, int BY, int TY = ST_TY>
 DEV void sweep_tile(const MeshDev& m, const R* __restrict__ xin, const R* __restrict__ b, R* __restrict__ xout,
                     int gx0, int gy0, int tx, int ty, R* ws) {
-    constexpr int HX = ST_TX + 2 * P, HY = ST_TY + 2 * P, NW = 2 * P + 1, NCL = P + 2, NJ = ST_TY / BY;
-    constexpr int FB = StFields<R, P, NV, 1>::value;
+    constexpr int HX = ST_TX + 2 * P, HY = TY + 2 * P, NW = 2 * P + 1, NCL = P + 2, NJ = TY / BY;
+    constexpr int FB = StFields<R, P, NV, 1, TY>::value;
     R(*xs)[HY][HX] = reinterpret_cast<R(*)[HY][HX]>(ws);
     R(*t)[HY][ST_TX] = reinterpret_cast<R(*)[HY][ST_TX]>(ws + FB * HY * HX);
     R(*W)[NW] = reinterpret_cast<R(*)[NW]>(ws + FB * (HY * HX + HY * ST_TX));
@@ -1503,7 +1503,7 @@ DEV void sweep_tile(const MeshDev& m, const R* __restrict__ xin, const R* __rest
         }
         if (v0 > 0) __syncthreads();
 #pragma unroll
-        for (int f = 0; f < FB; ++f) stage_tile<R, P, BY>(m, xin + (long long)(v0 + f) * m.NN, xs[f], gx0, gy0, tid);
+        for (int f = 0; f < FB; ++f) stage_tile<R, P, BY, TY>(m, xin + (long long)(v0 + f) * m.NN, xs[f], gx0, gy0, tid);
         __syncthreads();
         for (int r = ty; r < HY; r += BY) {
 #pragma unroll
@@ -1537,23 +1537,25 @@ DEV void sweep_tile(const MeshDev& m, const R* __restrict__ xin, const R* __rest
 // needs only u, whose last writer completed before k_pre let this kernel
 // start (pdl_wait_then_trigger), so it runs beside k_pre and waits for it
 // only before exiting
-template <class R, int P, int NC>
+// TY: node rows per tile (8 on small meshes: shorter per-block chains in a
+// partial wave; 16 on large ones: less halo)
+template <class R, int P, int NC, int TY = ST_TY>
 __global__ void __launch_bounds__(ST_TX * ST_BY) k_grad_rhs(MeshDev m, const R* __restrict__ u,
                                                             R* __restrict__ bout, R* __restrict__ gout) {
     pdl_trigger();
-    __shared__ R ws[StFields<R, P, NC, 2>::ws];
-    grad_tile<R, P, NC, ST_BY>(m, u, bout, gout, blockIdx.x * ST_TX, blockIdx.y * ST_TY, threadIdx.x, threadIdx.y,
-                               ws);
+    __shared__ R ws[StFields<R, P, NC, 2, TY>::ws];
+    grad_tile<R, P, NC, ST_BY, TY>(m, u, bout, gout, blockIdx.x * ST_TX, blockIdx.y * TY, threadIdx.x, threadIdx.y,
+                                   ws);
     pdl_wait();
 }
 
-template <class R, int P, int NV>
+template <class R, int P, int NV, int TY = ST_TY>
 __global__ void __launch_bounds__(ST_TX * ST_BY) k_mass_sweep(MeshDev m, const R* __restrict__ xin,
                                                               const R* __restrict__ b, R* __restrict__ xout) {
     pdl_begin();
-    __shared__ R ws[StFields<R, P, NV, 1>::ws];
-    sweep_tile<R, P, NV, ST_BY>(m, xin, b, xout, blockIdx.x * ST_TX, blockIdx.y * ST_TY, threadIdx.x, threadIdx.y,
-                                ws);
+    __shared__ R ws[StFields<R, P, NV, 1, TY>::ws];
+    sweep_tile<R, P, NV, ST_BY, TY>(m, xin, b, xout, blockIdx.x * ST_TX, blockIdx.y * TY, threadIdx.x, threadIdx.y,
+                                    ws);
 }
 
 // runtime-degree candidate list (diagnostics only)
