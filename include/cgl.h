@@ -127,7 +127,8 @@ typedef struct cgl_mesh_desc {
  * m_i udot^L_i = sum_e m_i^e (ubar^e - u_i)/dt_e of eq. (weak:low2) taken from
  * the stage's intermediate averages ubar^e.  The g_h projection, the target
  * residual and the udot solve are skipped.  The KPP entropy correction of that
- * section is not included. */
+ * section is not included.  Batched states (cgl_batch_create) reject this option
+ * and CGL_OPT_SUBCELL_DT. */
 #define CGL_OPT_AEC_Q1 8
 
 typedef struct cgl_problem {

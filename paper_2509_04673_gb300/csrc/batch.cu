@@ -373,6 +373,7 @@ extern "C" cgl_status cgl_batch_create(cgl_state* const* states, int32_t n, cgl_
         if (s->prec != CGL_FP32_MIXED) return bfail(CGL_EINVAL, "batched states must be FP32_MIXED");
         if (s->has_bnd) return bfail(CGL_EINVAL, "batched states take the mesh's boundary conditions");
         if (s->pd.opts & OPT_SUBCELL_DT) return bfail(CGL_EINVAL, "batched states take the macrocell dt_e");
+        if (s->pd.opts & OPT_AEC_Q1) return bfail(CGL_EINVAL, "batched states take the element contributions of eq. (aec)");
         if (s->nc != 1 || s->prob.flux == CGL_FLUX_EULER) return bfail(CGL_EINVAL, "batched states must be scalar");
         if (s->device != s0->device) return bfail(CGL_EINVAL, "batched states must share a device");
         if (s->prob.mode != s0->prob.mode || s->prob.k_g != s0->prob.k_g || s->prob.k_u != s0->prob.k_u)
