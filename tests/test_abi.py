@@ -76,3 +76,40 @@ def test_no_gpu_fails_loudly(L):
     with pytest.raises(cgl.CglError) as e:
         cgl.State(m, 1)
     assert e.value.status == cgl.ECUDA
+
+
+def test_ctypes_layouts_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the sizes and field offsets
+    that a C compiler gives the structs of include/cgl.h (host only)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"cgl_mesh_desc": cgl.cgl_mesh_desc, "cgl_problem": cgl.cgl_problem,
+               "cgl_boundary": cgl.cgl_boundary, "cgl_step_info": cgl.cgl_step_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cgl.h"', "int main(void) {"]
+    for name, py in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in py._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            name, key, val = line.split()
+            got[(name, key)] = int(val)
+    for name, py in structs.items():
+        assert got[(name, "size")] == C_sizeof(py), name
+        for field, _ in py._fields_:
+            assert got[(name, field)] == getattr(py, field).offset, (name, field)
+
+
+def C_sizeof(t):
+    import ctypes
+    return ctypes.sizeof(t)
