@@ -67,7 +67,10 @@ class OracleMesh:
     """Index sets of a uniform nx x ny mesh of degree-p Bernstein squares
     (Table 1 of the paper: N_e, E_i, B_e) and dense element operators."""
 
-    def __init__(self, mesh):
+    def __init__(self, mesh, nq=None):
+        """nq: Gauss points per direction for the integrals of nonlinear
+        functions (default p + 2, reading R7; the pins use a high-order rule
+        to compare the weak form with a strong-form assembly)."""
         m = mesh if isinstance(mesh, dict) else mesh.as_dict()
         self.nx, self.ny, self.p = int(m["nx"]), int(m["ny"]), int(m["p"])
         self.x0, self.x1, self.y0, self.y1 = m["x0"], m["x1"], m["y0"], m["y1"]
@@ -136,10 +139,10 @@ class OracleMesh:
             "W": a_idx * n + 0, "E": a_idx * n + p,
             "S": 0 * n + a_idx, "N": p * n + a_idx,
         }
-        self._ops()
+        self._ops(nq)
 
-    def _ops(self):
-        T = tables(self.p)
+    def _ops(self, nq=None):
+        T = tables(self.p, nq)
         self.T = T
         h, p, n = self.h, self.p, self.n1
         M, C, D = T["M"], T["C"], T["D"]

@@ -118,6 +118,25 @@ class Brute:
                 a[i] += np.sum(W * B[l][0] * div)
         return a
 
+    def galerkin_strong_system(self, U, jac):
+        """a(phi_i, u_h) = sum_e int_K phi_i div f(u_h) for a system, with
+        div f = A_x(u_h) d_x u_h + A_y(u_h) d_y u_h; U has shape (nc, N) and
+        jac(uq) returns the flux Jacobians (A_x, A_y), each (nc, nc, nq)."""
+        nc = U.shape[0]
+        a = np.zeros((nc, self.N))
+        xi, eta, W = self.quad2()
+        B = self.basis_at(xi, eta)
+        for ex, ey in self.elements():
+            ids = [self.gid(ex, ey, aa, bb) for (aa, bb) in self.local()]
+            uq = np.array([sum(U[c, j] * B[l][0] for l, j in enumerate(ids)) for c in range(nc)])
+            ux = np.array([sum(U[c, j] * B[l][1] for l, j in enumerate(ids)) for c in range(nc)])
+            uy = np.array([sum(U[c, j] * B[l][2] for l, j in enumerate(ids)) for c in range(nc)])
+            Ax, Ay = jac(uq)
+            div = np.einsum("abq,bq->aq", Ax, ux) + np.einsum("abq,bq->aq", Ay, uy)
+            for l, i in enumerate(ids):
+                a[:, i] += np.sum(W * B[l][0] * div, axis=1)
+        return a
+
     def boundary_term(self, u, flux_n, F_llf, ub):
         """b(phi_i, u_h, u_hat) = int_dOmega phi_i [F(u_h, u_hat; n) - f(u_h).n] ds."""
         b = np.zeros(self.N)
