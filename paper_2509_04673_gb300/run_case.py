@@ -97,9 +97,10 @@ def run_batched(a):
     from paper_2509_04673_gb300 import build, cgl
     build.build()
     cases = inputs.batched_instances()
-    prob.options |= a.options
-    if a.fl >= 0:
-        prob.flux_limiter = a.fl
+    for _, prob, _ in cases:
+        prob.options |= a.options
+        if a.fl >= 0:
+            prob.flux_limiter = a.fl
     stream = torch.cuda.Stream()
     states = []
     for mesh, prob, u0 in cases:

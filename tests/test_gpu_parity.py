@@ -128,6 +128,11 @@ def test_stage_parity_fp64(cgl, name, ab):
     assert np.abs(f["dte"] - info["dte"]).max() <= 1e-13 * info["dte"].max()
     assert _rel(f["ubL"], info["ubL"], nc) <= 1e-13
     assert _rel(f["ube"], info["ube"], nc) <= TOL64
+    # the sensor and the slope limiter element by element: gamma_e and beta_e
+    # are continuous functions of the stage data with values in [0, 1]
+    if prob.mode != inputs.MODE_LO:
+        assert np.abs(f["gamma"] - info["gamma"]).max() <= 1e-10, np.abs(f["gamma"] - info["gamma"]).max()
+    assert np.abs(f["beta"] - info["beta"]).max() <= 1e-10, np.abs(f["beta"] - info["beta"]).max()
     assert ginfo["violations"] == info["violations"] == 0
 
 
