@@ -316,7 +316,9 @@ cgl_status cgl_get_field(cgl_state *state, int32_t field, double *host, size_t n
    on one device, with the same mode, k_g and k_u; the batch uses the first
    state's stream and references (does not copy) the states, which must
    outlive it. A batched instance evolves bitwise like the same state stepped
-   alone with cgl_step. */
+   alone with cgl_step. The batch copies each state's problem parameters at
+   creation: a later cgl_set_problem or cgl_set_boundary on a member state
+   is not seen by the batch (create a new batch after changing them). */
 typedef struct cgl_batch cgl_batch;
 cgl_status cgl_batch_create(cgl_state *const *states, int32_t n, cgl_batch **out);
 void cgl_batch_destroy(cgl_batch *batch);
@@ -329,8 +331,11 @@ cgl_status cgl_batch_step(cgl_batch *batch, int32_t nsteps, int64_t *violations)
 /* Enqueue nsteps steps without waiting. */
 cgl_status cgl_batch_step_async(cgl_batch *batch, int32_t nsteps);
 
-/* Launch geometry: persistent grid size, block size, tile counts, and
-   whether the step runs as a captured CUDA graph (1) or as direct launches. */
+/* Launch geometry: persistent grid size, block size, tile counts, and how
+   a step runs: 1 = a captured CUDA graph, 0 = no step has run yet (the
+   graph is captured at the first step), -1 = the capture failed and steps
+   run as direct cooperative launches (same results; cgl_last_error() then
+   names the CUDA error of the capture). */
 cgl_status cgl_batch_info(cgl_batch *batch, int32_t *grid, int32_t *block, int32_t *elem_tiles,
                           int32_t *node_tiles, int32_t *graph);
 
@@ -377,17 +382,27 @@ cgl_status cgl_gradient_noalloc(const cgl_mesh *mesh, const double *u, double *g
 
 /* --- measurement ------------------------------------------------------------ */
 
-/* Name of kernel identifier id (0 <= id < 12), "" otherwise. */
+/* Name of kernel identifier id (identifiers are below 32), "" for an
+   unused identifier. */
 const char *cgl_kernel_name(int32_t id);
 
 /* Run nsteps (1..1000) SSP-RK3 steps launch by launch (no graph) with CUDA
    events recorded around every kernel on the state's stream; ms[id] and
    launches[id] receive the summed device time and the launch count per
-   kernel identifier (nk >= 12). The state is advanced like cgl_step. */
+   kernel identifier (nk >= 32). The state is advanced like cgl_step. */
 cgl_status cgl_profile(cgl_state *state, int32_t nsteps, int32_t nk, double *ms, int64_t *launches);
 
 /* Number of kernels one cgl_step step launches with the current problem. */
 cgl_status cgl_launches_per_step(cgl_state *state, int64_t *kernels);
+
+/* Arithmetic peaks of the current device, measured with CUDA events: the
+   float64 and float32 fused multiply-add rates in FLOP/s (2 per FMA; eight
+   independent FMA chains per thread, 8 blocks of 256 threads per SM, best of
+   three timed launches after a warm-up).  They are the denominators of the
+   arithmetic roofs the benchmark reports beside the HBM roof; the paper has
+   no counterpart.  Allocates and frees a small device buffer; synchronises
+   the device's default stream.  CGL_ECUDA without a usable GPU. */
+cgl_status cgl_measure_peaks(double *fp64_flops, double *fp32_flops);
 
 #ifdef __cplusplus
 }

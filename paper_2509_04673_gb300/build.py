@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcgl.so")
-SOURCES = ["api.cu", "inst_adv.cu", "inst_burgers.cu", "inst_kpp.cu", "inst_euler.cu", "batch.cu", "noalloc.cu"]
+SOURCES = ["inst_euler_f32.cu", "inst_euler.cu", "inst_kpp_f32.cu", "inst_kpp.cu", "inst_burgers_f32.cu",
+           "inst_burgers.cu", "inst_adv_f32.cu", "inst_adv.cu", "batch.cu", "api.cu", "noalloc.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -112,6 +112,7 @@ _PROTOS = [
     ("cgl_batch_load_tuning", C.c_int, [C.c_void_p, C.c_char_p]),
     ("cgl_batch_debug", C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     ("cgl_gradient_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("cgl_measure_peaks", C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 ]
 
 
@@ -295,7 +296,7 @@ class State:
 
     def profile(self, nsteps):
         """Per-kernel device time (ms) and launch counts over nsteps steps."""
-        nk = 16
+        nk = 32
         ms = np.zeros(nk)
         ln = np.zeros(nk, dtype=np.int64)
         check(lib().cgl_profile(self.h, int(nsteps), nk, _dptr(ms),
@@ -391,3 +392,10 @@ def gradient_noalloc(mesh: Mesh, u_dev_ptr: int, g_dev_ptr: int, stream=None):
     allocation by the library (see cgl_gradient_noalloc in include/cgl.h)."""
     check(lib().cgl_gradient_noalloc(mesh.h, C.c_void_p(u_dev_ptr), C.c_void_p(g_dev_ptr),
                                      C.c_void_p(stream) if stream else None))
+
+
+def measure_peaks() -> dict:
+    """Measured float64 / float32 FMA rates of the current device (FLOP/s)."""
+    a, b = C.c_double(), C.c_double()
+    check(lib().cgl_measure_peaks(C.byref(a), C.byref(b)))
+    return {"fp64_flops": a.value, "fp32_flops": b.value}

@@ -376,7 +376,8 @@ static cgl_status ensure_tables(int dev) {
     for (int d : g_uploaded)
         if (d == dev) return CGL_OK;
     const HostTables& H = host_tables();
-    UploadFn fns[5] = {upload_adv, upload_burgers, upload_kpp, upload_euler, upload_batch};
+    UploadFn fns[9] = {upload_adv,   upload_burgers,   upload_kpp,   upload_euler,  upload_adv32,
+                       upload_burgers32, upload_kpp32, upload_euler32, upload_batch};
     for (UploadFn f : fns) CUDA_TRY(f(H.td, H.tf, H.a2d, H.a2f));
     g_uploaded.push_back(dev);
     return CGL_OK;
@@ -1026,9 +1027,11 @@ extern "C" cgl_status cgl_time_step(cgl_state* S, double* dt) {
 // ---------------------------------------------------------------------------
 // per-kernel timing
 // ---------------------------------------------------------------------------
+static_assert(KID_COUNT <= 32, "cgl_profile reports at most 32 kernel identifiers");
 static const char* const KNAMES[KID_COUNT] = {
     "k_avg", "k_pre", "k_dt", "k_grad_rhs", "k_gather_init", "k_grad_sweep", "k_mass_sweep",
-    "k_res_ev", "k_update_ev", "k_final", "k_t_advance", "k_udot_sweep", "k_facet", "k_res_w", "k_q1_facet", "k_udl"};
+    "k_res_ev", "k_update_ev", "k_final", "k_t_advance", "k_udot_sweep", "k_facet", "k_res_w", "k_q1_facet", "k_udl",
+    "k_sens"};
 
 // fixed-length delay (bounded both by a cycle count and by an iteration cap;
 // it waits on nothing) that keeps the stream busy while the host enqueues the
@@ -1046,7 +1049,7 @@ extern "C" const char* cgl_kernel_name(int32_t id) {
 extern "C" cgl_status cgl_profile(cgl_state* S, int32_t nsteps, int32_t nk, double* ms, int64_t* launches) {
     if (!S || !ms || !launches) return fail(CGL_EINVAL, "null argument");
     if (!S->has_problem) return fail(CGL_EINVAL, "cgl_set_problem first");
-    if (nk < KID_COUNT) return fail(CGL_EINVAL, "need room for %d kernels", (int)KID_COUNT);
+    if (nk < 32) return fail(CGL_EINVAL, "need room for 32 kernel identifiers");
     if (nsteps < 1 || nsteps > 1000) return fail(CGL_EINVAL, "nsteps in [1, 1000]");
     Prof P;
     P.cap = nsteps * (40 + 6 * (S->prob.k_g + S->prob.k_u));
@@ -1096,7 +1099,7 @@ extern "C" cgl_status cgl_launches_per_step(cgl_state* S, int64_t* kernels) {
     if (!S->has_problem) return fail(CGL_EINVAL, "cgl_set_problem first");
     const int lo = S->prob.mode == CGL_MODE_LO;
     int64_t per_stage = 1 + 2 + (lo ? 0 : 3 + (S->prob.k_g + S->prob.k_u));
-    if (S->prec == CGL_FP32_MIXED && S->nc > 1) per_stage += 1;  // k_avg
+    if (S->prec == CGL_FP32_MIXED && S->nc > 1) per_stage += 2;  // k_avg, k_sens
     if (S->prec == CGL_FP32_MIXED) per_stage += 1;                // k_facet
     if (S->prec == CGL_FP32_MIXED && !lo && split_residual(S->mesh->m)) per_stage += 1;  // k_res_w beside k_res_s
     if (S->prec == CGL_FP32_MIXED && !lo && fuse_sweeps(S->mesh->m) && !(S->prob.options & CGL_OPT_UNFUSED_SWEEPS)) {
@@ -1104,8 +1107,8 @@ extern "C" cgl_status cgl_launches_per_step(cgl_state* S, int64_t* kernels) {
         per_stage -= (S->prob.k_g >= 1) + (S->prob.k_u >= 1);
     }
     if ((S->prob.options & CGL_OPT_AEC_Q1) && !lo) {
-        // k_pre, k_q1_facet, k_udl, k_q1_update, k_final (+ k_avg for mixed systems)
-        per_stage = 5 + ((S->prec == CGL_FP32_MIXED && S->nc > 1) ? 1 : 0);
+        // k_pre, k_q1_facet, k_udl, k_q1_update, k_final (+ k_avg, k_sens for mixed systems)
+        per_stage = 5 + ((S->prec == CGL_FP32_MIXED && S->nc > 1) ? 2 : 0);
     }
     *kernels = 3 * per_stage + 1;  // + dt finalisation; the time advance rides in the last k_final
     return CGL_OK;

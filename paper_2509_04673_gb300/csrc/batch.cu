@@ -277,6 +277,7 @@ struct cgl_batch {
     int phantom;
     cudaGraphExec_t graph;
     bool use_graph;
+    cudaError_t graph_err;  // why the capture failed (cudaSuccess: not failed)
 };
 
 static cgl_status bfail(cgl_status st, const char* msg, cudaError_t e = cudaSuccess) {
@@ -326,12 +327,17 @@ static cudaError_t enqueue_batch_step(cgl_batch* B) {
     return e;
 }
 
+// Capture the three stage launches of a step into a graph once.  If the
+// capture fails the batch falls back to direct cooperative launches (same
+// results); cgl_batch_info reports graph = -1 then, and the CUDA error is
+// kept in graph_err.
 static cgl_status ensure_graph(cgl_batch* B) {
     if (B->graph || !B->use_graph) return CGL_OK;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(B->st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
         B->use_graph = false;
+        B->graph_err = e;
         cudaGetLastError();
         return CGL_OK;
     }
@@ -341,6 +347,7 @@ static cgl_status ensure_graph(cgl_batch* B) {
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();
         B->use_graph = false;  // cooperative launches not capturable here: launch directly
+        B->graph_err = e1 != cudaSuccess ? e1 : e2;
         return CGL_OK;
     }
     e = cudaGraphInstantiate(&B->graph, g, 0);
@@ -349,6 +356,7 @@ static cgl_status ensure_graph(cgl_batch* B) {
         cudaGetLastError();
         B->graph = nullptr;
         B->use_graph = false;
+        B->graph_err = e;
     }
     return CGL_OK;
 }
@@ -392,6 +400,7 @@ extern "C" cgl_status cgl_batch_create(cgl_state* const* states, int32_t n, cgl_
     B->phantom = 0;
     B->node_tile = ST_TX * ST_TY;
     B->use_graph = true;
+    B->graph_err = cudaSuccess;
     for (int p = 0; p <= PMAX; ++p) B->tile_elems[p] = BT;
     std::vector<InstDev> h(n);
     for (int i = 0; i < n; ++i) {
@@ -505,7 +514,9 @@ extern "C" cgl_status cgl_batch_info(cgl_batch* B, int32_t* grid, int32_t* block
     if (block) *block = BT;
     if (elem_tiles) *elem_tiles = B->net;
     if (node_tiles) *node_tiles = B->nnt;
-    if (graph) *graph = B->graph ? 1 : 0;
+    if (graph) *graph = B->graph ? 1 : (B->graph_err != cudaSuccess ? -1 : 0);
+    if (B->graph_err != cudaSuccess)
+        set_error(CGL_OK, "graph capture failed (direct launches): %s", cudaGetErrorString(B->graph_err));
     return CGL_OK;
 }
 

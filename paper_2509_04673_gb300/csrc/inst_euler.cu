@@ -1,13 +1,13 @@
-// Stage instantiations for the PhysEuler physics policy (all degrees, both precisions).
+// Stage instantiations for the PhysEuler physics policy: the FP64 form (all
+// degrees); the FP32-mixed form is compiled in inst_euler_f32.cu.
 #include "stage.cuh"
 
 namespace cgl {
-StageFn stage_fn_euler(int prec, int p) { return select_stage<PhysEuler>(prec, p); }
-}  // namespace cgl
+StageFn stage_fn_euler(int prec, int p) {
+    return prec == 0 ? select_stage_r<PhysEuler, double>(p) : stage_fn_euler32(p);
+}
 
-namespace cgl {
-cudaError_t upload_euler(const Tab<double>* td, const Tab<float>* tf, const double* a2d,
-                        const float* a2f) {
+cudaError_t upload_euler(const Tab<double>* td, const Tab<float>* tf, const double* a2d, const float* a2f) {
     return upload_tables_here(td, tf, a2d, a2f);
 }
 }  // namespace cgl

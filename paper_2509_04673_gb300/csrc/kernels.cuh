@@ -507,15 +507,17 @@ DEV R sensor_scalar(const ProbDev& pr, const R (&U)[Dim<P>::N2], const R (&V)[4]
     R sig0 = fmax(qform<R, P>(U0), R(0));
     R wt[5];
     wt[0] = (R(1) - R(ne) * wl) / ((r2 ? sig0 : pow(sig0, rh)) + eps);
+    // the continued candidates, each formed once and kept for both passes
+    R W[4][N2];
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
         wt[d + 1] = R(0);
         if (nb[d] >= 0) {
-            R Vc[N2], W[N2];
+            R Vc[N2];
 #pragma unroll
             for (int i = 0; i < N2; ++i) Vc[i] = V[d][i] - V[d][0];
-            continue_nb<R, P>(d, Vc, W);
-            R sg = fmax(qform<R, P>(W), R(0));
+            continue_nb<R, P>(d, Vc, W[d]);
+            R sg = fmax(qform<R, P>(W[d]), R(0));
             wt[d + 1] = wl / ((r2 ? sg : pow(sg, rh)) + eps);
         }
     }
@@ -526,13 +528,9 @@ DEV R sensor_scalar(const ProbDev& pr, const R (&U)[Dim<P>::N2], const R (&V)[4]
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
         if (nb[d] >= 0) {
-            R Vc[N2], W[N2];
-#pragma unroll
-            for (int i = 0; i < N2; ++i) Vc[i] = V[d][i] - V[d][0];
-            continue_nb<R, P>(d, Vc, W);
             R wd = wt[d + 1] / tot;
 #pragma unroll
-            for (int i = 0; i < N2; ++i) Dl[i] += wd * (U0[i] - W[i]);
+            for (int i = 0; i < N2; ++i) Dl[i] += wd * (U0[i] - W[d][i]);
         }
     }
     R num = sqrt(fmax(qform<R, P>(Dl), R(0)));
@@ -590,6 +588,22 @@ DEV void ff_sum4(float a, float b, float c, float d, float& hi, float& lo) {
     two_sum(s2, -d, s3, t3);
     hi = s3;
     lo = __fadd_rn(__fadd_rn(t1, t2), t3);
+}
+
+// sum of N floats as a float-float pair hi + lo: Knuth's TwoSum into a
+// running sum with the rounding errors collected separately (relative error
+// of hi + lo about N^2 2^-48 of the sum of magnitudes)
+template <int N>
+DEV void ff_sum(const float (&v)[N], float& hi, float& lo) {
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        float t, e;
+        two_sum(s, v[i], t, e);
+        c = __fadd_rn(c, e);
+        s = t;
+    }
+    two_sum(s, c, hi, lo);
 }
 
 // LLF flux value 0.5 (nL + nR) - 0.5 lambda jump, with a fixed evaluation order
@@ -749,8 +763,12 @@ __device__ __noinline__ CompVec<float, Ph::NC + 1> boundary_facet_lo(const MeshD
 }
 
 // SUB: pseudo time steps from the subcell bound of Lemma 1 (a separate
-// instantiation, so that the default kernels carry none of its code)
-template <int P, class Ph, bool SUB = false>
+// instantiation, so that the default kernels carry none of its code).
+// LO (systems): the low-order part only: the element's own float-float mean
+// comes from k_avg like its neighbours' (the same ff_mean of the same block,
+// hence the same bits), no coefficient block is loaded, and gamma_e, nu_e
+// are left to k_sens
+template <int P, class Ph, bool SUB = false, bool LO = false>
 DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __restrict__ u,
                         double* __restrict__ ue_out, double* __restrict__ dte_out,
                         double* __restrict__ ubl_out, double* __restrict__ gam_out,
@@ -758,16 +776,22 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
                         float* __restrict__ fl_out, float* __restrict__ EV, float* __restrict__ cf_out,
                         float* __restrict__ avg, int ex, int ey, int e) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
+    static_assert(!LO || NC > 1, "the low-order-only form reads the means of k_avg (systems)");
     int nb[4];
 #pragma unroll
     for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
-    float U[NC][N2];
-    load_block<float, P, NC>(u, m, ex, ey, U);
+    float U[LO ? 1 : NC][LO ? 1 : N2];
+    if constexpr (!LO) load_block<float, P, NC>(u, m, ex, ey, U);
     float uh[NC], ul[NC], fxs[NC], fys[NC];
     double ued[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        ff_mean<N2>(U[c], uh[c], ul[c]);
+        if constexpr (LO) {
+            uh[c] = avg[(2 * c) * m.E + e];
+            ul[c] = avg[(2 * c + 1) * m.E + e];
+        } else {
+            ff_mean<N2>(U[c], uh[c], ul[c]);
+        }
         ued[c] = (double)uh[c] + (double)ul[c];
         ue_out[c * m.E + e] = ued[c];
     }
@@ -895,6 +919,9 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
         }
     }
     cf_out[e] = sf;  // the float speed sum (dt_e in float for k_update_ev)
+    if constexpr (LO) {
+        return dte;
+    } else {
     float gam;
     if (pr.mode == MODE_WENO || pr.mode == MODE_WENO_L) {
         if constexpr (keepV) {
@@ -920,6 +947,7 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
     nu_out[e] = (double)(lm * (m.h_f * (0.5f / P)));
     if (EV) grad_vectors<float, P, NC>(U, m.h_f, m.E, e, EV);
     return dte;
+    }
 }
 
 template <class R, int P, class Ph, bool SUB = false>
@@ -1056,6 +1084,104 @@ __global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __
         dte = pre_at<R, P, Ph, SUB>(m, pr, u, ue_out, dte_out, ubl_out, gam_out, nu_out, q_out, fl_out, EV, cf_out,
                                     avg, ex, ey, e);
     if (dtbits) block_min_to(dte, dtbits);
+}
+
+// FP32-mixed systems: the low-order part of k_pre (cell states from k_avg,
+// facet speeds and f^L, dt_e, ubar^{e,L}, the float copies for the facet
+// limiter's certificate); gamma_e and nu_e come from k_sens
+template <int P, class Ph, bool SUB = false>
+__global__ void k_pre_lo(MeshDev m, ProbDev pr, const float* __restrict__ u, double* __restrict__ ue_out,
+                         double* __restrict__ dte_out, double* __restrict__ ubl_out,
+                         float* __restrict__ fl_out, float* __restrict__ cf_out, float* __restrict__ avg,
+                         unsigned long long* __restrict__ dtbits) {
+    pdl_wait_then_trigger();
+    int ex, ey, e;
+    double dte = __longlong_as_double(0x7ff0000000000000LL);
+    if (elem_of_thread(m, ex, ey, e))
+        dte = pre_at_mixed<P, Ph, SUB, true>(m, pr, u, ue_out, dte_out, ubl_out, nullptr, nullptr, nullptr, fl_out,
+                                             nullptr, cf_out, avg, ex, ey, e);
+    if (dtbits) block_min_to(dte, dtbits);
+}
+
+// FP32-mixed systems: the WENO sensor gamma_e (eqs. (WENO:alpha),
+// (WENO:norm)) and nu_e (eq. (stab:WENO)) with one thread per element and
+// component.  A block holds K_SENS_TX consecutive elements of one row, one
+// warp per component (threadIdx.y = c): each thread evaluates the scalar
+// sensor of its component (the arithmetic of sensor() for that component),
+// the block takes gamma_e = min over the components and the node speeds of
+// nu_e from the element blocks it stages in shared memory.
+constexpr int K_SENS_TX = 32;
+template <int P, class Ph>
+__global__ void __launch_bounds__(K_SENS_TX * Ph::NC) k_sens(MeshDev m, ProbDev pr, const float* __restrict__ u,
+                                                             double* __restrict__ gam_out,
+                                                             double* __restrict__ nu_out) {
+    constexpr int NC = Ph::NC, N2 = Dim<P>::N2, TX = K_SENS_TX;
+    __shared__ float sU[NC][N2][TX];
+    __shared__ float sG[NC][TX], sL[NC][TX];
+    pdl_wait_then_trigger();
+    const int tx = threadIdx.x, c = threadIdx.y;
+    const int ex = blockIdx.x * TX + tx, ey = blockIdx.y;
+    const bool valid = ex < m.nx;
+    float gam = 1.f;
+    if (valid) {
+        int nb[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
+        const float* uc = u + c * m.NN;
+        float U[1][N2];
+        load_comp<float, P, Ph>(u, m, ex, ey, c, U[0]);
+#pragma unroll
+        for (int i = 0; i < N2; ++i) sU[c][i][tx] = U[0][i];
+        if (pr.mode == MODE_WENO || pr.mode == MODE_WENO_L) {
+            if constexpr (P <= 2) {
+                float V[4][N2];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    if (nb[d] >= 0) {
+                        int jx, jy;
+                        neighbour_xy(m, ex, ey, d, jx, jy);
+                        load_comp<float, P, Ph>(u, m, jx, jy, c, V[d]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < N2; ++i) V[d][i] = 0.f;
+                    }
+                }
+                gam = sensor_scalar<float, P>(pr, U[0], V, nb);
+            } else {
+                // one component as a scalar field (neighbour blocks reloaded,
+                // fewer live registers at p >= 3)
+                gam = sensor<float, P, PhysAdv>(m, pr, uc, U, nb, ex, ey);
+            }
+        } else {
+            gam = (pr.mode == MODE_HO) ? 1.f : 0.f;
+        }
+    }
+    sG[c][tx] = gam;
+    __syncthreads();
+    float lm = 0.f;
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < N2; ++i) {
+            if (i % NC != c) continue;
+            float ui[NC];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) ui[k] = sU[k][i][tx];
+            lm = fmaxf(lm, Ph::template node_speed<float>(ui, pr));
+        }
+    }
+    sL[c][tx] = lm;
+    __syncthreads();
+    if (c == 0 && valid) {
+        float g = 1.f, l = 0.f;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            g = fminf(g, sG[k][tx]);
+            l = fmaxf(l, sL[k][tx]);
+        }
+        const int e = ey * m.nx + ex;
+        gam_out[e] = (double)g;
+        nu_out[e] = (double)(l * (m.h_f * (0.5f / P)));
+    }
 }
 
 // global dt from the block minima folded into the bit pattern by k_pre
@@ -1934,6 +2060,9 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
                     const R* __restrict__ qcap, const R* __restrict__ fl_in, const float* __restrict__ cf, int e,
                     double (&ubec)[Ph::NC], R (&fh)[Ph::NC]) {
     constexpr int NC = Ph::NC, N1 = P + 1;
+    // FP32-mixed systems: the limited facet fluxes enter ubar^e as float-float
+    // terms (below), so f^H stays in float and no float64 copy is formed
+    constexpr bool mixed_sys = sizeof(R) == 4 && NC > 1;
     const double h = m.h;
     // canonical high-order facet fluxes f^H (eq. (hoflux)): face average of
     // f(u_j).n (or of F(u_j, u_hat; n) on a FIXED boundary), summed along the
@@ -1978,7 +2107,7 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
             for (int c = 0; c < NC; ++c) {
                 const R a = acc[c] / R(N1);
                 FHr[d][c] = fixed_b ? sg * a : a;
-                FH[d][c] = (double)FHr[d][c];
+                if constexpr (!mixed_sys) FH[d][c] = (double)FHr[d][c];
             }
         }
     }
@@ -1989,7 +2118,14 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
     } else if (pr.fl == FL_NONE) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            double os = ((FH[1][c] - FH[0][c]) + FH[3][c]) - FH[2][c];
+            double os;
+            if constexpr (mixed_sys) {
+                float osh, osl;
+                ff_sum4(FHr[1][c], FHr[0][c], FHr[3][c], FHr[2][c], osh, osl);
+                os = (double)osh + (double)osl;
+            } else {
+                os = ((FH[1][c] - FH[0][c]) + FH[3][c]) - FH[2][c];
+            }
             ubec[c] = uec[c] - rs * os;
         }
     } else {
@@ -2000,6 +2136,11 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
             for (int c = 0; c < NC; ++c) FLr[d][c] = fl_in[((long long)e * 4 + d) * NC + c];
         double FB[4][NC];
         R FBr[4];  // scalar limited fluxes in the bulk precision
+        // mixed systems: facet d enters as the float pair (TH, TL) per
+        // component: (f^L, -f^H) where alpha = 1 (certified in float, or
+        // computed as 1 in float64: the same terms either way, so the
+        // certificate changes no bit), else alpha f^A split into two floats
+        float TH[mixed_sys ? 4 : 1][mixed_sys ? NC : 1], TL[mixed_sys ? 4 : 1][mixed_sys ? NC : 1];
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
             const bool self_is_L = (d == 1 || d == 3);
@@ -2024,7 +2165,7 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
             } else {
                 double fA[NC];
 #pragma unroll
-                for (int c = 0; c < NC; ++c) fA[c] = (double)FLr[d][c] - FH[d][c];
+                for (int c = 0; c < NC; ++c) fA[c] = (double)FLr[d][c] - (double)FHr[d][c];
                 if constexpr (sizeof(R) == 4) {
                     // float32 certificate first: where both cells certainly
                     // give alpha = 1 the float64 formula is skipped (same result)
@@ -2048,7 +2189,10 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
                         }
                         if (one) {
 #pragma unroll
-                            for (int c = 0; c < NC; ++c) FB[d][c] = fA[c];
+                            for (int c = 0; c < NC; ++c) {
+                                TH[d][c] = FLr[d][c];
+                                TL[d][c] = -FHr[d][c];
+                            }
                             continue;
                         }
                     }
@@ -2071,8 +2215,22 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
                     double mR = (0.25 * h) * dte_a[2 * m.E + Rc];
                     alpha = fmin(alpha, euler_alpha<double>(ub, fm, mR, pr.pos_eps));
                 }
+                if constexpr (mixed_sys) {
 #pragma unroll
-                for (int c = 0; c < NC; ++c) FB[d][c] = alpha * fA[c];
+                    for (int c = 0; c < NC; ++c) {
+                        if (alpha == 1.0) {
+                            TH[d][c] = FLr[d][c];
+                            TL[d][c] = -FHr[d][c];
+                        } else {
+                            const double v = alpha * fA[c];
+                            TH[d][c] = __double2float_rn(v);
+                            TL[d][c] = __double2float_rn(v - (double)TH[d][c]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) FB[d][c] = alpha * fA[c];
+                }
             }
         }
 #pragma unroll
@@ -2082,6 +2240,14 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
                 // float limited fluxes summed as a float-float pair, widened once
                 float osh, osl;
                 ff_sum4(FBr[1], FBr[0], FBr[3], FBr[2], osh, osl);
+                os = (double)osh + (double)osl;
+            } else if constexpr (mixed_sys) {
+                // (fbar_E - fbar_W) + fbar_N - fbar_S from the eight float terms,
+                // compensated, widened once
+                const float t[8] = {TH[1][c], TL[1][c], -TH[0][c], -TL[0][c],
+                                    TH[3][c], TL[3][c], -TH[2][c], -TL[2][c]};
+                float osh, osl;
+                ff_sum<8>(t, osh, osl);
                 os = (double)osh + (double)osl;
             } else {
                 os = ((FB[1][c] - FB[0][c]) + FB[3][c]) - FB[2][c];
@@ -2551,6 +2717,29 @@ __global__ void __launch_bounds__(128) k_res_s(MeshDev m, const float* __restric
 // invariant-domain check and clamp (scalar IDP modes, bounds rounded inward
 // to the storage precision) or the positivity count (Euler), non-finite count.
 // ---------------------------------------------------------------------------
+// Float certificate of the positivity check of a stored state (rho, m, E):
+// true only when rho > 0 and rho E - |m|^2/2 > 0 hold for these values
+// exactly, so p = (gamma - 1)(E - |m|^2 / (2 rho)) > 0 as well (and the
+// float64 check agrees).  The float evaluation t = fma(rho, E, -kin), kin =
+// 0.5 fma(mx, mx, my^2), differs from the exact value by at most about
+// 3.1 2^-24 A, A = |rho E| + kin, so t > 2^-21 A certifies it; A is kept in
+// [2^-100, 2^100] (no underflow or overflow in the products).  Otherwise
+// (near-vacuum or near-zero pressure states, NaN) the float64 check decides.
+// Float64 states never take this path.
+template <class R>
+DEV bool euler_positive_certified(const R* u) {
+    if constexpr (sizeof(R) == 4) {
+        const float rho = u[0], mx = u[1], my = u[2], E = u[3];
+        if (!(rho > 0.f)) return false;
+        const float kin = __fmul_rn(0.5f, __fmaf_rn(mx, mx, __fmul_rn(my, my)));
+        const float t = __fmaf_rn(rho, E, -kin);
+        const float A = __fadd_rn(fabsf(__fmul_rn(rho, E)), kin);
+        return t > 0x1p-21f * A && A > 0x1p-100f && A < 0x1p100f;
+    } else {
+        return false;
+    }
+}
+
 template <class R, int P, int NC>
 DEV void final_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ EW,
                         R* __restrict__ un, R* __restrict__ u, R a, R b,
@@ -2586,11 +2775,13 @@ DEV void final_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ EW,
             }
         }
     } else {
-        double dd[NC];
+        if (!euler_positive_certified(out)) {
+            double dd[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) dd[c] = (double)out[c];
-        double pres = PhysEuler::pressure<double>(dd, pr.gam);
-        if (!(dd[0] > 0.0) || !(pres > 0.0)) atomicAdd(&cnt[CNT_VIOL], 1ull);
+            for (int c = 0; c < NC; ++c) dd[c] = (double)out[c];
+            double pres = PhysEuler::pressure<double>(dd, pr.gam);
+            if (!(dd[0] > 0.0) || !(pres > 0.0)) atomicAdd(&cnt[CNT_VIOL], 1ull);
+        }
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) u[c * m.NN + node] = out[c];

@@ -35,7 +35,7 @@ struct Bufs {
 // kernel identifiers for per-kernel timing
 enum KernelId {
     KID_AVG = 0, KID_PRE, KID_DT, KID_GRAD, KID_GATHER, KID_GRADF, KID_SWEEP, KID_RES,
-    KID_UPDATE, KID_FINAL, KID_TADV, KID_UDOTF, KID_FACET, KID_RESW, KID_Q1F, KID_UDL, KID_COUNT
+    KID_UPDATE, KID_FINAL, KID_TADV, KID_UDOTF, KID_FACET, KID_RESW, KID_Q1F, KID_UDL, KID_SENS, KID_COUNT
 };
 
 // optional per-launch timing: CUDA events recorded around every launch on
@@ -140,16 +140,43 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
     constexpr bool use_avg = sizeof(R) == 4 && NC > 1;
     if constexpr (use_avg)
         CGL_LAUNCH(prof, KID_AVG, st, chk(launch(pdl, k_avg<P, NC>, ge, be, st, m, (const float*)u, B.avg)));
-    auto* kpre = (pr.opts & OPT_SUBCELL_DT) ? k_pre<R, P, Ph, true> : k_pre<R, P, Ph, false>;
-    CGL_LAUNCH(prof, KID_PRE, st,
-               chk(launch(pdl, kpre, ge, be, st, m, pr, (const R*)u, B.ue, B.dte, B.ubl, B.gam, B.nu,
-                          (R*)B.q, (R*)B.fl, (R*)nullptr, B.cf, B.avg,
-                          first ? B.dtbits : nullptr)));
+    if constexpr (use_avg) {
+        // mixed systems: the low-order part here, the sensor in k_sens below
+        auto* kpre = (pr.opts & OPT_SUBCELL_DT) ? k_pre_lo<P, Ph, true> : k_pre_lo<P, Ph, false>;
+        CGL_LAUNCH(prof, KID_PRE, st,
+                   chk(launch(pdl, kpre, ge, be, st, m, pr, (const float*)u, B.ue, B.dte, B.ubl, (float*)B.fl, B.cf,
+                              B.avg, first ? B.dtbits : nullptr)));
+    } else {
+        auto* kpre = (pr.opts & OPT_SUBCELL_DT) ? k_pre<R, P, Ph, true> : k_pre<R, P, Ph, false>;
+        CGL_LAUNCH(prof, KID_PRE, st,
+                   chk(launch(pdl, kpre, ge, be, st, m, pr, (const R*)u, B.ue, B.dte, B.ubl, B.gam, B.nu,
+                              (R*)B.q, (R*)B.fl, (R*)nullptr, B.cf, B.avg,
+                              first ? B.dtbits : nullptr)));
+    }
     if (first)
         CGL_LAUNCH(prof, KID_DT, st,
                    chk(launch(pdl, k_dt_final, dim3(1), dim3(1), st, B.dtbits, pr.cfl, (const double*)B.t,
                               (const double*)B.t_end, B.dt)));
     if (dt_only) return err != cudaSuccess ? err : cudaGetLastError();
+    // FP32-mixed: the facet part of the update on the second stream, beside
+    // the g_h and udot kernels (and beside k_sens for systems)
+    constexpr bool split_update = sizeof(R) == 4;
+    if constexpr (split_update) {
+        if (!q1) {
+            chk(cudaEventRecord(B.ev_fork, st));
+            chk(cudaStreamWaitEvent(B.st2, B.ev_fork, 0));
+            CGL_LAUNCH(prof, KID_FACET, B.st2,
+                       chk(launch(false, k_facet<P, Ph>, ge, be, B.st2, m, pr, (const float*)u, (const double*)B.ue,
+                                  (const double*)B.dte, (const double*)B.ubl, (const float*)B.q,
+                                  (const float*)B.fl, (const float*)B.cf, B.ube, B.fht)));
+            chk(cudaEventRecord(B.ev_join, B.st2));
+        }
+    }
+    if constexpr (use_avg) {
+        const dim3 bs(K_SENS_TX, NC), gs(nblk(m.nx, K_SENS_TX), m.ny);
+        CGL_LAUNCH(prof, KID_SENS, st,
+                   chk(launch(pdl, k_sens<P, Ph>, gs, bs, st, m, pr, (const float*)u, B.gam, B.nu)));
+    }
     if (q1) {
         CGL_LAUNCH(prof, KID_Q1F, st,
                    chk(launch(pdl, k_q1_facet<R, P, Ph>, ge, be, st, m, pr, (const R*)u, (const double*)B.ue,
@@ -167,18 +194,6 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
                    chk(launch(pdl, k_final<R, P, NC>, gn, bn, st, m, pr, (const R*)B.EW, (R*)B.un, u, R(a), R(b),
                               B.cnt, pr.last_stage ? B.t : (double*)nullptr, (const double*)B.dt)));
         return err != cudaSuccess ? err : cudaGetLastError();
-    }
-    // FP32-mixed: the facet part of the update on the second stream, beside
-    // the g_h and udot kernels
-    constexpr bool split_update = sizeof(R) == 4;
-    if constexpr (split_update) {
-        chk(cudaEventRecord(B.ev_fork, st));
-        chk(cudaStreamWaitEvent(B.st2, B.ev_fork, 0));
-        CGL_LAUNCH(prof, KID_FACET, B.st2,
-                   chk(launch(false, k_facet<P, Ph>, ge, be, B.st2, m, pr, (const float*)u, (const double*)B.ue,
-                              (const double*)B.dte, (const double*)B.ubl, (const float*)B.q, (const float*)B.fl,
-                              (const float*)B.cf, B.ube, B.fht)));
-        chk(cudaEventRecord(B.ev_join, B.st2));
     }
     R* ud = (R*)B.ud;
     if (pr.mode != MODE_LO) {
@@ -266,22 +281,16 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
     return err != cudaSuccess ? err : cudaGetLastError();
 }
 
-template <class Ph>
-StageFn select_stage(int prec, int p) {
-    if (prec == 0) {
-        switch (p) {
-            case 1: return run_stage<double, 1, Ph>;
-            case 2: return run_stage<double, 2, Ph>;
-            case 3: return run_stage<double, 3, Ph>;
-            case 4: return run_stage<double, 4, Ph>;
-        }
-    } else {
-        switch (p) {
-            case 1: return run_stage<float, 1, Ph>;
-            case 2: return run_stage<float, 2, Ph>;
-            case 3: return run_stage<float, 3, Ph>;
-            case 4: return run_stage<float, 4, Ph>;
-        }
+// stage of one precision R (float64: the FP64 form; float: FP32-mixed) for
+// degrees 1..4; each physics compiles its two precisions in separate
+// translation units (inst_*.cu, inst_*_f32.cu), built in parallel
+template <class Ph, class R>
+StageFn select_stage_r(int p) {
+    switch (p) {
+        case 1: return run_stage<R, 1, Ph>;
+        case 2: return run_stage<R, 2, Ph>;
+        case 3: return run_stage<R, 3, Ph>;
+        case 4: return run_stage<R, 4, Ph>;
     }
     return nullptr;
 }
@@ -302,10 +311,18 @@ StageFn stage_fn_adv(int prec, int p);
 StageFn stage_fn_burgers(int prec, int p);
 StageFn stage_fn_kpp(int prec, int p);
 StageFn stage_fn_euler(int prec, int p);
+StageFn stage_fn_adv32(int p);
+StageFn stage_fn_burgers32(int p);
+StageFn stage_fn_kpp32(int p);
+StageFn stage_fn_euler32(int p);
 cudaError_t upload_adv(const Tab<double>*, const Tab<float>*, const double*, const float*);
 cudaError_t upload_burgers(const Tab<double>*, const Tab<float>*, const double*, const float*);
 cudaError_t upload_kpp(const Tab<double>*, const Tab<float>*, const double*, const float*);
 cudaError_t upload_euler(const Tab<double>*, const Tab<float>*, const double*, const float*);
+cudaError_t upload_adv32(const Tab<double>*, const Tab<float>*, const double*, const float*);
+cudaError_t upload_burgers32(const Tab<double>*, const Tab<float>*, const double*, const float*);
+cudaError_t upload_kpp32(const Tab<double>*, const Tab<float>*, const double*, const float*);
+cudaError_t upload_euler32(const Tab<double>*, const Tab<float>*, const double*, const float*);
 cudaError_t upload_batch(const Tab<double>*, const Tab<float>*, const double*, const float*);
 
 }  // namespace cgl

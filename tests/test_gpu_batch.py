@@ -77,6 +77,8 @@ def test_batch_bitwise_equals_single(cgl):
         assert np.array_equal(s.get_state(), r)
     info = b.info()
     assert info["grid"] > 0 and info["block"] == 128
+    # the steps ran as one captured CUDA graph per step
+    assert info["graph"] == 1, cgl.lib().cgl_last_error()
 
 
 def test_batch_times_are_per_instance(cgl):
