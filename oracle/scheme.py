@@ -43,6 +43,7 @@ from .tables import tables
 BC_PERIODIC, BC_OUTFLOW, BC_FIXED, BC_WALL = 0, 1, 2, 3
 OPT_SUBCELL_DT = 4
 OPT_AEC_Q1 = 8
+OPT_DTE_REDUCE = 16
 SIDES = ("W", "E", "S", "N")
 # SSP-RK3 stage times t + c dt of the Shu-Osher stages
 SSP3_C = (0.0, 1.0, 0.5)
@@ -689,6 +690,37 @@ def slope_limit(om: OracleMesh, fie, ube, prob):
     return euler_alpha(ub, fie, m, prob).min(axis=1)
 
 
+def in_domain(prob, ub):
+    """Per element: is the average ub (nc, E) in G?  Scalars: umin <= ub <=
+    umax; Euler: rho > 0 and rho E - |m|^2/2 > 0 (p > 0)."""
+    if prob["flux"] == ph.EULER:
+        return (ub[0] > 0.0) & (ub[0] * ub[3] - 0.5 * (ub[1] ** 2 + ub[2] ** 2) > 0.0)
+    return (ub[0] >= prob["umin"]) & (ub[0] <= prob["umax"])
+
+
+def reduced_time_steps(prob, ue, osum, rs):
+    """The strategy of the remark after eq. (dtmaxcell) for the unlimited
+    averages of eq. (uebar), ubar^e(r) = u^e - r S_e with r = dt_e / h and
+    S_e the outward sum of the facet fluxes f^H: where ubar^e(rs) leaves G,
+    the largest r in [0, rs] with ubar^e(r) in G (returned as r).  Scalars:
+    the bound that is crossed, solved exactly (u^e itself lies in G).  Euler
+    (reading): the largest r allowed by the positivity criterion of
+    Appendix A for the state u^e moved by r S_e: rho >= eps rho^e and the
+    linear minorant of rho E - |m|^2/2 at least eps times its value at u^e,
+    i.e. r = rs alpha(u^e, -rs S_e, m = 1)."""
+    keep = in_domain(prob, ue - rs * osum)
+    if prob["flux"] == ph.EULER:
+        alpha = euler_alpha(ue, -rs[None, :] * osum, np.ones_like(rs), prob)
+        return np.where(keep, rs, rs * alpha)
+    umin, umax = prob["umin"], prob["umax"]
+    d = osum[0]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r_hi = np.where(d < 0.0, (umax - ue[0]) / np.where(d < 0.0, -d, 1.0), np.inf)
+        r_lo = np.where(d > 0.0, (ue[0] - umin) / np.where(d > 0.0, d, 1.0), np.inf)
+    r = np.maximum(np.minimum(rs, np.minimum(r_hi, r_lo)), 0.0)
+    return np.where(keep, rs, r)
+
+
 def fe_stage(mesh, prob, u, dt, t=0.0):
     """One forward-Euler stage u -> u^SSP, eq. (eq:SSPupdate), with all
     intermediates.  u has shape (nc, nny, nnx); t is the stage time, which
@@ -706,7 +738,7 @@ def fe_stage(mesh, prob, u, dt, t=0.0):
         dte = subcell_time_steps(om, U, prob)
     FLx, FLy = lo["x"][0], lo["y"][0]
     ubL = ue - (dte / om.h) * outward_sum(om, FLx, FLy)          # eq. (uelowFCT)
-    info = dict(ue=ue, dte=dte, ubL=ubL)
+    info = dict(ue=ue, dte=dte, ubL=ubL, ubar_outside=0, dte_reduced=0)
     need_ho = mode != MODE_LO or fl != FL_LOW
     if need_ho:
         FHx, FHy = high_order_facets(om, u, prob, t)
@@ -714,7 +746,17 @@ def fe_stage(mesh, prob, u, dt, t=0.0):
     if fl == FL_LOW:
         ube = ubL.copy()
     elif fl == FL_NONE:
-        ube = ue - (dte / om.h) * outward_sum(om, FHx, FHy)       # eq. (uebar)
+        osum = outward_sum(om, FHx, FHy)
+        rs = dte / om.h
+        ube = ue - rs * osum                                      # eq. (uebar)
+        info["ubar_outside"] = int(np.count_nonzero(~in_domain(prob, ube)))
+        if int(prob.get("options", 0)) & OPT_DTE_REDUCE:
+            # remark after eq. (dtmaxcell): decrease dt_e where ubar^e left G
+            rs2 = reduced_time_steps(prob, ue, osum, rs)
+            info["dte_reduced"] = int(np.count_nonzero(rs2 < rs))
+            dte = rs2 * om.h
+            ube = ue - rs2 * osum
+            info["dte"] = dte
     else:
         fAx = FLx - FHx
         fAy = FLy - FHy
