@@ -130,6 +130,19 @@ typedef struct cgl_mesh_desc {
  * section is not included.  Batched states (cgl_batch_create) reject this option
  * and CGL_OPT_SUBCELL_DT. */
 #define CGL_OPT_AEC_Q1 8
+/* cgl_problem.options.  CGL_OPT_DTE_REDUCE: the strategy of the remark after
+ * eq. (dtmaxcell) for the unlimited averages of eq. (uebar): where the
+ * macrocell dt_e gives ubar^e = u^e - (dt_e/|K_e|) sum |S| f^H outside G,
+ * dt_e is decreased to the largest value that brings ubar^e back into G
+ * (scalars: the crossed bound solved exactly; Euler: the Appendix-A
+ * positivity criterion, margin pos_eps, for u^e moved along the step), and
+ * that dt_e enters the element contributions and the SSP weights of the
+ * element.  The global dt is not changed: theta = dt/dt_e > 1 is counted in
+ * cfl_violations.  Requires flux_limiter = CGL_FL_NONE and neither
+ * CGL_OPT_SUBCELL_DT nor CGL_OPT_AEC_Q1 (CGL_EINVAL otherwise); batched
+ * states reject it.  Whether or not it is set, cgl_step_info.ubar_outside
+ * counts the elements whose unlimited ubar^e left G. */
+#define CGL_OPT_DTE_REDUCE 16
 
 typedef struct cgl_problem {
     int32_t flux;          /* CGL_FLUX_* */
@@ -162,6 +175,8 @@ typedef struct cgl_step_info {
     double mass[4];        /* sum_i m_i u_i per component after the call (float64) */
     double umin[4];        /* range of the coefficients after the call */
     double umax[4];
+    int64_t ubar_outside;  /* flux limiter off: elements whose ubar^e of eq. (uebar) left G, summed over stages */
+    int64_t dte_reduced;   /* CGL_OPT_DTE_REDUCE: elements whose dt_e was decreased, summed over stages */
 } cgl_step_info;
 
 /* --- library ------------------------------------------------------------ */
@@ -310,9 +325,10 @@ cgl_status cgl_get_field(cgl_state *state, int32_t field, double *host, size_t n
 /* --- batches ------------------------------------------------------------------ */
 
 /* Many independent scalar instances (uneven sizes, degrees 1..4, own time
-   steps) advanced together: one persistent cooperative launch per SSP-RK
-   stage over all instances, the three launches of a step captured in a CUDA
-   graph. Every state must be FP32_MIXED, scalar (advection, Burgers, KPP),
+   steps) advanced together: per SSP-RK stage one persistent cooperative
+   launch for each degree present, over all instances of that degree (a
+   kernel compiled for the degree, with its own register budget), all
+   launches of a step captured in one CUDA graph. Every state must be FP32_MIXED, scalar (advection, Burgers, KPP),
    on one device, with the same mode, k_g and k_u; the batch uses the first
    state's stream and references (does not copy) the states, which must
    outlive it. A batched instance evolves bitwise like the same state stepped
@@ -331,7 +347,8 @@ cgl_status cgl_batch_step(cgl_batch *batch, int32_t nsteps, int64_t *violations)
 /* Enqueue nsteps steps without waiting. */
 cgl_status cgl_batch_step_async(cgl_batch *batch, int32_t nsteps);
 
-/* Launch geometry: persistent grid size, block size, tile counts, and how
+/* Launch geometry: the largest persistent grid of the per-degree kernels,
+   block size, tile counts (summed over the degrees), and how
    a step runs: 1 = a captured CUDA graph, 0 = no step has run yet (the
    graph is captured at the first step), -1 = the capture failed and steps
    run as direct cooperative launches (same results; cgl_last_error() then

@@ -27,6 +27,7 @@ OPT_FP64_LIMITER = 1
 OPT_UNFUSED_SWEEPS = 2
 OPT_SUBCELL_DT = 4
 OPT_AEC_Q1 = 8
+OPT_DTE_REDUCE = 16
 FIELD_UE, FIELD_DTE, FIELD_UBL, FIELD_UBE, FIELD_GAMMA, FIELD_NU, FIELD_BETA = 0, 1, 2, 3, 4, 5, 6
 FIELD_GX, FIELD_GY, FIELD_R, FIELD_UDOT = 16, 17, 18, 19
 
@@ -55,12 +56,14 @@ class cgl_boundary(C.Structure):
 class cgl_step_info(C.Structure):
     _fields_ = [("t", C.c_double), ("dt_last", C.c_double), ("steps", C.c_int64),
                 ("violations", C.c_int64), ("clamps", C.c_int64), ("cfl_violations", C.c_int64),
-                ("mass", C.c_double * 4), ("umin", C.c_double * 4), ("umax", C.c_double * 4)]
+                ("mass", C.c_double * 4), ("umin", C.c_double * 4), ("umax", C.c_double * 4),
+                ("ubar_outside", C.c_int64), ("dte_reduced", C.c_int64)]
 
     def as_dict(self, nc=4):
         return dict(t=self.t, dt_last=self.dt_last, steps=self.steps, violations=self.violations,
                     clamps=self.clamps, cfl_violations=self.cfl_violations,
-                    mass=list(self.mass)[:nc], umin=list(self.umin)[:nc], umax=list(self.umax)[:nc])
+                    mass=list(self.mass)[:nc], umin=list(self.umin)[:nc], umax=list(self.umax)[:nc],
+                    ubar_outside=self.ubar_outside, dte_reduced=self.dte_reduced)
 
 
 class CglError(RuntimeError):

@@ -643,10 +643,17 @@ extern "C" cgl_status cgl_set_problem(cgl_state* S, const cgl_problem* p) {
     if (p->mode < CGL_MODE_LO || p->mode > CGL_MODE_WENO_L) return fail(CGL_EINVAL, "unknown mode");
     if (p->flux_limiter < CGL_FL_NONE || p->flux_limiter > CGL_FL_LOW) return fail(CGL_EINVAL, "unknown flux_limiter");
     if (p->k_g < 0 || p->k_u < 0 || p->k_g > 64 || p->k_u > 64) return fail(CGL_EINVAL, "k_g, k_u in [0, 64]");
-    if (p->options & ~(CGL_OPT_FP64_LIMITER | CGL_OPT_UNFUSED_SWEEPS | CGL_OPT_SUBCELL_DT | CGL_OPT_AEC_Q1))
+    if (p->options &
+        ~(CGL_OPT_FP64_LIMITER | CGL_OPT_UNFUSED_SWEEPS | CGL_OPT_SUBCELL_DT | CGL_OPT_AEC_Q1 | CGL_OPT_DTE_REDUCE))
         return fail(CGL_EINVAL, "unknown option bits");
     if ((p->options & CGL_OPT_SUBCELL_DT) && p->flux_limiter != CGL_FL_NONE)
         return fail(CGL_EINVAL, "CGL_OPT_SUBCELL_DT needs flux_limiter = CGL_FL_NONE");
+    if (p->options & CGL_OPT_DTE_REDUCE) {
+        if (p->flux_limiter != CGL_FL_NONE)
+            return fail(CGL_EINVAL, "CGL_OPT_DTE_REDUCE needs flux_limiter = CGL_FL_NONE");
+        if (p->options & (CGL_OPT_SUBCELL_DT | CGL_OPT_AEC_Q1))
+            return fail(CGL_EINVAL, "CGL_OPT_DTE_REDUCE does not combine with CGL_OPT_SUBCELL_DT or CGL_OPT_AEC_Q1");
+    }
     if (!(p->cfl > 0.0) || !(p->cfl <= 1.0)) return fail(CGL_EINVAL, "cfl must be in (0, 1]");
     if (!(p->q >= 1.0) || !(p->r >= 1.0)) return fail(CGL_EINVAL, "q, r must be >= 1");
     if (!(p->weno_eps > 0.0) || !(p->gamma_eps >= 0.0) || !(p->lambda_floor > 0.0))
@@ -916,6 +923,8 @@ static cgl_status read_info(cgl_state* S, cgl_step_info* info, long long steps, 
         info->violations = (int64_t)d[CNT_VIOL];
         info->clamps = (int64_t)d[CNT_CLAMP];
         info->cfl_violations = (int64_t)d[CNT_CFL];
+        info->ubar_outside = (int64_t)d[CNT_UBAR];
+        info->dte_reduced = (int64_t)d[CNT_DTE_RED];
         for (int c = 0; c < S->nc; ++c) {
             double ms = 0.0, mn = INFINITY, mx = -INFINITY;
             for (int b = 0; b < NB; ++b) {

@@ -77,7 +77,7 @@ struct ProbDev {
     int last_stage;        // the stage ends a step: its k_final advances t
 };
 
-enum { OPT_FP64_LIMITER = 1, OPT_UNFUSED_SWEEPS = 2, OPT_SUBCELL_DT = 4, OPT_AEC_Q1 = 8 };
+enum { OPT_FP64_LIMITER = 1, OPT_UNFUSED_SWEEPS = 2, OPT_SUBCELL_DT = 4, OPT_AEC_Q1 = 8, OPT_DTE_REDUCE = 16 };
 
 // typed views of the problem and mesh constants: float kernels read the
 // float copies, float64 kernels the originals

@@ -71,7 +71,10 @@ struct Dim {
     static constexpr int N1 = P + 1, N2 = N1 * N1, NQ = P + 2;
 };
 
-enum { CNT_VIOL = 0, CNT_CLAMP = 1, CNT_CFL = 2, CNT_NONFINITE = 3, CNT_N = 8 };
+// device counters: invariant-domain violations, rounding clamps, theta > 1,
+// non-finite values, unlimited averages ubar^e outside G (flux limiter off),
+// pseudo time steps reduced by the remark after eq. (dtmaxcell)
+enum { CNT_VIOL = 0, CNT_CLAMP = 1, CNT_CFL = 2, CNT_NONFINITE = 3, CNT_UBAR = 4, CNT_DTE_RED = 5, CNT_N = 8 };
 
 // global node of local (a, b) in element (ex, ey); periodic wrap at the far side
 DEV long long node_of(const MeshDev& m, int ex, int ey, int a, int b) {
@@ -2050,6 +2053,54 @@ __device__ __noinline__ CompVec<R, Ph::NC> bnd_face_llf_sum(const MeshDev& m, co
     return out;
 }
 
+// ubar^e in G: scalars umin <= ubar <= umax, Euler rho > 0 and
+// rho E - |m|^2/2 > 0 (explicit float64 roundings, the same decision in
+// every kernel)
+template <class Ph>
+DEV bool average_in_G(const ProbDev& pr, const double (&ub)[Ph::NC]) {
+    if constexpr (Ph::NC == 1) {
+        return ub[0] >= pr.umin && ub[0] <= pr.umax;
+    } else {
+        const double kin = __dmul_rn(0.5, __dadd_rn(__dmul_rn(ub[1], ub[1]), __dmul_rn(ub[2], ub[2])));
+        return ub[0] > 0.0 && __dsub_rn(__dmul_rn(ub[0], ub[3]), kin) > 0.0;
+    }
+}
+
+// An unlimited average ubar^e = u^e - r S_e (eq. (uebar), r = dt_e / h, S_e
+// the outward sum of f^H) that left G: counted; with OPT_DTE_REDUCE the
+// strategy of the remark after eq. (dtmaxcell): the largest r in [0, rs]
+// with ubar^e in G (scalars: the crossed bound solved exactly; Euler: the
+// Appendix-A criterion for u^e moved by -rs S_e, r = rs alpha).  Returns
+// [ubar^e .., r].
+template <class Ph>
+__device__ __noinline__ CompVec<double, Ph::NC + 1> reduce_pseudo_step(const ProbDev& pr,
+                                                                      const double (&ue)[Ph::NC],
+                                                                      const double (&os)[Ph::NC], double rs,
+                                                                      unsigned long long* __restrict__ cnt) {
+    constexpr int NC = Ph::NC;
+    atomicAdd(&cnt[CNT_UBAR], 1ull);
+    CompVec<double, NC + 1> out;
+    double r = rs;
+    if (pr.opts & OPT_DTE_REDUCE) {
+        if constexpr (NC == 1) {
+            const double d = os[0];
+            if (d < 0.0) r = fmin(r, (pr.umax - ue[0]) / (-d));
+            if (d > 0.0) r = fmin(r, (ue[0] - pr.umin) / d);
+            r = fmax(r, 0.0);
+        } else {
+            double g[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) g[c] = (-rs) * os[c];
+            r = rs * euler_alpha<double>(ue, g, 1.0, pr.pos_eps);
+        }
+        if (r < rs) atomicAdd(&cnt[CNT_DTE_RED], 1ull);
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) out.v[c] = ue[c] - r * os[c];
+    out.v[NC] = r;
+    return out;
+}
+
 // facet part of the element update: canonical f^H, the flux limiter and
 // ubar^e (eqs. (hoflux), (fAlim)/(uelim), Appendix A), and the facet term
 // (h/(p+1)^2) sum_d +-f^H_d of the element contributions f_i^e (eq. (aec))
@@ -2058,8 +2109,10 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
                     const double (&uec)[Ph::NC], const double (&ublc)[Ph::NC], double rs,
                     const double* __restrict__ dte_a, const double* __restrict__ ubl,
                     const R* __restrict__ qcap, const R* __restrict__ fl_in, const float* __restrict__ cf, int e,
-                    double (&ubec)[Ph::NC], R (&fh)[Ph::NC]) {
+                    double (&ubec)[Ph::NC], R (&fh)[Ph::NC], double& rs_out,
+                    unsigned long long* __restrict__ cnt) {
     constexpr int NC = Ph::NC, N1 = P + 1;
+    rs_out = rs;
     // FP32-mixed systems: the limited facet fluxes enter ubar^e as float-float
     // terms (below), so f^H stays in float and no float64 copy is formed
     constexpr bool mixed_sys = sizeof(R) == 4 && NC > 1;
@@ -2116,6 +2169,7 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
 #pragma unroll
         for (int c = 0; c < NC; ++c) ubec[c] = ublc[c];
     } else if (pr.fl == FL_NONE) {
+        double osv[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             double os;
@@ -2126,7 +2180,17 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
             } else {
                 os = ((FH[1][c] - FH[0][c]) + FH[3][c]) - FH[2][c];
             }
+            osv[c] = os;
             ubec[c] = uec[c] - rs * os;
+        }
+        // eq. (uebar) with the macrocell dt_e need not stay in G: count such
+        // averages, and with the option decrease dt_e as the remark after
+        // eq. (dtmaxcell) says (out of line: rare)
+        if (!average_in_G<Ph>(pr, ubec)) {
+            const CompVec<double, NC + 1> red = reduce_pseudo_step<Ph>(pr, uec, osv, rs, cnt);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ubec[c] = red.v[c];
+            rs_out = red.v[NC];
         }
     } else {
         R FLr[4][NC];
@@ -2408,7 +2472,8 @@ DEV void element_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][
 
 template <class R, int P, class Ph>
 DEV void update_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u, const R* __restrict__ ud,
-                            const double* __restrict__ ue, const double* __restrict__ dte_a, const double* __restrict__ ubl,
+                            const double* __restrict__ ue, double* dte_a,
+                            const double* __restrict__ ubl,
                             const R* __restrict__ qcap, const R* __restrict__ fl_in,
                             const R* __restrict__ ER, const float* __restrict__ cf,
                             const float* __restrict__ avg,
@@ -2436,9 +2501,20 @@ DEV void update_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
     }
     double ubec[NC];
     R fh[NC];
-    facet_part<R, P, Ph>(m, pr, U, nb, uec, ublc, rs, dte_a, ubl, qcap, fl_in, cf, e, ubec, fh);
+    double rs2;
+    facet_part<R, P, Ph>(m, pr, U, nb, uec, ublc, rs, dte_a, ubl, qcap, fl_in, cf, e, ubec, fh, rs2, cnt);
 #pragma unroll
     for (int c = 0; c < NC; ++c) ube_out[c * m.E + e] = ubec[c];
+    if (rs2 != rs) {
+        // a pseudo time step decreased by the remark after eq. (dtmaxcell)
+        const double dte2 = h * rs2;
+        dte_a[e] = dte2;
+        dte_a[m.E + e] = rs2;
+        dte_a[2 * m.E + e] = 1.0 / dte2;
+        element_part<R, P, Ph>(m, pr, U, ud, ER, cf, avg, uec, dt, dte2, 1.0 / dte2, ubec, fh, EW, beta_out, cnt, ex,
+                               ey, e);
+        return;
+    }
     element_part<R, P, Ph>(m, pr, U, ud, ER, cf, avg, uec, dt, dte, rdte, ubec, fh, EW, beta_out, cnt, ex, ey, e);
 }
 
@@ -2456,7 +2532,8 @@ __global__ void __launch_bounds__(128) k_q1_facet(MeshDev m, ProbDev pr, const R
                                                   const double* __restrict__ ue, const double* __restrict__ dte_a,
                                                   const double* __restrict__ ubl, const R* __restrict__ qcap,
                                                   const R* __restrict__ fl_in, const float* __restrict__ cf,
-                                                  R* __restrict__ ER, double* __restrict__ ube_out) {
+                                                  R* __restrict__ ER, double* __restrict__ ube_out,
+                                                  unsigned long long* __restrict__ cnt) {
     pdl_begin();
     int ex, ey, e;
     if (!elem_of_thread(m, ex, ey, e)) return;
@@ -2475,7 +2552,9 @@ __global__ void __launch_bounds__(128) k_q1_facet(MeshDev m, ProbDev pr, const R
     }
     double ubec[NC];
     R fh[NC];
-    facet_part<R, P, Ph>(m, pr, U, nb, uec, ublc, dte_a[m.E + e], dte_a, ubl, qcap, fl_in, cf, e, ubec, fh);
+    double rs2;  // eq. (aecQ1) is not combined with the pseudo-time-step reduction
+    facet_part<R, P, Ph>(m, pr, U, nb, uec, ublc, dte_a[m.E + e], dte_a, ubl, qcap, fl_in, cf, e, ubec, fh, rs2,
+                         cnt);
 #pragma unroll
     for (int c = 0; c < NC; ++c) ube_out[c * m.E + e] = ubec[c];
     // nodal fluxes f(u_j)
@@ -2595,7 +2674,7 @@ __global__ void __launch_bounds__(128) k_q1_update(MeshDev m, ProbDev pr, const 
 // instead of the 2 that the uncapped allocation leaves (measured faster)
 template <class R, int P, class Ph>
 __global__ void __launch_bounds__(128, (Ph::NC > 1 && P == 2) ? 3 : 1) k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
-                            const double* __restrict__ ue, const double* __restrict__ dte_a, const double* __restrict__ ubl,
+                            const double* __restrict__ ue, double* dte_a, const double* __restrict__ ubl,
                             const R* __restrict__ qcap, const R* __restrict__ fl_in,
                             const R* __restrict__ ER, const float* __restrict__ cf,
                             const float* __restrict__ avg,
@@ -2616,10 +2695,11 @@ __global__ void __launch_bounds__(128, (Ph::NC > 1 && P == 2) ? 3 : 1) k_update_
 // compute what k_update_ev computes, in the same arithmetic.
 template <int P, class Ph>
 __global__ void __launch_bounds__(128) k_facet(MeshDev m, ProbDev pr, const float* __restrict__ u,
-                                               const double* __restrict__ ue, const double* __restrict__ dte_a,
+                                               const double* __restrict__ ue, double* dte_a,
                                                const double* __restrict__ ubl, const float* __restrict__ qcap,
-                                               const float* __restrict__ fl_in, const float* __restrict__ cf,
-                                               double* __restrict__ ube_out, float* __restrict__ fht) {
+                                               const float* __restrict__ fl_in, float* cf,
+                                               double* __restrict__ ube_out, float* __restrict__ fht,
+                                               unsigned long long* __restrict__ cnt) {
     pdl_begin();
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
     int ex, ey, e;
@@ -2637,11 +2717,23 @@ __global__ void __launch_bounds__(128) k_facet(MeshDev m, ProbDev pr, const floa
         uec[c] = need_ue ? ue[c * m.E + e] : 0.0;
         ublc[c] = ubl[c * m.E + e];
     }
-    facet_part<float, P, Ph>(m, pr, U, nb, uec, ublc, dte_a[m.E + e], dte_a, ubl, qcap, fl_in, cf, e, ubec, fh);
+    const double rs = dte_a[m.E + e];
+    double rs2;
+    facet_part<float, P, Ph>(m, pr, U, nb, uec, ublc, rs, dte_a, ubl, qcap, fl_in, cf, e, ubec, fh, rs2, cnt);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         ube_out[c * m.E + e] = ubec[c];
         fht[c * m.E + e] = fh[c];
+    }
+    if (rs2 != rs) {
+        // a pseudo time step decreased by the remark after eq. (dtmaxcell):
+        // the float speed sum that k_update_el reads is rounded up (its float
+        // dt_e never exceeds the reduced one)
+        const double dte2 = m.h * rs2;
+        dte_a[e] = dte2;
+        dte_a[m.E + e] = rs2;
+        dte_a[2 * m.E + e] = 1.0 / dte2;
+        cf[e] = __double2float_ru(1.0 / rs2);
     }
 }
 

@@ -167,8 +167,8 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
             chk(cudaStreamWaitEvent(B.st2, B.ev_fork, 0));
             CGL_LAUNCH(prof, KID_FACET, B.st2,
                        chk(launch(false, k_facet<P, Ph>, ge, be, B.st2, m, pr, (const float*)u, (const double*)B.ue,
-                                  (const double*)B.dte, (const double*)B.ubl, (const float*)B.q,
-                                  (const float*)B.fl, (const float*)B.cf, B.ube, B.fht)));
+                                  B.dte, (const double*)B.ubl, (const float*)B.q, (const float*)B.fl, B.cf, B.ube,
+                                  B.fht, B.cnt)));
             chk(cudaEventRecord(B.ev_join, B.st2));
         }
     }
@@ -181,7 +181,7 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
         CGL_LAUNCH(prof, KID_Q1F, st,
                    chk(launch(pdl, k_q1_facet<R, P, Ph>, ge, be, st, m, pr, (const R*)u, (const double*)B.ue,
                               (const double*)B.dte, (const double*)B.ubl, (const R*)B.q, (const R*)B.fl,
-                              (const float*)B.cf, (R*)B.ER, B.ube)));
+                              (const float*)B.cf, (R*)B.ER, B.ube, B.cnt)));
         CGL_LAUNCH(prof, KID_UDL, st,
                    chk(launch(pdl, k_udl<R, P, NC>, gn, bn, st, m, (const R*)u, (const double*)B.ube,
                               (const double*)B.dte, (R*)B.ud)));
@@ -271,7 +271,7 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
     } else
     CGL_LAUNCH(prof, KID_UPDATE, st,
                chk(launch(pdl, k_update_ev<R, P, Ph>, ge, be, st, m, pr, (const R*)u, (const R*)ud,
-                          (const double*)B.ue, (const double*)B.dte, (const double*)B.ubl, (const R*)B.q,
+                          (const double*)B.ue, B.dte, (const double*)B.ubl, (const R*)B.q,
                           (const R*)B.fl, (const R*)B.ER, (const float*)B.cf, (const float*)B.avg,
                           (const double*)B.dt, (R*)B.EW,
                           B.ube, B.beta, B.cnt)));
