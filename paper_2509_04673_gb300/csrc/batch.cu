@@ -1,6 +1,8 @@
 // batch.cu — many independent scalar instances (uneven mesh sizes and
-// degrees, own time steps) advanced by one persistent cooperative launch per
-// SSP-RK stage, the three launches of a step captured in a CUDA graph.
+// degrees, own time steps) advanced by persistent cooperative launches: per
+// SSP-RK stage one launch for each degree present (a kernel compiled for that
+// degree, with its own register budget), all launches of a step captured in
+// one CUDA graph.
 //
 // The work of every phase of the stage (the passes of Sec. 4.3 of the
 // paper, see kernels.cuh) is cut into tiles: (instance, run of elements) for
@@ -63,7 +65,6 @@ template <int P>
 constexpr int ws_deg() {
     return cmax(StFields<float, P, 1, 2>::ws, cmax(StFields<float, P, 2, 1>::ws, StFields<float, P, 1, 1>::ws));
 }
-constexpr int WS_MAX = cmax(cmax(ws_deg<1>(), ws_deg<2>()), cmax(ws_deg<3>(), ws_deg<4>()));
 
 // bounded grid barrier: returns false if it gave up (or another block did)
 DEV bool grid_sync(BatchSync* s, long long limit) {
@@ -102,10 +103,10 @@ DEV bool grid_sync(BatchSync* s, long long limit) {
 DEV const float* g_final(const InstDev& D, int kg) { return (kg & 1) ? D.g2 : D.g; }
 DEV const float* ud_final(const InstDev& D, int ku) { return (ku & 1) ? D.ud2 : D.ud; }
 
-// per-degree phase bodies are separate functions (not inlined into the
-// persistent kernel) so that each gets its own register allocation
+// element phase bodies, inlined into the degree's persistent kernel (a call
+// would spill the caller's live registers at every element)
 template <int P, class Ph>
-__device__ __noinline__ void elem_phase(int phase, const InstDev& D, int ex, int ey, int e, double& dte, int kg,
+DEV void elem_phase(int phase, const InstDev& D, int ex, int ey, int e, double& dte, int kg,
                                         int ku) {
     switch (phase) {
         case PH_PRE:
@@ -121,20 +122,12 @@ __device__ __noinline__ void elem_phase(int phase, const InstDev& D, int ex, int
     }
 }
 
+template <int P>
 DEV void elem_dispatch(int phase, const InstDev& D, int ex, int ey, int e, double& dte, int kg, int ku) {
-    switch (D.p * 3 + D.phys) {
-        case 3: elem_phase<1, PhysAdv>(phase, D, ex, ey, e, dte, kg, ku); break;
-        case 4: elem_phase<1, PhysBurgers>(phase, D, ex, ey, e, dte, kg, ku); break;
-        case 5: elem_phase<1, PhysKPP>(phase, D, ex, ey, e, dte, kg, ku); break;
-        case 6: elem_phase<2, PhysAdv>(phase, D, ex, ey, e, dte, kg, ku); break;
-        case 7: elem_phase<2, PhysBurgers>(phase, D, ex, ey, e, dte, kg, ku); break;
-        case 8: elem_phase<2, PhysKPP>(phase, D, ex, ey, e, dte, kg, ku); break;
-        case 9: elem_phase<3, PhysAdv>(phase, D, ex, ey, e, dte, kg, ku); break;
-        case 10: elem_phase<3, PhysBurgers>(phase, D, ex, ey, e, dte, kg, ku); break;
-        case 11: elem_phase<3, PhysKPP>(phase, D, ex, ey, e, dte, kg, ku); break;
-        case 12: elem_phase<4, PhysAdv>(phase, D, ex, ey, e, dte, kg, ku); break;
-        case 13: elem_phase<4, PhysBurgers>(phase, D, ex, ey, e, dte, kg, ku); break;
-        default: elem_phase<4, PhysKPP>(phase, D, ex, ey, e, dte, kg, ku); break;
+    switch (D.phys) {
+        case 0: elem_phase<P, PhysAdv>(phase, D, ex, ey, e, dte, kg, ku); break;
+        case 1: elem_phase<P, PhysBurgers>(phase, D, ex, ey, e, dte, kg, ku); break;
+        default: elem_phase<P, PhysKPP>(phase, D, ex, ey, e, dte, kg, ku); break;
     }
 }
 
@@ -170,15 +163,7 @@ __device__ __noinline__ void node_phase(int phase, const InstDev& D, int gx0, in
     }
 }
 
-DEV void node_dispatch(int phase, const InstDev& D, int gx0, int gy0, float a, float b, int k, float* ws) {
-    switch (D.p) {
-        case 1: node_phase<1>(phase, D, gx0, gy0, a, b, k, ws); break;
-        case 2: node_phase<2>(phase, D, gx0, gy0, a, b, k, ws); break;
-        case 3: node_phase<3>(phase, D, gx0, gy0, a, b, k, ws); break;
-        default: node_phase<4>(phase, D, gx0, gy0, a, b, k, ws); break;
-    }
-}
-
+template <int P>
 DEV void elem_loop(int phase, const InstDev* __restrict__ I, const Tile* __restrict__ et, int net, bool first,
                    int kg, int ku) {
     for (int t = blockIdx.x; t < net; t += gridDim.x) {
@@ -189,32 +174,40 @@ DEV void elem_loop(int phase, const InstDev* __restrict__ I, const Tile* __restr
             const int e = T.begin + threadIdx.x;
             const int nx = D.m.nx;
             const int ey = e / nx, ex = e - ey * nx;
-            elem_dispatch(phase, D, ex, ey, e, dte, kg, ku);
+            elem_dispatch<P>(phase, D, ex, ey, e, dte, kg, ku);
         }
         if (phase == PH_PRE && first) block_min_to(dte, D.dtbits);
     }
 }
 
 // every block takes whole node tiles (the tiled stencils synchronise the block)
+template <int P>
 DEV void node_loop(int phase, const InstDev* __restrict__ I, const Tile* __restrict__ nt, int nnt, float a,
                    float b, int k, float* ws) {
     for (int t = blockIdx.x; t < nnt; t += gridDim.x) {
         const Tile T = nt[t];
-        node_dispatch(phase, I[T.inst], T.begin, T.count, a, b, k, ws);
+        node_phase<P>(phase, I[T.inst], T.begin, T.count, a, b, k, ws);
     }
 }
 
-// one SSP stage u <- a u^n + b FE(u) for every instance
-// 7 blocks per SM (a 72-register cap): the spills it costs in the element
-// phases are cheaper than the latency that fewer resident warps leave
-// unhidden in the tile loops (measured: 4 blocks 11.6 ms, 6: 10.4, 7: 10.2,
-// 8: 10.3 per step of the 256-instance batch)
-__global__ void __launch_bounds__(BT, 7)
+// one SSP stage u <- a u^n + b FE(u) for every instance of degree P.
+// A kernel that carries only one degree's code keeps the instruction working
+// set small: measured on the 256-instance batch, the four degrees launched
+// apart took 7.0 ms per step against 10.3 ms for one kernel over all
+// degrees.  7 blocks of 128 threads per SM (a 72-register cap) for every
+// degree: the tile loops are latency-bound, and the register budgets the
+// element phases would take at p = 3 and 4 (4 and 3 blocks per SM) measured
+// slower, 2.34 and 3.94 ms against 2.19 and 3.17 ms per step for those
+// degrees' instances.
+constexpr int batch_min_blocks(int) { return 7; }
+
+template <int P>
+__global__ void __launch_bounds__(BT, batch_min_blocks(P))
     k_batch_stage(const InstDev* __restrict__ I, int ninst, const Tile* __restrict__ et, int net,
                   const Tile* __restrict__ nt, int nnt, BatchSync* sync, float a, float b, int first,
                   int last, int kg, int ku, int mode_lo, long long limit) {
-    __shared__ float ws[WS_MAX];
-    elem_loop(PH_PRE, I, et, net, first != 0, kg, ku);
+    __shared__ float ws[ws_deg<P>()];
+    elem_loop<P>(PH_PRE, I, et, net, first != 0, kg, ku);
     if (!grid_sync(sync, limit)) return;
     if (first) {
         // global dt of each instance from its block minima (eq. (cflglob),
@@ -230,26 +223,37 @@ __global__ void __launch_bounds__(BT, 7)
         if (mode_lo && !grid_sync(sync, limit)) return;
     }
     if (!mode_lo) {
-        node_loop(PH_GRAD, I, nt, nnt, a, b, 0, ws);
+        node_loop<P>(PH_GRAD, I, nt, nnt, a, b, 0, ws);
         if (!grid_sync(sync, limit)) return;
         for (int k = 0; k < kg; ++k) {
-            node_loop(PH_SWEEP_G, I, nt, nnt, a, b, k, ws);
+            node_loop<P>(PH_SWEEP_G, I, nt, nnt, a, b, k, ws);
             if (!grid_sync(sync, limit)) return;
         }
-        elem_loop(PH_RES, I, et, net, false, kg, ku);
+        elem_loop<P>(PH_RES, I, et, net, false, kg, ku);
         if (!grid_sync(sync, limit)) return;
-        node_loop(PH_GATHER_R, I, nt, nnt, a, b, 0, ws);
+        node_loop<P>(PH_GATHER_R, I, nt, nnt, a, b, 0, ws);
         if (!grid_sync(sync, limit)) return;
         for (int k = 0; k < ku; ++k) {
-            node_loop(PH_SWEEP_U, I, nt, nnt, a, b, k, ws);
+            node_loop<P>(PH_SWEEP_U, I, nt, nnt, a, b, k, ws);
             if (!grid_sync(sync, limit)) return;
         }
     }
-    elem_loop(PH_UPDATE, I, et, net, false, kg, ku);
+    elem_loop<P>(PH_UPDATE, I, et, net, false, kg, ku);
     if (!grid_sync(sync, limit)) return;
-    node_loop(PH_FINAL, I, nt, nnt, a, b, 0, ws);
+    node_loop<P>(PH_FINAL, I, nt, nnt, a, b, 0, ws);
     if (last) {
         for (int i = blockIdx.x * BT + threadIdx.x; i < ninst; i += gridDim.x * BT) *I[i].t += *I[i].dt;
+    }
+}
+
+typedef void (*BatchKernel)(const InstDev*, int, const Tile*, int, const Tile*, int, BatchSync*, float, float, int,
+                            int, int, int, int, long long);
+static BatchKernel batch_kernel(int p) {
+    switch (p) {
+        case 1: return k_batch_stage<1>;
+        case 2: return k_batch_stage<2>;
+        case 3: return k_batch_stage<3>;
+        default: return k_batch_stage<4>;
     }
 }
 
@@ -261,15 +265,22 @@ cudaError_t upload_batch(const Tab<double>* td, const Tab<float>* tf, const doub
 
 using namespace cgl;
 
-struct cgl_batch {
-    std::vector<cgl_state*> states;
-    cudaStream_t st;
-    int ninst;
+// the instances of one degree and the persistent kernel that carries them
+struct DegreeGroup {
+    int p;
+    std::vector<int> members;  // indices into cgl_batch::states
     InstDev* d_inst;
     Tile *d_et, *d_nt;
     int net, nnt;
     BatchSync* d_sync;
     int grid;
+};
+
+struct cgl_batch {
+    std::vector<cgl_state*> states;
+    cudaStream_t st;
+    int ninst;
+    std::vector<DegreeGroup> groups;  // one per degree present, ascending
     int tile_elems[PMAX + 1];
     int node_tile;
     int mode_lo, kg, ku;
@@ -286,27 +297,29 @@ static cgl_status bfail(cgl_status st, const char* msg, cudaError_t e = cudaSucc
 }
 
 static cgl_status build_tiles(cgl_batch* B) {
-    std::vector<Tile> et, nt;
-    for (int i = 0; i < B->ninst; ++i) {
-        const MeshDev& m = B->states[i]->mesh->m;
-        const int T = std::max(1, std::min(BT, B->tile_elems[m.p]));
-        for (int b = 0; b < m.E; b += T) et.push_back(Tile{i, b, std::min(T, m.E - b), 0});
-        for (int gy0 = 0; gy0 < m.nny; gy0 += ST_TY)
-            for (int gx0 = 0; gx0 < m.nnx; gx0 += ST_TX) nt.push_back(Tile{i, gx0, gy0, 0});
+    for (DegreeGroup& G : B->groups) {
+        std::vector<Tile> et, nt;
+        const int T = std::max(1, std::min(BT, B->tile_elems[G.p]));
+        for (int k = 0; k < (int)G.members.size(); ++k) {
+            const MeshDev& m = B->states[G.members[k]]->mesh->m;
+            for (int b = 0; b < m.E; b += T) et.push_back(Tile{k, b, std::min(T, m.E - b), 0});
+            for (int gy0 = 0; gy0 < m.nny; gy0 += ST_TY)
+                for (int gx0 = 0; gx0 < m.nnx; gx0 += ST_TX) nt.push_back(Tile{k, gx0, gy0, 0});
+        }
+        if (G.d_et) cudaFree(G.d_et);
+        if (G.d_nt) cudaFree(G.d_nt);
+        G.d_et = G.d_nt = nullptr;
+        cudaError_t e = cudaMalloc(&G.d_et, et.size() * sizeof(Tile));
+        if (e == cudaSuccess) e = cudaMalloc(&G.d_nt, nt.size() * sizeof(Tile));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(G.d_et, et.data(), et.size() * sizeof(Tile), cudaMemcpyHostToDevice, B->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(G.d_nt, nt.data(), nt.size() * sizeof(Tile), cudaMemcpyHostToDevice, B->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(B->st);
+        if (e != cudaSuccess) return bfail(CGL_ECUDA, "tile upload", e);
+        G.net = (int)et.size();
+        G.nnt = (int)nt.size();
     }
-    if (B->d_et) cudaFree(B->d_et);
-    if (B->d_nt) cudaFree(B->d_nt);
-    B->d_et = B->d_nt = nullptr;
-    cudaError_t e = cudaMalloc(&B->d_et, et.size() * sizeof(Tile));
-    if (e == cudaSuccess) e = cudaMalloc(&B->d_nt, nt.size() * sizeof(Tile));
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(B->d_et, et.data(), et.size() * sizeof(Tile), cudaMemcpyHostToDevice, B->st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(B->d_nt, nt.data(), nt.size() * sizeof(Tile), cudaMemcpyHostToDevice, B->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(B->st);
-    if (e != cudaSuccess) return bfail(CGL_ECUDA, "tile upload", e);
-    B->net = (int)et.size();
-    B->nnt = (int)nt.size();
     if (B->graph) {
         cudaGraphExecDestroy(B->graph);
         B->graph = nullptr;
@@ -314,23 +327,29 @@ static cgl_status build_tiles(cgl_batch* B) {
     return CGL_OK;
 }
 
-static cudaError_t launch_stage(cgl_batch* B, float a, float b, int first, int last) {
-    void* args[] = {&B->d_inst, &B->ninst, &B->d_et, &B->net, &B->d_nt, &B->nnt, &B->d_sync, &a, &b,
+static cudaError_t launch_stage(cgl_batch* B, DegreeGroup& G, float a, float b, int first, int last) {
+    int ninst = (int)G.members.size();
+    void* args[] = {&G.d_inst, &ninst, &G.d_et, &G.net, &G.d_nt, &G.nnt, &G.d_sync, &a, &b,
                     &first, &last, &B->kg, &B->ku, &B->mode_lo, &B->limit};
-    return cudaLaunchCooperativeKernel((const void*)k_batch_stage, dim3(B->grid), dim3(BT), args, 0, B->st);
+    return cudaLaunchCooperativeKernel((const void*)batch_kernel(G.p), dim3(G.grid), dim3(BT), args, 0, B->st);
 }
 
+// one step: three stages, each a persistent launch per degree present
 static cudaError_t enqueue_batch_step(cgl_batch* B) {
-    cudaError_t e = launch_stage(B, 0.f, 1.f, 1, 0);
-    if (e == cudaSuccess) e = launch_stage(B, 0.75f, 0.25f, 0, 0);
-    if (e == cudaSuccess) e = launch_stage(B, 1.f / 3.f, 2.f / 3.f, 0, 1);
+    const float sa[3] = {0.f, 0.75f, 1.f / 3.f}, sb[3] = {1.f, 0.25f, 2.f / 3.f};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        for (DegreeGroup& G : B->groups) {
+            e = launch_stage(B, G, sa[k], sb[k], k == 0, k == 2);
+            if (e != cudaSuccess) break;
+        }
     return e;
 }
 
-// Capture the three stage launches of a step into a graph once.  If the
-// capture fails the batch falls back to direct cooperative launches (same
-// results); cgl_batch_info reports graph = -1 then, and the CUDA error is
-// kept in graph_err.
+// Capture the stage launches of a step into a graph once.  If the capture
+// fails the batch falls back to direct cooperative launches (same results);
+// cgl_batch_info reports graph = -1 then, and the CUDA error is kept in
+// graph_err.
 static cgl_status ensure_graph(cgl_batch* B) {
     if (B->graph || !B->use_graph) return CGL_OK;
     cudaGraph_t g = nullptr;
@@ -364,11 +383,49 @@ static cgl_status ensure_graph(cgl_batch* B) {
 extern "C" void cgl_batch_destroy(cgl_batch* B) {
     if (!B) return;
     if (B->graph) cudaGraphExecDestroy(B->graph);
-    if (B->d_inst) cudaFree(B->d_inst);
-    if (B->d_et) cudaFree(B->d_et);
-    if (B->d_nt) cudaFree(B->d_nt);
-    if (B->d_sync) cudaFree(B->d_sync);
+    for (DegreeGroup& G : B->groups) {
+        if (G.d_inst) cudaFree(G.d_inst);
+        if (G.d_et) cudaFree(G.d_et);
+        if (G.d_nt) cudaFree(G.d_nt);
+        if (G.d_sync) cudaFree(G.d_sync);
+    }
     delete B;
+}
+
+static InstDev inst_of(const cgl_state* s) {
+    const Bufs& b = s->B;
+    InstDev d;
+    d.m = s->mesh->m;
+    d.pr = s->pd;
+    d.u = (float*)b.u;
+    d.un = (float*)b.un;
+    d.g = (float*)b.g;
+    d.g2 = (float*)b.g2;
+    d.ud2 = (float*)b.ud2;
+    d.bg = (float*)b.bg;
+    d.r = (float*)b.r;
+    d.ud = (float*)b.ud;
+    d.ER = (float*)b.ER;
+    d.EW = (float*)b.EW;
+    d.avg = b.avg;
+    d.cf = b.cf;
+    d.ue = b.ue;
+    d.dte = b.dte;
+    d.ubl = b.ubl;
+    d.gam = b.gam;
+    d.nu = b.nu;
+    d.q = (float*)b.q;
+    d.fl = (float*)b.fl;
+    d.ube = b.ube;
+    d.beta = b.beta;
+    d.cnt = b.cnt;
+    d.dtbits = b.dtbits;
+    d.dt = b.dt;
+    d.t = b.t;
+    d.t_end = b.t_end;
+    d.p = s->mesh->m.p;
+    d.phys = s->prob.flux;  // 0 advection, 1 Burgers, 2 KPP
+    return d;
 }
 
 extern "C" cgl_status cgl_batch_create(cgl_state* const* states, int32_t n, cgl_batch** out) {
@@ -382,6 +439,7 @@ extern "C" cgl_status cgl_batch_create(cgl_state* const* states, int32_t n, cgl_
         if (s->has_bnd) return bfail(CGL_EINVAL, "batched states take the mesh's boundary conditions");
         if (s->pd.opts & OPT_SUBCELL_DT) return bfail(CGL_EINVAL, "batched states take the macrocell dt_e");
         if (s->pd.opts & OPT_AEC_Q1) return bfail(CGL_EINVAL, "batched states take the element contributions of eq. (aec)");
+        if (s->pd.opts & OPT_DTE_REDUCE) return bfail(CGL_EINVAL, "batched states keep the macrocell dt_e");
         if (s->nc != 1 || s->prob.flux == CGL_FLUX_EULER) return bfail(CGL_EINVAL, "batched states must be scalar");
         if (s->device != s0->device) return bfail(CGL_EINVAL, "batched states must share a device");
         if (s->prob.mode != s0->prob.mode || s->prob.k_g != s0->prob.k_g || s->prob.k_u != s0->prob.k_u)
@@ -401,59 +459,39 @@ extern "C" cgl_status cgl_batch_create(cgl_state* const* states, int32_t n, cgl_
     B->node_tile = ST_TX * ST_TY;
     B->use_graph = true;
     B->graph_err = cudaSuccess;
+    B->graph = nullptr;
     for (int p = 0; p <= PMAX; ++p) B->tile_elems[p] = BT;
-    std::vector<InstDev> h(n);
-    for (int i = 0; i < n; ++i) {
-        const cgl_state* s = states[i];
-        const Bufs& b = s->B;
-        InstDev& d = h[i];
-        d.m = s->mesh->m;
-        d.pr = s->pd;
-        d.u = (float*)b.u;
-        d.un = (float*)b.un;
-        d.g = (float*)b.g;
-        d.g2 = (float*)b.g2;
-        d.ud2 = (float*)b.ud2;
-        d.bg = (float*)b.bg;
-        d.r = (float*)b.r;
-        d.ud = (float*)b.ud;
-        d.ER = (float*)b.ER;
-        d.EW = (float*)b.EW;
-        d.avg = b.avg;
-        d.cf = b.cf;
-        d.ue = b.ue;
-        d.dte = b.dte;
-        d.ubl = b.ubl;
-        d.gam = b.gam;
-        d.nu = b.nu;
-        d.q = (float*)b.q;
-        d.fl = (float*)b.fl;
-        d.ube = b.ube;
-        d.beta = b.beta;
-        d.cnt = b.cnt;
-        d.dtbits = b.dtbits;
-        d.dt = b.dt;
-        d.t = b.t;
-        d.t_end = b.t_end;
-        d.p = s->mesh->m.p;
-        d.phys = s->prob.flux;  // 0 advection, 1 Burgers, 2 KPP
-    }
-    cudaError_t e = cudaMalloc(&B->d_inst, n * sizeof(InstDev));
-    if (e == cudaSuccess) e = cudaMalloc(&B->d_sync, sizeof(BatchSync));
-    if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_inst, h.data(), n * sizeof(InstDev), cudaMemcpyHostToDevice, B->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_sync, 0, sizeof(BatchSync), B->st);
+    int nsm = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s0->device);
     if (e != cudaSuccess) {
-        cgl_batch_destroy(B);
-        return bfail(CGL_ECUDA, "batch allocation", e);
+        delete B;
+        return bfail(CGL_ECUDA, "device query", e);
     }
-    int nsm = 0, per_sm = 0;
-    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s0->device);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_stage, BT, 0);
-    if (e != cudaSuccess || per_sm < 1) {
-        cgl_batch_destroy(B);
-        return bfail(CGL_ECUDA, "occupancy query", e);
+    for (int p = 1; p <= PMAX; ++p) {
+        std::vector<InstDev> h;
+        DegreeGroup G{};
+        G.p = p;
+        for (int i = 0; i < n; ++i)
+            if (states[i]->mesh->m.p == p) {
+                G.members.push_back(i);
+                h.push_back(inst_of(states[i]));
+            }
+        if (G.members.empty()) continue;
+        int per_sm = 0;
+        e = cudaMalloc(&G.d_inst, h.size() * sizeof(InstDev));
+        if (e == cudaSuccess) e = cudaMalloc(&G.d_sync, sizeof(BatchSync));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(G.d_inst, h.data(), h.size() * sizeof(InstDev), cudaMemcpyHostToDevice, B->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(G.d_sync, 0, sizeof(BatchSync), B->st);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)batch_kernel(p), BT, 0);
+        B->groups.push_back(G);
+        if (e != cudaSuccess || per_sm < 1) {
+            cgl_batch_destroy(B);
+            return bfail(CGL_ECUDA, "batch allocation or occupancy query", e);
+        }
+        B->groups.back().grid = nsm * per_sm;
     }
-    B->grid = nsm * per_sm;
     cgl_status rc = build_tiles(B);
     if (rc) {
         cgl_batch_destroy(B);
@@ -464,15 +502,21 @@ extern "C" cgl_status cgl_batch_create(cgl_state* const* states, int32_t n, cgl_
 }
 
 static cgl_status check_sync(cgl_batch* B) {
-    BatchSync hs;
-    cudaError_t e = cudaMemcpyAsync(&hs, B->d_sync, sizeof(hs), cudaMemcpyDeviceToHost, B->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(B->st);
-    if (e != cudaSuccess) return bfail(CGL_ECUDA, "batch step", e);
-    if (hs.err) {
-        // reset the barrier for the next call
-        cudaMemsetAsync(B->d_sync, 0, sizeof(BatchSync), B->st);
-        int ph = B->phantom;
-        cudaMemcpyAsync(&B->d_sync->phantom, &ph, sizeof(int), cudaMemcpyHostToDevice, B->st);
+    bool err = false;
+    for (DegreeGroup& G : B->groups) {
+        BatchSync hs;
+        cudaError_t e = cudaMemcpyAsync(&hs, G.d_sync, sizeof(hs), cudaMemcpyDeviceToHost, B->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(B->st);
+        if (e != cudaSuccess) return bfail(CGL_ECUDA, "batch step", e);
+        err = err || hs.err;
+    }
+    if (err) {
+        // reset the barriers for the next call
+        for (DegreeGroup& G : B->groups) {
+            cudaMemsetAsync(G.d_sync, 0, sizeof(BatchSync), B->st);
+            int ph = B->phantom;
+            cudaMemcpyAsync(&G.d_sync->phantom, &ph, sizeof(int), cudaMemcpyHostToDevice, B->st);
+        }
         cudaStreamSynchronize(B->st);
         return set_error(CGL_ETIMEOUT, "a grid barrier of the batched stage gave up");
     }
@@ -510,10 +554,16 @@ extern "C" cgl_status cgl_batch_step(cgl_batch* B, int32_t nsteps, int64_t* viol
 extern "C" cgl_status cgl_batch_info(cgl_batch* B, int32_t* grid, int32_t* block, int32_t* elem_tiles,
                                      int32_t* node_tiles, int32_t* graph) {
     if (!B) return bfail(CGL_EINVAL, "null batch");
-    if (grid) *grid = B->grid;
+    int gmax = 0, net = 0, nnt = 0;
+    for (const DegreeGroup& G : B->groups) {
+        gmax = std::max(gmax, G.grid);
+        net += G.net;
+        nnt += G.nnt;
+    }
+    if (grid) *grid = gmax;
     if (block) *block = BT;
-    if (elem_tiles) *elem_tiles = B->net;
-    if (node_tiles) *node_tiles = B->nnt;
+    if (elem_tiles) *elem_tiles = net;
+    if (node_tiles) *node_tiles = nnt;
     if (graph) *graph = B->graph ? 1 : (B->graph_err != cudaSuccess ? -1 : 0);
     if (B->graph_err != cudaSuccess)
         set_error(CGL_OK, "graph capture failed (direct launches): %s", cudaGetErrorString(B->graph_err));
@@ -626,7 +676,9 @@ extern "C" cgl_status cgl_batch_debug(cgl_batch* B, int32_t phantom_blocks, int6
     B->phantom = phantom_blocks;
     B->limit = spin_limit;
     int ph = phantom_blocks;
-    cudaError_t e = cudaMemcpyAsync(&B->d_sync->phantom, &ph, sizeof(int), cudaMemcpyHostToDevice, B->st);
+    cudaError_t e = cudaSuccess;
+    for (DegreeGroup& G : B->groups)
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&G.d_sync->phantom, &ph, sizeof(int), cudaMemcpyHostToDevice, B->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(B->st);
     if (e != cudaSuccess) return bfail(CGL_ECUDA, "debug", e);
     if (B->graph) {
