@@ -24,7 +24,10 @@
  *     NULL;
  *   - a state is used from one host thread at a time; all its device work
  *     runs on the stream given at creation, and every function that returns
- *     host data synchronises that stream first.
+ *     host data synchronises that stream first;
+ *   - the library uploads its constant tables (and finds the address of its
+ *     no-allocation scratch) once per device and process; resetting a device
+ *     (cudaDeviceReset) while the library is loaded is not supported.
  */
 #ifndef CGL_H
 #define CGL_H
@@ -367,9 +370,11 @@ cgl_status cgl_batch_get_tiles(cgl_batch *batch, int32_t *tile_elems);
 cgl_status cgl_batch_autotune(cgl_batch *batch, int32_t steps, const char *json_path);
 cgl_status cgl_batch_load_tuning(cgl_batch *batch, const char *json_path);
 
-/* Test hook: every grid barrier waits for phantom_blocks arrivals that never
-   come (0 = normal) and gives up after spin_limit polls, so the timeout path
-   (CGL_ETIMEOUT) can be exercised without any fault. */
+/* TEST ONLY, not for production use: every grid barrier waits for
+   phantom_blocks arrivals that never come (0 = normal) and gives up after
+   spin_limit polls, so the timeout path (CGL_ETIMEOUT) can be exercised
+   without any fault.  A batch with phantom_blocks > 0 cannot step; set 0
+   and a spin limit again (or create a new batch) to use it. */
 cgl_status cgl_batch_debug(cgl_batch *batch, int32_t phantom_blocks, int64_t spin_limit);
 
 /* --- no-allocation entry point --------------------------------------------------- */

@@ -42,6 +42,10 @@ struct GradSweepWs {
     static constexpr int size = A + B + C + D + 2 * NCL * NW;
 };
 
+// The block's geometry (wrapped node indices, node classes, weights, masses)
+// is the same for every component, so it is formed once into registers
+// before the component loop; the halo passes give each thread a fixed
+// column (its x weights stay in registers) and a set of rows.
 template <int P, int NC>
 __global__ void __launch_bounds__(ST_TX * ST_BY)
     k_grad_sweep(MeshDev m, const float* __restrict__ u, float* __restrict__ bout, float* __restrict__ gout) {
@@ -50,6 +54,11 @@ __global__ void __launch_bounds__(ST_TX * ST_BY)
     using WS = GradSweepWs<P, NC>;
     constexpr int HX1 = WS::HX1, HY1 = WS::HY1, HX2 = WS::HX2, HY2 = WS::HY2, NW = WS::NW, NCL = WS::NCL;
     constexpr int NT = ST_TX * ST_BY, NJ = ST_TY / ST_BY;
+    constexpr int RG = NT / HX1;                    // row groups of the halo passes
+    constexpr int NA = (HY2 * HX2 + NT - 1) / NT;  // staged values per thread
+    constexpr int NXP = (HY2 + RG - 1) / RG;        // x-pass rows per thread
+    constexpr int NYP = (HY1 + RG - 1) / RG;        // y-pass rows per thread
+    constexpr int NSX = (HY1 + ST_BY - 1) / ST_BY;  // rows of the sweep's x-pass per thread
     __shared__ float ws[WS::size];
     float(*A)[HX2] = reinterpret_cast<float(*)[HX2]>(ws);
     float(*tC)[HX1] = reinterpret_cast<float(*)[HX1]>(ws + WS::A);
@@ -68,67 +77,116 @@ __global__ void __launch_bounds__(ST_TX * ST_BY)
     }
     const int gx0 = blockIdx.x * ST_TX, gy0 = blockIdx.y * ST_TY;
     const float h = m.h_f, h2 = m.h2_f;
-    for (int c = 0; c < NC; ++c) {
-        __syncthreads();  // weights ready; previous component consumed
-        // u of component c on the tile plus a halo of 2p nodes
-        for (int i = tid; i < HY2 * HX2; i += NT) {
+    // staged values of u: node offsets (-1 outside the mesh)
+    long long aoff[NA];
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        const int i = tid + j * NT;
+        aoff[j] = -1;
+        if (i < HY2 * HX2) {
             const int r = i / HX2, cc = i - r * HX2;
             int gx = gx0 - 2 * P + cc, gy = gy0 - 2 * P + r;
-            const bool in = wrap_node(m, gx, gy);
-            A[r][cc] = in ? __ldcg(&u[(long long)c * m.NN + (long long)gy * m.nnx + gx]) : 0.f;
+            if (wrap_node(m, gx, gy)) aoff[j] = (long long)gy * m.nnx + gx;
+        }
+    }
+    // halo passes: column cx of the p halo, rows rg + RG j
+    const int cx = tid % HX1, rg = tid / HX1;
+    const bool hv = rg < RG;
+    int clx;
+    {
+        int gx = gx0 - P + cx, gy = 0;
+        wrap_node(m, gx, gy);
+        clx = node_class<P>(gx, m.nnx, m.px);
+    }
+    bool yin[NYP];
+    int ycl[NYP];
+    float yinv[NYP];
+#pragma unroll
+    for (int j = 0; j < NYP; ++j) {
+        const int r = rg + RG * j;
+        int gx = gx0 - P + cx, gy = gy0 - P + r;
+        yin[j] = wrap_node(m, gx, gy) && hv && r < HY1;
+        ycl[j] = node_class<P>(gy, m.nny, m.py);
+        const int cnt = (clx == 0 ? 2 : 1) * (ycl[j] == 0 ? 2 : 1);
+        yinv[j] = mul_r(m.inv_me_f, inv_count<float>(cnt));
+    }
+    // the sweep: column tx of the tile, its x class and rows
+    const int gxt = gx0 + tx;
+    const int clxt = node_class<P>(gxt, m.nnx, m.px);
+    __syncthreads();  // weights ready
+    float wcx[NW], wmx[NW], wst[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+        wcx[k] = WC[clx][k];
+        wmx[k] = WM[clx][k];
+        wst[k] = WM[clxt][k];
+    }
+    for (int c = 0; c < NC; ++c) {
+        if (c > 0) __syncthreads();  // previous component consumed
+        // u of component c on the tile plus a halo of 2p nodes
+        const float* uc = u + (long long)c * m.NN;
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            const int i = tid + j * NT;
+            if (i < HY2 * HX2) ws[i] = aoff[j] >= 0 ? __ldcg(&uc[aoff[j]]) : 0.f;
         }
         __syncthreads();
         // grad stencil along x for the columns of the p halo, all 2p-halo rows
-        for (int i = tid; i < HY2 * HX1; i += NT) {
-            const int r = i / HX1, cc = i - r * HX1;
-            int gx = gx0 - P + cc, gy = 0;
-            wrap_node(m, gx, gy);
-            const int clx = node_class<P>(gx, m.nnx, m.px);
-            float sc = 0.f, sm = 0.f;
+        if (hv) {
 #pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                const float x = A[r][cc + k];
-                sc = fma_r(WC[clx][k], x, sc);
-                sm = fma_r(WM[clx][k], x, sm);
+            for (int j = 0; j < NXP; ++j) {
+                const int r = rg + RG * j;
+                if (r < HY2) {
+                    float sc = 0.f, sm = 0.f;
+#pragma unroll
+                    for (int k = 0; k < NW; ++k) {
+                        const float x = A[r][cx + k];
+                        sc = fma_r(wcx[k], x, sc);
+                        sm = fma_r(wmx[k], x, sm);
+                    }
+                    tC[r][cx] = sc;
+                    tM[r][cx] = sm;
+                }
             }
-            tC[r][cc] = sc;
-            tM[r][cc] = sm;
         }
         __syncthreads();
         // along y: b and g0 = b / m_i on the p halo (zero outside the mesh)
-        for (int i = tid; i < HY1 * HX1; i += NT) {
-            const int r = i / HX1, cc = i - r * HX1;
-            int gx = gx0 - P + cc, gy = gy0 - P + r;
-            const bool in = wrap_node(m, gx, gy);
-            const int clx = node_class<P>(gx, m.nnx, m.px), cly = node_class<P>(gy, m.nny, m.py);
-            float sx = 0.f, sy = 0.f;
+        if (hv) {
 #pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                sx = fma_r(WM[cly][k], tC[r + k][cc], sx);
-                sy = fma_r(WC[cly][k], tM[r + k][cc], sy);
-            }
-            const int cnt = (clx == 0 ? 2 : 1) * (cly == 0 ? 2 : 1);
-            const float inv_mi = mul_r(m.inv_me_f, inv_count<float>(cnt));
-            const float bx = mul_r(h, sx), by = mul_r(h, sy);
-            G[0][r][cc] = in ? mul_r(bx, inv_mi) : 0.f;
-            G[1][r][cc] = in ? mul_r(by, inv_mi) : 0.f;
-            const int rt = r - P, ct = cc - P;
-            if (rt >= 0 && rt < ST_TY && ct >= 0 && ct < ST_TX) {
-                Bt[0][rt][ct] = bx;
-                Bt[1][rt][ct] = by;
+            for (int j = 0; j < NYP; ++j) {
+                const int r = rg + RG * j;
+                if (r < HY1) {
+                    const int cly = ycl[j];
+                    float sx = 0.f, sy = 0.f;
+#pragma unroll
+                    for (int k = 0; k < NW; ++k) {
+                        sx = fma_r(WM[cly][k], tC[r + k][cx], sx);
+                        sy = fma_r(WC[cly][k], tM[r + k][cx], sy);
+                    }
+                    const float bx = mul_r(h, sx), by = mul_r(h, sy);
+                    G[0][r][cx] = yin[j] ? mul_r(bx, yinv[j]) : 0.f;
+                    G[1][r][cx] = yin[j] ? mul_r(by, yinv[j]) : 0.f;
+                    const int rt = r - P, ct = cx - P;
+                    if (rt >= 0 && rt < ST_TY && ct >= 0 && ct < ST_TX) {
+                        Bt[0][rt][ct] = bx;
+                        Bt[1][rt][ct] = by;
+                    }
+                }
             }
         }
         __syncthreads();
         // first sweep, along x for every p-halo row (the mass weights)
-        const int gxt = gx0 + tx;
-        const int clxt = node_class<P>(gxt, m.nnx, m.px);
-        for (int r = ty; r < HY1; r += ST_BY) {
 #pragma unroll
-            for (int f = 0; f < 2; ++f) {
-                float sx = 0.f;
+        for (int j = 0; j < NSX; ++j) {
+            const int r = ty + ST_BY * j;
+            if (r < HY1) {
 #pragma unroll
-                for (int k = 0; k < NW; ++k) sx = fma_r(WM[clxt][k], G[f][r][tx + k], sx);
-                t[f][r][tx] = sx;
+                for (int f = 0; f < 2; ++f) {
+                    float sx = 0.f;
+#pragma unroll
+                    for (int k = 0; k < NW; ++k) sx = fma_r(wst[k], G[f][r][tx + k], sx);
+                    t[f][r][tx] = sx;
+                }
             }
         }
         __syncthreads();
