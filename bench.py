@@ -526,18 +526,19 @@ def run_gpu(args):
     # ---- e2e through the C ABI with host buffers --------------------------
     st = h32["st"]
     host_in = torch.empty(h32["u0"].size, dtype=torch.float64, pin_memory=True).numpy().reshape(h32["u0"].shape)
+    host_out = torch.empty(h32["u0"].size, dtype=torch.float64, pin_memory=True).numpy().reshape(h32["u0"].shape)
     host_in[...] = h32["u0"]
     st.set_time(0.0)
     for _ in range(2):
         st.set_state(host_in)
         st.step(1)
-        res = st.get_state()
+        res = st.get_state(out=host_out)
     sync_all()
     t0 = time.perf_counter()
     for _ in range(K):
         st.set_state(host_in)
         st.step(1)
-        res = st.get_state()
+        res = st.get_state(out=host_out)
     torch.cuda.synchronize()
     e2e_s = reduce_over_ranks(time.perf_counter() - t0, dist, "cuda")
     del res
@@ -699,7 +700,8 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "e2e": {"value": aggregate_rate(nd_h * 3 * K, e2e_s * 1e3, world), "unit": UNIT,
                 "h2d_bytes_per_step": nd_h * 8, "d2h_bytes_per_step": nd_h * 8,
-                "path": "cgl_set_state (float64 host) + cgl_step + cgl_get_state (float64 host) per step"},
+                "path": "cgl_set_state (float64, pinned host) + cgl_step + cgl_get_state (float64, pinned host) "
+                        "per step"},
         "gpu_launches": h32["launches"] * K,
         "peaks_live": {"fp64_tflops": round(peaks_live["fp64_flops"] / 1e12, 4),
                        "fp32_tflops": round(peaks_live["fp32_flops"] / 1e12, 2)},

@@ -265,7 +265,11 @@ typedef struct cgl_boundary {
 cgl_status cgl_set_boundary(cgl_state *state, const cgl_boundary *b);
 
 /* Copy n = ncomp*nny*nnx float64 coefficients from the host into the state
-   (rounded to float32 in FP32_MIXED). Synchronous. */
+   (rounded to float32 in FP32_MIXED). The values pass through a float64
+   staging buffer on the device (allocated at the first copy, 8 bytes per
+   value, kept by the state), where they are checked and converted; a host
+   buffer in pinned memory copies fastest. CGL_ENONFINITE (state unchanged)
+   if any value is NaN or infinite. Synchronous. */
 cgl_status cgl_set_state(cgl_state *state, const double *host, size_t n);
 
 /* Nodal initialisation u_j(0) = u0(x_j) at the Bernstein nodal points x_j
@@ -275,7 +279,8 @@ cgl_status cgl_set_state(cgl_state *state, const double *host, size_t n);
 cgl_status cgl_set_state_nodal(cgl_state *state, double (*u0)(double x, double y, int32_t comp, void *ctx),
                                void *ctx);
 
-/* Copy the state to the host as float64 (exact widening in FP32_MIXED). */
+/* Copy the state to the host as float64 (exact widening in FP32_MIXED, on
+   the device through the staging buffer). Synchronous. */
 cgl_status cgl_get_state(cgl_state *state, double *host, size_t n);
 
 /* Set the base state u^n used by cgl_stage (same layout as cgl_set_state). */

@@ -257,8 +257,12 @@ class State:
         a = np.ascontiguousarray(u, dtype=np.float64).reshape(self.shape)
         check(lib().cgl_set_base_state(self.h, _dptr(a), a.size))
 
-    def get_state(self):
-        a = np.empty(self.shape, dtype=np.float64)
+    def get_state(self, out=None):
+        """The state as float64 [comp][gy][gx]; `out` (C-contiguous float64 of
+        that shape, e.g. pinned host memory) receives it in place."""
+        a = np.empty(self.shape, dtype=np.float64) if out is None else out
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size != self.nc * self.mesh.nny * self.mesh.nnx:
+            raise ValueError("out must be C-contiguous float64 of the state's shape")
         check(lib().cgl_get_state(self.h, _dptr(a), a.size))
         return a
 

@@ -739,29 +739,69 @@ extern "C" cgl_status cgl_set_problem(cgl_state* S, const cgl_problem* p) {
 
 static size_t state_count(const cgl_state* S) { return (size_t)S->nc * (size_t)S->mesh->m.NN; }
 
+// Host copies go through a float64 staging buffer on the device: one DMA
+// copy of the caller's buffer (fast when it is pinned), then the finiteness
+// check and the conversion to the state's precision in kernels.
+static __global__ void k_count_nonfinite(const double* __restrict__ x, long long n,
+                                         unsigned long long* __restrict__ cnt) {
+    unsigned long long c = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        c += !isfinite(x[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
+}
+
+// x -> dst rounded to R (round to nearest), only when no value was non-finite
+template <class R>
+static __global__ void k_import(const double* __restrict__ x, R* __restrict__ dst, long long n,
+                                const unsigned long long* __restrict__ bad) {
+    if (*bad) return;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (R)x[i];
+}
+
+static __global__ void k_export(const float* __restrict__ src, double* __restrict__ y, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (double)src[i];
+}
+
+static unsigned copy_grid(size_t n) { return (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16); }
+
+static cgl_status ensure_stage(cgl_state* S) {
+    if (S->host_stage) return CGL_OK;
+    return dalloc(S, (void**)&S->host_stage, state_count(S) * 8);
+}
+
 static cgl_status upload_nodal(cgl_state* S, void* dst, const double* host, size_t n) {
     if (!S || !host) return fail(CGL_EINVAL, "null argument");
     if (n != state_count(S)) return fail(CGL_EINVAL, "expected %zu values, got %zu", state_count(S), n);
-    for (size_t i = 0; i < n; ++i)
-        if (!std::isfinite(host[i])) return fail(CGL_ENONFINITE, "non-finite input at %zu", i);
-    if (S->prec == CGL_FP64) {
-        CUDA_TRY(cudaMemcpyAsync(dst, host, n * 8, cudaMemcpyHostToDevice, S->st));
-        CUDA_TRY(cudaStreamSynchronize(S->st));
-    } else {
-        std::vector<float> tmp(n);
-        for (size_t i = 0; i < n; ++i) tmp[i] = (float)host[i];
-        CUDA_TRY(cudaMemcpyAsync(dst, tmp.data(), n * 4, cudaMemcpyHostToDevice, S->st));
-        CUDA_TRY(cudaStreamSynchronize(S->st));
-    }
+    cgl_status rc = ensure_stage(S);
+    if (rc) return rc;
+    unsigned long long* bad = &S->B.cnt[CNT_IMPORT];
+    CUDA_TRY(cudaMemcpyAsync(S->host_stage, host, n * 8, cudaMemcpyHostToDevice, S->st));
+    CUDA_TRY(cudaMemsetAsync(bad, 0, 8, S->st));
+    k_count_nonfinite<<<copy_grid(n), 256, 0, S->st>>>(S->host_stage, (long long)n, bad);
+    if (S->prec == CGL_FP64)
+        k_import<double><<<copy_grid(n), 256, 0, S->st>>>(S->host_stage, (double*)dst, (long long)n, bad);
+    else
+        k_import<float><<<copy_grid(n), 256, 0, S->st>>>(S->host_stage, (float*)dst, (long long)n, bad);
+    CUDA_TRY(cudaGetLastError());
+    unsigned long long nbad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&nbad, bad, 8, cudaMemcpyDeviceToHost, S->st));
+    CUDA_TRY(cudaStreamSynchronize(S->st));
+    if (nbad) return fail(CGL_ENONFINITE, "%llu non-finite input values (the state is unchanged)", nbad);
     return CGL_OK;
 }
 
 static cgl_status download_any(cgl_state* S, const void* src, bool bulk, double* host, size_t n) {
     if (bulk && S->prec != CGL_FP64) {
-        std::vector<float> tmp(n);
-        CUDA_TRY(cudaMemcpyAsync(tmp.data(), src, n * 4, cudaMemcpyDeviceToHost, S->st));
+        cgl_status rc = ensure_stage(S);
+        if (rc) return rc;
+        k_export<<<copy_grid(n), 256, 0, S->st>>>((const float*)src, S->host_stage, (long long)n);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(host, S->host_stage, n * 8, cudaMemcpyDeviceToHost, S->st));
         CUDA_TRY(cudaStreamSynchronize(S->st));
-        for (size_t i = 0; i < n; ++i) host[i] = (double)tmp[i];
     } else {
         CUDA_TRY(cudaMemcpyAsync(host, src, n * 8, cudaMemcpyDeviceToHost, S->st));
         CUDA_TRY(cudaStreamSynchronize(S->st));

@@ -29,6 +29,7 @@ struct cgl_state {
     size_t rsz;  // bytes per bulk value
     cudaGraphExec_t step_graph;
     double* diag;       // device partials for diagnostics
+    double* host_stage; // float64 staging of host copies (nc*NN values), allocated at first use
     std::vector<void*> allocs;
 };
 
