@@ -9,19 +9,33 @@ imports, links or calls anything here.
 Parity status per function (what pins it, tests/test_oracle_*.py):
   tables.tables          exact rationals; pinned by partition of unity,
                          closed-form mass entries, derivative identities
-  scheme.cell_averages   pinned by conservation / LO finite-volume identity
+  physics.flux           Euler: Rankine-Hugoniot on exact normal shocks,
+                         Jacobian eigenvalues and the textbook Jacobian;
+                         KPP: the speed of a small perturbation
+  physics.max_speed      an upper bound of the exact Riemann speeds
+  scheme.cell_averages   quadrature mean of u_h; conservation; LO identity
   scheme.low_order_facets, pseudo_time_steps
                          pinned by the LO finite-volume identity and IDP
+  scheme.high_order_facets
+                         face mean of the group flux by quadrature
   scheme.sensor          pinned by special cases (constant, linear and
                          polynomial data give gamma = 1) and a brute-force
                          semi-norm; the candidate construction is a reading
+                         (parity of the exact gamma_e values unpinned)
   scheme.gradient_projection
                          pinned against a dense consistent-mass solve
   scheme.element_residual, fe_stage
                          pinned by brute-force global assembly (Theorem of
                          Sec. 4: MCL with alpha = beta = 1 equals CG-WENO),
-                         zero-sum, conservation, free stream, dt_e
-                         independence and the p+1 convergence rate
-  scheme.flux_limit, slope_limit, euler_alpha
-                         pinned by IDP invariants and closed-form cases
+                         the weak form against a strong-form assembly for
+                         the nonlinear fluxes, f_i^e from eq. (aec) by
+                         quadrature, zero-sum, conservation, free stream,
+                         dt_e independence and the p+1 convergence rate
+  scheme.flux_limit, slope_limit
+                         pinned by IDP invariants, maximality, closed forms
+  scheme.euler_alpha     admissibility and maximality derived from the
+                         definition of the limited state
+  scheme.subcell_time_steps, aec_q1, reduced_time_steps, boundary data
+                         pinned by closed forms and invariants in their
+                         own test files
 """
