@@ -148,7 +148,9 @@ def impl_algorithmic_bytes(kernel, mesh, nc, rsz, k_g, k_u):
         # k_res_s: u, g, gamma, nu, W^e -> element residual; k_facet: u,
         # ubar^{e,L}, dt_e/h, Q, f^L -> ubar^e, facet terms; k_update_el: u,
         # udot, residuals, ubar^e, facet terms, speed sum, means -> increments, beta
-        b["k_res_ev"] = 3 * nc * NN * 4 + 2 * E * d + 2 * E * N2 * nc * 4 if NN >= (1 << 20) else b["k_res_ev"]
+        # (scalars from 2^20 nodes; systems keep the single k_res_ev)
+        b["k_res_ev"] = (3 * nc * NN * 4 + 2 * E * d + 2 * E * N2 * nc * 4 if (NN >= (1 << 20) and nc == 1)
+                         else b["k_res_ev"])
         b["k_facet"] = nc * NN * 4 + (nc + 1) * E * d + (2 + 4 * nc) * E * 4 + nc * E * d + nc * E * 4
         b["k_update_ev"] = (2 * nc * NN * 4 + E * N2 * nc * 4 + nc * E * d + nc * E * 4 + E * 4
                             + 2 * nc * E * 4 + E * N2 * nc * 4 + E * d)

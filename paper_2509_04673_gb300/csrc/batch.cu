@@ -54,7 +54,7 @@ struct BatchSync {
 };
 
 enum { PH_PRE = 0, PH_RES, PH_UPDATE };
-enum { PH_GRAD = 0, PH_SWEEP_G, PH_GATHER_R, PH_SWEEP_U, PH_FINAL };
+enum { PH_GRAD = 0, PH_SWEEP_G, PH_GATHER_R, PH_SWEEP_U, PH_FINAL, PH_GRADF, PH_GATHERF };
 
 constexpr int BT = 128;  // threads per block of the persistent grid
 constexpr int BY = BT / ST_TX;  // node tiles of ST_TX x ST_TY nodes: the block as 32 x BY threads
@@ -63,7 +63,8 @@ constexpr int BY = BT / ST_TX;  // node tiles of ST_TX x ST_TY nodes: the block 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 template <int P>
 constexpr int ws_deg() {
-    return cmax(StFields<float, P, 1, 2>::ws, cmax(StFields<float, P, 2, 1>::ws, StFields<float, P, 1, 1>::ws));
+    return cmax(cmax(StFields<float, P, 1, 2>::ws, cmax(StFields<float, P, 2, 1>::ws, StFields<float, P, 1, 1>::ws)),
+                cmax(GradSweepWs<P, 1>::size, UdotSweepWs<P, 1>::size));
 }
 
 // bounded grid barrier: returns false if it gave up (or another block did)
@@ -140,6 +141,12 @@ __device__ __noinline__ void node_phase(int phase, const InstDev& D, int gx0, in
                                         float* ws) {
     const int tx = threadIdx.x % ST_TX, ty = threadIdx.x / ST_TX;
     switch (phase) {
+        case PH_GRADF:
+            // right-hand side and first sweep in one pass (k carries k_g: b is
+            // kept only when more sweeps follow)
+            grad_sweep_tile<P, 1, BT>(D.m, D.u, k > 1 ? D.bg : nullptr, D.g2, gx0, gy0, threadIdx.x, ws);
+            break;
+        case PH_GATHERF: udot_sweep_tile<P, 1, BT>(D.m, D.ER, D.r, D.ud2, gx0, gy0, threadIdx.x, ws); break;
         case PH_GRAD: grad_tile<float, P, 1, BY>(D.m, D.u, D.bg, D.g, gx0, gy0, tx, ty, ws); break;
         case PH_SWEEP_G:
             if (k & 1) sweep_tile<float, P, 2, BY>(D.m, D.g2, D.bg, D.g, gx0, gy0, tx, ty, ws);
@@ -223,17 +230,29 @@ __global__ void __launch_bounds__(BT, batch_min_blocks(P))
         if (mode_lo && !grid_sync(sync, limit)) return;
     }
     if (!mode_lo) {
-        node_loop<P>(PH_GRAD, I, nt, nnt, a, b, 0, ws);
-        if (!grid_sync(sync, limit)) return;
-        for (int k = 0; k < kg; ++k) {
+        // the right-hand sides and the first Richardson sweeps fused (the
+        // arithmetic of the separate stencils, same bits): two phases and two
+        // grid barriers fewer per stage
+        if (kg >= 1) {
+            node_loop<P>(PH_GRADF, I, nt, nnt, a, b, kg, ws);
+            if (!grid_sync(sync, limit)) return;
+        } else {
+            node_loop<P>(PH_GRAD, I, nt, nnt, a, b, 0, ws);
+            if (!grid_sync(sync, limit)) return;
+        }
+        for (int k = (kg >= 1 ? 1 : 0); k < kg; ++k) {
             node_loop<P>(PH_SWEEP_G, I, nt, nnt, a, b, k, ws);
             if (!grid_sync(sync, limit)) return;
         }
         elem_loop<P>(PH_RES, I, et, net, false, kg, ku);
         if (!grid_sync(sync, limit)) return;
-        node_loop<P>(PH_GATHER_R, I, nt, nnt, a, b, 0, ws);
+        if (ku >= 1) {
+            node_loop<P>(PH_GATHERF, I, nt, nnt, a, b, 0, ws);
+        } else {
+            node_loop<P>(PH_GATHER_R, I, nt, nnt, a, b, 0, ws);
+        }
         if (!grid_sync(sync, limit)) return;
-        for (int k = 0; k < ku; ++k) {
+        for (int k = (ku >= 1 ? 1 : 0); k < ku; ++k) {
             node_loop<P>(PH_SWEEP_U, I, nt, nnt, a, b, k, ws);
             if (!grid_sync(sync, limit)) return;
         }

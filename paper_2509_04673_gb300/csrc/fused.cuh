@@ -297,4 +297,188 @@ __global__ void __launch_bounds__(ST_TX * ST_BY)
     }
 }
 
+// ---------------------------------------------------------------------------
+// The two fused sweeps as functions of one ST_TX x ST_TY node tile for a block
+// of NT threads (the batched stage runs them with 128 threads per block),
+// geometry formed per component: the same arithmetic, in the same order, as
+// k_grad_sweep and k_udot_sweep, hence the same bits as the separate
+// stencils.  ws holds GradSweepWs<P, NC>::size or UdotSweepWs<P, NC>::size
+// floats; the block's threads all call them (they synchronise the block).
+// ---------------------------------------------------------------------------
+template <int P, int NC, int NT>
+DEV void grad_sweep_tile(const MeshDev& m, const float* __restrict__ u, float* __restrict__ bout,
+                         float* __restrict__ gout, int gx0, int gy0, int tid, float* ws) {
+    using WS = GradSweepWs<P, NC>;
+    constexpr int HX1 = WS::HX1, HY1 = WS::HY1, HX2 = WS::HX2, HY2 = WS::HY2, NW = WS::NW, NCL = WS::NCL;
+    constexpr int BYT = NT / ST_TX, NJ = ST_TY / BYT;
+    float(*A)[HX2] = reinterpret_cast<float(*)[HX2]>(ws);
+    float(*tC)[HX1] = reinterpret_cast<float(*)[HX1]>(ws + WS::A);
+    float(*tM)[HX1] = reinterpret_cast<float(*)[HX1]>(ws + WS::A + HY2 * HX1);
+    float(*t)[HY1][ST_TX] = reinterpret_cast<float(*)[HY1][ST_TX]>(ws + WS::A);
+    float(*G)[HY1][HX1] = reinterpret_cast<float(*)[HY1][HX1]>(ws + WS::A + WS::B);
+    float(*Bt)[ST_TY][ST_TX] = reinterpret_cast<float(*)[ST_TY][ST_TX]>(ws + WS::A + WS::B + WS::C);
+    float(*WM)[NW] = reinterpret_cast<float(*)[NW]>(ws + WS::A + WS::B + WS::C + WS::D);
+    float(*WC)[NW] = reinterpret_cast<float(*)[NW]>(ws + WS::A + WS::B + WS::C + WS::D + NCL * NW);
+    const Tab<float>& T = TabSel<float>::t(P);
+    const int tx = tid % ST_TX, ty = tid / ST_TX;
+    __syncthreads();  // the previous user of ws is done
+    if (tid < NCL * NW) {
+        const int cls = tid / NW, k = tid - cls * NW;
+        WM[cls][k] = class_weight<float, P, 0>(T, cls, k - P);
+        WC[cls][k] = class_weight<float, P, 1>(T, cls, k - P);
+    }
+    const float h = m.h_f, h2 = m.h2_f;
+    for (int c = 0; c < NC; ++c) {
+        __syncthreads();
+        for (int i = tid; i < HY2 * HX2; i += NT) {
+            const int r = i / HX2, cc = i - r * HX2;
+            int gx = gx0 - 2 * P + cc, gy = gy0 - 2 * P + r;
+            const bool in = wrap_node(m, gx, gy);
+            A[r][cc] = in ? __ldcg(&u[(long long)c * m.NN + (long long)gy * m.nnx + gx]) : 0.f;
+        }
+        __syncthreads();
+        for (int i = tid; i < HY2 * HX1; i += NT) {
+            const int r = i / HX1, cc = i - r * HX1;
+            int gx = gx0 - P + cc, gy = 0;
+            wrap_node(m, gx, gy);
+            const int clx = node_class<P>(gx, m.nnx, m.px);
+            float sc = 0.f, sm = 0.f;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const float x = A[r][cc + k];
+                sc = fma_r(WC[clx][k], x, sc);
+                sm = fma_r(WM[clx][k], x, sm);
+            }
+            tC[r][cc] = sc;
+            tM[r][cc] = sm;
+        }
+        __syncthreads();
+        for (int i = tid; i < HY1 * HX1; i += NT) {
+            const int r = i / HX1, cc = i - r * HX1;
+            int gx = gx0 - P + cc, gy = gy0 - P + r;
+            const bool in = wrap_node(m, gx, gy);
+            const int clx = node_class<P>(gx, m.nnx, m.px), cly = node_class<P>(gy, m.nny, m.py);
+            float sx = 0.f, sy = 0.f;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                sx = fma_r(WM[cly][k], tC[r + k][cc], sx);
+                sy = fma_r(WC[cly][k], tM[r + k][cc], sy);
+            }
+            const int cnt = (clx == 0 ? 2 : 1) * (cly == 0 ? 2 : 1);
+            const float inv_mi = mul_r(m.inv_me_f, inv_count<float>(cnt));
+            const float bx = mul_r(h, sx), by = mul_r(h, sy);
+            G[0][r][cc] = in ? mul_r(bx, inv_mi) : 0.f;
+            G[1][r][cc] = in ? mul_r(by, inv_mi) : 0.f;
+            const int rt = r - P, ct = cc - P;
+            if (rt >= 0 && rt < ST_TY && ct >= 0 && ct < ST_TX) {
+                Bt[0][rt][ct] = bx;
+                Bt[1][rt][ct] = by;
+            }
+        }
+        __syncthreads();
+        const int gxt = gx0 + tx;
+        const int clxt = node_class<P>(gxt, m.nnx, m.px);
+        for (int r = ty; r < HY1; r += BYT) {
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                float sx = 0.f;
+#pragma unroll
+                for (int k = 0; k < NW; ++k) sx = fma_r(WM[clxt][k], G[f][r][tx + k], sx);
+                t[f][r][tx] = sx;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int r = ty + j * BYT, gy = gy0 + r;
+            if (gxt >= m.nnx || gy >= m.nny) continue;
+            const int cly = node_class<P>(gy, m.nny, m.py);
+            const int cnt = (clxt == 0 ? 2 : 1) * (cly == 0 ? 2 : 1);
+            const float inv_mi = mul_r(m.inv_me_f, inv_count<float>(cnt));
+            const long long node = (long long)gy * m.nnx + gxt;
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                float sy = 0.f;
+#pragma unroll
+                for (int k = 0; k < NW; ++k) sy = fma_r(WM[cly][k], t[f][r + k][tx], sy);
+                const long long k = (long long)(f * NC + c) * m.NN + node;
+                gout[k] = sweep_value(G[f][r + P][tx + P], Bt[f][r][tx], sy, h2, inv_mi);
+                if (bout) bout[k] = Bt[f][r][tx];
+            }
+        }
+    }
+}
+
+template <int P, int NC, int NT>
+DEV void udot_sweep_tile(const MeshDev& m, const float* __restrict__ ER, float* __restrict__ rout,
+                         float* __restrict__ xout, int gx0, int gy0, int tid, float* ws) {
+    using WS = UdotSweepWs<P, NC>;
+    constexpr int HX = WS::HX, HY = WS::HY, NW = WS::NW, NCL = WS::NCL;
+    constexpr int BYT = NT / ST_TX, NJ = ST_TY / BYT;
+    float(*xs)[HY][HX] = reinterpret_cast<float(*)[HY][HX]>(ws);
+    float(*t)[HY][ST_TX] = reinterpret_cast<float(*)[HY][ST_TX]>(ws + NC * HY * HX);
+    float(*rt)[ST_TY][ST_TX] = reinterpret_cast<float(*)[ST_TY][ST_TX]>(ws + NC * (HY * HX + HY * ST_TX));
+    float(*W)[NW] = reinterpret_cast<float(*)[NW]>(ws + NC * (HY * HX + HY * ST_TX + ST_TY * ST_TX));
+    const Tab<float>& T = TabSel<float>::t(P);
+    const int tx = tid % ST_TX, ty = tid / ST_TX;
+    __syncthreads();  // the previous user of ws is done
+    if (tid < NCL * NW) {
+        const int cls = tid / NW, k = tid - cls * NW;
+        W[cls][k] = class_weight<float, P, 0>(T, cls, k - P);
+    }
+    for (int i = tid; i < HY * HX; i += NT) {
+        const int r = i / HX, cc = i - r * HX;
+        int gx = gx0 - P + cc, gy = gy0 - P + r;
+        const bool in = wrap_node(m, gx, gy);
+        float s[NC];
+        float inv_mi = 0.f;
+        if (in) {
+            const NodeC<P> nc = node_c<P>(m, gx, gy);
+            gather_at<float, P, NC>(m, ER, nc, s);
+            inv_mi = PV<float>::inv_me(m) * inv_count<float>(nc.nxc * nc.nyc);
+        }
+        const int rr = r - P, ct = cc - P;
+        const bool tile = rr >= 0 && rr < ST_TY && ct >= 0 && ct < ST_TX;
+        const long long node = (long long)gy * m.nnx + gx;
+#pragma unroll
+        for (int v = 0; v < NC; ++v) {
+            xs[v][r][cc] = in ? s[v] * inv_mi : 0.f;
+            if (tile) {
+                rt[v][rr][ct] = in ? s[v] : 0.f;
+                if (in) rout[v * m.NN + node] = s[v];
+            }
+        }
+    }
+    __syncthreads();
+    const int gx = gx0 + tx;
+    const int clx = node_class<P>(gx, m.nnx, m.px);
+    for (int r = ty; r < HY; r += BYT) {
+#pragma unroll
+        for (int v = 0; v < NC; ++v) {
+            float sx = 0.f;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) sx = fma_r(W[clx][k], xs[v][r][tx + k], sx);
+            t[v][r][tx] = sx;
+        }
+    }
+    __syncthreads();
+    const float h2 = PV<float>::h2(m);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int r = ty + j * BYT, gy = gy0 + r;
+        if (gx >= m.nnx || gy >= m.nny) continue;
+        const int cly = node_class<P>(gy, m.nny, m.py);
+        const int cnt = (clx == 0 ? 2 : 1) * (cly == 0 ? 2 : 1);
+        const float inv_mi = mul_r(PV<float>::inv_me(m), inv_count<float>(cnt));
+        const long long node = (long long)gy * m.nnx + gx;
+#pragma unroll
+        for (int v = 0; v < NC; ++v) {
+            float sy = 0.f;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) sy = fma_r(W[cly][k], t[v][r + k][tx], sy);
+            xout[v * m.NN + node] = sweep_value(xs[v][r + P][tx + P], rt[v][r][tx], sy, h2, inv_mi);
+        }
+    }
+}
+
 }  // namespace cgl
