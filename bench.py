@@ -629,7 +629,7 @@ def run_gpu(args):
     alg = impl_algorithmic_bytes(dom, mesh_h, nc_h, 4, pr["k_g"], pr["k_u"])
     E_h = mesh_h.nx * mesh_h.ny
     roof = {"kernel": dom, "avg_launch_ms": round(avg_ms, 5),
-            "timing": "CUDA events around each launch of a non-graph replay on the launching stream "
+            "timing": "CUDA events around each launch of a non-graph replay serialised on one stream "
                       f"({PROF_STEPS} steps); launches of 0.1 ms or more, so the event gaps are small"}
     ncu = NCU_PER_ELEMENT.get((dom, HEADLINE))
     clk = sampler.summary()

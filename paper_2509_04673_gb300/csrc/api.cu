@@ -483,6 +483,7 @@ extern "C" cgl_status cgl_state_create(const cgl_mesh* mesh, int32_t ncomp, int3
         {&B.EV, 16},                  {&B.ER, E * N2 * nc * r},    {&B.EW, E * N2 * nc * r},     {(void**)&B.q, 2 * E * r},
         {(void**)&B.ue, nc * E * 8},  {(void**)&B.cf, (1 + nc) * E * 4},  {(void**)&B.avg, 2 * nc * E * 4},
         {(void**)&B.fht, nc * E * 4},
+        {(void**)&B.cq, (precision == CGL_FP32_MIXED && nc > 1) ? (2 * nc + 5) * E * 4 : 16},
         {(void**)&B.dte, 3 * E * 8},  {(void**)&B.fl, 4 * nc * E * r},      {(void**)&B.ubl, nc * E * 8}, {(void**)&B.gam, E * 8},
         {(void**)&B.nu, E * 8},       {(void**)&B.ube, nc * E * 8}, {(void**)&B.beta, E * 8},
         {(void**)&B.cnt, CNT_N * 8},  {(void**)&B.dtbits, 8},      {(void**)&B.dt, 8},
@@ -1150,7 +1151,7 @@ extern "C" cgl_status cgl_launches_per_step(cgl_state* S, int64_t* kernels) {
     int64_t per_stage = 1 + 2 + (lo ? 0 : 3 + (S->prob.k_g + S->prob.k_u));
     if (S->prec == CGL_FP32_MIXED && S->nc > 1) per_stage += 2;  // k_avg, k_sens
     if (S->prec == CGL_FP32_MIXED) per_stage += 1;                // k_facet
-    if (S->prec == CGL_FP32_MIXED && !lo && split_residual(S->mesh->m)) per_stage += 1;  // k_res_w beside k_res_s
+    if (S->prec == CGL_FP32_MIXED && !lo && split_residual(S->mesh->m, S->nc)) per_stage += 1;  // k_res_w beside k_res_s
     if (S->prec == CGL_FP32_MIXED && !lo && fuse_sweeps(S->mesh->m) && !(S->prob.options & CGL_OPT_UNFUSED_SWEEPS)) {
         // the first sweep of each solve runs inside k_grad_sweep / k_udot_sweep
         per_stage -= (S->prob.k_g >= 1) + (S->prob.k_u >= 1);

@@ -167,6 +167,7 @@ template <> struct TabSel<float> {
 
 struct PhysAdv {
     static constexpr int NC = 1;
+    static constexpr int NPART_OR_1 = 1;
     template <class T> static DEV void flux(const T* u, T* fx, T* fy, const ProbDev& pr) {
         fx[0] = PV<T>::vx(pr) * u[0];
         fy[0] = PV<T>::vy(pr) * u[0];
@@ -181,6 +182,7 @@ struct PhysAdv {
 
 struct PhysBurgers {
     static constexpr int NC = 1;
+    static constexpr int NPART_OR_1 = 1;
     template <class T> static DEV void flux(const T* u, T* fx, T* fy, const ProbDev&) {
         T f = T(0.5) * u[0] * u[0];
         fx[0] = f;
@@ -248,6 +250,7 @@ HDEV void kpp_sincos(float x, float& s, float& c) {
 
 struct PhysKPP {
     static constexpr int NC = 1;
+    static constexpr int NPART_OR_1 = 1;
     template <class T> static DEV void flux(const T* u, T* fx, T* fy, const ProbDev&) {
         if constexpr (sizeof(T) == 4) {
             kpp_sincos(u[0], fx[0], fy[0]);
@@ -262,14 +265,27 @@ struct PhysKPP {
 
 struct PhysEuler {
     static constexpr int NC = 4;
+    static constexpr int NPART_OR_1 = 5;  // speed parts per cell (speed_parts)
     template <class T> static DEV T pressure(const T* u, T g) {
         return (g - T(1)) * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) / u[0]);
     }
     template <class T> static DEV void flux(const T* u, T* fx, T* fy, const ProbDev& pr) {
         const T g = PV<T>::gam(pr);
         T rho = u[0], mx = u[1], my = u[2], E = u[3];
-        T vx = mx / rho, vy = my / rho;
-        T p = (g - T(1)) * (E - T(0.5) * (mx * mx + my * my) / rho);
+        T vx, vy, p;
+        if constexpr (sizeof(T) == 4) {
+            // float: one correctly rounded reciprocal of rho instead of three
+            // divisions (the flux is evaluated at every quadrature point and
+            // face node of the float kernels)
+            const T r = __frcp_rn(rho);
+            vx = mx * r;
+            vy = my * r;
+            p = (g - T(1)) * (E - T(0.5) * (mx * vx + my * vy));
+        } else {
+            vx = mx / rho;
+            vy = my / rho;
+            p = (g - T(1)) * (E - T(0.5) * (mx * mx + my * my) / rho);
+        }
         fx[0] = mx;
         fx[1] = mx * vx + p;
         fx[2] = my * vx;
@@ -296,10 +312,47 @@ struct PhysEuler {
         T lam3 = vR + aR * sqrt(T(1) + cg * fmax(T(0), (ptr - pR) / pR));
         return fmax(fabs(lam1), fabs(lam3));
     }
+    // max_speed split into its per-cell and per-facet parts (float, interior
+    // facets with normal +x or +y): the cell part holds v_x, v_y, p, the
+    // sound speed a = sqrt(g p / rho) and p^(-(g-1)/(2g)), formed with the
+    // operations max_speed applies to each state; the facet part completes
+    // the two-rarefaction bound from the parts of the left and right cells
+    // along axis 0 (x) or 1 (y)
+    static DEV void speed_parts(const float* u, float g, float* q) {
+        const float rho = u[0];
+        q[0] = (u[1] * 1.f + u[2] * 0.f) / rho;
+        q[1] = (u[1] * 0.f + u[2] * 1.f) / rho;
+        const float p = pressure(u, g);
+        q[2] = p;
+        q[3] = sqrt(g * p / rho);
+        const float expo = (g - 1.f) / (2.f * g);
+        q[4] = pow(p, -expo);
+    }
+    static DEV float facet_speed_parts(const float* L, const float* R, int axis, float g) {
+        const float vL = L[axis], vR = R[axis];
+        const float pL = L[2], pR = R[2], aL = L[3], aR = R[3];
+        const float expo = (g - 1.f) / (2.f * g);
+        const float num = aL + aR - 0.5f * (g - 1.f) * (vR - vL);
+        const float den = aL * L[4] + aR * R[4];
+        const float base = num > 0.f ? fmaxf(num, 0.f) / den : 0.f;
+        const float ptr = pow(base, 1.f / expo);
+        const float cg = (g + 1.f) / (2.f * g);
+        const float lam1 = vL - aL * sqrt(1.f + cg * fmaxf(0.f, (ptr - pL) / pL));
+        const float lam3 = vR + aR * sqrt(1.f + cg * fmaxf(0.f, (ptr - pR) / pR));
+        return fmaxf(fabsf(lam1), fabsf(lam3));
+    }
     template <class T> static DEV T node_speed(const T* u, const ProbDev& pr) {
         const T g = PV<T>::gam(pr);
-        T c = sqrt(fmax(T(0), g * pressure(u, g) / u[0]));
-        return hypot(u[1], u[2]) / u[0] + c;
+        if constexpr (sizeof(T) == 4) {
+            // float: one reciprocal of rho (nu_e takes the largest node speed)
+            const T r = __frcp_rn(u[0]);
+            const T vx = u[1] * r, vy = u[2] * r;
+            const T p = (g - T(1)) * (u[3] - T(0.5) * (u[1] * vx + u[2] * vy));
+            return sqrt(vx * vx + vy * vy) + sqrt(fmax(T(0), g * p * r));
+        } else {
+            T c = sqrt(fmax(T(0), g * pressure(u, g) / u[0]));
+            return hypot(u[1], u[2]) / u[0] + c;
+        }
     }
 };
 

@@ -86,6 +86,28 @@ DEV long long node_of(const MeshDev& m, int ex, int ey, int a, int b) {
     return (long long)gy * m.nnx + gx;
 }
 
+// the global node indices of element (ex, ey), degree P = m.p: the columns
+// and row offsets are formed once per element (only the last column and row
+// can wrap, in a periodic direction), so that each node index is one add;
+// the same indices as node_of
+template <int P>
+struct ElemNodes {
+    int gx[P + 1];
+    long long row[P + 1];
+    DEV ElemNodes(const MeshDev& m, int ex, int ey) {
+#pragma unroll
+        for (int a = 0; a <= P; ++a) gx[a] = ex * P + a;
+        if (m.px && gx[P] == m.nnx) gx[P] = 0;
+#pragma unroll
+        for (int b = 0; b <= P; ++b) {
+            int gy = ey * P + b;
+            if (b == P && m.py && gy == m.nny) gy = 0;
+            row[b] = (long long)gy * m.nnx;
+        }
+    }
+    DEV long long operator()(int a, int b) const { return row[b] + gx[a]; }
+};
+
 // face neighbour (0 W, 1 E, 2 S, 3 N) or -1 on a non-periodic boundary
 DEV int neighbour(const MeshDev& m, int ex, int ey, int dir) {
     int jx = ex, jy = ey;
@@ -192,11 +214,12 @@ template <class R, int P, int NC>
 DEV void load_block(const R* __restrict__ u, const MeshDev& m, int ex, int ey,
                     R (&U)[NC][Dim<P>::N2]) {
     constexpr int N1 = P + 1;
+    const ElemNodes<P> en(m, ex, ey);
 #pragma unroll
     for (int b = 0; b < N1; ++b)
 #pragma unroll
         for (int a = 0; a < N1; ++a) {
-            long long g = node_of(m, ex, ey, a, b);
+            const long long g = en(a, b);
 #pragma unroll
             for (int c = 0; c < NC; ++c) U[c][b * N1 + a] = u[c * m.NN + g];
         }
@@ -419,10 +442,12 @@ DEV void continue_nb(int dir, const R (&src)[Dim<P>::N2], R (&dst)[Dim<P>::N2]) 
 template <class R, int P, class Ph>
 DEV void load_comp(const R* __restrict__ u, const MeshDev& m, int ex, int ey, int c, R (&V)[Dim<P>::N2]) {
     constexpr int N1 = P + 1;
+    const ElemNodes<P> en(m, ex, ey);
+    const R* __restrict__ uc = u + (long long)c * m.NN;
 #pragma unroll
     for (int b = 0; b < N1; ++b)
 #pragma unroll
-        for (int a = 0; a < N1; ++a) V[b * N1 + a] = u[c * m.NN + node_of(m, ex, ey, a, b)];
+        for (int a = 0; a < N1; ++a) V[b * N1 + a] = uc[en(a, b)];
 }
 
 // WENO smoothness sensor gamma_e, eq. (WENO:alpha), minimum over components.
@@ -779,7 +804,7 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
                         double* __restrict__ ubl_out, double* __restrict__ gam_out,
                         double* __restrict__ nu_out, float* __restrict__ q_out,
                         float* __restrict__ fl_out, float* __restrict__ EV, float* __restrict__ cf_out,
-                        float* __restrict__ avg, int ex, int ey, int e) {
+                        float* __restrict__ avg, int ex, int ey, int e, const float* __restrict__ cq = nullptr) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
     static_assert(!LO || NC > 1, "the low-order-only form reads the means of k_avg (systems)");
     int nb[4];
@@ -800,7 +825,20 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
         ued[c] = (double)uh[c] + (double)ul[c];
         ue_out[c * m.E + e] = ued[c];
     }
-    Ph::template flux<float>(uh, fxs, fys, pr);
+    // LO: the fluxes of the means and the speed parts were formed by k_avg
+    constexpr int NQP = LO ? Ph::NPART_OR_1 : 1;
+    float qs[NQP], qn[4][NQP];
+    if constexpr (LO) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            fxs[c] = cq[c * m.E + e];
+            fys[c] = cq[(NC + c) * m.E + e];
+        }
+#pragma unroll
+        for (int k = 0; k < NQP; ++k) qs[k] = cq[(2 * NC + k) * m.E + e];
+    } else {
+        Ph::template flux<float>(uh, fxs, fys, pr);
+    }
     // neighbours: means, fluxes (and, for scalars, the blocks for the sensor)
     float oh[4][NC], ol[4][NC], ofx[4][NC], ofy[4][NC];
     // scalars at p <= 2 keep the neighbour blocks for the sensor; at p >= 3
@@ -817,6 +855,15 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
                     oh[d][c] = avg[(2 * c) * m.E + nb[d]];
                     ol[d][c] = avg[(2 * c + 1) * m.E + nb[d]];
                 }
+                if constexpr (LO) {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        ofx[d][c] = cq[c * m.E + nb[d]];
+                        ofy[d][c] = cq[(NC + c) * m.E + nb[d]];
+                    }
+#pragma unroll
+                    for (int k = 0; k < NQP; ++k) qn[d][k] = cq[(2 * NC + k) * m.E + nb[d]];
+                }
             } else {
                 int jx, jy;
                 neighbour_xy(m, ex, ey, d, jx, jy);
@@ -829,7 +876,7 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
                     for (int i = 0; i < N2; ++i) V1[d][i] = B[0][i];
                 }
             }
-            Ph::template flux<float>(oh[d], ofx[d], ofy[d], pr);
+            if constexpr (!LO) Ph::template flux<float>(oh[d], ofx[d], ofy[d], pr);
         } else {
 #pragma unroll
             for (int c = 0; c < NC; ++c) oh[d][c] = ol[d][c] = ofx[d][c] = ofy[d][c] = 0.f;
@@ -854,7 +901,15 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
             const float* Rl = self_is_L ? ol[d] : ul;
             const float* fL = xf ? (self_is_L ? fxs : ofx[d]) : (self_is_L ? fys : ofy[d]);
             const float* fR = xf ? (self_is_L ? ofx[d] : fxs) : (self_is_L ? ofy[d] : fys);
-            const float l = __fmul_rn(Ph::template max_speed<float>(Lh, Rh, cnx, cny, pr), inflate);
+            float ls;
+            if constexpr (LO) {
+                const float* qL = self_is_L ? qs : qn[d];
+                const float* qR = self_is_L ? qn[d] : qs;
+                ls = Ph::facet_speed_parts(qL, qR, xf ? 0 : 1, PV<float>::gam(pr));
+            } else {
+                ls = Ph::template max_speed<float>(Lh, Rh, cnx, cny, pr);
+            }
+            const float l = __fmul_rn(ls, inflate);
             lam[d] = l;
 #pragma unroll
             for (int c = 0; c < NC; ++c)
@@ -1056,23 +1111,59 @@ DEV double pre_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u, 
 }
 
 // k_avg (FP32-mixed systems): float-float cell means of every element, read
-// by k_pre for the four face neighbours instead of their coefficient blocks;
-// avg[(2c) E + e] = high part, avg[(2c+1) E + e] = low part of component c
-template <int P, int NC>
-__global__ void k_avg(MeshDev m, const float* __restrict__ u, float* __restrict__ avg) {
+// by k_pre_lo for the element and its four face neighbours instead of their
+// coefficient blocks; avg[(2c) E + e] = high part, avg[(2c+1) E + e] = low
+// part of component c.  Beside them the quantities of the mean's state that
+// every facet of the cell needs, formed once per cell: cq[c E + e] = f_x(u^e)
+// and cq[(NC + c) E + e] = f_y(u^e) (the flux of the high parts), then the
+// speed parts of the two-rarefaction bound.
+template <int P, class Ph>
+__global__ void k_avg(MeshDev m, ProbDev pr, const float* __restrict__ u, float* __restrict__ avg,
+                      float* __restrict__ cq) {
     pdl_begin();
     int ex, ey, e;
     if (!elem_of_thread(m, ex, ey, e)) return;
-    constexpr int N2 = Dim<P>::N2;
+    constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
     float U[NC][N2];
     load_block<float, P, NC>(u, m, ex, ey, U);
+    float uh[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         float hi, lo;
         ff_mean<N2>(U[c], hi, lo);
         avg[(2 * c) * m.E + e] = hi;
         avg[(2 * c + 1) * m.E + e] = lo;
+        uh[c] = hi;
     }
+    float fx[NC], fy[NC], q[Ph::NPART_OR_1];
+    Ph::template flux<float>(uh, fx, fy, pr);
+    Ph::speed_parts(uh, PV<float>::gam(pr), q);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        cq[c * m.E + e] = fx[c];
+        cq[(NC + c) * m.E + e] = fy[c];
+    }
+#pragma unroll
+    for (int k = 0; k < Ph::NPART_OR_1; ++k) cq[(2 * NC + k) * m.E + e] = q[k];
+}
+
+// Resident blocks of 128 threads per SM requested from the compiler for the
+// one-thread-per-element kernels (a register cap of 65536 / (128 n)),
+// chosen by measurement on GB300 (time per launch against the uncapped
+// form): FP32-mixed Euler at p = 2 (blast 2048^2 Q2) k_pre_lo 5 (-13 %),
+// k_facet 7 (-25 %), k_res_ev and k_update_el 4 (-8 %, -13 %); at p = 3
+// (quadrants 512^2 Q3) k_pre_lo 5 (-9 %), k_facet 6 (-17 %), the residual
+// and the update uncapped (3 blocks: +18 %, +7 %); the FP64 Euler p = 2
+// residual and update 3; every other instantiation 1 (the compiler's choice).
+enum { EK_PRE_LO = 0, EK_FACET, EK_RES, EK_UPD };
+template <int P, int NC, int RSZ>
+constexpr int elem_blocks(int k) {
+    if (NC > 1 && P == 2) {
+        if (RSZ == 8) return (k == EK_RES || k == EK_UPD) ? 3 : 1;
+        return k == EK_PRE_LO ? 5 : k == EK_FACET ? 7 : 4;
+    }
+    if (NC > 1 && P == 3 && RSZ == 4) return k == EK_PRE_LO ? 5 : k == EK_FACET ? 6 : 1;
+    return 1;
 }
 
 template <class R, int P, class Ph, bool SUB = false>
@@ -1095,16 +1186,16 @@ __global__ void k_pre(MeshDev m, ProbDev pr, const R* __restrict__ u, double* __
 // facet speeds and f^L, dt_e, ubar^{e,L}, the float copies for the facet
 // limiter's certificate); gamma_e and nu_e come from k_sens
 template <int P, class Ph, bool SUB = false>
-__global__ void k_pre_lo(MeshDev m, ProbDev pr, const float* __restrict__ u, double* __restrict__ ue_out,
+__global__ void __launch_bounds__(128, elem_blocks<P, Ph::NC, 4>(EK_PRE_LO)) k_pre_lo(MeshDev m, ProbDev pr, const float* __restrict__ u, double* __restrict__ ue_out,
                          double* __restrict__ dte_out, double* __restrict__ ubl_out,
                          float* __restrict__ fl_out, float* __restrict__ cf_out, float* __restrict__ avg,
-                         unsigned long long* __restrict__ dtbits) {
+                         const float* __restrict__ cq, unsigned long long* __restrict__ dtbits) {
     pdl_wait_then_trigger();
     int ex, ey, e;
     double dte = __longlong_as_double(0x7ff0000000000000LL);
     if (elem_of_thread(m, ex, ey, e))
         dte = pre_at_mixed<P, Ph, SUB, true>(m, pr, u, ue_out, dte_out, ubl_out, nullptr, nullptr, nullptr, fl_out,
-                                             nullptr, cf_out, avg, ex, ey, e);
+                                             nullptr, cf_out, avg, ex, ey, e, cq);
     if (dtbits) block_min_to(dte, dtbits);
 }
 
@@ -1923,6 +2014,7 @@ DEV void stab_part(const MeshDev& m, const R (&U)[Ph::NC][Dim<P>::N2], const R* 
     const R h = PV<R>::h(m);
     // stabilisation s = nu (K u - gamma (Gx gx + Gy gy))
     const R nue = R(nu[e]), ge = R(gam[e]);
+    const ElemNodes<P> en(m, ex, ey);
 #pragma unroll 1
     for (int c = 0; c < NC; ++c) {
         R GX[N2], GY[N2];
@@ -1930,7 +2022,7 @@ DEV void stab_part(const MeshDev& m, const R (&U)[Ph::NC][Dim<P>::N2], const R* 
         for (int b = 0; b < N1; ++b)
 #pragma unroll
             for (int a = 0; a < N1; ++a) {
-                long long n = node_of(m, ex, ey, a, b);
+                const long long n = en(a, b);
                 GX[b * N1 + a] = g[(long long)c * m.NN + n];
                 GY[b * N1 + a] = g[(long long)(NC + c) * m.NN + n];
             }
@@ -1984,7 +2076,7 @@ DEV void res_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u, co
 }
 
 template <class R, int P, class Ph>
-__global__ void __launch_bounds__(128, (Ph::NC > 1 && P == 2) ? 3 : 1) k_res_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ g,
+__global__ void __launch_bounds__(128, elem_blocks<P, Ph::NC, sizeof(R)>(EK_RES)) k_res_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ g,
                          const double* __restrict__ gam, const double* __restrict__ nu,
                          R* __restrict__ ER) {
     pdl_begin();
@@ -2373,6 +2465,7 @@ DEV void element_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][
     R F[NC][N2];
     // components unrolled for p >= 3 (registers); at p <= 2 the rolled loop
     // keeps occupancy higher (measured on the Euler workloads)
+    const ElemNodes<P> en(m, ex, ey);
 #pragma unroll (P >= 3 ? Ph::NC : 1)
     for (int c = 0; c < NC; ++c) {
         R UD[N2];
@@ -2380,7 +2473,7 @@ DEV void element_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][
         for (int b = 0; b < N1; ++b)
 #pragma unroll
             for (int a = 0; a < N1; ++a)
-                UD[b * N1 + a] = ud[(long long)c * m.NN + node_of(m, ex, ey, a, b)];
+                UD[b * N1 + a] = ud[(long long)c * m.NN + en(a, b)];
         R Y[N1][N1];
 #pragma unroll
         for (int d = 0; d < N1; ++d)
@@ -2675,7 +2768,7 @@ __global__ void __launch_bounds__(128) k_q1_update(MeshDev m, ProbDev pr, const 
 // Euler at p = 2: 3 blocks of 128 per SM (a 170-register cap, no spills)
 // instead of the 2 that the uncapped allocation leaves (measured faster)
 template <class R, int P, class Ph>
-__global__ void __launch_bounds__(128, (Ph::NC > 1 && P == 2) ? 3 : 1) k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
+__global__ void __launch_bounds__(128, elem_blocks<P, Ph::NC, sizeof(R)>(EK_UPD)) k_update_ev(MeshDev m, ProbDev pr, const R* __restrict__ u, const R* __restrict__ ud,
                             const double* __restrict__ ue, double* dte_a, const double* __restrict__ ubl,
                             const R* __restrict__ qcap, const R* __restrict__ fl_in,
                             const R* __restrict__ ER, const float* __restrict__ cf,
@@ -2696,7 +2789,7 @@ __global__ void __launch_bounds__(128, (Ph::NC > 1 && P == 2) ? 3 : 1) k_update_
 // kernels; k_update_el then reads its ubar^e and facet terms.  Together they
 // compute what k_update_ev computes, in the same arithmetic.
 template <int P, class Ph>
-__global__ void __launch_bounds__(128) k_facet(MeshDev m, ProbDev pr, const float* __restrict__ u,
+__global__ void __launch_bounds__(128, elem_blocks<P, Ph::NC, 4>(EK_FACET)) k_facet(MeshDev m, ProbDev pr, const float* __restrict__ u,
                                                const double* __restrict__ ue, double* dte_a,
                                                const double* __restrict__ ubl, const float* __restrict__ qcap,
                                                const float* __restrict__ fl_in, float* cf,
@@ -2740,7 +2833,7 @@ __global__ void __launch_bounds__(128) k_facet(MeshDev m, ProbDev pr, const floa
 }
 
 template <int P, class Ph>
-__global__ void __launch_bounds__(128, (Ph::NC > 1 && P == 2) ? 3 : 1)
+__global__ void __launch_bounds__(128, elem_blocks<P, Ph::NC, 4>(EK_UPD))
     k_update_el(MeshDev m, ProbDev pr, const float* __restrict__ u, const float* __restrict__ ud,
                 const double* __restrict__ ue, const double* __restrict__ dte_a, const float* __restrict__ ER,
                 const float* __restrict__ cf, const float* __restrict__ avg, const double* __restrict__ ube,

@@ -23,6 +23,7 @@ struct Bufs {
     void* fl;     // low-order facet fluxes [E][4][NC]         (R)
     float* cf;    // float copies for the Euler limiter certificate [1+NC][E]: s, ubar^{e,L}
     float* avg;   // float-float cell means [2NC][E] (FP32-mixed: k_avg for systems, k_pre for scalars)
+    float* cq;    // FP32-mixed systems: flux of the mean and speed parts per cell [2NC + 5][E] (k_avg)
     float* fht;   // facet terms of f_i^e [NC][E] (FP32-mixed, k_facet -> k_update_el)
     cudaStream_t st2;            // second stream of a stage (k_facet)
     cudaEvent_t ev_fork0, ev_fork, ev_w, ev_join;
@@ -77,9 +78,11 @@ inline bool fuse_sweeps(const MeshDev& m) { return m.NN >= (1LL << 22); }
 
 // The split residual (k_res_w on the second stream, k_res_s) overlaps the
 // quadrature with k_pre and the g_h kernels but adds a kernel and the W^e
-// traffic: measured, it wins on KPP 1024^2 (-4 % per step) and Euler 512^2
-// Q3 (-1 %) and loses slightly at 256^2 (+0.7 %).
-inline bool split_residual(const MeshDev& m) { return m.NN >= (1LL << 20); }
+// traffic: measured, it wins on KPP 1024^2 (-4 % per step) and loses
+// slightly at 256^2 (+0.7 %); for systems (four components: a W^e of four
+// element vectors) the single k_res_ev is faster (Euler blast 2048^2 Q2:
+// 17.0 against 17.8 ms per step).
+inline bool split_residual(const MeshDev& m, int nc) { return nc == 1 && m.NN >= (1LL << 20); }
 
 // Launch with programmatic stream serialisation (pdl): the kernel may be
 // scheduled while the previous kernel of the stream drains and waits for it
@@ -128,24 +131,27 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
     constexpr bool split = sizeof(R) == 4;
     // the Q1 variant of eq. (aecQ1) needs neither g_h, nor the residual, nor udot
     const bool q1 = (pr.opts & OPT_AEC_Q1) != 0 && pr.mode != MODE_LO;
-    const bool split_res = split && split_residual(m) && !q1;
+    const bool split_res = split && split_residual(m, NC) && !q1;
+    // per-launch timing serialises the stage on one stream, so that each
+    // kernel's events bracket its own run and no overlap with the other stream
+    const cudaStream_t s2 = prof ? st : B.st2;
     if (split_res && !dt_only && pr.mode != MODE_LO) {
         chk(cudaEventRecord(B.ev_fork0, st));
-        chk(cudaStreamWaitEvent(B.st2, B.ev_fork0, 0));
+        chk(cudaStreamWaitEvent(s2, B.ev_fork0, 0));
         if constexpr (split)
-            CGL_LAUNCH(prof, KID_RESW, B.st2,
-                       chk(launch(false, k_res_w<P, Ph>, ge, be, B.st2, m, pr, (const float*)u, (float*)B.EW)));
-        chk(cudaEventRecord(B.ev_w, B.st2));
+            CGL_LAUNCH(prof, KID_RESW, s2,
+                       chk(launch(false, k_res_w<P, Ph>, ge, be, s2, m, pr, (const float*)u, (float*)B.EW)));
+        chk(cudaEventRecord(B.ev_w, s2));
     }
     constexpr bool use_avg = sizeof(R) == 4 && NC > 1;
     if constexpr (use_avg)
-        CGL_LAUNCH(prof, KID_AVG, st, chk(launch(pdl, k_avg<P, NC>, ge, be, st, m, (const float*)u, B.avg)));
+        CGL_LAUNCH(prof, KID_AVG, st, chk(launch(pdl, k_avg<P, Ph>, ge, be, st, m, pr, (const float*)u, B.avg, B.cq)));
     if constexpr (use_avg) {
         // mixed systems: the low-order part here, the sensor in k_sens below
         auto* kpre = (pr.opts & OPT_SUBCELL_DT) ? k_pre_lo<P, Ph, true> : k_pre_lo<P, Ph, false>;
         CGL_LAUNCH(prof, KID_PRE, st,
                    chk(launch(pdl, kpre, ge, be, st, m, pr, (const float*)u, B.ue, B.dte, B.ubl, (float*)B.fl, B.cf,
-                              B.avg, first ? B.dtbits : nullptr)));
+                              B.avg, (const float*)B.cq, first ? B.dtbits : nullptr)));
     } else {
         auto* kpre = (pr.opts & OPT_SUBCELL_DT) ? k_pre<R, P, Ph, true> : k_pre<R, P, Ph, false>;
         CGL_LAUNCH(prof, KID_PRE, st,
@@ -164,12 +170,12 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
     if constexpr (split_update) {
         if (!q1) {
             chk(cudaEventRecord(B.ev_fork, st));
-            chk(cudaStreamWaitEvent(B.st2, B.ev_fork, 0));
-            CGL_LAUNCH(prof, KID_FACET, B.st2,
-                       chk(launch(false, k_facet<P, Ph>, ge, be, B.st2, m, pr, (const float*)u, (const double*)B.ue,
+            chk(cudaStreamWaitEvent(s2, B.ev_fork, 0));
+            CGL_LAUNCH(prof, KID_FACET, s2,
+                       chk(launch(false, k_facet<P, Ph>, ge, be, s2, m, pr, (const float*)u, (const double*)B.ue,
                                   B.dte, (const double*)B.ubl, (const float*)B.q, (const float*)B.fl, B.cf, B.ube,
                                   B.fht, B.cnt)));
-            chk(cudaEventRecord(B.ev_join, B.st2));
+            chk(cudaEventRecord(B.ev_join, s2));
         }
     }
     if constexpr (use_avg) {
