@@ -364,6 +364,19 @@ cgl_status cgl_batch_step_async(cgl_batch *batch, int32_t nsteps);
 cgl_status cgl_batch_info(cgl_batch *batch, int32_t *grid, int32_t *block, int32_t *elem_tiles,
                           int32_t *node_tiles, int32_t *graph);
 
+/* How a batch step runs.  CGL_BATCH_PERSISTENT (the default): per SSP-RK
+   stage one persistent cooperative launch for each degree present, its
+   phases separated by bounded grid barriers.  CGL_BATCH_PHASES: the same
+   phases (the same device functions, so the same bits) as one launch each,
+   one block per tile, so that every phase has the register budget of its
+   own code; each degree's launches run on a stream of their own inside the
+   step's graph, so the degrees overlap.  Changing the form waits for the
+   batch's stream and captures a new graph at the next step. */
+#define CGL_BATCH_PERSISTENT 0
+#define CGL_BATCH_PHASES 1
+cgl_status cgl_batch_set_form(cgl_batch *batch, int32_t form);
+cgl_status cgl_batch_get_form(cgl_batch *batch, int32_t *form);
+
 /* Element-tile length per degree (tile_elems[p], p = 1..4, in [1, 128]). */
 cgl_status cgl_batch_set_tiles(cgl_batch *batch, const int32_t *tile_elems);
 cgl_status cgl_batch_get_tiles(cgl_batch *batch, int32_t *tile_elems);
@@ -413,8 +426,9 @@ cgl_status cgl_gradient_noalloc(const cgl_mesh *mesh, const double *u, double *g
    unused identifier. */
 const char *cgl_kernel_name(int32_t id);
 
-/* Run nsteps (1..1000) SSP-RK3 steps launch by launch (no graph) with CUDA
-   events recorded around every kernel on the state's stream; ms[id] and
+/* Run nsteps (1..1000) SSP-RK3 steps launch by launch (no graph, every
+   kernel on the state's stream, the second stream's kernels included, so
+   that no two kernels overlap) with CUDA events around every kernel; ms[id] and
    launches[id] receive the summed device time and the launch count per
    kernel identifier (nk >= 32). The state is advanced like cgl_step. */
 cgl_status cgl_profile(cgl_state *state, int32_t nsteps, int32_t nk, double *ms, int64_t *launches);

@@ -28,6 +28,7 @@ OPT_UNFUSED_SWEEPS = 2
 OPT_SUBCELL_DT = 4
 OPT_AEC_Q1 = 8
 OPT_DTE_REDUCE = 16
+BATCH_PERSISTENT, BATCH_PHASES = 0, 1
 FIELD_UE, FIELD_DTE, FIELD_UBL, FIELD_UBE, FIELD_GAMMA, FIELD_NU, FIELD_BETA = 0, 1, 2, 3, 4, 5, 6
 FIELD_GX, FIELD_GY, FIELD_R, FIELD_UDOT = 16, 17, 18, 19
 
@@ -114,6 +115,8 @@ _PROTOS = [
     ("cgl_batch_autotune", C.c_int, [C.c_void_p, C.c_int32, C.c_char_p]),
     ("cgl_batch_load_tuning", C.c_int, [C.c_void_p, C.c_char_p]),
     ("cgl_batch_debug", C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    ("cgl_batch_set_form", C.c_int, [C.c_void_p, C.c_int32]),
+    ("cgl_batch_get_form", C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     ("cgl_gradient_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("cgl_measure_peaks", C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 ]
@@ -392,6 +395,14 @@ class Batch:
 
     def debug(self, phantom_blocks, spin_limit):
         check(lib().cgl_batch_debug(self.h, int(phantom_blocks), int(spin_limit)))
+
+    def set_form(self, form):
+        check(lib().cgl_batch_set_form(self.h, int(form)))
+
+    def form(self):
+        v = C.c_int32()
+        check(lib().cgl_batch_get_form(self.h, C.byref(v)))
+        return v.value
 
 
 def gradient_noalloc(mesh: Mesh, u_dev_ptr: int, g_dev_ptr: int, stream=None):

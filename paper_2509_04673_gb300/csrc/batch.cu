@@ -276,6 +276,98 @@ static BatchKernel batch_kernel(int p) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// The phase form: the same phases as separate launches, one block per tile
+// of the phase (no grid barrier: the launch boundary orders the phases), so
+// that every phase kernel gets the register budget of its own code. The
+// launches of each degree run on a stream of their own inside the step's
+// graph, so that the degrees overlap; they are programmatic dependent
+// launches (each kernel waits for its predecessor, then lets the next one
+// be scheduled), so a launch's set-up overlaps the tail of the previous one.
+// ---------------------------------------------------------------------------
+template <int P, int PHASE>
+__global__ void __launch_bounds__(BT) k_bph_elem(const InstDev* __restrict__ I, const Tile* __restrict__ et,
+                                                 int first, int kg, int ku) {
+    pdl_wait_then_trigger();
+    const Tile T = et[blockIdx.x];
+    const InstDev& D = I[T.inst];
+    double dte = __longlong_as_double(0x7ff0000000000000LL);
+    if ((int)threadIdx.x < T.count) {
+        const int e = T.begin + threadIdx.x;
+        const int nx = D.m.nx;
+        const int ey = e / nx, ex = e - ey * nx;
+        elem_dispatch<P>(PHASE, D, ex, ey, e, dte, kg, ku);
+    }
+    if (PHASE == PH_PRE && first) block_min_to(dte, D.dtbits);
+}
+
+template <int P, int PHASE>
+__global__ void __launch_bounds__(BT) k_bph_node(const InstDev* __restrict__ I, const Tile* __restrict__ nt,
+                                                 float a, float b, int k) {
+    __shared__ float ws[ws_deg<P>()];
+    pdl_wait_then_trigger();
+    const Tile T = nt[blockIdx.x];
+    node_phase<P>(PHASE, I[T.inst], T.begin, T.count, a, b, k, ws);
+}
+
+// global dt of every instance of the group from its block minima (eq.
+// (cflglob), scaled by omega_CFL, capped at t_end - t)
+__global__ void k_bph_dt(const InstDev* __restrict__ I, int ninst) {
+    pdl_wait_then_trigger();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ninst; i += gridDim.x * blockDim.x) {
+        const InstDev& D = I[i];
+        double d = D.pr.cfl * __longlong_as_double((long long)*D.dtbits);
+        *D.dtbits = 0x7ff0000000000000ull;
+        double rem = *D.t_end - *D.t;
+        if (rem < d) d = rem > 0.0 ? rem : 0.0;
+        *D.dt = d;
+    }
+}
+
+__global__ void k_bph_tadv(const InstDev* __restrict__ I, int ninst) {
+    pdl_wait_then_trigger();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ninst; i += gridDim.x * blockDim.x) *I[i].t += *I[i].dt;
+}
+
+template <int P>
+static cudaError_t bph_stage(const InstDev* I, int ninst, const Tile* et, int net, const Tile* nt, int nnt,
+                             float a, float b, int first, int last, int kg, int ku, int mode_lo, cudaStream_t st) {
+    const dim3 blk(BT);
+    const dim3 gi((ninst + BT - 1) / BT), ge(net), gn(nnt);
+    cudaError_t err = cudaSuccess;
+    auto chk = [&](cudaError_t e) {
+        if (e != cudaSuccess && err == cudaSuccess) err = e;
+    };
+    chk(launch(true, k_bph_elem<P, PH_PRE>, ge, blk, st, I, et, first, kg, ku));
+    if (first) chk(launch(true, k_bph_dt, gi, blk, st, I, ninst));
+    if (!mode_lo) {
+        if (kg >= 1) chk(launch(true, k_bph_node<P, PH_GRADF>, gn, blk, st, I, nt, a, b, kg));
+        else chk(launch(true, k_bph_node<P, PH_GRAD>, gn, blk, st, I, nt, a, b, 0));
+        for (int k = (kg >= 1 ? 1 : 0); k < kg; ++k)
+            chk(launch(true, k_bph_node<P, PH_SWEEP_G>, gn, blk, st, I, nt, a, b, k));
+        chk(launch(true, k_bph_elem<P, PH_RES>, ge, blk, st, I, et, 0, kg, ku));
+        if (ku >= 1) chk(launch(true, k_bph_node<P, PH_GATHERF>, gn, blk, st, I, nt, a, b, 0));
+        else chk(launch(true, k_bph_node<P, PH_GATHER_R>, gn, blk, st, I, nt, a, b, 0));
+        for (int k = (ku >= 1 ? 1 : 0); k < ku; ++k)
+            chk(launch(true, k_bph_node<P, PH_SWEEP_U>, gn, blk, st, I, nt, a, b, k));
+    }
+    chk(launch(true, k_bph_elem<P, PH_UPDATE>, ge, blk, st, I, et, 0, kg, ku));
+    chk(launch(true, k_bph_node<P, PH_FINAL>, gn, blk, st, I, nt, a, b, 0));
+    if (last) chk(launch(true, k_bph_tadv, gi, blk, st, I, ninst));
+    return err;
+}
+
+typedef cudaError_t (*PhaseStage)(const InstDev*, int, const Tile*, int, const Tile*, int, float, float, int, int, int,
+                                  int, int, cudaStream_t);
+static PhaseStage phase_stage(int p) {
+    switch (p) {
+        case 1: return bph_stage<1>;
+        case 2: return bph_stage<2>;
+        case 3: return bph_stage<3>;
+        default: return bph_stage<4>;
+    }
+}
+
 cudaError_t upload_batch(const Tab<double>* td, const Tab<float>* tf, const double* a2d, const float* a2f) {
     return upload_tables_here(td, tf, a2d, a2f);
 }
@@ -293,6 +385,8 @@ struct DegreeGroup {
     int net, nnt;
     BatchSync* d_sync;
     int grid;
+    cudaStream_t gst;  // the phase form: this degree's stream
+    cudaEvent_t ev;    // the phase form: end of this degree's step
 };
 
 struct cgl_batch {
@@ -305,6 +399,8 @@ struct cgl_batch {
     int mode_lo, kg, ku;
     long long limit;
     int phantom;
+    int form;  // CGL_BATCH_PERSISTENT or CGL_BATCH_PHASES
+    cudaEvent_t ev_fork;
     cudaGraphExec_t graph;
     bool use_graph;
     cudaError_t graph_err;  // why the capture failed (cudaSuccess: not failed)
@@ -354,9 +450,24 @@ static cudaError_t launch_stage(cgl_batch* B, DegreeGroup& G, float a, float b, 
 }
 
 // one step: three stages, each a persistent launch per degree present
+// (persistent form), or each degree's phase launches on its own stream,
+// forked from and joined back to the batch's stream (phase form)
 static cudaError_t enqueue_batch_step(cgl_batch* B) {
     const float sa[3] = {0.f, 0.75f, 1.f / 3.f}, sb[3] = {1.f, 0.25f, 2.f / 3.f};
     cudaError_t e = cudaSuccess;
+    if (B->form == CGL_BATCH_PHASES) {
+        e = cudaEventRecord(B->ev_fork, B->st);
+        for (DegreeGroup& G : B->groups) {
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(G.gst, B->ev_fork, 0);
+            const int ninst = (int)G.members.size();
+            for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+                e = phase_stage(G.p)(G.d_inst, ninst, G.d_et, G.net, G.d_nt, G.nnt, sa[k], sb[k], k == 0, k == 2,
+                                     B->kg, B->ku, B->mode_lo, G.gst);
+            if (e == cudaSuccess) e = cudaEventRecord(G.ev, G.gst);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(B->st, G.ev, 0);
+        }
+        return e;
+    }
     for (int k = 0; k < 3 && e == cudaSuccess; ++k)
         for (DegreeGroup& G : B->groups) {
             e = launch_stage(B, G, sa[k], sb[k], k == 0, k == 2);
@@ -407,7 +518,10 @@ extern "C" void cgl_batch_destroy(cgl_batch* B) {
         if (G.d_et) cudaFree(G.d_et);
         if (G.d_nt) cudaFree(G.d_nt);
         if (G.d_sync) cudaFree(G.d_sync);
+        if (G.gst) cudaStreamDestroy(G.gst);
+        if (G.ev) cudaEventDestroy(G.ev);
     }
+    if (B->ev_fork) cudaEventDestroy(B->ev_fork);
     delete B;
 }
 
@@ -479,6 +593,8 @@ extern "C" cgl_status cgl_batch_create(cgl_state* const* states, int32_t n, cgl_
     B->use_graph = true;
     B->graph_err = cudaSuccess;
     B->graph = nullptr;
+    B->form = CGL_BATCH_PERSISTENT;
+    B->ev_fork = nullptr;
     for (int p = 0; p <= PMAX; ++p) B->tile_elems[p] = BT;
     int nsm = 0;
     cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s0->device);
@@ -504,12 +620,19 @@ extern "C" cgl_status cgl_batch_create(cgl_state* const* states, int32_t n, cgl_
         if (e == cudaSuccess) e = cudaMemsetAsync(G.d_sync, 0, sizeof(BatchSync), B->st);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)batch_kernel(p), BT, 0);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G.gst, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming);
         B->groups.push_back(G);
         if (e != cudaSuccess || per_sm < 1) {
             cgl_batch_destroy(B);
             return bfail(CGL_ECUDA, "batch allocation or occupancy query", e);
         }
         B->groups.back().grid = nsm * per_sm;
+    }
+    e = cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cgl_batch_destroy(B);
+        return bfail(CGL_ECUDA, "batch event", e);
     }
     cgl_status rc = build_tiles(B);
     if (rc) {
@@ -586,6 +709,28 @@ extern "C" cgl_status cgl_batch_info(cgl_batch* B, int32_t* grid, int32_t* block
     if (graph) *graph = B->graph ? 1 : (B->graph_err != cudaSuccess ? -1 : 0);
     if (B->graph_err != cudaSuccess)
         set_error(CGL_OK, "graph capture failed (direct launches): %s", cudaGetErrorString(B->graph_err));
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_batch_set_form(cgl_batch* B, int32_t form) {
+    if (!B || (form != CGL_BATCH_PERSISTENT && form != CGL_BATCH_PHASES)) return bfail(CGL_EINVAL, "bad argument");
+    if (form != B->form) {
+        cudaError_t e = cudaStreamSynchronize(B->st);
+        if (e != cudaSuccess) return bfail(CGL_ECUDA, "batch form", e);
+        B->form = form;
+        if (B->graph) {
+            cudaGraphExecDestroy(B->graph);
+            B->graph = nullptr;
+        }
+        B->use_graph = true;
+        B->graph_err = cudaSuccess;
+    }
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_batch_get_form(cgl_batch* B, int32_t* form) {
+    if (!B || !form) return bfail(CGL_EINVAL, "null argument");
+    *form = B->form;
     return CGL_OK;
 }
 

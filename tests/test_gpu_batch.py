@@ -1,6 +1,6 @@
 """Batched persistent stage (many uneven instances, one cooperative launch per
-SSP stage under a CUDA graph): every batched instance must evolve bitwise
-like the same state stepped alone, tile lengths must not change results,
+SSP stage under a CUDA graph) and its phase form (one launch per phase): every
+batched instance must evolve bitwise like the same state stepped alone, tile lengths must not change results,
 the invariant domain must hold, the barrier timeout must surface as
 CGL_ETIMEOUT without any fault, and the autotuner must persist its choice.
 """
@@ -54,7 +54,8 @@ def _states(C, cases):
     return st
 
 
-def test_batch_bitwise_equals_single(cgl):
+@pytest.mark.parametrize("form", [0, 1])
+def test_batch_bitwise_equals_single(cgl, form):
     cases = _small_instances()
     singles = _states(cgl, cases)
     ref = []
@@ -63,6 +64,8 @@ def test_batch_bitwise_equals_single(cgl):
         ref.append(s.get_state())
     states = _states(cgl, cases)
     b = cgl.Batch(states)
+    b.set_form(form)
+    assert b.form() == form
     viol = b.step(3)
     assert viol == 0
     for s, r in zip(states, ref):
@@ -71,6 +74,7 @@ def test_batch_bitwise_equals_single(cgl):
     # different tile lengths, same results
     states2 = _states(cgl, cases)
     b2 = cgl.Batch(states2)
+    b2.set_form(form)
     b2.set_tiles([0, 17, 64, 5, 128])
     b2.step(3)
     for s, r in zip(states2, ref):
@@ -131,6 +135,14 @@ def test_config4_batch_full(cgl):
     states = _states(cgl, cases)
     b = cgl.Batch(states)
     assert b.step(2) == 0
+    # the phase form continues the same instances bitwise like the persistent form
+    states_b = _states(cgl, cases)
+    bb = cgl.Batch(states_b)
+    assert bb.step(1) == 0
+    bb.set_form(cgl.BATCH_PHASES)
+    assert bb.step(1) == 0
+    for sa, sb in zip(states, states_b):
+        assert np.array_equal(sa.get_state(), sb.get_state())
     picks = {}
     for k, (mesh, prob, u0) in enumerate(cases):
         picks.setdefault((mesh.p, prob.flux), k)
