@@ -40,6 +40,8 @@ MODE_LO = 0
 MODE_HO = 1
 MODE_WENO = 2
 MODE_WENO_L = 3
+# element basis: Bernstein (the paper's) or Lagrange at the LGL points
+BASIS_BERNSTEIN, BASIS_LGL = 0, 1
 
 FP64 = 0
 FP32_MIXED = 1
@@ -82,6 +84,7 @@ class Mesh:
     y1: float = 1.0
     bc_x: int = BC_PERIODIC
     bc_y: int = BC_PERIODIC
+    basis: int = BASIS_BERNSTEIN
 
     @property
     def nnx(self) -> int:
@@ -136,14 +139,31 @@ class Problem:
         return d
 
 
+def _lobatto_offsets(p: int) -> np.ndarray:
+    """Positions in [0, 1] of the p + 1 Legendre-Gauss-Lobatto points
+    (0, 1 and the roots of P_p', by numpy's root finder), ascending; used
+    only to place the nodal points of LGL meshes."""
+    if p == 1:
+        return np.array([0.0, 1.0])
+    inner = np.sort(np.real(np.polynomial.legendre.Legendre.basis(p).deriv().roots()))
+    return 0.5 * (np.concatenate(([-1.0], inner, [1.0])) + 1.0)
+
+
 def node_coords(mesh: Mesh):
-    """Physical coordinates of the nodal points, arrays of shape (nny, nnx)."""
+    """Physical coordinates of the nodal points, arrays of shape (nny, nnx):
+    the uniform points x0 + k h/p for Bernstein meshes, the LGL points of
+    each element for LGL meshes."""
     h = mesh.h
     hy = (mesh.y1 - mesh.y0) / mesh.ny
     gx = np.arange(mesh.nnx)
     gy = np.arange(mesh.nny)
-    x = mesh.x0 + gx * (h / mesh.p)
-    y = mesh.y0 + gy * (hy / mesh.p)
+    if getattr(mesh, "basis", BASIS_BERNSTEIN) == BASIS_LGL:
+        off = _lobatto_offsets(mesh.p)
+        x = mesh.x0 + ((gx // mesh.p) + off[gx % mesh.p]) * h
+        y = mesh.y0 + ((gy // mesh.p) + off[gy % mesh.p]) * hy
+    else:
+        x = mesh.x0 + gx * (h / mesh.p)
+        y = mesh.y0 + gy * (hy / mesh.p)
     return np.meshgrid(x, y, indexing="xy")
 
 

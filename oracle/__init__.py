@@ -38,4 +38,11 @@ Parity status per function (what pins it, tests/test_oracle_*.py):
   scheme.subcell_time_steps, aec_q1, reduced_time_steps, boundary data
                          pinned by closed forms and invariants in their
                          own test files
+  tables.lgl_points, lgl_tables, and the LGL basis of OracleMesh (basis 1:
+  Lagrange at the Lobatto points, m_i^e = |K| w_a w_b, face weights w_a)
+                         closed-form Lobatto points and weights, exactness
+                         to degree 2p - 1, tables against the independent
+                         product formula, Q1 equal to Bernstein Q1, u^e,
+                         f^H and f_i^e by brute force, conservation, free
+                         stream, invariant domain, optimal HO rate
 """

@@ -38,7 +38,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import physics as ph
-from .tables import tables
+from .tables import basis_tables
 
 BC_PERIODIC, BC_OUTFLOW, BC_FIXED, BC_WALL = 0, 1, 2, 3
 OPT_SUBCELL_DT = 4
@@ -65,14 +65,20 @@ def op2(Ax: np.ndarray, Ay: np.ndarray) -> np.ndarray:
 
 
 class OracleMesh:
-    """Index sets of a uniform nx x ny mesh of degree-p Bernstein squares
-    (Table 1 of the paper: N_e, E_i, B_e) and dense element operators."""
+    """Index sets of a uniform nx x ny mesh of degree-p squares (Table 1 of
+    the paper: N_e, E_i, B_e) and dense element operators.  The basis is the
+    paper's Bernstein basis, or (basis 1) the Lagrange basis at the LGL
+    points, the collocated spectral-element basis of the concluding section:
+    the scheme is written with m_i^e = int phi_i throughout, so the same
+    stage runs on either basis with its own tables, lumped masses and face
+    weights."""
 
     def __init__(self, mesh, nq=None):
         """nq: Gauss points per direction for the integrals of nonlinear
         functions (default p + 2, reading R7; the pins use a high-order rule
         to compare the weak form with a strong-form assembly)."""
         m = mesh if isinstance(mesh, dict) else mesh.as_dict()
+        self.basis = int(m.get("basis", 0))
         self.nx, self.ny, self.p = int(m["nx"]), int(m["ny"]), int(m["p"])
         self.x0, self.x1, self.y0, self.y1 = m["x0"], m["x1"], m["y0"], m["y1"]
         self.bc_x, self.bc_y = int(m["bc_x"]), int(m["bc_y"])
@@ -131,9 +137,6 @@ class OracleMesh:
         self.fE = EY * self.nfx + ((EX + 1) % nx if self.px else EX + 1)
         self.fS = EX * self.nfy + EY          # y-facets stored [ex, j]
         self.fN = EX * self.nfy + ((EY + 1) % ny if self.py else EY + 1)
-        # lumped masses m_i^e = |K| / (p+1)^2 and m_i = sum_{e in E_i} m_i^e (Sec. 3)
-        self.me = self.h * self.h / self.n2
-        self.mi = np.bincount(self.conn.ravel(), minlength=self.N) * self.me
         # local node lists of the four faces (position along the face = index)
         a_idx = np.arange(n)
         self.face_nodes = {
@@ -141,9 +144,38 @@ class OracleMesh:
             "S": 0 * n + a_idx, "N": p * n + a_idx,
         }
         self._ops(nq)
+        # lumped masses m_i^e = int_{K_e} phi_i and m_i = sum_{e in E_i} m_i^e
+        # (Sec. 3).  Bernstein: |K| / (p+1)^2 for every i (kept as the scalar
+        # me); LGL: |K| w_a w_b with the LGL weights, per local node (me_i).
+        if self.basis == 0:
+            self.me = self.h * self.h / self.n2
+            self.me_i = np.full(self.n2, self.me)
+            self.mi = np.bincount(self.conn.ravel(), minlength=self.N) * self.me
+            # (m_i^e / |K_e|) |S| = h / (p+1)^2: the weight of the facet fluxes in eq. (aecb)
+            self.kface = np.full(self.n2, self.h / self.n2)
+        else:
+            wl = self.T["wl"]
+            self.me_i = self.h * self.h * np.outer(wl, wl).ravel()   # index b*n + a
+            self.me = self.me_i
+            self.mi = np.bincount(self.conn.ravel(), weights=np.tile(self.me_i, self.E), minlength=self.N)
+            self.kface = self.h * np.outer(wl, wl).ravel()
+        self.xn = self.T["xn"]
+
+    def cell_mean(self, U):
+        """(1/|K_e|) sum_i m_i^e U_i over the last axis (n2 values)."""
+        if self.basis == 0:
+            return U.mean(axis=-1)
+        return U @ (self.me_i / (self.h * self.h))
+
+    def face_mean(self, F):
+        """(1/|S|) int_S f_h over one face from the values of f at its p + 1
+        nodes (last axis): Bernstein 1/(p+1) each, LGL the weights w_a."""
+        if self.basis == 0:
+            return F.mean(axis=-1)
+        return F @ self.T["wl"]
 
     def _ops(self, nq=None):
-        T = tables(self.p, nq)
+        T = basis_tables(self.p, nq, self.basis)
         self.T = T
         h, p, n = self.h, self.p, self.n1
         M, C, D = T["M"], T["C"], T["D"]
@@ -264,8 +296,9 @@ def external_state(side, spec, hi, Uin):
 
 
 def cell_averages(om: OracleMesh, U):
-    """u^e = (1/|K_e|) sum_i m_i^e u_i = mean of the (p+1)^2 coefficients, eq. (ueold)."""
-    return U.mean(axis=2)
+    """u^e = (1/|K_e|) sum_i m_i^e u_i, eq. (ueold): the mean of the (p+1)^2
+    Bernstein coefficients, the LGL-weighted mean of the nodal values."""
+    return om.cell_mean(U)
 
 
 def facet_states(om: OracleMesh, ue, prob, t=0.0):
@@ -373,6 +406,8 @@ def subcell_time_steps(om: OracleMesh, U, prob):
     nodes (Q1): u_0^e = u^e, m_0^e = |K_e| and s = 2 (the lemma's second
     case).  Readings: a node term with zero speed is dropped, and the sum is
     floored at lambda_floor |S| (as eq. (dtmaxcell) floors its speed sum)."""
+    if om.basis != 0:
+        raise ValueError("the subcell bound of Lemma 1 is stated for Bernstein elements")
     kind = prob["flux"]
     p, n, h = om.p, om.n1, om.h
     nc = U.shape[0]
@@ -564,12 +599,16 @@ def high_order_facets(om: OracleMesh, u, prob, t=0.0):
     # x-facets [ey, i]: face nodes gx = i p, gy = ey p + b
     GX = (np.arange(om.nfx) * p) % om.nnx
     GY = np.arange(ny)[:, None] * p + b[None, :]
-    # positions along a side: the unwrapped node index of the face (x_e + k h/p)
-    posy = om.y0 + GY * hn
+    # positions along a side: the unwrapped node of the face, x_e + k h/p
+    # (Bernstein) or x_e + xn_k h (LGL)
+    if om.basis == 0:
+        posy = om.y0 + GY * hn
+    else:
+        posy = om.y0 + (np.arange(ny)[:, None] + om.xn[None, :]) * om.h
     if om.py:
         GY = GY % om.nny
     Uf = uu[:, GY[:, None, :], GX[None, :, None]]            # (nc, ny, nfx, p+1)
-    Fx = ph.normal_flux(kind, Uf, 1.0, 0.0, prob).mean(axis=-1)
+    Fx = om.face_mean(ph.normal_flux(kind, Uf, 1.0, 0.0, prob))
     if not om.px:
         for side, i, sgn in (("W", 0, -1.0), ("E", nx, 1.0)):
             spec = tab[side]
@@ -578,15 +617,18 @@ def high_order_facets(om: OracleMesh, u, prob, t=0.0):
             Ub = Uf[:, :, i, :]
             ext = external_state(side, spec, side_hi(spec, posy, t), Ub)
             Fj, _ = ph.llf(kind, Ub, ext, sgn, 0.0, prob)
-            Fx[:, :, i] = sgn * Fj.mean(axis=-1)
+            Fx[:, :, i] = sgn * om.face_mean(Fj)
     # y-facets [ex, j]: face nodes gy = j p, gx = ex p + b
     GY = (np.arange(om.nfy) * p) % om.nny
     GX = np.arange(nx)[:, None] * p + b[None, :]
-    posx = om.x0 + GX * hn
+    if om.basis == 0:
+        posx = om.x0 + GX * hn
+    else:
+        posx = om.x0 + (np.arange(nx)[:, None] + om.xn[None, :]) * om.h
     if om.px:
         GX = GX % om.nnx
     Uf = uu[:, GY[None, :, None], GX[:, None, :]]            # (nc, nx, nfy, p+1)
-    Fy = ph.normal_flux(kind, Uf, 0.0, 1.0, prob).mean(axis=-1)
+    Fy = om.face_mean(ph.normal_flux(kind, Uf, 0.0, 1.0, prob))
     if not om.py:
         for side, j, sgn in (("S", 0, -1.0), ("N", ny, 1.0)):
             spec = tab[side]
@@ -595,7 +637,7 @@ def high_order_facets(om: OracleMesh, u, prob, t=0.0):
             Ub = Uf[:, :, j, :]
             ext = external_state(side, spec, side_hi(spec, posx, t), Ub)
             Fj, _ = ph.llf(kind, Ub, ext, 0.0, sgn, prob)
-            Fy[:, :, j] = sgn * Fj.mean(axis=-1)
+            Fy[:, :, j] = sgn * om.face_mean(Fj)
     return Fx.reshape(nc, -1), Fy.reshape(nc, -1)
 
 
@@ -793,7 +835,7 @@ def fe_stage(mesh, prob, u, dt, t=0.0):
         fHsum = outward_sum(om, FHx, FHy)
         # eq. (aec) with eq. (aecb) folded in (see element_residual)
         fie = me * (U - ue[:, :, None]) + dte[None, :, None] * (
-            Rl + (om.h / om.n2) * fHsum[:, :, None] - UD @ om.Mass2.T + me * UD)
+            Rl + om.kface * fHsum[:, :, None] - UD @ om.Mass2.T + me * UD)
         if mode == MODE_WENO_L:
             beta = slope_limit(om, fie, ube, prob)
         else:

@@ -120,7 +120,87 @@ def tables(p: int, nq: int | None = None) -> dict:
             Em[b, a] = float(bm[b])
     return dict(p=p, nq=nq, M=M, C=C, D=D, S=S, xq=xq, wq=wq, Bq=Bq, dBq=dBq, Ep=Ep, Em=Em,
                 B1=np.array([poly_eval_exact(polys[a], 1.0) for a in range(n)]),
-                B0=np.array([poly_eval_exact(polys[a], 0.0) for a in range(n)]))
+                B0=np.array([poly_eval_exact(polys[a], 0.0) for a in range(n)]),
+                wl=np.full(n, 1.0 / n), xn=np.arange(n) / p, basis="bernstein")
+
+
+# ---------------------------------------------------------------------------
+# Lagrange basis at the Legendre-Gauss-Lobatto points (the collocated LGL
+# spectral-element basis the paper's concluding section names as the next
+# step).  The nodes on [-1, 1] are -1, 1 and the roots of P_p'; the weights
+# are 2 / (p (p + 1) P_p(x_j)^2).  The polynomials are held as float64
+# monomial coefficients (numpy.polynomial.polynomial, a library primitive);
+# every integral is an exact Gauss-Legendre sum of a polynomial of degree
+# at most 2p, so each table entry is accurate to rounding.
+# ---------------------------------------------------------------------------
+def lgl_points(p: int):
+    """LGL nodes and weights on [0, 1] (weights sum to 1), ascending."""
+    P = np.polynomial.legendre.Legendre.basis(p)
+    inner = np.sort(np.real(P.deriv().roots())) if p >= 2 else np.zeros(0)
+    xs = np.concatenate(([-1.0], inner, [1.0]))
+    # one Newton polish of the interior roots on P_p'
+    dP, d2P = P.deriv(), P.deriv(2)
+    for _ in range(3):
+        xs[1:-1] = xs[1:-1] - dP(xs[1:-1]) / d2P(xs[1:-1])
+    w = 2.0 / (p * (p + 1) * P(xs) ** 2)
+    return 0.5 * (xs + 1.0), 0.5 * w
+
+
+def lagrange_polys(xn):
+    """Monomial coefficients (ascending) of the Lagrange polynomials l_a
+    with l_a(xn[b]) = delta_ab."""
+    npoly = np.polynomial.polynomial
+    out = []
+    for a in range(len(xn)):
+        c = np.array([1.0])
+        for b in range(len(xn)):
+            if b != a:
+                c = npoly.polymul(c, np.array([-xn[b], 1.0]) / (xn[a] - xn[b]))
+        out.append(c)
+    return out
+
+
+@lru_cache(maxsize=None)
+def lgl_tables(p: int, nq: int | None = None) -> dict:
+    """The tables of ``tables`` for the Lagrange basis at the LGL points:
+    same keys and meanings with l_a in place of B_a; Ep[b, a] = l_a(xn[b] - 1)
+    and Em[b, a] = l_a(xn[b] + 1) (a Lagrange coefficient is the value at
+    the node); wl[a] = int_0^1 l_a (the LGL weight); xn the nodes."""
+    if nq is None:
+        nq = p + 2
+    npoly = np.polynomial.polynomial
+    xn, wl = lgl_points(p)
+    L = lagrange_polys(xn)
+    n = p + 1
+    xg, wg = np.polynomial.legendre.leggauss(p + 2)      # exact to degree 2p + 3
+    xg, wg = 0.5 * (xg + 1.0), 0.5 * wg
+
+    def der(c, k):
+        return npoly.polyder(c, k) if k > 0 else c
+
+    def integ(c1, c2):
+        return float(np.dot(wg, npoly.polyval(xg, c1) * npoly.polyval(xg, c2)))
+
+    M = np.array([[integ(L[a], L[b]) for b in range(n)] for a in range(n)])
+    C = np.array([[integ(der(L[a], 1), L[b]) for b in range(n)] for a in range(n)])
+    D = np.array([[integ(der(L[a], 1), der(L[b], 1)) for b in range(n)] for a in range(n)])
+    S = np.array([[[integ(der(L[a], k), der(L[b], k)) for b in range(n)] for a in range(n)]
+                  for k in range(p + 1)])
+    xq, wq = np.polynomial.legendre.leggauss(nq)
+    xq, wq = 0.5 * (xq + 1.0), 0.5 * wq
+    Bq = np.array([[npoly.polyval(x, L[a]) for a in range(n)] for x in xq])
+    dBq = np.array([[npoly.polyval(x, der(L[a], 1)) for a in range(n)] for x in xq])
+    Ep = np.array([[npoly.polyval(xn[b] - 1.0, L[a]) for a in range(n)] for b in range(n)])
+    Em = np.array([[npoly.polyval(xn[b] + 1.0, L[a]) for a in range(n)] for b in range(n)])
+    return dict(p=p, nq=nq, M=M, C=C, D=D, S=S, xq=xq, wq=wq, Bq=Bq, dBq=dBq, Ep=Ep, Em=Em,
+                B1=np.array([npoly.polyval(1.0, L[a]) for a in range(n)]),
+                B0=np.array([npoly.polyval(0.0, L[a]) for a in range(n)]),
+                wl=wl, xn=xn, basis="lgl")
+
+
+def basis_tables(p: int, nq: int | None = None, basis: int = 0) -> dict:
+    """Tables of the Bernstein basis (basis 0) or the LGL Lagrange basis (1)."""
+    return lgl_tables(p, nq) if basis == 1 else tables(p, nq)
 
 
 def bern_eval(p: int, a: int, x: np.ndarray, k: int = 0) -> np.ndarray:

@@ -2,14 +2,46 @@
 
 Everything here is written from the definitions in Sec. 2 of the paper,
 independently of oracle/: basis functions evaluated from the Bernstein
-formula, global matrices assembled element by element with a high-order
-Gauss rule from scipy, and the Galerkin form a(v, u) taken in its STRONG
-form  sum_e int_K v div f(u_h)  (the oracle uses the weak form with face
-terms; the two agree only if both are right)."""
-from math import comb
+formula (or, for LGL meshes, the Lagrange product formula at the textbook
+closed-form Lobatto points), global matrices assembled element by element
+with a high-order Gauss rule from scipy, and the Galerkin form a(v, u) taken
+in its STRONG form  sum_e int_K v div f(u_h)  (the oracle uses the weak form
+with face terms; the two agree only if both are right)."""
+from math import comb, sqrt
 
 import numpy as np
 from scipy.special import roots_legendre
+
+# Legendre-Gauss-Lobatto points and weights on [0, 1] in closed form
+# (textbook values: Simpson for p = 2; +-1/sqrt(5) and +-sqrt(3/7) on [-1, 1])
+LOBATTO = {
+    1: ([0.0, 1.0], [0.5, 0.5]),
+    2: ([0.0, 0.5, 1.0], [1 / 6, 2 / 3, 1 / 6]),
+    3: ([0.0, 0.5 * (1 - 1 / sqrt(5)), 0.5 * (1 + 1 / sqrt(5)), 1.0], [1 / 12, 5 / 12, 5 / 12, 1 / 12]),
+    4: ([0.0, 0.5 * (1 - sqrt(3 / 7)), 0.5, 0.5 * (1 + sqrt(3 / 7)), 1.0],
+        [1 / 20, 49 / 180, 16 / 45, 49 / 180, 1 / 20]),
+}
+
+
+def lagr(p, a, x, k=0):
+    """k-th derivative (k <= 1) of the Lagrange polynomial l_a at the
+    Lobatto points of degree p, from the product formula."""
+    xn = LOBATTO[p][0]
+    x = np.asarray(x, dtype=np.float64)
+    others = [b for b in range(p + 1) if b != a]
+    if k == 0:
+        out = np.ones_like(x)
+        for b in others:
+            out = out * (x - xn[b]) / (xn[a] - xn[b])
+        return out
+    out = np.zeros_like(x)
+    for c in others:
+        term = np.full_like(x, 1.0 / (xn[a] - xn[c]))
+        for b in others:
+            if b != c:
+                term = term * (x - xn[b]) / (xn[a] - xn[b])
+        out = out + term
+    return out
 
 
 def bern(p, a, x, k=0):
@@ -22,8 +54,9 @@ def bern(p, a, x, k=0):
 
 
 class Brute:
-    def __init__(self, nx, ny, p, x0, x1, y0, y1, periodic, nq=None):
+    def __init__(self, nx, ny, p, x0, x1, y0, y1, periodic, nq=None, basis=0):
         self.nx, self.ny, self.p = nx, ny, p
+        self.basis = basis
         self.h = (x1 - x0) / nx
         self.x0, self.y0 = x0, y0
         self.periodic = periodic
@@ -51,14 +84,27 @@ class Brute:
         p = self.p
         return [(a, b) for b in range(p + 1) for a in range(p + 1)]
 
+    def phi1(self, a, x, k=0):
+        """1D basis function a (or its derivative) at reference points."""
+        return lagr(self.p, a, x, k) if self.basis == 1 else bern(self.p, a, x, k)
+
+    def mass_e(self, a, b):
+        """m_i^e = int_K phi_i for local node (a, b): |K|/(p+1)^2 (Bernstein)
+        or |K| w_a w_b (LGL)."""
+        if self.basis == 1:
+            w = LOBATTO[self.p][1]
+            return self.h * self.h * w[a] * w[b]
+        return self.h * self.h / (self.p + 1) ** 2
+
     def basis_at(self, xi, eta):
         """values, d/dx, d/dy of all local basis functions at reference points."""
         p, h = self.p, self.h
+        f = self.phi1
         out = []
         for (a, b) in self.local():
-            v = bern(p, a, xi) * bern(p, b, eta)
-            dx = bern(p, a, xi, 1) * bern(p, b, eta) / h
-            dy = bern(p, a, xi) * bern(p, b, eta, 1) / h
+            v = f(a, xi) * f(b, eta)
+            dx = f(a, xi, 1) * f(b, eta) / h
+            dy = f(a, xi) * f(b, eta, 1) / h
             out.append((v, dx, dy))
         return out
 

@@ -1,9 +1,10 @@
 """Brute-force pins of the oracle's stage intermediates on small meshes (CPU).
 
 Each intermediate is recomputed here from its defining integral with the
-basis functions evaluated from the Bernstein formula and a high-order Gauss
-rule (tests/bruteforce.py), element by element, independently of the
-oracle's tables and operator algebra:
+basis functions evaluated from the Bernstein formula, or for LGL meshes the
+Lagrange product formula at the closed-form Lobatto points, and a high-order
+Gauss rule (tests/bruteforce.py), element by element, independently of the
+oracle's tables and operator algebra (m_i^e = int phi_i per node):
   * u^e = (1/|K_e|) int_K u_h, eq. (ueold);
   * f^H_ee' = (1/|S|) int_S f_h . n with the group flux f_h = sum_j f(u_j)
     phi_j, eq. (hoflux), for every flux (Euler included);
@@ -30,8 +31,8 @@ def _flux(kind, U, prob):
     return np.asarray(fx), np.asarray(fy)
 
 
-def _case(kind, p):
-    mesh = Mesh(3, 3, p)  # periodic
+def _case(kind, p, basis=0):
+    mesh = Mesh(3, 3, p, basis=basis)  # periodic
     if kind == inputs.FLUX_EULER:
         prob = Problem(flux=kind, mode=inputs.MODE_WENO, flux_limiter=S.FL_NONE)
         u = inputs.random_euler_state(mesh, 90 + p)
@@ -45,11 +46,12 @@ def _case(kind, p):
 FLUXES = [inputs.FLUX_ADVECTION, inputs.FLUX_BURGERS, inputs.FLUX_KPP, inputs.FLUX_EULER]
 
 
+@pytest.mark.parametrize("basis", [0, 1])
 @pytest.mark.parametrize("kind", FLUXES)
 @pytest.mark.parametrize("p", [1, 2, 3])
-def test_cell_averages_by_quadrature(kind, p):
-    mesh, prob, u = _case(kind, p)
-    bf = Brute(mesh.nx, mesh.ny, p, mesh.x0, mesh.x1, mesh.y0, mesh.y1, True, nq=NQ)
+def test_cell_averages_by_quadrature(kind, p, basis):
+    mesh, prob, u = _case(kind, p, basis)
+    bf = Brute(mesh.nx, mesh.ny, p, mesh.x0, mesh.x1, mesh.y0, mesh.y1, True, nq=NQ, basis=basis)
     xi, eta, W = bf.quad2()
     B = bf.basis_at(xi, eta)
     nc = u.shape[0]
@@ -64,17 +66,18 @@ def test_cell_averages_by_quadrature(kind, p):
             assert abs(info["ue"][c, e] - avg) <= 1e-14 * max(1.0, abs(avg))
 
 
+@pytest.mark.parametrize("basis", [0, 1])
 @pytest.mark.parametrize("kind", FLUXES)
 @pytest.mark.parametrize("p", [1, 2, 3])
-def test_high_order_facet_fluxes_by_quadrature(kind, p):
+def test_high_order_facet_fluxes_by_quadrature(kind, p, basis):
     """f^H on every canonical facet (x-facets: normal +x at x = i h; y-facets:
     +y at y = j h) as the face mean of the group flux."""
-    mesh, prob, u = _case(kind, p)
+    mesh, prob, u = _case(kind, p, basis)
     om = S.OracleMesh(mesh)
     FHx, FHy = S.high_order_facets(om, u, prob)
     nc = u.shape[0]
     uf = u.reshape(nc, -1)
-    bf = Brute(mesh.nx, mesh.ny, p, mesh.x0, mesh.x1, mesh.y0, mesh.y1, True, nq=NQ)
+    bf = Brute(mesh.nx, mesh.ny, p, mesh.x0, mesh.x1, mesh.y0, mesh.y1, True, nq=NQ, basis=basis)
     s = bf.xq
     # face of element (ex, ey) at its west side (xi = 0) is the canonical
     # x-facet (ey, ex); its south side (eta = 0) the y-facet (ex, ey)
@@ -90,10 +93,11 @@ def test_high_order_facet_fluxes_by_quadrature(kind, p):
             assert np.abs(val - mean).max() <= 1e-13 * max(1.0, np.abs(mean).max()), (side, val, mean)
 
 
+@pytest.mark.parametrize("basis", [0, 1])
 @pytest.mark.parametrize("kind", FLUXES)
 @pytest.mark.parametrize("p", [1, 2])
-def test_element_contributions_from_eq_aec(kind, p):
-    mesh, prob, u = _case(kind, p)
+def test_element_contributions_from_eq_aec(kind, p, basis):
+    mesh, prob, u = _case(kind, p, basis)
     nc = u.shape[0]
     # the same high-order rule on both sides for the integrals of f(u_h)
     # (the stage's default p + 2 points are exact only for polynomial fluxes)
@@ -102,11 +106,11 @@ def test_element_contributions_from_eq_aec(kind, p):
     fie, dte, gam, nu = info["fie"], info["dte"], info["gamma"], info["nu"]
     ue = info["ue"]
     gx, gy, ud = info["gx"], info["gy"], info["udot"]
-    bf = Brute(mesh.nx, mesh.ny, p, mesh.x0, mesh.x1, mesh.y0, mesh.y1, True, nq=NQ)
+    bf = Brute(mesh.nx, mesh.ny, p, mesh.x0, mesh.x1, mesh.y0, mesh.y1, True, nq=NQ, basis=basis)
     xi, eta, W = bf.quad2()
     B = bf.basis_at(xi, eta)
     h = bf.h
-    me = h * h / (p + 1) ** 2
+    loc = bf.local()
     uf = u.reshape(nc, -1)
     for ex, ey in bf.elements():
         e = ey * mesh.nx + ex
@@ -129,6 +133,7 @@ def test_element_contributions_from_eq_aec(kind, p):
         udq = np.array([sum(UD[c, l] * B[l][0] for l in range(n2)) for c in range(nc)])
         for i in range(n2):
             v, vx, vy = B[i]
+            me = bf.mass_e(*loc[i])
             vol = np.sum(W * (vx * (fxq - fhx) + vy * (fyq - fhy)), axis=1)
             div = np.sum(W * (v - me / (h * h)) * divfh, axis=1)
             stab = nu[e] * np.sum(W * (vx * (uxq - gam[e] * gxq) + vy * (uyq - gam[e] * gyq)), axis=1)
