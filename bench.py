@@ -726,8 +726,9 @@ def _share(prof):
 
 def run_batch(cgl, torch, stream, flush, K, W, world, rank, dist, timed, hbm_peak, hbm_src):
     """The 256-instance batch, FP32-mixed, one persistent launch per stage
-    under a CUDA graph; with several ranks each takes its share of the
-    instances (a disjoint deterministic split, no exchange)."""
+    under a CUDA graph, then the phase form on the same instances; with
+    several ranks each takes its share of the instances (a disjoint
+    deterministic split, no exchange)."""
     import inputs
     from paper_2509_04673_gb300.partition import partition_instances
     cases = inputs.batched_instances()
@@ -746,19 +747,34 @@ def run_batch(cgl, torch, stream, flush, K, W, world, rank, dist, timed, hbm_pea
     ms = timed(lambda: b.step_async(1), K)
     viol = b.step(0)
     info = b.info()
+    # the phase form (one launch per phase, degrees on their own streams) on
+    # the same instances, continuing from the state the persistent form left
+    b.set_form(cgl.BATCH_PHASES)
+    b.step(W)
+    ms_ph = timed(lambda: b.step_async(1), K)
+    viol_ph = b.step(0)
+    info_ph = b.info()
     nd = sum(sizes[i] for i in mine)
     nd_all = sum(sizes)
     # method bytes: DOF-weighted over the instances' degrees (k_g = k_u = 1)
     bm = sum(method_bytes_per_dof_stage(cases[i][0].p, 4, 1, 1) * sizes[i] for i in mine) / nd
     rate = nd_all * 3 * K / (ms * 1e-3)
     ach = rate / world * bm / 1e9
+    rate_ph = nd_all * 3 * K / (ms_ph * 1e-3)
+    ach_ph = rate_ph / world * bm / 1e9
     res = {"config": {"workload": BATCH, "instances": len(cases), "sizes": "16^2..128^2 periodic",
                       "degrees": "1..4", "fluxes": "advection or Burgers", "mode": "WENO-L + flux limiter"},
            "n_dof": nd_all, "value": rate, "ms_per_step": ms / K, "scaling": "strong (instances split over ranks)",
            "graph": info["graph"], "grid": info["grid"], "block": info["block"],
            "roofline": {"bytes_per_dof_stage": round(bm, 2), "achieved": round(ach, 1), "peak": hbm_peak,
                         "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "peak_source": hbm_src},
-           "violations": int(viol)}
+           "violations": int(viol),
+           "form": "persistent: one cooperative launch per degree and stage",
+           "phase_form": {"value": rate_ph, "ms_per_step": ms_ph / K, "graph": info_ph["graph"],
+                          "form": "one launch per phase, each degree on its own stream in the step graph",
+                          "roofline": {"achieved": round(ach_ph, 1), "peak": hbm_peak, "unit": "GB/s",
+                                       "frac": round(ach_ph / hbm_peak, 4)},
+                          "violations": int(viol_ph) - int(viol)}}
     b.close()
     for s in states:
         s.close()

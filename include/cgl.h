@@ -88,11 +88,23 @@ typedef struct cgl_mesh cgl_mesh;
 typedef struct cgl_state cgl_state;
 
 /* Uniform mesh of nx x ny squares on [x0,x1] x [y0,y1] (Sec. 2.1, Table 1 of
-   the paper). Requires (x1-x0)/nx == (y1-y0)/ny, 1 <= p <= 4, nx, ny >= 1. */
+   the paper). Requires (x1-x0)/nx == (y1-y0)/ny, 1 <= p <= 4, nx, ny >= 1.
+   basis: CGL_BASIS_BERNSTEIN (0, the paper's basis) or CGL_BASIS_LGL (1):
+   the Lagrange basis at the Legendre-Gauss-Lobatto points, the collocated
+   spectral-element basis the paper's concluding section names as the next
+   step.  On an LGL mesh the state holds nodal values at the LGL points of
+   every element (node gx at x0 + (gx / p + xn[gx % p]) h, xn the Lobatto
+   points on [0, 1]); the stage is the same with m_i^e = |K| w_a w_b (the
+   LGL weights) in every lumped mass, cell average and face average.  LGL
+   meshes run in the FP64 form only and take neither CGL_OPT_SUBCELL_DT (the
+   subcell bound of Lemma 1 is stated for Bernstein elements) nor
+   CGL_OPT_AEC_Q1 (CGL_EINVAL). */
+#define CGL_BASIS_BERNSTEIN 0
+#define CGL_BASIS_LGL 1
 typedef struct cgl_mesh_desc {
     int32_t nx, ny, p;
     int32_t bc_x, bc_y;
-    int32_t reserved;
+    int32_t basis;
     double x0, x1, y0, y1;
 } cgl_mesh_desc;
 
@@ -199,6 +211,11 @@ cgl_status cgl_problem_defaults(cgl_problem *p, int32_t flux);
    ((p+2)(p+1) each, [q][a]) and the semi-norm matrix A ((p+1)^4, [i][j]).
    n must be at least the total count, returned in *needed. */
 cgl_status cgl_debug_tables(int32_t p, double *out, size_t n, size_t *needed);
+
+/* The same export for either basis (CGL_BASIS_BERNSTEIN or CGL_BASIS_LGL),
+   followed by the weights int_0^1 phi_a and the node positions on [0, 1]
+   (p+1 each). */
+cgl_status cgl_debug_basis_tables(int32_t p, int32_t basis, double *out, size_t n, size_t *needed);
 
 /* --- mesh ---------------------------------------------------------------- */
 

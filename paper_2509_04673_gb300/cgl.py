@@ -29,13 +29,14 @@ OPT_SUBCELL_DT = 4
 OPT_AEC_Q1 = 8
 OPT_DTE_REDUCE = 16
 BATCH_PERSISTENT, BATCH_PHASES = 0, 1
+BASIS_BERNSTEIN, BASIS_LGL = 0, 1
 FIELD_UE, FIELD_DTE, FIELD_UBL, FIELD_UBE, FIELD_GAMMA, FIELD_NU, FIELD_BETA = 0, 1, 2, 3, 4, 5, 6
 FIELD_GX, FIELD_GY, FIELD_R, FIELD_UDOT = 16, 17, 18, 19
 
 
 class cgl_mesh_desc(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("p", C.c_int32), ("bc_x", C.c_int32),
-                ("bc_y", C.c_int32), ("reserved", C.c_int32), ("x0", C.c_double),
+                ("bc_y", C.c_int32), ("basis", C.c_int32), ("x0", C.c_double),
                 ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double)]
 
 
@@ -81,6 +82,8 @@ _PROTOS = [
     ("cgl_version", C.c_char_p, []),
     ("cgl_problem_defaults", C.c_int, [C.POINTER(cgl_problem), C.c_int32]),
     ("cgl_debug_tables", C.c_int, [C.c_int32, C.POINTER(C.c_double), C.c_size_t, C.POINTER(C.c_size_t)]),
+    ("cgl_debug_basis_tables", C.c_int,
+     [C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_size_t, C.POINTER(C.c_size_t)]),
     ("cgl_mesh_create", C.c_int, [C.POINTER(cgl_mesh_desc), C.POINTER(C.c_void_p)]),
     ("cgl_mesh_destroy", None, [C.c_void_p]),
     ("cgl_mesh_sizes", C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
@@ -183,7 +186,8 @@ def boundary_struct(bnd) -> cgl_boundary:
 class Mesh:
     def __init__(self, mesh):
         d = mesh if isinstance(mesh, dict) else mesh.as_dict()
-        desc = cgl_mesh_desc(int(d["nx"]), int(d["ny"]), int(d["p"]), int(d["bc_x"]), int(d["bc_y"]), 0,
+        desc = cgl_mesh_desc(int(d["nx"]), int(d["ny"]), int(d["p"]), int(d["bc_x"]), int(d["bc_y"]),
+                             int(d.get("basis", 0)),
                              float(d["x0"]), float(d["x1"]), float(d["y0"]), float(d["y1"]))
         h = C.c_void_p()
         check(lib().cgl_mesh_create(C.byref(desc), C.byref(h)))
@@ -328,17 +332,17 @@ class State:
         return a
 
 
-def debug_tables(p: int) -> dict:
-    """The library's host tables of degree p (no GPU needed)."""
+def debug_tables(p: int, basis: int = 0) -> dict:
+    """The library's host tables of degree p on the given basis (no GPU needed)."""
     need = C.c_size_t()
-    check(lib().cgl_debug_tables(p, None, 0, C.byref(need)))
+    check(lib().cgl_debug_basis_tables(p, basis, None, 0, C.byref(need)))
     buf = np.empty(need.value)
-    check(lib().cgl_debug_tables(p, _dptr(buf), buf.size, None))
+    check(lib().cgl_debug_basis_tables(p, basis, _dptr(buf), buf.size, None))
     n1, nq = p + 1, p + 2
     out, k = {}, 0
     for name, shape in (("M", (n1, n1)), ("C", (n1, n1)), ("D", (n1, n1)), ("Ep", (n1, n1)),
                         ("Em", (n1, n1)), ("xq", (nq,)), ("wq", (nq,)), ("Bq", (nq, n1)),
-                        ("dBq", (nq, n1)), ("A2", (n1 * n1, n1 * n1))):
+                        ("dBq", (nq, n1)), ("A2", (n1 * n1, n1 * n1)), ("wl", (n1,)), ("xn", (n1,))):
         sz = int(np.prod(shape))
         out[name] = buf[k:k + sz].reshape(shape)
         k += sz

@@ -146,11 +146,176 @@ static void continuation(int p, int side, double out[N1MAX][N1MAX]) {
 }
 
 struct HostTables {
-    Tab<double> td[PMAX + 1];
+    Tab<double> td[NTABD];  // Bernstein at p, LGL at PMAX + 1 + p
     Tab<float> tf[PMAX + 1];
-    double a2d[A2_TOTAL];
+    double a2d[2 * A2_TOTAL];
     float a2f[A2_TOTAL];
 };
+
+// ---------------------------------------------------------------------------
+// Lagrange basis at the Legendre-Gauss-Lobatto points of degree p: nodes
+// 0, 1 and the roots of P_p' (Newton on the derivative of the three-term
+// recurrence from Chebyshev-Gauss-Lobatto guesses), weights
+// 2 / (p (p+1) P_p(x)^2) on [-1, 1]; l_a evaluated by the product formula
+// and its derivatives from the monomial coefficients built from the roots.
+// ---------------------------------------------------------------------------
+static void legendre_and_derivs(int n, double z, double& P, double& dP, double& d2P) {
+    double p0 = 1.0, p1 = z;
+    if (n == 0) {
+        P = 1.0;
+        dP = d2P = 0.0;
+        return;
+    }
+    for (int k = 2; k <= n; ++k) {
+        const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+    }
+    P = p1;
+    // (1 - z^2) P' = n (P_{n-1} - z P_n); (1 - z^2) P'' = 2 z P' - n (n+1) P
+    dP = n * (p0 - z * p1) / (1.0 - z * z);
+    d2P = (2.0 * z * dP - n * (n + 1.0) * p1) / (1.0 - z * z);
+}
+
+static void lobatto(int p, double* x, double* w) {
+    // on [-1, 1], ascending
+    x[0] = -1.0;
+    x[p] = 1.0;
+    for (int j = 1; j < p; ++j) {
+        double z = -std::cos(M_PI * j / p);
+        for (int it = 0; it < 100; ++it) {
+            double P, dP, d2P;
+            legendre_and_derivs(p, z, P, dP, d2P);
+            const double dz = dP / d2P;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[j] = z;
+    }
+    for (int j = 0; j <= p; ++j) {
+        double P, dP, d2P;
+        if (j == 0 || j == p) {
+            P = (j == 0 && (p % 2)) ? -1.0 : 1.0;
+        } else {
+            legendre_and_derivs(p, x[j], P, dP, d2P);
+        }
+        w[j] = 2.0 / (p * (p + 1.0) * P * P);
+    }
+    // to [0, 1]; symmetric pairs made exactly symmetric
+    for (int j = 0; j <= p; ++j) {
+        x[j] = 0.5 * (x[j] + 1.0);
+        w[j] = 0.5 * w[j];
+    }
+    for (int j = 0; j <= p / 2; ++j) {
+        const double wa = 0.5 * (w[j] + w[p - j]);
+        w[j] = w[p - j] = wa;
+        x[p - j] = 1.0 - x[j];
+    }
+}
+
+// monomial coefficients (ascending) of l_a for the nodes xn[0..p]
+static void lagrange_coeffs(int p, const double* xn, int a, double* c) {
+    for (int k = 0; k <= p; ++k) c[k] = 0.0;
+    c[0] = 1.0;
+    int deg = 0;
+    for (int b = 0; b <= p; ++b) {
+        if (b == a) continue;
+        const double inv = 1.0 / (xn[a] - xn[b]);
+        // c <- c * (x - xn[b]) * inv
+        for (int k = deg + 1; k >= 0; --k) {
+            const double lo = (k >= 1) ? c[k - 1] : 0.0;
+            const double hi = (k <= deg) ? c[k] : 0.0;
+            c[k] = (lo - xn[b] * hi) * inv;
+        }
+        ++deg;
+    }
+}
+
+static double poly_eval(int deg, const double* c, double x) {
+    double s = 0.0;
+    for (int k = deg; k >= 0; --k) s = s * x + c[k];
+    return s;
+}
+
+// k-th derivative coefficients of a degree-p polynomial
+static void poly_deriv(int p, const double* c, int k, double* out) {
+    for (int j = 0; j <= p; ++j) out[j] = 0.0;
+    for (int j = k; j <= p; ++j) {
+        double f = 1.0;
+        for (int i = 0; i < k; ++i) f *= (j - i);
+        out[j - k] = c[j] * f;
+    }
+}
+
+static void build_lgl_tables(int p, Tab<double>& T, double* a2) {
+    const int n = p + 1, nq = p + 2;
+    double xn[N1MAX], wl[N1MAX];
+    lobatto(p, xn, wl);
+    double L[N1MAX][N1MAX];
+    for (int a = 0; a < n; ++a) lagrange_coeffs(p, xn, a, L[a]);
+    // integrals of products of derivatives: Gauss-Legendre with p + 2 points
+    // (exact to degree 2p + 3)
+    double xg[NQMAX + 1], wg[NQMAX + 1];
+    gauss_legendre(nq, xg, wg);
+    std::vector<std::vector<double>> S(p + 1, std::vector<double>(n * n, 0.0));
+    double V[PMAX + 1][N1MAX][NQMAX];  // V[k][a][q] = l_a^(k)(x_q)
+    for (int k = 0; k <= p; ++k)
+        for (int a = 0; a < n; ++a) {
+            double dc[N1MAX];
+            poly_deriv(p, L[a], k, dc);
+            for (int q = 0; q < nq; ++q) V[k][a][q] = poly_eval(p, dc, 0.5 * (xg[q] + 1.0));
+        }
+    for (int k = 0; k <= p; ++k)
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) {
+                double s = 0.0;
+                for (int q = 0; q < nq; ++q) s += 0.5 * wg[q] * V[k][a][q] * V[k][b][q];
+                S[k][a * n + b] = s;
+            }
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+            double c = 0.0;
+            for (int q = 0; q < nq; ++q) c += 0.5 * wg[q] * V[1][a][q] * V[0][b][q];
+            T.M[a][b] = S[0][a * n + b];
+            T.C[a][b] = c;
+            T.D[a][b] = S[1][a * n + b];
+        }
+    // continuation: a Lagrange coefficient is the value at the node, so the
+    // east neighbour's l_a continued onto [0, 1] has coefficient l_a(xn_b - 1)
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+            T.Ep[b][a] = poly_eval(p, L[a], xn[b] - 1.0);
+            T.Em[b][a] = poly_eval(p, L[a], xn[b] + 1.0);
+        }
+    for (int q = 0; q < nq; ++q) {
+        const double x = 0.5 * (xg[q] + 1.0);
+        T.wq[q] = 0.5 * wg[q];
+        T.xq[q] = x;
+        double dc[N1MAX];
+        for (int a = 0; a < n; ++a) {
+            T.Bq[q][a] = poly_eval(p, L[a], x);
+            poly_deriv(p, L[a], 1, dc);
+            T.dBq[q][a] = poly_eval(p, dc, x);
+        }
+    }
+    for (int a = 0; a < n; ++a) {
+        T.wl[a] = wl[a];
+        T.iwl[a] = 1.0 / wl[a];
+        T.xn[a] = xn[a];
+    }
+    // semi-norm matrix of eq. (WENO:norm) in this basis
+    const int n2 = n * n;
+    for (int i = 0; i < n2 * n2; ++i) a2[i] = 0.0;
+    for (int k1 = 0; k1 <= p; ++k1)
+        for (int k2 = 0; k2 <= p; ++k2) {
+            if (k1 + k2 < 1 || k1 + k2 > p) continue;
+            for (int b = 0; b < n; ++b)
+                for (int a = 0; a < n; ++a)
+                    for (int d = 0; d < n; ++d)
+                        for (int c = 0; c < n; ++c)
+                            a2[(b * n + a) * n2 + d * n + c] += S[k1][a * n + c] * S[k2][b * n + d];
+        }
+}
 
 static void semi_norm_blocks(int p, std::vector<std::vector<double>>& S) {
     // S[k][a*(p+1)+b] = int B_a^(k) B_b^(k), with
@@ -188,6 +353,11 @@ static void build_tables(HostTables& H) {
             }
         continuation(p, +1, T.Ep);
         continuation(p, -1, T.Em);
+        for (int a = 0; a < n; ++a) {
+            T.wl[a] = 1.0 / n;
+            T.iwl[a] = (double)n;
+            T.xn[a] = (double)a / p;
+        }
         double xg[NQMAX], wg[NQMAX];
         gauss_legendre(nq, xg, wg);
         for (int q = 0; q < nq; ++q) {
@@ -221,6 +391,7 @@ static void build_tables(HostTables& H) {
         for (size_t i = 0; i < sizeof(Tab<double>) / sizeof(double); ++i) dst[i] = (float)src[i];
     }
     for (int i = 0; i < A2_TOTAL; ++i) H.a2f[i] = (float)H.a2d[i];
+    for (int p = 1; p <= PMAX; ++p) build_lgl_tables(p, H.td[PMAX + 1 + p], H.a2d + A2_TOTAL + A2_OFF[p]);
 }
 
 static const HostTables& host_tables() {
@@ -241,6 +412,24 @@ cudaError_t upload_host_tables(UploadFn f) {
 }
 }  // namespace cgl
 
+static cgl_status cgl_debug_tables_of(int p, int basis, double* out);
+
+extern "C" cgl_status cgl_debug_basis_tables(int32_t p, int32_t basis, double* out, size_t n, size_t* needed) {
+    if (p < 1 || p > PMAX) return fail(CGL_EINVAL, "degree p=%d outside [1,%d]", p, PMAX);
+    if (basis != CGL_BASIS_BERNSTEIN && basis != CGL_BASIS_LGL) return fail(CGL_EINVAL, "unknown basis %d", basis);
+    const int n1 = p + 1, nq = p + 2, n2 = n1 * n1;
+    const size_t base = 5 * n1 * n1 + 2 * nq + 2 * nq * n1 + n2 * n2;
+    const size_t need = base + 2 * n1;
+    if (needed) *needed = need;
+    if (!out) return CGL_OK;
+    if (n < need) return fail(CGL_EINVAL, "buffer too small: %zu < %zu", n, need);
+    cgl_status rc = cgl_debug_tables_of(p, basis, out);
+    const Tab<double>& T = host_tables().td[basis ? PMAX + 1 + p : p];
+    for (int a = 0; a < n1; ++a) out[base + a] = T.wl[a];
+    for (int a = 0; a < n1; ++a) out[base + n1 + a] = T.xn[a];
+    return rc;
+}
+
 extern "C" cgl_status cgl_debug_tables(int32_t p, double* out, size_t n, size_t* needed) {
     if (p < 1 || p > PMAX) return fail(CGL_EINVAL, "degree p=%d outside [1,%d]", p, PMAX);
     const int n1 = p + 1, nq = p + 2, n2 = n1 * n1;
@@ -248,8 +437,15 @@ extern "C" cgl_status cgl_debug_tables(int32_t p, double* out, size_t n, size_t*
     if (needed) *needed = need;
     if (!out) return CGL_OK;
     if (n < need) return fail(CGL_EINVAL, "buffer too small: %zu < %zu", n, need);
+    return cgl_debug_tables_of(p, CGL_BASIS_BERNSTEIN, out);
+}
+
+// the tables of cgl_debug_tables for degree p on the given basis into out
+static cgl_status cgl_debug_tables_of(int p, int basis, double* out) {
+    const int n1 = p + 1, nq = p + 2, n2 = n1 * n1;
     const HostTables& H = host_tables();
-    const Tab<double>& T = H.td[p];
+    const Tab<double>& T = H.td[basis ? PMAX + 1 + p : p];
+    const double* A2 = H.a2d + (basis ? A2_TOTAL : 0) + A2_OFF[p];
     size_t k = 0;
     for (int a = 0; a < n1; ++a) for (int b = 0; b < n1; ++b) out[k++] = T.M[a][b];
     for (int a = 0; a < n1; ++a) for (int b = 0; b < n1; ++b) out[k++] = T.C[a][b];
@@ -262,7 +458,7 @@ extern "C" cgl_status cgl_debug_tables(int32_t p, double* out, size_t n, size_t*
     for (int q = 0; q < nq; ++q) out[k++] = T.wq[q];
     for (int q = 0; q < nq; ++q) for (int a = 0; a < n1; ++a) out[k++] = T.Bq[q][a];
     for (int q = 0; q < nq; ++q) for (int a = 0; a < n1; ++a) out[k++] = T.dBq[q][a];
-    for (int i = 0; i < n2 * n2; ++i) out[k++] = H.a2d[A2_OFF[p] + i];
+    for (int i = 0; i < n2 * n2; ++i) out[k++] = A2[i];
     return CGL_OK;
 }
 
@@ -279,6 +475,8 @@ extern "C" cgl_status cgl_mesh_create(const cgl_mesh_desc* d, cgl_mesh** out) {
     for (int bc : {d->bc_x, d->bc_y})
         if (bc != CGL_BC_PERIODIC && bc != CGL_BC_OUTFLOW && bc != CGL_BC_FIXED)
             return fail(CGL_EINVAL, "unknown boundary condition %d", bc);
+    if (d->basis != CGL_BASIS_BERNSTEIN && d->basis != CGL_BASIS_LGL)
+        return fail(CGL_EINVAL, "unknown basis %d", d->basis);
     if (!(d->x1 > d->x0) || !(d->y1 > d->y0)) return fail(CGL_EINVAL, "empty domain");
     double hx = (d->x1 - d->x0) / d->nx, hy = (d->y1 - d->y0) / d->ny;
     if (std::fabs(hx - hy) > 1e-12 * std::fabs(hx))
@@ -321,6 +519,8 @@ extern "C" cgl_status cgl_mesh_create(const cgl_mesh_desc* d, cgl_mesh** out) {
     m.x0 = d->x0;
     m.y0 = d->y0;
     m.hn = m.h / d->p;
+    m.basis = d->basis;
+    m.inv_h2 = 1.0 / (hx * hx);
     *out = M;
     return CGL_OK;
 }
@@ -446,6 +646,8 @@ extern "C" cgl_status cgl_state_create(const cgl_mesh* mesh, int32_t ncomp, int3
     *out = nullptr;
     if (ncomp != 1 && ncomp != 4) return fail(CGL_EINVAL, "ncomp must be 1 or 4");
     if (precision != CGL_FP64 && precision != CGL_FP32_MIXED) return fail(CGL_EINVAL, "unknown precision");
+    if (mesh->m.basis != CGL_BASIS_BERNSTEIN && precision != CGL_FP64)
+        return fail(CGL_EINVAL, "LGL meshes run in the FP64 form");
     int ndev = 0;
     cudaError_t ce = cudaGetDeviceCount(&ndev);
     if (ce != cudaSuccess || ndev == 0)
@@ -649,6 +851,8 @@ extern "C" cgl_status cgl_set_problem(cgl_state* S, const cgl_problem* p) {
         return fail(CGL_EINVAL, "unknown option bits");
     if ((p->options & CGL_OPT_SUBCELL_DT) && p->flux_limiter != CGL_FL_NONE)
         return fail(CGL_EINVAL, "CGL_OPT_SUBCELL_DT needs flux_limiter = CGL_FL_NONE");
+    if (S->mesh->m.basis != CGL_BASIS_BERNSTEIN && (p->options & (CGL_OPT_SUBCELL_DT | CGL_OPT_AEC_Q1)))
+        return fail(CGL_EINVAL, "CGL_OPT_SUBCELL_DT and CGL_OPT_AEC_Q1 are stated for Bernstein elements");
     if (p->options & CGL_OPT_DTE_REDUCE) {
         if (p->flux_limiter != CGL_FL_NONE)
             return fail(CGL_EINVAL, "CGL_OPT_DTE_REDUCE needs flux_limiter = CGL_FL_NONE");
@@ -819,8 +1023,14 @@ extern "C" cgl_status cgl_set_state_nodal(cgl_state* S, double (*u0)(double, dou
     if (!S || !u0) return fail(CGL_EINVAL, "null argument");
     const cgl_mesh_desc& d = S->mesh->d;
     const MeshDev& m = S->mesh->m;
-    // nodal points of the uniform sub-grid: spacing h/p in each direction
+    // nodal points: the uniform sub-grid of spacing h/p (Bernstein), the
+    // LGL points of every element (LGL)
     const double hx = (d.x1 - d.x0) / d.nx / d.p, hy = (d.y1 - d.y0) / d.ny / d.p;
+    const Tab<double>& TL = host_tables().td[PMAX + 1 + d.p];
+    auto pos = [&](int g, double o, double hh) {
+        if (d.basis == CGL_BASIS_LGL) return o + ((g / d.p) + TL.xn[g % d.p]) * (hh * d.p);
+        return o + g * hh;
+    };
     std::vector<double> host;
     try {
         host.resize(state_count(S));
@@ -830,7 +1040,7 @@ extern "C" cgl_status cgl_set_state_nodal(cgl_state* S, double (*u0)(double, dou
     size_t k = 0;
     for (int c = 0; c < S->nc; ++c)
         for (int gy = 0; gy < m.nny; ++gy)
-            for (int gx = 0; gx < m.nnx; ++gx) host[k++] = u0(d.x0 + gx * hx, d.y0 + gy * hy, c, ctx);
+            for (int gx = 0; gx < m.nnx; ++gx) host[k++] = u0(pos(gx, d.x0, hx), pos(gy, d.y0, hy), c, ctx);
     return upload_nodal(S, S->B.u, host.data(), host.size());
 }
 

@@ -38,6 +38,10 @@ struct MeshDev {
     float me_rz_f;         // m_i^e rounded toward zero (admissible bound gaps)
     float inv_h_f;
     double x0, y0, hn;     // domain corner; node spacing h/p (node gx sits at x0 + gx*hn)
+    // element basis: 0 Bernstein (the paper's), 1 Lagrange at the LGL points
+    // (float64 form only: m_i^e = h^2 w_a w_b, node a at x_e + xn_a h)
+    int basis;
+    double inv_h2;         // 1/h^2
 };
 
 // Boundary data of one side of the domain (W, E, S, N), Sec. 2: weakly
@@ -134,6 +138,9 @@ struct Tab {
     T dBq[NQMAX][N1MAX];   // B_a'(x_q)
     T wq[NQMAX];           // Gauss weights on [0,1]
     T xq[NQMAX];           // Gauss points on [0,1]
+    T wl[N1MAX];           // int_0^1 phi_a: 1/(p+1) (Bernstein), the LGL weights
+    T iwl[N1MAX];          // 1 / wl[a]
+    T xn[N1MAX];           // node positions on [0,1]: a/p, the LGL points
 };
 
 // semi-norm matrices (n2 x n2 for p = 1..4) packed at offsets
@@ -141,10 +148,14 @@ constexpr int A2_OFF[PMAX + 1] = {0, 0, 16, 97, 353};
 constexpr int A2_TOTAL = 978;
 
 // one copy per translation unit (no relocatable device code); every unit
-// uploads the same host tables through its own upload function
-static __constant__ Tab<double> c_tabd[PMAX + 1];
+// uploads the same host tables through its own upload function.  The
+// float64 tables hold both bases: Bernstein at index p, the Lagrange basis
+// at the LGL points at PMAX + 1 + p (semi-norm matrices at A2_TOTAL + ...);
+// the float tables hold Bernstein only (the FP32-mixed form refuses LGL)
+constexpr int NTABD = 2 * (PMAX + 1);
+static __constant__ Tab<double> c_tabd[NTABD];
 static __constant__ Tab<float> c_tabf[PMAX + 1];
-static __constant__ double c_A2d[A2_TOTAL];
+static __constant__ double c_A2d[2 * A2_TOTAL];
 static __constant__ float c_A2f[A2_TOTAL];
 
 template <class T> struct TabSel;
@@ -156,6 +167,23 @@ template <> struct TabSel<float> {
     static DEV const Tab<float>& t(int p) { return c_tabf[p]; }
     static DEV float A2(int off) { return c_A2f[off]; }
 };
+
+// the mesh's basis in the float64 form (always Bernstein in float)
+template <class R>
+DEV bool is_lgl(const MeshDev& m) {
+    return sizeof(R) == 8 && m.basis != 0;
+}
+// tables of degree p on the mesh's basis
+template <class R>
+DEV const Tab<R>& tab_of(const MeshDev& m, int p) {
+    if constexpr (sizeof(R) == 8) return c_tabd[m.basis ? PMAX + 1 + p : p];
+    else return c_tabf[p];
+}
+// offset of the mesh's basis in the packed semi-norm matrices
+template <class R>
+DEV int a2_base(const MeshDev& m) {
+    return is_lgl<R>(m) ? A2_TOTAL : 0;
+}
 
 // ---------------------------------------------------------------------------
 // physics policies. Each provides, for value type T:

@@ -159,9 +159,15 @@ DEV int side_slot(const ProbDev& pr, int d, double pos) {
     return pos < sp ? 0 : 1;
 }
 
-// coordinate along side d of node k (0..p) of the face of element (ex, ey)
+// coordinate along side d of node k (0..p) of the face of element (ex, ey):
+// x0 + g h/p (Bernstein), x_e + xn_k h (LGL)
 DEV double side_node_pos(const MeshDev& m, int d, int ex, int ey, int k) {
-    const int g = ((d < 2) ? ey : ex) * m.p + k;
+    const int c = (d < 2) ? ey : ex;
+    if (m.basis) {
+        const double xk = c_tabd[PMAX + 1 + m.p].xn[k];
+        return __dadd_rn(__dadd_rn((d < 2) ? m.y0 : m.x0, __dmul_rn((double)c, m.h)), __dmul_rn(xk, m.h));
+    }
+    const int g = c * m.p + k;
     return __dadd_rn((d < 2) ? m.y0 : m.x0, __dmul_rn((double)g, m.hn));
 }
 
@@ -247,12 +253,36 @@ DEV double block_mean(const float (&v)[N]) {
     return ((double)s + (double)c) * (1.0 / N);
 }
 
+// u^e of eq. (ueold), (1/|K_e|) sum_i m_i^e u_i: the mean of the Bernstein
+// coefficients, or on an LGL mesh (float64 form) the nodal values weighted
+// by w_a w_b
+template <class R, int P>
+DEV double cell_mean(const MeshDev& m, const R (&v)[Dim<P>::N2]) {
+    if constexpr (sizeof(R) == 8) {
+        if (m.basis) {
+            constexpr int N1 = P + 1;
+            const Tab<double>& T = c_tabd[PMAX + 1 + P];
+            double s = 0.0;
+#pragma unroll
+            for (int b = 0; b < N1; ++b) {
+                double r = 0.0;
+#pragma unroll
+                for (int a = 0; a < N1; ++a) r += T.wl[a] * v[b * N1 + a];
+                s += T.wl[b] * r;
+            }
+            return s;
+        }
+    }
+    return block_mean<Dim<P>::N2>(v);
+}
+
 // b^e_i = (int phi_i d_x u_h, int phi_i d_y u_h), sum-factorised, into EV
 // at ev_at(E, e, i, v, 2NC), v = dim*NC + c
 template <class R, int P, int NC>
-DEV void grad_vectors(const R (&U)[NC][Dim<P>::N2], R h, long long E, int e, R* __restrict__ EV) {
+DEV void grad_vectors(const MeshDev& m, const R (&U)[NC][Dim<P>::N2], R h, long long E, int e,
+                      R* __restrict__ EV) {
     constexpr int N1 = P + 1, N2 = Dim<P>::N2, NV = 2 * NC;
-    const Tab<R>& T = TabSel<R>::t(P);
+    const Tab<R>& T = tab_of<R>(m, P);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         R Y[N1][N1], Z[N1][N1];
@@ -382,7 +412,7 @@ DEV void cell_state(const R* __restrict__ u, const MeshDev& m, const ProbDev& pr
     R aR[NC], fxR[NC], fyR[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        avg[c] = block_mean<N2>(U[c]);
+        avg[c] = cell_mean<R, P>(m, U[c]);
         aR[c] = R(avg[c]);
     }
     Ph::template flux<R>(aR, fxR, fyR, pr);
@@ -395,9 +425,10 @@ DEV void cell_state(const R* __restrict__ u, const MeshDev& m, const ProbDev& pr
 
 // quadratic form of the semi-norm matrix A; A annihilates constants, so the
 // block is shifted by its first coefficient first (exact zeros for constant
-// data, no cancellation for nearly constant data)
+// data, no cancellation for nearly constant data).  a2b: the basis's offset
+// in the packed matrices (a2_base; 0 for Bernstein)
 template <class R, int P>
-DEV R qform(const R (&v)[Dim<P>::N2]) {
+DEV R qform(const R (&v)[Dim<P>::N2], int a2b = 0) {
     constexpr int N2 = Dim<P>::N2;
     constexpr int off = A2_OFF[P];
     // d = v - v_0 (d_0 = 0); A symmetric: s = sum_i d_i (A_ii d_i + 2 sum_{j>i} A_ij d_j)
@@ -409,8 +440,8 @@ DEV R qform(const R (&v)[Dim<P>::N2]) {
     for (int i = 1; i < N2; ++i) {
         R t = R(0);
 #pragma unroll
-        for (int j = i + 1; j < N2; ++j) t += TabSel<R>::A2(off + i * N2 + j) * d[j];
-        s += d[i] * (TabSel<R>::A2(off + i * N2 + i) * d[i] + R(2) * t);
+        for (int j = i + 1; j < N2; ++j) t += TabSel<R>::A2(a2b + off + i * N2 + j) * d[j];
+        s += d[i] * (TabSel<R>::A2(a2b + off + i * N2 + i) * d[i] + R(2) * t);
     }
     return s;
 }
@@ -418,9 +449,8 @@ DEV R qform(const R (&v)[Dim<P>::N2]) {
 // neighbour polynomial continued onto K_e: dir 0 W (Em in x), 1 E (Ep in x),
 // 2 S (Em in y), 3 N (Ep in y)
 template <class R, int P>
-DEV void continue_nb(int dir, const R (&src)[Dim<P>::N2], R (&dst)[Dim<P>::N2]) {
+DEV void continue_nb(const Tab<R>& T, int dir, const R (&src)[Dim<P>::N2], R (&dst)[Dim<P>::N2]) {
     constexpr int N1 = P + 1;
-    const Tab<R>& T = TabSel<R>::t(P);
 #pragma unroll
     for (int b = 0; b < N1; ++b)
 #pragma unroll
@@ -461,6 +491,8 @@ DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
     const R wl = PV<R>::w_lin(pr), eps = PV<R>::weno_eps(pr), geps = PV<R>::gamma_eps(pr);
     const bool r2 = (pr.r == 2.0);
     const R rh = R(0.5 * pr.r);
+    const Tab<R>& T = tab_of<R>(m, P);
+    const int a2b = a2_base<R>(m);
     int ne = 0;
 #pragma unroll
     for (int d = 0; d < 4; ++d) ne += (nb[d] >= 0);
@@ -470,7 +502,7 @@ DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
         R U0[N2];
 #pragma unroll
         for (int i = 0; i < N2; ++i) U0[i] = U[c][i] - U[c][0];
-        R sig0 = fmax(qform<R, P>(U0), R(0));
+        R sig0 = fmax(qform<R, P>(U0, a2b), R(0));
         R wt[5];
         wt[0] = (R(1) - R(ne) * wl) / ((r2 ? sig0 : pow(sig0, rh)) + eps);
 #pragma unroll 1
@@ -484,8 +516,8 @@ DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
                 const R v0 = V[0];
 #pragma unroll
                 for (int i = 0; i < N2; ++i) V[i] -= v0;
-                continue_nb<R, P>(d, V, W);
-                R sg = fmax(qform<R, P>(W), R(0));
+                continue_nb<R, P>(T, d, V, W);
+                R sg = fmax(qform<R, P>(W, a2b), R(0));
                 wt[d + 1] = wl / ((r2 ? sg : pow(sg, rh)) + eps);
             }
         }
@@ -503,13 +535,13 @@ DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
                 const R v0 = V[0];
 #pragma unroll
                 for (int i = 0; i < N2; ++i) V[i] -= v0;
-                continue_nb<R, P>(d, V, W);
+                continue_nb<R, P>(T, d, V, W);
                 R wd = wt[d + 1] / tot;
 #pragma unroll
                 for (int i = 0; i < N2; ++i) Dl[i] += wd * (U0[i] - W[i]);
             }
         }
-        R num = sqrt(fmax(qform<R, P>(Dl), R(0)));
+        R num = sqrt(fmax(qform<R, P>(Dl, a2b), R(0)));
         R den = sqrt(sig0);
         R ratio = num / (den + geps);
         R gc = R(1) - (pr.q == 1.0 ? fmin(R(1), ratio) : pow(fmin(R(1), ratio), PV<R>::q(pr)));
@@ -546,7 +578,7 @@ DEV R sensor_scalar(const ProbDev& pr, const R (&U)[Dim<P>::N2], const R (&V)[4]
             R Vc[N2];
 #pragma unroll
             for (int i = 0; i < N2; ++i) Vc[i] = V[d][i] - V[d][0];
-            continue_nb<R, P>(d, Vc, W[d]);
+            continue_nb<R, P>(TabSel<R>::t(P), d, Vc, W[d]);
             R sg = fmax(qform<R, P>(W[d]), R(0));
             wt[d + 1] = wl / ((r2 ? sg : pow(sg, rh)) + eps);
         }
@@ -1005,7 +1037,7 @@ DEV double pre_at_mixed(const MeshDev& m, const ProbDev& pr, const float* __rest
         lm = fmaxf(lm, Ph::template node_speed<float>(ui, pr));
     }
     nu_out[e] = (double)(lm * (m.h_f * (0.5f / P)));
-    if (EV) grad_vectors<float, P, NC>(U, m.h_f, m.E, e, EV);
+    if (EV) grad_vectors<float, P, NC>(m, U, m.h_f, m.E, e, EV);
     return dte;
     }
 }
@@ -1033,7 +1065,7 @@ DEV double pre_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u, 
             R aR[NC], fxR[NC], fyR[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                us[c] = block_mean<N2>(U[c]);
+                us[c] = cell_mean<R, P>(m, U[c]);
                 aR[c] = R(us[c]);
                 ue_out[c * m.E + e] = us[c];
             }
@@ -1104,7 +1136,7 @@ DEV double pre_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u, 
             lm = fmax(lm, Ph::template node_speed<R>(ui, pr));
         }
         nu_out[e] = (double)lm * (m.h * (0.5 / m.p));
-        if (EV) grad_vectors<R, P, NC>(U, PV<R>::h(m), m.E, e, EV);
+        if (EV) grad_vectors<R, P, NC>(m, U, PV<R>::h(m), m.E, e, EV);
     }
     return dte;
     }
@@ -1342,6 +1374,17 @@ DEV R inv_count(int n) {
     return n == 4 ? R(0.25) : (n == 2 ? R(0.5) : R(1));
 }
 
+// 1 / m_i on an LGL mesh (float64 form): m_i = sum over the cnt elements
+// containing node i of h^2 w_a w_b, with the node's local indices (a0, b0)
+// in the first of them; the LGL weights are symmetric (w_0 = w_p), so a
+// shared node has the same weight in every element containing it
+template <int P>
+DEV double inv_lumped_lgl(const MeshDev& m, int cnt, int a0, int b0) {
+    const Tab<double>& T = c_tabd[PMAX + 1 + P];
+    return inv_count<double>(cnt) * (m.inv_h2 * (T.iwl[a0] * T.iwl[b0]));
+}
+
+
 // s[v] = sum over E_i of the element vectors at node (gx, gy), fixed order
 template <class R, int P, int NV>
 DEV void gather_at(const MeshDev& m, const R* __restrict__ EV, const NodeC<P>& c, R (&s)[NV]) {
@@ -1372,7 +1415,8 @@ DEV void gather_init_at(MeshDev m, const R* __restrict__ EV, R* __restrict__ bou
     const NodeC<P> c = node_c<P>(m, gx, gy);
     R s[NV];
     gather_at<R, P, NV>(m, EV, c, s);
-    const R inv_mi = PV<R>::inv_me(m) * inv_count<R>(c.nxc * c.nyc);
+    const R inv_mi = is_lgl<R>(m) ? R(inv_lumped_lgl<P>(m, c.nxc * c.nyc, c.a0, c.b0))
+                                  : PV<R>::inv_me(m) * inv_count<R>(c.nxc * c.nyc);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         if (bout) bout[v * m.NN + node] = s[v];
@@ -1458,7 +1502,7 @@ DEV void offsets_1d(int g, int n, int periodic, int (&idx)[2 * P + 1]) {
 template <class R, int P, int NC>
 DEV void grad_rhs_at(MeshDev m, const R* __restrict__ u, R* __restrict__ bout, R* __restrict__ gout,
                      int gx, int gy, long long node) {
-    const Tab<R>& T = TabSel<R>::t(P);
+    const Tab<R>& T = tab_of<R>(m, P);
     const NodeC<P> c = node_c<P>(m, gx, gy);
     R wMx[2 * P + 1], wCx[2 * P + 1], wMy[2 * P + 1], wCy[2 * P + 1];
     weights_1d<R, P, 0>(T, c.nxc, c.a0, c.a1, wMx);
@@ -1494,7 +1538,8 @@ DEV void grad_rhs_at(MeshDev m, const R* __restrict__ u, R* __restrict__ bout, R
         }
     }
     const R h = PV<R>::h(m);
-    const R inv_mi = mul_r(PV<R>::inv_me(m), inv_count<R>(c.nxc * c.nyc));
+    const R inv_mi = is_lgl<R>(m) ? R(inv_lumped_lgl<P>(m, c.nxc * c.nyc, c.a0, c.b0))
+                                  : mul_r(PV<R>::inv_me(m), inv_count<R>(c.nxc * c.nyc));
 #pragma unroll
     for (int v = 0; v < NC; ++v) {
         const R bx = mul_r(h, sx[v]), by = mul_r(h, sy[v]);
@@ -1510,7 +1555,7 @@ DEV void grad_rhs_at(MeshDev m, const R* __restrict__ u, R* __restrict__ bout, R
 template <class R, int P, int NV>
 DEV void mass_sweep_at(MeshDev m, const R* __restrict__ xin, const R* __restrict__ b, R* __restrict__ xout,
                        int gx, int gy, long long node) {
-    const Tab<R>& T = TabSel<R>::t(P);
+    const Tab<R>& T = tab_of<R>(m, P);
     const NodeC<P> c = node_c<P>(m, gx, gy);
     R wx[2 * P + 1], wy[2 * P + 1];
     weights_1d<R, P, 0>(T, c.nxc, c.a0, c.a1, wx);
@@ -1537,7 +1582,8 @@ DEV void mass_sweep_at(MeshDev m, const R* __restrict__ xin, const R* __restrict
         for (int v = 0; v < NV; ++v) s[v] = fma_r(wy[ky], t[v], s[v]);
     }
     const R h2 = PV<R>::h2(m);
-    const R inv_mi = mul_r(PV<R>::inv_me(m), inv_count<R>(c.nxc * c.nyc));
+    const R inv_mi = is_lgl<R>(m) ? R(inv_lumped_lgl<P>(m, c.nxc * c.nyc, c.a0, c.b0))
+                                  : mul_r(PV<R>::inv_me(m), inv_count<R>(c.nxc * c.nyc));
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         const long long k = v * m.NN + node;
@@ -1570,6 +1616,14 @@ DEV int node_class(int g, int n, int periodic) {
         if (g == n - 1) return P + 1;
     }
     return 0;
+}
+
+// local index of a node of class cls in the first element containing it
+// (a shared vertex: p in the lower element; a low / high boundary vertex:
+// 0 / p; inside an element: cls)
+template <int P>
+DEV int class_index(int cls) {
+    return (cls == 0 || cls == P + 1) ? P : (cls == P ? 0 : cls);
 }
 
 // weight of offset off (-P..P) for a node of class cls (WHICH 0: mass,
@@ -1632,7 +1686,7 @@ DEV void grad_tile(const MeshDev& m, const R* __restrict__ u, R* __restrict__ bo
     R(*tM)[HY][ST_TX] = reinterpret_cast<R(*)[HY][ST_TX]>(ws + FB * HY * HX + FB * HY * ST_TX);
     R(*WM)[NW] = reinterpret_cast<R(*)[NW]>(ws + FB * (HY * HX + 2 * HY * ST_TX));
     R(*WC)[NW] = reinterpret_cast<R(*)[NW]>(ws + FB * (HY * HX + 2 * HY * ST_TX) + NCL * NW);
-    const Tab<R>& T = TabSel<R>::t(P);
+    const Tab<R>& T = tab_of<R>(m, P);
     const int tid = ty * ST_TX + tx;
     __syncthreads();  // the workspace is free
     if (tid < NCL * NW) {
@@ -1671,7 +1725,8 @@ DEV void grad_tile(const MeshDev& m, const R* __restrict__ u, R* __restrict__ bo
             if (gx >= m.nnx || gy >= m.nny) continue;
             const int cly = node_class<P>(gy, m.nny, m.py);
             const int cnt = (clx == 0 ? 2 : 1) * (cly == 0 ? 2 : 1);
-            const R inv_mi = mul_r(PV<R>::inv_me(m), inv_count<R>(cnt));
+            const R inv_mi = is_lgl<R>(m) ? R(inv_lumped_lgl<P>(m, cnt, class_index<P>(clx), class_index<P>(cly)))
+                                          : mul_r(PV<R>::inv_me(m), inv_count<R>(cnt));
             const long long node = (long long)gy * m.nnx + gx;
 #pragma unroll
             for (int f = 0; f < FB; ++f) {
@@ -1702,7 +1757,7 @@ DEV void sweep_tile(const MeshDev& m, const R* __restrict__ xin, const R* __rest
     R(*xs)[HY][HX] = reinterpret_cast<R(*)[HY][HX]>(ws);
     R(*t)[HY][ST_TX] = reinterpret_cast<R(*)[HY][ST_TX]>(ws + FB * HY * HX);
     R(*W)[NW] = reinterpret_cast<R(*)[NW]>(ws + FB * (HY * HX + HY * ST_TX));
-    const Tab<R>& T = TabSel<R>::t(P);
+    const Tab<R>& T = tab_of<R>(m, P);
     const int tid = ty * ST_TX + tx;
     __syncthreads();  // the workspace is free
     if (tid < NCL * NW) {
@@ -1743,7 +1798,8 @@ DEV void sweep_tile(const MeshDev& m, const R* __restrict__ xin, const R* __rest
             if (gx >= m.nnx || gy >= m.nny) continue;
             const int cly = node_class<P>(gy, m.nny, m.py);
             const int cnt = (clx == 0 ? 2 : 1) * (cly == 0 ? 2 : 1);
-            const R inv_mi = mul_r(PV<R>::inv_me(m), inv_count<R>(cnt));
+            const R inv_mi = is_lgl<R>(m) ? R(inv_lumped_lgl<P>(m, cnt, class_index<P>(clx), class_index<P>(cly)))
+                                          : mul_r(PV<R>::inv_me(m), inv_count<R>(cnt));
 #pragma unroll
             for (int f = 0; f < FB; ++f) {
                 R sy = R(0);
@@ -1840,8 +1896,8 @@ template <class R, int P, class Ph>
 __device__ __noinline__ void boundary_face_term(const MeshDev& m, const ProbDev& pr, int d, int ex, int ey,
                                                 const R* Uf, R* term) {
     constexpr int NC = Ph::NC, N1 = P + 1, NQ = Dim<P>::NQ;
-    const Tab<R>& T = TabSel<R>::t(P);
-    const Tab<double>& Td = TabSel<double>::t(P);
+    const Tab<R>& T = tab_of<R>(m, P);
+    const Tab<double>& Td = tab_of<double>(m, P);
     const R h = PV<R>::h(m);
     const R nxo = (d == 0) ? R(-1) : (d == 1) ? R(1) : R(0);
     const R nyo = (d == 2) ? R(-1) : (d == 3) ? R(1) : R(0);
@@ -1899,7 +1955,7 @@ template <class R, int P, class Ph>
 DEV void w_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Dim<P>::N2], int ex, int ey,
                 R (&W)[Ph::NC][Dim<P>::N2]) {
     constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2, NQ = Dim<P>::NQ;
-    const Tab<R>& T = TabSel<R>::t(P);
+    const Tab<R>& T = tab_of<R>(m, P);
     const R h = PV<R>::h(m);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
@@ -2010,7 +2066,7 @@ DEV void stab_part(const MeshDev& m, const R (&U)[Ph::NC][Dim<P>::N2], const R* 
                    const double* __restrict__ gam, const double* __restrict__ nu, const R (&W)[Ph::NC][Dim<P>::N2],
                    R* __restrict__ ER, int ex, int ey, int e) {
     constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2;
-    const Tab<R>& T = TabSel<R>::t(P);
+    const Tab<R>& T = tab_of<R>(m, P);
     const R h = PV<R>::h(m);
     // stabilisation s = nu (K u - gamma (Gx gx + Gy gy))
     const R nue = R(nu[e]), ge = R(gam[e]);
@@ -2104,7 +2160,8 @@ DEV void split(double v, T& hi, T& lo) {
 
 // sum over the face nodes of F(u_j, u_hat_j; n) on a boundary face of side
 // d that is not OUTFLOW everywhere (f^H of eq. (hoflux) before the division
-// by p+1), u_hat_j of the side at node j; Uf is [NC][p+1]
+// by p+1; on an LGL mesh the sum weighted by w_j, f^H itself), u_hat_j of
+// the side at node j; Uf is [NC][p+1]
 template <class R, int P, class Ph>
 __device__ __noinline__ CompVec<R, Ph::NC> bnd_face_llf_sum(const MeshDev& m, const ProbDev& pr, int d, int e,
                                                            R nx, R ny, const R* Uf) {
@@ -2134,15 +2191,19 @@ __device__ __noinline__ CompVec<R, Ph::NC> bnd_face_llf_sum(const MeshDev& m, co
         for (int c = 0; c < NC; ++c) uk[c] = Uf[c * N1 + k];
         if (fixed1) {
             llf_given_fR<Ph, R>(uk, ub1, fxb, fyb, nx, ny, pr, F);
+        } else {
+            const int slot = split ? side_slot(pr, d, side_node_pos(m, d, ex, ey, k)) : 0;
+            ext_state<R, NC>(pr, d, slot, uk, ub);
+            llf<Ph, R>(uk, ub, nx, ny, pr, F, (R*)nullptr);
+        }
+        if (is_lgl<R>(m)) {
+            const R wk = R(c_tabd[PMAX + 1 + P].wl[k]);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c] += wk * F[c];
+        } else {
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] += F[c];
-            continue;
         }
-        const int slot = split ? side_slot(pr, d, side_node_pos(m, d, ex, ey, k)) : 0;
-        ext_state<R, NC>(pr, d, slot, uk, ub);
-        llf<Ph, R>(uk, ub, nx, ny, pr, F, (R*)nullptr);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] += F[c];
     }
     return out;
 }
@@ -2246,13 +2307,20 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
 #pragma unroll
                     for (int c = 0; c < NC; ++c) uk[c] = U[c][li];
                     Ph::template flux<R>(uk, fx, fy, pr);
+                    if (is_lgl<R>(m)) {
+                        // LGL: the face mean weights node k by w_k
+                        const R wk = R(c_tabd[PMAX + 1 + P].wl[k]);
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) acc[c] += fx[c] * cnx + fy[c] * cny;
+                        for (int c = 0; c < NC; ++c) acc[c] += wk * (fx[c] * cnx + fy[c] * cny);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) acc[c] += fx[c] * cnx + fy[c] * cny;
+                    }
                 }
             }
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                const R a = acc[c] / R(N1);
+                const R a = is_lgl<R>(m) ? acc[c] : acc[c] / R(N1);
                 FHr[d][c] = fixed_b ? sg * a : a;
                 if constexpr (!mixed_sys) FH[d][c] = (double)FHr[d][c];
             }
@@ -2413,7 +2481,10 @@ DEV void facet_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][Di
             ubec[c] = ublc[c] + rs * os;
         }
     }
-    const R h_over_n2R = (sizeof(R) == 4) ? R(m.h_over_n2_f) : R(m.h_over_n2);
+    // (m_i^e / |K_e|) |S| times the outward sum of f^H, the facet term of
+    // eq. (aecb): h / (p+1)^2 for every node (Bernstein); on an LGL mesh h,
+    // weighted by w_a w_b per node in element_part
+    const R h_over_n2R = (sizeof(R) == 4) ? R(m.h_over_n2_f) : (is_lgl<R>(m) ? R(m.h) : R(m.h_over_n2));
 #pragma unroll
     for (int c = 0; c < NC; ++c)
         fh[c] = need_fh ? h_over_n2R * (((FHr[1][c] - FHr[0][c]) + FHr[3][c]) - FHr[2][c]) : R(0);
@@ -2432,7 +2503,7 @@ DEV void element_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][
                       double* __restrict__ beta_out, unsigned long long* __restrict__ cnt, int ex, int ey, int e,
                       double gq = 1.0) {
     constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2;
-    const Tab<R>& T = TabSel<R>::t(P);
+    const Tab<R>& T = tab_of<R>(m, P);
     const double me = m.me;
     // theta = dt / dt_e = dt s / h; FP32-mixed: in float from the float
     // speed sum of k_pre (it weights float increments; the check counts only)
@@ -2459,6 +2530,10 @@ DEV void element_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][
     }
     // f_i^e, eq. (aec) with eq. (aecb) folded into the residual
     const R meR = PV<R>::me(m), h2 = PV<R>::h2(m), inv_meR = PV<R>::inv_me(m);
+    // LGL mesh (float64 form): m_i^e = h^2 w_a w_b and 1/m_i^e per node, the
+    // facet term fh weighted by w_a w_b (see facet_part)
+    const bool lgl = is_lgl<R>(m);
+    const Tab<double>& TL = c_tabd[PMAX + 1 + P];
     R dteR;
     if constexpr (sizeof(R) == 4) dteR = __fmul_rn(m.h_f, __frcp_rn(cf[e]));  // h / s in float
     else dteR = R(dte);
@@ -2503,7 +2578,13 @@ DEV void element_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][
                 const int i = b * N1 + a;
                 R Ri = ER[ev_at(m.E, e, i, c, NC)];
                 R dev = (U[c][i] - ueh) - uel;
-                F[c][i] = meR * dev + dteR * (((Ri + fh_term) - h2 * s) + meR * UD[i]);
+                if (lgl) {
+                    const R w2 = R(TL.wl[a] * TL.wl[b]);
+                    const R mi = h2 * w2;
+                    F[c][i] = mi * dev + dteR * (((Ri + fh_term * w2) - h2 * s) + mi * UD[i]);
+                } else {
+                    F[c][i] = meR * dev + dteR * (((Ri + fh_term) - h2 * s) + meR * UD[i]);
+                }
                 if constexpr (Q1) F[c][i] = R(gq) * F[c][i];
             }
     }
@@ -2526,9 +2607,16 @@ DEV void element_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][
 #pragma unroll
             for (int i = 0; i < N2; ++i) {
                 R f = F[0][i];
+                R gpi = gp, gmi = gm;
+                if (lgl) {
+                    // m_i^e of this node (the gaps scale with it)
+                    const double mi = m.h * m.h * (TL.wl[i % N1] * TL.wl[i / N1]);
+                    gpi = R(mi * (pr.umax - ubec[0]));
+                    gmi = R(mi * (pr.umin - ubec[0]));
+                }
                 R bi = R(1);
-                if (f > R(0)) bi = fmin(R(1), gp / f);
-                else if (f < R(0)) bi = fmin(R(1), gm / f);
+                if (f > R(0)) bi = fmin(R(1), gpi / f);
+                else if (f < R(0)) bi = fmin(R(1), gmi / f);
                 b = fmin(b, bi);
             }
             beta = fmin(fmax(b, R(0)), R(1));
@@ -2551,7 +2639,8 @@ DEV void element_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][
                 double f[NC];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) f[c] = (double)F[c][i];
-                b = fmin(b, euler_alpha<double>(ubec, f, me, pr.pos_eps));
+                const double mi = lgl ? m.h * m.h * (TL.wl[i % N1] * TL.wl[i / N1]) : me;
+                b = fmin(b, euler_alpha<double>(ubec, f, mi, pr.pos_eps));
             }
             beta = R(b);
         }
@@ -2560,9 +2649,10 @@ DEV void element_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int i = 0; i < N2; ++i)
-            EW[ev_at(m.E, e, i, c, NC)] =
-                thR * (((ubh[c] - U[c][i]) + ubo[c]) + (beta * F[c][i]) * inv_meR);
+        for (int i = 0; i < N2; ++i) {
+            const R inv_mi = lgl ? R(m.inv_h2 * (TL.iwl[i % N1] * TL.iwl[i / N1])) : inv_meR;
+            EW[ev_at(m.E, e, i, c, NC)] = thR * (((ubh[c] - U[c][i]) + ubo[c]) + (beta * F[c][i]) * inv_mi);
+        }
 }
 
 template <class R, int P, class Ph>
@@ -2576,7 +2666,7 @@ DEV void update_at(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
                             double* __restrict__ ube_out, double* __restrict__ beta_out,
                             unsigned long long* __restrict__ cnt, int ex, int ey, int e) {
     constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2;
-    const Tab<R>& T = TabSel<R>::t(P);
+    const Tab<R>& T = tab_of<R>(m, P);
     const double h = m.h;
     const double me = m.me;
     const double dt = *dtp;
@@ -2633,7 +2723,7 @@ __global__ void __launch_bounds__(128) k_q1_facet(MeshDev m, ProbDev pr, const R
     int ex, ey, e;
     if (!elem_of_thread(m, ex, ey, e)) return;
     constexpr int NC = Ph::NC, N1 = P + 1, N2 = Dim<P>::N2;
-    const Tab<R>& T = TabSel<R>::t(P);
+    const Tab<R>& T = tab_of<R>(m, P);
     int nb[4];
 #pragma unroll
     for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);

@@ -30,7 +30,7 @@ __global__ void k_noalloc_grad(MeshDev m, const double* __restrict__ u, double* 
     if (!elem_of_thread(m, ex, ey, e)) return;
     double U[1][Dim<P>::N2];
     load_block<double, P, 1>(u, m, ex, ey, U);
-    grad_vectors<double, P, 1>(U, m.h, m.E, e, EV);
+    grad_vectors<double, P, 1>(m, U, m.h, m.E, e, EV);
 }
 
 template <int P>

@@ -302,11 +302,12 @@ StageFn select_stage_r(int p) {
 }
 
 // copy the host tables into this translation unit's constant memory
+// (td: NTABD float64 tables, a2d: 2 A2_TOTAL values, both bases)
 static inline cudaError_t upload_tables_here(const Tab<double>* td, const Tab<float>* tf,
                                              const double* a2d, const float* a2f) {
-    cudaError_t e = cudaMemcpyToSymbol(c_tabd, td, sizeof(Tab<double>) * (PMAX + 1));
+    cudaError_t e = cudaMemcpyToSymbol(c_tabd, td, sizeof(Tab<double>) * NTABD);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tabf, tf, sizeof(Tab<float>) * (PMAX + 1));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_A2d, a2d, sizeof(double) * A2_TOTAL);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_A2d, a2d, sizeof(double) * 2 * A2_TOTAL);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_A2f, a2f, sizeof(float) * A2_TOTAL);
     return e;
 }

@@ -48,6 +48,21 @@ def test_host_tables_match_oracle(L, p):
     assert np.abs(T["A2"] - A2).max() <= 1e-15 * np.abs(A2).max()
 
 
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_lgl_host_tables_match_oracle(L, p):
+    """The library's LGL tables (its own Lobatto points and Lagrange
+    polynomials in C++) against the oracle's (numpy), which the closed-form
+    Lobatto rules and the product formula pin."""
+    from oracle.tables import lgl_tables
+    import oracle.scheme as S
+    T = cgl.debug_tables(p, cgl.BASIS_LGL)
+    O = lgl_tables(p)
+    for k in ("M", "C", "D", "Ep", "Em", "xq", "wq", "Bq", "dBq", "wl", "xn"):
+        assert np.abs(T[k] - O[k]).max() <= 2e-14 * max(1.0, np.abs(O[k]).max()), k
+    A2 = S.OracleMesh(inputs.Mesh(2, 2, p, basis=inputs.BASIS_LGL)).A2
+    assert np.abs(T["A2"] - A2).max() <= 1e-13 * np.abs(A2).max()
+
+
 def test_mesh_validation(L):
     with pytest.raises(cgl.CglError) as e:
         cgl.Mesh(inputs.Mesh(4, 4, 5))
@@ -59,6 +74,10 @@ def test_mesh_validation(L):
     with pytest.raises(cgl.CglError):
         cgl.Mesh(inputs.Mesh(3, 3, 2, bc_x=7))
     m = cgl.Mesh(inputs.Mesh(5, 3, 3, 0.0, 5.0, 0.0, 3.0, inputs.BC_FIXED, inputs.BC_PERIODIC))
+    assert (m.nnx, m.nny, m.E) == (16, 9, 15)
+    with pytest.raises(cgl.CglError):
+        cgl.Mesh(inputs.Mesh(3, 3, 2, basis=2))
+    m = cgl.Mesh(inputs.Mesh(5, 3, 3, 0.0, 5.0, 0.0, 3.0, inputs.BC_FIXED, inputs.BC_PERIODIC, inputs.BASIS_LGL))
     assert (m.nnx, m.nny, m.E) == (16, 9, 15)
 
 
