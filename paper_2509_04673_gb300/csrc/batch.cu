@@ -285,7 +285,7 @@ static BatchKernel batch_kernel(int p) {
 // launches (each kernel waits for its predecessor, then lets the next one
 // be scheduled), so a launch's set-up overlaps the tail of the previous one.
 // ---------------------------------------------------------------------------
-template <int P, int PHASE>
+template <int P, int PHASE, class Ph>
 __global__ void __launch_bounds__(BT) k_bph_elem(const InstDev* __restrict__ I, const Tile* __restrict__ et,
                                                  int first, int kg, int ku) {
     pdl_wait_then_trigger();
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(BT) k_bph_elem(const InstDev* __restrict__ I, 
         const int e = T.begin + threadIdx.x;
         const int nx = D.m.nx;
         const int ey = e / nx, ex = e - ey * nx;
-        elem_dispatch<P>(PHASE, D, ex, ey, e, dte, kg, ku);
+        elem_phase<P, Ph>(PHASE, D, ex, ey, e, dte, kg, ku);
     }
     if (PHASE == PH_PRE && first) block_min_to(dte, D.dtbits);
 }
@@ -329,36 +329,57 @@ __global__ void k_bph_tadv(const InstDev* __restrict__ I, int ninst) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ninst; i += gridDim.x * blockDim.x) *I[i].t += *I[i].dt;
 }
 
-template <int P>
-static cudaError_t bph_stage(const InstDev* I, int ninst, const Tile* et, int net, const Tile* nt, int nnt,
-                             float a, float b, int first, int last, int kg, int ku, int mode_lo, cudaStream_t st) {
+// element tiles of a degree group ordered by flux: [eoff[f], eoff[f] + ecnt[f])
+// are the tiles of the instances with flux f (0 advection, 1 Burgers, 2 KPP),
+// each range launched with the kernel of its own flux
+struct ElemRanges {
+    int eoff[3], ecnt[3];
+};
+
+template <int P, int PHASE>
+static void bph_elem(const InstDev* I, const Tile* et, const ElemRanges& er, int first, int kg, int ku,
+                     cudaStream_t st, cudaError_t& err) {
     const dim3 blk(BT);
-    const dim3 gi((ninst + BT - 1) / BT), ge(net), gn(nnt);
+    auto chk = [&](cudaError_t e) {
+        if (e != cudaSuccess && err == cudaSuccess) err = e;
+    };
+    if (er.ecnt[0]) chk(launch(true, k_bph_elem<P, PHASE, PhysAdv>, dim3(er.ecnt[0]), blk, st, I, et + er.eoff[0], first, kg, ku));
+    if (er.ecnt[1])
+        chk(launch(true, k_bph_elem<P, PHASE, PhysBurgers>, dim3(er.ecnt[1]), blk, st, I, et + er.eoff[1], first, kg, ku));
+    if (er.ecnt[2]) chk(launch(true, k_bph_elem<P, PHASE, PhysKPP>, dim3(er.ecnt[2]), blk, st, I, et + er.eoff[2], first, kg, ku));
+}
+
+template <int P>
+static cudaError_t bph_stage(const InstDev* I, int ninst, const Tile* et, const ElemRanges& er, const Tile* nt,
+                             int nnt, float a, float b, int first, int last, int kg, int ku, int mode_lo,
+                             cudaStream_t st) {
+    const dim3 blk(BT);
+    const dim3 gi((ninst + BT - 1) / BT), gn(nnt);
     cudaError_t err = cudaSuccess;
     auto chk = [&](cudaError_t e) {
         if (e != cudaSuccess && err == cudaSuccess) err = e;
     };
-    chk(launch(true, k_bph_elem<P, PH_PRE>, ge, blk, st, I, et, first, kg, ku));
+    bph_elem<P, PH_PRE>(I, et, er, first, kg, ku, st, err);
     if (first) chk(launch(true, k_bph_dt, gi, blk, st, I, ninst));
     if (!mode_lo) {
         if (kg >= 1) chk(launch(true, k_bph_node<P, PH_GRADF>, gn, blk, st, I, nt, a, b, kg));
         else chk(launch(true, k_bph_node<P, PH_GRAD>, gn, blk, st, I, nt, a, b, 0));
         for (int k = (kg >= 1 ? 1 : 0); k < kg; ++k)
             chk(launch(true, k_bph_node<P, PH_SWEEP_G>, gn, blk, st, I, nt, a, b, k));
-        chk(launch(true, k_bph_elem<P, PH_RES>, ge, blk, st, I, et, 0, kg, ku));
+        bph_elem<P, PH_RES>(I, et, er, 0, kg, ku, st, err);
         if (ku >= 1) chk(launch(true, k_bph_node<P, PH_GATHERF>, gn, blk, st, I, nt, a, b, 0));
         else chk(launch(true, k_bph_node<P, PH_GATHER_R>, gn, blk, st, I, nt, a, b, 0));
         for (int k = (ku >= 1 ? 1 : 0); k < ku; ++k)
             chk(launch(true, k_bph_node<P, PH_SWEEP_U>, gn, blk, st, I, nt, a, b, k));
     }
-    chk(launch(true, k_bph_elem<P, PH_UPDATE>, ge, blk, st, I, et, 0, kg, ku));
+    bph_elem<P, PH_UPDATE>(I, et, er, 0, kg, ku, st, err);
     chk(launch(true, k_bph_node<P, PH_FINAL>, gn, blk, st, I, nt, a, b, 0));
     if (last) chk(launch(true, k_bph_tadv, gi, blk, st, I, ninst));
     return err;
 }
 
-typedef cudaError_t (*PhaseStage)(const InstDev*, int, const Tile*, int, const Tile*, int, float, float, int, int, int,
-                                  int, int, cudaStream_t);
+typedef cudaError_t (*PhaseStage)(const InstDev*, int, const Tile*, const ElemRanges&, const Tile*, int, float, float,
+                                  int, int, int, int, int, cudaStream_t);
 static PhaseStage phase_stage(int p) {
     switch (p) {
         case 1: return bph_stage<1>;
@@ -383,6 +404,7 @@ struct DegreeGroup {
     InstDev* d_inst;
     Tile *d_et, *d_nt;
     int net, nnt;
+    ElemRanges er;  // element tiles per flux (ordered by flux)
     BatchSync* d_sync;
     int grid;
     cudaStream_t gst;  // the phase form: this degree's stream
@@ -415,9 +437,18 @@ static cgl_status build_tiles(cgl_batch* B) {
     for (DegreeGroup& G : B->groups) {
         std::vector<Tile> et, nt;
         const int T = std::max(1, std::min(BT, B->tile_elems[G.p]));
+        for (int f = 0; f < 3; ++f) {
+            G.er.eoff[f] = (int)et.size();
+            for (int k = 0; k < (int)G.members.size(); ++k) {
+                const cgl_state* S = B->states[G.members[k]];
+                if (S->prob.flux != f) continue;
+                const MeshDev& m = S->mesh->m;
+                for (int b = 0; b < m.E; b += T) et.push_back(Tile{k, b, std::min(T, m.E - b), 0});
+            }
+            G.er.ecnt[f] = (int)et.size() - G.er.eoff[f];
+        }
         for (int k = 0; k < (int)G.members.size(); ++k) {
             const MeshDev& m = B->states[G.members[k]]->mesh->m;
-            for (int b = 0; b < m.E; b += T) et.push_back(Tile{k, b, std::min(T, m.E - b), 0});
             for (int gy0 = 0; gy0 < m.nny; gy0 += ST_TY)
                 for (int gx0 = 0; gx0 < m.nnx; gx0 += ST_TX) nt.push_back(Tile{k, gx0, gy0, 0});
         }
@@ -461,7 +492,7 @@ static cudaError_t enqueue_batch_step(cgl_batch* B) {
             if (e == cudaSuccess) e = cudaStreamWaitEvent(G.gst, B->ev_fork, 0);
             const int ninst = (int)G.members.size();
             for (int k = 0; k < 3 && e == cudaSuccess; ++k)
-                e = phase_stage(G.p)(G.d_inst, ninst, G.d_et, G.net, G.d_nt, G.nnt, sa[k], sb[k], k == 0, k == 2,
+                e = phase_stage(G.p)(G.d_inst, ninst, G.d_et, G.er, G.d_nt, G.nnt, sa[k], sb[k], k == 0, k == 2,
                                      B->kg, B->ku, B->mode_lo, G.gst);
             if (e == cudaSuccess) e = cudaEventRecord(G.ev, G.gst);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(B->st, G.ev, 0);

@@ -423,6 +423,13 @@ DEV void cell_state(const R* __restrict__ u, const MeshDev& m, const ProbDev& pr
     }
 }
 
+// x^e for the exponents other than the defaults r = 2, q = 1 of the sensor
+// (eqs. (WENO:alpha), (stab:WENO)): out of line, so that the sensor's hot
+// code, which the default exponents take, stays small in the instruction
+// cache (the same powf / pow as an inlined call)
+static __device__ __noinline__ float pow_rare(float x, float e) { return powf(x, e); }
+static __device__ __noinline__ double pow_rare(double x, double e) { return pow(x, e); }
+
 // quadratic form of the semi-norm matrix A; A annihilates constants, so the
 // block is shifted by its first coefficient first (exact zeros for constant
 // data, no cancellation for nearly constant data).  a2b: the basis's offset
@@ -504,7 +511,7 @@ DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
         for (int i = 0; i < N2; ++i) U0[i] = U[c][i] - U[c][0];
         R sig0 = fmax(qform<R, P>(U0, a2b), R(0));
         R wt[5];
-        wt[0] = (R(1) - R(ne) * wl) / ((r2 ? sig0 : pow(sig0, rh)) + eps);
+        wt[0] = (R(1) - R(ne) * wl) / ((r2 ? sig0 : pow_rare(sig0, rh)) + eps);
 #pragma unroll 1
         for (int d = 0; d < 4; ++d) {
             wt[d + 1] = R(0);
@@ -518,7 +525,7 @@ DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
                 for (int i = 0; i < N2; ++i) V[i] -= v0;
                 continue_nb<R, P>(T, d, V, W);
                 R sg = fmax(qform<R, P>(W, a2b), R(0));
-                wt[d + 1] = wl / ((r2 ? sg : pow(sg, rh)) + eps);
+                wt[d + 1] = wl / ((r2 ? sg : pow_rare(sg, rh)) + eps);
             }
         }
         R tot = (((wt[0] + wt[1]) + wt[2]) + wt[3]) + wt[4];
@@ -544,7 +551,7 @@ DEV R sensor(const MeshDev& m, const ProbDev& pr, const R* __restrict__ u,
         R num = sqrt(fmax(qform<R, P>(Dl, a2b), R(0)));
         R den = sqrt(sig0);
         R ratio = num / (den + geps);
-        R gc = R(1) - (pr.q == 1.0 ? fmin(R(1), ratio) : pow(fmin(R(1), ratio), PV<R>::q(pr)));
+        R gc = R(1) - (pr.q == 1.0 ? fmin(R(1), ratio) : pow_rare(fmin(R(1), ratio), PV<R>::q(pr)));
         gam = fmin(gam, gc);
     }
     return gam;
@@ -568,7 +575,7 @@ DEV R sensor_scalar(const ProbDev& pr, const R (&U)[Dim<P>::N2], const R (&V)[4]
     for (int i = 0; i < N2; ++i) U0[i] = U[i] - U[0];
     R sig0 = fmax(qform<R, P>(U0), R(0));
     R wt[5];
-    wt[0] = (R(1) - R(ne) * wl) / ((r2 ? sig0 : pow(sig0, rh)) + eps);
+    wt[0] = (R(1) - R(ne) * wl) / ((r2 ? sig0 : pow_rare(sig0, rh)) + eps);
     // the continued candidates, each formed once and kept for both passes
     R W[4][N2];
 #pragma unroll
@@ -580,7 +587,7 @@ DEV R sensor_scalar(const ProbDev& pr, const R (&U)[Dim<P>::N2], const R (&V)[4]
             for (int i = 0; i < N2; ++i) Vc[i] = V[d][i] - V[d][0];
             continue_nb<R, P>(TabSel<R>::t(P), d, Vc, W[d]);
             R sg = fmax(qform<R, P>(W[d]), R(0));
-            wt[d + 1] = wl / ((r2 ? sg : pow(sg, rh)) + eps);
+            wt[d + 1] = wl / ((r2 ? sg : pow_rare(sg, rh)) + eps);
         }
     }
     R tot = (((wt[0] + wt[1]) + wt[2]) + wt[3]) + wt[4];
@@ -598,7 +605,7 @@ DEV R sensor_scalar(const ProbDev& pr, const R (&U)[Dim<P>::N2], const R (&V)[4]
     R num = sqrt(fmax(qform<R, P>(Dl), R(0)));
     R den = sqrt(sig0);
     R ratio = num / (den + geps);
-    return R(1) - (pr.q == 1.0 ? fmin(R(1), ratio) : pow(fmin(R(1), ratio), PV<R>::q(pr)));
+    return R(1) - (pr.q == 1.0 ? fmin(R(1), ratio) : pow_rare(fmin(R(1), ratio), PV<R>::q(pr)));
 }
 
 // float-float mean of N floats: compensated (Neumaier) sum, then a division
