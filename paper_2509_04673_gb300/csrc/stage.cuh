@@ -164,13 +164,23 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
                    chk(launch(pdl, k_dt_final, dim3(1), dim3(1), st, B.dtbits, pr.cfl, (const double*)B.t,
                               (const double*)B.t_end, B.dt)));
     if (dt_only) return err != cudaSuccess ? err : cudaGetLastError();
-    // FP32-mixed: the facet part of the update on the second stream, beside
-    // the g_h and udot kernels (and beside k_sens for systems)
+    // FP32-mixed: the facet part of the update (for systems after the sensor)
+    // on the second stream, beside the g_h and udot kernels
     constexpr bool split_update = sizeof(R) == 4;
     if constexpr (split_update) {
         if (!q1) {
             chk(cudaEventRecord(B.ev_fork, st));
             chk(cudaStreamWaitEvent(s2, B.ev_fork, 0));
+            if constexpr (use_avg) {
+                // systems: the sensor first on the second stream, beside the
+                // g_h kernels of the main stream (k_sens is arithmetic-bound,
+                // the fused g_h sweep shared-memory-bound; measured: quadrants
+                // 512^2 Q3 2.368 -> 2.312 ms per step, blast 2048^2 -0.3 %)
+                const dim3 bs(K_SENS_TX, NC), gs(nblk(m.nx, K_SENS_TX), m.ny);
+                CGL_LAUNCH(prof, KID_SENS, s2,
+                           chk(launch(false, k_sens<P, Ph>, gs, bs, s2, m, pr, (const float*)u, B.gam, B.nu)));
+                chk(cudaEventRecord(B.ev_w, s2));
+            }
             CGL_LAUNCH(prof, KID_FACET, s2,
                        chk(launch(false, k_facet<P, Ph>, ge, be, s2, m, pr, (const float*)u, (const double*)B.ue,
                                   B.dte, (const double*)B.ubl, (const float*)B.q, (const float*)B.fl, B.cf, B.ube,
@@ -179,9 +189,12 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
         }
     }
     if constexpr (use_avg) {
-        const dim3 bs(K_SENS_TX, NC), gs(nblk(m.nx, K_SENS_TX), m.ny);
-        CGL_LAUNCH(prof, KID_SENS, st,
-                   chk(launch(pdl, k_sens<P, Ph>, gs, bs, st, m, pr, (const float*)u, B.gam, B.nu)));
+        if (q1) {
+            // eq. (aecQ1) scales its contributions by gamma_e: the sensor on the main stream
+            const dim3 bs(K_SENS_TX, NC), gs(nblk(m.nx, K_SENS_TX), m.ny);
+            CGL_LAUNCH(prof, KID_SENS, st,
+                       chk(launch(pdl, k_sens<P, Ph>, gs, bs, st, m, pr, (const float*)u, B.gam, B.nu)));
+        }
     }
     if (q1) {
         CGL_LAUNCH(prof, KID_Q1F, st,
@@ -241,6 +254,7 @@ cudaError_t run_stage(const Bufs& B, const MeshDev& m, const ProbDev& pr_in, dou
                        chk(launch(pdl, k_res_s<P, Ph>, ge, be, st, m, (const float*)u, (const float*)g,
                                   (const double*)B.gam, (const double*)B.nu, (const float*)B.EW, (float*)ER)));
         } else {
+            if constexpr (use_avg) chk(cudaStreamWaitEvent(st, B.ev_w, 0));  // gamma_e, nu_e of k_sens
             CGL_LAUNCH(prof, KID_RES, st,
                        chk(launch(pdl, k_res_ev<R, P, Ph>, ge, be, st, m, pr, (const R*)u, (const R*)g,
                                   (const double*)B.gam, (const double*)B.nu, ER)));
