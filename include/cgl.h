@@ -300,6 +300,30 @@ cgl_status cgl_set_state_nodal(cgl_state *state, double (*u0)(double x, double y
    the device through the staging buffer). Synchronous. */
 cgl_status cgl_get_state(cgl_state *state, double *host, size_t n);
 
+/* Pipelined host copies, for a loop that feeds the state from the host and
+   reads it back every step without waiting (an application; not in the
+   paper).  cgl_set_state_async enqueues the copy of host (n float64 values,
+   the layout of cgl_set_state) into one of two device staging buffers on a
+   copy stream of the state, then, on the state's stream after the work
+   enqueued before it, the finiteness check and the import; it returns
+   without waiting, so the copy overlaps the steps still running.  A copy
+   holding a non-finite value leaves the state as it was and is counted.
+   cgl_get_state_async enqueues, on the state's stream, the export of the
+   state as the work enqueued before it leaves it into one of two staging
+   buffers, then its copy into host on a second copy stream, which overlaps
+   the steps enqueued after it.  Both need host memory that is page-locked
+   (cudaMallocHost, cudaHostRegister, a pinned torch tensor) for the copies
+   to overlap, and the caller keeps each host buffer untouched until
+   cgl_sync returns.  The staging buffers (4 x 8 n bytes) are allocated at
+   the first call. */
+cgl_status cgl_set_state_async(cgl_state *state, const double *host, size_t n);
+cgl_status cgl_get_state_async(cgl_state *state, double *host, size_t n);
+
+/* Wait for the state's work and its pipelined copies. CGL_ENONFINITE if a
+   cgl_set_state_async since the last cgl_sync was refused (the count is
+   reset); CGL_ECUDA on a CUDA error. */
+cgl_status cgl_sync(cgl_state *state);
+
 /* Set the base state u^n used by cgl_stage (same layout as cgl_set_state). */
 cgl_status cgl_set_base_state(cgl_state *state, const double *host, size_t n);
 

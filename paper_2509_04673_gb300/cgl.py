@@ -96,6 +96,9 @@ _PROTOS = [
     ("cgl_set_boundary", C.c_int, [C.c_void_p, C.c_void_p]),
     ("cgl_set_state", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_size_t]),
     ("cgl_get_state", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_size_t]),
+    ("cgl_set_state_async", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_size_t]),
+    ("cgl_get_state_async", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_size_t]),
+    ("cgl_sync", C.c_int, [C.c_void_p]),
     ("cgl_set_base_state", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_size_t]),
     ("cgl_set_time", C.c_int, [C.c_void_p, C.c_double]),
     ("cgl_get_time", C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -272,6 +275,28 @@ class State:
             raise ValueError("out must be C-contiguous float64 of the state's shape")
         check(lib().cgl_get_state(self.h, _dptr(a), a.size))
         return a
+
+    def _host_array(self, a):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size != self.nc * self.mesh.nny * self.mesh.nnx:
+            raise ValueError("host buffer must be C-contiguous float64 of the state's shape")
+        return a
+
+    def set_state_async(self, host):
+        """Enqueue the copy of `host` (page-locked float64 [comp][gy][gx])
+        into the state (cgl_set_state_async); keep `host` untouched until sync()."""
+        a = self._host_array(host)
+        check(lib().cgl_set_state_async(self.h, _dptr(a), a.size))
+
+    def get_state_async(self, out):
+        """Enqueue the copy of the state into `out` (page-locked float64 of the
+        state's shape, cgl_get_state_async); valid after sync()."""
+        a = self._host_array(out)
+        check(lib().cgl_get_state_async(self.h, _dptr(a), a.size))
+        return a
+
+    def sync(self):
+        """Wait for the state's work and pipelined copies (cgl_sync)."""
+        check(lib().cgl_sync(self.h))
 
     def set_time(self, t):
         check(lib().cgl_set_time(self.h, float(t)))

@@ -597,8 +597,20 @@ static cgl_status dalloc(cgl_state* S, void** p, size_t bytes) {
 
 extern "C" void cgl_state_destroy(cgl_state* S) {
     if (!S) return;
+    // pipelined host copies still in flight finish before their buffers go
+    if (S->cst_in) cudaStreamSynchronize(S->cst_in);
+    if (S->cst_out) cudaStreamSynchronize(S->cst_out);
+    if (S->st) cudaStreamSynchronize(S->st);
     if (S->step_graph) cudaGraphExecDestroy(S->step_graph);
     for (void* p : S->allocs) cudaFree(p);
+    for (int k = 0; k < 2; ++k) {
+        if (S->ev_in_ready[k]) cudaEventDestroy(S->ev_in_ready[k]);
+        if (S->ev_in_free[k]) cudaEventDestroy(S->ev_in_free[k]);
+        if (S->ev_out_ready[k]) cudaEventDestroy(S->ev_out_ready[k]);
+        if (S->ev_out_free[k]) cudaEventDestroy(S->ev_out_free[k]);
+    }
+    if (S->cst_in) cudaStreamDestroy(S->cst_in);
+    if (S->cst_out) cudaStreamDestroy(S->cst_out);
     if (S->B.ev_fork) cudaEventDestroy(S->B.ev_fork);
     if (S->B.ev_join) cudaEventDestroy(S->B.ev_join);
     if (S->B.ev_fork0) cudaEventDestroy(S->B.ev_fork0);
@@ -958,10 +970,15 @@ static __global__ void k_count_nonfinite(const double* __restrict__ x, long long
 }
 
 // x -> dst rounded to R (round to nearest), only when no value was non-finite
+// (refused, when given: one count per refused copy)
 template <class R>
 static __global__ void k_import(const double* __restrict__ x, R* __restrict__ dst, long long n,
-                                const unsigned long long* __restrict__ bad) {
-    if (*bad) return;
+                                const unsigned long long* __restrict__ bad,
+                                unsigned long long* __restrict__ refused = nullptr) {
+    if (*bad) {
+        if (refused && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(refused, 1ull);
+        return;
+    }
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         dst[i] = (R)x[i];
 }
@@ -1010,6 +1027,97 @@ static cgl_status download_any(cgl_state* S, const void* src, bool bulk, double*
     } else {
         CUDA_TRY(cudaMemcpyAsync(host, src, n * 8, cudaMemcpyDeviceToHost, S->st));
         CUDA_TRY(cudaStreamSynchronize(S->st));
+    }
+    return CGL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pipelined host copies: two staging buffers per direction, a copy stream per
+// direction.  set: the copy stream waits until its buffer's previous import
+// is done, copies, and the state's stream waits for the copy before the
+// check and the import; get: the state's stream waits until its buffer's
+// previous copy is done, exports, and the copy stream waits for the export.
+// ---------------------------------------------------------------------------
+static cgl_status ensure_pipeline(cgl_state* S) {
+    if (S->cst_in) return CGL_OK;
+    const size_t bytes = state_count(S) * 8;
+    for (int k = 0; k < 2; ++k) {
+        cgl_status rc = dalloc(S, (void**)&S->stage_in[k], bytes);
+        if (!rc) rc = dalloc(S, (void**)&S->stage_out[k], bytes);
+        if (rc) return rc;
+        CUDA_TRY(cudaEventCreateWithFlags(&S->ev_in_ready[k], cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&S->ev_in_free[k], cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&S->ev_out_ready[k], cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&S->ev_out_free[k], cudaEventDisableTiming));
+        // every buffer starts free
+        CUDA_TRY(cudaEventRecord(S->ev_in_free[k], S->st));
+        CUDA_TRY(cudaEventRecord(S->ev_out_free[k], S->st));
+    }
+    CUDA_TRY(cudaStreamCreateWithFlags(&S->cst_out, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&S->cst_in, cudaStreamNonBlocking));
+    S->in_k = S->out_k = 0;
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_set_state_async(cgl_state* S, const double* host, size_t n) {
+    if (!S || !host) return fail(CGL_EINVAL, "null argument");
+    if (n != state_count(S)) return fail(CGL_EINVAL, "expected %zu values, got %zu", state_count(S), n);
+    cgl_status rc = ensure_pipeline(S);
+    if (rc) return rc;
+    const int k = S->in_k;
+    S->in_k ^= 1;
+    double* stage = S->stage_in[k];
+    unsigned long long* bad = &S->B.cnt[CNT_IMPORT];
+    CUDA_TRY(cudaStreamWaitEvent(S->cst_in, S->ev_in_free[k], 0));
+    CUDA_TRY(cudaMemcpyAsync(stage, host, n * 8, cudaMemcpyHostToDevice, S->cst_in));
+    CUDA_TRY(cudaEventRecord(S->ev_in_ready[k], S->cst_in));
+    CUDA_TRY(cudaStreamWaitEvent(S->st, S->ev_in_ready[k], 0));
+    CUDA_TRY(cudaMemsetAsync(bad, 0, 8, S->st));
+    k_count_nonfinite<<<copy_grid(n), 256, 0, S->st>>>(stage, (long long)n, bad);
+    if (S->prec == CGL_FP64)
+        k_import<double><<<copy_grid(n), 256, 0, S->st>>>(stage, (double*)S->B.u, (long long)n, bad,
+                                                          &S->B.cnt[CNT_REFUSED]);
+    else
+        k_import<float><<<copy_grid(n), 256, 0, S->st>>>(stage, (float*)S->B.u, (long long)n, bad,
+                                                         &S->B.cnt[CNT_REFUSED]);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventRecord(S->ev_in_free[k], S->st));
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_get_state_async(cgl_state* S, double* host, size_t n) {
+    if (!S || !host) return fail(CGL_EINVAL, "null argument");
+    if (n != state_count(S)) return fail(CGL_EINVAL, "expected %zu values, got %zu", state_count(S), n);
+    cgl_status rc = ensure_pipeline(S);
+    if (rc) return rc;
+    const int k = S->out_k;
+    S->out_k ^= 1;
+    double* stage = S->stage_out[k];
+    CUDA_TRY(cudaStreamWaitEvent(S->st, S->ev_out_free[k], 0));
+    if (S->prec == CGL_FP64) {
+        CUDA_TRY(cudaMemcpyAsync(stage, S->B.u, n * 8, cudaMemcpyDeviceToDevice, S->st));
+    } else {
+        k_export<<<copy_grid(n), 256, 0, S->st>>>((const float*)S->B.u, stage, (long long)n);
+        CUDA_TRY(cudaGetLastError());
+    }
+    CUDA_TRY(cudaEventRecord(S->ev_out_ready[k], S->st));
+    CUDA_TRY(cudaStreamWaitEvent(S->cst_out, S->ev_out_ready[k], 0));
+    CUDA_TRY(cudaMemcpyAsync(host, stage, n * 8, cudaMemcpyDeviceToHost, S->cst_out));
+    CUDA_TRY(cudaEventRecord(S->ev_out_free[k], S->cst_out));
+    return CGL_OK;
+}
+
+extern "C" cgl_status cgl_sync(cgl_state* S) {
+    if (!S) return fail(CGL_EINVAL, "null state");
+    CUDA_TRY(cudaStreamSynchronize(S->st));
+    if (S->cst_in) CUDA_TRY(cudaStreamSynchronize(S->cst_in));
+    if (S->cst_out) CUDA_TRY(cudaStreamSynchronize(S->cst_out));
+    unsigned long long refused = 0;
+    CUDA_TRY(cudaMemcpy(&refused, &S->B.cnt[CNT_REFUSED], 8, cudaMemcpyDeviceToHost));
+    if (refused) {
+        CUDA_TRY(cudaMemset(&S->B.cnt[CNT_REFUSED], 0, 8));
+        return fail(CGL_ENONFINITE, "%llu pipelined host copies held non-finite values (refused; the state kept "
+                    "its previous values there)", refused);
     }
     return CGL_OK;
 }

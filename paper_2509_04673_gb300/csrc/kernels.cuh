@@ -74,9 +74,11 @@ struct Dim {
 // device counters: invariant-domain violations, rounding clamps, theta > 1,
 // non-finite values, unlimited averages ubar^e outside G (flux limiter off),
 // pseudo time steps reduced by the remark after eq. (dtmaxcell)
-// (slot CNT_IMPORT: non-finite values of the last host copy into the state)
+// (slot CNT_IMPORT: non-finite values of the last host copy into the state;
+// CNT_REFUSED: pipelined host copies refused for a non-finite value since the
+// last cgl_sync)
 enum { CNT_VIOL = 0, CNT_CLAMP = 1, CNT_CFL = 2, CNT_NONFINITE = 3, CNT_UBAR = 4, CNT_DTE_RED = 5, CNT_IMPORT = 6,
-       CNT_N = 8 };
+       CNT_REFUSED = 7, CNT_N = 8 };
 
 // global node of local (a, b) in element (ex, ey); periodic wrap at the far side
 DEV long long node_of(const MeshDev& m, int ex, int ey, int a, int b) {

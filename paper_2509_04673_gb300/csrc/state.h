@@ -30,6 +30,14 @@ struct cgl_state {
     cudaGraphExec_t step_graph;
     double* diag;       // device partials for diagnostics
     double* host_stage; // float64 staging of host copies (nc*NN values), allocated at first use
+    // pipelined host copies (cgl_set_state_async / cgl_get_state_async), set
+    // up at first use: two float64 staging buffers per direction, one copy
+    // stream per direction, events that order the buffers' reuse
+    double* stage_in[2];
+    double* stage_out[2];
+    int in_k, out_k;
+    cudaStream_t cst_in, cst_out;
+    cudaEvent_t ev_in_ready[2], ev_in_free[2], ev_out_ready[2], ev_out_free[2];
     std::vector<void*> allocs;
 };
 
