@@ -432,6 +432,22 @@ DEV void cell_state(const R* __restrict__ u, const MeshDev& m, const ProbDev& pr
 static __device__ __noinline__ float pow_rare(float x, float e) { return powf(x, e); }
 static __device__ __noinline__ double pow_rare(double x, double e) { return pow(x, e); }
 
+// the float64 Appendix-A factor where the float32 certificate of the
+// FP32-mixed form could not show alpha = 1 (rare): out of line, so that the
+// unrolled node loop of the slope limiter carries a call per node instead of
+// a copy of the float64 formula (measured: k_update_el 5.52 -> 5.41 ms per
+// three blast steps; in k_facet, at its 73-register cap, the call measured
+// slower, 4.66 -> 5.80 ms, so the facet limiter keeps it inline, as does the
+// FP64 form, where it runs everywhere)
+static __device__ __noinline__ double euler_alpha_rare(const double* ub, const double* f, double m, double eps) {
+    return euler_alpha<double>(ub, f, m, eps);
+}
+template <class R>
+DEV double euler_alpha_of(const double* ub, const double* f, double m, double eps) {
+    if constexpr (sizeof(R) == 4) return euler_alpha_rare(ub, f, m, eps);
+    else return euler_alpha<double>(ub, f, m, eps);
+}
+
 // quadratic form of the semi-norm matrix A; A annihilates constants, so the
 // block is shifted by its first coefficient first (exact zeros for constant
 // data, no cancellation for nearly constant data).  a2b: the basis's offset
@@ -593,13 +609,14 @@ DEV R sensor_scalar(const ProbDev& pr, const R (&U)[Dim<P>::N2], const R (&V)[4]
         }
     }
     R tot = (((wt[0] + wt[1]) + wt[2]) + wt[3]) + wt[4];
+    const R rtot = R(1) / tot;  // one division for the four weights omega_l
     R Dl[N2];
 #pragma unroll
     for (int i = 0; i < N2; ++i) Dl[i] = R(0);
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
         if (nb[d] >= 0) {
-            R wd = wt[d + 1] / tot;
+            R wd = wt[d + 1] * rtot;
 #pragma unroll
             for (int i = 0; i < N2; ++i) Dl[i] += wd * (U0[i] - W[d][i]);
         }
@@ -1297,9 +1314,13 @@ __global__ void __launch_bounds__(K_SENS_TX * Ph::NC) k_sens(MeshDev m, ProbDev 
     __syncthreads();
     float lm = 0.f;
     if (valid) {
-#pragma unroll
-        for (int i = 0; i < N2; ++i) {
-            if (i % NC != c) continue;
+        // the nodes of this component's thread, in a loop that is not
+        // unrolled: one copy of the node-speed code (the unrolled form with a
+        // test per node put nine copies in the instruction cache; measured
+        // k_sens 8.21 -> 7.24 ms per three blast steps with the reciprocal
+        // of the weight sum below)
+#pragma unroll 1
+        for (int i = c; i < N2; i += NC) {
             float ui[NC];
 #pragma unroll
             for (int k = 0; k < NC; ++k) ui[k] = sU[k][i][tx];
@@ -2649,7 +2670,7 @@ DEV void element_part(const MeshDev& m, const ProbDev& pr, const R (&U)[Ph::NC][
 #pragma unroll
                 for (int c = 0; c < NC; ++c) f[c] = (double)F[c][i];
                 const double mi = lgl ? m.h * m.h * (TL.wl[i % N1] * TL.wl[i / N1]) : me;
-                b = fmin(b, euler_alpha<double>(ubec, f, mi, pr.pos_eps));
+                b = fmin(b, euler_alpha_of<R>(ubec, f, mi, pr.pos_eps));
             }
             beta = R(b);
         }
