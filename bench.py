@@ -173,10 +173,10 @@ def load_peaks():
 NCU_PER_ELEMENT = {
     # profiles/euler_blast_1024_q2_kernel_counts.md (kernel names as cgl_profile reports them:
     # k_pre is k_pre_lo and k_update_ev is k_update_el in this FP32-mixed Euler stage)
-    ("k_sens", HEADLINE): {"warp_inst": 204.1, "fp64_flops": 0.0, "dram_bytes": 70.4},
+    ("k_sens", HEADLINE): {"warp_inst": 195.4, "fp64_flops": 0.0, "dram_bytes": 69.6},
     ("k_grad_sweep", HEADLINE): {"warp_inst": 142.91, "fp64_flops": 0.0, "dram_bytes": 138.1},
     ("k_res_ev", HEADLINE): {"warp_inst": 146.29, "fp64_flops": 0.0, "dram_bytes": 403.2},
-    ("k_update_ev", HEADLINE): {"warp_inst": 72.27, "fp64_flops": 15.026, "dram_bytes": 533.6},
+    ("k_update_ev", HEADLINE): {"warp_inst": 70.4, "fp64_flops": 4.02, "dram_bytes": 545.8},
     ("k_facet", HEADLINE): {"warp_inst": 79.32, "fp64_flops": 12.051, "dram_bytes": 248.5},
     ("k_pre", HEADLINE): {"warp_inst": 49.71, "fp64_flops": 22.0, "dram_bytes": 218.3},
     ("k_udot_sweep", HEADLINE): {"warp_inst": 82.08, "fp64_flops": 0.0, "dram_bytes": 233.3},
