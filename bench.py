@@ -140,10 +140,14 @@ def impl_algorithmic_bytes(kernel, mesh, nc, rsz, k_g, k_u):
         "k_mass_sweep": 3 * ((2 * nc * k_g + nc * k_u) / max(1, k_g + k_u)) * NN * rsz,
     }
     if mixed and nc > 1:
-        # systems: k_pre_lo reads the float-float means of k_avg and writes
-        # u^e, dt_e (3), ubar^{e,L} (float64), f^L (4 nc), the float speed sum
-        # and ubar^{e,L} copies; k_sens reads u and writes gamma, nu
-        b["k_pre"] = 2 * nc * E * 4 + (nc + 3 + nc) * E * d + 4 * nc * E * 4 + (1 + nc) * E * 4
+        # systems: k_avg also writes the flux of each mean and 5 speed parts
+        # (2 nc + 5 floats per cell); k_pre_lo reads those and the
+        # float-float means and writes u^e, dt_e (3), ubar^{e,L} (float64),
+        # f^L (4 nc), the float speed sum and ubar^{e,L} copies; k_sens reads
+        # u and writes gamma, nu
+        b["k_avg"] = nc * NN * 4 + 2 * nc * E * 4 + (2 * nc + 5) * E * 4
+        b["k_pre"] = ((2 * nc + 2 * nc + 5) * E * 4 + (nc + 3 + nc) * E * d + 4 * nc * E * 4
+                      + (1 + nc) * E * 4)
     if mixed:
         # k_res_s: u, g, gamma, nu, W^e -> element residual; k_facet: u,
         # ubar^{e,L}, dt_e/h, Q, f^L -> ubar^e, facet terms; k_update_el: u,
