@@ -212,9 +212,9 @@ cgl_status cgl_problem_defaults(cgl_problem *p, int32_t flux);
    n must be at least the total count, returned in *needed. */
 cgl_status cgl_debug_tables(int32_t p, double *out, size_t n, size_t *needed);
 
-/* The same export for either basis (CGL_BASIS_BERNSTEIN or CGL_BASIS_LGL),
-   followed by the weights int_0^1 phi_a and the node positions on [0, 1]
-   (p+1 each). */
+/* The same export for either basis (CGL_BASIS_BERNSTEIN, Sec. 2.1, or
+   CGL_BASIS_LGL, the basis the concluding section names), followed by the
+   weights int_0^1 phi_a and the node positions on [0, 1] (p+1 each). */
 cgl_status cgl_debug_basis_tables(int32_t p, int32_t basis, double *out, size_t n, size_t *needed);
 
 /* --- mesh ---------------------------------------------------------------- */
@@ -412,7 +412,8 @@ cgl_status cgl_batch_info(cgl_batch *batch, int32_t *grid, int32_t *block, int32
    one block per tile, so that every phase has the register budget of its
    own code; each degree's launches run on a stream of their own inside the
    step's graph, so the degrees overlap.  Changing the form waits for the
-   batch's stream and captures a new graph at the next step. */
+   batch's stream and captures a new graph at the next step.  (Batching is an
+   application of the stage; the paper has no counterpart.) */
 #define CGL_BATCH_PERSISTENT 0
 #define CGL_BATCH_PHASES 1
 cgl_status cgl_batch_set_form(cgl_batch *batch, int32_t form);
