@@ -1732,6 +1732,12 @@ DEV void grad_tile(const MeshDev& m, const R* __restrict__ u, R* __restrict__ bo
 #pragma unroll
         for (int f = 0; f < FB; ++f) stage_tile<R, P, BY, TY>(m, u + (long long)(v0 + f) * m.NN, xs[f], gx0, gy0, tid);
         __syncthreads();
+        R wcx[NW], wmx[NW];  // the column's x weights, for every row and field
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            wcx[k] = WC[clx][k];
+            wmx[k] = WM[clx][k];
+        }
         // along x, every halo row: derivative (for b_x) and mass (for b_y)
         for (int r = ty; r < HY; r += BY) {
 #pragma unroll
@@ -1740,8 +1746,8 @@ DEV void grad_tile(const MeshDev& m, const R* __restrict__ u, R* __restrict__ bo
 #pragma unroll
                 for (int k = 0; k < NW; ++k) {
                     const R x = xs[f][r][tx + k];
-                    sc = fma_r(WC[clx][k], x, sc);
-                    sm = fma_r(WM[clx][k], x, sm);
+                    sc = fma_r(wcx[k], x, sc);
+                    sm = fma_r(wmx[k], x, sm);
                 }
                 tC[f][r][tx] = sc;
                 tM[f][r][tx] = sm;
@@ -1758,14 +1764,20 @@ DEV void grad_tile(const MeshDev& m, const R* __restrict__ u, R* __restrict__ bo
             const R inv_mi = is_lgl<R>(m) ? R(inv_lumped_lgl<P>(m, cnt, class_index<P>(clx), class_index<P>(cly)))
                                           : mul_r(PV<R>::inv_me(m), inv_count<R>(cnt));
             const long long node = (long long)gy * m.nnx + gx;
+            R wmy[NW], wcy[NW];  // once for every field
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                wmy[k] = WM[cly][k];
+                wcy[k] = WC[cly][k];
+            }
 #pragma unroll
             for (int f = 0; f < FB; ++f) {
                 const int v = v0 + f;
                 R sx = R(0), sy = R(0);
 #pragma unroll
                 for (int k = 0; k < NW; ++k) {
-                    sx = fma_r(WM[cly][k], tC[f][r + k][tx], sx);
-                    sy = fma_r(WC[cly][k], tM[f][r + k][tx], sy);
+                    sx = fma_r(wmy[k], tC[f][r + k][tx], sx);
+                    sy = fma_r(wcy[k], tM[f][r + k][tx], sy);
                 }
                 const R bx = mul_r(h, sx), by = mul_r(h, sy);
                 bout[v * m.NN + node] = bx;
