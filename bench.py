@@ -56,6 +56,7 @@ METRIC = "DOF-stage updates/s (FP32-mixed vs FP64 plain, same GB300); % of HBM r
 UNIT = "DOF-stage/s"
 HEADLINE = "euler_blast_2048x2048_q2"
 QUADRANTS = "euler_quadrants_512x512_q3"
+QUADRANTS_LGL = "euler_quadrants_512x512_q3_lgl"
 BATCH = "batched_256_instances"
 # oracle windows: W x W elements, compared on the nodes of the elements at
 # least MARGIN elements inside the window (a stage reads at most 5 elements
@@ -82,6 +83,8 @@ def workload(name):
         return inputs.euler_blast_config(2048, 2048, 2)
     if name == QUADRANTS:
         return inputs.euler_quadrant_config(512, 512, 3)
+    if name == QUADRANTS_LGL:
+        return inputs.euler_quadrant_config(512, 512, 3, basis=inputs.BASIS_LGL)
     raise ValueError(name)
 
 
@@ -618,6 +621,9 @@ def run_gpu(args):
         q32 = run_single(QUADRANTS, cgl.FP32_MIXED, profile_steps=PROF_STEPS)
         q32["prof_steps"] = PROF_STEPS
         q64 = run_single(QUADRANTS, cgl.FP64)
+        # the same data on the LGL basis (nodal values at the Lobatto points),
+        # FP64 form
+        ql = run_single(QUADRANTS_LGL, cgl.FP64)
         mq = q32["mesh"]
         nd_q = mq.nnx * mq.nny * 4
         meth_q = roofline_entry(QUADRANTS, q32, 4)
@@ -628,7 +634,11 @@ def run_gpu(args):
                            "roofline": roofline_entry(QUADRANTS, q64, 8)},
             "roofline": meth_q,
             "impl_bytes": impl_bytes_entry(q32, 4, meth_q["bytes_per_dof_stage"]),
-            "violations": q32["violations"] + q64["violations"],
+            "lgl_fp64": {"basis": "Lagrange at the Legendre-Gauss-Lobatto points (nodal values), same data",
+                         "value": aggregate_rate(nd_q * 3 * K, ql["ms"], world), "ms_per_step": ql["ms"] / K,
+                         "over_bernstein_fp64": q64["ms"] / ql["ms"], "violations": ql["violations"],
+                         "roofline": roofline_entry(QUADRANTS_LGL, ql, 8)},
+            "violations": q32["violations"] + q64["violations"] + ql["violations"],
             # outflow boundaries carry mass out: the mixed form's FP64 mass sums
             # against the FP64 form's after the same W + K steps
             "mass_vs_fp64": {c: abs(q32["after"]["mass"][i] - q64["after"]["mass"][i]) / abs(q64["after"]["mass"][i])
@@ -637,7 +647,7 @@ def run_gpu(args):
         }
         if do_extra:
             accuracy_sample(QUADRANTS, q32, q64, 6, False)
-        for r in (q32, q64):
+        for r in (q32, q64, ql):
             r["st"].close()
         # ---- config 4: the batch -------------------------------------------
         cfg[BATCH] = run_batch(cgl, torch, stream, flush, K, W, world, rank, dist, timed, hbm_peak, hbm_src)

@@ -201,10 +201,10 @@ def advection_config(nx=32, ny=32, p=2, seed_index=1, **prob):
     return mesh, problem, u0[None, :, :].copy()
 
 
-def kpp_config(nx=256, ny=256, p=2, **prob):
+def kpp_config(nx=256, ny=256, p=2, basis=BASIS_BERNSTEIN, **prob):
     """KPP problem: f(u) = (sin u, cos u) on (-2,2)x(-2.5,1.5), u0 = 7pi/2 in r<=1
     else pi/4 (Sec. 5.3.2), fixed boundary state pi/4."""
-    mesh = Mesh(nx, ny, p, -2.0, 2.0, -2.5, 1.5, BC_FIXED, BC_FIXED)
+    mesh = Mesh(nx, ny, p, -2.0, 2.0, -2.5, 1.5, BC_FIXED, BC_FIXED, basis)
     lo, hi = math.pi / 4, 3.5 * math.pi
     problem = Problem(flux=FLUX_KPP, umin=lo, umax=hi, cfl=0.2, w_lin=0.2,
                       ubc=(lo, 0.0, 0.0, 0.0))
@@ -221,9 +221,9 @@ def euler_primitive_to_conserved(rho, vx, vy, p, gamma=1.4):
     return np.stack([rho, rho * vx, rho * vy, E])
 
 
-def euler_quadrant_config(nx=512, ny=512, p=3, seed_index=3, **prob):
+def euler_quadrant_config(nx=512, ny=512, p=3, seed_index=3, basis=BASIS_BERNSTEIN, **prob):
     """Four-quadrant Riemann data on the unit square, outflow boundaries."""
-    mesh = Mesh(nx, ny, p, 0.0, 1.0, 0.0, 1.0, BC_OUTFLOW, BC_OUTFLOW)
+    mesh = Mesh(nx, ny, p, 0.0, 1.0, 0.0, 1.0, BC_OUTFLOW, BC_OUTFLOW, basis)
     problem = Problem(flux=FLUX_EULER, w_lin=1e-3, cfl=0.2, umin=0.0, umax=0.0)
     for k, v in prob.items():
         setattr(problem, k, v)
@@ -242,11 +242,11 @@ def euler_quadrant_config(nx=512, ny=512, p=3, seed_index=3, **prob):
     return mesh, problem, u0
 
 
-def euler_blast_config(nx=2048, ny=2048, p=2, energy=0.25, **prob):
+def euler_blast_config(nx=2048, ny=2048, p=2, energy=0.25, basis=BASIS_BERNSTEIN, **prob):
     """Near-vacuum blast: rho=1, v=0, p=1e-6 background, total energy excess
     `energy` deposited on the nodes of the closed central 2x2 cell block."""
     assert nx % 2 == 0 and ny % 2 == 0
-    mesh = Mesh(nx, ny, p, 0.0, 1.0, 0.0, 1.0, BC_OUTFLOW, BC_OUTFLOW)
+    mesh = Mesh(nx, ny, p, 0.0, 1.0, 0.0, 1.0, BC_OUTFLOW, BC_OUTFLOW, basis)
     problem = Problem(flux=FLUX_EULER, w_lin=1e-3, cfl=0.2, umin=0.0, umax=0.0)
     for k, v in prob.items():
         setattr(problem, k, v)
@@ -257,14 +257,22 @@ def euler_blast_config(nx=2048, ny=2048, p=2, energy=0.25, **prob):
     cx, cy = nx // 2, ny // 2
     gx0, gx1 = (cx - 1) * p, (cx + 1) * p
     gy0, gy1 = (cy - 1) * p, (cy + 1) * p
-    # integral weight of each block node = |K|/(p+1)^2 times the number of
-    # cells containing it (Bernstein basis functions integrate to |K|/(p+1)^2
-    # per cell, Sec. 3); counted here only to size the deposit.
+    # integral weight of each block node, summed over the cells containing it:
+    # |K|/(p+1)^2 per cell for Bernstein basis functions (Sec. 3), |K| w_a w_b
+    # for the Lagrange basis at the LGL points (w: the Lobatto weights on
+    # [0, 1], 1 / (p (p+1) P_p(x_a)^2) there); counted here only to size the
+    # deposit.
     h = mesh.h
+    if basis == BASIS_LGL:
+        xa = _lobatto_offsets(p)
+        wa = 1.0 / (p * (p + 1) * np.polynomial.legendre.Legendre.basis(p)(2.0 * xa - 1.0) ** 2)
+        wcell = h * h * np.outer(wa, wa)
+    else:
+        wcell = np.full((p + 1, p + 1), h * h / (p + 1) ** 2)
     w = np.zeros(shape)
     for ey in range(cy - 2, cy + 2):
         for ex in range(cx - 2, cx + 2):
-            w[ey * p:(ey + 1) * p + 1, ex * p:(ex + 1) * p + 1] += h * h / (p + 1) ** 2
+            w[ey * p:(ey + 1) * p + 1, ex * p:(ex + 1) * p + 1] += wcell
     block = np.zeros(shape, dtype=bool)
     block[gy0:gy1 + 1, gx0:gx1 + 1] = True
     total_w = w[block].sum()

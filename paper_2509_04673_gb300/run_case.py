@@ -30,6 +30,7 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--p", type=int, default=0, help="degree (0 = the workload's own)")
     ap.add_argument("--prec", type=int, default=1, help="0 FP64, 1 FP32-mixed")
+    ap.add_argument("--basis", type=int, default=0, help="0 Bernstein, 1 Lagrange at the LGL points (FP64 only)")
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=1, help="untimed steps first (graph capture, caches)")
     ap.add_argument("--profile", type=int, default=0,
@@ -41,17 +42,19 @@ def main():
     build.build()
     if a.workload == "batched":
         return run_batched(a)
+    if a.basis and a.workload not in ("kpp", "euler_quadrants", "euler_blast"):
+        raise SystemExit("--basis 1: kpp, euler_quadrants or euler_blast")
     if a.workload == "kpp":
-        mesh, prob, u0 = inputs.kpp_config(a.n, a.n, a.p or 2)
+        mesh, prob, u0 = inputs.kpp_config(a.n, a.n, a.p or 2, basis=a.basis)
     elif a.workload == "advection":
         mesh, prob, u0 = inputs.advection_config(a.n, a.n, a.p or 2)
     elif a.workload == "euler_quadrants":
-        mesh, prob, u0 = inputs.euler_quadrant_config(a.n, a.n, a.p or 3)
+        mesh, prob, u0 = inputs.euler_quadrant_config(a.n, a.n, a.p or 3, basis=a.basis)
     elif a.workload == "dmr":
         # --n is the number of elements across the height (4n x n elements)
         mesh, prob, u0 = inputs.dmr_config(a.n, a.p or 2)
     else:
-        mesh, prob, u0 = inputs.euler_blast_config(a.n, a.n, a.p or 2)
+        mesh, prob, u0 = inputs.euler_blast_config(a.n, a.n, a.p or 2, basis=a.basis)
     prob.options |= a.options
     if a.fl >= 0:
         prob.flux_limiter = a.fl
@@ -76,7 +79,7 @@ def main():
     info["steps"] = taken
     info["violations"] = st.counters()["violations"]
     ndof = u0.size
-    info.update(workload=a.workload, n=a.n, p=mesh.p, prec=a.prec, n_dof=ndof,
+    info.update(workload=a.workload, n=a.n, p=mesh.p, prec=a.prec, basis=a.basis, n_dof=ndof,
                 ms=ev0.elapsed_time(ev1),
                 dof_stage_per_s=ndof * 3 * info["steps"] / (ev0.elapsed_time(ev1) * 1e-3))
     if a.profile:

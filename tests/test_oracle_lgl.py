@@ -193,3 +193,26 @@ def _l2_error_1d(N, p, tend):
 def test_lgl_ho_converges_at_optimal_rate(p, Ns, rate):
     e = [_l2_error_1d(N, p, 0.25) for N in Ns]
     assert math.log2(e[0] / e[1]) >= rate, e
+
+
+@pytest.mark.parametrize("basis", [inputs.BASIS_BERNSTEIN, inputs.BASIS_LGL])
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_blast_deposit_is_the_stated_energy(basis, p):
+    """The blast recipe sizes its deposit with the basis's integral weights,
+    so sum_i m_i u_i of the energy exceeds the background's by exactly the
+    stated 0.25 in either basis (m_i: the oracle's lumped masses)."""
+    mesh, prob, u0 = inputs.euler_blast_config(8, 8, p, basis=basis)
+    bg = inputs.euler_primitive_to_conserved(np.ones(u0.shape[1:]), np.zeros(u0.shape[1:]),
+                                             np.zeros(u0.shape[1:]), np.full(u0.shape[1:], 1e-6), 1.4)
+    d = S.mass(mesh, u0) - S.mass(mesh, bg)
+    assert abs(d[3] - 0.25) <= 1e-14 and np.abs(d[:3]).max() == 0.0
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_lgl_blast_positivity(p):
+    mesh, prob, u0 = inputs.euler_blast_config(8, 8, p, basis=inputs.BASIS_LGL)
+    u1, t, st = S.run(mesh, prob.as_dict(), u0, 6)
+    assert st["violations"] == 0
+    assert np.all(u1[0] > 0)
+    e_int = u1[3] - 0.5 * (u1[1] ** 2 + u1[2] ** 2) / u1[0]
+    assert np.all(e_int > 0)
