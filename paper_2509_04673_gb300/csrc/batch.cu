@@ -136,31 +136,33 @@ DEV void elem_dispatch(int phase, const InstDev& D, int ex, int ey, int e, doubl
 // (g_h right-hand side, Richardson sweeps) with the tiled shared-memory
 // functions of the single-state kernels, the gathers node by node
 // (ST_TY / BY nodes per thread)
-template <int P>
-__device__ __noinline__ void node_phase(int phase, const InstDev& D, int gx0, int gy0, float a, float b, int k,
-                                        float* ws) {
+// NT threads per block (the block as 32 x NT/32 threads); inlined, so a
+// caller with a compile-time phase carries only that phase's code
+template <int P, int NT>
+DEV void node_phase_body(int phase, const InstDev& D, int gx0, int gy0, float a, float b, int k, float* ws) {
+    constexpr int BYN = NT / ST_TX;
     const int tx = threadIdx.x % ST_TX, ty = threadIdx.x / ST_TX;
     switch (phase) {
         case PH_GRADF:
             // right-hand side and first sweep in one pass (k carries k_g: b is
             // kept only when more sweeps follow)
-            grad_sweep_tile<P, 1, BT>(D.m, D.u, k > 1 ? D.bg : nullptr, D.g2, gx0, gy0, threadIdx.x, ws);
+            grad_sweep_tile<P, 1, NT>(D.m, D.u, k > 1 ? D.bg : nullptr, D.g2, gx0, gy0, threadIdx.x, ws);
             break;
-        case PH_GATHERF: udot_sweep_tile<P, 1, BT>(D.m, D.ER, D.r, D.ud2, gx0, gy0, threadIdx.x, ws); break;
-        case PH_GRAD: grad_tile<float, P, 1, BY>(D.m, D.u, D.bg, D.g, gx0, gy0, tx, ty, ws); break;
+        case PH_GATHERF: udot_sweep_tile<P, 1, NT>(D.m, D.ER, D.r, D.ud2, gx0, gy0, threadIdx.x, ws); break;
+        case PH_GRAD: grad_tile<float, P, 1, BYN>(D.m, D.u, D.bg, D.g, gx0, gy0, tx, ty, ws); break;
         case PH_SWEEP_G:
-            if (k & 1) sweep_tile<float, P, 2, BY>(D.m, D.g2, D.bg, D.g, gx0, gy0, tx, ty, ws);
-            else sweep_tile<float, P, 2, BY>(D.m, D.g, D.bg, D.g2, gx0, gy0, tx, ty, ws);
+            if (k & 1) sweep_tile<float, P, 2, BYN>(D.m, D.g2, D.bg, D.g, gx0, gy0, tx, ty, ws);
+            else sweep_tile<float, P, 2, BYN>(D.m, D.g, D.bg, D.g2, gx0, gy0, tx, ty, ws);
             break;
         case PH_SWEEP_U:
-            if (k & 1) sweep_tile<float, P, 1, BY>(D.m, D.ud2, D.r, D.ud, gx0, gy0, tx, ty, ws);
-            else sweep_tile<float, P, 1, BY>(D.m, D.ud, D.r, D.ud2, gx0, gy0, tx, ty, ws);
+            if (k & 1) sweep_tile<float, P, 1, BYN>(D.m, D.ud2, D.r, D.ud, gx0, gy0, tx, ty, ws);
+            else sweep_tile<float, P, 1, BYN>(D.m, D.ud, D.r, D.ud2, gx0, gy0, tx, ty, ws);
             break;
         default: {
             const int gx = gx0 + tx, nnx = D.m.nnx, nny = D.m.nny;
 #pragma unroll
-            for (int j = 0; j < ST_TY / BY; ++j) {
-                const int gy = gy0 + ty + j * BY;
+            for (int j = 0; j < ST_TY / BYN; ++j) {
+                const int gy = gy0 + ty + j * BYN;
                 if (gx >= nnx || gy >= nny) continue;
                 const long long node = (long long)gy * nnx + gx;
                 if (phase == PH_GATHER_R) gather_init_at<float, P, 1>(D.m, D.ER, D.r, D.ud, gx, gy, node);
@@ -168,6 +170,12 @@ __device__ __noinline__ void node_phase(int phase, const InstDev& D, int gx0, in
             }
         }
     }
+}
+
+template <int P>
+__device__ __noinline__ void node_phase(int phase, const InstDev& D, int gx0, int gy0, float a, float b, int k,
+                                        float* ws) {
+    node_phase_body<P, BT>(phase, D, gx0, gy0, a, b, k, ws);
 }
 
 template <int P>
@@ -285,12 +293,27 @@ static BatchKernel batch_kernel(int p) {
 // launches (each kernel waits for its predecessor, then lets the next one
 // be scheduled), so a launch's set-up overlaps the tail of the previous one.
 // ---------------------------------------------------------------------------
+// the instance's descriptor (mesh, problem, field pointers) copied into
+// shared memory once per block: the phase bodies read its fields many times,
+// and a shared broadcast is cheaper than a global load each time.  The
+// descriptors and tiles are written once, at batch creation, so the copy
+// runs before the wait for the previous launch.
+DEV void stage_inst(const InstDev* __restrict__ I, int inst, InstDev& sD) {
+    static_assert(sizeof(InstDev) % 8 == 0, "descriptor copied in 8-byte words");
+    const long long* src = reinterpret_cast<const long long*>(I + inst);
+    long long* dst = reinterpret_cast<long long*>(&sD);
+    for (int i = threadIdx.x; i < (int)(sizeof(InstDev) / 8); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+}
+
 template <int P, int PHASE, class Ph>
 __global__ void __launch_bounds__(BT) k_bph_elem(const InstDev* __restrict__ I, const Tile* __restrict__ et,
                                                  int first, int kg, int ku) {
-    pdl_wait_then_trigger();
+    __shared__ InstDev sD;
     const Tile T = et[blockIdx.x];
-    const InstDev& D = I[T.inst];
+    stage_inst(I, T.inst, sD);
+    pdl_wait_then_trigger();
+    const InstDev& D = sD;
     double dte = __longlong_as_double(0x7ff0000000000000LL);
     if ((int)threadIdx.x < T.count) {
         const int e = T.begin + threadIdx.x;
@@ -301,13 +324,18 @@ __global__ void __launch_bounds__(BT) k_bph_elem(const InstDev* __restrict__ I, 
     if (PHASE == PH_PRE && first) block_min_to(dte, D.dtbits);
 }
 
+// node tiles with 256 threads per block (2 rows per thread, as the
+// single-state stencils), the phase's code alone
+constexpr int BTN = 256;
 template <int P, int PHASE>
-__global__ void __launch_bounds__(BT) k_bph_node(const InstDev* __restrict__ I, const Tile* __restrict__ nt,
-                                                 float a, float b, int k) {
+__global__ void __launch_bounds__(BTN) k_bph_node(const InstDev* __restrict__ I, const Tile* __restrict__ nt,
+                                                  float a, float b, int k) {
     __shared__ float ws[ws_deg<P>()];
-    pdl_wait_then_trigger();
+    __shared__ InstDev sD;
     const Tile T = nt[blockIdx.x];
-    node_phase<P>(PHASE, I[T.inst], T.begin, T.count, a, b, k, ws);
+    stage_inst(I, T.inst, sD);
+    pdl_wait_then_trigger();
+    node_phase_body<P, BTN>(PHASE, sD, T.begin, T.count, a, b, k, ws);
 }
 
 // global dt of every instance of the group from its block minima (eq.
@@ -353,7 +381,7 @@ template <int P>
 static cudaError_t bph_stage(const InstDev* I, int ninst, const Tile* et, const ElemRanges& er, const Tile* nt,
                              int nnt, float a, float b, int first, int last, int kg, int ku, int mode_lo,
                              cudaStream_t st) {
-    const dim3 blk(BT);
+    const dim3 blk(BT), bn(BTN);
     const dim3 gi((ninst + BT - 1) / BT), gn(nnt);
     cudaError_t err = cudaSuccess;
     auto chk = [&](cudaError_t e) {
@@ -362,18 +390,18 @@ static cudaError_t bph_stage(const InstDev* I, int ninst, const Tile* et, const 
     bph_elem<P, PH_PRE>(I, et, er, first, kg, ku, st, err);
     if (first) chk(launch(true, k_bph_dt, gi, blk, st, I, ninst));
     if (!mode_lo) {
-        if (kg >= 1) chk(launch(true, k_bph_node<P, PH_GRADF>, gn, blk, st, I, nt, a, b, kg));
-        else chk(launch(true, k_bph_node<P, PH_GRAD>, gn, blk, st, I, nt, a, b, 0));
+        if (kg >= 1) chk(launch(true, k_bph_node<P, PH_GRADF>, gn, bn, st, I, nt, a, b, kg));
+        else chk(launch(true, k_bph_node<P, PH_GRAD>, gn, bn, st, I, nt, a, b, 0));
         for (int k = (kg >= 1 ? 1 : 0); k < kg; ++k)
-            chk(launch(true, k_bph_node<P, PH_SWEEP_G>, gn, blk, st, I, nt, a, b, k));
+            chk(launch(true, k_bph_node<P, PH_SWEEP_G>, gn, bn, st, I, nt, a, b, k));
         bph_elem<P, PH_RES>(I, et, er, 0, kg, ku, st, err);
-        if (ku >= 1) chk(launch(true, k_bph_node<P, PH_GATHERF>, gn, blk, st, I, nt, a, b, 0));
-        else chk(launch(true, k_bph_node<P, PH_GATHER_R>, gn, blk, st, I, nt, a, b, 0));
+        if (ku >= 1) chk(launch(true, k_bph_node<P, PH_GATHERF>, gn, bn, st, I, nt, a, b, 0));
+        else chk(launch(true, k_bph_node<P, PH_GATHER_R>, gn, bn, st, I, nt, a, b, 0));
         for (int k = (ku >= 1 ? 1 : 0); k < ku; ++k)
-            chk(launch(true, k_bph_node<P, PH_SWEEP_U>, gn, blk, st, I, nt, a, b, k));
+            chk(launch(true, k_bph_node<P, PH_SWEEP_U>, gn, bn, st, I, nt, a, b, k));
     }
     bph_elem<P, PH_UPDATE>(I, et, er, 0, kg, ku, st, err);
-    chk(launch(true, k_bph_node<P, PH_FINAL>, gn, blk, st, I, nt, a, b, 0));
+    chk(launch(true, k_bph_node<P, PH_FINAL>, gn, bn, st, I, nt, a, b, 0));
     if (last) chk(launch(true, k_bph_tadv, gi, blk, st, I, ninst));
     return err;
 }

@@ -27,6 +27,7 @@ def main():
     ap.add_argument("--t-end", type=float, default=0.0,
                     help="run to this time instead of a step count (reports the steps taken)")
     ap.add_argument("--autotune", action="store_true", help="batched: tune tile lengths first")
+    ap.add_argument("--form", type=int, default=0, help="batched: 0 persistent launches, 1 phase launches")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--p", type=int, default=0, help="degree (0 = the workload's own)")
     ap.add_argument("--prec", type=int, default=1, help="0 FP64, 1 FP32-mixed")
@@ -113,6 +114,7 @@ def run_batched(a):
         st.set_time(0.0)
         states.append(st)
     b = cgl.Batch(states)
+    b.set_form(a.form)
     if a.autotune:
         b.autotune(2)
     b.step(1)
