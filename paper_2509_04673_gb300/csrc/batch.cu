@@ -36,7 +36,7 @@ struct InstDev {
     ProbDev pr;
     float *u, *un, *g, *g2, *bg, *r, *ud, *ud2, *ER, *EW;
     double *ue, *dte, *ubl, *gam, *nu, *ube, *beta;
-    float *q, *fl, *avg, *cf;
+    float *q, *fl, *avg, *cf, *fht;
     unsigned long long *cnt, *dtbits;
     double *dt, *t, *t_end;
     int p, phys;
@@ -54,6 +54,10 @@ struct BatchSync {
 };
 
 enum { PH_PRE = 0, PH_RES, PH_UPDATE };
+// the phase form's split element phases: the update as facet + element part,
+// the residual as Galerkin part + stabilisation (the single-state kernels'
+// device functions, same bits as PH_UPDATE and PH_RES)
+enum { PH_FACET = 3, PH_UPDATE_EL, PH_RES_W, PH_RES_S };
 enum { PH_GRAD = 0, PH_SWEEP_G, PH_GATHER_R, PH_SWEEP_U, PH_FINAL, PH_GRADF, PH_GATHERF };
 
 constexpr int BT = 128;  // threads per block of the persistent grid
@@ -121,6 +125,22 @@ DEV void elem_phase(int phase, const InstDev& D, int ex, int ey, int e, double& 
             update_at<float, P, Ph>(D.m, D.pr, D.u, ud_final(D, ku), D.ue, D.dte, D.ubl, D.q, D.fl, D.ER, D.cf,
                                     D.avg, D.dt, D.EW, D.ube, D.beta, D.cnt, ex, ey, e);
     }
+}
+
+// a phase known at compile time: the split phases, else elem_phase
+template <int P, int PHASE, class Ph>
+DEV void elem_phase_ct(const InstDev& D, int ex, int ey, int e, double& dte, int kg, int ku) {
+    if constexpr (PHASE == PH_FACET)
+        facet_el_at<P, Ph>(D.m, D.pr, D.u, D.ue, D.dte, D.ubl, D.q, D.fl, D.cf, D.ube, D.fht, D.cnt, ex, ey, e);
+    else if constexpr (PHASE == PH_UPDATE_EL)
+        update_el_at<P, Ph>(D.m, D.pr, D.u, ud_final(D, ku), D.ER, D.cf, D.avg, D.ube, D.fht, D.dt, D.EW, D.beta,
+                            D.cnt, ex, ey, e);
+    else if constexpr (PHASE == PH_RES_W)
+        res_w_at<P, Ph>(D.m, D.pr, D.u, D.EW, ex, ey, e);  // W^e in the increment buffer until PH_UPDATE_EL
+    else if constexpr (PHASE == PH_RES_S)
+        res_s_at<P, Ph>(D.m, D.u, g_final(D, kg), D.gam, D.nu, D.EW, D.ER, ex, ey, e);
+    else
+        elem_phase<P, Ph>(PHASE, D, ex, ey, e, dte, kg, ku);
 }
 
 template <int P>
@@ -289,9 +309,10 @@ static BatchKernel batch_kernel(int p) {
 // of the phase (no grid barrier: the launch boundary orders the phases), so
 // that every phase kernel gets the register budget of its own code. The
 // launches of each degree run on a stream of their own inside the step's
-// graph, so that the degrees overlap; they are programmatic dependent
-// launches (each kernel waits for its predecessor, then lets the next one
-// be scheduled), so a launch's set-up overlaps the tail of the previous one.
+// graph, so that the degrees overlap.  They are plain stream-ordered
+// launches: as programmatic dependent launches, whose early blocks wait on
+// an SM for their predecessor while other degrees' blocks could run there,
+// the 256-instance batch took 3.93 instead of 3.91 ms per step.
 // ---------------------------------------------------------------------------
 // the instance's descriptor (mesh, problem, field pointers) copied into
 // shared memory once per block: the phase bodies read its fields many times,
@@ -319,7 +340,7 @@ __global__ void __launch_bounds__(BT) k_bph_elem(const InstDev* __restrict__ I, 
         const int e = T.begin + threadIdx.x;
         const int nx = D.m.nx;
         const int ey = e / nx, ex = e - ey * nx;
-        elem_phase<P, Ph>(PHASE, D, ex, ey, e, dte, kg, ku);
+        elem_phase_ct<P, PHASE, Ph>(D, ex, ey, e, dte, kg, ku);
     }
     if (PHASE == PH_PRE && first) block_min_to(dte, D.dtbits);
 }
@@ -371,10 +392,10 @@ static void bph_elem(const InstDev* I, const Tile* et, const ElemRanges& er, int
     auto chk = [&](cudaError_t e) {
         if (e != cudaSuccess && err == cudaSuccess) err = e;
     };
-    if (er.ecnt[0]) chk(launch(true, k_bph_elem<P, PHASE, PhysAdv>, dim3(er.ecnt[0]), blk, st, I, et + er.eoff[0], first, kg, ku));
+    if (er.ecnt[0]) chk(launch(false, k_bph_elem<P, PHASE, PhysAdv>, dim3(er.ecnt[0]), blk, st, I, et + er.eoff[0], first, kg, ku));
     if (er.ecnt[1])
-        chk(launch(true, k_bph_elem<P, PHASE, PhysBurgers>, dim3(er.ecnt[1]), blk, st, I, et + er.eoff[1], first, kg, ku));
-    if (er.ecnt[2]) chk(launch(true, k_bph_elem<P, PHASE, PhysKPP>, dim3(er.ecnt[2]), blk, st, I, et + er.eoff[2], first, kg, ku));
+        chk(launch(false, k_bph_elem<P, PHASE, PhysBurgers>, dim3(er.ecnt[1]), blk, st, I, et + er.eoff[1], first, kg, ku));
+    if (er.ecnt[2]) chk(launch(false, k_bph_elem<P, PHASE, PhysKPP>, dim3(er.ecnt[2]), blk, st, I, et + er.eoff[2], first, kg, ku));
 }
 
 template <int P>
@@ -388,21 +409,27 @@ static cudaError_t bph_stage(const InstDev* I, int ninst, const Tile* et, const 
         if (e != cudaSuccess && err == cudaSuccess) err = e;
     };
     bph_elem<P, PH_PRE>(I, et, er, first, kg, ku, st, err);
-    if (first) chk(launch(true, k_bph_dt, gi, blk, st, I, ninst));
+    if (first) chk(launch(false, k_bph_dt, gi, blk, st, I, ninst));
+    // the element phases split in two kernels each, as in the single-state
+    // stage (fewer registers per kernel; measured 4.08 -> 3.94 ms per step of
+    // the 256-instance batch): the facet part and the Galerkin part of the
+    // residual need only u and the pre phase's outputs
+    bph_elem<P, PH_FACET>(I, et, er, 0, kg, ku, st, err);
     if (!mode_lo) {
-        if (kg >= 1) chk(launch(true, k_bph_node<P, PH_GRADF>, gn, bn, st, I, nt, a, b, kg));
-        else chk(launch(true, k_bph_node<P, PH_GRAD>, gn, bn, st, I, nt, a, b, 0));
+        bph_elem<P, PH_RES_W>(I, et, er, 0, kg, ku, st, err);
+        if (kg >= 1) chk(launch(false, k_bph_node<P, PH_GRADF>, gn, bn, st, I, nt, a, b, kg));
+        else chk(launch(false, k_bph_node<P, PH_GRAD>, gn, bn, st, I, nt, a, b, 0));
         for (int k = (kg >= 1 ? 1 : 0); k < kg; ++k)
-            chk(launch(true, k_bph_node<P, PH_SWEEP_G>, gn, bn, st, I, nt, a, b, k));
-        bph_elem<P, PH_RES>(I, et, er, 0, kg, ku, st, err);
-        if (ku >= 1) chk(launch(true, k_bph_node<P, PH_GATHERF>, gn, bn, st, I, nt, a, b, 0));
-        else chk(launch(true, k_bph_node<P, PH_GATHER_R>, gn, bn, st, I, nt, a, b, 0));
+            chk(launch(false, k_bph_node<P, PH_SWEEP_G>, gn, bn, st, I, nt, a, b, k));
+        bph_elem<P, PH_RES_S>(I, et, er, 0, kg, ku, st, err);
+        if (ku >= 1) chk(launch(false, k_bph_node<P, PH_GATHERF>, gn, bn, st, I, nt, a, b, 0));
+        else chk(launch(false, k_bph_node<P, PH_GATHER_R>, gn, bn, st, I, nt, a, b, 0));
         for (int k = (ku >= 1 ? 1 : 0); k < ku; ++k)
-            chk(launch(true, k_bph_node<P, PH_SWEEP_U>, gn, bn, st, I, nt, a, b, k));
+            chk(launch(false, k_bph_node<P, PH_SWEEP_U>, gn, bn, st, I, nt, a, b, k));
     }
-    bph_elem<P, PH_UPDATE>(I, et, er, 0, kg, ku, st, err);
-    chk(launch(true, k_bph_node<P, PH_FINAL>, gn, bn, st, I, nt, a, b, 0));
-    if (last) chk(launch(true, k_bph_tadv, gi, blk, st, I, ninst));
+    bph_elem<P, PH_UPDATE_EL>(I, et, er, 0, kg, ku, st, err);
+    chk(launch(false, k_bph_node<P, PH_FINAL>, gn, bn, st, I, nt, a, b, 0));
+    if (last) chk(launch(false, k_bph_tadv, gi, blk, st, I, ninst));
     return err;
 }
 
@@ -601,6 +628,7 @@ static InstDev inst_of(const cgl_state* s) {
     d.EW = (float*)b.EW;
     d.avg = b.avg;
     d.cf = b.cf;
+    d.fht = (float*)b.fht;
     d.ue = b.ue;
     d.dte = b.dte;
     d.ubl = b.ubl;

@@ -2919,18 +2919,15 @@ __global__ void __launch_bounds__(128, elem_blocks<P, Ph::NC, sizeof(R)>(EK_UPD)
 // FP32-mixed: the update in two kernels.  k_facet needs only u and the
 // outputs of k_pre, so it runs on a second stream beside the g_h and udot
 // kernels; k_update_el then reads its ubar^e and facet terms.  Together they
-// compute what k_update_ev computes, in the same arithmetic.
+// compute what k_update_ev computes, in the same arithmetic.  The bodies are
+// device functions of one element, also run by the batched stage.
 template <int P, class Ph>
-__global__ void __launch_bounds__(128, elem_blocks<P, Ph::NC, 4>(EK_FACET)) k_facet(MeshDev m, ProbDev pr, const float* __restrict__ u,
-                                               const double* __restrict__ ue, double* dte_a,
-                                               const double* __restrict__ ubl, const float* __restrict__ qcap,
-                                               const float* __restrict__ fl_in, float* cf,
-                                               double* __restrict__ ube_out, float* __restrict__ fht,
-                                               unsigned long long* __restrict__ cnt) {
-    pdl_begin();
+DEV void facet_el_at(const MeshDev& m, const ProbDev& pr, const float* __restrict__ u,
+                     const double* __restrict__ ue, double* dte_a, const double* __restrict__ ubl,
+                     const float* __restrict__ qcap, const float* __restrict__ fl_in, float* cf,
+                     double* __restrict__ ube_out, float* __restrict__ fht, unsigned long long* __restrict__ cnt,
+                     int ex, int ey, int e) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
-    int ex, ey, e;
-    if (!elem_of_thread(m, ex, ey, e)) return;
     int nb[4];
 #pragma unroll
     for (int d = 0; d < 4; ++d) nb[d] = neighbour(m, ex, ey, d);
@@ -2965,16 +2962,12 @@ __global__ void __launch_bounds__(128, elem_blocks<P, Ph::NC, 4>(EK_FACET)) k_fa
 }
 
 template <int P, class Ph>
-__global__ void __launch_bounds__(128, elem_blocks<P, Ph::NC, 4>(EK_UPD))
-    k_update_el(MeshDev m, ProbDev pr, const float* __restrict__ u, const float* __restrict__ ud,
-                const double* __restrict__ ue, const double* __restrict__ dte_a, const float* __restrict__ ER,
-                const float* __restrict__ cf, const float* __restrict__ avg, const double* __restrict__ ube,
-                const float* __restrict__ fht, const double* __restrict__ dtp, float* __restrict__ EW,
-                double* __restrict__ beta_out, unsigned long long* __restrict__ cnt) {
-    pdl_begin();
+DEV void update_el_at(const MeshDev& m, const ProbDev& pr, const float* __restrict__ u,
+                      const float* __restrict__ ud, const float* __restrict__ ER, const float* __restrict__ cf,
+                      const float* __restrict__ avg, const double* __restrict__ ube,
+                      const float* __restrict__ fht, const double* __restrict__ dtp, float* __restrict__ EW,
+                      double* __restrict__ beta_out, unsigned long long* __restrict__ cnt, int ex, int ey, int e) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
-    int ex, ey, e;
-    if (!elem_of_thread(m, ex, ey, e)) return;
     float U[NC][N2];
     load_block<float, P, NC>(u, m, ex, ey, U);
     // the float path of element_part takes dt_e and theta from the float
@@ -2992,18 +2985,41 @@ __global__ void __launch_bounds__(128, elem_blocks<P, Ph::NC, 4>(EK_UPD))
                                e);
 }
 
+template <int P, class Ph>
+__global__ void __launch_bounds__(128, elem_blocks<P, Ph::NC, 4>(EK_FACET)) k_facet(MeshDev m, ProbDev pr, const float* __restrict__ u,
+                                               const double* __restrict__ ue, double* dte_a,
+                                               const double* __restrict__ ubl, const float* __restrict__ qcap,
+                                               const float* __restrict__ fl_in, float* cf,
+                                               double* __restrict__ ube_out, float* __restrict__ fht,
+                                               unsigned long long* __restrict__ cnt) {
+    pdl_begin();
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
+    facet_el_at<P, Ph>(m, pr, u, ue, dte_a, ubl, qcap, fl_in, cf, ube_out, fht, cnt, ex, ey, e);
+}
+
+template <int P, class Ph>
+__global__ void __launch_bounds__(128, elem_blocks<P, Ph::NC, 4>(EK_UPD))
+    k_update_el(MeshDev m, ProbDev pr, const float* __restrict__ u, const float* __restrict__ ud,
+                const double* __restrict__ ue, const double* __restrict__ dte_a, const float* __restrict__ ER,
+                const float* __restrict__ cf, const float* __restrict__ avg, const double* __restrict__ ube,
+                const float* __restrict__ fht, const double* __restrict__ dtp, float* __restrict__ EW,
+                double* __restrict__ beta_out, unsigned long long* __restrict__ cnt) {
+    pdl_begin();
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
+    update_el_at<P, Ph>(m, pr, u, ud, ER, cf, avg, ube, fht, dtp, EW, beta_out, cnt, ex, ey, e);
+}
+
 // FP32-mixed: the residual in two kernels.  k_res_w (the Galerkin part W^e,
 // needs only u) runs on the second stream from the start of the stage,
 // beside k_pre and the g_h kernels; k_res_s adds the stabilisation, which
 // needs g_h, gamma_e and nu_e.  W^e passes through the increment buffer,
 // which is free until k_update_el.  Same device functions as k_res_ev.
 template <int P, class Ph>
-__global__ void __launch_bounds__(128) k_res_w(MeshDev m, ProbDev pr, const float* __restrict__ u,
-                                               float* __restrict__ WV) {
-    pdl_begin();
+DEV void res_w_at(const MeshDev& m, const ProbDev& pr, const float* __restrict__ u, float* __restrict__ WV, int ex,
+                  int ey, int e) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
-    int ex, ey, e;
-    if (!elem_of_thread(m, ex, ey, e)) return;
     float U[NC][N2], W[NC][N2];
     load_block<float, P, NC>(u, m, ex, ey, U);
     w_part<float, P, Ph>(m, pr, U, ex, ey, W);
@@ -3014,13 +3030,10 @@ __global__ void __launch_bounds__(128) k_res_w(MeshDev m, ProbDev pr, const floa
 }
 
 template <int P, class Ph>
-__global__ void __launch_bounds__(128) k_res_s(MeshDev m, const float* __restrict__ u, const float* __restrict__ g,
-                                               const double* __restrict__ gam, const double* __restrict__ nu,
-                                               const float* __restrict__ WV, float* __restrict__ ER) {
-    pdl_begin();
+DEV void res_s_at(const MeshDev& m, const float* __restrict__ u, const float* __restrict__ g,
+                  const double* __restrict__ gam, const double* __restrict__ nu, const float* __restrict__ WV,
+                  float* __restrict__ ER, int ex, int ey, int e) {
     constexpr int NC = Ph::NC, N2 = Dim<P>::N2;
-    int ex, ey, e;
-    if (!elem_of_thread(m, ex, ey, e)) return;
     float U[NC][N2], W[NC][N2];
     load_block<float, P, NC>(u, m, ex, ey, U);
 #pragma unroll
@@ -3028,6 +3041,25 @@ __global__ void __launch_bounds__(128) k_res_s(MeshDev m, const float* __restric
 #pragma unroll
         for (int i = 0; i < N2; ++i) W[c][i] = WV[ev_at(m.E, e, i, c, NC)];
     stab_part<float, P, Ph>(m, U, g, gam, nu, W, ER, ex, ey, e);
+}
+
+template <int P, class Ph>
+__global__ void __launch_bounds__(128) k_res_w(MeshDev m, ProbDev pr, const float* __restrict__ u,
+                                               float* __restrict__ WV) {
+    pdl_begin();
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
+    res_w_at<P, Ph>(m, pr, u, WV, ex, ey, e);
+}
+
+template <int P, class Ph>
+__global__ void __launch_bounds__(128) k_res_s(MeshDev m, const float* __restrict__ u, const float* __restrict__ g,
+                                               const double* __restrict__ gam, const double* __restrict__ nu,
+                                               const float* __restrict__ WV, float* __restrict__ ER) {
+    pdl_begin();
+    int ex, ey, e;
+    if (!elem_of_thread(m, ex, ey, e)) return;
+    res_s_at<P, Ph>(m, u, g, gam, nu, WV, ER, ex, ey, e);
 }
 
 // ---------------------------------------------------------------------------
