@@ -46,11 +46,12 @@ struct GradSweepWs {
 // is the same for every component, so it is formed once into registers
 // before the component loop; the halo passes give each thread a fixed
 // column (its x weights stay in registers) and a set of rows.
+// One block of ST_TX x ST_BY threads (thread (tx, ty)) on the tile at (gx0,
+// gy0); ws: GradSweepWs<P, NC>::size floats of shared memory.  k_grad_sweep
+// and the batched stage's phase kernels run it.
 template <int P, int NC>
-__global__ void __launch_bounds__(ST_TX * ST_BY)
-    k_grad_sweep(MeshDev m, const float* __restrict__ u, float* __restrict__ bout, float* __restrict__ gout) {
-    // like k_grad_rhs: runs beside k_pre, waits for it before exiting
-    pdl_trigger();
+DEV void grad_sweep_block(const MeshDev& m, const float* __restrict__ u, float* __restrict__ bout,
+                          float* __restrict__ gout, int gx0, int gy0, int tx, int ty, float* ws) {
     using WS = GradSweepWs<P, NC>;
     constexpr int HX1 = WS::HX1, HY1 = WS::HY1, HX2 = WS::HX2, HY2 = WS::HY2, NW = WS::NW, NCL = WS::NCL;
     constexpr int NT = ST_TX * ST_BY, NJ = ST_TY / ST_BY;
@@ -59,7 +60,6 @@ __global__ void __launch_bounds__(ST_TX * ST_BY)
     constexpr int NXP = (HY2 + RG - 1) / RG;        // x-pass rows per thread
     constexpr int NYP = (HY1 + RG - 1) / RG;        // y-pass rows per thread
     constexpr int NSX = (HY1 + ST_BY - 1) / ST_BY;  // rows of the sweep's x-pass per thread
-    __shared__ float ws[WS::size];
     float(*A)[HX2] = reinterpret_cast<float(*)[HX2]>(ws);
     float(*tC)[HX1] = reinterpret_cast<float(*)[HX1]>(ws + WS::A);
     float(*tM)[HX1] = reinterpret_cast<float(*)[HX1]>(ws + WS::A + HY2 * HX1);
@@ -69,13 +69,12 @@ __global__ void __launch_bounds__(ST_TX * ST_BY)
     float(*WM)[NW] = reinterpret_cast<float(*)[NW]>(ws + WS::A + WS::B + WS::C + WS::D);
     float(*WC)[NW] = reinterpret_cast<float(*)[NW]>(ws + WS::A + WS::B + WS::C + WS::D + NCL * NW);
     const Tab<float>& T = TabSel<float>::t(P);
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ST_TX + tx;
+    const int tid = ty * ST_TX + tx;
     if (tid < NCL * NW) {
         const int cls = tid / NW, k = tid - cls * NW;
         WM[cls][k] = class_weight<float, P, 0>(T, cls, k - P);
         WC[cls][k] = class_weight<float, P, 1>(T, cls, k - P);
     }
-    const int gx0 = blockIdx.x * ST_TX, gy0 = blockIdx.y * ST_TY;
     const float h = m.h_f, h2 = m.h2_f;
     // staged values of u: node offsets (-1 outside the mesh)
     long long aoff[NA];
@@ -210,8 +209,18 @@ __global__ void __launch_bounds__(ST_TX * ST_BY)
             }
         }
     }
+}
+
+template <int P, int NC>
+__global__ void __launch_bounds__(ST_TX * ST_BY)
+    k_grad_sweep(MeshDev m, const float* __restrict__ u, float* __restrict__ bout, float* __restrict__ gout) {
+    // like k_grad_rhs: runs beside k_pre, waits for it before exiting
+    pdl_trigger();
+    __shared__ float ws[GradSweepWs<P, NC>::size];
+    grad_sweep_block<P, NC>(m, u, bout, gout, blockIdx.x * ST_TX, blockIdx.y * ST_TY, threadIdx.x, threadIdx.y, ws);
     pdl_wait();
 }
+
 
 template <int P, int NC>
 struct UdotSweepWs {
