@@ -397,7 +397,8 @@ cgl_status cgl_batch_step(cgl_batch *batch, int32_t nsteps, int64_t *violations)
 cgl_status cgl_batch_step_async(cgl_batch *batch, int32_t nsteps);
 
 /* Launch geometry: the largest persistent grid of the per-degree kernels,
-   block size, tile counts (summed over the degrees), and how
+   its block size (also the phase form's element blocks), tile counts
+   (summed over the degrees), and how
    a step runs: 1 = a captured CUDA graph, 0 = no step has run yet (the
    graph is captured at the first step), -1 = the capture failed and steps
    run as direct cooperative launches (same results; cgl_last_error() then
@@ -410,8 +411,10 @@ cgl_status cgl_batch_info(cgl_batch *batch, int32_t *grid, int32_t *block, int32
    phases separated by bounded grid barriers.  CGL_BATCH_PHASES: the same
    phases (the same device functions, so the same bits) as one launch each,
    one block per tile, so that every phase has the register budget of its
-   own code; each degree's launches run on a stream of their own inside the
-   step's graph, so the degrees overlap.  Changing the form waits for the
+   own code; the element and residual phases are split in two launches each
+   as in the single-state stage, element tiles take 128-thread blocks and
+   node tiles 256-thread blocks; each degree's launches run on a stream of
+   their own inside the step's graph, so the degrees overlap.  Changing the form waits for the
    batch's stream and captures a new graph at the next step.  (Batching is an
    application of the stage; the paper has no counterpart.) */
 #define CGL_BATCH_PERSISTENT 0
