@@ -411,7 +411,7 @@ cgl_status cgl_batch_info(cgl_batch *batch, int32_t *grid, int32_t *block, int32
    phases separated by bounded grid barriers.  CGL_BATCH_PHASES: the same
    phases (the same device functions, so the same bits) as one launch each,
    one block per tile, so that every phase has the register budget of its
-   own code; the element and residual phases are split in two launches each
+   own code; the update and residual phases are split in two launches each
    as in the single-state stage, element tiles take 128-thread blocks and
    node tiles 256-thread blocks; each degree's launches run on a stream of
    their own inside the step's graph, so the degrees overlap.  Changing the form waits for the
