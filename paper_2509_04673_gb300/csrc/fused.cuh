@@ -20,12 +20,13 @@
 
 namespace cgl {
 
-// wrap (gx, gy) on periodic directions; false outside a non-periodic mesh
+// wrap (gx, gy) on periodic directions (wrap_periodic: any number of
+// periods); false outside a non-periodic mesh
 DEV bool wrap_node(const MeshDev& m, int& gx, int& gy) {
     bool in = true;
-    if (m.py) gy = gy < 0 ? gy + m.nny : (gy >= m.nny ? gy - m.nny : gy);
+    if (m.py) gy = wrap_periodic(gy, m.nny);
     else in = gy >= 0 && gy < m.nny;
-    if (m.px) gx = gx < 0 ? gx + m.nnx : (gx >= m.nnx ? gx - m.nnx : gx);
+    if (m.px) gx = wrap_periodic(gx, m.nnx);
     else in = in && gx >= 0 && gx < m.nnx;
     return in;
 }
@@ -264,13 +265,15 @@ __global__ void __launch_bounds__(ST_TX * ST_BY)
         }
         const int rr = r - P, ct = cc - P;
         const bool tile = rr >= 0 && rr < ST_TY && ct >= 0 && ct < ST_TX;
+        // a node of this tile itself, not a wrapped copy of another tile's
+        const bool own = tile && gx0 + ct < m.nnx && gy0 + rr < m.nny;
         const long long node = (long long)gy * m.nnx + gx;
 #pragma unroll
         for (int v = 0; v < NC; ++v) {
             xs[v][r][cc] = in ? s[v] * inv_mi : 0.f;
             if (tile) {
                 rt[v][rr][ct] = in ? s[v] : 0.f;
-                if (in) rout[v * m.NN + node] = s[v];
+                if (in && own) rout[v * m.NN + node] = s[v];
             }
         }
     }
@@ -448,13 +451,15 @@ DEV void udot_sweep_tile(const MeshDev& m, const float* __restrict__ ER, float* 
         }
         const int rr = r - P, ct = cc - P;
         const bool tile = rr >= 0 && rr < ST_TY && ct >= 0 && ct < ST_TX;
+        // a node of this tile itself, not a wrapped copy of another tile's
+        const bool own = tile && gx0 + ct < m.nnx && gy0 + rr < m.nny;
         const long long node = (long long)gy * m.nnx + gx;
 #pragma unroll
         for (int v = 0; v < NC; ++v) {
             xs[v][r][cc] = in ? s[v] * inv_mi : 0.f;
             if (tile) {
                 rt[v][rr][ct] = in ? s[v] : 0.f;
-                if (in) rout[v * m.NN + node] = s[v];
+                if (in && own) rout[v * m.NN + node] = s[v];
             }
         }
     }

@@ -1671,6 +1671,16 @@ DEV R class_weight(const Tab<R>& T, int cls, int off) {
 }
 
 // stage one field (rows gy0-P.., columns gx0-P..) of the tile in shared memory
+// a node index on a periodic direction of n nodes taken into [0, n): one
+// period covers every node of a tile and its halo on meshes at least a tile
+// wide; a narrower mesh (down to one element) takes the remainder, so a
+// staged halo value is always a node of the mesh
+DEV int wrap_periodic(int g, int n) {
+    g = g < 0 ? g + n : (g >= n ? g - n : g);
+    if ((unsigned)g >= (unsigned)n) g = ((g % n) + n) % n;
+    return g;
+}
+
 template <class R, int P, int BY, int TY = ST_TY>
 DEV void stage_tile(const MeshDev& m, const R* __restrict__ x, R (*xs)[ST_TX + 2 * P], int gx0, int gy0, int tid) {
     constexpr int HX = ST_TX + 2 * P, HY = TY + 2 * P;
@@ -1678,9 +1688,9 @@ DEV void stage_tile(const MeshDev& m, const R* __restrict__ x, R (*xs)[ST_TX + 2
         const int r = i / HX, c = i - r * HX;
         int gy = gy0 - P + r, gx = gx0 - P + c;
         bool in = true;
-        if (m.py) gy = gy < 0 ? gy + m.nny : (gy >= m.nny ? gy - m.nny : gy);
+        if (m.py) gy = wrap_periodic(gy, m.nny);
         else in = gy >= 0 && gy < m.nny;
-        if (m.px) gx = gx < 0 ? gx + m.nnx : (gx >= m.nnx ? gx - m.nnx : gx);
+        if (m.px) gx = wrap_periodic(gx, m.nnx);
         else in = in && gx >= 0 && gx < m.nnx;
         // through L2 (ld.global.cg): k_grad_rhs reads u without waiting for
         // the kernel launched just before it

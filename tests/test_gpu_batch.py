@@ -85,6 +85,58 @@ def test_batch_bitwise_equals_single(cgl, form):
     assert info["graph"] == 1, cgl.lib().cgl_last_error()
 
 
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("mode,fl,kg,ku", [(inputs.MODE_LO, S.FL_LIMITED, 1, 1), (inputs.MODE_WENO, S.FL_NONE, 1, 1),
+                                           (inputs.MODE_HO, S.FL_LIMITED, 2, 3), (inputs.MODE_WENO_L, S.FL_LIMITED, 0, 0)])
+def test_batch_modes_bitwise_equal_single(cgl, form, mode, fl, kg, ku):
+    """Every mode, with and without the flux limiter and with other sweep
+    counts (k = 0: the unfused right-hand sides; k > 1: further sweeps),
+    in both forms: the batch gives the bits of the states stepped alone (the
+    low-order mode skips the residual phases)."""
+    cases = _small_instances()
+    for _, prob, _ in cases:
+        prob.mode, prob.flux_limiter, prob.k_g, prob.k_u = mode, fl, kg, ku
+    singles = _states(cgl, cases)
+    ref = []
+    for s in singles:
+        s.step(2)
+        ref.append(s.get_state())
+    states = _states(cgl, cases)
+    b = cgl.Batch(states)
+    b.set_form(form)
+    assert b.step(2) == 0
+    for s, r in zip(states, ref):
+        assert np.array_equal(s.get_state(), r)
+    assert b.info()["graph"] == 1
+
+
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("kg,ku", [(1, 1), (2, 3)])
+def test_batch_narrow_periodic_instances(cgl, form, kg, ku):
+    """Periodic instances narrower than a node tile and its halo (down to one
+    element per side): the fused stencils of the batch wrap every halo node
+    into the mesh, and only the tile that owns a node writes it; results
+    equal the states stepped alone (whose separate stencils need one wrap)."""
+    cases = []
+    for k, (nx, ny, p, flux) in enumerate([(1, 4, 2, 0), (1, 1, 1, 1), (5, 1, 3, 0), (2, 3, 4, 1), (3, 1, 1, 0),
+                                          (1, 2, 3, 1)]):
+        mesh = inputs.Mesh(nx, ny, p, 0.0, nx / ny, 0.0, 1.0)
+        prob = inputs.Problem(flux=flux, vx=0.6 - 0.1 * k, vy=0.35 + 0.05 * k, umin=0.0, umax=1.0, w_lin=0.2,
+                              k_g=kg, k_u=ku)
+        cases.append((mesh, prob, inputs.random_scalar_state(mesh, 700 + k, 0.0, 1.0, 0.5)))
+    singles = _states(cgl, cases)
+    ref = []
+    for s in singles:
+        s.step(2)
+        ref.append(s.get_state())
+    states = _states(cgl, cases)
+    b = cgl.Batch(states)
+    b.set_form(form)
+    assert b.step(2) == 0
+    for s, r in zip(states, ref):
+        assert np.array_equal(s.get_state(), r)
+
+
 def test_batch_times_are_per_instance(cgl):
     cases = _small_instances()[:4]
     states = _states(cgl, cases)
