@@ -22,10 +22,15 @@ def cgl():
     return C
 
 
-@pytest.mark.parametrize("which", ["kpp_2048_q2", "advection_1536_q2_kg2"])
+@pytest.mark.parametrize("which", ["kpp_2048_q2", "advection_1536_q2_kg2", "euler_blast_1024_q2",
+                                   "euler_blast_1024_q2_kg2"])
 def test_fused_sweeps_change_no_bit(cgl, which):
     if which == "kpp_2048_q2":
         mesh, prob, u0 = inputs.kpp_config(2048, 2048, 2)
+    elif which.startswith("euler"):
+        # four components per kernel (the headline's fused kernels); outflow
+        kw = dict(k_g=2, k_u=3) if which.endswith("kg2") else {}
+        mesh, prob, u0 = inputs.euler_blast_config(1024, 1024, 2, **kw)
     else:
         # periodic, two sweeps of each solve (fused first sweep, then a plain one)
         mesh, prob, u0 = inputs.advection_config(1536, 1536, 2, k_g=2, k_u=2)
@@ -34,7 +39,7 @@ def test_fused_sweeps_change_no_bit(cgl, which):
     for opts in (0, cgl.OPT_UNFUSED_SWEEPS):
         d = prob.as_dict()
         d["options"] = opts
-        st = cgl.State(cgl.Mesh(mesh), 1, cgl.FP32_MIXED)
+        st = cgl.State(cgl.Mesh(mesh), u0.shape[0], cgl.FP32_MIXED)
         st.set_problem(d)
         st.set_state(u0)
         st.set_time(0.0)
