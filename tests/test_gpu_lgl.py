@@ -56,6 +56,8 @@ CASES = {
     "euler_p3_outflow_wenol": (Mesh(8, 6, 3, 0.0, 4 / 3, 0.0, 1.0, 1, 1, LGL), 3, 3, 1),
     "euler_p2_fixed_weno": (Mesh(6, 6, 2, 0.0, 1.0, 0.0, 1.0, 2, 2, LGL), 3, 2, 1),
     "euler_p4_periodic_ho_none": (Mesh(5, 4, 4, 0.0, 1.25, 0.0, 1.0, basis=LGL), 3, 1, 0),
+    "adv_p2_1x4_periodic_wenol": (Mesh(1, 4, 2, 0.0, 0.25, 0.0, 1.0, basis=LGL), 0, 3, 1),
+    "burgers_p3_1x1_periodic_weno": (Mesh(1, 1, 3, basis=LGL), 1, 2, 1),
 }
 
 
