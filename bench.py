@@ -180,15 +180,15 @@ def load_peaks():
 NCU_PER_ELEMENT = {
     # profiles/euler_blast_1024_q2_kernel_counts.md (kernel names as cgl_profile reports them:
     # k_pre is k_pre_lo and k_update_ev is k_update_el in this FP32-mixed Euler stage)
-    ("k_sens", HEADLINE): {"warp_inst": 195.4, "fp64_flops": 0.0, "dram_bytes": 69.6},
-    ("k_grad_sweep", HEADLINE): {"warp_inst": 142.91, "fp64_flops": 0.0, "dram_bytes": 138.1},
-    ("k_res_ev", HEADLINE): {"warp_inst": 146.29, "fp64_flops": 0.0, "dram_bytes": 403.2},
-    ("k_update_ev", HEADLINE): {"warp_inst": 70.4, "fp64_flops": 4.02, "dram_bytes": 545.8},
-    ("k_facet", HEADLINE): {"warp_inst": 79.32, "fp64_flops": 12.051, "dram_bytes": 248.5},
-    ("k_pre", HEADLINE): {"warp_inst": 49.71, "fp64_flops": 22.0, "dram_bytes": 218.3},
-    ("k_udot_sweep", HEADLINE): {"warp_inst": 82.08, "fp64_flops": 0.0, "dram_bytes": 233.3},
+    ("k_sens", HEADLINE): {"warp_inst": 195.41, "fp64_flops": 0.0, "dram_bytes": 69.6},
+    ("k_grad_sweep", HEADLINE): {"warp_inst": 142.62, "fp64_flops": 0.0, "dram_bytes": 138.1},
+    ("k_res_ev", HEADLINE): {"warp_inst": 146.29, "fp64_flops": 0.0, "dram_bytes": 403.1},
+    ("k_update_ev", HEADLINE): {"warp_inst": 70.4, "fp64_flops": 4.024, "dram_bytes": 545.6},
+    ("k_facet", HEADLINE): {"warp_inst": 79.32, "fp64_flops": 12.051, "dram_bytes": 248.4},
+    ("k_pre", HEADLINE): {"warp_inst": 49.71, "fp64_flops": 22.0, "dram_bytes": 218.2},
+    ("k_udot_sweep", HEADLINE): {"warp_inst": 81.14, "fp64_flops": 0.0, "dram_bytes": 233.1},
     ("k_final", HEADLINE): {"warp_inst": 37.17, "fp64_flops": 0.0, "dram_bytes": 316.9},
-    ("k_avg", HEADLINE): {"warp_inst": 21.69, "fp64_flops": 0.0, "dram_bytes": 98.3},
+    ("k_avg", HEADLINE): {"warp_inst": 21.69, "fp64_flops": 0.0, "dram_bytes": 98.4},
 }
 
 SM_COUNT_GB300 = 152
