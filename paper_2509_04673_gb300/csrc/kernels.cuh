@@ -1671,10 +1671,10 @@ DEV R class_weight(const Tab<R>& T, int cls, int off) {
 }
 
 // stage one field (rows gy0-P.., columns gx0-P..) of the tile in shared memory
-// a node index on a periodic direction of n nodes taken into [0, n): one
-// period covers every node of a tile and its halo on meshes at least a tile
-// wide; a narrower mesh (down to one element) takes the remainder, so a
-// staged halo value is always a node of the mesh
+// a node index on a periodic direction of n nodes taken into [0, n) (the
+// fused stencils, halo 2p): one period covers every node of a tile and its
+// halo on meshes at least a tile wide; a narrower mesh (down to one element)
+// takes the remainder, so a staged halo value is always a node of the mesh
 DEV int wrap_periodic(int g, int n) {
     g = g < 0 ? g + n : (g >= n ? g - n : g);
     if ((unsigned)g >= (unsigned)n) g = ((g % n) + n) % n;
@@ -1687,11 +1687,13 @@ DEV void stage_tile(const MeshDev& m, const R* __restrict__ x, R (*xs)[ST_TX + 2
     for (int i = tid; i < HX * HY; i += ST_TX * BY) {
         const int r = i / HX, c = i - r * HX;
         int gy = gy0 - P + r, gx = gx0 - P + c;
-        bool in = true;
-        if (m.py) gy = wrap_periodic(gy, m.nny);
-        else in = gy >= 0 && gy < m.nny;
-        if (m.px) gx = wrap_periodic(gx, m.nnx);
-        else in = in && gx >= 0 && gx < m.nnx;
+        // one period on periodic directions: a halo of p never needs more on a
+        // mesh of at least one element (p nodes) per side; a position still
+        // outside after it (two periods away, on a mesh narrower than the
+        // tile) feeds no output of the tile and is not read
+        if (m.py) gy = gy < 0 ? gy + m.nny : (gy >= m.nny ? gy - m.nny : gy);
+        if (m.px) gx = gx < 0 ? gx + m.nnx : (gx >= m.nnx ? gx - m.nnx : gx);
+        const bool in = (unsigned)gy < (unsigned)m.nny && (unsigned)gx < (unsigned)m.nnx;
         // through L2 (ld.global.cg): k_grad_rhs reads u without waiting for
         // the kernel launched just before it
         xs[r][c] = in ? __ldcg(&x[(long long)gy * m.nnx + gx]) : R(0);
