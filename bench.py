@@ -178,17 +178,18 @@ def load_peaks():
 # dfma counted twice as flops) and DRAM bytes read + written.  None where the
 # kernel changed after the capture.
 NCU_PER_ELEMENT = {
-    # profiles/euler_blast_1024_q2_kernel_counts.md (kernel names as cgl_profile reports them:
+    # profiles/euler_blast_1024_q2_kernel_counts.md and, for the shared-memory wavefronts,
+    # profiles/euler_blast_1024_q2_shared_wavefronts.md (kernel names as cgl_profile reports them:
     # k_pre is k_pre_lo and k_update_ev is k_update_el in this FP32-mixed Euler stage)
-    ("k_sens", HEADLINE): {"warp_inst": 195.41, "fp64_flops": 0.0, "dram_bytes": 69.6},
-    ("k_grad_sweep", HEADLINE): {"warp_inst": 142.62, "fp64_flops": 0.0, "dram_bytes": 138.1},
-    ("k_res_ev", HEADLINE): {"warp_inst": 146.29, "fp64_flops": 0.0, "dram_bytes": 403.1},
-    ("k_update_ev", HEADLINE): {"warp_inst": 70.4, "fp64_flops": 4.024, "dram_bytes": 545.6},
-    ("k_facet", HEADLINE): {"warp_inst": 79.32, "fp64_flops": 12.051, "dram_bytes": 248.4},
-    ("k_pre", HEADLINE): {"warp_inst": 49.71, "fp64_flops": 22.0, "dram_bytes": 218.2},
-    ("k_udot_sweep", HEADLINE): {"warp_inst": 81.14, "fp64_flops": 0.0, "dram_bytes": 233.1},
-    ("k_final", HEADLINE): {"warp_inst": 37.17, "fp64_flops": 0.0, "dram_bytes": 316.9},
-    ("k_avg", HEADLINE): {"warp_inst": 21.69, "fp64_flops": 0.0, "dram_bytes": 98.4},
+    ("k_sens", HEADLINE): {"warp_inst": 195.41, "fp64_flops": 0.0, "dram_bytes": 69.6, "shared_wavefronts": 3.38},
+    ("k_grad_sweep", HEADLINE): {"warp_inst": 142.62, "fp64_flops": 0.0, "dram_bytes": 138.1, "shared_wavefronts": 46.82},
+    ("k_res_ev", HEADLINE): {"warp_inst": 146.29, "fp64_flops": 0.0, "dram_bytes": 403.1, "shared_wavefronts": 0.12},
+    ("k_update_ev", HEADLINE): {"warp_inst": 70.4, "fp64_flops": 4.024, "dram_bytes": 545.6, "shared_wavefronts": 0.16},
+    ("k_facet", HEADLINE): {"warp_inst": 79.32, "fp64_flops": 12.051, "dram_bytes": 248.4, "shared_wavefronts": 0.06},
+    ("k_pre", HEADLINE): {"warp_inst": 49.71, "fp64_flops": 22.0, "dram_bytes": 218.2, "shared_wavefronts": 0.15},
+    ("k_udot_sweep", HEADLINE): {"warp_inst": 81.14, "fp64_flops": 0.0, "dram_bytes": 233.1, "shared_wavefronts": 13.66},
+    ("k_final", HEADLINE): {"warp_inst": 37.17, "fp64_flops": 0.0, "dram_bytes": 316.9, "shared_wavefronts": 0.66},
+    ("k_avg", HEADLINE): {"warp_inst": 21.69, "fp64_flops": 0.0, "dram_bytes": 98.4, "shared_wavefronts": 0.06},
 }
 
 SM_COUNT_GB300 = 152
@@ -697,9 +698,17 @@ def run_gpu(args):
             roofs["issue"] = {"achieved": round(ipk / 1e9, 1), "peak": round(peak_i / 1e9, 1), "unit": "Ginst/s",
                               "frac": round(ipk / peak_i, 4),
                               "peak_source": "152 SMs x 4 warp instructions per clock x median SM clock"}
+        if ncu.get("shared_wavefronts") is not None:
+            # the shared-memory data stage moves one 128 B wavefront per SM per clock
+            swr = ncu["shared_wavefronts"] * E_h / (avg_ms * 1e-3)
+            peak_s = SM_COUNT_GB300 * sm_hz
+            roofs["shared"] = {"achieved": round(swr / 1e9, 1), "peak": round(peak_s / 1e9, 1),
+                               "unit": "Gwavefronts/s", "frac": round(swr / peak_s, 4),
+                               "peak_source": "152 SMs x 1 shared-memory wavefront (128 B) per clock x median SM "
+                                              "clock (an on-chip pipe: reported as bound alu)"}
     bound = max(roofs, key=lambda k: roofs[k]["frac"]) if roofs else "hbm"
     main = roofs.get(bound, {})
-    roof.update({"bound": {"hbm": "hbm", "fp64": "alu", "issue": "alu"}[bound], "roof": bound,
+    roof.update({"bound": {"hbm": "hbm", "fp64": "alu", "issue": "alu", "shared": "alu"}[bound], "roof": bound,
                  "achieved": main.get("achieved"), "peak": main.get("peak"), "unit": main.get("unit"),
                  "frac": main.get("frac"), "traffic": traffic, "roofs": roofs})
     meth_h = roofline_entry(HEADLINE, h32, 4)
